@@ -1,0 +1,189 @@
+"""Seeded synthetic inputs shared by the CUDA path and the CPU oracle.
+
+This module only *draws* inputs: particle phase-space coordinates, particle ids,
+reference-particle presets and lattice element lists.  It holds none of the
+tracking arithmetic (maps, deposition, field solve, kicks); both the oracle and
+the CUDA path receive the same bytes from here.
+
+Random numbers come from numpy's Philox4x32-10 counter-based bit generator
+(Salmon et al., SC'11) keyed by the seed, so every array is reproducible on any
+host.
+
+Phase-space coordinates follow the ImpactX convention used throughout the
+package (paper §ImpactX, Listing 1): x, y [m]; px, py = transverse momentum over
+the reference momentum; t = c * (arrival-time lag) [m]; pt = -(energy deviation)
+/ (reference momentum * c).  Arrays are returned as a (6, n) float64 C-contiguous
+block in the order (x, px, y, py, t, pt), plus int64 ids 0..n-1.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Sequence
+
+import numpy as np
+
+# element type codes (shared with the C-ABI header's BX_DRIFT / BX_QUAD / BX_SBEND)
+DRIFT, QUAD, SBEND = 0, 1, 2
+
+# rest energies, CODATA 2018 [MeV]
+MASS_PROTON_MEV = 938.27208816
+MASS_ELECTRON_MEV = 0.51099895000
+
+
+@dataclass(frozen=True)
+class Element:
+    """One lattice element: type code, length [m], focusing strength k [1/m^2]
+    (quadrupole only; k > 0 focuses x), total bend angle [rad] (sector bend only)
+    and the number of slices (space-charge kicks) through it."""
+    kind: int
+    length: float
+    k: float = 0.0
+    angle: float = 0.0
+    nslice: int = 1
+
+
+def drift(length, nslice=1):
+    return Element(DRIFT, float(length), 0.0, 0.0, int(nslice))
+
+
+def quad(length, k, nslice=1):
+    return Element(QUAD, float(length), float(k), 0.0, int(nslice))
+
+
+def sbend(length, angle, nslice=1):
+    return Element(SBEND, float(length), 0.0, float(angle), int(nslice))
+
+
+def fodo_cell(nslice, kf=1.0, kd=-1.0):
+    """The FODO cell of the paper's Listing 1: drift 0.25 m, QF (1 m, k=kf),
+    drift 0.5 m, QD (1 m, k=kd), drift 0.25 m."""
+    return [drift(0.25, nslice), quad(1.0, kf, nslice), drift(0.5, nslice),
+            quad(1.0, kd, nslice), drift(0.25, nslice)]
+
+
+def fodo_lattice(periods, nslice, kf=1.0, kd=-1.0):
+    return fodo_cell(nslice, kf, kd) * int(periods)
+
+
+def chicane_lattice(nslice=50):
+    """Four sector bends (L=0.5 m, +-0.1 rad) separated by 1 m drifts, preceded
+    by two matching quadrupoles (L=0.5 m, k=+-0.5 /m^2)."""
+    return [quad(0.5, 0.5, nslice), quad(0.5, -0.5, nslice),
+            sbend(0.5, 0.1, nslice), drift(1.0, nslice),
+            sbend(0.5, -0.1, nslice), drift(1.0, nslice),
+            sbend(0.5, -0.1, nslice), drift(1.0, nslice),
+            sbend(0.5, 0.1, nslice), drift(1.0, nslice)]
+
+
+def count_kicks(lattice: Sequence[Element]) -> int:
+    return int(sum(e.nslice for e in lattice))
+
+
+def lattice_array(lattice: Sequence[Element]) -> np.ndarray:
+    """Lattice as a (m, 5) float64 table: kind, length, k, angle, nslice."""
+    return np.array([[e.kind, e.length, e.k, e.angle, e.nslice] for e in lattice],
+                    dtype=np.float64).reshape(-1, 5)
+
+
+@dataclass(frozen=True)
+class Species:
+    """Reference particle: rest energy and kinetic energy [MeV], charge sign."""
+    mass_MeV: float
+    kinetic_MeV: float
+    charge_sign: float
+
+
+PROTON_2GEV = Species(MASS_PROTON_MEV, 2000.0, +1.0)
+PROTON_1GEV = Species(MASS_PROTON_MEV, 1000.0, +1.0)
+ELECTRON_500MEV = Species(MASS_ELECTRON_MEV, 500.0, -1.0)
+ELECTRON_2GEV = Species(MASS_ELECTRON_MEV, 2000.0, -1.0)
+
+SIGMAS_DEFAULT = (1e-3, 1e-4, 1e-3, 1e-4, 1e-3, 1e-4)  # x, px, y, py, t, pt
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=int(seed)))
+
+
+def gaussian6d(n: int, sigmas=SIGMAS_DEFAULT, seed: int = 0) -> np.ndarray:
+    """Uncorrelated 6D Gaussian bunch, zero mean, given rms per coordinate."""
+    g = _rng(seed).standard_normal((6, int(n)))
+    return np.ascontiguousarray(g * np.asarray(sigmas, dtype=np.float64)[:, None])
+
+
+def gaussian_with_halo(n: int, sigmas=SIGMAS_DEFAULT, halo_fraction=0.2,
+                       halo_semi_axes_in_sigma=3.0, seed: int = 0) -> np.ndarray:
+    """Gaussian core plus a halo whose positions (x, y, t) are uniform in the
+    ellipsoid with semi-axes `halo_semi_axes_in_sigma` * sigma and whose momenta
+    are Gaussian.  The last round(halo_fraction * n) particles are the halo."""
+    n = int(n)
+    nh = int(round(halo_fraction * n))
+    rng = _rng(seed)
+    out = rng.standard_normal((6, n)) * np.asarray(sigmas, dtype=np.float64)[:, None]
+    if nh > 0:
+        d = rng.standard_normal((3, nh))
+        d /= np.sqrt((d * d).sum(axis=0))
+        r = rng.random(nh) ** (1.0 / 3.0)
+        for row, ax in zip((0, 2, 4), range(3)):
+            out[row, n - nh:] = halo_semi_axes_in_sigma * sigmas[row] * r * d[ax]
+    return np.ascontiguousarray(out)
+
+
+def uniform_lattice_points(n_side: int, semi_axes=(1e-3, 1e-3, 1e-3)):
+    """Deterministic points of a cubic lattice clipped to the ellipsoid with the
+    given semi-axes (x, y, t); momenta zero.  Used for closed-form field checks."""
+    s = (np.arange(n_side) + 0.5) / n_side * 2.0 - 1.0
+    gx, gy, gz = np.meshgrid(s, s, s, indexing="ij")
+    m = gx * gx + gy * gy + gz * gz <= 1.0
+    out = np.zeros((6, int(m.sum())))
+    out[0] = gx[m] * semi_axes[0]
+    out[2] = gy[m] * semi_axes[1]
+    out[4] = gz[m] * semi_axes[2]
+    return out
+
+
+def ids(n: int) -> np.ndarray:
+    return np.arange(int(n), dtype=np.int64)
+
+
+@dataclass
+class Workload:
+    """A named tracking workload: bunch, reference particle, lattice, grid."""
+    name: str
+    n_particles: int
+    species: Species
+    bunch_charge_C: float
+    lattice: List[Element]
+    n_grid: int
+    seed: int = 0
+    halo: bool = False
+    sigmas: tuple = field(default=SIGMAS_DEFAULT)
+
+    @property
+    def kicks(self) -> int:
+        return count_kicks(self.lattice)
+
+    def particles(self, n: int | None = None) -> np.ndarray:
+        n = self.n_particles if n is None else int(n)
+        if self.halo:
+            return gaussian_with_halo(n, self.sigmas, seed=self.seed)
+        return gaussian6d(n, self.sigmas, seed=self.seed)
+
+
+def workload(name: str) -> Workload:
+    """The three tracking workloads:
+
+    fodo_1e4_32  : 1e4 particles, 2 GeV p, FODO x10, 5 kicks/element (250), 32^3, 1 nC
+    fodo_1e6_64  : 1e6 particles (20% halo), 1 GeV p, FODO x50, 4 kicks/element
+                   (1000), 64^3, 10 nC
+    chicane_25e6_128 : 2.5e7 particles, 500 MeV e-, quads + 4-bend chicane,
+                   50 kicks/element (500), 128^3
+    """
+    if name == "fodo_1e4_32":
+        return Workload(name, 10_000, PROTON_2GEV, 1e-9, fodo_lattice(10, 5), 32)
+    if name == "fodo_1e6_64":
+        return Workload(name, 1_000_000, PROTON_1GEV, 10e-9, fodo_lattice(50, 4), 64,
+                        halo=True)
+    if name == "chicane_25e6_128":
+        return Workload(name, 25_000_000, ELECTRON_500MEV, 1e-9, chicane_lattice(50), 128)
+    raise KeyError(name)
