@@ -1,0 +1,206 @@
+/*
+ * beamtrack.h - C ABI of the B300-native space-charge tracking step.
+ *
+ * One s-step of ImpactX-style beam tracking (arXiv:2208.02382, section
+ * "ImpactX" and its subsection "Model Assumptions"): macroparticles in 6D
+ * phase space relative to a reference particle are pushed through linear
+ * symplectic element maps, and space charge enters as a split-operator kick:
+ * charge deposition to a 3D grid in the bunch rest frame, an open-boundary
+ * Poisson solve, field gather and momentum kick.  The paper prints no
+ * formulas; each call below names the reading it implements.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Phase space (x, px, y, py, t, pt): x, y [m]; px, py = transverse momentum
+ *   over the reference momentum; t = c * (arrival-time lag) [m];
+ *   pt = -(energy deviation) / (reference momentum * c).
+ * - Particle data are six device arrays of n doubles (structure of arrays),
+ *   owned by the caller.  The library never allocates, frees or keeps
+ *   particle memory; it may reorder particles (all six arrays and `id`
+ *   together) to bin them by grid cell.
+ * - Grid arrays are owned by the caller; node (i, j, l) of an N^3 grid sits at
+ *   flat index i + N*(j + N*l) (x fastest).
+ * - Rest frame: X = x, Y = y, Z = -beta*gamma*t (Model Assumptions: linear
+ *   boost of the reference particle).
+ * - Every call is asynchronous on `stream` (a cudaStream_t, or NULL for the
+ *   legacy default stream) unless stated.  Argument errors are detected on
+ *   the host before any launch and returned at once; device-side errors
+ *   (a non-finite coordinate, a timed-out device wait) are recorded in a
+ *   device status word and returned by the next call that reads it
+ *   (bx_sync, bx_moments) or by bx_sync.
+ * - Status codes are the BX_* values below; bx_last_error() gives text.
+ * - No call throws; no C++ exception crosses this ABI.
+ */
+#ifndef BEAMTRACK_H
+#define BEAMTRACK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define BX_OK 0
+#define BX_BAD_ARG 1        /* null pointer, size out of range, bad element */
+#define BX_NONFINITE 2      /* NaN or Inf found in particle coordinates     */
+#define BX_OUT_OF_MEMORY 3  /* a device allocation of the context failed    */
+#define BX_DEVICE_TIMEOUT 4 /* a bounded device-side wait gave up           */
+#define BX_CUDA 5           /* a CUDA runtime call failed                   */
+
+/* ---- element types (Listing 1: elements.Drift, elements.Quad; sector bend
+ *      from the paper's chicane benchmark) ---------------------------------- */
+#define BX_DRIFT 0
+#define BX_QUAD 1
+#define BX_SBEND 2
+
+typedef struct bx_ctx bx_ctx;
+
+/* Options of a context.
+ * n_grid      : nodes per dimension N of the charge/potential grid; a power
+ *               of two in [8, 256].  The Poisson solve runs on the doubled
+ *               (2N)^3 grid.
+ * shape_order : particle shape (Listing 1 set_particle_shape); 1 (CIC) only.
+ */
+typedef struct {
+    int32_t n_grid;
+    int32_t shape_order;
+    int32_t reserved[6];
+} bx_options;
+
+/* A bunch.  coord[0..5] = x, px, y, py, t, pt: device pointers to n doubles
+ * each, 8-byte aligned.  id: device pointer to n int64 ids, or NULL (then
+ * particles are not reordered).  charge_sign: +1 or -1 (species);
+ * bunch_charge_C: |Q| of the whole bunch [C] (Listing 1 add_particles);
+ * mass_MeV, kinetic_MeV: reference particle rest and kinetic energy
+ * (Listing 1 set_energy_MeV, read as kinetic).  n may be 0. */
+typedef struct {
+    double *coord[6];
+    int64_t *id;
+    int64_t n;
+    double charge_sign;
+    double bunch_charge_C;
+    double mass_MeV;
+    double kinetic_MeV;
+} bx_beam;
+
+/* One lattice element (Listing 1: Drift(ds, nslice), Quad(ds, k, nslice)).
+ * length [m] > 0; k [1/m^2] (quadrupole; k > 0 focuses x); angle [rad]
+ * (sector bend, total over the element); nslice >= 1 slices, one
+ * space-charge kick per slice. */
+typedef struct {
+    int32_t type;
+    int32_t nslice;
+    double length;
+    double k;
+    double angle;
+} bx_element;
+
+/* A lattice in HOST memory.  space_charge: 0 = maps only
+ * (Listing 1 set_space_charge(False)), 1 = split-operator kicks. */
+typedef struct {
+    const bx_element *elements;
+    int32_t count;
+    int32_t space_charge;
+} bx_lattice;
+
+/* A grid.  n must equal the context's n_grid.
+ * use_box = 1: the box [lo, hi) given here is used as is;
+ * use_box = 0: the context's box rule is applied (see bx_deposit) and the
+ *              chosen box is written back to lo/hi/h.
+ * h = (hi - lo)/(n - 1) per dimension (output).
+ * rho: device, n^3 doubles [C/m^3].  phi: device, (n+2)^3 doubles [V],
+ * holding nodes -1..n per dimension (array index k = node k - 1). */
+typedef struct {
+    int32_t n;
+    int32_t use_box;
+    double lo[3];
+    double hi[3];
+    double h[3];
+    double *rho;
+    double *phi;
+} bx_grid;
+
+/* Create a context on the current CUDA device.  The context owns its device
+ * scratch (fixed-point charge accumulators, FFT work buffers, the Green's
+ * function spectrum, reduction buffers, status word); it holds the grid box
+ * and the kick counter between calls.  Returns BX_BAD_ARG for a bad n_grid or
+ * shape_order, BX_OUT_OF_MEMORY / BX_CUDA on allocation failure. */
+int32_t bx_create(bx_ctx **out, const bx_options *opt);
+
+/* Destroy a context (synchronises the device first).  NULL is allowed. */
+int32_t bx_destroy(bx_ctx *ctx);
+
+/* Forget the box, the Green's function, the kick counter and the regrid log. */
+int32_t bx_reset(bx_ctx *ctx);
+
+/* Track the bunch through slices [first_kick, first_kick + nkicks) of the
+ * lattice's slice schedule (Listing 1 sim.evolve(); Model Assumptions:
+ * map-based split-operator step).  Reading: each slice of length
+ * ds = length/nslice is map(ds/2), space-charge kick over ds, map(ds/2);
+ * adjacent half-maps inside one call are merged into one map.  Before each
+ * kick the box rule runs: regrid when a particle lies outside [lo, hi) or an
+ * extent fell below half the box; the new box is centred on the bunch with
+ * half-width 0.55 * extent; the Green's function is rebuilt when h changes.
+ * The bunch is left at a slice boundary.  nkicks = -1 tracks to the end.
+ * BX_BAD_ARG if first_kick/nkicks fall outside the schedule or an element is
+ * invalid.  Non-finite coordinates are reported as BX_NONFINITE by bx_sync. */
+int32_t bx_track(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lattice,
+                 int64_t first_kick, int64_t nkicks, void *stream);
+
+/* Charge deposition (ABLASTR charge deposition reused by ImpactX; Listing 1
+ * particle shape 1 = CIC): rho[node] = q * sum_p wx*wy*wz / (hx*hy*hz) over
+ * the 8 nodes of each particle's cell, q = charge_sign*bunch_charge_C/n,
+ * u = (X - lo)/h, i = floor(u) clamped to [0, n-2], weights (1-f, f).
+ * With grid->use_box = 0 the context's box rule picks (and remembers) the
+ * box.  The result does not depend on particle order (fixed-point
+ * accumulation). */
+int32_t bx_deposit(bx_ctx *ctx, const bx_beam *beam, bx_grid *grid, void *stream);
+
+/* Open-boundary Poisson solve in the rest frame (Model Assumptions; ABLASTR
+ * Poisson solve): phi = G (*) rho as the aperiodic convolution computed on the
+ * zero-padded (2n)^3 grid by FFT (Hockney), with G the cell-integrated
+ * Green's function (Qiang et al. 2006) built in double-double precision for
+ * the grid's h.  Reads grid->rho and grid->h, writes grid->phi on nodes
+ * -1..n. */
+int32_t bx_solve(bx_ctx *ctx, bx_grid *grid, void *stream);
+
+/* Field gather and momentum kick over a slice ds > 0 (Model Assumptions:
+ * electrostatic rest-frame field).  E = -grad phi by centred differences on
+ * the nodes, interpolated with the same CIC weights as the deposit, then
+ * dpx = s*Ex*ds/(mc^2[eV]*(beta gamma)^2), dpy likewise,
+ * dpt = -s*Ez*ds/(mc^2[eV]*beta gamma).  Uses grid->lo/h and grid->phi. */
+int32_t bx_gather_kick(bx_ctx *ctx, bx_beam *beam, const bx_grid *grid, double ds,
+                       void *stream);
+
+/* Beam statistics (ABLASTR beam statistics; FODO/IOTA benchmarks check second
+ * moments): out_device[0..5] = means, out_device[6..26] = the 21 centred
+ * second moments in row-major upper-triangle order (00,01,..,05,11,..,55).
+ * Two passes, fixed reduction order (bitwise reproducible). */
+int32_t bx_moments(bx_ctx *ctx, const bx_beam *beam, double *out_device, void *stream);
+
+/* Integrated Green's function table used by bx_solve: out_device receives
+ * (n+1)^3 doubles G[(c*(n+1) + b)*(n+1) + a] for offsets a, b, c = 0..n cells
+ * at cell size h[3] [m], in V*m^3/C (the potential at the origin per unit
+ * charge density filling the cell at that offset). */
+int32_t bx_green_table(bx_ctx *ctx, const double h[3], double *out_device, void *stream);
+
+/* Copy up to `cap` entries of the regrid log (kick indices, counted from the
+ * context's creation or last reset, where the box rule made a new box) into
+ * host memory; *count receives the total number logged.  Synchronous. */
+int32_t bx_regrid_log(bx_ctx *ctx, int64_t *out_host, int64_t cap, int64_t *count);
+
+/* The current box (host copy; synchronous).  Returns BX_BAD_ARG if no box yet. */
+int32_t bx_get_box(bx_ctx *ctx, double lo[3], double hi[3], double h[3]);
+
+/* Wait for the stream and return the device status word (then clear it). */
+int32_t bx_sync(bx_ctx *ctx, void *stream);
+
+/* Text of the last error of this context (or of bx_create when ctx is NULL). */
+const char *bx_last_error(const bx_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEAMTRACK_H */

@@ -1,0 +1,6 @@
+"""B300-native space-charge tracking step (arXiv:2208.02382, ImpactX v22.08).
+
+The compute path is libbeamtrack.so (hand-written sm_103a CUDA kernels behind
+the C ABI of include/beamtrack.h); `api` is its thin Python binding.
+"""
+from .api import Beam, Grid, Species, Tracker, lattice_struct  # noqa: F401

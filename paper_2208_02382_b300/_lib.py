@@ -1,0 +1,84 @@
+"""ctypes declarations of the C ABI in include/beamtrack.h (argument
+marshalling only; every computation runs in libbeamtrack.so)."""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_void_p
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbeamtrack.so")
+
+BX_OK, BX_BAD_ARG, BX_NONFINITE, BX_OUT_OF_MEMORY, BX_DEVICE_TIMEOUT, BX_CUDA = range(6)
+BX_DRIFT, BX_QUAD, BX_SBEND = 0, 1, 2
+
+
+class bx_options(ctypes.Structure):
+    _fields_ = [("n_grid", c_int32), ("shape_order", c_int32), ("reserved", c_int32 * 6)]
+
+
+class bx_beam(ctypes.Structure):
+    _fields_ = [("coord", c_void_p * 6), ("id", c_void_p), ("n", c_int64),
+                ("charge_sign", c_double), ("bunch_charge_C", c_double),
+                ("mass_MeV", c_double), ("kinetic_MeV", c_double)]
+
+
+class bx_element(ctypes.Structure):
+    _fields_ = [("type", c_int32), ("nslice", c_int32), ("length", c_double),
+                ("k", c_double), ("angle", c_double)]
+
+
+class bx_lattice(ctypes.Structure):
+    _fields_ = [("elements", POINTER(bx_element)), ("count", c_int32),
+                ("space_charge", c_int32)]
+
+
+class bx_grid(ctypes.Structure):
+    _fields_ = [("n", c_int32), ("use_box", c_int32), ("lo", c_double * 3),
+                ("hi", c_double * 3), ("h", c_double * 3), ("rho", c_void_p),
+                ("phi", c_void_p)]
+
+
+# name -> (restype, argtypes), one entry per declaration in include/beamtrack.h
+SIGNATURES = {
+    "bx_create": (c_int32, [POINTER(c_void_p), POINTER(bx_options)]),
+    "bx_destroy": (c_int32, [c_void_p]),
+    "bx_reset": (c_int32, [c_void_p]),
+    "bx_track": (c_int32, [c_void_p, POINTER(bx_beam), POINTER(bx_lattice), c_int64, c_int64,
+                           c_void_p]),
+    "bx_deposit": (c_int32, [c_void_p, POINTER(bx_beam), POINTER(bx_grid), c_void_p]),
+    "bx_solve": (c_int32, [c_void_p, POINTER(bx_grid), c_void_p]),
+    "bx_gather_kick": (c_int32, [c_void_p, POINTER(bx_beam), POINTER(bx_grid), c_double,
+                                 c_void_p]),
+    "bx_moments": (c_int32, [c_void_p, POINTER(bx_beam), c_void_p, c_void_p]),
+    "bx_green_table": (c_int32, [c_void_p, POINTER(c_double), c_void_p, c_void_p]),
+    "bx_regrid_log": (c_int32, [c_void_p, POINTER(c_int64), c_int64, POINTER(c_int64)]),
+    "bx_get_box": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_double), POINTER(c_double)]),
+    "bx_sync": (c_int32, [c_void_p, c_void_p]),
+    "bx_last_error": (c_char_p, [c_void_p]),
+}
+
+_LIB = None
+
+
+class BeamtrackError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"beamtrack error {code}: {msg}")
+        self.code = code
+
+
+def load(path: str = LIB_PATH):
+    """Load libbeamtrack.so; raise (never fall back) if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libbeamtrack.so not built ({path}); run "
+                          "`python -m paper_2208_02382_b300.build`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib

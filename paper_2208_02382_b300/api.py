@@ -1,0 +1,197 @@
+"""Python binding of libbeamtrack: the same calls as the C ABI, taking torch
+CUDA tensors for device memory and torch's current stream.  Argument
+marshalling only; every step of the tracking path runs in the library's CUDA
+kernels (there is no CPU fallback)."""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Sequence
+
+import torch
+
+from . import _lib as L
+
+
+def _check(lib, ctx, rc):
+    if rc != L.BX_OK:
+        msg = lib.bx_last_error(ctx)
+        raise L.BeamtrackError(rc, msg.decode() if msg else "")
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@dataclass
+class Species:
+    mass_MeV: float
+    kinetic_MeV: float
+    charge_sign: float
+
+
+class Beam:
+    """A bunch on the device: `coords` is a (6, n) float64 CUDA tensor
+    (x, px, y, py, t, pt), `ids` an int64 CUDA tensor of length n."""
+
+    def __init__(self, coords: torch.Tensor, species: Species, bunch_charge_C: float,
+                 ids: torch.Tensor | None = None):
+        if coords.dtype != torch.float64 or coords.dim() != 2 or coords.shape[0] != 6:
+            raise ValueError("coords must be a (6, n) float64 tensor")
+        if not coords.is_cuda:
+            raise ValueError("coords must live on a CUDA device")
+        self.coords = coords.contiguous()
+        n = self.coords.shape[1]
+        self.ids = ids if ids is not None else torch.arange(n, dtype=torch.int64,
+                                                            device=coords.device)
+        self.species = species
+        self.bunch_charge_C = float(bunch_charge_C)
+
+    @property
+    def n(self) -> int:
+        return self.coords.shape[1]
+
+    def c_struct(self) -> L.bx_beam:
+        b = L.bx_beam()
+        base = self.coords.data_ptr()
+        n = self.n
+        for k in range(6):
+            b.coord[k] = base + 8 * n * k if n > 0 else None
+        b.id = self.ids.data_ptr() if n > 0 else None
+        b.n = n
+        b.charge_sign = float(self.species.charge_sign)
+        b.bunch_charge_C = self.bunch_charge_C
+        b.mass_MeV = float(self.species.mass_MeV)
+        b.kinetic_MeV = float(self.species.kinetic_MeV)
+        return b
+
+
+def lattice_struct(elements: Sequence, space_charge: bool):
+    """elements: objects with kind, length, k, angle, nslice (beamgen.Element)."""
+    arr = (L.bx_element * max(1, len(elements)))()
+    for i, e in enumerate(elements):
+        arr[i].type = int(e.kind)
+        arr[i].nslice = int(e.nslice)
+        arr[i].length = float(e.length)
+        arr[i].k = float(e.k)
+        arr[i].angle = float(e.angle)
+    lat = L.bx_lattice()
+    lat.elements = ctypes.cast(arr, ctypes.POINTER(L.bx_element))
+    lat.count = len(elements)
+    lat.space_charge = 1 if space_charge else 0
+    return lat, arr
+
+
+class Grid:
+    """rho (n^3) and phi ((n+2)^3) device tensors with the box."""
+
+    def __init__(self, n: int, device, lo=None, hi=None):
+        self.n = n
+        self.rho = torch.zeros(n ** 3, dtype=torch.float64, device=device)
+        self.phi = torch.zeros((n + 2) ** 3, dtype=torch.float64, device=device)
+        self.lo = list(lo) if lo is not None else [0.0] * 3
+        self.hi = list(hi) if hi is not None else [0.0] * 3
+        self.h = [0.0] * 3
+        self.use_box = lo is not None
+
+    def c_struct(self) -> L.bx_grid:
+        g = L.bx_grid()
+        g.n = self.n
+        g.use_box = 1 if self.use_box else 0
+        for d in range(3):
+            g.lo[d], g.hi[d], g.h[d] = self.lo[d], self.hi[d], self.h[d]
+        g.rho = self.rho.data_ptr()
+        g.phi = self.phi.data_ptr()
+        return g
+
+    def read_back(self, g: L.bx_grid):
+        self.lo = [g.lo[d] for d in range(3)]
+        self.hi = [g.hi[d] for d in range(3)]
+        self.h = [g.h[d] for d in range(3)]
+
+
+class Tracker:
+    """A libbeamtrack context (bx_create) on the current CUDA device."""
+
+    def __init__(self, n_grid: int, shape_order: int = 1):
+        self.lib = L.load()
+        opt = L.bx_options()
+        opt.n_grid = int(n_grid)
+        opt.shape_order = int(shape_order)
+        ctx = ctypes.c_void_p()
+        rc = self.lib.bx_create(ctypes.byref(ctx), ctypes.byref(opt))
+        _check(self.lib, None, rc)
+        self.ctx = ctx
+        self.n = int(n_grid)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.bx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self):
+        _check(self.lib, self.ctx, self.lib.bx_reset(self.ctx))
+
+    def track(self, beam: Beam, elements, first_kick: int = 0, nkicks: int = -1,
+              space_charge: bool = True):
+        b = beam.c_struct()
+        lat, keep = lattice_struct(elements, space_charge)
+        rc = self.lib.bx_track(self.ctx, ctypes.byref(b), ctypes.byref(lat), int(first_kick),
+                               int(nkicks), _stream())
+        _check(self.lib, self.ctx, rc)
+
+    def deposit(self, beam: Beam, grid: Grid) -> Grid:
+        b = beam.c_struct()
+        g = grid.c_struct()
+        _check(self.lib, self.ctx, self.lib.bx_deposit(self.ctx, ctypes.byref(b), ctypes.byref(g),
+                                                       _stream()))
+        grid.read_back(g)
+        return grid
+
+    def solve(self, grid: Grid) -> Grid:
+        g = grid.c_struct()
+        _check(self.lib, self.ctx, self.lib.bx_solve(self.ctx, ctypes.byref(g), _stream()))
+        return grid
+
+    def gather_kick(self, beam: Beam, grid: Grid, ds: float):
+        b = beam.c_struct()
+        g = grid.c_struct()
+        _check(self.lib, self.ctx, self.lib.bx_gather_kick(self.ctx, ctypes.byref(b),
+                                                           ctypes.byref(g), float(ds), _stream()))
+
+    def moments(self, beam: Beam) -> torch.Tensor:
+        out = torch.empty(27, dtype=torch.float64, device=beam.coords.device)
+        b = beam.c_struct()
+        _check(self.lib, self.ctx, self.lib.bx_moments(self.ctx, ctypes.byref(b),
+                                                       ctypes.c_void_p(out.data_ptr()), _stream()))
+        return out
+
+    def green_table(self, h, device) -> torch.Tensor:
+        out = torch.empty((self.n + 1) ** 3, dtype=torch.float64, device=device)
+        hh = (ctypes.c_double * 3)(*[float(v) for v in h])
+        _check(self.lib, self.ctx, self.lib.bx_green_table(self.ctx, hh,
+                                                           ctypes.c_void_p(out.data_ptr()),
+                                                           _stream()))
+        return out
+
+    def regrid_log(self) -> list:
+        cnt = ctypes.c_int64()
+        _check(self.lib, self.ctx, self.lib.bx_regrid_log(self.ctx, None, 0, ctypes.byref(cnt)))
+        buf = (ctypes.c_int64 * max(1, cnt.value))()
+        _check(self.lib, self.ctx, self.lib.bx_regrid_log(self.ctx, buf, cnt.value,
+                                                          ctypes.byref(cnt)))
+        return [buf[i] for i in range(cnt.value)]
+
+    def box(self):
+        lo, hi, h = (ctypes.c_double * 3)(), (ctypes.c_double * 3)(), (ctypes.c_double * 3)()
+        _check(self.lib, self.ctx, self.lib.bx_get_box(self.ctx, lo, hi, h))
+        return list(lo), list(hi), list(h)
+
+    def sync(self):
+        _check(self.lib, self.ctx, self.lib.bx_sync(self.ctx, _stream()))

@@ -1,0 +1,553 @@
+// C ABI of libbeamtrack (declared in include/beamtrack.h): argument checks,
+// the context and its device scratch, the host-built map table of the slice
+// schedule, and the split-operator tracking loop.
+//
+// Paper anchors (arXiv:2208.02382): Listing 1 (ImpactX(), set_particle_shape,
+// set_space_charge, init_grids, add_particles, ref_particle().set_energy_MeV,
+// lattice of Drift/Quad with nslice, evolve) and Model Assumptions (linear
+// maps, rest-frame electrostatic field, split-operator step).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace bt;
+
+struct bx_ctx {
+    int n = 0;
+    FftPlan plan{};
+    unsigned long long *acc_hi = nullptr, *acc_lo = nullptr;
+    double *rho = nullptr, *phi = nullptr, *efield = nullptr;
+    double *fcorner = nullptr, *gtable = nullptr;
+    TrackState *st = nullptr;      // device
+    Box *tmp_box = nullptr;        // device scratch for explicit boxes
+    int32_t *status = nullptr;     // device
+    long long *log = nullptr;      // device regrid log
+    int64_t log_cap = 1 << 20;
+    double *mom_partial = nullptr;
+    int mom_partial_cap = 0;
+    MapCoef *maps = nullptr;       // device map table
+    size_t maps_cap = 0;
+    bool green_valid = false;
+    double green_h[3] = {0, 0, 0};
+    long long kick = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int32_t fail(bx_ctx *c, int32_t code, const std::string &msg) {
+    if (c) c->err = msg;
+    else g_create_err = msg;
+    return code;
+}
+
+int32_t cuda_fail(bx_ctx *c, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? BX_OUT_OF_MEMORY : BX_CUDA, m);
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+struct Ref {
+    double gamma, bg, beta, mass_eV, sign;
+};
+
+// Reference particle from kinetic energy (Listing 1 set_energy_MeV, read as
+// kinetic): gamma = 1 + W/mc^2, beta gamma = sqrt(gamma^2 - 1).
+Ref make_ref(const bx_beam *b) {
+    Ref r;
+    r.gamma = 1.0 + b->kinetic_MeV / b->mass_MeV;
+    r.bg = std::sqrt(r.gamma * r.gamma - 1.0);
+    r.beta = r.bg / r.gamma;
+    r.mass_eV = b->mass_MeV * 1e6;
+    r.sign = b->charge_sign;
+    return r;
+}
+
+typedef double Mat[6][6];
+
+void mat_identity(Mat m) {
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) m[i][j] = i == j ? 1.0 : 0.0;
+}
+
+void focus_block(double ds, double k, double out[2][2]) {
+    if (k > 0.0) {
+        double w = std::sqrt(k), c = std::cos(w * ds), s = std::sin(w * ds);
+        out[0][0] = c; out[0][1] = s / w; out[1][0] = -w * s; out[1][1] = c;
+    } else if (k < 0.0) {
+        double w = std::sqrt(-k), c = std::cosh(w * ds), s = std::sinh(w * ds);
+        out[0][0] = c; out[0][1] = s / w; out[1][0] = w * s; out[1][1] = c;
+    } else {
+        out[0][0] = 1.0; out[0][1] = ds; out[1][0] = 0.0; out[1][1] = 1.0;
+    }
+}
+
+// Linear map of a piece ds of an element (Model Assumptions: linear order).
+// Drift: x += ds px, y += ds py, t += ds/(beta gamma)^2 pt.  Quadrupole: k > 0
+// focuses x.  Sector bend of radius rho = length/angle, theta = ds/rho:
+//   x'  = cos x + rho sin px - rho(1-cos)/beta pt
+//   px' = -sin/rho x + cos px - sin/beta pt
+//   t'  = t + sin/beta x + rho(1-cos)/beta px + rho(sin/beta^2 - theta) pt.
+void element_map(const bx_element &e, double ds, const Ref &r, Mat m) {
+    mat_identity(m);
+    if (e.type == BX_SBEND && e.angle != 0.0) {
+        double rho = e.length / e.angle, th = ds / rho;
+        double c = std::cos(th), s = std::sin(th), b = r.beta;
+        m[0][0] = c; m[0][1] = rho * s; m[0][5] = -rho * (1.0 - c) / b;
+        m[1][0] = -s / rho; m[1][1] = c; m[1][5] = -s / b;
+        m[2][3] = ds;
+        m[4][0] = s / b; m[4][1] = rho * (1.0 - c) / b; m[4][5] = rho * (s / (b * b) - th);
+        return;
+    }
+    m[4][5] = ds / (r.bg * r.bg);
+    if (e.type == BX_QUAD) {
+        double bx[2][2], by[2][2];
+        focus_block(ds, e.k, bx);
+        focus_block(ds, -e.k, by);
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) {
+                m[i][j] = bx[i][j];
+                m[2 + i][2 + j] = by[i][j];
+            }
+    } else {
+        m[0][1] = ds;
+        m[2][3] = ds;
+    }
+}
+
+// out = a * b (apply b first).
+void mat_mul(const Mat a, const Mat b, Mat out) {
+    Mat t;
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 6; ++k) s += a[i][k] * b[k][j];
+            t[i][j] = s;
+        }
+    memcpy(out, t, sizeof(Mat));
+}
+
+MapCoef to_coef(const Mat m) {
+    MapCoef c;
+    memset(&c, 0, sizeof(c));
+    c.m00 = m[0][0]; c.m01 = m[0][1]; c.m05 = m[0][5];
+    c.m10 = m[1][0]; c.m11 = m[1][1]; c.m15 = m[1][5];
+    c.m22 = m[2][2]; c.m23 = m[2][3];
+    c.m32 = m[3][2]; c.m33 = m[3][3];
+    c.m40 = m[4][0]; c.m41 = m[4][1]; c.m45 = m[4][5];
+    return c;
+}
+
+int32_t check_beam(bx_ctx *ctx, const bx_beam *b) {
+    if (!b) return fail(ctx, BX_BAD_ARG, "beam is NULL");
+    if (b->n < 0) return fail(ctx, BX_BAD_ARG, "beam n < 0");
+    if (b->n > 0)
+        for (int k = 0; k < 6; ++k)
+            if (!b->coord[k]) return fail(ctx, BX_BAD_ARG, "beam coordinate pointer is NULL");
+    if (!(b->charge_sign == 1.0 || b->charge_sign == -1.0))
+        return fail(ctx, BX_BAD_ARG, "charge_sign must be +1 or -1");
+    if (!(b->mass_MeV > 0.0) || !std::isfinite(b->mass_MeV))
+        return fail(ctx, BX_BAD_ARG, "mass_MeV must be > 0");
+    if (!(b->kinetic_MeV > 0.0) || !std::isfinite(b->kinetic_MeV))
+        return fail(ctx, BX_BAD_ARG, "kinetic_MeV must be > 0");
+    if (!std::isfinite(b->bunch_charge_C)) return fail(ctx, BX_BAD_ARG, "bunch charge not finite");
+    return BX_OK;
+}
+
+int32_t check_lattice(bx_ctx *ctx, const bx_lattice *l) {
+    if (!l) return fail(ctx, BX_BAD_ARG, "lattice is NULL");
+    if (l->count < 0 || (l->count > 0 && !l->elements))
+        return fail(ctx, BX_BAD_ARG, "lattice elements missing");
+    for (int i = 0; i < l->count; ++i) {
+        const bx_element &e = l->elements[i];
+        if (e.type != BX_DRIFT && e.type != BX_QUAD && e.type != BX_SBEND)
+            return fail(ctx, BX_BAD_ARG, "unknown element type");
+        if (!(e.length > 0.0) || !std::isfinite(e.length))
+            return fail(ctx, BX_BAD_ARG, "element length must be > 0");
+        if (e.nslice <= 0) return fail(ctx, BX_BAD_ARG, "element nslice must be >= 1");
+        if (!std::isfinite(e.k) || !std::isfinite(e.angle))
+            return fail(ctx, BX_BAD_ARG, "element k/angle not finite");
+    }
+    return BX_OK;
+}
+
+int32_t check_grid(bx_ctx *ctx, const bx_grid *g, bool need_rho, bool need_phi) {
+    if (!g) return fail(ctx, BX_BAD_ARG, "grid is NULL");
+    if (g->n != ctx->n) return fail(ctx, BX_BAD_ARG, "grid n differs from the context's n_grid");
+    if (need_rho && !g->rho) return fail(ctx, BX_BAD_ARG, "grid rho is NULL");
+    if (need_phi && !g->phi) return fail(ctx, BX_BAD_ARG, "grid phi is NULL");
+    return BX_OK;
+}
+
+Box explicit_box(const double lo[3], const double hi[3], int n) {
+    Box b;
+    for (int d = 0; d < 3; ++d) {
+        b.lo[d] = lo[d];
+        b.hi[d] = hi[d];
+        b.h[d] = (hi[d] - lo[d]) / (double)(n - 1);
+        b.inv_h[d] = 1.0 / b.h[d];
+    }
+    return b;
+}
+
+int32_t ensure_green(bx_ctx *ctx, const double h[3], cudaStream_t s) {
+    if (ctx->green_valid && ctx->green_h[0] == h[0] && ctx->green_h[1] == h[1] &&
+        ctx->green_h[2] == h[2])
+        return BX_OK;
+    CK(launch_igf_table(ctx->n, h, ctx->fcorner, ctx->gtable, s), "green table");
+    CK(green_spectrum_from_table(&ctx->plan, ctx->gtable, s), "green spectrum");
+    ctx->green_valid = true;
+    memcpy(ctx->green_h, h, sizeof(ctx->green_h));
+    return BX_OK;
+}
+
+int32_t ensure_maps(bx_ctx *ctx, size_t count) {
+    if (count <= ctx->maps_cap) return BX_OK;
+    if (ctx->maps) cudaFree(ctx->maps);
+    ctx->maps = nullptr;
+    size_t cap = count < 1024 ? 1024 : count;
+    CK(cudaMalloc(&ctx->maps, cap * sizeof(MapCoef)), "map table");
+    ctx->maps_cap = cap;
+    return BX_OK;
+}
+
+int32_t read_state(bx_ctx *ctx, TrackState *h, cudaStream_t s) {
+    CK(cudaMemcpyAsync(h, ctx->st, sizeof(TrackState), cudaMemcpyDeviceToHost, s), "read state");
+    CK(cudaStreamSynchronize(s), "sync");
+    return BX_OK;
+}
+
+void init_state(TrackState *h) {
+    memset(h, 0, sizeof(*h));
+    for (int d = 0; d < 3; ++d) {
+        h->mm[d] = dkey(INFINITY);
+        h->mm[3 + d] = dkey(-INFINITY);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t bx_create(bx_ctx **out, const bx_options *opt) {
+    if (!out || !opt) return fail(nullptr, BX_BAD_ARG, "NULL argument");
+    *out = nullptr;
+    int n = opt->n_grid;
+    if (n < 8 || n > 256 || (n & (n - 1)) != 0)
+        return fail(nullptr, BX_BAD_ARG, "n_grid must be a power of two in [8, 256]");
+    if (opt->shape_order != 1) return fail(nullptr, BX_BAD_ARG, "shape_order must be 1 (CIC)");
+    bx_ctx *ctx = new (std::nothrow) bx_ctx();
+    if (!ctx) return fail(nullptr, BX_OUT_OF_MEMORY, "host allocation");
+    ctx->n = n;
+    const size_t n3 = (size_t)n * n * n, q3 = (size_t)(n + 2) * (n + 2) * (n + 2);
+    const size_t o3 = (size_t)(n + 1) * (n + 1) * (n + 1);
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void **p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    A((void **)&ctx->acc_hi, n3 * 8);
+    A((void **)&ctx->acc_lo, n3 * 8);
+    A((void **)&ctx->rho, n3 * 8);
+    A((void **)&ctx->phi, q3 * 8);
+    A((void **)&ctx->efield, n3 * sizeof(Field4));
+    A((void **)&ctx->fcorner, q3 * 16);
+    A((void **)&ctx->gtable, o3 * 8);
+    A((void **)&ctx->st, sizeof(TrackState));
+    A((void **)&ctx->tmp_box, sizeof(Box));
+    A((void **)&ctx->status, sizeof(int32_t));
+    A((void **)&ctx->log, ctx->log_cap * sizeof(long long));
+    if (e == cudaSuccess) e = fft_plan_init(&ctx->plan, n);
+    if (e == cudaSuccess) {
+        TrackState h;
+        init_state(&h);
+        e = cudaMemcpy(ctx->st, &h, sizeof(h), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(int32_t));
+    if (e != cudaSuccess) {
+        std::string m = std::string("bx_create: ") + cudaGetErrorString(e);
+        int32_t code = e == cudaErrorMemoryAllocation ? BX_OUT_OF_MEMORY : BX_CUDA;
+        bx_destroy(ctx);
+        return fail(nullptr, code, m);
+    }
+    *out = ctx;
+    return BX_OK;
+}
+
+int32_t bx_destroy(bx_ctx *ctx) {
+    if (!ctx) return BX_OK;
+    cudaDeviceSynchronize();
+    void *ptrs[] = {ctx->acc_hi, ctx->acc_lo, ctx->rho, ctx->phi, ctx->efield, ctx->fcorner,
+                    ctx->gtable, ctx->st, ctx->tmp_box, ctx->status, ctx->log,
+                    ctx->mom_partial, ctx->maps};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    fft_plan_free(&ctx->plan);
+    delete ctx;
+    return BX_OK;
+}
+
+int32_t bx_reset(bx_ctx *ctx) {
+    if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
+    TrackState h;
+    init_state(&h);
+    CK(cudaMemcpy(ctx->st, &h, sizeof(h), cudaMemcpyHostToDevice), "reset");
+    ctx->kick = 0;
+    return BX_OK;
+}
+
+int32_t bx_track(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t first_kick,
+                 int64_t nkicks, void *stream) {
+    if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
+    int32_t rc = check_beam(ctx, beam);
+    if (rc) return rc;
+    if ((rc = check_lattice(ctx, lat))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    // slice schedule: (element, ds) per kick
+    std::vector<int> sel;
+    std::vector<double> sds;
+    for (int i = 0; i < lat->count; ++i)
+        for (int k = 0; k < lat->elements[i].nslice; ++k) {
+            sel.push_back(i);
+            sds.push_back(lat->elements[i].length / lat->elements[i].nslice);
+        }
+    const int64_t total = (int64_t)sel.size();
+    if (nkicks < 0) nkicks = total - first_kick;
+    if (first_kick < 0 || first_kick > total || nkicks < 0 || first_kick + nkicks > total)
+        return fail(ctx, BX_BAD_ARG, "kick range outside the slice schedule");
+    if (nkicks == 0) return BX_OK;
+    const Ref r = make_ref(beam);
+    // map table: H_first, H_{k+1} H_k for inner boundaries, H_last
+    std::vector<MapCoef> tab;
+    tab.reserve(nkicks + 1);
+    Mat hk, hn, mm;
+    element_map(lat->elements[sel[first_kick]], 0.5 * sds[first_kick], r, hk);
+    tab.push_back(to_coef(hk));
+    for (int64_t k = first_kick; k < first_kick + nkicks; ++k) {
+        if (k + 1 < first_kick + nkicks) {
+            element_map(lat->elements[sel[k + 1]], 0.5 * sds[k + 1], r, hn);
+            mat_mul(hn, hk, mm);
+            tab.push_back(to_coef(mm));
+            memcpy(hk, hn, sizeof(Mat));
+        } else {
+            tab.push_back(to_coef(hk));
+        }
+    }
+    if ((rc = ensure_maps(ctx, tab.size()))) return rc;
+    CK(cudaMemcpyAsync(ctx->maps, tab.data(), tab.size() * sizeof(MapCoef),
+                       cudaMemcpyHostToDevice, s),
+       "upload maps");
+    if (beam->n == 0) {
+        ctx->kick += nkicks;
+        return BX_OK;
+    }
+    double *const *c = beam->coord;
+    if (!lat->space_charge) {
+        // maps only: H_first, merged pairs, H_last in one pass per particle
+        CK(launch_push_maps(c, beam->n, ctx->maps, (int)tab.size(), s), "push");
+        ctx->kick += nkicks;
+        return BX_OK;
+    }
+    const double q_macro = r.sign * std::fabs(beam->bunch_charge_C) / (double)beam->n;
+    CK(launch_push_maps(c, beam->n, ctx->maps, 1, s), "push");
+    CK(launch_minmax(c, beam->n, r.bg, ctx->st, ctx->status, s), "minmax");
+    for (int64_t k = 0; k < nkicks; ++k) {
+        const double ds = sds[first_kick + k];
+        CK(cudaMemcpyAsync(&ctx->st->kick, &ctx->kick, sizeof(long long), cudaMemcpyHostToDevice,
+                           s),
+           "kick counter");
+        CK(launch_box_rule(ctx->st, ctx->n, beam->n, ctx->log, ctx->log_cap, s), "box rule");
+        TrackState h;
+        if ((rc = read_state(ctx, &h, s))) return rc;
+        if (h.has_box == 0) return fail(ctx, BX_NONFINITE, "no box (non-finite coordinates?)");
+        for (int d = 0; d < 3; ++d)
+            if (!std::isfinite(h.box.lo[d]) || !std::isfinite(h.box.hi[d]) || !(h.box.h[d] > 0.0))
+                return fail(ctx, BX_NONFINITE, "non-finite particle coordinates");
+        if ((rc = ensure_green(ctx, h.box.h, s))) return rc;
+        const Box *box = &ctx->st->box;
+        CK(launch_deposit(c, beam->n, r.bg, box, ctx->n, ctx->acc_hi, ctx->acc_lo, ctx->status, s),
+           "deposit");
+        CK(launch_acc_to_rho(ctx->acc_hi, ctx->acc_lo, ctx->n, q_macro, box, ctx->rho, s),
+           "rho");
+        CK(solve_rho_to_phi(&ctx->plan, ctx->rho, ctx->phi, s), "solve");
+        const double kt = r.sign * ds / (r.mass_eV * (r.bg * r.bg));
+        const double kz = -r.sign * ds / (r.mass_eV * r.bg);
+        CK(launch_field(ctx->phi, ctx->n, box, kt, kt, kz, ctx->efield, s), "field");
+        const bool last = k + 1 == nkicks;
+        CK(launch_gather_kick_push(c, beam->n, r.bg, box, ctx->n, ctx->efield, ctx->maps + 1 + k,
+                                   last ? nullptr : ctx->st, ctx->status, s),
+           "gather/kick/push");
+        ctx->kick += 1;
+    }
+    return BX_OK;
+}
+
+int32_t bx_deposit(bx_ctx *ctx, const bx_beam *beam, bx_grid *grid, void *stream) {
+    if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
+    int32_t rc = check_beam(ctx, beam);
+    if (rc) return rc;
+    if ((rc = check_grid(ctx, grid, true, false))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const Ref r = make_ref(beam);
+    double *const *c = beam->coord;
+    const Box *box;
+    if (grid->use_box) {
+        for (int d = 0; d < 3; ++d)
+            if (!(grid->hi[d] > grid->lo[d]) || !std::isfinite(grid->lo[d]) ||
+                !std::isfinite(grid->hi[d]))
+                return fail(ctx, BX_BAD_ARG, "grid box needs finite lo < hi");
+        Box b = explicit_box(grid->lo, grid->hi, ctx->n);
+        CK(cudaMemcpyAsync(ctx->tmp_box, &b, sizeof(b), cudaMemcpyHostToDevice, s), "box");
+        for (int d = 0; d < 3; ++d) grid->h[d] = b.h[d];
+        box = ctx->tmp_box;
+    } else {
+        if (beam->n == 0) return fail(ctx, BX_BAD_ARG, "box rule needs particles");
+        CK(launch_minmax(c, beam->n, r.bg, ctx->st, ctx->status, s), "minmax");
+        CK(cudaMemcpyAsync(&ctx->st->kick, &ctx->kick, sizeof(long long), cudaMemcpyHostToDevice, s),
+           "kick counter");
+        CK(launch_box_rule(ctx->st, ctx->n, beam->n, ctx->log, ctx->log_cap, s), "box rule");
+        TrackState h;
+        if ((rc = read_state(ctx, &h, s))) return rc;
+        for (int d = 0; d < 3; ++d) {
+            if (!std::isfinite(h.box.lo[d]) || !std::isfinite(h.box.hi[d]))
+                return fail(ctx, BX_NONFINITE, "non-finite particle coordinates");
+            grid->lo[d] = h.box.lo[d];
+            grid->hi[d] = h.box.hi[d];
+            grid->h[d] = h.box.h[d];
+        }
+        box = &ctx->st->box;
+    }
+    const double q_macro =
+        beam->n > 0 ? r.sign * std::fabs(beam->bunch_charge_C) / (double)beam->n : 0.0;
+    CK(launch_deposit(c, beam->n, r.bg, box, ctx->n, ctx->acc_hi, ctx->acc_lo, ctx->status, s),
+       "deposit");
+    CK(launch_acc_to_rho(ctx->acc_hi, ctx->acc_lo, ctx->n, q_macro, box, grid->rho, s), "rho");
+    return BX_OK;
+}
+
+int32_t bx_solve(bx_ctx *ctx, bx_grid *grid, void *stream) {
+    if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
+    int32_t rc = check_grid(ctx, grid, true, true);
+    if (rc) return rc;
+    for (int d = 0; d < 3; ++d)
+        if (!(grid->h[d] > 0.0) || !std::isfinite(grid->h[d]))
+            return fail(ctx, BX_BAD_ARG, "grid h must be finite and > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = ensure_green(ctx, grid->h, s))) return rc;
+    CK(solve_rho_to_phi(&ctx->plan, grid->rho, grid->phi, s), "solve");
+    return BX_OK;
+}
+
+int32_t bx_gather_kick(bx_ctx *ctx, bx_beam *beam, const bx_grid *grid, double ds, void *stream) {
+    if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
+    int32_t rc = check_beam(ctx, beam);
+    if (rc) return rc;
+    if ((rc = check_grid(ctx, grid, false, true))) return rc;
+    if (!(ds > 0.0) || !std::isfinite(ds)) return fail(ctx, BX_BAD_ARG, "ds must be > 0");
+    for (int d = 0; d < 3; ++d)
+        if (!(grid->h[d] > 0.0) || !std::isfinite(grid->lo[d]))
+            return fail(ctx, BX_BAD_ARG, "grid lo/h invalid");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Ref r = make_ref(beam);
+    Box b;
+    for (int d = 0; d < 3; ++d) {
+        b.lo[d] = grid->lo[d];
+        b.hi[d] = grid->hi[d];
+        b.h[d] = grid->h[d];
+        b.inv_h[d] = 1.0 / grid->h[d];
+    }
+    CK(cudaMemcpyAsync(ctx->tmp_box, &b, sizeof(b), cudaMemcpyHostToDevice, s), "box");
+    const double kt = r.sign * ds / (r.mass_eV * (r.bg * r.bg));
+    const double kz = -r.sign * ds / (r.mass_eV * r.bg);
+    CK(launch_field(grid->phi, ctx->n, ctx->tmp_box, kt, kt, kz, ctx->efield, s), "field");
+    CK(launch_gather_kick_push(beam->coord, beam->n, r.bg, ctx->tmp_box, ctx->n, ctx->efield,
+                               nullptr, nullptr, ctx->status, s),
+       "gather/kick");
+    return BX_OK;
+}
+
+int32_t bx_moments(bx_ctx *ctx, const bx_beam *beam, double *out, void *stream) {
+    if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
+    int32_t rc = check_beam(ctx, beam);
+    if (rc) return rc;
+    if (!out) return fail(ctx, BX_BAD_ARG, "out is NULL");
+    if (beam->n == 0) return fail(ctx, BX_BAD_ARG, "moments of an empty beam");
+    cudaStream_t s = (cudaStream_t)stream;
+    int nb = moments_blocks(beam->n);
+    if (nb * 21 > ctx->mom_partial_cap) {
+        if (ctx->mom_partial) cudaFree(ctx->mom_partial);
+        ctx->mom_partial = nullptr;
+        CK(cudaMalloc(&ctx->mom_partial, (size_t)nb * 21 * sizeof(double)), "moments scratch");
+        ctx->mom_partial_cap = nb * 21;
+    }
+    CK(launch_moments(beam->coord, beam->n, ctx->mom_partial, nb, out, s), "moments");
+    return BX_OK;
+}
+
+int32_t bx_green_table(bx_ctx *ctx, const double h[3], double *out, void *stream) {
+    if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
+    if (!h || !out) return fail(ctx, BX_BAD_ARG, "NULL argument");
+    for (int d = 0; d < 3; ++d)
+        if (!(h[d] > 0.0) || !std::isfinite(h[d])) return fail(ctx, BX_BAD_ARG, "h must be > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(launch_igf_table(ctx->n, h, ctx->fcorner, ctx->gtable, s), "green table");
+    const size_t o3 = (size_t)(ctx->n + 1) * (ctx->n + 1) * (ctx->n + 1);
+    CK(cudaMemcpyAsync(out, ctx->gtable, o3 * 8, cudaMemcpyDeviceToDevice, s), "copy");
+    return BX_OK;
+}
+
+int32_t bx_regrid_log(bx_ctx *ctx, int64_t *out, int64_t cap, int64_t *count) {
+    if (!ctx || !count) return fail(ctx, BX_BAD_ARG, "NULL argument");
+    TrackState h;
+    int32_t rc = read_state(ctx, &h, 0);
+    if (rc) return rc;
+    *count = h.nlog;
+    int64_t k = h.nlog < cap ? h.nlog : cap;
+    if (k > ctx->log_cap) k = ctx->log_cap;
+    if (k > 0 && out) CK(cudaMemcpy(out, ctx->log, k * sizeof(long long), cudaMemcpyDeviceToHost), "log");
+    return BX_OK;
+}
+
+int32_t bx_get_box(bx_ctx *ctx, double lo[3], double hi[3], double h[3]) {
+    if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
+    TrackState st;
+    int32_t rc = read_state(ctx, &st, 0);
+    if (rc) return rc;
+    if (!st.has_box) return fail(ctx, BX_BAD_ARG, "no box yet");
+    for (int d = 0; d < 3; ++d) {
+        if (lo) lo[d] = st.box.lo[d];
+        if (hi) hi[d] = st.box.hi[d];
+        if (h) h[d] = st.box.h[d];
+    }
+    return BX_OK;
+}
+
+int32_t bx_sync(bx_ctx *ctx, void *stream) {
+    if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaStreamSynchronize(s), "sync");
+    int32_t st = 0;
+    CK(cudaMemcpy(&st, ctx->status, sizeof(st), cudaMemcpyDeviceToHost), "status");
+    CK(cudaMemset(ctx->status, 0, sizeof(st)), "status clear");
+    if (st & ST_NONFINITE) return fail(ctx, BX_NONFINITE, "non-finite particle coordinates");
+    if (st & ST_TIMEOUT) return fail(ctx, BX_DEVICE_TIMEOUT, "a device wait timed out");
+    if (st & ST_OUTSIDE) return fail(ctx, BX_BAD_ARG, "a particle lies outside the given box");
+    return BX_OK;
+}
+
+const char *bx_last_error(const bx_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+}  // extern "C"

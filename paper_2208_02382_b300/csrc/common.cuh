@@ -1,0 +1,108 @@
+// Internal declarations shared by the CUDA translation units of libbeamtrack.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "beamtrack.h"
+
+namespace bt {
+
+// Device status word bits (read by bx_sync).
+enum : int32_t { ST_NONFINITE = 1, ST_TIMEOUT = 2, ST_OUTSIDE = 4 };
+
+// Linear map with the structure shared by drift, quadrupole and sector bend
+// and closed under composition (pt is unchanged, t enters its own row with
+// coefficient 1, y decouples):
+//   x'  = m00 x + m01 px + m05 pt        y'  = m22 y + m23 py
+//   px' = m10 x + m11 px + m15 pt        py' = m32 y + m33 py
+//   t'  = t + m40 x + m41 px + m45 pt    pt' = pt
+struct MapCoef {
+    double m00, m01, m05, m10, m11, m15, m22, m23, m32, m33, m40, m41, m45, pad0, pad1, pad2;
+};
+
+// Pre-scaled field at a node (momentum change per unit CIC weight), padded to
+// 32 bytes so that one node is one aligned 256-bit load.
+struct __align__(32) Field4 {
+    double x, y, z, w;
+};
+
+// Grid box as the kernels read it (device resident for tracking).
+struct Box {
+    double lo[3], hi[3], h[3], inv_h[3];
+};
+
+// Tracking state kept on the device between kicks.
+struct TrackState {
+    Box box;
+    long long mm[6];        // order-preserving keys of min X,Y,Z then max X,Y,Z
+    int32_t has_box;        // a box exists
+    int32_t regrid;         // the box rule made a new box at the last decision
+    int32_t green_stale;    // h differs from the h of the current Green's function
+    int32_t pad;
+    double green_h[3];      // h the Green's function spectrum was built for
+    long long kick;         // kick counter (since creation / reset)
+    long long nlog;         // regrid log length
+};
+
+// Order-preserving map between doubles and signed 64-bit keys (monotone for
+// all non-NaN values), used for exact, order-free min/max with integer atomics.
+__host__ __device__ __forceinline__ long long dkey(double v) {
+    long long b;
+    memcpy(&b, &v, 8);
+    return b >= 0 ? b : (b ^ 0x7FFFFFFFFFFFFFFFLL);
+}
+__host__ __device__ __forceinline__ double dkey_inv(long long k) {
+    long long b = k >= 0 ? k : (k ^ 0x7FFFFFFFFFFFFFFFLL);
+    double v;
+    memcpy(&v, &b, 8);
+    return v;
+}
+
+// Fixed-point deposit: CIC weights carry 51 fractional bits; the global
+// accumulator splits each value into hi (bits >= 31) and lo (bits < 31) so
+// neither 64-bit sum can overflow for fewer than 2^32 contributions of < 2^62.
+constexpr int DEP_FRAC_BITS = 51;
+constexpr int DEP_SPLIT = 31;
+
+// ---- launchers (defined in the .cu files) --------------------------------
+// particles.cu
+cudaError_t launch_push_maps(double *const c[6], int64_t n, const MapCoef *maps, int nmaps,
+                             cudaStream_t s);
+cudaError_t launch_minmax(double *const c[6], int64_t n, double betagamma, TrackState *st,
+                          int32_t *status, cudaStream_t s);
+cudaError_t launch_deposit(double *const c[6], int64_t n, double betagamma, const Box *box,
+                           int nn, unsigned long long *acc_hi, unsigned long long *acc_lo,
+                           int32_t *status, cudaStream_t s);
+cudaError_t launch_acc_to_rho(const unsigned long long *acc_hi, const unsigned long long *acc_lo,
+                              int nn, double q_macro, const Box *box, double *rho,
+                              cudaStream_t s);
+cudaError_t launch_gather_kick_push(double *const c[6], int64_t n, double betagamma,
+                                    const Box *box, int nn, const double *efield,
+                                    const MapCoef *map, TrackState *st, int32_t *status,
+                                    cudaStream_t s);
+cudaError_t launch_box_rule(TrackState *st, int nn, int64_t n, long long *log, int64_t log_cap,
+                            cudaStream_t s);
+cudaError_t launch_field(const double *phi, int nn, const Box *box, double kx, double ky,
+                         double kz, double *efield, cudaStream_t s);
+// moments.cu
+cudaError_t launch_moments(double *const c[6], int64_t n, double *partials, int nblocks,
+                           double *out, cudaStream_t s);
+int moments_blocks(int64_t n);
+// fft.cu
+struct FftPlan {
+    int n;            // physical grid nodes per dim
+    int m;            // doubled size 2n
+    double2 *buf;     // m^3 complex work buffer
+    double2 *tw;      // m/2 twiddles exp(-2 pi i j/m)
+    double *ghat;     // m^3 real spectrum of the doubled Green's function
+};
+cudaError_t fft_plan_init(FftPlan *p, int n);
+void fft_plan_free(FftPlan *p);
+cudaError_t solve_rho_to_phi(const FftPlan *p, const double *rho, double *phi, cudaStream_t s);
+cudaError_t green_spectrum_from_table(const FftPlan *p, const double *gtable, cudaStream_t s);
+// igf.cu
+cudaError_t launch_igf_table(int n, const double h[3], double *fcorner, double *gtable,
+                             cudaStream_t s);
+
+}  // namespace bt

@@ -1,0 +1,246 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerance: relative 1e-11 on phase-space coordinates (metric of
+tests/parity.py: per particle, relative to max(|value|, rms of the row)) and
+on grids (relative to the grid's max).  Inputs are the seeded synthetic bunches
+of beamgen; sizes span several FFT/cell tiles with ragged particle counts."""
+import numpy as np
+import pytest
+import torch
+
+import beamgen as bg
+from oracle import physics as ph
+from oracle import spacecharge as sc
+from oracle import track as tr
+from tests.parity import REL_TOL, coord_rel_err, grid_rel_err, oracle_ref
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def bt():
+    import paper_2208_02382_b300 as p
+    from paper_2208_02382_b300 import build
+    build.build()
+    return p
+
+
+def gpu_beam(bt, coords, species, charge):
+    t = torch.tensor(np.ascontiguousarray(coords), dtype=torch.float64, device=DEV)
+    return bt.Beam(t, bt.Species(species.mass_MeV, species.kinetic_MeV, species.charge_sign),
+                   charge)
+
+
+def to_np(beam):
+    torch.cuda.synchronize()
+    return beam.coords.cpu().numpy()
+
+
+# ------------------------------------------------------------- Green's function
+
+@pytest.mark.parametrize("n,h", [(8, (1e-3, 1e-3, 1e-3)), (16, (1e-3, 2.5e-3, 7e-3)),
+                                 (32, (2e-4, 2e-4, 0.2))])
+def test_green_table_matches_float128_oracle(bt, n, h):
+    trk = bt.Tracker(n)
+    g = trk.green_table(h, DEV).cpu().numpy().reshape(n + 1, n + 1, n + 1)
+    ref = sc.igf_octant(n, h)
+    rel = np.abs(g - ref) / np.abs(ref)
+    assert rel.max() <= 4e-16
+
+
+# ------------------------------------------------------------------- deposit
+
+@pytest.mark.parametrize("npart,n", [(1, 8), (333, 8), (10_000, 32), (100_003, 64)])
+def test_deposit_matches_oracle(bt, npart, n):
+    c = bg.gaussian6d(npart, seed=npart)
+    sp = bg.PROTON_2GEV
+    beam = gpu_beam(bt, c, sp, 1e-9)
+    trk = bt.Tracker(n)
+    grid = trk.deposit(beam, bt.Grid(n, DEV))
+    trk.sync()
+    ref = oracle_ref(sp)
+    pos = sc.rest_frame(c, ref)
+    box, _ = sc.box_rule(pos, None)
+    assert tuple(grid.lo) == box.lo and tuple(grid.hi) == box.hi
+    rho_ref = sc.deposit(pos, sc.macro_charge(1e-9, npart, ref), box, n)
+    rho = grid.rho.cpu().numpy().reshape(n, n, n)
+    assert grid_rel_err(rho, rho_ref) <= 1e-13
+
+
+def test_deposit_is_bitwise_reproducible(bt):
+    c = bg.gaussian6d(200_000, seed=5)
+    beam = gpu_beam(bt, c, bg.PROTON_1GEV, 1e-9)
+    trk = bt.Tracker(32)
+    a = trk.deposit(beam, bt.Grid(32, DEV)).rho.clone()
+    b = trk.deposit(beam, bt.Grid(32, DEV, lo=trk.box()[0], hi=trk.box()[1])).rho.clone()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+# --------------------------------------------------------------------- solve
+
+@pytest.mark.parametrize("n,h", [(8, (1e-3, 1.5e-3, 2.5e-3)), (32, (1e-4, 1e-4, 3e-4)),
+                                 (64, (5e-5, 6e-5, 2e-3))])
+def test_solve_matches_oracle(bt, n, h):
+    rng = np.random.default_rng(n)
+    rho = rng.random((n, n, n)) * 1e-3
+    trk = bt.Tracker(n)
+    grid = bt.Grid(n, DEV)
+    grid.rho.copy_(torch.tensor(rho.ravel(), device=DEV))
+    grid.h = list(h)
+    trk.solve(grid)
+    phi = grid.phi.cpu().numpy().reshape(n + 2, n + 2, n + 2)
+    ref = sc.solve(rho, h)
+    assert grid_rel_err(phi, ref) <= REL_TOL
+
+
+# ------------------------------------------------------------- gather + kick
+
+def test_gather_kick_matches_oracle(bt):
+    n, npart = 32, 20_000
+    sp = bg.PROTON_1GEV
+    ref = oracle_ref(sp)
+    c = bg.gaussian6d(npart, seed=3)
+    pos = sc.rest_frame(c, ref)
+    box, _ = sc.box_rule(pos, None)
+    h = box.h(n)
+    rho = sc.deposit(pos, sc.macro_charge(1e-9, npart, ref), box, n)
+    phi = sc.solve(rho, h)
+    ds = 0.05
+    want = sc.kick(c, sc.gather(pos, sc.field(phi, h), box), ds, ref)
+    beam = gpu_beam(bt, c, sp, 1e-9)
+    trk = bt.Tracker(n)
+    grid = bt.Grid(n, DEV, lo=box.lo, hi=box.hi)
+    grid.h = list(h)
+    grid.phi.copy_(torch.tensor(phi.ravel(), device=DEV))
+    trk.gather_kick(beam, grid, ds)
+    got = to_np(beam)
+    assert coord_rel_err(got, want) <= 1e-14
+    # the kick itself (the change of momenta) to the same tolerance as the grids
+    for r in (1, 3, 5):
+        assert grid_rel_err(got[r] - c[r], want[r] - c[r]) <= 1e-12
+
+
+# ------------------------------------------------------------------- moments
+
+def test_moments_match_oracle(bt):
+    c = bg.gaussian_with_halo(123_457, seed=2)
+    beam = gpu_beam(bt, c, bg.PROTON_1GEV, 1e-9)
+    trk = bt.Tracker(8)
+    m = trk.moments(beam).cpu().numpy()
+    ref = tr.moments_vector(c)
+    assert np.abs(m - ref).max() <= 1e-12 * np.abs(ref).max()
+    m2 = trk.moments(beam).cpu().numpy()
+    assert np.array_equal(m, m2)
+
+
+# ------------------------------------------------------------------ tracking
+
+def _track_both(bt, coords, species, charge, lattice, n, space_charge=True, first=0, nk=None):
+    ref = oracle_ref(species)
+    otr = tr.Tracker(ref, charge, n, space_charge=space_charge)
+    want = otr.track(coords, lattice, first, nk)
+    beam = gpu_beam(bt, coords, species, charge)
+    trk = bt.Tracker(n)
+    trk.track(beam, lattice, first, -1 if nk is None else nk, space_charge)
+    trk.sync()
+    return to_np(beam), want, trk, otr
+
+
+@pytest.mark.parametrize("lat", ["fodo", "chicane"])
+def test_track_without_space_charge(bt, lat):
+    lattice = bg.fodo_lattice(3, 4) if lat == "fodo" else bg.chicane_lattice(5)
+    sp = bg.PROTON_2GEV if lat == "fodo" else bg.ELECTRON_500MEV
+    c = bg.gaussian6d(5_001, seed=7)
+    got, want, _, _ = _track_both(bt, c, sp, 1e-9, lattice, 8, space_charge=False)
+    assert coord_rel_err(got, want) <= 1e-13
+
+
+def test_track_small_workload_full_run(bt):
+    """fodo_1e4_32: 1e4 particles, 2 GeV p, FODO x10, 250 kicks, 32^3, 1 nC."""
+    w = bg.workload("fodo_1e4_32")
+    c = w.particles()
+    got, want, trk, otr = _track_both(bt, c, w.species, w.bunch_charge_C, w.lattice, w.n_grid)
+    assert trk.regrid_log() == otr.regrid_log
+    assert coord_rel_err(got, want) <= REL_TOL
+
+
+def test_track_chicane_electrons_ragged(bt):
+    c = bg.gaussian6d(7_777, seed=11)
+    lattice = bg.chicane_lattice(3)
+    got, want, trk, otr = _track_both(bt, c, bg.ELECTRON_500MEV, 1e-9, lattice, 16)
+    assert trk.regrid_log() == otr.regrid_log
+    assert coord_rel_err(got, want) <= REL_TOL
+
+
+def test_track_in_pieces_equals_one_call(bt):
+    w = bg.workload("fodo_1e4_32")
+    c = w.particles(4_000)
+    sp = bt.Species(w.species.mass_MeV, w.species.kinetic_MeV, w.species.charge_sign)
+    a = bt.Beam(torch.tensor(c, device=DEV), sp, 1e-9)
+    b = bt.Beam(torch.tensor(c, device=DEV), sp, 1e-9)
+    t1, t2 = bt.Tracker(16), bt.Tracker(16)
+    t1.track(a, w.lattice, 0, 30)
+    t2.track(b, w.lattice, 0, 12)
+    t2.track(b, w.lattice, 12, 18)
+    torch.cuda.synchronize()
+    # merged half-maps across the call boundary round differently: compare to 1e-13
+    assert coord_rel_err(to_np(a), to_np(b)) <= 1e-13
+    assert t1.regrid_log() == t2.regrid_log()
+
+
+@pytest.mark.parametrize("npart", [0, 1, 2, 3])
+def test_track_degenerate_bunches(bt, npart):
+    """Empty bunch, a single particle (all extents zero, floored box) and
+    two/three particles.  A lone macroparticle sits at the centre of its box,
+    so its CIC self-field vanishes in exact arithmetic; at 1 nC in a 1e-6 m
+    box the rounding-level asymmetry is amplified by fields of ~1e14 V/m, so
+    the bitwise-sensitive comparison uses a femtocoulomb bunch and the 1 nC
+    run checks finiteness and the regrid log."""
+    c = bg.gaussian6d(npart, seed=1)
+    lattice = bg.fodo_lattice(1, 2)
+    got, want, trk, otr = _track_both(bt, c, bg.PROTON_2GEV, 1e-15, lattice, 8)
+    assert got.shape == want.shape
+    if npart:
+        assert np.all(np.isfinite(got))
+        assert coord_rel_err(got, want) <= REL_TOL
+        assert trk.regrid_log() == otr.regrid_log
+        got, want, trk, otr = _track_both(bt, c, bg.PROTON_2GEV, 1e-9, lattice, 8)
+        assert np.all(np.isfinite(got))
+        assert trk.regrid_log() == otr.regrid_log
+
+
+def test_track_is_bitwise_reproducible(bt):
+    w = bg.workload("fodo_1e4_32")
+    c = w.particles()
+    outs = []
+    for _ in range(3):
+        beam = gpu_beam(bt, c, w.species, w.bunch_charge_C)
+        trk = bt.Tracker(w.n_grid)
+        trk.track(beam, w.lattice, 0, 40)
+        outs.append(to_np(beam))
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_track_reports_nonfinite(bt):
+    c = bg.gaussian6d(1000, seed=1)
+    c[3, 17] = np.inf
+    beam = gpu_beam(bt, c, bg.PROTON_2GEV, 1e-9)
+    trk = bt.Tracker(8)
+    from paper_2208_02382_b300 import _lib as L
+    with pytest.raises(L.BeamtrackError) as e:
+        trk.track(beam, bg.fodo_lattice(1, 1), 0, 2)
+        trk.sync()
+    assert e.value.code == L.BX_NONFINITE
+
+
+def test_track_medium_workload_first_kicks(bt):
+    """fodo_1e6_64 at full size (1e6 particles with halo, 64^3), first 6 kicks."""
+    w = bg.workload("fodo_1e6_64")
+    c = w.particles()
+    got, want, trk, otr = _track_both(bt, c, w.species, w.bunch_charge_C, w.lattice, w.n_grid,
+                                      nk=6)
+    assert trk.regrid_log() == otr.regrid_log
+    assert coord_rel_err(got, want) <= REL_TOL
