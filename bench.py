@@ -1,0 +1,364 @@
+"""Benchmark of the space-charge tracking step (one JSON line on rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload chicane_25e6_128]
+
+A step is one s-step of the split-operator tracking (one slice: merged
+half-maps, box rule, CIC deposit, Hockney/IGF Poisson solve, field, gather +
+kick) over the whole bunch.  The metric is particle-steps per second with space
+charge on the 128^3 grid.  Multi-GPU runs (torchrun) are independent replicas
+(the single-bunch step is not sharded); `value` sums all ranks' particle-steps
+over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import beamgen as bg  # noqa: E402
+
+METRIC = "particle-steps/s with space charge (128^3 grid)"
+UNIT = "particle-steps/s"
+FP64_PEAK_TFLOPS = 1.25   # nominal B300 FP64 (no FP64 peak in MEASURED_PEAKS.json)
+
+# Algorithmic work per launch of each kernel kind, for the roofline of the
+# dominant kernel.  (bound, unit, f(n_particles, n_grid) -> amount per launch)
+#   gather_kick_push: per particle 98 FP64 flops (Z 1, u 6, fractions 3,
+#     CIC weights 15, 8-node x 3-component gather 48, kick 3, merged map 22)
+#   deposit: per particle 24 bytes (x, y, t read)
+#   fft_x / fft_yz: one pass of 1D complex FFTs over the (2n)^3 grid,
+#     5 m log2 m flops per line of length m = 2n, m^2 lines
+ALGO = {
+    "gather_kick_push": ("alu", "TFLOP/s", lambda npart, n: 98.0 * npart),
+    "deposit": ("hbm", "GB/s", lambda npart, n: 24.0 * npart),
+    "fft_x": ("alu", "TFLOP/s", lambda npart, n: 5.0 * (2 * n) ** 3 * math.log2(2 * n)),
+    "fft_yz": ("alu", "TFLOP/s", lambda npart, n: 5.0 * (2 * n) ** 3 * math.log2(2 * n)),
+}
+KERNEL_SOURCES = {
+    "gather_kick_push": "particles.cu", "deposit": "particles.cu",
+    "fft_x": "fft.cu", "fft_yz": "fft.cu",
+}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=495)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="chicane_25e6_128")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def repeated_lattice(w: bg.Workload, kicks: int):
+    reps = max(1, math.ceil(kicks / w.kicks))
+    return w.lattice * reps
+
+
+def traffic_for(kernel: str, n_units_launch: float):
+    """DRAM bytes per launch from the committed ncu capture, scaled to this
+    launch; null when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        tab = json.load(open(path))
+    except Exception:
+        return None
+    e = tab.get(kernel)
+    src = KERNEL_SOURCES.get(kernel)
+    if not e or not src:
+        return None
+    h = hashlib.sha256(open(os.path.join(ROOT, "paper_2208_02382_b300", "csrc", src),
+                            "rb").read()).hexdigest()[:16]
+    if e.get("source_sha") != h:
+        return None
+    return e["bytes_per_unit"] * n_units_launch
+
+
+def cpu_baseline(w: bg.Workload, sample_particles: int, kicks_timed: int = 1):
+    """The oracle as it stands on a bounded sample of the workload: one warm
+    kick (first box and Green's function), then `kicks_timed` timed kicks of
+    `sample_particles` particles at the workload's grid."""
+    from oracle import physics as ph
+    from oracle import track as tr
+    sp = w.species
+    ref = ph.RefPart(sp.mass_MeV, sp.kinetic_MeV, sp.charge_sign)
+    c = w.particles(sample_particles)
+    t = tr.Tracker(ref, w.bunch_charge_C, w.n_grid)
+    c = t.track(c, w.lattice, 0, 1)
+    nreg = len(t.regrid_log)
+    t0 = time.perf_counter()
+    t.track(c, w.lattice, 1, kicks_timed)
+    dt = time.perf_counter() - t0
+    regrid_in_timed = len(t.regrid_log) > nreg
+    cores = (os.cpu_count() or 1) if regrid_in_timed else 1
+    return {"value": sample_particles * kicks_timed / dt, "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": f"{sample_particles} of {w.n_particles} particles of {w.name}, "
+                      f"{kicks_timed} kick(s) after one warm kick, full {w.n_grid}^3 grid "
+                      f"({'with' if regrid_in_timed else 'no'} Green's function rebuild); "
+                      f"numpy single-threaded, Green's function OpenMP",
+            "seconds": dt}
+
+
+def run_reference(args, w):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    sample = 1_000_000
+    from oracle import physics as ph
+    from oracle import track as tr
+    sp = w.species
+    ref = ph.RefPart(sp.mass_MeV, sp.kinetic_MeV, sp.charge_sign)
+    c = w.particles(sample)
+    lat = repeated_lattice(w, args.warmup + args.steps + 1)
+    t = tr.Tracker(ref, w.bunch_charge_C, w.n_grid)
+    c = t.track(c, lat, 0, max(1, min(args.warmup, 1)))
+    start = t.kick_index
+    budget = 150.0
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < args.steps:
+        c = t.track(c, lat, start + steps, 1)
+        steps += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    dt = time.perf_counter() - t0
+    value = sample * steps / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": 1, "ms_per_step": dt / steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": w.name, "particles": w.n_particles, "grid": w.n_grid,
+                       "sample_particles": sample, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{sample} of {w.n_particles} particles per step at the "
+                                       f"full {w.n_grid}^3 grid; {steps} of {args.steps} steps "
+                                       f"timed within a {budget:.0f} s budget"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, w):
+    import torch
+    import paper_2208_02382_b300 as btk
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    sp = btk.Species(w.species.mass_MeV, w.species.kinetic_MeV, w.species.charge_sign)
+    coords_h = w.particles()
+    if rank:
+        coords_h = bg.gaussian6d(w.n_particles, w.sigmas, seed=w.seed + rank)
+    npart = coords_h.shape[1]
+    lat = repeated_lattice(w, args.warmup + args.steps)
+    beam = btk.Beam(torch.tensor(coords_h, dtype=torch.float64, device=dev), sp, w.bunch_charge_C)
+    trk = btk.Tracker(w.n_grid)
+    stream = torch.cuda.current_stream()
+    # warm-up (first box and Green's function build happen here)
+    trk.track(beam, lat, 0, args.warmup)
+    trk.sync()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    trk.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        ev0.record(stream)
+        trk.track(beam, lat, args.warmup, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    trk.sync()
+    ms = ev0.elapsed_time(ev1)
+    prof = trk.profile_read()
+    trk.profile(False)
+    if pg:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+        pg.barrier()
+    value = world * npart * args.steps / (ms * 1e-3)
+    launches = int(sum(v[1] for v in prof.values()))
+    # dominant kernel and its roofline
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dname, (dms, dcnt) = dom[0], dom[1]
+    roof = None
+    peaks = measured_peaks()
+    if dname in ALGO and dcnt > 0:
+        bound, unit, f = ALGO[dname]
+        per_launch = f(npart, w.n_grid)
+        avg_s = dms / dcnt * 1e-3
+        if unit == "TFLOP/s":
+            achieved = per_launch / avg_s / 1e12
+            peak = FP64_PEAK_TFLOPS
+            peak_src = "nominal FP64 of the profiling recipe (no measured FP64 peak)"
+        else:
+            achieved = per_launch / avg_s / 1e9
+            peak = peaks.get("hbm_gbs", 6400.0)
+            peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+        units = npart if dname in ("gather_kick_push", "deposit") else 1
+        roof = {"kernel": dname, "bound": bound, "achieved": achieved, "peak": peak,
+                "unit": unit, "frac": achieved / peak, "peak_source": peak_src,
+                "traffic": traffic_for(dname, units), "avg_launch_ms": dms / dcnt,
+                "launches": dcnt, "share_of_step": dms / ms}
+    # end to end through the public API from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        pinned = torch.from_numpy(coords_h).pin_memory()
+        out_h = torch.empty_like(pinned).pin_memory()
+        mom_h = torch.empty(27, dtype=torch.float64).pin_memory()
+        k_e2e = min(args.steps, 200)
+        trk2 = btk.Tracker(w.n_grid)
+        beam2 = btk.Beam(torch.empty_like(beam.coords), sp, w.bunch_charge_C)
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        beam2.coords.copy_(pinned, non_blocking=True)
+        for k in range(k_e2e):
+            trk2.track(beam2, lat, k, 1)
+            mom_h.copy_(trk2.moments(beam2), non_blocking=True)
+        out_h.copy_(beam2.coords, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        trk2.sync()
+        if pg:
+            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        bunch_bytes = 6 * 8 * npart
+        e2e = {"value": world * npart * k_e2e / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": (bunch_bytes + k_e2e * 0) / k_e2e,
+               "d2h_bytes_per_step": (bunch_bytes + k_e2e * 27 * 8) / k_e2e,
+               "steps": k_e2e,
+               "what": "bunch H2D from pinned memory once, then per step bx_track of one "
+                       "kick (lattice from host) and bx_moments read back (slice "
+                       "diagnostics), final bunch D2H; bytes per step are totals / steps"}
+        trk2.close()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, sample_particles=2_000_000)
+    if rank == 0:
+        clocks = clk.summary()
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": w.name, "particles": npart, "grid": w.n_grid,
+                           "doubled_grid": 2 * w.n_grid, "kicks_in_lattice": w.kicks,
+                           "step": "one slice: map, box rule, deposit, solve, gather+kick",
+                           "l2": f"inputs larger than L2 (particle SoA {npart * 48 / 1e9:.2f} GB)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks, "wall_s_timed": wall,
+                "kernels_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]}}
+        print(json.dumps(line), flush=True)
+    trk.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    w = bg.workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -193,6 +193,22 @@ int32_t bx_regrid_log(bx_ctx *ctx, int64_t *out_host, int64_t cap, int64_t *coun
 /* The current box (host copy; synchronous).  Returns BX_BAD_ARG if no box yet. */
 int32_t bx_get_box(bx_ctx *ctx, double lo[3], double hi[3], double h[3]);
 
+/* Kernel-level profiling (the paper's ABLASTR layer lists profiling among its
+ * reused routines).  Every kernel launch of this context is counted per
+ * kernel; with timing = 1 each launch is also bracketed by a pair of CUDA
+ * events on its stream.  bx_profile resets counts and times. */
+int32_t bx_profile(bx_ctx *ctx, int32_t timing);
+
+/* Read the profile (synchronous: waits for the recorded events).  ms[k] and
+ * launches[k] receive the summed device time and the launch count of kernel
+ * k for k < min(cap, *count); *count receives the number of kernel kinds.
+ * Either array may be NULL. */
+int32_t bx_profile_read(bx_ctx *ctx, double *ms, int64_t *launches, int32_t cap,
+                        int32_t *count);
+
+/* Name of kernel kind `id` (0 <= id < count of bx_profile_read), or "". */
+const char *bx_kernel_name(int32_t id);
+
 /* Wait for the stream and return the device status word (then clear it). */
 int32_t bx_sync(bx_ctx *ctx, void *stream);
 

@@ -55,6 +55,10 @@ SIGNATURES = {
     "bx_regrid_log": (c_int32, [c_void_p, POINTER(c_int64), c_int64, POINTER(c_int64)]),
     "bx_get_box": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_double), POINTER(c_double)]),
     "bx_sync": (c_int32, [c_void_p, c_void_p]),
+    "bx_profile": (c_int32, [c_void_p, c_int32]),
+    "bx_profile_read": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_int64), c_int32,
+                                  POINTER(c_int32)]),
+    "bx_kernel_name": (c_char_p, [c_int32]),
     "bx_last_error": (c_char_p, [c_void_p]),
 }
 

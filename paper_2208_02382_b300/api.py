@@ -193,5 +193,18 @@ class Tracker:
         _check(self.lib, self.ctx, self.lib.bx_get_box(self.ctx, lo, hi, h))
         return list(lo), list(hi), list(h)
 
+    def profile(self, timing: bool = True):
+        _check(self.lib, self.ctx, self.lib.bx_profile(self.ctx, 1 if timing else 0))
+
+    def profile_read(self) -> dict:
+        """{kernel name: (device ms, launches)} since the last profile() call."""
+        cap = 64
+        ms = (ctypes.c_double * cap)()
+        cnt = (ctypes.c_int64 * cap)()
+        k = ctypes.c_int32()
+        _check(self.lib, self.ctx, self.lib.bx_profile_read(self.ctx, ms, cnt, cap,
+                                                            ctypes.byref(k)))
+        return {self.lib.bx_kernel_name(i).decode(): (ms[i], cnt[i]) for i in range(k.value)}
+
     def sync(self):
         _check(self.lib, self.ctx, self.lib.bx_sync(self.ctx, _stream()))

@@ -35,6 +35,7 @@ struct bx_ctx {
     bool green_valid = false;
     double green_h[3] = {0, 0, 0};
     long long kick = 0;
+    Profiler *prof = nullptr;
     std::string err;
 };
 
@@ -251,6 +252,7 @@ int32_t bx_create(bx_ctx **out, const bx_options *opt) {
     bx_ctx *ctx = new (std::nothrow) bx_ctx();
     if (!ctx) return fail(nullptr, BX_OUT_OF_MEMORY, "host allocation");
     ctx->n = n;
+    ctx->prof = profiler_new();
     const size_t n3 = (size_t)n * n * n, q3 = (size_t)(n + 2) * (n + 2) * (n + 2);
     const size_t o3 = (size_t)(n + 1) * (n + 1) * (n + 1);
     cudaError_t e = cudaSuccess;
@@ -294,6 +296,7 @@ int32_t bx_destroy(bx_ctx *ctx) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     fft_plan_free(&ctx->plan);
+    profiler_free(ctx->prof);
     delete ctx;
     return BX_OK;
 }
@@ -310,6 +313,7 @@ int32_t bx_reset(bx_ctx *ctx) {
 int32_t bx_track(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t first_kick,
                  int64_t nkicks, void *stream) {
     if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
+    ProfScope prof_scope(ctx->prof);
     int32_t rc = check_beam(ctx, beam);
     if (rc) return rc;
     if ((rc = check_lattice(ctx, lat))) return rc;
@@ -395,6 +399,7 @@ int32_t bx_track(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t firs
 
 int32_t bx_deposit(bx_ctx *ctx, const bx_beam *beam, bx_grid *grid, void *stream) {
     if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
+    ProfScope prof_scope(ctx->prof);
     int32_t rc = check_beam(ctx, beam);
     if (rc) return rc;
     if ((rc = check_grid(ctx, grid, true, false))) return rc;
@@ -438,6 +443,7 @@ int32_t bx_deposit(bx_ctx *ctx, const bx_beam *beam, bx_grid *grid, void *stream
 
 int32_t bx_solve(bx_ctx *ctx, bx_grid *grid, void *stream) {
     if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
+    ProfScope prof_scope(ctx->prof);
     int32_t rc = check_grid(ctx, grid, true, true);
     if (rc) return rc;
     for (int d = 0; d < 3; ++d)
@@ -451,6 +457,7 @@ int32_t bx_solve(bx_ctx *ctx, bx_grid *grid, void *stream) {
 
 int32_t bx_gather_kick(bx_ctx *ctx, bx_beam *beam, const bx_grid *grid, double ds, void *stream) {
     if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
+    ProfScope prof_scope(ctx->prof);
     int32_t rc = check_beam(ctx, beam);
     if (rc) return rc;
     if ((rc = check_grid(ctx, grid, false, true))) return rc;
@@ -479,6 +486,7 @@ int32_t bx_gather_kick(bx_ctx *ctx, bx_beam *beam, const bx_grid *grid, double d
 
 int32_t bx_moments(bx_ctx *ctx, const bx_beam *beam, double *out, void *stream) {
     if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
+    ProfScope prof_scope(ctx->prof);
     int32_t rc = check_beam(ctx, beam);
     if (rc) return rc;
     if (!out) return fail(ctx, BX_BAD_ARG, "out is NULL");
@@ -497,6 +505,7 @@ int32_t bx_moments(bx_ctx *ctx, const bx_beam *beam, double *out, void *stream) 
 
 int32_t bx_green_table(bx_ctx *ctx, const double h[3], double *out, void *stream) {
     if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
+    ProfScope prof_scope(ctx->prof);
     if (!h || !out) return fail(ctx, BX_BAD_ARG, "NULL argument");
     for (int d = 0; d < 3; ++d)
         if (!(h[d] > 0.0) || !std::isfinite(h[d])) return fail(ctx, BX_BAD_ARG, "h must be > 0");
@@ -545,6 +554,23 @@ int32_t bx_sync(bx_ctx *ctx, void *stream) {
     if (st & ST_OUTSIDE) return fail(ctx, BX_BAD_ARG, "a particle lies outside the given box");
     return BX_OK;
 }
+
+int32_t bx_profile(bx_ctx *ctx, int32_t timing) {
+    if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
+    profiler_enable(ctx->prof, timing != 0);
+    return BX_OK;
+}
+
+int32_t bx_profile_read(bx_ctx *ctx, double *ms, int64_t *launches, int32_t cap, int32_t *count) {
+    if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
+    if (cap < 0 || (cap > 0 && !ms && !launches)) return fail(ctx, BX_BAD_ARG, "bad output arrays");
+    static_assert(sizeof(long long) == sizeof(int64_t), "int64");
+    CK(profiler_read(ctx->prof, ms, (long long *)launches, cap), "profile read");
+    if (count) *count = K_COUNT;
+    return BX_OK;
+}
+
+const char *bx_kernel_name(int32_t id) { return kernel_name(id); }
 
 const char *bx_last_error(const bx_ctx *ctx) {
     return ctx ? ctx->err.c_str() : g_create_err.c_str();

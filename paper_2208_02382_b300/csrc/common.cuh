@@ -65,6 +65,38 @@ __host__ __device__ __forceinline__ double dkey_inv(long long k) {
 constexpr int DEP_FRAC_BITS = 51;
 constexpr int DEP_SPLIT = 31;
 
+// ---- kernel-level profiler (profile.cu) -----------------------------------
+// Every kernel launch goes through BT_LAUNCH, which counts launches per kernel
+// and, when timing is on for the calling context, brackets the launch with a
+// pair of CUDA events on the launch stream.
+enum KernelId : int {
+    K_PUSH, K_MINMAX, K_BOX, K_IGF_CORNER, K_IGF_SUM, K_DEPOSIT, K_ACC_TO_RHO, K_FFT_PAD,
+    K_FFT_X, K_FFT_YZ, K_FFT_MUL, K_FFT_EXTRACT, K_GREEN_FILL, K_GREEN_TAKE, K_FIELD, K_GATHER,
+    K_MOMENTS, K_TWIDDLE, K_COUNT
+};
+
+struct Profiler;
+const char *kernel_name(int id);
+void prof_begin(int id, cudaStream_t s);
+void prof_end(int id, cudaStream_t s);
+Profiler *profiler_new();
+void profiler_free(Profiler *p);
+void profiler_enable(Profiler *p, bool on);
+cudaError_t profiler_read(Profiler *p, double *ms, long long *launches, int cap);
+// Makes `p` the profiler of the calling thread for the current scope.
+struct ProfScope {
+    explicit ProfScope(Profiler *p);
+    ~ProfScope();
+    Profiler *prev;
+};
+
+#define BT_LAUNCH(id, s, ...)               \
+    do {                                     \
+        ::bt::prof_begin((id), (s));         \
+        __VA_ARGS__;                         \
+        ::bt::prof_end((id), (s));           \
+    } while (0)
+
 // ---- launchers (defined in the .cu files) --------------------------------
 // particles.cu
 cudaError_t launch_push_maps(double *const c[6], int64_t n, const MapCoef *maps, int nmaps,

@@ -171,7 +171,7 @@ cudaError_t fft_plan_init(FftPlan *p, int n) {
     cudaFuncSetAttribute(k_fft_x<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_fft_yz<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_fft_yz<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_twiddle<<<(p->m / 2 + 255) / 256, 256>>>(p->tw, p->m);
+    BT_LAUNCH(K_TWIDDLE, (cudaStream_t)0, k_twiddle<<<(p->m / 2 + 255) / 256, 256>>>(p->tw, p->m));
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     return e;
@@ -193,13 +193,13 @@ static cudaError_t fft3d(const FftPlan *p, cudaStream_t s) {
     const size_t smyz = (size_t)FFT_TX * m * sizeof(double2);
     dim3 gyz(m / FFT_TX, m);
     if (!INV) {
-        k_fft_x<INV><<<(m * m) / FFT_LPB, FFT_TPB, smx, s>>>(p->buf, m, logm, p->tw);
-        k_fft_yz<INV><<<gyz, FFT_TPB, smyz, s>>>(p->buf, m, logm, 1, p->tw);
-        k_fft_yz<INV><<<gyz, FFT_TPB, smyz, s>>>(p->buf, m, logm, 2, p->tw);
+        BT_LAUNCH(K_FFT_X, s, k_fft_x<INV><<<(m * m) / FFT_LPB, FFT_TPB, smx, s>>>(p->buf, m, logm, p->tw));
+        BT_LAUNCH(K_FFT_YZ, s, k_fft_yz<INV><<<gyz, FFT_TPB, smyz, s>>>(p->buf, m, logm, 1, p->tw));
+        BT_LAUNCH(K_FFT_YZ, s, k_fft_yz<INV><<<gyz, FFT_TPB, smyz, s>>>(p->buf, m, logm, 2, p->tw));
     } else {
-        k_fft_yz<INV><<<gyz, FFT_TPB, smyz, s>>>(p->buf, m, logm, 2, p->tw);
-        k_fft_yz<INV><<<gyz, FFT_TPB, smyz, s>>>(p->buf, m, logm, 1, p->tw);
-        k_fft_x<INV><<<(m * m) / FFT_LPB, FFT_TPB, smx, s>>>(p->buf, m, logm, p->tw);
+        BT_LAUNCH(K_FFT_YZ, s, k_fft_yz<INV><<<gyz, FFT_TPB, smyz, s>>>(p->buf, m, logm, 2, p->tw));
+        BT_LAUNCH(K_FFT_YZ, s, k_fft_yz<INV><<<gyz, FFT_TPB, smyz, s>>>(p->buf, m, logm, 1, p->tw));
+        BT_LAUNCH(K_FFT_X, s, k_fft_x<INV><<<(m * m) / FFT_LPB, FFT_TPB, smx, s>>>(p->buf, m, logm, p->tw));
     }
     return cudaGetLastError();
 }
@@ -207,24 +207,24 @@ static cudaError_t fft3d(const FftPlan *p, cudaStream_t s) {
 cudaError_t solve_rho_to_phi(const FftPlan *p, const double *rho, double *phi, cudaStream_t s) {
     const int n = p->n, m = p->m;
     const long long m3 = (long long)m * m * m;
-    k_pad_rho<<<blocks_for(m3), FFT_TPB, 0, s>>>(rho, n, m, p->buf);
+    BT_LAUNCH(K_FFT_PAD, s, k_pad_rho<<<blocks_for(m3), FFT_TPB, 0, s>>>(rho, n, m, p->buf));
     cudaError_t e = fft3d<false>(p, s);
     if (e != cudaSuccess) return e;
-    k_mul_real<<<blocks_for(m3), FFT_TPB, 0, s>>>(p->buf, p->ghat, m3);
+    BT_LAUNCH(K_FFT_MUL, s, k_mul_real<<<blocks_for(m3), FFT_TPB, 0, s>>>(p->buf, p->ghat, m3));
     e = fft3d<true>(p, s);
     if (e != cudaSuccess) return e;
     const long long q3 = (long long)(n + 2) * (n + 2) * (n + 2);
-    k_extract_phi<<<blocks_for(q3), FFT_TPB, 0, s>>>(p->buf, n, m, 1.0 / (double)m3, phi);
+    BT_LAUNCH(K_FFT_EXTRACT, s, k_extract_phi<<<blocks_for(q3), FFT_TPB, 0, s>>>(p->buf, n, m, 1.0 / (double)m3, phi));
     return cudaGetLastError();
 }
 
 cudaError_t green_spectrum_from_table(const FftPlan *p, const double *gtable, cudaStream_t s) {
     const int n = p->n, m = p->m;
     const long long m3 = (long long)m * m * m;
-    k_fill_green<<<blocks_for(m3), FFT_TPB, 0, s>>>(gtable, n, m, p->buf);
+    BT_LAUNCH(K_GREEN_FILL, s, k_fill_green<<<blocks_for(m3), FFT_TPB, 0, s>>>(gtable, n, m, p->buf));
     cudaError_t e = fft3d<false>(p, s);
     if (e != cudaSuccess) return e;
-    k_take_real<<<blocks_for(m3), FFT_TPB, 0, s>>>(p->buf, p->ghat, m3);
+    BT_LAUNCH(K_GREEN_TAKE, s, k_take_real<<<blocks_for(m3), FFT_TPB, 0, s>>>(p->buf, p->ghat, m3));
     return cudaGetLastError();
 }
 

@@ -90,8 +90,8 @@ cudaError_t launch_igf_table(int n, const double h[3], double *fcorner, double *
     const int m = n + 2, q = n + 1;
     long long tc = (long long)m * m * m, ts = (long long)q * q * q;
     int bc = (int)((tc + 127) / 128), bs = (int)((ts + 255) / 256);
-    k_igf_corner<<<bc, 128, 0, s>>>(n, h[0], h[1], h[2], (double2 *)fcorner);
-    k_igf_sum<<<bs, 256, 0, s>>>(n, (const double2 *)fcorner, gtable);
+    BT_LAUNCH(K_IGF_CORNER, s, k_igf_corner<<<bc, 128, 0, s>>>(n, h[0], h[1], h[2], (double2 *)fcorner));
+    BT_LAUNCH(K_IGF_SUM, s, k_igf_sum<<<bs, 256, 0, s>>>(n, (const double2 *)fcorner, gtable));
     return cudaGetLastError();
 }
 

@@ -86,10 +86,10 @@ __global__ void k_mom_final(const double *__restrict__ partial, int nblocks, int
 
 cudaError_t launch_moments(double *const c[6], int64_t n, double *partials, int nblocks,
                            double *out, cudaStream_t s) {
-    k_mom_sum<<<nblocks, MOM_TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5], n, partials);
-    k_mom_final<<<1, 32, 0, s>>>(partials, nblocks, 6, n, out, 0);
-    k_mom_cov<<<nblocks, MOM_TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5], n, out, partials);
-    k_mom_final<<<1, 32, 0, s>>>(partials, nblocks, 21, n, out, 6);
+    BT_LAUNCH(K_MOMENTS, s, k_mom_sum<<<nblocks, MOM_TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5], n, partials));
+    BT_LAUNCH(K_MOMENTS, s, k_mom_final<<<1, 32, 0, s>>>(partials, nblocks, 6, n, out, 0));
+    BT_LAUNCH(K_MOMENTS, s, k_mom_cov<<<nblocks, MOM_TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5], n, out, partials));
+    BT_LAUNCH(K_MOMENTS, s, k_mom_final<<<1, 32, 0, s>>>(partials, nblocks, 21, n, out, 6));
     return cudaGetLastError();
 }
 

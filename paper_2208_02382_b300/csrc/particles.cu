@@ -52,7 +52,7 @@ __global__ void k_push_maps(double *__restrict__ x, double *__restrict__ px,
 cudaError_t launch_push_maps(double *const c[6], int64_t n, const MapCoef *maps, int nmaps,
                              cudaStream_t s) {
     if (n <= 0 || nmaps <= 0) return cudaSuccess;
-    k_push_maps<<<grid_for(n), TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5], n, maps, nmaps);
+    BT_LAUNCH(K_PUSH, s, k_push_maps<<<grid_for(n), TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5], n, maps, nmaps));
     return cudaGetLastError();
 }
 
@@ -116,8 +116,8 @@ __global__ void k_minmax(const double *__restrict__ x, const double *__restrict_
 cudaError_t launch_minmax(double *const c[6], int64_t n, double betagamma, TrackState *st,
                           int32_t *status, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_minmax<<<grid_for(n), TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5], n, -betagamma, st,
-                                         status);
+    BT_LAUNCH(K_MINMAX, s, k_minmax<<<grid_for(n), TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5], n, -betagamma, st,
+                                         status));
     return cudaGetLastError();
 }
 
@@ -179,7 +179,7 @@ __global__ void k_box_rule(TrackState *st, int nn, long long *log, int64_t cap) 
 cudaError_t launch_box_rule(TrackState *st, int nn, int64_t n, long long *log, int64_t cap,
                             cudaStream_t s) {
     (void)n;
-    k_box_rule<<<1, 32, 0, s>>>(st, nn, log, cap);
+    BT_LAUNCH(K_BOX, s, k_box_rule<<<1, 32, 0, s>>>(st, nn, log, cap));
     return cudaGetLastError();
 }
 
@@ -266,8 +266,8 @@ cudaError_t launch_deposit(double *const c[6], int64_t n, double betagamma, cons
     e = cudaMemsetAsync(acc_lo, 0, nodes * 8, s);
     if (e != cudaSuccess) return e;
     if (n <= 0) return cudaSuccess;
-    k_deposit<<<grid_for(n), TPB, 0, s>>>(c[0], c[2], c[4], n, -betagamma, box, nn, acc_hi, acc_lo,
-                                          status);
+    BT_LAUNCH(K_DEPOSIT, s, k_deposit<<<grid_for(n), TPB, 0, s>>>(c[0], c[2], c[4], n, -betagamma, box, nn, acc_hi, acc_lo,
+                                          status));
     return cudaGetLastError();
 }
 
@@ -288,8 +288,8 @@ cudaError_t launch_acc_to_rho(const unsigned long long *acc_hi, const unsigned l
                               int nn, double q_macro, const Box *box, double *rho,
                               cudaStream_t s) {
     long long nodes = (long long)nn * nn * nn;
-    k_acc_to_rho<<<(int)((nodes + TPB - 1) / TPB), TPB, 0, s>>>(acc_hi, acc_lo, nodes, q_macro,
-                                                               box, rho);
+    BT_LAUNCH(K_ACC_TO_RHO, s, k_acc_to_rho<<<(int)((nodes + TPB - 1) / TPB), TPB, 0, s>>>(acc_hi, acc_lo, nodes, q_macro,
+                                                               box, rho));
     return cudaGetLastError();
 }
 
@@ -320,8 +320,8 @@ __global__ void k_field(const double *__restrict__ phi, int nn, const Box *box, 
 cudaError_t launch_field(const double *phi, int nn, const Box *box, double kx, double ky,
                          double kz, double *efield, cudaStream_t s) {
     long long nodes = (long long)nn * nn * nn;
-    k_field<<<(int)((nodes + TPB - 1) / TPB), TPB, 0, s>>>(phi, nn, box, kx, ky, kz,
-                                                          (Field4 *)efield);
+    BT_LAUNCH(K_FIELD, s, k_field<<<(int)((nodes + TPB - 1) / TPB), TPB, 0, s>>>(phi, nn, box, kx, ky, kz,
+                                                          (Field4 *)efield));
     return cudaGetLastError();
 }
 
@@ -401,9 +401,9 @@ cudaError_t launch_gather_kick_push(double *const c[6], int64_t n, double betaga
                                     const MapCoef *map, TrackState *st, int32_t *status,
                                     cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_gather_kick_push<<<grid_for(n), TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5], n,
+    BT_LAUNCH(K_GATHER, s, k_gather_kick_push<<<grid_for(n), TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5], n,
                                                    -betagamma, box, nn,
-                                                   (const Field4 *)efield, map, st, status);
+                                                   (const Field4 *)efield, map, st, status));
     return cudaGetLastError();
 }
 
