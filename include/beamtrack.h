@@ -209,6 +209,26 @@ int32_t bx_profile_read(bx_ctx *ctx, double *ms, int64_t *launches, int32_t cap,
 /* Name of kernel kind `id` (0 <= id < count of bx_profile_read), or "". */
 const char *bx_kernel_name(int32_t id);
 
+/* Charge deposition that allocates nothing, for callers that may not
+ * allocate device memory once they are running (for example an on-line model
+ * in an accelerator control loop with a fixed memory footprint, or a host
+ * framework that owns all device memory through its own pool).  The paper has
+ * no counterpart; it is the arithmetic of bx_deposit with use_box = 1 and
+ * needs no context.
+ * beam: as for bx_deposit (device arrays); lo, hi: host arrays, the box (the
+ * bunch must lie inside; particles outside are skipped); n: nodes per
+ * dimension, a power of two in [8, 64]; rho: device output of n^3 doubles.
+ * Scratch: the fixed-point accumulators live in one static device array of
+ * 2 x 64^3 x 8 bytes = 4 MiB that the library holds on every GPU that loads
+ * it until the process exits; n > 64 is rejected with BX_BAD_ARG.  Every call
+ * on a device shares that array and clears it first, so calls that overlap on
+ * the GPU race: order them on one stream.  The first call on a device looks up
+ * the array's device address with that device current and caches it; make
+ * that first call before any stream capture.  Asynchronous on `stream`;
+ * errors are returned at once and described by bx_last_error(NULL). */
+int32_t bx_deposit_noalloc(const bx_beam *beam, const double lo[3], const double hi[3],
+                           int32_t n, double *rho, void *stream);
+
 /* Wait for the stream and return the device status word (then clear it). */
 int32_t bx_sync(bx_ctx *ctx, void *stream);
 

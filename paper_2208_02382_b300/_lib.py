@@ -59,6 +59,8 @@ SIGNATURES = {
     "bx_profile_read": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_int64), c_int32,
                                   POINTER(c_int32)]),
     "bx_kernel_name": (c_char_p, [c_int32]),
+    "bx_deposit_noalloc": (c_int32, [POINTER(bx_beam), POINTER(c_double), POINTER(c_double),
+                                     c_int32, c_void_p, c_void_p]),
     "bx_last_error": (c_char_p, [c_void_p]),
 }
 

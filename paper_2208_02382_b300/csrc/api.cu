@@ -240,6 +240,8 @@ void init_state(TrackState *h) {
 
 }  // namespace
 
+int32_t bt::set_noctx_error(int32_t code, const char *msg) { return fail(nullptr, code, msg); }
+
 extern "C" {
 
 int32_t bx_create(bx_ctx **out, const bx_options *opt) {

@@ -97,6 +97,10 @@ struct ProfScope {
         ::bt::prof_end((id), (s));           \
     } while (0)
 
+// Records `msg` as the error text returned by bx_last_error(NULL) and returns
+// `code` (for entry points that take no context).
+int32_t set_noctx_error(int32_t code, const char *msg);
+
 // ---- launchers (defined in the .cu files) --------------------------------
 // particles.cu
 cudaError_t launch_push_maps(double *const c[6], int64_t n, const MapCoef *maps, int nmaps,
