@@ -384,9 +384,9 @@ int32_t bx_track(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t firs
         const Box *box = &ctx->st->box;
         CK(launch_deposit(c, beam->n, r.bg, box, ctx->n, ctx->acc_hi, ctx->acc_lo, ctx->status, s),
            "deposit");
-        CK(launch_acc_to_rho(ctx->acc_hi, ctx->acc_lo, ctx->n, q_macro, box, ctx->rho, s),
-           "rho");
-        CK(solve_rho_to_phi(&ctx->plan, ctx->rho, ctx->phi, s), "solve");
+        const double rho_scale = q_macro / (h.box.h[0] * h.box.h[1] * h.box.h[2]);
+        CK(solve_acc_to_phi(&ctx->plan, ctx->acc_hi, ctx->acc_lo, rho_scale, ctx->phi, s),
+           "solve");
         const double kt = r.sign * ds / (r.mass_eV * (r.bg * r.bg));
         const double kz = -r.sign * ds / (r.mass_eV * r.bg);
         CK(launch_field(ctx->phi, ctx->n, box, kt, kt, kz, ctx->efield, s), "field");

@@ -70,9 +70,9 @@ constexpr int DEP_SPLIT = 31;
 // and, when timing is on for the calling context, brackets the launch with a
 // pair of CUDA events on the launch stream.
 enum KernelId : int {
-    K_PUSH, K_MINMAX, K_BOX, K_IGF_CORNER, K_IGF_SUM, K_DEPOSIT, K_ACC_TO_RHO, K_FFT_PAD,
-    K_FFT_X, K_FFT_YZ, K_FFT_MUL, K_FFT_EXTRACT, K_GREEN_FILL, K_GREEN_TAKE, K_FIELD, K_GATHER,
-    K_MOMENTS, K_TWIDDLE, K_COUNT
+    K_PUSH, K_MINMAX, K_BOX, K_IGF_CORNER, K_IGF_SUM, K_DEPOSIT, K_ACC_TO_RHO, K_FFT_X,
+    K_FFT_YZ, K_FFT_ZSOLVE, K_FFT_XINV, K_GREEN_X, K_GREEN_YZ, K_FIELD, K_GATHER, K_MOMENTS,
+    K_TWIDDLE, K_COUNT
 };
 
 struct Profiler;
@@ -129,13 +129,17 @@ int moments_blocks(int64_t n);
 struct FftPlan {
     int n;            // physical grid nodes per dim
     int m;            // doubled size 2n
-    double2 *buf;     // m^3 complex work buffer
-    double2 *tw;      // m/2 twiddles exp(-2 pi i j/m)
-    double *ghat;     // m^3 real spectrum of the doubled Green's function
+    double2 *buf;     // spectrum work buffers, m*m*(n+1) complex each
+    double2 *buf2;
+    double2 *tw;      // m twiddles exp(-2 pi i j/m)
+    double *ghat;     // (n+1)^3 real even octant of the doubled Green's function spectrum
 };
 cudaError_t fft_plan_init(FftPlan *p, int n);
 void fft_plan_free(FftPlan *p);
 cudaError_t solve_rho_to_phi(const FftPlan *p, const double *rho, double *phi, cudaStream_t s);
+cudaError_t solve_acc_to_phi(const FftPlan *p, const unsigned long long *acc_hi,
+                             const unsigned long long *acc_lo, double scale, double *phi,
+                             cudaStream_t s);
 cudaError_t green_spectrum_from_table(const FftPlan *p, const double *gtable, cudaStream_t s);
 // igf.cu
 cudaError_t launch_igf_table(int n, const double h[3], double *fcorner, double *gtable,
