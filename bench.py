@@ -62,6 +62,8 @@ def parse():
     p.add_argument("--workload", default="chicane_25e6_128")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--particles", type=int, default=None,
+                   help="override the workload's particle count (small profiling cases)")
     return p.parse_args()
 
 
@@ -354,6 +356,8 @@ def main():
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     w = bg.workload(args.workload)
+    if args.particles:
+        w.n_particles = int(args.particles)
     if args.impl == "reference":
         run_reference(args, w)
     else:

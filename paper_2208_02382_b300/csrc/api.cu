@@ -35,6 +35,16 @@ struct bx_ctx {
     bool green_valid = false;
     double green_h[3] = {0, 0, 0};
     long long kick = 0;
+    EFix *efix = nullptr;                  // field in fixed point
+    unsigned long long *emax = nullptr;    // max |E'| per component (bits)
+    int *escale = nullptr;                 // fixed-point exponents
+    // particle binning scratch, sized for sort_n particles
+    int64_t sort_n = 0;
+    int *keys = nullptr;
+    long long *counts = nullptr, *offs = nullptr, *sums = nullptr, *id_scr = nullptr;
+    double *scr[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    double **dev_ptrs = nullptr;
+    int sort_interval = 16;                // kicks between re-binning
     Profiler *prof = nullptr;
     std::string err;
 };
@@ -224,6 +234,31 @@ int32_t ensure_maps(bx_ctx *ctx, size_t count) {
     return BX_OK;
 }
 
+// Binning scratch for n particles, allocated on the first call for a larger n.
+int32_t ensure_sort_scratch(bx_ctx *ctx, int64_t n) {
+    if (n <= ctx->sort_n) return BX_OK;
+    cudaDeviceSynchronize();
+    void **ps[] = {(void **)&ctx->keys, (void **)&ctx->counts, (void **)&ctx->offs,
+                   (void **)&ctx->sums, (void **)&ctx->id_scr, (void **)&ctx->scr[0],
+                   (void **)&ctx->scr[1], (void **)&ctx->scr[2], (void **)&ctx->scr[3],
+                   (void **)&ctx->scr[4], (void **)&ctx->scr[5]};
+    for (void **p : ps)
+        if (*p) {
+            cudaFree(*p);
+            *p = nullptr;
+        }
+    ctx->sort_n = 0;
+    const long long len = (long long)sort_bricks(ctx->n) * sort_chunks(n);
+    CK(cudaMalloc(&ctx->keys, n * sizeof(int)), "sort keys");
+    CK(cudaMalloc(&ctx->counts, len * sizeof(long long)), "sort counts");
+    CK(cudaMalloc(&ctx->offs, len * sizeof(long long)), "sort offsets");
+    CK(cudaMalloc(&ctx->sums, (len / 2048 + 2) * sizeof(long long)), "sort sums");
+    CK(cudaMalloc(&ctx->id_scr, n * sizeof(long long)), "sort ids");
+    for (int k = 0; k < 6; ++k) CK(cudaMalloc(&ctx->scr[k], n * sizeof(double)), "sort arrays");
+    ctx->sort_n = n;
+    return BX_OK;
+}
+
 int32_t read_state(bx_ctx *ctx, TrackState *h, cudaStream_t s) {
     CK(cudaMemcpyAsync(h, ctx->st, sizeof(TrackState), cudaMemcpyDeviceToHost, s), "read state");
     CK(cudaStreamSynchronize(s), "sync");
@@ -272,6 +307,10 @@ int32_t bx_create(bx_ctx **out, const bx_options *opt) {
     A((void **)&ctx->tmp_box, sizeof(Box));
     A((void **)&ctx->status, sizeof(int32_t));
     A((void **)&ctx->log, ctx->log_cap * sizeof(long long));
+    A((void **)&ctx->efix, n3 * sizeof(EFix));
+    A((void **)&ctx->emax, 3 * sizeof(unsigned long long));
+    A((void **)&ctx->escale, 4 * sizeof(int));
+    A((void **)&ctx->dev_ptrs, 12 * sizeof(double *));
     if (e == cudaSuccess) e = fft_plan_init(&ctx->plan, n);
     if (e == cudaSuccess) {
         TrackState h;
@@ -294,7 +333,9 @@ int32_t bx_destroy(bx_ctx *ctx) {
     cudaDeviceSynchronize();
     void *ptrs[] = {ctx->acc_hi, ctx->acc_lo, ctx->rho, ctx->phi, ctx->efield, ctx->fcorner,
                     ctx->gtable, ctx->st, ctx->tmp_box, ctx->status, ctx->log,
-                    ctx->mom_partial, ctx->maps};
+                    ctx->mom_partial, ctx->maps, ctx->efix, ctx->emax, ctx->escale,
+                    ctx->dev_ptrs, ctx->keys, ctx->counts, ctx->offs, ctx->sums, ctx->id_scr,
+                    ctx->scr[0], ctx->scr[1], ctx->scr[2], ctx->scr[3], ctx->scr[4], ctx->scr[5]};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     fft_plan_free(&ctx->plan);
@@ -366,8 +407,17 @@ int32_t bx_track(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t firs
         return BX_OK;
     }
     const double q_macro = r.sign * std::fabs(beam->bunch_charge_C) / (double)beam->n;
+    const bool binning = beam->id != nullptr;
+    if (binning && (rc = ensure_sort_scratch(ctx, beam->n))) return rc;
+    // Per kick k: box rule on the current positions; the charge of those
+    // positions is already in the accumulators (deposited by the previous
+    // kick's particle kernel with the same box) unless this is the first kick
+    // or the box changed, in which case it is deposited here; re-binning every
+    // sort_interval kicks; solve; field; then one particle kernel does the
+    // gather, kick, merged half-maps and the next kick's deposit.
     CK(launch_push_maps(c, beam->n, ctx->maps, 1, s), "push");
     CK(launch_minmax(c, beam->n, r.bg, ctx->st, ctx->status, s), "minmax");
+    const size_t acc_bytes = (size_t)ctx->n * ctx->n * ctx->n * sizeof(unsigned long long);
     for (int64_t k = 0; k < nkicks; ++k) {
         const double ds = sds[first_kick + k];
         CK(cudaMemcpyAsync(&ctx->st->kick, &ctx->kick, sizeof(long long), cudaMemcpyHostToDevice,
@@ -382,18 +432,32 @@ int32_t bx_track(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t firs
                 return fail(ctx, BX_NONFINITE, "non-finite particle coordinates");
         if ((rc = ensure_green(ctx, h.box.h, s))) return rc;
         const Box *box = &ctx->st->box;
-        CK(launch_deposit(c, beam->n, r.bg, box, ctx->n, ctx->acc_hi, ctx->acc_lo, ctx->status, s),
-           "deposit");
+        if (binning && k % ctx->sort_interval == 0)
+            CK(launch_sort(c, (long long *)beam->id, beam->n, r.bg, box, ctx->n, ctx->keys,
+                           ctx->counts, ctx->offs, ctx->sums, ctx->scr, ctx->id_scr,
+                           ctx->dev_ptrs, s),
+               "sort");
+        if (k == 0 || h.regrid)
+            CK(launch_deposit(c, beam->n, r.bg, box, ctx->n, ctx->acc_hi, ctx->acc_lo, ctx->status,
+                              s),
+               "deposit");
         const double rho_scale = q_macro / (h.box.h[0] * h.box.h[1] * h.box.h[2]);
         CK(solve_acc_to_phi(&ctx->plan, ctx->acc_hi, ctx->acc_lo, rho_scale, ctx->phi, s),
            "solve");
         const double kt = r.sign * ds / (r.mass_eV * (r.bg * r.bg));
         const double kz = -r.sign * ds / (r.mass_eV * r.bg);
-        CK(launch_field(ctx->phi, ctx->n, box, kt, kt, kz, ctx->efield, s), "field");
+        CK(launch_field(ctx->phi, ctx->n, box, kt, kt, kz, ctx->efield, ctx->emax, ctx->efix,
+                        ctx->escale, s),
+           "field");
         const bool last = k + 1 == nkicks;
-        CK(launch_gather_kick_push(c, beam->n, r.bg, box, ctx->n, ctx->efield, ctx->maps + 1 + k,
-                                   last ? nullptr : ctx->st, ctx->status, s),
-           "gather/kick/push");
+        if (!last) {
+            CK(cudaMemsetAsync(ctx->acc_hi, 0, acc_bytes, s), "clear");
+            CK(cudaMemsetAsync(ctx->acc_lo, 0, acc_bytes, s), "clear");
+        }
+        CK(launch_kick_push_deposit(c, beam->n, r.bg, box, ctx->n, ctx->efix, ctx->escale,
+                                    &tab[1 + k], !last, ctx->acc_hi, ctx->acc_lo, ctx->st,
+                                    ctx->status, s),
+           "gather/kick/push/deposit");
         ctx->kick += 1;
     }
     return BX_OK;
@@ -479,9 +543,12 @@ int32_t bx_gather_kick(bx_ctx *ctx, bx_beam *beam, const bx_grid *grid, double d
     CK(cudaMemcpyAsync(ctx->tmp_box, &b, sizeof(b), cudaMemcpyHostToDevice, s), "box");
     const double kt = r.sign * ds / (r.mass_eV * (r.bg * r.bg));
     const double kz = -r.sign * ds / (r.mass_eV * r.bg);
-    CK(launch_field(grid->phi, ctx->n, ctx->tmp_box, kt, kt, kz, ctx->efield, s), "field");
-    CK(launch_gather_kick_push(beam->coord, beam->n, r.bg, ctx->tmp_box, ctx->n, ctx->efield,
-                               nullptr, nullptr, ctx->status, s),
+    CK(launch_field(grid->phi, ctx->n, ctx->tmp_box, kt, kt, kz, ctx->efield, ctx->emax,
+                    ctx->efix, ctx->escale, s),
+       "field");
+    CK(launch_kick_push_deposit(beam->coord, beam->n, r.bg, ctx->tmp_box, ctx->n, ctx->efix,
+                                ctx->escale, nullptr, false, nullptr, nullptr, nullptr,
+                                ctx->status, s),
        "gather/kick");
     return BX_OK;
 }

@@ -27,6 +27,12 @@ struct __align__(32) Field4 {
     double x, y, z, w;
 };
 
+// The same field in int64 fixed point: E_fix = rint(E * 2^e_d) per component
+// (exponents kept separately), so the interpolation runs on the integer pipes.
+struct __align__(32) EFix {
+    long long x, y, z, w;
+};
+
 // Grid box as the kernels read it (device resident for tracking).
 struct Box {
     double lo[3], hi[3], h[3], inv_h[3];
@@ -72,7 +78,7 @@ constexpr int DEP_SPLIT = 31;
 enum KernelId : int {
     K_PUSH, K_MINMAX, K_BOX, K_IGF_CORNER, K_IGF_SUM, K_DEPOSIT, K_ACC_TO_RHO, K_FFT_X,
     K_FFT_YZ, K_FFT_ZSOLVE, K_FFT_XINV, K_GREEN_X, K_GREEN_YZ, K_FIELD, K_GATHER, K_MOMENTS,
-    K_TWIDDLE, K_COUNT
+    K_TWIDDLE, K_EFIX, K_SORT, K_COUNT
 };
 
 struct Profiler;
@@ -113,14 +119,24 @@ cudaError_t launch_deposit(double *const c[6], int64_t n, double betagamma, cons
 cudaError_t launch_acc_to_rho(const unsigned long long *acc_hi, const unsigned long long *acc_lo,
                               int nn, double q_macro, const Box *box, double *rho,
                               cudaStream_t s);
-cudaError_t launch_gather_kick_push(double *const c[6], int64_t n, double betagamma,
-                                    const Box *box, int nn, const double *efield,
-                                    const MapCoef *map, TrackState *st, int32_t *status,
-                                    cudaStream_t s);
+cudaError_t launch_kick_push_deposit(double *const c[6], int64_t n, double betagamma,
+                                     const Box *box, int nn, const EFix *ef, const int *escale,
+                                     const MapCoef *map_host, bool deposit,
+                                     unsigned long long *acc_hi, unsigned long long *acc_lo,
+                                     TrackState *st, int32_t *status, cudaStream_t s);
 cudaError_t launch_box_rule(TrackState *st, int nn, int64_t n, long long *log, int64_t log_cap,
                             cudaStream_t s);
 cudaError_t launch_field(const double *phi, int nn, const Box *box, double kx, double ky,
-                         double kz, double *efield, cudaStream_t s);
+                         double kz, double *efield, unsigned long long *emax, EFix *efix,
+                         int *escale, cudaStream_t s);
+// sort.cu
+int sort_brick_edge(int nn);
+int sort_bricks(int nn);
+int64_t sort_chunks(int64_t n);
+cudaError_t launch_sort(double *const c[6], long long *id, int64_t n, double betagamma,
+                        const Box *box, int nn, int *keys, long long *counts, long long *offs,
+                        long long *sums, double *const scratch[6], long long *id_scratch,
+                        double **dev_ptrs, cudaStream_t s);
 // moments.cu
 cudaError_t launch_moments(double *const c[6], int64_t n, double *partials, int nblocks,
                            double *out, cudaStream_t s);

@@ -1,34 +1,72 @@
 // Particle-side kernels of the tracking step: element push, exact min/max of
-// the rest-frame positions, the grid-box rule, CIC charge deposition in fixed
-// point, the rest-frame field and the fused gather + kick + push.
+// the rest-frame positions, the grid-box rule, the rest-frame field in fixed
+// point, and the fused particle kernel (CIC gather + kick + merged half-slice
+// map + the next kick's CIC deposit + min/max).
 //
 // Paper anchors (arXiv:2208.02382): Model Assumptions (linear symplectic maps
 // in s; electrostatic rest-frame field; map-based split-operator step) and
-// Listing 1 (particle shape, init_grids, elements with nslice).
+// Listing 1 (particle shape 1 = CIC, init_grids, elements with nslice).
+//
+// FP64 is spent only where the phase-space state is updated: u = (X - lo)/h,
+// the linear map, and adding the kick.  Cell indices, CIC fractions and
+// weights, the field interpolation, the charge accumulation and the min/max
+// run in 64-bit fixed point on the integer pipes.
 #include "common.cuh"
+#include "fixed.cuh"
 
 namespace bt {
 
 constexpr int TPB = 256;
 
-__device__ __forceinline__ void apply_map(const MapCoef &m, double &x, double &px, double &y,
-                                          double &py, double &t, double pt) {
-    double nx = m.m00 * x + m.m01 * px + m.m05 * pt;
-    double npx = m.m10 * x + m.m11 * px + m.m15 * pt;
-    double ny = m.m22 * y + m.m23 * py;
-    double npy = m.m32 * y + m.m33 * py;
-    double nt = t + m.m40 * x + m.m41 * px + m.m45 * pt;
-    x = nx;
-    px = npx;
-    y = ny;
-    py = npy;
-    t = nt;
-}
-
 static inline int grid_for(int64_t n) {
     int64_t b = (n + TPB - 1) / TPB;
     if (b > 148 * 16) b = 148 * 16;
     return (int)(b < 1 ? 1 : b);
+}
+
+// Map structure classes (see MapCoef): drift (x += m01 px, y += m23 py,
+// t += m45 pt), no dispersion (2x2 blocks and the t-pt term), general.
+enum MapKind { MAP_NONE = 0, MAP_DRIFT = 1, MAP_QUAD = 2, MAP_GENERAL = 3 };
+
+template <int MK>
+__device__ __forceinline__ void apply_map_k(const MapCoef &m, double &x, double &px, double &y,
+                                            double &py, double &t, double pt) {
+    if constexpr (MK == MAP_DRIFT) {
+        x = fma(m.m01, px, x);
+        y = fma(m.m23, py, y);
+        t = fma(m.m45, pt, t);
+    } else if constexpr (MK == MAP_QUAD) {
+        double nx = m.m00 * x + m.m01 * px;
+        double npx = m.m10 * x + m.m11 * px;
+        double ny = m.m22 * y + m.m23 * py;
+        double npy = m.m32 * y + m.m33 * py;
+        t = fma(m.m45, pt, t);
+        x = nx;
+        px = npx;
+        y = ny;
+        py = npy;
+    } else if constexpr (MK == MAP_GENERAL) {
+        double nx = m.m00 * x + m.m01 * px + m.m05 * pt;
+        double npx = m.m10 * x + m.m11 * px + m.m15 * pt;
+        double ny = m.m22 * y + m.m23 * py;
+        double npy = m.m32 * y + m.m33 * py;
+        double nt = t + m.m40 * x + m.m41 * px + m.m45 * pt;
+        x = nx;
+        px = npx;
+        y = ny;
+        py = npy;
+        t = nt;
+    }
+}
+
+int map_kind(const MapCoef &m) {
+    if (m.m05 == 0.0 && m.m15 == 0.0 && m.m40 == 0.0 && m.m41 == 0.0) {
+        if (m.m00 == 1.0 && m.m10 == 0.0 && m.m11 == 1.0 && m.m22 == 1.0 && m.m32 == 0.0 &&
+            m.m33 == 1.0)
+            return MAP_DRIFT;
+        return MAP_QUAD;
+    }
+    return MAP_GENERAL;
 }
 
 // ---------------------------------------------------------------- push only
@@ -40,7 +78,7 @@ __global__ void k_push_maps(double *__restrict__ x, double *__restrict__ px,
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         double a = x[p], b = px[p], c = y[p], d = py[p], e = t[p], f = pt[p];
-        for (int k = 0; k < nmaps; ++k) apply_map(maps[k], a, b, c, d, e, f);
+        for (int k = 0; k < nmaps; ++k) apply_map_k<MAP_GENERAL>(maps[k], a, b, c, d, e, f);
         x[p] = a;
         px[p] = b;
         y[p] = c;
@@ -52,23 +90,25 @@ __global__ void k_push_maps(double *__restrict__ x, double *__restrict__ px,
 cudaError_t launch_push_maps(double *const c[6], int64_t n, const MapCoef *maps, int nmaps,
                              cudaStream_t s) {
     if (n <= 0 || nmaps <= 0) return cudaSuccess;
-    BT_LAUNCH(K_PUSH, s, k_push_maps<<<grid_for(n), TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5], n, maps, nmaps));
+    BT_LAUNCH(K_PUSH, s, k_push_maps<<<grid_for(n), TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4],
+                                                                 c[5], n, maps, nmaps));
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ min/max
 
-// Block-level min/max of the rest-frame positions, folded into the state with
-// integer atomics on order-preserving keys (exact and order-free).
-__device__ __forceinline__ void block_minmax_commit(double lo[3], double hi[3], TrackState *st) {
-    __shared__ double s_lo[3][TPB / 32], s_hi[3][TPB / 32];
+// Block min/max of order-preserving keys, folded into the state with integer
+// atomics (exact, order-free).  All threads of the block must call it.
+__device__ __forceinline__ void block_keys_commit(long long lo[3], long long hi[3],
+                                                  TrackState *st) {
+    __shared__ long long s_lo[3][TPB / 32], s_hi[3][TPB / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        double a = lo[d], b = hi[d];
+        long long a = lo[d], b = hi[d];
         for (int o = 16; o > 0; o >>= 1) {
-            a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
-            b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+            a = min(a, __shfl_xor_sync(0xffffffffu, a, o));
+            b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
         }
         if (lane == 0) {
             s_lo[d][w] = a;
@@ -79,45 +119,48 @@ __device__ __forceinline__ void block_minmax_commit(double lo[3], double hi[3], 
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            double a = s_lo[d][0], b = s_hi[d][0];
+            long long a = s_lo[d][0], b = s_hi[d][0];
             for (int k = 1; k < TPB / 32; ++k) {
-                a = fmin(a, s_lo[d][k]);
-                b = fmax(b, s_hi[d][k]);
+                a = min(a, s_lo[d][k]);
+                b = max(b, s_hi[d][k]);
             }
-            atomicMin(&st->mm[d], dkey(a));
-            atomicMax(&st->mm[3 + d], dkey(b));
+            atomicMin(&st->mm[d], a);
+            atomicMax(&st->mm[3 + d], b);
         }
     }
+}
+
+__device__ __forceinline__ bool finite6(double a, double b, double c, double d, double e, double f) {
+    return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d) && isfinite(e) && isfinite(f);
 }
 
 __global__ void k_minmax(const double *__restrict__ x, const double *__restrict__ px,
                          const double *__restrict__ y, const double *__restrict__ py,
                          const double *__restrict__ t, const double *__restrict__ pt, int64_t n,
                          double nbg, TrackState *st, int32_t *status) {
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
     bool bad = false;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         double a = x[p], b = y[p], c = t[p];
-        bad |= !(isfinite(a) && isfinite(px[p]) && isfinite(b) && isfinite(py[p]) &&
-                 isfinite(c) && isfinite(pt[p]));
-        double z = nbg * c;
-        lo[0] = fmin(lo[0], a);
-        hi[0] = fmax(hi[0], a);
-        lo[1] = fmin(lo[1], b);
-        hi[1] = fmax(hi[1], b);
-        lo[2] = fmin(lo[2], z);
-        hi[2] = fmax(hi[2], z);
+        bad |= !finite6(a, px[p], b, py[p], c, pt[p]);
+        const long long k0 = dkey(a), k1 = dkey(b), k2 = dkey(__dmul_rn(nbg, c));
+        lo[0] = min(lo[0], k0);
+        hi[0] = max(hi[0], k0);
+        lo[1] = min(lo[1], k1);
+        hi[1] = max(hi[1], k1);
+        lo[2] = min(lo[2], k2);
+        hi[2] = max(hi[2], k2);
     }
     if (bad) atomicOr(status, ST_NONFINITE);
-    block_minmax_commit(lo, hi, st);
+    block_keys_commit(lo, hi, st);
 }
 
 cudaError_t launch_minmax(double *const c[6], int64_t n, double betagamma, TrackState *st,
                           int32_t *status, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    BT_LAUNCH(K_MINMAX, s, k_minmax<<<grid_for(n), TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5], n, -betagamma, st,
-                                         status));
+    BT_LAUNCH(K_MINMAX, s, k_minmax<<<grid_for(n), TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5],
+                                                                n, -betagamma, st, status));
     return cudaGetLastError();
 }
 
@@ -171,8 +214,8 @@ __global__ void k_box_rule(TrackState *st, int nn, long long *log, int64_t cap) 
                           ? 1
                           : 0;
     for (int d = 0; d < 3; ++d) {
-        st->mm[d] = dkey(INFINITY);
-        st->mm[3 + d] = dkey(-INFINITY);
+        st->mm[d] = LLONG_MAX;
+        st->mm[3 + d] = LLONG_MIN;
     }
 }
 
@@ -183,93 +226,7 @@ cudaError_t launch_box_rule(TrackState *st, int nn, int64_t n, long long *log, i
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ deposit
-
-// u (>= 0, < 2^11) to unsigned fixed point with 52 fractional bits, by
-// exponent/mantissa arithmetic: exact for u >= 1, truncated below 1.
-__device__ __forceinline__ unsigned long long to_fixed52(double u) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(u);
-    int e = (int)((b >> 52) & 0x7FF) - 1023;
-    if (e < -60 || u <= 0.0) return 0ull;
-    unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    return e >= 0 ? (mant << e) : (mant >> (-e));
-}
-
-// (a * b) >> 52 for a, b <= 2^52 (the top bits of the 104-bit product).
-__device__ __forceinline__ unsigned long long mulshr52(unsigned long long a,
-                                                      unsigned long long b) {
-    unsigned long long lo = a * b, hi = __umul64hi(a, b);
-    return (hi << 12) | (lo >> 52);
-}
-
-// Charge deposition (Listing 1 particle shape 1 = CIC; ABLASTR deposition):
-// node weights (1-f, f) per dimension, products in unsigned fixed point
-// (52-bit fractions, 51-bit result), accumulated by integer atomics so the
-// result is independent of particle order.
-__global__ void k_deposit(const double *__restrict__ x, const double *__restrict__ y,
-                          const double *__restrict__ t, int64_t n, double nbg, const Box *box,
-                          int nn, unsigned long long *__restrict__ acc_hi,
-                          unsigned long long *__restrict__ acc_lo, int32_t *status) {
-    const double lo0 = box->lo[0], lo1 = box->lo[1], lo2 = box->lo[2];
-    const double ih0 = box->inv_h[0], ih1 = box->inv_h[1], ih2 = box->inv_h[2];
-    const unsigned long long one = 1ull << 52;
-    const unsigned long long umax = (unsigned long long)(nn - 1) << 52;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        double u[3];
-        u[0] = (x[p] - lo0) * ih0;
-        u[1] = (y[p] - lo1) * ih1;
-        u[2] = (__dmul_rn(nbg, t[p]) - lo2) * ih2;  // Z rounded as stored, then offset
-        int cell[3];
-        unsigned long long w[3][2];
-        bool outside = false;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            // a box that contains the particle gives u in [0, n-1] up to rounding
-            outside |= !(u[d] >= 0.0) || u[d] > (double)(nn - 1) + 1e-6;
-            unsigned long long U = to_fixed52(u[d]);
-            if (U > umax) U = umax;
-            unsigned long long i = U >> 52;
-            if (i > (unsigned long long)(nn - 2)) i = nn - 2;
-            unsigned long long f = U - (i << 52);
-            cell[d] = (int)i;
-            w[d][0] = one - f;
-            w[d][1] = f;
-        }
-        if (outside) {
-            atomicOr(status, ST_OUTSIDE);
-            continue;
-        }
-        const long long base = ((long long)cell[2] * nn + cell[1]) * nn + cell[0];
-#pragma unroll
-        for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-            for (int dy = 0; dy < 2; ++dy) {
-                unsigned long long wyz = mulshr52(w[1][dy], w[2][dz]);
-#pragma unroll
-                for (int dx = 0; dx < 2; ++dx) {
-                    unsigned long long v = mulshr52(w[0][dx], wyz) >> 1;  // 51-bit result
-                    long long node = base + ((long long)dz * nn + dy) * nn + dx;
-                    atomicAdd(&acc_hi[node], v >> DEP_SPLIT);
-                    atomicAdd(&acc_lo[node], v & ((1ull << DEP_SPLIT) - 1));
-                }
-            }
-    }
-}
-
-cudaError_t launch_deposit(double *const c[6], int64_t n, double betagamma, const Box *box,
-                              int nn, unsigned long long *acc_hi, unsigned long long *acc_lo,
-                              int32_t *status, cudaStream_t s) {
-    size_t nodes = (size_t)nn * nn * nn;
-    cudaError_t e = cudaMemsetAsync(acc_hi, 0, nodes * 8, s);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(acc_lo, 0, nodes * 8, s);
-    if (e != cudaSuccess) return e;
-    if (n <= 0) return cudaSuccess;
-    BT_LAUNCH(K_DEPOSIT, s, k_deposit<<<grid_for(n), TPB, 0, s>>>(c[0], c[2], c[4], n, -betagamma, box, nn, acc_hi, acc_lo,
-                                          status));
-    return cudaGetLastError();
-}
+// -------------------------------------------------- rho from accumulators
 
 // rho[node] = q * W / (hx hy hz) with W = (hi * 2^31 + lo) * 2^-51 the summed weights.
 __global__ void k_acc_to_rho(const unsigned long long *__restrict__ acc_hi,
@@ -288,8 +245,8 @@ cudaError_t launch_acc_to_rho(const unsigned long long *acc_hi, const unsigned l
                               int nn, double q_macro, const Box *box, double *rho,
                               cudaStream_t s) {
     long long nodes = (long long)nn * nn * nn;
-    BT_LAUNCH(K_ACC_TO_RHO, s, k_acc_to_rho<<<(int)((nodes + TPB - 1) / TPB), TPB, 0, s>>>(acc_hi, acc_lo, nodes, q_macro,
-                                                               box, rho));
+    BT_LAUNCH(K_ACC_TO_RHO, s, k_acc_to_rho<<<(int)((nodes + TPB - 1) / TPB), TPB, 0, s>>>(
+                                   acc_hi, acc_lo, nodes, q_macro, box, rho));
     return cudaGetLastError();
 }
 
@@ -297,15 +254,17 @@ cudaError_t launch_acc_to_rho(const unsigned long long *acc_hi, const unsigned l
 
 // Rest-frame field by centred differences on nodes 0..n-1 from phi on nodes
 // -1..n, pre-multiplied by the kick factor of the slice:
-//   efield[node] = (c_x (phi(i+1) - phi(i-1)), c_y (...), c_z (...), 0)
-// with c_d = -kick_d / (2 h_d), so the gathered value is the momentum change.
+//   E'_d = c_d (phi(+e_d) - phi(-e_d)),  c_d = -kick_d / (2 h_d),
+// so the interpolated value is the momentum change.  Also the max |E'_d|.
 __global__ void k_field(const double *__restrict__ phi, int nn, const Box *box, double kx,
-                        double ky, double kz, Field4 *__restrict__ ef) {
+                        double ky, double kz, Field4 *__restrict__ ef,
+                        unsigned long long *__restrict__ emax) {
     const int q = nn + 2;
     const double cx = -kx / (2.0 * box->h[0]);
     const double cy = -ky / (2.0 * box->h[1]);
     const double cz = -kz / (2.0 * box->h[2]);
     const long long nodes = (long long)nn * nn * nn;
+    double m0 = 0.0, m1 = 0.0, m2 = 0.0;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nodes;
          idx += (long long)gridDim.x * blockDim.x) {
         int i = (int)(idx % nn), j = (int)((idx / nn) % nn), l = (int)(idx / ((long long)nn * nn));
@@ -314,97 +273,347 @@ __global__ void k_field(const double *__restrict__ phi, int nn, const Box *box, 
         double ey = cy * (phi[c + q] - phi[c - q]);
         double ez = cz * (phi[c + (long long)q * q] - phi[c - (long long)q * q]);
         ef[idx] = Field4{ex, ey, ez, 0.0};
+        m0 = fmax(m0, fabs(ex));
+        m1 = fmax(m1, fabs(ey));
+        m2 = fmax(m2, fabs(ez));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m0 = fmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+        m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    }
+    if ((threadIdx.x & 31) == 0) {  // bit patterns of non-negative doubles order like the values
+        atomicMax(&emax[0], (unsigned long long)__double_as_longlong(m0));
+        atomicMax(&emax[1], (unsigned long long)__double_as_longlong(m1));
+        atomicMax(&emax[2], (unsigned long long)__double_as_longlong(m2));
+    }
+}
+
+// Scale exponent e with max * 2^e in [2^60, 2^61), so node values and their
+// differences fit in int64 with room to spare.
+__device__ __forceinline__ int field_exponent(unsigned long long maxbits) {
+    const double m = __longlong_as_double((long long)maxbits);
+    if (!(m > 0.0) || !isfinite(m)) return 0;
+    return 60 - ilogb(m);
+}
+
+// Field in int64 fixed point: E_fix = rint(E' * 2^e_d); exponents in escale.
+__global__ void k_efix(const Field4 *__restrict__ ef, long long nodes,
+                       const unsigned long long *__restrict__ emax, EFix *__restrict__ out,
+                       int *__restrict__ escale) {
+    const int e0 = field_exponent(emax[0]), e1 = field_exponent(emax[1]), e2 = field_exponent(emax[2]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        escale[0] = e0;
+        escale[1] = e1;
+        escale[2] = e2;
+    }
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
+         i += (long long)gridDim.x * blockDim.x) {
+        const Field4 v = ef[i];
+        out[i] = EFix{__double2ll_rn(ldexp(v.x, e0)), __double2ll_rn(ldexp(v.y, e1)),
+                      __double2ll_rn(ldexp(v.z, e2)), 0};
     }
 }
 
 cudaError_t launch_field(const double *phi, int nn, const Box *box, double kx, double ky,
-                         double kz, double *efield, cudaStream_t s) {
+                         double kz, double *efield, unsigned long long *emax, EFix *efix,
+                         int *escale, cudaStream_t s) {
     long long nodes = (long long)nn * nn * nn;
-    BT_LAUNCH(K_FIELD, s, k_field<<<(int)((nodes + TPB - 1) / TPB), TPB, 0, s>>>(phi, nn, box, kx, ky, kz,
-                                                          (Field4 *)efield));
+    cudaError_t e = cudaMemsetAsync(emax, 0, 3 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const int blocks = (int)((nodes + TPB - 1) / TPB);
+    BT_LAUNCH(K_FIELD, s, k_field<<<blocks, TPB, 0, s>>>(phi, nn, box, kx, ky, kz,
+                                                         (Field4 *)efield, emax));
+    BT_LAUNCH(K_EFIX, s, k_efix<<<blocks, TPB, 0, s>>>((const Field4 *)efield, nodes, emax, efix,
+                                                       escale));
     return cudaGetLastError();
 }
 
-// ------------------------------------------------- gather + kick (+ push)
+// -------------------------------------------------- fused particle kernel
 
-// CIC gather of the pre-scaled field at the particle (same weights as the
-// deposit), momentum kick, then (optionally) the merged half-slice map, and
-// (optionally) the min/max of the new rest-frame positions for the next box.
-__global__ void k_gather_kick_push(double *__restrict__ x, double *__restrict__ px,
-                                   double *__restrict__ y, double *__restrict__ py,
-                                   double *__restrict__ t, double *__restrict__ pt, int64_t n,
-                                   double nbg, const Box *box, int nn,
-                                   const Field4 *__restrict__ ef, const MapCoef *map,
-                                   TrackState *st, int32_t *status) {
-    const double lo0 = box->lo[0], lo1 = box->lo[1], lo2 = box->lo[2];
-    const double ih0 = box->inv_h[0], ih1 = box->inv_h[1], ih2 = box->inv_h[2];
-    MapCoef m;
-    if (map) m = *map;
-    double mlo[3] = {INFINITY, INFINITY, INFINITY}, mhi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    bool bad = false;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        double a = x[p], b = px[p], c = y[p], d = py[p], e = t[p], f = pt[p];
-        double u[3] = {(a - lo0) * ih0, (c - lo1) * ih1, (__dmul_rn(nbg, e) - lo2) * ih2};
-        int cell[3];
-        double wt[3][2];
+constexpr int PPT = 8;                 // particles per thread
+constexpr int CHUNK = TPB * PPT;       // particles per block
+constexpr int TILE_CAP = 4096;         // nodes of the shared-memory deposit tile
+
+struct PartArgs {
+    double *x, *px, *y, *py, *t, *pt;
+    int64_t n;
+    double nbg;                        // -beta*gamma
+    const Box *box;
+    int nn;
+    const EFix *ef;                    // field in fixed point (GATHER)
+    const int *escale;
+    MapCoef map;
+    unsigned long long *acc_hi, *acc_lo;   // deposit accumulators (DEP)
+    TrackState *st;                    // min/max (MM)
+    int32_t *status;
+};
+
+// Cell index and 52-bit fraction per dimension from u; u outside
+// [0, n-1] (beyond rounding) sets `outside`.
+__device__ __forceinline__ void cell_frac(double u, int nn, int &cell, unsigned long long &F,
+                                          bool &outside) {
+    const unsigned long long umax = (unsigned long long)(nn - 1) << 52;
+    outside |= !(u >= -1e-9) || u > (double)(nn - 1) + 1e-6;
+    unsigned long long U = to_fixed52(u);
+    if (U > umax) U = umax;
+    unsigned long long i = U >> 52;
+    if (i > (unsigned long long)(nn - 2)) i = nn - 2;
+    F = U - (i << 52);
+    cell = (int)i;
+}
+
+// GATHER: CIC interpolation of the fixed-point field at the current position,
+//         kick, then the map (MK) and the store.
+// DEP:    CIC deposit of the new position (same box) into the accumulators,
+//         through a shared-memory tile covering the block's cells when they fit.
+// MM:     min/max keys of the new rest-frame positions.
+template <int MK, bool GATHER, bool DEP, bool MM>
+__global__ void __launch_bounds__(TPB, 2) k_particles(PartArgs a) {
+    extern __shared__ unsigned long long dsm[];
+    unsigned long long *sF = dsm;                                // [3][CHUNK] fractions
+    int *scell = (int *)(dsm + 3 * CHUNK);                       // [CHUNK] linear cell or -1
+    unsigned long long *tile = dsm + 3 * CHUNK + CHUNK / 2;      // [TILE_CAP]
+    __shared__ int s_bb[6];
+    const int nn = a.nn;
+    const double lo0 = a.box->lo[0], lo1 = a.box->lo[1], lo2 = a.box->lo[2];
+    const double ih0 = a.box->inv_h[0], ih1 = a.box->inv_h[1], ih2 = a.box->inv_h[2];
+    int e0 = 0, e1 = 0, e2 = 0;
+    if constexpr (GATHER) {
+        e0 = a.escale[0];
+        e1 = a.escale[1];
+        e2 = a.escale[2];
+    }
+    if (DEP && threadIdx.x < 6) s_bb[threadIdx.x] = threadIdx.x < 3 ? INT_MAX : INT_MIN;
+    long long klo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, khi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+    int blo[3] = {INT_MAX, INT_MAX, INT_MAX}, bhi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    bool bad = false, outside = false;
+    const int64_t base = (int64_t)blockIdx.x * CHUNK;
+    if (DEP) __syncthreads();
+#pragma unroll 1
+    for (int it = 0; it < PPT; ++it) {
+        const int slot = it * TPB + threadIdx.x;
+        const int64_t p = base + slot;
+        if (DEP) scell[slot] = -1;
+        if (p >= a.n) continue;
+        double x = a.x[p], y = a.y[p], t = a.t[p];
+        if constexpr (GATHER) {
+            double px = a.px[p], py = a.py[p], pt = a.pt[p];
+            int c0, c1, c2;
+            unsigned long long F0, F1, F2;
+            bool out0 = false;
+            cell_frac((x - lo0) * ih0, nn, c0, F0, out0);
+            cell_frac((y - lo1) * ih1, nn, c1, F1, out0);
+            cell_frac((__dmul_rn(a.nbg, t) - lo2) * ih2, nn, c2, F2, out0);
+            outside |= out0;
+            const EFix *e = a.ef + (((long long)c2 * nn + c1) * nn + c0);
+            const long long sy = nn, sz = (long long)nn * nn;
+            // lerp in x on the four (y, z) edges, then y, then z
+            long long gx[2][2], gy[2][2], gz[2][2];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            double fl = fmin(fmax(floor(u[k]), 0.0), (double)(nn - 2));
-            double fr = u[k] - fl;
-            cell[k] = (int)fl;
-            wt[k][0] = 1.0 - fr;
-            wt[k][1] = fr;
+            for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+                for (int dy = 0; dy < 2; ++dy) {
+                    const EFix v0 = e[dz * sz + dy * sy], v1 = e[dz * sz + dy * sy + 1];
+                    gx[dz][dy] = lerp52(v0.x, v1.x, F0);
+                    gy[dz][dy] = lerp52(v0.y, v1.y, F0);
+                    gz[dz][dy] = lerp52(v0.z, v1.z, F0);
+                }
+            const long long ex = lerp52(lerp52(gx[0][0], gx[0][1], F1), lerp52(gx[1][0], gx[1][1], F1), F2);
+            const long long ey = lerp52(lerp52(gy[0][0], gy[0][1], F1), lerp52(gy[1][0], gy[1][1], F1), F2);
+            const long long ez = lerp52(lerp52(gz[0][0], gz[0][1], F1), lerp52(gz[1][0], gz[1][1], F1), F2);
+            px += i64_scaled_to_double(ex, e0);
+            py += i64_scaled_to_double(ey, e1);
+            pt += i64_scaled_to_double(ez, e2);
+            apply_map_k<MK>(a.map, x, px, y, py, t, pt);
+            bad |= !finite6(x, px, y, py, t, pt);
+            a.x[p] = x;
+            a.px[p] = px;
+            a.y[p] = y;
+            a.py[p] = py;
+            a.t[p] = t;
+            a.pt[p] = pt;
         }
-        const long long base = ((long long)cell[2] * nn + cell[1]) * nn + cell[0];
-        double ex = 0.0, ey = 0.0, ez = 0.0;
-#pragma unroll
-        for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-            for (int dy = 0; dy < 2; ++dy) {
-                double wyz = wt[1][dy] * wt[2][dz];
-#pragma unroll
-                for (int dx = 0; dx < 2; ++dx) {
-                    double w = wt[0][dx] * wyz;
-                    Field4 v = ef[base + ((long long)dz * nn + dy) * nn + dx];
-                    ex += w * v.x;
-                    ey += w * v.y;
-                    ez += w * v.z;
+        if constexpr (DEP || MM) {
+            const double z = __dmul_rn(a.nbg, t);
+            if constexpr (MM) {
+                const long long k0 = dkey(x), k1 = dkey(y), k2 = dkey(z);
+                klo[0] = min(klo[0], k0);
+                khi[0] = max(khi[0], k0);
+                klo[1] = min(klo[1], k1);
+                khi[1] = max(khi[1], k1);
+                klo[2] = min(klo[2], k2);
+                khi[2] = max(khi[2], k2);
+            }
+            if constexpr (DEP) {
+                int c0, c1, c2;
+                unsigned long long F0, F1, F2;
+                bool out1 = false;
+                cell_frac((x - lo0) * ih0, nn, c0, F0, out1);
+                cell_frac((y - lo1) * ih1, nn, c1, F1, out1);
+                cell_frac((z - lo2) * ih2, nn, c2, F2, out1);
+                if (out1 && !GATHER) outside = true;  // explicit box not containing the bunch
+                if (!out1) {  // particles outside are left out: the box rule then regrids
+                    sF[slot] = F0;
+                    sF[CHUNK + slot] = F1;
+                    sF[2 * CHUNK + slot] = F2;
+                    scell[slot] = (c2 * nn + c1) * nn + c0;
+                    blo[0] = min(blo[0], c0);
+                    bhi[0] = max(bhi[0], c0);
+                    blo[1] = min(blo[1], c1);
+                    bhi[1] = max(bhi[1], c1);
+                    blo[2] = min(blo[2], c2);
+                    bhi[2] = max(bhi[2], c2);
                 }
             }
-        b += ex;
-        d += ey;
-        f += ez;
-        if (map) apply_map(m, a, b, c, d, e, f);
-        bad |= !(isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d) && isfinite(e) &&
-                 isfinite(f));
-        x[p] = a;
-        px[p] = b;
-        y[p] = c;
-        py[p] = d;
-        t[p] = e;
-        pt[p] = f;
-        double z = nbg * e;
-        mlo[0] = fmin(mlo[0], a);
-        mhi[0] = fmax(mhi[0], a);
-        mlo[1] = fmin(mlo[1], c);
-        mhi[1] = fmax(mhi[1], c);
-        mlo[2] = fmin(mlo[2], z);
-        mhi[2] = fmax(mhi[2], z);
+        }
     }
-    if (bad) atomicOr(status, ST_NONFINITE);
-    if (st) block_minmax_commit(mlo, mhi, st);
+    if (bad) atomicOr(a.status, ST_NONFINITE);
+    if (outside) atomicOr(a.status, ST_OUTSIDE);
+    if constexpr (MM) block_keys_commit(klo, khi, a.st);
+    if constexpr (DEP) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            int l = blo[d], h = bhi[d];
+            for (int o = 16; o > 0; o >>= 1) {
+                l = min(l, __shfl_xor_sync(0xffffffffu, l, o));
+                h = max(h, __shfl_xor_sync(0xffffffffu, h, o));
+            }
+            if ((threadIdx.x & 31) == 0) {
+                atomicMin(&s_bb[d], l);
+                atomicMax(&s_bb[3 + d], h);
+            }
+        }
+        __syncthreads();
+        const int i0 = s_bb[0], j0 = s_bb[1], l0 = s_bb[2];
+        if (i0 == INT_MAX) return;  // nothing to deposit in this block
+        const int tx = s_bb[3] - i0 + 2, ty = s_bb[4] - j0 + 2, tz = s_bb[5] - l0 + 2;
+        const bool use_tile = (long long)tx * ty * tz <= TILE_CAP;
+        const unsigned long long one = 1ull << 52;
+        if (use_tile) {
+            for (int i = threadIdx.x; i < tx * ty * tz; i += TPB) tile[i] = 0ull;
+            __syncthreads();
+        }
+        const int nn2 = nn * nn;
+#pragma unroll 1
+        for (int it = 0; it < PPT; ++it) {
+            const int slot = it * TPB + threadIdx.x;
+            const int cell = scell[slot];
+            if (cell < 0) continue;
+            const unsigned long long F0 = sF[slot], F1 = sF[CHUNK + slot], F2 = sF[2 * CHUNK + slot];
+            const unsigned long long wx[2] = {one - F0, F0}, wy[2] = {one - F1, F1},
+                                     wz[2] = {one - F2, F2};
+            const int c2 = cell / nn2, c1 = (cell / nn) % nn, c0 = cell % nn;
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz)
+#pragma unroll
+                for (int dy = 0; dy < 2; ++dy) {
+                    const unsigned long long wyz = mulshr52(wy[dy], wz[dz]);
+#pragma unroll
+                    for (int dx = 0; dx < 2; ++dx) {
+                        const unsigned long long v = mulshr52(wx[dx], wyz) >> 1;  // 51-bit
+                        if (use_tile) {
+                            const int li = ((c2 + dz - l0) * ty + (c1 + dy - j0)) * tx + (c0 + dx - i0);
+                            atomicAdd(&tile[li], v);
+                        } else {
+                            const long long node = cell + (long long)dz * nn2 + dy * nn + dx;
+                            atomicAdd(&a.acc_hi[node], v >> DEP_SPLIT);
+                            atomicAdd(&a.acc_lo[node], v & ((1ull << DEP_SPLIT) - 1));
+                        }
+                    }
+                }
+        }
+        if (use_tile) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < tx * ty * tz; i += TPB) {
+                const unsigned long long v = tile[i];
+                if (v == 0ull) continue;
+                const int ii = i % tx, jj = (i / tx) % ty, ll = i / (tx * ty);
+                const long long node = ((long long)(l0 + ll) * nn + (j0 + jj)) * nn + (i0 + ii);
+                atomicAdd(&a.acc_hi[node], v >> DEP_SPLIT);
+                atomicAdd(&a.acc_lo[node], v & ((1ull << DEP_SPLIT) - 1));
+            }
+        }
+    }
 }
 
-cudaError_t launch_gather_kick_push(double *const c[6], int64_t n, double betagamma,
-                                    const Box *box, int nn, const double *efield,
-                                    const MapCoef *map, TrackState *st, int32_t *status,
-                                    cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    BT_LAUNCH(K_GATHER, s, k_gather_kick_push<<<grid_for(n), TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5], n,
-                                                   -betagamma, box, nn,
-                                                   (const Field4 *)efield, map, st, status));
+static size_t particles_smem(bool dep) {
+    return dep ? (size_t)(3 * CHUNK + CHUNK / 2 + TILE_CAP) * sizeof(unsigned long long) : 0;
+}
+
+template <int MK, bool G, bool D, bool M>
+static cudaError_t launch_pk(const PartArgs &a, cudaStream_t s, int kid) {
+    const size_t sm = particles_smem(D);
+    if (D) cudaFuncSetAttribute(k_particles<MK, G, D, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)sm);
+    const unsigned blocks = (unsigned)((a.n + CHUNK - 1) / CHUNK);
+    BT_LAUNCH(kid, s, k_particles<MK, G, D, M><<<blocks, TPB, sm, s>>>(a));
     return cudaGetLastError();
+}
+
+static PartArgs part_args(double *const c[6], int64_t n, double betagamma, const Box *box, int nn) {
+    PartArgs a{};
+    a.x = c[0];
+    a.px = c[1];
+    a.y = c[2];
+    a.py = c[3];
+    a.t = c[4];
+    a.pt = c[5];
+    a.n = n;
+    a.nbg = -betagamma;
+    a.box = box;
+    a.nn = nn;
+    return a;
+}
+
+cudaError_t launch_kick_push_deposit(double *const c[6], int64_t n, double betagamma,
+                                     const Box *box, int nn, const EFix *ef, const int *escale,
+                                     const MapCoef *map_host, bool deposit,
+                                     unsigned long long *acc_hi, unsigned long long *acc_lo,
+                                     TrackState *st, int32_t *status, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    PartArgs a = part_args(c, n, betagamma, box, nn);
+    a.ef = ef;
+    a.escale = escale;
+    a.acc_hi = acc_hi;
+    a.acc_lo = acc_lo;
+    a.st = st;
+    a.status = status;
+    const int mk = map_host ? map_kind(*map_host) : MAP_NONE;
+    if (map_host) a.map = *map_host;
+    if (!deposit) {
+        switch (mk) {
+            case MAP_NONE: return launch_pk<MAP_NONE, true, false, false>(a, s, K_GATHER);
+            case MAP_DRIFT: return launch_pk<MAP_DRIFT, true, false, false>(a, s, K_GATHER);
+            case MAP_QUAD: return launch_pk<MAP_QUAD, true, false, false>(a, s, K_GATHER);
+            default: return launch_pk<MAP_GENERAL, true, false, false>(a, s, K_GATHER);
+        }
+    }
+    switch (mk) {
+        case MAP_DRIFT: return launch_pk<MAP_DRIFT, true, true, true>(a, s, K_GATHER);
+        case MAP_QUAD: return launch_pk<MAP_QUAD, true, true, true>(a, s, K_GATHER);
+        default: return launch_pk<MAP_GENERAL, true, true, true>(a, s, K_GATHER);
+    }
+}
+
+// Charge deposition alone (Listing 1 particle shape 1 = CIC): node weights
+// (1-f, f) per dimension as unsigned fixed-point products (52-bit fractions,
+// 51-bit result), summed with integer atomics, so the result does not depend
+// on particle order.  Particles outside the box are left out and flagged.
+cudaError_t launch_deposit(double *const c[6], int64_t n, double betagamma, const Box *box,
+                           int nn, unsigned long long *acc_hi, unsigned long long *acc_lo,
+                           int32_t *status, cudaStream_t s) {
+    size_t nodes = (size_t)nn * nn * nn;
+    cudaError_t e = cudaMemsetAsync(acc_hi, 0, nodes * 8, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(acc_lo, 0, nodes * 8, s);
+    if (e != cudaSuccess) return e;
+    if (n <= 0) return cudaSuccess;
+    PartArgs a = part_args(c, n, betagamma, box, nn);
+    a.acc_hi = acc_hi;
+    a.acc_lo = acc_lo;
+    a.status = status;
+    return launch_pk<MAP_NONE, false, true, false>(a, s, K_DEPOSIT);
 }
 
 }  // namespace bt

@@ -1,0 +1,201 @@
+// Binning of particles by grid brick: a stable counting sort that keeps the
+// particles of each brick contiguous, so the fused particle kernel's blocks
+// each touch a compact set of cells and accumulate their charge in a
+// shared-memory tile.  Stable and deterministic: the order after sorting is a
+// fixed function of the order before (ties keep their relative order).
+//
+//   keys:    brick of each particle's cell (bricks of be^3 cells, be = 8, or
+//            n/16 above n = 128, so there are at most 16^3 bricks), plus a
+//            per-chunk brick histogram (chunks of SORT_CHUNK particles)
+//   scan:    exclusive prefix over the histograms in brick-major, chunk-minor
+//            order -> the destination of each (brick, chunk) run
+//   scatter: within a chunk, each particle's rank among the earlier particles
+//            of its brick (warp match_any, warps taking turns in order);
+//            writes the six coordinates and the id to scratch arrays, which
+//            are then copied back over the caller's arrays.
+#include "common.cuh"
+#include "fixed.cuh"
+
+namespace bt {
+
+constexpr int SORT_TPB = 256;
+constexpr int SORT_ROUNDS = 64;
+constexpr int SORT_CHUNK = SORT_TPB * SORT_ROUNDS;   // 16384 particles per block
+constexpr int SCAN_TILE = 2048;                      // elements per scan block
+
+int sort_brick_edge(int nn) { return nn <= 128 ? 8 : nn / 16; }
+int sort_bricks(int nn) {
+    int nb = nn / sort_brick_edge(nn);
+    return nb * nb * nb;
+}
+int64_t sort_chunks(int64_t n) { return (n + SORT_CHUNK - 1) / SORT_CHUNK; }
+
+__device__ __forceinline__ int brick_of(double x, double y, double t, double nbg, const Box &b,
+                                        int nn, int be) {
+    const double u[3] = {(x - b.lo[0]) * b.inv_h[0], (y - b.lo[1]) * b.inv_h[1],
+                         (__dmul_rn(nbg, t) - b.lo[2]) * b.inv_h[2]};
+    const int nb = nn / be;
+    int k[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        long long c = (long long)(to_fixed52(u[d]) >> 52);  // outside: clamped
+        if (c > nn - 2) c = nn - 2;
+        k[d] = (int)(c / be);
+    }
+    return (k[2] * nb + k[1]) * nb + k[0];
+}
+
+__global__ void k_sort_keys(const double *__restrict__ x, const double *__restrict__ y,
+                            const double *__restrict__ t, int64_t n, double nbg,
+                            const Box *__restrict__ box, int nn, int be, int nbricks,
+                            int64_t nchunks, int *__restrict__ keys,
+                            long long *__restrict__ counts) {
+    extern __shared__ int hist[];
+    for (int i = threadIdx.x; i < nbricks; i += SORT_TPB) hist[i] = 0;
+    __syncthreads();
+    const Box b = *box;
+    const int64_t base = (int64_t)blockIdx.x * SORT_CHUNK;
+    for (int r = 0; r < SORT_ROUNDS; ++r) {
+        const int64_t p = base + r * SORT_TPB + threadIdx.x;
+        if (p >= n) break;
+        const int k = brick_of(x[p], y[p], t[p], nbg, b, nn, be);
+        keys[p] = k;
+        atomicAdd(&hist[k], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nbricks; i += SORT_TPB)
+        counts[(long long)i * nchunks + blockIdx.x] = hist[i];
+}
+
+// Exclusive scan, three kernels: per-tile sums, scan of the sums, tiles.
+__global__ void k_scan_tiles(const long long *__restrict__ in, long long len,
+                             long long *__restrict__ sums) {
+    __shared__ long long sm[SORT_TPB];
+    const long long b0 = (long long)blockIdx.x * SCAN_TILE;
+    long long s = 0;
+    for (int i = threadIdx.x; i < SCAN_TILE; i += SORT_TPB)
+        if (b0 + i < len) s += in[b0 + i];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = SORT_TPB / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[blockIdx.x] = sm[0];
+}
+
+__global__ void k_scan_sums(long long *sums, long long nt) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        long long run = 0;
+        for (long long i = 0; i < nt; ++i) {
+            long long v = sums[i];
+            sums[i] = run;
+            run += v;
+        }
+    }
+}
+
+__global__ void k_scan_apply(const long long *__restrict__ in, long long len,
+                             const long long *__restrict__ sums, long long *__restrict__ out) {
+    __shared__ long long sm[SORT_TPB];
+    constexpr int PER = SCAN_TILE / SORT_TPB;
+    const long long b0 = (long long)blockIdx.x * SCAN_TILE + threadIdx.x * PER;
+    long long v[PER], s = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        v[k] = (b0 + k < len) ? in[b0 + k] : 0;
+        s += v[k];
+    }
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < SORT_TPB; o <<= 1) {  // inclusive Hillis-Steele
+        long long add = threadIdx.x >= o ? sm[threadIdx.x - o] : 0;
+        __syncthreads();
+        sm[threadIdx.x] += add;
+        __syncthreads();
+    }
+    long long run = sums[blockIdx.x] + sm[threadIdx.x] - s;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        if (b0 + k < len) out[b0 + k] = run;
+        run += v[k];
+    }
+}
+
+__global__ void k_sort_scatter(const int *__restrict__ keys, const long long *__restrict__ offs,
+                               int64_t n, int nbricks, int64_t nchunks,
+                               const double *const *__restrict__ src,
+                               const long long *__restrict__ id_src,
+                               double *const *__restrict__ dst, long long *__restrict__ id_dst) {
+    extern __shared__ int running[];
+    for (int i = threadIdx.x; i < nbricks; i += SORT_TPB) running[i] = 0;
+    __shared__ int s_base[SORT_TPB];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t base = (int64_t)blockIdx.x * SORT_CHUNK;
+    for (int r = 0; r < SORT_ROUNDS; ++r) {
+        const int64_t p = base + r * SORT_TPB + threadIdx.x;
+        const bool valid = p < n;
+        const int key = valid ? keys[p] : -1 - lane;  // invalid lanes never match valid ones
+        const unsigned same = __match_any_sync(0xffffffffu, key);
+        const int rank = __popc(same & lt), cnt = __popc(same);
+        const int leader = __ffs(same) - 1;
+        for (int w = 0; w < SORT_TPB / 32; ++w) {  // warps take turns, in order
+            if (warp == w && valid && lane == leader) {
+                s_base[threadIdx.x] = running[key];
+                running[key] += cnt;
+            }
+            __syncthreads();
+        }
+        const int gbase = s_base[(threadIdx.x & ~31) + leader];
+        if (valid) {
+            const long long d = offs[(long long)key * nchunks + blockIdx.x] + gbase + rank;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) dst[c][d] = src[c][p];
+            id_dst[d] = id_src[p];
+        }
+        __syncthreads();
+    }
+}
+
+struct SortScratch;  // owned by the context (api.cu)
+
+cudaError_t launch_sort(double *const c[6], long long *id, int64_t n, double betagamma,
+                        const Box *box, int nn, int *keys, long long *counts, long long *offs,
+                        long long *sums, double *const scratch[6], long long *id_scratch,
+                        double **dev_ptrs, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int be = sort_brick_edge(nn), nb = sort_bricks(nn);
+    const int64_t nch = sort_chunks(n);
+    const size_t hsm = (size_t)nb * sizeof(int);
+    cudaFuncSetAttribute(k_sort_keys, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+    cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+    BT_LAUNCH(K_SORT, s, k_sort_keys<<<(unsigned)nch, SORT_TPB, hsm, s>>>(
+                             c[0], c[2], c[4], n, -betagamma, box, nn, be, nb, nch, keys, counts));
+    const long long len = (long long)nb * nch;
+    const long long nt = (len + SCAN_TILE - 1) / SCAN_TILE;
+    BT_LAUNCH(K_SORT, s, k_scan_tiles<<<(unsigned)nt, SORT_TPB, 0, s>>>(counts, len, sums));
+    BT_LAUNCH(K_SORT, s, k_scan_sums<<<1, 32, 0, s>>>(sums, nt));
+    BT_LAUNCH(K_SORT, s, k_scan_apply<<<(unsigned)nt, SORT_TPB, 0, s>>>(counts, len, sums, offs));
+    // device arrays of the 6+6 coordinate pointers
+    double *h[12];
+    for (int k = 0; k < 6; ++k) {
+        h[k] = c[k];
+        h[6 + k] = scratch[k];
+    }
+    cudaError_t e = cudaMemcpyAsync(dev_ptrs, h, sizeof(h), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    BT_LAUNCH(K_SORT, s, k_sort_scatter<<<(unsigned)nch, SORT_TPB, hsm, s>>>(
+                             keys, offs, n, nb, nch, (const double *const *)dev_ptrs, id,
+                             (double *const *)(dev_ptrs + 6), id_scratch));
+    for (int k = 0; k < 6; ++k) {
+        e = cudaMemcpyAsync(c[k], scratch[k], n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaMemcpyAsync(id, id_scratch, n * sizeof(long long), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+}  // namespace bt

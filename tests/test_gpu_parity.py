@@ -34,8 +34,11 @@ def gpu_beam(bt, coords, species, charge):
 
 
 def to_np(beam):
+    """Coordinates in id order (the tracking may re-bin particles)."""
     torch.cuda.synchronize()
-    return beam.coords.cpu().numpy()
+    ids = beam.ids.cpu().numpy()
+    assert np.array_equal(np.sort(ids), np.arange(len(ids)))
+    return beam.coords.cpu().numpy()[:, np.argsort(ids)]
 
 
 # ------------------------------------------------------------- Green's function
@@ -220,8 +223,11 @@ def test_track_is_bitwise_reproducible(bt):
         beam = gpu_beam(bt, c, w.species, w.bunch_charge_C)
         trk = bt.Tracker(w.n_grid)
         trk.track(beam, w.lattice, 0, 40)
-        outs.append(to_np(beam))
-    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+        torch.cuda.synchronize()
+        outs.append((beam.coords.cpu().numpy(), beam.ids.cpu().numpy()))
+    for k in (1, 2):  # same particle order and bitwise the same coordinates
+        assert np.array_equal(outs[0][1], outs[k][1])
+        assert np.array_equal(outs[0][0], outs[k][0])
 
 
 def test_track_reports_nonfinite(bt):
