@@ -438,8 +438,8 @@ int32_t bx_track(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t firs
                            ctx->dev_ptrs, s),
                "sort");
         if (k == 0 || h.regrid)
-            CK(launch_deposit(c, beam->n, r.bg, box, ctx->n, ctx->acc_hi, ctx->acc_lo, ctx->status,
-                              s),
+            CK(launch_deposit(c, beam->n, r.bg, box, h.box, ctx->n, ctx->acc_hi, ctx->acc_lo,
+                              ctx->status, s),
                "deposit");
         const double rho_scale = q_macro / (h.box.h[0] * h.box.h[1] * h.box.h[2]);
         CK(solve_acc_to_phi(&ctx->plan, ctx->acc_hi, ctx->acc_lo, rho_scale, ctx->phi, s),
@@ -454,7 +454,7 @@ int32_t bx_track(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t firs
             CK(cudaMemsetAsync(ctx->acc_hi, 0, acc_bytes, s), "clear");
             CK(cudaMemsetAsync(ctx->acc_lo, 0, acc_bytes, s), "clear");
         }
-        CK(launch_kick_push_deposit(c, beam->n, r.bg, box, ctx->n, ctx->efix, ctx->escale,
+        CK(launch_kick_push_deposit(c, beam->n, r.bg, box, h.box, ctx->n, ctx->efix, ctx->escale,
                                     &tab[1 + k], !last, ctx->acc_hi, ctx->acc_lo, ctx->st,
                                     ctx->status, s),
            "gather/kick/push/deposit");
@@ -473,12 +473,14 @@ int32_t bx_deposit(bx_ctx *ctx, const bx_beam *beam, bx_grid *grid, void *stream
     const Ref r = make_ref(beam);
     double *const *c = beam->coord;
     const Box *box;
+    Box hb;
     if (grid->use_box) {
         for (int d = 0; d < 3; ++d)
             if (!(grid->hi[d] > grid->lo[d]) || !std::isfinite(grid->lo[d]) ||
                 !std::isfinite(grid->hi[d]))
                 return fail(ctx, BX_BAD_ARG, "grid box needs finite lo < hi");
         Box b = explicit_box(grid->lo, grid->hi, ctx->n);
+        hb = b;
         CK(cudaMemcpyAsync(ctx->tmp_box, &b, sizeof(b), cudaMemcpyHostToDevice, s), "box");
         for (int d = 0; d < 3; ++d) grid->h[d] = b.h[d];
         box = ctx->tmp_box;
@@ -498,10 +500,11 @@ int32_t bx_deposit(bx_ctx *ctx, const bx_beam *beam, bx_grid *grid, void *stream
             grid->h[d] = h.box.h[d];
         }
         box = &ctx->st->box;
+        hb = h.box;
     }
     const double q_macro =
         beam->n > 0 ? r.sign * std::fabs(beam->bunch_charge_C) / (double)beam->n : 0.0;
-    CK(launch_deposit(c, beam->n, r.bg, box, ctx->n, ctx->acc_hi, ctx->acc_lo, ctx->status, s),
+    CK(launch_deposit(c, beam->n, r.bg, box, hb, ctx->n, ctx->acc_hi, ctx->acc_lo, ctx->status, s),
        "deposit");
     CK(launch_acc_to_rho(ctx->acc_hi, ctx->acc_lo, ctx->n, q_macro, box, grid->rho, s), "rho");
     return BX_OK;
@@ -546,7 +549,7 @@ int32_t bx_gather_kick(bx_ctx *ctx, bx_beam *beam, const bx_grid *grid, double d
     CK(launch_field(grid->phi, ctx->n, ctx->tmp_box, kt, kt, kz, ctx->efield, ctx->emax,
                     ctx->efix, ctx->escale, s),
        "field");
-    CK(launch_kick_push_deposit(beam->coord, beam->n, r.bg, ctx->tmp_box, ctx->n, ctx->efix,
+    CK(launch_kick_push_deposit(beam->coord, beam->n, r.bg, ctx->tmp_box, b, ctx->n, ctx->efix,
                                 ctx->escale, nullptr, false, nullptr, nullptr, nullptr,
                                 ctx->status, s),
        "gather/kick");

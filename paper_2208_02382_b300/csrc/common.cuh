@@ -114,13 +114,14 @@ cudaError_t launch_push_maps(double *const c[6], int64_t n, const MapCoef *maps,
 cudaError_t launch_minmax(double *const c[6], int64_t n, double betagamma, TrackState *st,
                           int32_t *status, cudaStream_t s);
 cudaError_t launch_deposit(double *const c[6], int64_t n, double betagamma, const Box *box,
-                           int nn, unsigned long long *acc_hi, unsigned long long *acc_lo,
-                           int32_t *status, cudaStream_t s);
+                           const Box &box_host, int nn, unsigned long long *acc_hi,
+                           unsigned long long *acc_lo, int32_t *status, cudaStream_t s);
 cudaError_t launch_acc_to_rho(const unsigned long long *acc_hi, const unsigned long long *acc_lo,
                               int nn, double q_macro, const Box *box, double *rho,
                               cudaStream_t s);
 cudaError_t launch_kick_push_deposit(double *const c[6], int64_t n, double betagamma,
-                                     const Box *box, int nn, const EFix *ef, const int *escale,
+                                     const Box *box, const Box &box_host, int nn, const EFix *ef,
+                                     const int *escale,
                                      const MapCoef *map_host, bool deposit,
                                      unsigned long long *acc_hi, unsigned long long *acc_lo,
                                      TrackState *st, int32_t *status, cudaStream_t s);

@@ -6,14 +6,29 @@
 
 namespace bt {
 
-// u (>= 0, < 2^11) to unsigned fixed point with 52 fractional bits, by
-// exponent/mantissa arithmetic: exact for u >= 1, truncated below 1.
+// u to unsigned fixed point with 52 fractional bits by exponent/mantissa
+// arithmetic (integer operations only; on this GPU even an FP64 comparison
+// takes an FP64-pipe slot): exact for 1 <= u < 2^11, truncated below 1;
+// negative u gives 0, u >= 2^11 (and Inf/NaN) saturates to 2^63 - 1.
 __device__ __forceinline__ unsigned long long to_fixed52(double u) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(u);
-    int e = (int)((b >> 52) & 0x7FF) - 1023;
-    if (e < -60 || !(u > 0.0)) return 0ull;
-    unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(u);
+    if (b >> 63) return 0ull;
+    const int e = (int)(b >> 52) - 1023;
+    if (e < -60) return 0ull;
+    if (e > 10) return 0x7FFFFFFFFFFFFFFFull;
+    const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
     return e >= 0 ? (mant << e) : (mant >> (-e));
+}
+
+// Bits of |u| (orders like the magnitude for non-NaN values).
+__device__ __forceinline__ unsigned long long abs_bits(double u) {
+    return (unsigned long long)__double_as_longlong(u) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// Inf or NaN, tested on the exponent bits.
+__device__ __forceinline__ bool nonfinite_bits(double v) {
+    return ((unsigned long long)__double_as_longlong(v) & 0x7FF0000000000000ull) ==
+           0x7FF0000000000000ull;
 }
 
 // (a * b) >> 52 for a, b <= 2^52 (the top bits of the 104-bit product).

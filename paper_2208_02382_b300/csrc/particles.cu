@@ -131,7 +131,8 @@ __device__ __forceinline__ void block_keys_commit(long long lo[3], long long hi[
 }
 
 __device__ __forceinline__ bool finite6(double a, double b, double c, double d, double e, double f) {
-    return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d) && isfinite(e) && isfinite(f);
+    return !(nonfinite_bits(a) | nonfinite_bits(b) | nonfinite_bits(c) | nonfinite_bits(d) |
+             nonfinite_bits(e) | nonfinite_bits(f));
 }
 
 __global__ void k_minmax(const double *__restrict__ x, const double *__restrict__ px,
@@ -347,15 +348,30 @@ struct PartArgs {
     unsigned long long *acc_hi, *acc_lo;   // deposit accumulators (DEP)
     TrackState *st;                    // min/max (MM)
     int32_t *status;
+    int exact_u;                       // u = (X - lo) * (1/h) instead of one FMA
 };
 
-// Cell index and 52-bit fraction per dimension from u; u outside
-// [0, n-1] (beyond rounding) sets `outside`.
+// u = (X - lo)/h.  For a box whose offset is small against its cell size
+// (|lo/h| <= 4096, every ordinary box) one FMA, X*(1/h) - lo/h, is within
+// 1e-12 of a cell; a box far from the origin relative to its size (e.g. the
+// floored box of a single particle) takes the subtraction first.
+bool box_needs_exact_u(const Box &b) {
+    for (int d = 0; d < 3; ++d)
+        if (fabs(b.lo[d] * b.inv_h[d]) > 4096.0 || fabs(b.hi[d] * b.inv_h[d]) > 4096.0)
+            return true;
+    return false;
+}
+
+// Cell index and 52-bit fraction per dimension from u, with integer
+// operations only.  u below -1e-9 or above n-1+1e-6 (beyond the rounding of
+// u for a particle inside [lo, hi)) sets `outside`.
+constexpr unsigned long long NEG_TOL_BITS = 0x3E112E0BE826D695ull;  // bits of 1e-9
 __device__ __forceinline__ void cell_frac(double u, int nn, int &cell, unsigned long long &F,
                                           bool &outside) {
     const unsigned long long umax = (unsigned long long)(nn - 1) << 52;
-    outside |= !(u >= -1e-9) || u > (double)(nn - 1) + 1e-6;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(u);
     unsigned long long U = to_fixed52(u);
+    outside |= ((b >> 63) && abs_bits(u) > NEG_TOL_BITS) || U > umax + 4503599627ull;
     if (U > umax) U = umax;
     unsigned long long i = U >> 52;
     if (i > (unsigned long long)(nn - 2)) i = nn - 2;
@@ -376,8 +392,11 @@ __global__ void __launch_bounds__(TPB, 2) k_particles(PartArgs a) {
     unsigned long long *tile = dsm + 3 * CHUNK + CHUNK / 2;      // [TILE_CAP]
     __shared__ int s_bb[6];
     const int nn = a.nn;
-    const double lo0 = a.box->lo[0], lo1 = a.box->lo[1], lo2 = a.box->lo[2];
+    // u = (X - lo)/h as one FMA per dimension: X * (1/h) - lo/h
     const double ih0 = a.box->inv_h[0], ih1 = a.box->inv_h[1], ih2 = a.box->inv_h[2];
+    const double o0 = -a.box->lo[0] * ih0, o1 = -a.box->lo[1] * ih1, o2 = -a.box->lo[2] * ih2;
+    const double tz = a.nbg * ih2;
+    const double lo0 = a.box->lo[0], lo1 = a.box->lo[1], lo2 = a.box->lo[2];
     int e0 = 0, e1 = 0, e2 = 0;
     if constexpr (GATHER) {
         e0 = a.escale[0];
@@ -402,9 +421,15 @@ __global__ void __launch_bounds__(TPB, 2) k_particles(PartArgs a) {
             int c0, c1, c2;
             unsigned long long F0, F1, F2;
             bool out0 = false;
-            cell_frac((x - lo0) * ih0, nn, c0, F0, out0);
-            cell_frac((y - lo1) * ih1, nn, c1, F1, out0);
-            cell_frac((__dmul_rn(a.nbg, t) - lo2) * ih2, nn, c2, F2, out0);
+            if (a.exact_u) {
+                cell_frac((x - lo0) * ih0, nn, c0, F0, out0);
+                cell_frac((y - lo1) * ih1, nn, c1, F1, out0);
+                cell_frac((__dmul_rn(a.nbg, t) - lo2) * ih2, nn, c2, F2, out0);
+            } else {
+                cell_frac(fma(x, ih0, o0), nn, c0, F0, out0);
+                cell_frac(fma(y, ih1, o1), nn, c1, F1, out0);
+                cell_frac(fma(t, tz, o2), nn, c2, F2, out0);
+            }
             outside |= out0;
             const EFix *e = a.ef + (((long long)c2 * nn + c1) * nn + c0);
             const long long sy = nn, sz = (long long)nn * nn;
@@ -435,9 +460,8 @@ __global__ void __launch_bounds__(TPB, 2) k_particles(PartArgs a) {
             a.pt[p] = pt;
         }
         if constexpr (DEP || MM) {
-            const double z = __dmul_rn(a.nbg, t);
             if constexpr (MM) {
-                const long long k0 = dkey(x), k1 = dkey(y), k2 = dkey(z);
+                const long long k0 = dkey(x), k1 = dkey(y), k2 = dkey(__dmul_rn(a.nbg, t));
                 klo[0] = min(klo[0], k0);
                 khi[0] = max(khi[0], k0);
                 klo[1] = min(klo[1], k1);
@@ -449,9 +473,15 @@ __global__ void __launch_bounds__(TPB, 2) k_particles(PartArgs a) {
                 int c0, c1, c2;
                 unsigned long long F0, F1, F2;
                 bool out1 = false;
-                cell_frac((x - lo0) * ih0, nn, c0, F0, out1);
-                cell_frac((y - lo1) * ih1, nn, c1, F1, out1);
-                cell_frac((z - lo2) * ih2, nn, c2, F2, out1);
+                if (a.exact_u) {
+                    cell_frac((x - lo0) * ih0, nn, c0, F0, out1);
+                    cell_frac((y - lo1) * ih1, nn, c1, F1, out1);
+                    cell_frac((__dmul_rn(a.nbg, t) - lo2) * ih2, nn, c2, F2, out1);
+                } else {
+                    cell_frac(fma(x, ih0, o0), nn, c0, F0, out1);
+                    cell_frac(fma(y, ih1, o1), nn, c1, F1, out1);
+                    cell_frac(fma(t, tz, o2), nn, c2, F2, out1);
+                }
                 if (out1 && !GATHER) outside = true;  // explicit box not containing the bunch
                 if (!out1) {  // particles outside are left out: the box rule then regrids
                     sF[slot] = F0;
@@ -567,12 +597,13 @@ static PartArgs part_args(double *const c[6], int64_t n, double betagamma, const
 }
 
 cudaError_t launch_kick_push_deposit(double *const c[6], int64_t n, double betagamma,
-                                     const Box *box, int nn, const EFix *ef, const int *escale,
-                                     const MapCoef *map_host, bool deposit,
+                                     const Box *box, const Box &box_host, int nn, const EFix *ef,
+                                     const int *escale, const MapCoef *map_host, bool deposit,
                                      unsigned long long *acc_hi, unsigned long long *acc_lo,
                                      TrackState *st, int32_t *status, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     PartArgs a = part_args(c, n, betagamma, box, nn);
+    a.exact_u = box_needs_exact_u(box_host) ? 1 : 0;
     a.ef = ef;
     a.escale = escale;
     a.acc_hi = acc_hi;
@@ -601,8 +632,8 @@ cudaError_t launch_kick_push_deposit(double *const c[6], int64_t n, double betag
 // 51-bit result), summed with integer atomics, so the result does not depend
 // on particle order.  Particles outside the box are left out and flagged.
 cudaError_t launch_deposit(double *const c[6], int64_t n, double betagamma, const Box *box,
-                           int nn, unsigned long long *acc_hi, unsigned long long *acc_lo,
-                           int32_t *status, cudaStream_t s) {
+                           const Box &box_host, int nn, unsigned long long *acc_hi,
+                           unsigned long long *acc_lo, int32_t *status, cudaStream_t s) {
     size_t nodes = (size_t)nn * nn * nn;
     cudaError_t e = cudaMemsetAsync(acc_hi, 0, nodes * 8, s);
     if (e != cudaSuccess) return e;
@@ -613,6 +644,7 @@ cudaError_t launch_deposit(double *const c[6], int64_t n, double betagamma, cons
     a.acc_hi = acc_hi;
     a.acc_lo = acc_lo;
     a.status = status;
+    a.exact_u = box_needs_exact_u(box_host) ? 1 : 0;
     return launch_pk<MAP_NONE, false, true, false>(a, s, K_DEPOSIT);
 }
 
