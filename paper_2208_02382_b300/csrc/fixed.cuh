@@ -31,43 +31,47 @@ __device__ __forceinline__ bool nonfinite_bits(double v) {
            0x7FF0000000000000ull;
 }
 
-// (a * b) >> 52 for a, b <= 2^52 (the top bits of the 104-bit product).
-__device__ __forceinline__ unsigned long long mulshr52(unsigned long long a, unsigned long long b) {
-    unsigned long long lo = a * b, hi = __umul64hi(a, b);
-    return (hi << 12) | (lo >> 52);
+// A 52-bit fraction split into two 26-bit limbs, so that products run on
+// 32x32->64-bit multiplies: F = hi * 2^26 + lo.
+struct Frac {
+    unsigned hi, lo;
+};
+__device__ __forceinline__ Frac split26(unsigned long long F) {
+    return Frac{(unsigned)(F >> 26), (unsigned)(F & 0x3FFFFFFull)};
 }
 
-// a + (b - a) * F / 2^52 for |a|, |b| < 2^61 and 0 <= F <= 2^52 (truncated
-// to 4 units of the last place).
-__device__ __forceinline__ long long lerp52(long long a, long long b, unsigned long long F) {
-    return a + (__mul64hi(b - a, (long long)(F << 10)) << 2);
+// (a * b) >> 52 for fractions a, b <= 2^52, from three 26x26-bit partial
+// products (the dropped low product and the truncated middle term leave an
+// error below 2 units of 2^-52).
+__device__ __forceinline__ unsigned long long mulshr52(Frac a, Frac b) {
+    const unsigned long long hh = (unsigned long long)a.hi * b.hi;
+    const unsigned long long mid = (unsigned long long)a.hi * b.lo + (unsigned long long)a.lo * b.hi;
+    return hh + (mid >> 26);
 }
 
-// v * 2^-e rounded to nearest-even double, with integer operations only.
-// Results below the normal range flush to zero.
+// a + (b - a) * F / 2^52 for |a|, |b| < 2^50 (so |b - a| < 2^51) and a
+// fraction F <= 2^52: d = b - a split as dh * 2^26 + dl (dh signed, dl in
+// [0, 2^26)), d * F / 2^52 = dh*Fh + (dh*Fl + dl*Fh) / 2^26 (+ dl*Fl/2^52,
+// below one unit, dropped).  Error below 2 units of the last place.
+__device__ __forceinline__ long long lerp52(long long a, long long b, Frac F) {
+    const long long d = b - a;
+    const int dh = (int)(d >> 26);
+    const unsigned dl = (unsigned)(d & 0x3FFFFFFll);
+    const long long hh = (long long)dh * (long long)F.hi;
+    const long long mid = (long long)dh * (long long)F.lo + (long long)((unsigned long long)dl * F.hi);
+    return a + hh + (mid >> 26);
+}
+
+// v * 2^-e as a double for |v| < 2^53 (exact: no rounding needed), with
+// integer operations only.  Results below the normal range flush to zero.
 __device__ __forceinline__ double i64_scaled_to_double(long long v, int e) {
     if (v == 0) return 0.0;
     const unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
     const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
     const int msb = 63 - __clzll((long long)a);
-    long long ex = (long long)msb - e + 1023;
-    unsigned long long mant;
-    if (msb <= 52) {
-        mant = a << (52 - msb);
-    } else {
-        const int sh = msb - 52;
-        mant = a >> sh;
-        const unsigned long long rem = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-        if (rem > half || (rem == half && (mant & 1ull))) {
-            mant += 1;
-            if (mant >> 53) {
-                mant >>= 1;
-                ex += 1;
-            }
-        }
-    }
+    const long long ex = (long long)msb - e + 1023;
     if (ex <= 0) return __longlong_as_double((long long)sign);
-    if (ex >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
+    const unsigned long long mant = a << (52 - msb);
     return __longlong_as_double((long long)(sign | ((unsigned long long)ex << 52) |
                                             (mant & 0xFFFFFFFFFFFFFull)));
 }

@@ -130,9 +130,15 @@ __device__ __forceinline__ void block_keys_commit(long long lo[3], long long hi[
     }
 }
 
+// All six finite: the largest exponent field (from the 32-bit high words,
+// combined with integer max so the test stays on the integer pipes) is below
+// the all-ones exponent of Inf/NaN.
 __device__ __forceinline__ bool finite6(double a, double b, double c, double d, double e, double f) {
-    return !(nonfinite_bits(a) | nonfinite_bits(b) | nonfinite_bits(c) | nonfinite_bits(d) |
-             nonfinite_bits(e) | nonfinite_bits(f));
+    const unsigned m = 0x7FF00000u;
+    const unsigned hm = max(max(max((unsigned)__double2hiint(a) & m, (unsigned)__double2hiint(b) & m),
+                                max((unsigned)__double2hiint(c) & m, (unsigned)__double2hiint(d) & m)),
+                            max((unsigned)__double2hiint(e) & m, (unsigned)__double2hiint(f) & m));
+    return hm != m;
 }
 
 __global__ void k_minmax(const double *__restrict__ x, const double *__restrict__ px,
@@ -278,24 +284,38 @@ __global__ void k_field(const double *__restrict__ phi, int nn, const Box *box, 
         m1 = fmax(m1, fabs(ey));
         m2 = fmax(m2, fabs(ez));
     }
+    // maxima of non-negative doubles as their bit patterns (they order alike):
+    // warp, then block, then one atomic per block and component
+    unsigned long long b0 = (unsigned long long)__double_as_longlong(m0);
+    unsigned long long b1 = (unsigned long long)__double_as_longlong(m1);
+    unsigned long long b2 = (unsigned long long)__double_as_longlong(m2);
     for (int o = 16; o > 0; o >>= 1) {
-        m0 = fmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
-        m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
-        m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+        b0 = max(b0, __shfl_xor_sync(0xffffffffu, b0, o));
+        b1 = max(b1, __shfl_xor_sync(0xffffffffu, b1, o));
+        b2 = max(b2, __shfl_xor_sync(0xffffffffu, b2, o));
     }
-    if ((threadIdx.x & 31) == 0) {  // bit patterns of non-negative doubles order like the values
-        atomicMax(&emax[0], (unsigned long long)__double_as_longlong(m0));
-        atomicMax(&emax[1], (unsigned long long)__double_as_longlong(m1));
-        atomicMax(&emax[2], (unsigned long long)__double_as_longlong(m2));
+    __shared__ unsigned long long sm[3][TPB / 32];
+    if ((threadIdx.x & 31) == 0) {
+        sm[0][threadIdx.x >> 5] = b0;
+        sm[1][threadIdx.x >> 5] = b1;
+        sm[2][threadIdx.x >> 5] = b2;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        unsigned long long v = 0;
+        for (int w = 0; w < TPB / 32; ++w) v = max(v, sm[threadIdx.x][w]);
+        atomicMax(&emax[threadIdx.x], v);
     }
 }
 
-// Scale exponent e with max * 2^e in [2^60, 2^61), so node values and their
-// differences fit in int64 with room to spare.
+// Scale exponent e with max * 2^e in [2^49, 2^50): node values and their
+// differences fit the 26-bit-limb interpolation, interpolated values convert
+// to double exactly, and the resolution (2^-49 of the largest value) is that
+// of a double.
 __device__ __forceinline__ int field_exponent(unsigned long long maxbits) {
     const double m = __longlong_as_double((long long)maxbits);
     if (!(m > 0.0) || !isfinite(m)) return 0;
-    return 60 - ilogb(m);
+    return 49 - ilogb(m);
 }
 
 // Field in int64 fixed point: E_fix = rint(E' * 2^e_d); exponents in escale.
@@ -323,8 +343,9 @@ cudaError_t launch_field(const double *phi, int nn, const Box *box, double kx, d
     cudaError_t e = cudaMemsetAsync(emax, 0, 3 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const int blocks = (int)((nodes + TPB - 1) / TPB);
-    BT_LAUNCH(K_FIELD, s, k_field<<<blocks, TPB, 0, s>>>(phi, nn, box, kx, ky, kz,
-                                                         (Field4 *)efield, emax));
+    const int fblocks = blocks < 148 * 8 ? blocks : 148 * 8;
+    BT_LAUNCH(K_FIELD, s, k_field<<<fblocks, TPB, 0, s>>>(phi, nn, box, kx, ky, kz,
+                                                          (Field4 *)efield, emax));
     BT_LAUNCH(K_EFIX, s, k_efix<<<blocks, TPB, 0, s>>>((const Field4 *)efield, nodes, emax, efix,
                                                        escale));
     return cudaGetLastError();
@@ -332,7 +353,7 @@ cudaError_t launch_field(const double *phi, int nn, const Box *box, double kx, d
 
 // -------------------------------------------------- fused particle kernel
 
-constexpr int PPT = 8;                 // particles per thread
+constexpr int PPT = 4;                 // particles per thread
 constexpr int CHUNK = TPB * PPT;       // particles per block
 constexpr int TILE_CAP = 4096;         // nodes of the shared-memory deposit tile
 
@@ -349,6 +370,7 @@ struct PartArgs {
     TrackState *st;                    // min/max (MM)
     int32_t *status;
     int exact_u;                       // u = (X - lo) * (1/h) instead of one FMA
+    int flag_outside;                  // report deposit particles outside the box
 };
 
 // u = (X - lo)/h.  For a box whose offset is small against its cell size
@@ -385,7 +407,7 @@ __device__ __forceinline__ void cell_frac(double u, int nn, int &cell, unsigned 
 //         through a shared-memory tile covering the block's cells when they fit.
 // MM:     min/max keys of the new rest-frame positions.
 template <int MK, bool GATHER, bool DEP, bool MM>
-__global__ void __launch_bounds__(TPB, 2) k_particles(PartArgs a) {
+__global__ void __launch_bounds__(TPB, 3) k_particles(PartArgs a) {
     extern __shared__ unsigned long long dsm[];
     unsigned long long *sF = dsm;                                // [3][CHUNK] fractions
     int *scell = (int *)(dsm + 3 * CHUNK);                       // [CHUNK] linear cell or -1
@@ -419,34 +441,33 @@ __global__ void __launch_bounds__(TPB, 2) k_particles(PartArgs a) {
         if constexpr (GATHER) {
             double px = a.px[p], py = a.py[p], pt = a.pt[p];
             int c0, c1, c2;
-            unsigned long long F0, F1, F2;
+            unsigned long long G0, G1, G2;
             bool out0 = false;
             if (a.exact_u) {
-                cell_frac((x - lo0) * ih0, nn, c0, F0, out0);
-                cell_frac((y - lo1) * ih1, nn, c1, F1, out0);
-                cell_frac((__dmul_rn(a.nbg, t) - lo2) * ih2, nn, c2, F2, out0);
+                cell_frac((x - lo0) * ih0, nn, c0, G0, out0);
+                cell_frac((y - lo1) * ih1, nn, c1, G1, out0);
+                cell_frac((__dmul_rn(a.nbg, t) - lo2) * ih2, nn, c2, G2, out0);
             } else {
-                cell_frac(fma(x, ih0, o0), nn, c0, F0, out0);
-                cell_frac(fma(y, ih1, o1), nn, c1, F1, out0);
-                cell_frac(fma(t, tz, o2), nn, c2, F2, out0);
+                cell_frac(fma(x, ih0, o0), nn, c0, G0, out0);
+                cell_frac(fma(y, ih1, o1), nn, c1, G1, out0);
+                cell_frac(fma(t, tz, o2), nn, c2, G2, out0);
             }
+            const Frac F0 = split26(G0), F1 = split26(G1), F2 = split26(G2);
             outside |= out0;
-            const EFix *e = a.ef + (((long long)c2 * nn + c1) * nn + c0);
-            const long long sy = nn, sz = (long long)nn * nn;
-            // lerp in x on the four (y, z) edges, then y, then z
-            long long gx[2][2], gy[2][2], gz[2][2];
+            // CIC interpolation in lerp form, one field component at a time (a
+            // small live register set): x on the four (y, z) edges, then y, z.
+            const long long *e = &a.ef[((long long)c2 * nn + c1) * nn + c0].x;
+            const long long sy = 4LL * nn, sz = 4LL * nn * nn;  // in int64 units (4 per node)
+            long long comp[3];
 #pragma unroll
-            for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-                for (int dy = 0; dy < 2; ++dy) {
-                    const EFix v0 = e[dz * sz + dy * sy], v1 = e[dz * sz + dy * sy + 1];
-                    gx[dz][dy] = lerp52(v0.x, v1.x, F0);
-                    gy[dz][dy] = lerp52(v0.y, v1.y, F0);
-                    gz[dz][dy] = lerp52(v0.z, v1.z, F0);
-                }
-            const long long ex = lerp52(lerp52(gx[0][0], gx[0][1], F1), lerp52(gx[1][0], gx[1][1], F1), F2);
-            const long long ey = lerp52(lerp52(gy[0][0], gy[0][1], F1), lerp52(gy[1][0], gy[1][1], F1), F2);
-            const long long ez = lerp52(lerp52(gz[0][0], gz[0][1], F1), lerp52(gz[1][0], gz[1][1], F1), F2);
+            for (int cc = 0; cc < 3; ++cc) {
+                const long long *q = e + cc;
+                const long long g00 = lerp52(q[0], q[4], F0), g01 = lerp52(q[sy], q[sy + 4], F0);
+                const long long g10 = lerp52(q[sz], q[sz + 4], F0),
+                                g11 = lerp52(q[sz + sy], q[sz + sy + 4], F0);
+                comp[cc] = lerp52(lerp52(g00, g01, F1), lerp52(g10, g11, F1), F2);
+            }
+            const long long ex = comp[0], ey = comp[1], ez = comp[2];
             px += i64_scaled_to_double(ex, e0);
             py += i64_scaled_to_double(ey, e1);
             pt += i64_scaled_to_double(ez, e2);
@@ -482,7 +503,7 @@ __global__ void __launch_bounds__(TPB, 2) k_particles(PartArgs a) {
                     cell_frac(fma(y, ih1, o1), nn, c1, F1, out1);
                     cell_frac(fma(t, tz, o2), nn, c2, F2, out1);
                 }
-                if (out1 && !GATHER) outside = true;  // explicit box not containing the bunch
+                if (out1 && a.flag_outside) outside = true;  // box not containing the bunch
                 if (!out1) {  // particles outside are left out: the box rule then regrids
                     sF[slot] = F0;
                     sF[CHUNK + slot] = F1;
@@ -531,14 +552,14 @@ __global__ void __launch_bounds__(TPB, 2) k_particles(PartArgs a) {
             const int cell = scell[slot];
             if (cell < 0) continue;
             const unsigned long long F0 = sF[slot], F1 = sF[CHUNK + slot], F2 = sF[2 * CHUNK + slot];
-            const unsigned long long wx[2] = {one - F0, F0}, wy[2] = {one - F1, F1},
-                                     wz[2] = {one - F2, F2};
+            const Frac wx[2] = {split26(one - F0), split26(F0)}, wy[2] = {split26(one - F1), split26(F1)},
+                       wz[2] = {split26(one - F2), split26(F2)};
             const int c2 = cell / nn2, c1 = (cell / nn) % nn, c0 = cell % nn;
 #pragma unroll
             for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
                 for (int dy = 0; dy < 2; ++dy) {
-                    const unsigned long long wyz = mulshr52(wy[dy], wz[dz]);
+                    const Frac wyz = split26(mulshr52(wy[dy], wz[dz]));
 #pragma unroll
                     for (int dx = 0; dx < 2; ++dx) {
                         const unsigned long long v = mulshr52(wx[dx], wyz) >> 1;  // 51-bit
@@ -612,19 +633,17 @@ cudaError_t launch_kick_push_deposit(double *const c[6], int64_t n, double betag
     a.status = status;
     const int mk = map_host ? map_kind(*map_host) : MAP_NONE;
     if (map_host) a.map = *map_host;
-    if (!deposit) {
-        switch (mk) {
-            case MAP_NONE: return launch_pk<MAP_NONE, true, false, false>(a, s, K_GATHER);
-            case MAP_DRIFT: return launch_pk<MAP_DRIFT, true, false, false>(a, s, K_GATHER);
-            case MAP_QUAD: return launch_pk<MAP_QUAD, true, false, false>(a, s, K_GATHER);
-            default: return launch_pk<MAP_GENERAL, true, false, false>(a, s, K_GATHER);
-        }
-    }
+    // gather + kick + map (no shared memory, 3 blocks/SM) ...
+    cudaError_t e;
     switch (mk) {
-        case MAP_DRIFT: return launch_pk<MAP_DRIFT, true, true, true>(a, s, K_GATHER);
-        case MAP_QUAD: return launch_pk<MAP_QUAD, true, true, true>(a, s, K_GATHER);
-        default: return launch_pk<MAP_GENERAL, true, true, true>(a, s, K_GATHER);
+        case MAP_NONE: e = launch_pk<MAP_NONE, true, false, false>(a, s, K_GATHER); break;
+        case MAP_DRIFT: e = launch_pk<MAP_DRIFT, true, false, false>(a, s, K_GATHER); break;
+        case MAP_QUAD: e = launch_pk<MAP_QUAD, true, false, false>(a, s, K_GATHER); break;
+        default: e = launch_pk<MAP_GENERAL, true, false, false>(a, s, K_GATHER); break;
     }
+    if (e != cudaSuccess || !deposit) return e;
+    // ... then the next kick's deposit and the min/max from the new x, y, t
+    return launch_pk<MAP_NONE, false, true, true>(a, s, K_DEPOSIT);
 }
 
 // Charge deposition alone (Listing 1 particle shape 1 = CIC): node weights
@@ -645,6 +664,7 @@ cudaError_t launch_deposit(double *const c[6], int64_t n, double betagamma, cons
     a.acc_lo = acc_lo;
     a.status = status;
     a.exact_u = box_needs_exact_u(box_host) ? 1 : 0;
+    a.flag_outside = 1;
     return launch_pk<MAP_NONE, false, true, false>(a, s, K_DEPOSIT);
 }
 
