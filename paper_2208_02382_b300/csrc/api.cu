@@ -45,6 +45,14 @@ struct bx_ctx {
     double *scr[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     double **dev_ptrs = nullptr;
     int sort_interval = 16;                // kicks between re-binning
+    // per-kick CUDA graph (conditional nodes), rebuilt when the bunch changes
+    cudaGraphExec_t kick_exec = nullptr;
+    double *graph_c[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int64_t *graph_id = nullptr;
+    int64_t graph_n = -1;
+    double graph_bg = 0.0;
+    cudaStream_t cap_stream = nullptr, body_stream = nullptr;
+    bool graphs_off = false;               // the graph path failed once: plain launches
     Profiler *prof = nullptr;
     std::string err;
 };
@@ -221,6 +229,10 @@ int32_t ensure_green(bx_ctx *ctx, const double h[3], cudaStream_t s) {
     CK(green_spectrum_from_table(&ctx->plan, ctx->gtable, s), "green spectrum");
     ctx->green_valid = true;
     memcpy(ctx->green_h, h, sizeof(ctx->green_h));
+    // the tracking loop decides on the device from the state's copy of h
+    CK(cudaMemcpyAsync(ctx->st->green_h, ctx->green_h, sizeof(ctx->green_h),
+                       cudaMemcpyHostToDevice, s),
+       "green h");
     return BX_OK;
 }
 
@@ -271,6 +283,135 @@ void init_state(TrackState *h) {
         h->mm[d] = dkey(INFINITY);
         h->mm[3 + d] = dkey(-INFINITY);
     }
+}
+
+// The kernels of one device-driven kick, in pieces (so the graph builder can
+// put the gated pieces into conditional bodies).
+struct KickArgs {
+    bx_ctx *ctx;
+    double *const *c;
+    int64_t *id;
+    int64_t n;
+    double bg;
+    bool binning;
+};
+
+cudaError_t kick_green(const KickArgs &k, cudaStream_t s) {
+    bx_ctx *ctx = k.ctx;
+    cudaError_t e = launch_igf_table(ctx->n, nullptr, ctx->fcorner, ctx->gtable, s, ctx->st);
+    if (e == cudaSuccess) e = green_spectrum_from_table(&ctx->plan, ctx->gtable, s, &ctx->st->green_stale);
+    if (e == cudaSuccess) e = launch_green_commit(ctx->st, s);
+    return e;
+}
+
+cudaError_t kick_sort(const KickArgs &k, cudaStream_t s) {
+    bx_ctx *ctx = k.ctx;
+    return launch_sort(k.c, (long long *)k.id, k.n, k.bg, &ctx->st->box, ctx->n, ctx->keys,
+                       ctx->counts, ctx->offs, ctx->sums, ctx->scr, ctx->id_scr, ctx->dev_ptrs, s,
+                       &ctx->st->sort_gate);
+}
+
+cudaError_t kick_deposit(const KickArgs &k, cudaStream_t s) {
+    bx_ctx *ctx = k.ctx;
+    return launch_track_deposit(k.c, k.n, k.bg, &ctx->st->box, ctx->n, ctx->acc_hi, ctx->acc_lo,
+                                ctx->st, ctx->status, s);
+}
+
+cudaError_t kick_solve_field_push(const KickArgs &k, cudaStream_t s) {
+    bx_ctx *ctx = k.ctx;
+    cudaError_t e = solve_acc_to_phi(&ctx->plan, ctx->acc_hi, ctx->acc_lo, 0.0, ctx->phi, s,
+                                     &ctx->st->rho_scale);
+    if (e == cudaSuccess)
+        e = launch_field(ctx->phi, ctx->n, &ctx->st->box, 0.0, 0.0, 0.0, ctx->efield, ctx->emax,
+                         ctx->efix, ctx->escale, s, ctx->st, ctx->maps);
+    if (e == cudaSuccess)
+        e = launch_track_particles(k.c, k.n, k.bg, &ctx->st->box, ctx->n, ctx->efix, ctx->escale,
+                                   ctx->maps, ctx->acc_hi, ctx->acc_lo, ctx->st, ctx->status, s, 1);
+    return e;
+}
+
+cudaError_t kick_next_deposit(const KickArgs &k, cudaStream_t s) {
+    bx_ctx *ctx = k.ctx;
+    return launch_track_particles(k.c, k.n, k.bg, &ctx->st->box, ctx->n, ctx->efix, ctx->escale,
+                                  ctx->maps, ctx->acc_hi, ctx->acc_lo, ctx->st, ctx->status, s, 2);
+}
+
+// Plain launches of one kick (gated kernels return at once when not needed).
+cudaError_t kick_plain(const KickArgs &k, cudaStream_t s) {
+    bx_ctx *ctx = k.ctx;
+    cudaError_t e = launch_box_rule(ctx->st, ctx->n, k.n, ctx->log, ctx->log_cap, true, s);
+    if (e == cudaSuccess) e = kick_green(k, s);
+    if (e == cudaSuccess && k.binning) e = kick_sort(k, s);
+    if (e == cudaSuccess) e = kick_deposit(k, s);
+    if (e == cudaSuccess) e = kick_solve_field_push(k, s);
+    if (e == cudaSuccess) e = kick_next_deposit(k, s);
+    return e;
+}
+
+// Adds an IF node on condition `h` at the current point of the capture on
+// `cs` and captures `body` into it on `bs`.
+template <class F>
+cudaError_t capture_if(cudaStream_t cs, cudaStream_t bs, cudaGraph_t cg,
+                       cudaGraphConditionalHandle h, F body) {
+    cudaStreamCaptureStatus status;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &status, nullptr, nullptr, &deps, nullptr, &ndeps);
+    if (e != cudaSuccess) return e;
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &p);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t g = p.conditional.phGraph_out[0];
+    e = cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCaptureToGraph(bs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    cudaError_t eb = body(bs);
+    e = cudaStreamEndCapture(bs, &g);
+    return eb != cudaSuccess ? eb : e;
+}
+
+// One kick as a CUDA graph: box rule (sets the conditions), IF(Green's
+// function stale){rebuild}, IF(re-bin due){sort}, IF(deposit needed){deposit},
+// solve + field + gather/kick/map, IF(next kick){deposit for it}.
+cudaError_t build_kick_graph(const KickArgs &k, cudaGraphExec_t *exec) {
+    bx_ctx *ctx = k.ctx;
+    cudaError_t e = cudaSuccess;
+    if (!ctx->cap_stream) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !ctx->body_stream)
+        e = cudaStreamCreateWithFlags(&ctx->body_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaStream_t cs = ctx->cap_stream, bs = ctx->body_stream;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t cg = nullptr;
+    cudaStreamCaptureStatus status;
+    e = cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, nullptr, nullptr, nullptr);
+    cudaGraphConditionalHandle hg = 0, hs = 0, hd = 0, hn = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hg, cg, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hs, cg, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hd, cg, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hn, cg, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess)
+        e = launch_box_rule_graph(ctx->st, ctx->n, ctx->log, ctx->log_cap, hg, hs, hd, hn, cs);
+    if (e == cudaSuccess) e = capture_if(cs, bs, cg, hg, [&](cudaStream_t b) { return kick_green(k, b); });
+    if (e == cudaSuccess && k.binning)
+        e = capture_if(cs, bs, cg, hs, [&](cudaStream_t b) { return kick_sort(k, b); });
+    if (e == cudaSuccess) e = capture_if(cs, bs, cg, hd, [&](cudaStream_t b) { return kick_deposit(k, b); });
+    if (e == cudaSuccess) e = kick_solve_field_push(k, cs);
+    if (e == cudaSuccess)
+        e = capture_if(cs, bs, cg, hn, [&](cudaStream_t b) { return kick_next_deposit(k, b); });
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();  // clear a sticky capture error, if any
+    return e;
 }
 
 }  // namespace
@@ -339,6 +480,9 @@ int32_t bx_destroy(bx_ctx *ctx) {
     for (void *p : ptrs)
         if (p) cudaFree(p);
     fft_plan_free(&ctx->plan);
+    if (ctx->kick_exec) cudaGraphExecDestroy(ctx->kick_exec);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->body_stream) cudaStreamDestroy(ctx->body_stream);
     profiler_free(ctx->prof);
     delete ctx;
     return BX_OK;
@@ -391,6 +535,13 @@ int32_t bx_track(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t firs
             tab.push_back(to_coef(hk));
         }
     }
+    // kick factors of kick k and the map class, in table entry 1 + k
+    for (int64_t k = 0; k < nkicks; ++k) {
+        const double ds = sds[first_kick + k];
+        tab[1 + k].kick_t = r.sign * ds / (r.mass_eV * (r.bg * r.bg));
+        tab[1 + k].kick_z = -r.sign * ds / (r.mass_eV * r.bg);
+    }
+    for (auto &m : tab) m.kind = (double)map_kind(m);
     if ((rc = ensure_maps(ctx, tab.size()))) return rc;
     CK(cudaMemcpyAsync(ctx->maps, tab.data(), tab.size() * sizeof(MapCoef),
                        cudaMemcpyHostToDevice, s),
@@ -409,57 +560,46 @@ int32_t bx_track(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t firs
     const double q_macro = r.sign * std::fabs(beam->bunch_charge_C) / (double)beam->n;
     const bool binning = beam->id != nullptr;
     if (binning && (rc = ensure_sort_scratch(ctx, beam->n))) return rc;
-    // Per kick k: box rule on the current positions; the charge of those
-    // positions is already in the accumulators (deposited by the previous
-    // kick's particle kernel with the same box) unless this is the first kick
-    // or the box changed, in which case it is deposited here; re-binning every
-    // sort_interval kicks; solve; field; then one particle kernel does the
-    // gather, kick, merged half-maps and the next kick's deposit.
+    // Device-driven kicks: the box rule kernel of each kick sets the gates
+    // (Green's function rebuild, deposit of the current positions, re-binning,
+    // deposit for a next kick) that the later kernels of the kick read, and the
+    // per-kick map and kick factors come from the table at index 1 + k; no
+    // host decision or synchronisation between kicks.
+    CK(launch_call_init(ctx->st, (int)nkicks, q_macro, binning ? ctx->sort_interval : 0,
+                        ctx->kick, s),
+       "call init");
+    if (binning) CK(sort_set_pointers(c, ctx->scr, ctx->dev_ptrs, s), "sort pointers");
     CK(launch_push_maps(c, beam->n, ctx->maps, 1, s), "push");
     CK(launch_minmax(c, beam->n, r.bg, ctx->st, ctx->status, s), "minmax");
-    const size_t acc_bytes = (size_t)ctx->n * ctx->n * ctx->n * sizeof(unsigned long long);
-    for (int64_t k = 0; k < nkicks; ++k) {
-        const double ds = sds[first_kick + k];
-        CK(cudaMemcpyAsync(&ctx->st->kick, &ctx->kick, sizeof(long long), cudaMemcpyHostToDevice,
-                           s),
-           "kick counter");
-        CK(launch_box_rule(ctx->st, ctx->n, beam->n, ctx->log, ctx->log_cap, s), "box rule");
-        TrackState h;
-        if ((rc = read_state(ctx, &h, s))) return rc;
-        if (h.has_box == 0) return fail(ctx, BX_NONFINITE, "no box (non-finite coordinates?)");
-        for (int d = 0; d < 3; ++d)
-            if (!std::isfinite(h.box.lo[d]) || !std::isfinite(h.box.hi[d]) || !(h.box.h[d] > 0.0))
-                return fail(ctx, BX_NONFINITE, "non-finite particle coordinates");
-        if ((rc = ensure_green(ctx, h.box.h, s))) return rc;
-        const Box *box = &ctx->st->box;
-        if (binning && k % ctx->sort_interval == 0)
-            CK(launch_sort(c, (long long *)beam->id, beam->n, r.bg, box, ctx->n, ctx->keys,
-                           ctx->counts, ctx->offs, ctx->sums, ctx->scr, ctx->id_scr,
-                           ctx->dev_ptrs, s),
-               "sort");
-        if (k == 0 || h.regrid)
-            CK(launch_deposit(c, beam->n, r.bg, box, h.box, ctx->n, ctx->acc_hi, ctx->acc_lo,
-                              ctx->status, s),
-               "deposit");
-        const double rho_scale = q_macro / (h.box.h[0] * h.box.h[1] * h.box.h[2]);
-        CK(solve_acc_to_phi(&ctx->plan, ctx->acc_hi, ctx->acc_lo, rho_scale, ctx->phi, s),
-           "solve");
-        const double kt = r.sign * ds / (r.mass_eV * (r.bg * r.bg));
-        const double kz = -r.sign * ds / (r.mass_eV * r.bg);
-        CK(launch_field(ctx->phi, ctx->n, box, kt, kt, kz, ctx->efield, ctx->emax, ctx->efix,
-                        ctx->escale, s),
-           "field");
-        const bool last = k + 1 == nkicks;
-        if (!last) {
-            CK(cudaMemsetAsync(ctx->acc_hi, 0, acc_bytes, s), "clear");
-            CK(cudaMemsetAsync(ctx->acc_lo, 0, acc_bytes, s), "clear");
+    const KickArgs ka{ctx, c, beam->id, beam->n, r.bg, binning};
+    bool use_graph = !ctx->graphs_off && !profiler_timing(ctx->prof);
+    if (use_graph) {
+        bool same = ctx->kick_exec && ctx->graph_n == beam->n && ctx->graph_id == beam->id &&
+                    ctx->graph_bg == r.bg;
+        for (int q = 0; q < 6 && same; ++q) same = ctx->graph_c[q] == c[q];
+        if (!same) {
+            if (ctx->kick_exec) cudaGraphExecDestroy(ctx->kick_exec);
+            ctx->kick_exec = nullptr;
+            // the captured kernels must not run before the prologue above
+            CK(cudaStreamSynchronize(s), "sync");
+            if (build_kick_graph(ka, &ctx->kick_exec) != cudaSuccess) {
+                ctx->kick_exec = nullptr;
+                ctx->graphs_off = true;
+                use_graph = false;
+            } else {
+                for (int q = 0; q < 6; ++q) ctx->graph_c[q] = c[q];
+                ctx->graph_id = beam->id;
+                ctx->graph_n = beam->n;
+                ctx->graph_bg = r.bg;
+            }
         }
-        CK(launch_kick_push_deposit(c, beam->n, r.bg, box, h.box, ctx->n, ctx->efix, ctx->escale,
-                                    &tab[1 + k], !last, ctx->acc_hi, ctx->acc_lo, ctx->st,
-                                    ctx->status, s),
-           "gather/kick/push/deposit");
-        ctx->kick += 1;
     }
+    for (int64_t k = 0; k < nkicks; ++k) {
+        if (use_graph) CK(cudaGraphLaunch(ctx->kick_exec, s), "kick graph");
+        else CK(kick_plain(ka, s), "kick");
+    }
+    ctx->kick += nkicks;
+    ctx->green_valid = false;  // the device may have rebuilt the spectrum for another h
     return BX_OK;
 }
 
@@ -489,7 +629,7 @@ int32_t bx_deposit(bx_ctx *ctx, const bx_beam *beam, bx_grid *grid, void *stream
         CK(launch_minmax(c, beam->n, r.bg, ctx->st, ctx->status, s), "minmax");
         CK(cudaMemcpyAsync(&ctx->st->kick, &ctx->kick, sizeof(long long), cudaMemcpyHostToDevice, s),
            "kick counter");
-        CK(launch_box_rule(ctx->st, ctx->n, beam->n, ctx->log, ctx->log_cap, s), "box rule");
+        CK(launch_box_rule(ctx->st, ctx->n, beam->n, ctx->log, ctx->log_cap, false, s), "box rule");
         TrackState h;
         if ((rc = read_state(ctx, &h, s))) return rc;
         for (int d = 0; d < 3; ++d) {

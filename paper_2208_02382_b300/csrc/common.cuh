@@ -13,12 +13,15 @@ enum : int32_t { ST_NONFINITE = 1, ST_TIMEOUT = 2, ST_OUTSIDE = 4 };
 
 // Linear map with the structure shared by drift, quadrupole and sector bend
 // and closed under composition (pt is unchanged, t enters its own row with
-// coefficient 1, y decouples):
+// coefficient 1, y decouples).  In the per-call map table the three padding
+// slots carry the kick factors of the slice (transverse, longitudinal) and the
+// map's structure class:
 //   x'  = m00 x + m01 px + m05 pt        y'  = m22 y + m23 py
 //   px' = m10 x + m11 px + m15 pt        py' = m32 y + m33 py
 //   t'  = t + m40 x + m41 px + m45 pt    pt' = pt
 struct MapCoef {
-    double m00, m01, m05, m10, m11, m15, m22, m23, m32, m33, m40, m41, m45, pad0, pad1, pad2;
+    double m00, m01, m05, m10, m11, m15, m22, m23, m32, m33, m40, m41, m45;
+    double kick_t, kick_z, kind;
 };
 
 // Pre-scaled field at a node (momentum change per unit CIC weight), padded to
@@ -49,6 +52,19 @@ struct TrackState {
     double green_h[3];      // h the Green's function spectrum was built for
     long long kick;         // kick counter (since creation / reset)
     long long nlog;         // regrid log length
+    // Device-driven tracking: the box rule of each kick sets these gates,
+    // which the later kernels of the kick read (a gated kernel whose gate is
+    // 0 returns at once), so a call needs no host decision between kicks.
+    int32_t k_in_call;      // kick index within the current bx_track call
+    int32_t nkicks_call;    // kicks in the call
+    int32_t deposit_gate;   // deposit the current positions (first kick or new box)
+    int32_t sort_gate;      // re-bin the particles now
+    int32_t next_gate;      // a next kick follows in this call (deposit for it)
+    int32_t exact_u;        // box far from the origin: u = (X - lo)/h unfused
+    int32_t sort_interval;  // kicks between re-binning (0: never)
+    int32_t halt;           // non-finite box: skip the space-charge work
+    double q_macro;         // macroparticle charge [C]
+    double rho_scale;       // q_macro / (hx hy hz)
 };
 
 // Order-preserving map between doubles and signed 64-bit keys (monotone for
@@ -86,6 +102,7 @@ const char *kernel_name(int id);
 void prof_begin(int id, cudaStream_t s);
 void prof_end(int id, cudaStream_t s);
 Profiler *profiler_new();
+bool profiler_timing(const Profiler *p);
 void profiler_free(Profiler *p);
 void profiler_enable(Profiler *p, bool on);
 cudaError_t profiler_read(Profiler *p, double *ms, long long *launches, int cap);
@@ -126,18 +143,38 @@ cudaError_t launch_kick_push_deposit(double *const c[6], int64_t n, double betag
                                      unsigned long long *acc_hi, unsigned long long *acc_lo,
                                      TrackState *st, int32_t *status, cudaStream_t s);
 cudaError_t launch_box_rule(TrackState *st, int nn, int64_t n, long long *log, int64_t log_cap,
-                            cudaStream_t s);
+                            bool advance, cudaStream_t s);
 cudaError_t launch_field(const double *phi, int nn, const Box *box, double kx, double ky,
                          double kz, double *efield, unsigned long long *emax, EFix *efix,
-                         int *escale, cudaStream_t s);
+                         int *escale, cudaStream_t s, const TrackState *st = nullptr,
+                         const MapCoef *maps = nullptr);
+cudaError_t launch_call_init(TrackState *st, int nkicks, double q_macro, int sort_interval,
+                             long long kick0, cudaStream_t s);
+cudaError_t launch_zero_acc(unsigned long long *a, unsigned long long *b, int nn, const int *gate,
+                            cudaStream_t s);
+cudaError_t launch_track_particles(double *const c[6], int64_t n, double betagamma,
+                                   const Box *box, int nn, const EFix *ef, const int *escale,
+                                   const MapCoef *maps, unsigned long long *acc_hi,
+                                   unsigned long long *acc_lo, TrackState *st, int32_t *status,
+                                   cudaStream_t s, int part = 3);
+cudaError_t launch_box_rule_graph(TrackState *st, int nn, long long *log, int64_t cap,
+                                  cudaGraphConditionalHandle hg, cudaGraphConditionalHandle hs,
+                                  cudaGraphConditionalHandle hd, cudaGraphConditionalHandle hn,
+                                  cudaStream_t s);
+cudaError_t launch_track_deposit(double *const c[6], int64_t n, double betagamma, const Box *box,
+                                 int nn, unsigned long long *acc_hi, unsigned long long *acc_lo,
+                                 TrackState *st, int32_t *status, cudaStream_t s);
+int map_kind(const MapCoef &m);
 // sort.cu
 int sort_brick_edge(int nn);
+cudaError_t sort_set_pointers(double *const c[6], double *const scratch[6], double **dev_ptrs,
+                              cudaStream_t s);
 int sort_bricks(int nn);
 int64_t sort_chunks(int64_t n);
 cudaError_t launch_sort(double *const c[6], long long *id, int64_t n, double betagamma,
                         const Box *box, int nn, int *keys, long long *counts, long long *offs,
                         long long *sums, double *const scratch[6], long long *id_scratch,
-                        double **dev_ptrs, cudaStream_t s);
+                        double **dev_ptrs, cudaStream_t s, const int *gate = nullptr);
 // moments.cu
 cudaError_t launch_moments(double *const c[6], int64_t n, double *partials, int nblocks,
                            double *out, cudaStream_t s);
@@ -156,10 +193,12 @@ void fft_plan_free(FftPlan *p);
 cudaError_t solve_rho_to_phi(const FftPlan *p, const double *rho, double *phi, cudaStream_t s);
 cudaError_t solve_acc_to_phi(const FftPlan *p, const unsigned long long *acc_hi,
                              const unsigned long long *acc_lo, double scale, double *phi,
-                             cudaStream_t s);
-cudaError_t green_spectrum_from_table(const FftPlan *p, const double *gtable, cudaStream_t s);
+                             cudaStream_t s, const double *scale_dev = nullptr);
+cudaError_t green_spectrum_from_table(const FftPlan *p, const double *gtable, cudaStream_t s,
+                                      const int *gate = nullptr);
 // igf.cu
 cudaError_t launch_igf_table(int n, const double h[3], double *fcorner, double *gtable,
-                             cudaStream_t s);
+                             cudaStream_t s, const TrackState *gate = nullptr);
+cudaError_t launch_green_commit(TrackState *st, cudaStream_t s);
 
 }  // namespace bt

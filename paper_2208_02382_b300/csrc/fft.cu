@@ -228,6 +228,7 @@ struct XIn {
     const double *rho;
     const unsigned long long *acc_hi, *acc_lo;
     double scale;
+    const double *scale_ptr;  // if set, the scale is read from the device
     const double *g;
 };
 
@@ -252,7 +253,10 @@ __device__ __forceinline__ double x_value(const XIn &in, int n, int x, int y, in
 template <int M, int SRC>
 __global__ void __launch_bounds__(FFT_TPB) k_fft_x_fwd(XIn in, int n, int ny, int nz,
                                                        const double2 *__restrict__ tw,
-                                                       double2 *__restrict__ out) {
+                                                       double2 *__restrict__ out,
+                                                       const int *gate) {
+    if (gate && *gate == 0) return;
+    if (SRC == SRC_ACC && in.scale_ptr) in.scale = *in.scale_ptr;
     constexpr int T = Shape<M>::T, LPB = FFT_TPB / T, V = M / T;
     extern __shared__ double2 smem[];
     double2 *stw = smem, *sl = smem + M;
@@ -305,7 +309,9 @@ __global__ void __launch_bounds__(FFT_TPB) k_fft_lines(const double2 *__restrict
                                                        int no, int P,
                                                        const double *__restrict__ gh,
                                                        double *__restrict__ gh_out,
-                                                       const double2 *__restrict__ tw) {
+                                                       const double2 *__restrict__ tw,
+                                                       const int *gate) {
+    if (gate && *gate == 0) return;
     constexpr int T = Shape<M>::T, LPB = FFT_TPB / T, V = M / T;
     constexpr bool INV1 = MODE == MODE_INV;
     extern __shared__ double2 smem[];
@@ -486,22 +492,22 @@ static cudaError_t solve_m(const FftPlan *p, const XIn &in, int src, double *phi
     const long long xpairs = (long long)(n / 2) * n;
     if (src == SRC_ACC)
         BT_LAUNCH(K_FFT_X, s, k_fft_x_fwd<M, SRC_ACC><<<blocks_lines(xpairs, M), FFT_TPB, sm, s>>>(
-                                  in, n, n, n, p->tw, S1));
+                                  in, n, n, n, p->tw, S1, nullptr));
     else
         BT_LAUNCH(K_FFT_X, s, k_fft_x_fwd<M, SRC_RHO><<<blocks_lines(xpairs, M), FFT_TPB, sm, s>>>(
-                                  in, n, n, n, p->tw, S1));
+                                  in, n, n, n, p->tw, S1, nullptr));
     // y: lines (z < n, kx), inputs y < n -> S2[z][ky][kx], all ky
     BT_LAUNCH(K_FFT_YZ, s, k_fft_lines<M, MODE_FWD><<<blocks_lines(n * P, M), FFT_TPB, sm, s>>>(
-                               S1, n * P, P, n, S2, M * P, P, M, n, (int)P, nullptr, nullptr, p->tw));
+                               S1, n * P, P, n, S2, M * P, P, M, n, (int)P, nullptr, nullptr, p->tw, nullptr));
     // z fused: lines (ky < m, kx), inputs z < n -> S3[zz][ky][kx], zz < n+2
     BT_LAUNCH(K_FFT_ZSOLVE, s,
               k_fft_lines<M, MODE_ZSOLVE><<<blocks_lines((long long)M * P, M), FFT_TPB, sm, s>>>(
                   S2, P, (long long)M * P, n, S3, P, (long long)M * P, (int)q, M, (int)P, p->ghat,
-                  nullptr, p->tw));
+                  nullptr, p->tw, nullptr));
     // inverse y: lines (zz < n+2, kx), all ky -> S4[zz][yy][kx]
     BT_LAUNCH(K_FFT_YZ, s, k_fft_lines<M, MODE_INV><<<blocks_lines(q * P, M), FFT_TPB, sm, s>>>(
                                S3, (long long)M * P, P, M, S4, q * P, P, (int)q, (int)q, (int)P,
-                               nullptr, nullptr, p->tw));
+                               nullptr, nullptr, p->tw, nullptr));
     // inverse x (complex to real) -> phi on nodes -1..n
     const double scale = 1.0 / ((double)M * M * M);
     BT_LAUNCH(K_FFT_XINV, s, k_fft_x_inv<M><<<blocks_lines(q * (q / 2), M), FFT_TPB, sm, s>>>(
@@ -510,7 +516,7 @@ static cudaError_t solve_m(const FftPlan *p, const XIn &in, int src, double *phi
 }
 
 template <int M>
-static cudaError_t green_m(const FftPlan *p, const double *gtable, cudaStream_t s) {
+static cudaError_t green_m(const FftPlan *p, const double *gtable, cudaStream_t s, const int *gate) {
     const int n = p->n;
     const long long P = n + 1;
     const size_t sm = smem_bytes(M);
@@ -518,16 +524,16 @@ static cudaError_t green_m(const FftPlan *p, const double *gtable, cudaStream_t 
     in.g = gtable;
     // x over all m^2 rows of the even extension -> buf[z][y][kx], z, y < m
     BT_LAUNCH(K_GREEN_X, s, k_fft_x_fwd<M, SRC_GREEN><<<blocks_lines((long long)(M / 2) * M, M),
-                                                        FFT_TPB, sm, s>>>(in, n, M, M, p->tw, p->buf));
+                                                        FFT_TPB, sm, s>>>(in, n, M, M, p->tw, p->buf, gate));
     // y: lines (z < m, kx), all y -> buf2[z][ky][kx], ky <= n
     BT_LAUNCH(K_GREEN_YZ, s, k_fft_lines<M, MODE_FWD><<<blocks_lines((long long)M * P, M), FFT_TPB,
                                                         sm, s>>>(p->buf, (long long)M * P, P, M,
                                                                  p->buf2, P * P, P, (int)P, M,
-                                                                 (int)P, nullptr, nullptr, p->tw));
+                                                                 (int)P, nullptr, nullptr, p->tw, gate));
     // z: lines (ky <= n, kx), all z -> real part at kz <= n
     BT_LAUNCH(K_GREEN_YZ, s, k_fft_lines<M, MODE_GREEN><<<blocks_lines(P * P, M), FFT_TPB, sm, s>>>(
                                  p->buf2, P, P * P, M, nullptr, 0, 0, 0, (int)P, (int)P, nullptr,
-                                 p->ghat, p->tw));
+                                 p->ghat, p->tw, gate));
     return cudaGetLastError();
 }
 
@@ -551,22 +557,24 @@ cudaError_t solve_rho_to_phi(const FftPlan *p, const double *rho, double *phi, c
 
 cudaError_t solve_acc_to_phi(const FftPlan *p, const unsigned long long *acc_hi,
                              const unsigned long long *acc_lo, double scale, double *phi,
-                             cudaStream_t s) {
+                             cudaStream_t s, const double *scale_dev) {
     XIn in{};
     in.acc_hi = acc_hi;
     in.acc_lo = acc_lo;
     in.scale = scale;
+    in.scale_ptr = scale_dev;
     return solve_any(p, in, SRC_ACC, phi, s);
 }
 
-cudaError_t green_spectrum_from_table(const FftPlan *p, const double *gtable, cudaStream_t s) {
+cudaError_t green_spectrum_from_table(const FftPlan *p, const double *gtable, cudaStream_t s,
+                                      const int *gate) {
     switch (p->m) {
-        case 16: return green_m<16>(p, gtable, s);
-        case 32: return green_m<32>(p, gtable, s);
-        case 64: return green_m<64>(p, gtable, s);
-        case 128: return green_m<128>(p, gtable, s);
-        case 256: return green_m<256>(p, gtable, s);
-        case 512: return green_m<512>(p, gtable, s);
+        case 16: return green_m<16>(p, gtable, s, gate);
+        case 32: return green_m<32>(p, gtable, s, gate);
+        case 64: return green_m<64>(p, gtable, s, gate);
+        case 128: return green_m<128>(p, gtable, s, gate);
+        case 256: return green_m<256>(p, gtable, s, gate);
+        case 512: return green_m<512>(p, gtable, s, gate);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -46,7 +46,16 @@ __device__ dd igf_antiderivative(dd x, dd y, dd z) {
     return f;
 }
 
-__global__ void k_igf_corner(int n, double hx, double hy, double hz, double2 *__restrict__ fc) {
+// With a tracking state `gate`, the cell size is the state's box h and the
+// kernel does nothing unless the Green's function is stale.
+__global__ void k_igf_corner(int n, double hx, double hy, double hz, double2 *__restrict__ fc,
+                             const TrackState *gate) {
+    if (gate) {
+        if (!gate->green_stale || gate->halt) return;
+        hx = gate->box.h[0];
+        hy = gate->box.h[1];
+        hz = gate->box.h[2];
+    }
     const int m = n + 2;
     const long long total = (long long)m * m * m;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -62,7 +71,9 @@ __global__ void k_igf_corner(int n, double hx, double hy, double hz, double2 *__
     }
 }
 
-__global__ void k_igf_sum(int n, const double2 *__restrict__ fc, double *__restrict__ g) {
+__global__ void k_igf_sum(int n, const double2 *__restrict__ fc, double *__restrict__ g,
+                          const TrackState *gate) {
+    if (gate && (!gate->green_stale || gate->halt)) return;
     const int m = n + 2, q = n + 1;
     const long long total = (long long)q * q * q;
     const dd ke = {KE_HI, KE_LO};
@@ -86,12 +97,26 @@ __global__ void k_igf_sum(int n, const double2 *__restrict__ fc, double *__restr
 }
 
 cudaError_t launch_igf_table(int n, const double h[3], double *fcorner, double *gtable,
-                             cudaStream_t s) {
+                             cudaStream_t s, const TrackState *gate) {
     const int m = n + 2, q = n + 1;
     long long tc = (long long)m * m * m, ts = (long long)q * q * q;
     int bc = (int)((tc + 127) / 128), bs = (int)((ts + 255) / 256);
-    BT_LAUNCH(K_IGF_CORNER, s, k_igf_corner<<<bc, 128, 0, s>>>(n, h[0], h[1], h[2], (double2 *)fcorner));
-    BT_LAUNCH(K_IGF_SUM, s, k_igf_sum<<<bs, 256, 0, s>>>(n, (const double2 *)fcorner, gtable));
+    const double h0 = h ? h[0] : 0.0, h1 = h ? h[1] : 0.0, h2 = h ? h[2] : 0.0;
+    BT_LAUNCH(K_IGF_CORNER, s, k_igf_corner<<<bc, 128, 0, s>>>(n, h0, h1, h2, (double2 *)fcorner, gate));
+    BT_LAUNCH(K_IGF_SUM, s, k_igf_sum<<<bs, 256, 0, s>>>(n, (const double2 *)fcorner, gtable, gate));
+    return cudaGetLastError();
+}
+
+// After a gated rebuild: the spectrum now belongs to the box's h.
+__global__ void k_green_commit(TrackState *st) {
+    if (threadIdx.x == 0 && blockIdx.x == 0 && st->green_stale && !st->halt) {
+        for (int d = 0; d < 3; ++d) st->green_h[d] = st->box.h[d];
+        st->green_stale = 0;
+    }
+}
+
+cudaError_t launch_green_commit(TrackState *st, cudaStream_t s) {
+    BT_LAUNCH(K_BOX, s, k_green_commit<<<1, 32, 0, s>>>(st));
     return cudaGetLastError();
 }
 

@@ -26,7 +26,7 @@ static inline int grid_for(int64_t n) {
 
 // Map structure classes (see MapCoef): drift (x += m01 px, y += m23 py,
 // t += m45 pt), no dispersion (2x2 blocks and the t-pt term), general.
-enum MapKind { MAP_NONE = 0, MAP_DRIFT = 1, MAP_QUAD = 2, MAP_GENERAL = 3 };
+enum MapKind { MAP_NONE = 0, MAP_DRIFT = 1, MAP_QUAD = 2, MAP_GENERAL = 3, MAP_TABLE = 4 };
 
 template <int MK>
 __device__ __forceinline__ void apply_map_k(const MapCoef &m, double &x, double &px, double &y,
@@ -57,6 +57,16 @@ __device__ __forceinline__ void apply_map_k(const MapCoef &m, double &x, double 
         py = npy;
         t = nt;
     }
+}
+
+// MAP_TABLE: the map (and its class in `kind`) comes from the per-call
+// device table; the class branch is uniform across the grid.
+__device__ __forceinline__ void apply_map_table(const MapCoef &m, double &x, double &px, double &y,
+                                                double &py, double &t, double pt) {
+    const int k = (int)m.kind;
+    if (k == MAP_DRIFT) apply_map_k<MAP_DRIFT>(m, x, px, y, py, t, pt);
+    else if (k == MAP_QUAD) apply_map_k<MAP_QUAD>(m, x, px, y, py, t, pt);
+    else apply_map_k<MAP_GENERAL>(m, x, px, y, py, t, pt);
 }
 
 int map_kind(const MapCoef &m) {
@@ -179,8 +189,17 @@ cudaError_t launch_minmax(double *const c[6], int64_t n, double betagamma, Track
 // extents floored at 1e-6 of the largest (1e-6 m if all are zero).  Explicit
 // round-to-nearest intrinsics keep every operation as written (no FMA
 // contraction), so the decision matches a plain IEEE evaluation.
-__global__ void k_box_rule(TrackState *st, int nn, long long *log, int64_t cap) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// A box far from the origin relative to its cell size needs the unfused u.
+__host__ __device__ __forceinline__ bool box_far_offset(const Box &b) {
+    for (int d = 0; d < 3; ++d)
+        if (fabs(b.lo[d] * b.inv_h[d]) > 4096.0 || fabs(b.hi[d] * b.inv_h[d]) > 4096.0) return true;
+    return false;
+}
+
+// With `advance` (tracking), the kick index of the call advances, the global
+// kick counter is logged and incremented, and the gates of this kick are set.
+__device__ void box_rule_body(TrackState *st, int nn, long long *log, int64_t cap, int advance) {
+    if (advance) st->k_in_call += 1;
     double mn[3], mx[3], ext[3];
     double big = 0.0;
     for (int d = 0; d < 3; ++d) {
@@ -215,21 +234,99 @@ __global__ void k_box_rule(TrackState *st, int nn, long long *log, int64_t cap) 
         if (st->nlog < cap) log[st->nlog] = st->kick;
         st->nlog += 1;
     }
+    bool finite = true;
+    for (int d = 0; d < 3; ++d)
+        finite = finite && isfinite(st->box.lo[d]) && isfinite(st->box.hi[d]) && st->box.h[d] > 0.0;
     st->regrid = need ? 1 : 0;
-    st->green_stale = (st->box.h[0] != st->green_h[0] || st->box.h[1] != st->green_h[1] ||
-                       st->box.h[2] != st->green_h[2])
+    st->halt = finite ? 0 : 1;
+    st->green_stale = (finite && (st->box.h[0] != st->green_h[0] || st->box.h[1] != st->green_h[1] ||
+                                  st->box.h[2] != st->green_h[2]))
                           ? 1
                           : 0;
+    if (advance) {
+        const int k = st->k_in_call;
+        st->deposit_gate = (finite && (need || k == 0)) ? 1 : 0;
+        st->sort_gate = (finite && st->sort_interval > 0 && k % st->sort_interval == 0) ? 1 : 0;
+        st->next_gate = (finite && k + 1 < st->nkicks_call) ? 1 : 0;
+        st->exact_u = box_far_offset(st->box) ? 1 : 0;
+        st->rho_scale = st->q_macro / (st->box.h[0] * st->box.h[1] * st->box.h[2]);
+        st->kick += 1;
+    }
     for (int d = 0; d < 3; ++d) {
         st->mm[d] = LLONG_MAX;
         st->mm[3 + d] = LLONG_MIN;
     }
 }
 
+__global__ void k_box_rule(TrackState *st, int nn, long long *log, int64_t cap, int advance) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    box_rule_body(st, nn, log, cap, advance);
+}
+
+// Graph form: the gates also set the conditions of the kick graph's IF nodes.
+__global__ void k_box_rule_graph(TrackState *st, int nn, long long *log, int64_t cap,
+                                 cudaGraphConditionalHandle h_green,
+                                 cudaGraphConditionalHandle h_sort,
+                                 cudaGraphConditionalHandle h_dep,
+                                 cudaGraphConditionalHandle h_next) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    box_rule_body(st, nn, log, cap, 1);
+    cudaGraphSetConditional(h_green, st->green_stale ? 1u : 0u);
+    cudaGraphSetConditional(h_sort, st->sort_gate ? 1u : 0u);
+    cudaGraphSetConditional(h_dep, st->deposit_gate ? 1u : 0u);
+    cudaGraphSetConditional(h_next, st->next_gate ? 1u : 0u);
+}
+
+cudaError_t launch_box_rule_graph(TrackState *st, int nn, long long *log, int64_t cap,
+                                  cudaGraphConditionalHandle hg, cudaGraphConditionalHandle hs,
+                                  cudaGraphConditionalHandle hd, cudaGraphConditionalHandle hn,
+                                  cudaStream_t s) {
+    BT_LAUNCH(K_BOX, s, k_box_rule_graph<<<1, 32, 0, s>>>(st, nn, log, cap, hg, hs, hd, hn));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_box_rule(TrackState *st, int nn, int64_t n, long long *log, int64_t cap,
-                            cudaStream_t s) {
+                            bool advance, cudaStream_t s) {
     (void)n;
-    BT_LAUNCH(K_BOX, s, k_box_rule<<<1, 32, 0, s>>>(st, nn, log, cap));
+    BT_LAUNCH(K_BOX, s, k_box_rule<<<1, 32, 0, s>>>(st, nn, log, cap, advance ? 1 : 0));
+    return cudaGetLastError();
+}
+
+// Start of a device-driven bx_track call.
+__global__ void k_call_init(TrackState *st, int nkicks, double q_macro, int sort_interval,
+                            long long kick0) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        st->k_in_call = -1;
+        st->nkicks_call = nkicks;
+        st->q_macro = q_macro;
+        st->sort_interval = sort_interval;
+        st->kick = kick0;
+        st->deposit_gate = st->sort_gate = st->next_gate = 0;
+    }
+}
+
+cudaError_t launch_call_init(TrackState *st, int nkicks, double q_macro, int sort_interval,
+                             long long kick0, cudaStream_t s) {
+    BT_LAUNCH(K_BOX, s, k_call_init<<<1, 32, 0, s>>>(st, nkicks, q_macro, sort_interval, kick0));
+    return cudaGetLastError();
+}
+
+// Zero the deposit accumulators when `gate` is set (or unconditionally).
+__global__ void k_zero_acc(unsigned long long *__restrict__ a, unsigned long long *__restrict__ b,
+                           long long nodes, const int *gate) {
+    if (gate && *gate == 0) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
+         i += (long long)gridDim.x * blockDim.x) {
+        a[i] = 0ull;
+        b[i] = 0ull;
+    }
+}
+
+cudaError_t launch_zero_acc(unsigned long long *a, unsigned long long *b, int nn, const int *gate,
+                            cudaStream_t s) {
+    const long long nodes = (long long)nn * nn * nn;
+    const int blocks = (int)((nodes + TPB - 1) / TPB) < 148 * 8 ? (int)((nodes + TPB - 1) / TPB) : 148 * 8;
+    BT_LAUNCH(K_DEPOSIT, s, k_zero_acc<<<blocks, TPB, 0, s>>>(a, b, nodes, gate));
     return cudaGetLastError();
 }
 
@@ -265,7 +362,13 @@ cudaError_t launch_acc_to_rho(const unsigned long long *acc_hi, const unsigned l
 // so the interpolated value is the momentum change.  Also the max |E'_d|.
 __global__ void k_field(const double *__restrict__ phi, int nn, const Box *box, double kx,
                         double ky, double kz, Field4 *__restrict__ ef,
-                        unsigned long long *__restrict__ emax) {
+                        unsigned long long *__restrict__ emax, const TrackState *st,
+                        const MapCoef *maps) {
+    if (maps) {  // tracking: kick factors of this kick from the per-call table
+        const MapCoef &m = maps[1 + st->k_in_call];
+        kx = ky = m.kick_t;
+        kz = m.kick_z;
+    }
     const int q = nn + 2;
     const double cx = -kx / (2.0 * box->h[0]);
     const double cy = -ky / (2.0 * box->h[1]);
@@ -338,14 +441,15 @@ __global__ void k_efix(const Field4 *__restrict__ ef, long long nodes,
 
 cudaError_t launch_field(const double *phi, int nn, const Box *box, double kx, double ky,
                          double kz, double *efield, unsigned long long *emax, EFix *efix,
-                         int *escale, cudaStream_t s) {
+                         int *escale, cudaStream_t s, const TrackState *st,
+                         const MapCoef *maps) {
     long long nodes = (long long)nn * nn * nn;
     cudaError_t e = cudaMemsetAsync(emax, 0, 3 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const int blocks = (int)((nodes + TPB - 1) / TPB);
     const int fblocks = blocks < 148 * 8 ? blocks : 148 * 8;
     BT_LAUNCH(K_FIELD, s, k_field<<<fblocks, TPB, 0, s>>>(phi, nn, box, kx, ky, kz,
-                                                          (Field4 *)efield, emax));
+                                                          (Field4 *)efield, emax, st, maps));
     BT_LAUNCH(K_EFIX, s, k_efix<<<blocks, TPB, 0, s>>>((const Field4 *)efield, nodes, emax, efix,
                                                        escale));
     return cudaGetLastError();
@@ -371,18 +475,16 @@ struct PartArgs {
     int32_t *status;
     int exact_u;                       // u = (X - lo) * (1/h) instead of one FMA
     int flag_outside;                  // report deposit particles outside the box
+    const int *gate;                   // if set and 0, the kernel does nothing
+    const MapCoef *maps;               // MAP_TABLE: per-call map table (entry 1 + k)
+    const TrackState *dst;             // device-driven: exact_u and k from here
 };
 
 // u = (X - lo)/h.  For a box whose offset is small against its cell size
 // (|lo/h| <= 4096, every ordinary box) one FMA, X*(1/h) - lo/h, is within
 // 1e-12 of a cell; a box far from the origin relative to its size (e.g. the
 // floored box of a single particle) takes the subtraction first.
-bool box_needs_exact_u(const Box &b) {
-    for (int d = 0; d < 3; ++d)
-        if (fabs(b.lo[d] * b.inv_h[d]) > 4096.0 || fabs(b.hi[d] * b.inv_h[d]) > 4096.0)
-            return true;
-    return false;
-}
+bool box_needs_exact_u(const Box &b) { return box_far_offset(b); }
 
 // Cell index and 52-bit fraction per dimension from u, with integer
 // operations only.  u below -1e-9 or above n-1+1e-6 (beyond the rounding of
@@ -408,6 +510,9 @@ __device__ __forceinline__ void cell_frac(double u, int nn, int &cell, unsigned 
 // MM:     min/max keys of the new rest-frame positions.
 template <int MK, bool GATHER, bool DEP, bool MM>
 __global__ void __launch_bounds__(TPB, 3) k_particles(PartArgs a) {
+    if (a.gate && *a.gate == 0) return;
+    if (a.dst) a.exact_u = a.dst->exact_u;
+    if constexpr (MK == MAP_TABLE) a.map = a.maps[1 + a.dst->k_in_call];
     extern __shared__ unsigned long long dsm[];
     unsigned long long *sF = dsm;                                // [3][CHUNK] fractions
     int *scell = (int *)(dsm + 3 * CHUNK);                       // [CHUNK] linear cell or -1
@@ -471,7 +576,8 @@ __global__ void __launch_bounds__(TPB, 3) k_particles(PartArgs a) {
             px += i64_scaled_to_double(ex, e0);
             py += i64_scaled_to_double(ey, e1);
             pt += i64_scaled_to_double(ez, e2);
-            apply_map_k<MK>(a.map, x, px, y, py, t, pt);
+            if constexpr (MK == MAP_TABLE) apply_map_table(a.map, x, px, y, py, t, pt);
+            else apply_map_k<MK>(a.map, x, px, y, py, t, pt);
             bad |= !finite6(x, px, y, py, t, pt);
             a.x[p] = x;
             a.px[p] = px;
@@ -644,6 +750,49 @@ cudaError_t launch_kick_push_deposit(double *const c[6], int64_t n, double betag
     if (e != cudaSuccess || !deposit) return e;
     // ... then the next kick's deposit and the min/max from the new x, y, t
     return launch_pk<MAP_NONE, false, true, true>(a, s, K_DEPOSIT);
+}
+
+// Device-driven tracking kick: A with the map of this kick from the table
+// (part & 1), then, if a next kick follows, the zeroing of the accumulators
+// and B (part & 2).
+cudaError_t launch_track_particles(double *const c[6], int64_t n, double betagamma,
+                                   const Box *box, int nn, const EFix *ef, const int *escale,
+                                   const MapCoef *maps, unsigned long long *acc_hi,
+                                   unsigned long long *acc_lo, TrackState *st, int32_t *status,
+                                   cudaStream_t s, int part) {
+    if (n <= 0) return cudaSuccess;
+    PartArgs a = part_args(c, n, betagamma, box, nn);
+    a.ef = ef;
+    a.escale = escale;
+    a.acc_hi = acc_hi;
+    a.acc_lo = acc_lo;
+    a.st = st;
+    a.status = status;
+    a.maps = maps;
+    a.dst = st;
+    cudaError_t e = cudaSuccess;
+    if (part & 1) e = launch_pk<MAP_TABLE, true, false, false>(a, s, K_GATHER);
+    if (e != cudaSuccess || !(part & 2)) return e;
+    e = launch_zero_acc(acc_hi, acc_lo, nn, &st->next_gate, s);
+    if (e != cudaSuccess) return e;
+    a.gate = &st->next_gate;
+    return launch_pk<MAP_NONE, false, true, true>(a, s, K_DEPOSIT);
+}
+
+// Device-driven deposit of the current positions when the box rule asks for it.
+cudaError_t launch_track_deposit(double *const c[6], int64_t n, double betagamma, const Box *box,
+                                 int nn, unsigned long long *acc_hi, unsigned long long *acc_lo,
+                                 TrackState *st, int32_t *status, cudaStream_t s) {
+    cudaError_t e = launch_zero_acc(acc_hi, acc_lo, nn, &st->deposit_gate, s);
+    if (e != cudaSuccess || n <= 0) return e;
+    PartArgs a = part_args(c, n, betagamma, box, nn);
+    a.acc_hi = acc_hi;
+    a.acc_lo = acc_lo;
+    a.status = status;
+    a.gate = &st->deposit_gate;
+    a.dst = st;
+    a.flag_outside = 1;
+    return launch_pk<MAP_NONE, false, true, false>(a, s, K_DEPOSIT);
 }
 
 // Charge deposition alone (Listing 1 particle shape 1 = CIC): node weights

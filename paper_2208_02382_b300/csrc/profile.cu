@@ -67,6 +67,8 @@ void prof_end(int id, cudaStream_t s) {
 
 Profiler *profiler_new() { return new Profiler(); }
 
+bool profiler_timing(const Profiler *p) { return p && p->timing; }
+
 void profiler_free(Profiler *p) {
     if (!p) return;
     for (auto &q : p->pending) {

@@ -49,7 +49,14 @@ __global__ void k_sort_keys(const double *__restrict__ x, const double *__restri
                             const double *__restrict__ t, int64_t n, double nbg,
                             const Box *__restrict__ box, int nn, int be, int nbricks,
                             int64_t nchunks, int *__restrict__ keys,
-                            long long *__restrict__ counts) {
+                            long long *__restrict__ counts, const int *gate,
+                            const double *const *ptrs) {
+    if (gate && *gate == 0) return;
+    if (ptrs) {
+        x = ptrs[0];
+        y = ptrs[2];
+        t = ptrs[4];
+    }
     extern __shared__ int hist[];
     for (int i = threadIdx.x; i < nbricks; i += SORT_TPB) hist[i] = 0;
     __syncthreads();
@@ -69,7 +76,8 @@ __global__ void k_sort_keys(const double *__restrict__ x, const double *__restri
 
 // Exclusive scan, three kernels: per-tile sums, scan of the sums, tiles.
 __global__ void k_scan_tiles(const long long *__restrict__ in, long long len,
-                             long long *__restrict__ sums) {
+                             long long *__restrict__ sums, const int *gate) {
+    if (gate && *gate == 0) return;
     __shared__ long long sm[SORT_TPB];
     const long long b0 = (long long)blockIdx.x * SCAN_TILE;
     long long s = 0;
@@ -84,7 +92,8 @@ __global__ void k_scan_tiles(const long long *__restrict__ in, long long len,
     if (threadIdx.x == 0) sums[blockIdx.x] = sm[0];
 }
 
-__global__ void k_scan_sums(long long *sums, long long nt) {
+__global__ void k_scan_sums(long long *sums, long long nt, const int *gate) {
+    if (gate && *gate == 0) return;
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         long long run = 0;
         for (long long i = 0; i < nt; ++i) {
@@ -96,7 +105,9 @@ __global__ void k_scan_sums(long long *sums, long long nt) {
 }
 
 __global__ void k_scan_apply(const long long *__restrict__ in, long long len,
-                             const long long *__restrict__ sums, long long *__restrict__ out) {
+                             const long long *__restrict__ sums, long long *__restrict__ out,
+                             const int *gate) {
+    if (gate && *gate == 0) return;
     __shared__ long long sm[SORT_TPB];
     constexpr int PER = SCAN_TILE / SORT_TPB;
     const long long b0 = (long long)blockIdx.x * SCAN_TILE + threadIdx.x * PER;
@@ -126,7 +137,9 @@ __global__ void k_sort_scatter(const int *__restrict__ keys, const long long *__
                                int64_t n, int nbricks, int64_t nchunks,
                                const double *const *__restrict__ src,
                                const long long *__restrict__ id_src,
-                               double *const *__restrict__ dst, long long *__restrict__ id_dst) {
+                               double *const *__restrict__ dst, long long *__restrict__ id_dst,
+                               const int *gate) {
+    if (gate && *gate == 0) return;
     extern __shared__ int running[];
     for (int i = threadIdx.x; i < nbricks; i += SORT_TPB) running[i] = 0;
     __shared__ int s_base[SORT_TPB];
@@ -159,42 +172,57 @@ __global__ void k_sort_scatter(const int *__restrict__ keys, const long long *__
     }
 }
 
-struct SortScratch;  // owned by the context (api.cu)
+// Copy the sorted scratch arrays back over the caller's arrays.
+__global__ void k_sort_copy_back(double *const *__restrict__ ptrs, const long long *__restrict__ ids,
+                                 long long *__restrict__ id_dst, int64_t n, const int *gate) {
+    if (gate && *gate == 0) return;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) ptrs[c][p] = ptrs[6 + c][p];
+        id_dst[p] = ids[p];
+    }
+}
 
-cudaError_t launch_sort(double *const c[6], long long *id, int64_t n, double betagamma,
-                        const Box *box, int nn, int *keys, long long *counts, long long *offs,
-                        long long *sums, double *const scratch[6], long long *id_scratch,
-                        double **dev_ptrs, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    const int be = sort_brick_edge(nn), nb = sort_bricks(nn);
-    const int64_t nch = sort_chunks(n);
-    const size_t hsm = (size_t)nb * sizeof(int);
-    cudaFuncSetAttribute(k_sort_keys, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
-    cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
-    BT_LAUNCH(K_SORT, s, k_sort_keys<<<(unsigned)nch, SORT_TPB, hsm, s>>>(
-                             c[0], c[2], c[4], n, -betagamma, box, nn, be, nb, nch, keys, counts));
-    const long long len = (long long)nb * nch;
-    const long long nt = (len + SCAN_TILE - 1) / SCAN_TILE;
-    BT_LAUNCH(K_SORT, s, k_scan_tiles<<<(unsigned)nt, SORT_TPB, 0, s>>>(counts, len, sums));
-    BT_LAUNCH(K_SORT, s, k_scan_sums<<<1, 32, 0, s>>>(sums, nt));
-    BT_LAUNCH(K_SORT, s, k_scan_apply<<<(unsigned)nt, SORT_TPB, 0, s>>>(counts, len, sums, offs));
-    // device arrays of the 6+6 coordinate pointers
+// dev_ptrs (device, 12 pointers) must hold the six coordinate arrays then the
+// six scratch arrays (sort_set_pointers).  With `gate`, every kernel returns
+// at once unless *gate is set.
+cudaError_t sort_set_pointers(double *const c[6], double *const scratch[6], double **dev_ptrs,
+                              cudaStream_t s) {
     double *h[12];
     for (int k = 0; k < 6; ++k) {
         h[k] = c[k];
         h[6 + k] = scratch[k];
     }
-    cudaError_t e = cudaMemcpyAsync(dev_ptrs, h, sizeof(h), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(dev_ptrs, h, sizeof(h), cudaMemcpyHostToDevice, s);
+}
+
+cudaError_t launch_sort(double *const c[6], long long *id, int64_t n, double betagamma,
+                        const Box *box, int nn, int *keys, long long *counts, long long *offs,
+                        long long *sums, double *const scratch[6], long long *id_scratch,
+                        double **dev_ptrs, cudaStream_t s, const int *gate) {
+    if (n <= 0) return cudaSuccess;
+    (void)c;
+    (void)scratch;
+    const int be = sort_brick_edge(nn), nb = sort_bricks(nn);
+    const int64_t nch = sort_chunks(n);
+    const size_t hsm = (size_t)nb * sizeof(int);
+    cudaFuncSetAttribute(k_sort_keys, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+    cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
+    const double *const *dp = (const double *const *)dev_ptrs;
+    BT_LAUNCH(K_SORT, s, k_sort_keys<<<(unsigned)nch, SORT_TPB, hsm, s>>>(
+                             nullptr, nullptr, nullptr, n, -betagamma, box, nn, be, nb, nch, keys,
+                             counts, gate, dp));
+    const long long len = (long long)nb * nch;
+    const long long nt = (len + SCAN_TILE - 1) / SCAN_TILE;
+    BT_LAUNCH(K_SORT, s, k_scan_tiles<<<(unsigned)nt, SORT_TPB, 0, s>>>(counts, len, sums, gate));
+    BT_LAUNCH(K_SORT, s, k_scan_sums<<<1, 32, 0, s>>>(sums, nt, gate));
+    BT_LAUNCH(K_SORT, s, k_scan_apply<<<(unsigned)nt, SORT_TPB, 0, s>>>(counts, len, sums, offs, gate));
     BT_LAUNCH(K_SORT, s, k_sort_scatter<<<(unsigned)nch, SORT_TPB, hsm, s>>>(
-                             keys, offs, n, nb, nch, (const double *const *)dev_ptrs, id,
-                             (double *const *)(dev_ptrs + 6), id_scratch));
-    for (int k = 0; k < 6; ++k) {
-        e = cudaMemcpyAsync(c[k], scratch[k], n * sizeof(double), cudaMemcpyDeviceToDevice, s);
-        if (e != cudaSuccess) return e;
-    }
-    e = cudaMemcpyAsync(id, id_scratch, n * sizeof(long long), cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return e;
+                             keys, offs, n, nb, nch, dp, id, (double *const *)(dev_ptrs + 6),
+                             id_scratch, gate));
+    const int cb = (int)((n + 255) / 256) < 148 * 16 ? (int)((n + 255) / 256) : 148 * 16;
+    BT_LAUNCH(K_SORT, s, k_sort_copy_back<<<cb, 256, 0, s>>>(dev_ptrs, id_scratch, id, n, gate));
     return cudaGetLastError();
 }
 

@@ -250,3 +250,25 @@ def test_track_medium_workload_first_kicks(bt):
                                       nk=6)
     assert trk.regrid_log() == otr.regrid_log
     assert coord_rel_err(got, want) <= REL_TOL
+
+
+def test_graph_and_plain_launch_paths_agree_bitwise(bt):
+    """bx_track replays one CUDA graph per kick (conditional nodes for the
+    Green's function rebuild, re-binning and re-deposit); with kernel timing
+    on it launches the same kernels one by one.  Both give identical bits."""
+    w = bg.workload("fodo_1e4_32")
+    c = w.particles(6_000)
+    outs = []
+    for timing in (False, True):
+        beam = gpu_beam(bt, c, w.species, w.bunch_charge_C)
+        trk = bt.Tracker(16)
+        if timing:
+            trk.profile(True)
+        trk.track(beam, w.lattice, 0, 45)
+        trk.track(beam, w.lattice, 45, 20)
+        trk.sync()
+        torch.cuda.synchronize()
+        outs.append((beam.coords.cpu().numpy(), beam.ids.cpu().numpy(), trk.regrid_log()))
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][2] == outs[1][2] and len(outs[0][2]) > 3
