@@ -31,9 +31,9 @@ __device__ dd ln_u_plus_r(dd u, dd r, dd rest2) {
 __device__ dd igf_antiderivative(dd x, dd y, dd z) {
     dd x2 = dd_mul(x, x), y2 = dd_mul(y, y), z2 = dd_mul(z, z);
     dd r = dd_sqrt(dd_add(dd_add(x2, y2), z2));
-    dd a1 = dd_atan(dd_div(dd_mul(x, y), dd_mul(z, r)));
-    dd a2 = dd_atan(dd_div(dd_mul(x, z), dd_mul(y, r)));
-    dd a3 = dd_atan(dd_div(dd_mul(y, z), dd_mul(x, r)));
+    dd a1 = dd_atan_ratio(dd_mul(x, y), dd_mul(z, r));
+    dd a2 = dd_atan_ratio(dd_mul(x, z), dd_mul(y, r));
+    dd a3 = dd_atan_ratio(dd_mul(y, z), dd_mul(x, r));
     dd lx = ln_u_plus_r(x, r, dd_add(y2, z2));
     dd ly = ln_u_plus_r(y, r, dd_add(x2, z2));
     dd lz = ln_u_plus_r(z, r, dd_add(x2, y2));
