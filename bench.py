@@ -364,7 +364,7 @@ def run_ours(args, w):
         trk2.close()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, sample_particles=2_000_000)
+        cpu = cpu_baseline(w, sample_particles=2_000_000, kicks_timed=5)
     if rank == 0:
         clocks = clk.summary()
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
