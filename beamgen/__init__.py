@@ -65,6 +65,42 @@ def fodo_lattice(periods, nslice, kf=1.0, kd=-1.0):
     return fodo_cell(nslice, kf, kd) * int(periods)
 
 
+def fodo8_lattice(ks, periods=5, nslice=2):
+    """Super-period of four Listing-1 FODO cells whose eight quadrupoles each
+    have their own strength, ks = (QF1, QD1, QF2, QD2, QF3, QD3, QF4, QD4),
+    repeated `periods` times (5 periods = 20 cells)."""
+    ks = [float(v) for v in ks]
+    if len(ks) != 8:
+        raise ValueError("eight quadrupole strengths")
+    sp = []
+    for c in range(4):
+        sp += fodo_cell(nslice, ks[2 * c], ks[2 * c + 1])
+    return sp * int(periods)
+
+
+def fodo8_families(lattice: Sequence[Element]) -> np.ndarray:
+    """Index (0..7) of the quadrupole strength of each element of a
+    fodo8_lattice, -1 for drifts."""
+    fam = np.full(len(lattice), -1, dtype=np.int64)
+    for i, e in enumerate(lattice):
+        if e.kind == QUAD:
+            cell, pos = (i % 20) // 5, i % 5
+            fam[i] = 2 * cell + (0 if pos == 1 else 1)
+    return fam
+
+
+KS_FODO8 = (1.0, -1.0, 1.0, -1.0, 1.0, -1.0, 1.0, -1.0)
+# Matched Courant-Snyder parameters of the Listing-1 FODO cell at its start
+# (phase advance 67.8 deg, beta 2.8216 m, alpha -+1.5905), eps for ~1 mm rms,
+# then sigma_t, sigma_pt: (alpha_x, beta_x, eps_x, alpha_y, beta_y, eps_y, st, spt).
+TWISS_FODO = (-1.5905004, 2.8216194, 3.5e-7, 1.5905004, 2.8216194, 3.5e-7, 1e-3, 1e-4)
+
+
+def standard_normal6(n: int, seed: int = 0) -> np.ndarray:
+    """(6, n) independent standard normal draws (the xi of a Twiss bunch)."""
+    return np.ascontiguousarray(_rng(seed).standard_normal((6, int(n))))
+
+
 def chicane_lattice(nslice=50):
     """Four sector bends (L=0.5 m, +-0.1 rad) separated by 1 m drifts, preceded
     by two matching quadrupoles (L=0.5 m, k=+-0.5 /m^2)."""
@@ -178,6 +214,8 @@ def workload(name: str) -> Workload:
                    (1000), 64^3, 10 nC
     chicane_25e6_128 : 2.5e7 particles, 500 MeV e-, quads + 4-bend chicane,
                    50 kicks/element (500), 128^3
+    fodo8_grad_1e6_64 : 1e6 particles (Twiss bunch), 1 GeV p, 8-strength FODO
+                   super-period x5 (20 cells), 2 kicks/element (200), 64^3, 10 nC
     """
     if name == "fodo_1e4_32":
         return Workload(name, 10_000, PROTON_2GEV, 1e-9, fodo_lattice(10, 5), 32)
@@ -186,4 +224,6 @@ def workload(name: str) -> Workload:
                         halo=True)
     if name == "chicane_25e6_128":
         return Workload(name, 25_000_000, ELECTRON_500MEV, 1e-9, chicane_lattice(50), 128)
+    if name == "fodo8_grad_1e6_64":
+        return Workload(name, 1_000_000, PROTON_1GEV, 10e-9, fodo8_lattice(KS_FODO8, 5, 2), 64)
     raise KeyError(name)

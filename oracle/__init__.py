@@ -21,6 +21,8 @@ Modules:
                Hockney doubled-grid solve, field, gather + kick
   igf_quad.c   the integrated Green's function antiderivative in __float128
   track        the split-operator tracking loop and beam moments
+  adjoint      reverse-mode gradients of final rms sizes / emittances with
+               respect to quadrupole strengths and initial Twiss parameters
 
 Parity pins (closed forms, invariants, the paper's worked example, brute force)
 are in tests/test_oracle_*.py.  Functions without such a pin say "parity
