@@ -229,6 +229,68 @@ const char *bx_kernel_name(int32_t id);
 int32_t bx_deposit_noalloc(const bx_beam *beam, const double lo[3], const double hi[3],
                            int32_t n, double *rho, void *stream);
 
+/* ---- Differentiation (reverse mode) ------------------------------------
+ * The paper motivates coupling the code to machine-learning workflows
+ * (Introduction, Outlook) but gives no adjoint.  These calls give the
+ * gradient of L = w[0] eps_x + w[1] eps_y + w[2] sigma_x + w[3] sigma_y of
+ * the bunch after a whole lattice (eps = unnormalised rms emittance
+ * sqrt(<du^2><dpu^2> - <du dpu>^2), sigma = rms size) with respect to every
+ * element's quadrupole strength k and to the initial coordinates, by a
+ * hand-written reverse of each kernel (map transpose, scatter of the kick
+ * adjoint, the transposed field stencil, the same Green's convolution, the
+ * deposit's weight derivative) with step checkpointing and recomputation.
+ * Reading: the grid box is piecewise constant in the coordinates (it changes
+ * only at a regrid) and is held fixed: the gradient is the exact derivative
+ * of tracking with the run's box sequence replayed (box_replay below). */
+
+/* Twiss-parametrised bunch (Courant-Snyder): for each transverse plane
+ * u = sqrt(eps*beta)*xi_u, pu = sqrt(eps/beta)*(xi_pu - alpha*xi_u);
+ * t = sigma_t*xi_t, pt = sigma_pt*xi_pt.  twiss (host) = {alpha_x, beta_x,
+ * eps_x, alpha_y, beta_y, eps_y, sigma_t, sigma_pt}; xi: six device arrays of
+ * n standard-normal draws (x, px, y, py, t, pt order); out: six device arrays
+ * of n doubles (may be the beam's).  BX_BAD_ARG for beta <= 0, eps < 0 or
+ * non-finite parameters; errors via bx_last_error(NULL).  Asynchronous. */
+int32_t bx_twiss_beam(const double twiss[8], const double *const xi[6], int64_t n,
+                      double *const out[6], void *stream);
+
+/* dL/d(alpha_x, beta_x, eps_x, alpha_y, beta_y, eps_y) (out, host) from
+ * S[i*6 + j] = sum_p dL/dz0_i * z0_j (bx_grad_backward's S_out) by the chain
+ * rule through bx_twiss_beam: du/dbeta = u/(2 beta), dpu/dbeta = -pu/(2 beta),
+ * du/deps = u/(2 eps), dpu/deps = pu/(2 eps), dpu/dalpha = -u/beta. */
+int32_t bx_twiss_grad(const double twiss[8], const double S[36], double out[6]);
+
+/* Forward pass for differentiation: tracks the beam through the whole
+ * lattice (all kicks, from a fresh state: no box, kick counter 0; space
+ * charge as lattice->space_charge says), like bx_track but without particle
+ * re-binning, and records in the context: the initial bunch, a checkpoint
+ * (state and device tracking state) every `checkpoint_interval` kicks, the box
+ * of every kick and every Green's function spectrum built.  box_replay (host,
+ * may be NULL): 12 doubles per kick {lo[3], hi[3], h[3], 1/h[3]} as returned by
+ * bx_grad_boxes; the box of each kick is then taken from it instead of the
+ * box rule.  The beam arrays hold the final bunch afterwards.  Device memory
+ * of the recording: about (ceil(K/C) + C + 3) * 48 bytes per particle plus
+ * C * 32 * n^3 + (K + 1) * 8 * (n+1)^3 bytes (K kicks, C = checkpoint_interval,
+ * n = n_grid); allocated on the first call for a given size.  Asynchronous
+ * except the allocation; BX_BAD_ARG for an empty beam or lattice. */
+int32_t bx_grad_forward(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lattice,
+                        int32_t checkpoint_interval, const double *box_replay, void *stream);
+
+/* Reverse pass after bx_grad_forward on the same beam (its final bunch):
+ * weights (host, 4) as for L above.  dk_out (host, lattice count, may be
+ * NULL) receives dL/dk per element (0 for non-quadrupoles, summed over the
+ * element's slices); S_out (host, 36, may be NULL) receives
+ * S[i*6 + j] = sum_p dL/dz0_i * z0_j; zbar0 (six device arrays of n, may be
+ * NULL) receives dL/dz0 in the beam's particle order.  Recomputes each
+ * checkpoint segment from its checkpoint, then runs the reverse kernels of
+ * its kicks in reverse order.  Synchronous (waits for the stream); the
+ * recording is consumed.  Results are bitwise reproducible. */
+int32_t bx_grad_backward(bx_ctx *ctx, const bx_beam *beam, const double weights[4],
+                         double *dk_out, double *S_out, double *const zbar0[6], void *stream);
+
+/* Boxes of the last bx_grad_forward: up to `cap` kicks of 12 doubles
+ * {lo[3], hi[3], h[3], 1/h[3]} into out (host); *count = kicks.  Synchronous. */
+int32_t bx_grad_boxes(bx_ctx *ctx, double *out, int64_t cap, int64_t *count);
+
 /* Wait for the stream and return the device status word (then clear it). */
 int32_t bx_sync(bx_ctx *ctx, void *stream);
 

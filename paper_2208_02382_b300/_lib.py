@@ -61,6 +61,15 @@ SIGNATURES = {
     "bx_kernel_name": (c_char_p, [c_int32]),
     "bx_deposit_noalloc": (c_int32, [POINTER(bx_beam), POINTER(c_double), POINTER(c_double),
                                      c_int32, c_void_p, c_void_p]),
+    "bx_twiss_beam": (c_int32, [POINTER(c_double), POINTER(c_void_p), c_int64, POINTER(c_void_p),
+                                c_void_p]),
+    "bx_twiss_grad": (c_int32, [POINTER(c_double), POINTER(c_double), POINTER(c_double)]),
+    "bx_grad_forward": (c_int32, [c_void_p, POINTER(bx_beam), POINTER(bx_lattice), c_int32,
+                                  POINTER(c_double), c_void_p]),
+    "bx_grad_backward": (c_int32, [c_void_p, POINTER(bx_beam), POINTER(c_double),
+                                   POINTER(c_double), POINTER(c_double), POINTER(c_void_p),
+                                   c_void_p]),
+    "bx_grad_boxes": (c_int32, [c_void_p, POINTER(c_double), c_int64, POINTER(c_int64)]),
     "bx_last_error": (c_char_p, [c_void_p]),
 }
 

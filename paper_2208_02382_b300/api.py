@@ -30,6 +30,47 @@ class Species:
     charge_sign: float
 
 
+@dataclass(frozen=True)
+class Element:
+    """One lattice element (Listing 1 elements): kind L.BX_DRIFT / BX_QUAD /
+    BX_SBEND, length [m], quadrupole strength k [1/m^2], bend angle [rad],
+    slices (space-charge kicks)."""
+    kind: int
+    length: float
+    k: float
+    angle: float
+    nslice: int
+
+
+def _ptr6(t: torch.Tensor):
+    """Six device pointers of the rows of a contiguous (6, n) float64 tensor."""
+    n = t.shape[1]
+    base = t.data_ptr()
+    return (ctypes.c_void_p * 6)(*[base + 8 * n * k for k in range(6)])
+
+
+def twiss_beam(twiss, xi: torch.Tensor) -> torch.Tensor:
+    """(6, n) bunch from standard-normal draws xi and the Twiss parameters
+    (alpha_x, beta_x, eps_x, alpha_y, beta_y, eps_y, sigma_t, sigma_pt)."""
+    lib = L.load()
+    xi = xi.contiguous()
+    out = torch.empty_like(xi)
+    tw = (ctypes.c_double * 8)(*[float(v) for v in twiss])
+    _check(lib, None, lib.bx_twiss_beam(tw, _ptr6(xi), xi.shape[1], _ptr6(out), _stream()))
+    return out
+
+
+def twiss_grad(twiss, S) -> list:
+    """dL/d(alpha_x, beta_x, eps_x, alpha_y, beta_y, eps_y) from
+    S[i][j] = sum_p dL/dz0_i z0_j."""
+    lib = L.load()
+    tw = (ctypes.c_double * 8)(*[float(v) for v in twiss])
+    ss = (ctypes.c_double * 36)(*[float(v) for v in list(S)])
+    out = (ctypes.c_double * 6)()
+    _check(lib, None, lib.bx_twiss_grad(tw, ss, out))
+    return list(out)
+
+
 class Beam:
     """A bunch on the device: `coords` is a (6, n) float64 CUDA tensor
     (x, px, y, py, t, pt), `ids` an int64 CUDA tensor of length n."""
@@ -208,3 +249,42 @@ class Tracker:
 
     def sync(self):
         _check(self.lib, self.ctx, self.lib.bx_sync(self.ctx, _stream()))
+
+    # ---- differentiation
+    def grad_forward(self, beam: Beam, elements, checkpoint_interval: int = 20,
+                     box_replay=None, space_charge: bool = True):
+        """Track the whole lattice, recording what the reverse pass needs.
+        box_replay: (K, 12) boxes of an earlier run (grad_boxes) or None."""
+        b = beam.c_struct()
+        lat, keep = lattice_struct(elements, space_charge)
+        rp = None
+        if box_replay is not None:
+            flat = [float(v) for row in box_replay for v in row]
+            rp = (ctypes.c_double * len(flat))(*flat)
+        rc = self.lib.bx_grad_forward(self.ctx, ctypes.byref(b), ctypes.byref(lat),
+                                      int(checkpoint_interval), rp, _stream())
+        _check(self.lib, self.ctx, rc)
+        self._grad_nelem = len(elements)
+
+    def grad_backward(self, beam: Beam, weights, want_zbar0: bool = True):
+        """dL/dk per element, S = sum_p dL/dz0 z0^T (36, row-major) and
+        (optionally) dL/dz0 as a (6, n) tensor, for L = weights . (eps_x,
+        eps_y, sigma_x, sigma_y) of the final bunch."""
+        b = beam.c_struct()
+        w = (ctypes.c_double * 4)(*[float(v) for v in weights])
+        ne = getattr(self, "_grad_nelem", 0)
+        dk = (ctypes.c_double * max(1, ne))()
+        S = (ctypes.c_double * 36)()
+        zb = torch.empty_like(beam.coords) if want_zbar0 else None
+        rc = self.lib.bx_grad_backward(self.ctx, ctypes.byref(b), w, dk, S,
+                                       _ptr6(zb) if zb is not None else None, _stream())
+        _check(self.lib, self.ctx, rc)
+        return [dk[i] for i in range(ne)], list(S), zb
+
+    def grad_boxes(self) -> list:
+        cnt = ctypes.c_int64()
+        _check(self.lib, self.ctx, self.lib.bx_grad_boxes(self.ctx, None, 0, ctypes.byref(cnt)))
+        buf = (ctypes.c_double * (12 * max(1, cnt.value)))()
+        _check(self.lib, self.ctx, self.lib.bx_grad_boxes(self.ctx, buf, cnt.value,
+                                                          ctypes.byref(cnt)))
+        return [[buf[12 * i + j] for j in range(12)] for i in range(cnt.value)]

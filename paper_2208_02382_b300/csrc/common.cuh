@@ -65,6 +65,12 @@ struct TrackState {
     int32_t halt;           // non-finite box: skip the space-charge work
     double q_macro;         // macroparticle charge [C]
     double rho_scale;       // q_macro / (hx hy hz)
+    // Differentiation runs (null otherwise; indexed by the kick counter):
+    Box *box_hist;          // the box of every kick is recorded here
+    const Box *box_replay;  // the box of every kick is taken from here
+    int32_t *slot_hist;     // index of the Green's function build in use
+    int32_t green_builds;   // Green's function builds so far
+    int32_t pad2;
 };
 
 // Order-preserving map between doubles and signed 64-bit keys (monotone for
@@ -94,7 +100,7 @@ constexpr int DEP_SPLIT = 31;
 enum KernelId : int {
     K_PUSH, K_MINMAX, K_BOX, K_IGF_CORNER, K_IGF_SUM, K_DEPOSIT, K_ACC_TO_RHO, K_FFT_X,
     K_FFT_YZ, K_FFT_ZSOLVE, K_FFT_XINV, K_GREEN_X, K_GREEN_YZ, K_FIELD, K_GATHER, K_MOMENTS,
-    K_TWIDDLE, K_EFIX, K_SORT, K_COUNT
+    K_TWIDDLE, K_EFIX, K_SORT, K_ADJ_PART, K_ADJ_GRID, K_COUNT
 };
 
 struct Profiler;
@@ -161,6 +167,11 @@ cudaError_t launch_box_rule_graph(TrackState *st, int nn, long long *log, int64_
                                   cudaGraphConditionalHandle hg, cudaGraphConditionalHandle hs,
                                   cudaGraphConditionalHandle hd, cudaGraphConditionalHandle hn,
                                   cudaStream_t s);
+cudaError_t launch_track_particles_oop(double *const cin[6], double *const cout[6], int64_t n,
+                                       double betagamma, const Box *box, int nn, const EFix *ef,
+                                       const int *escale, const MapCoef *maps,
+                                       unsigned long long *acc_hi, unsigned long long *acc_lo,
+                                       TrackState *st, int32_t *status, cudaStream_t s);
 cudaError_t launch_track_deposit(double *const c[6], int64_t n, double betagamma, const Box *box,
                                  int nn, unsigned long long *acc_hi, unsigned long long *acc_lo,
                                  TrackState *st, int32_t *status, cudaStream_t s);
@@ -196,6 +207,49 @@ cudaError_t solve_acc_to_phi(const FftPlan *p, const unsigned long long *acc_hi,
                              cudaStream_t s, const double *scale_dev = nullptr);
 cudaError_t green_spectrum_from_table(const FftPlan *p, const double *gtable, cudaStream_t s,
                                       const int *gate = nullptr);
+cudaError_t solve_adjoint_shifted(const FftPlan *p, const double *phibar, double *out,
+                                  cudaStream_t s);
+// adjoint.cu
+struct P6 {
+    double *p[6];
+};
+// One reverse kick (see adjoint.cu): P = state before the kick, A = adjoint
+// (in place), the kick's field/box/map, scatter and grid scratch.
+struct AdjKick {
+    P6 P, A;
+    const EFix *ef;
+    const int *escale;
+    const Box *box;
+    const MapCoef *map;             // table entry 1 + k
+    double betagamma, q_macro;
+    int nn;
+    int64_t n;
+    long long kick;                 // kick index (for the Green's function slot)
+    const unsigned long long *amax_in;
+    unsigned long long *amax_out;
+    long long *kbar;                // 3 nn^3
+    int *sexp;                      // 3
+    double *part;                   // adj_blocks(n) * 13
+    double *mbar;                   // 13 (out)
+    double *phibar, *rb;            // (nn+2)^3 each
+    const FftPlan *plan;
+    const int32_t *slot_hist;
+    const double *ghat_store;
+    long long ghat_count;
+    int ghat_cap;
+};
+int adj_blocks(int64_t n);
+cudaError_t launch_adj_seed(P6 c, int64_t n, const double *mom, const double w[4], P6 A,
+                            unsigned long long *amax, cudaStream_t s);
+cudaError_t launch_adj_kick(const AdjKick &k, cudaStream_t s);
+cudaError_t launch_adj_initial(P6 A, P6 z0, int64_t n, const MapCoef *map0, P6 out, double *part,
+                               double *sums, cudaStream_t s);
+cudaError_t launch_ghat_store(const TrackState *st, double *store, double *ghat, long long count,
+                              int cap, int dir, int32_t *status, cudaStream_t s);
+cudaError_t launch_set_deposit_gate(TrackState *st, cudaStream_t s);
+cudaError_t launch_ghat_fetch(const int32_t *slot_hist, long long k, const double *store,
+                              double *ghat, long long count, int cap, cudaStream_t s);
+cudaError_t launch_twiss_beam(P6 xi, int64_t n, const double c[8], P6 out, cudaStream_t s);
 // igf.cu
 cudaError_t launch_igf_table(int n, const double h[3], double *fcorner, double *gtable,
                              cudaStream_t s, const TrackState *gate = nullptr);

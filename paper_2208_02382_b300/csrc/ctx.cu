@@ -1,0 +1,279 @@
+// Host helpers of the C ABI: error text, argument checks, the reference
+// particle, the linear element maps and the per-call map table, and the lazily
+// sized device scratch of the context.
+//
+// Paper anchors (arXiv:2208.02382): Listing 1 (set_energy_MeV, Drift/Quad
+// with nslice, the lattice walked slice by slice) and Model Assumptions
+// (linear symplectic maps, split-operator step).
+#include <cmath>
+#include <cstring>
+
+#include "ctx.cuh"
+
+namespace bt {
+
+thread_local std::string g_create_err;
+
+
+int32_t fail(bx_ctx *c, int32_t code, const std::string &msg) {
+    if (c) c->err = msg;
+    else g_create_err = msg;
+    return code;
+}
+
+int32_t cuda_fail(bx_ctx *c, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? BX_OUT_OF_MEMORY : BX_CUDA, m);
+}
+
+// Reference particle from kinetic energy (Listing 1 set_energy_MeV, read as
+// kinetic): gamma = 1 + W/mc^2, beta gamma = sqrt(gamma^2 - 1).
+Ref make_ref(const bx_beam *b) {
+    Ref r;
+    r.gamma = 1.0 + b->kinetic_MeV / b->mass_MeV;
+    r.bg = std::sqrt(r.gamma * r.gamma - 1.0);
+    r.beta = r.bg / r.gamma;
+    r.mass_eV = b->mass_MeV * 1e6;
+    r.sign = b->charge_sign;
+    return r;
+}
+
+void mat_identity(Mat m) {
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) m[i][j] = i == j ? 1.0 : 0.0;
+}
+
+void focus_block(double ds, double k, double out[2][2]) {
+    if (k > 0.0) {
+        double w = std::sqrt(k), c = std::cos(w * ds), s = std::sin(w * ds);
+        out[0][0] = c; out[0][1] = s / w; out[1][0] = -w * s; out[1][1] = c;
+    } else if (k < 0.0) {
+        double w = std::sqrt(-k), c = std::cosh(w * ds), s = std::sinh(w * ds);
+        out[0][0] = c; out[0][1] = s / w; out[1][0] = w * s; out[1][1] = c;
+    } else {
+        out[0][0] = 1.0; out[0][1] = ds; out[1][0] = 0.0; out[1][1] = 1.0;
+    }
+}
+
+// Linear map of a piece ds of an element (Model Assumptions: linear order).
+// Drift: x += ds px, y += ds py, t += ds/(beta gamma)^2 pt.  Quadrupole: k > 0
+// focuses x.  Sector bend of radius rho = length/angle, theta = ds/rho:
+//   x'  = cos x + rho sin px - rho(1-cos)/beta pt
+//   px' = -sin/rho x + cos px - sin/beta pt
+//   t'  = t + sin/beta x + rho(1-cos)/beta px + rho(sin/beta^2 - theta) pt.
+void element_map(const bx_element &e, double ds, const Ref &r, Mat m) {
+    mat_identity(m);
+    if (e.type == BX_SBEND && e.angle != 0.0) {
+        double rho = e.length / e.angle, th = ds / rho;
+        double c = std::cos(th), s = std::sin(th), b = r.beta;
+        m[0][0] = c; m[0][1] = rho * s; m[0][5] = -rho * (1.0 - c) / b;
+        m[1][0] = -s / rho; m[1][1] = c; m[1][5] = -s / b;
+        m[2][3] = ds;
+        m[4][0] = s / b; m[4][1] = rho * (1.0 - c) / b; m[4][5] = rho * (s / (b * b) - th);
+        return;
+    }
+    m[4][5] = ds / (r.bg * r.bg);
+    if (e.type == BX_QUAD) {
+        double bx[2][2], by[2][2];
+        focus_block(ds, e.k, bx);
+        focus_block(ds, -e.k, by);
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) {
+                m[i][j] = bx[i][j];
+                m[2 + i][2 + j] = by[i][j];
+            }
+    } else {
+        m[0][1] = ds;
+        m[2][3] = ds;
+    }
+}
+
+// out = a * b (apply b first).
+void mat_mul(const Mat a, const Mat b, Mat out) {
+    Mat t;
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 6; ++k) s += a[i][k] * b[k][j];
+            t[i][j] = s;
+        }
+    memcpy(out, t, sizeof(Mat));
+}
+
+MapCoef to_coef(const Mat m) {
+    MapCoef c;
+    memset(&c, 0, sizeof(c));
+    c.m00 = m[0][0]; c.m01 = m[0][1]; c.m05 = m[0][5];
+    c.m10 = m[1][0]; c.m11 = m[1][1]; c.m15 = m[1][5];
+    c.m22 = m[2][2]; c.m23 = m[2][3];
+    c.m32 = m[3][2]; c.m33 = m[3][3];
+    c.m40 = m[4][0]; c.m41 = m[4][1]; c.m45 = m[4][5];
+    return c;
+}
+
+int32_t check_beam(bx_ctx *ctx, const bx_beam *b) {
+    if (!b) return fail(ctx, BX_BAD_ARG, "beam is NULL");
+    if (b->n < 0) return fail(ctx, BX_BAD_ARG, "beam n < 0");
+    if (b->n > 0)
+        for (int k = 0; k < 6; ++k)
+            if (!b->coord[k]) return fail(ctx, BX_BAD_ARG, "beam coordinate pointer is NULL");
+    if (!(b->charge_sign == 1.0 || b->charge_sign == -1.0))
+        return fail(ctx, BX_BAD_ARG, "charge_sign must be +1 or -1");
+    if (!(b->mass_MeV > 0.0) || !std::isfinite(b->mass_MeV))
+        return fail(ctx, BX_BAD_ARG, "mass_MeV must be > 0");
+    if (!(b->kinetic_MeV > 0.0) || !std::isfinite(b->kinetic_MeV))
+        return fail(ctx, BX_BAD_ARG, "kinetic_MeV must be > 0");
+    if (!std::isfinite(b->bunch_charge_C)) return fail(ctx, BX_BAD_ARG, "bunch charge not finite");
+    return BX_OK;
+}
+
+int32_t check_lattice(bx_ctx *ctx, const bx_lattice *l) {
+    if (!l) return fail(ctx, BX_BAD_ARG, "lattice is NULL");
+    if (l->count < 0 || (l->count > 0 && !l->elements))
+        return fail(ctx, BX_BAD_ARG, "lattice elements missing");
+    for (int i = 0; i < l->count; ++i) {
+        const bx_element &e = l->elements[i];
+        if (e.type != BX_DRIFT && e.type != BX_QUAD && e.type != BX_SBEND)
+            return fail(ctx, BX_BAD_ARG, "unknown element type");
+        if (!(e.length > 0.0) || !std::isfinite(e.length))
+            return fail(ctx, BX_BAD_ARG, "element length must be > 0");
+        if (e.nslice <= 0) return fail(ctx, BX_BAD_ARG, "element nslice must be >= 1");
+        if (!std::isfinite(e.k) || !std::isfinite(e.angle))
+            return fail(ctx, BX_BAD_ARG, "element k/angle not finite");
+    }
+    return BX_OK;
+}
+
+int32_t check_grid(bx_ctx *ctx, const bx_grid *g, bool need_rho, bool need_phi) {
+    if (!g) return fail(ctx, BX_BAD_ARG, "grid is NULL");
+    if (g->n != ctx->n) return fail(ctx, BX_BAD_ARG, "grid n differs from the context's n_grid");
+    if (need_rho && !g->rho) return fail(ctx, BX_BAD_ARG, "grid rho is NULL");
+    if (need_phi && !g->phi) return fail(ctx, BX_BAD_ARG, "grid phi is NULL");
+    return BX_OK;
+}
+
+Box explicit_box(const double lo[3], const double hi[3], int n) {
+    Box b;
+    for (int d = 0; d < 3; ++d) {
+        b.lo[d] = lo[d];
+        b.hi[d] = hi[d];
+        b.h[d] = (hi[d] - lo[d]) / (double)(n - 1);
+        b.inv_h[d] = 1.0 / b.h[d];
+    }
+    return b;
+}
+
+int32_t ensure_green(bx_ctx *ctx, const double h[3], cudaStream_t s) {
+    if (ctx->green_valid && ctx->green_h[0] == h[0] && ctx->green_h[1] == h[1] &&
+        ctx->green_h[2] == h[2])
+        return BX_OK;
+    CK(launch_igf_table(ctx->n, h, ctx->fcorner, ctx->gtable, s), "green table");
+    CK(green_spectrum_from_table(&ctx->plan, ctx->gtable, s), "green spectrum");
+    ctx->green_valid = true;
+    memcpy(ctx->green_h, h, sizeof(ctx->green_h));
+    // the tracking loop decides on the device from the state's copy of h
+    CK(cudaMemcpyAsync(ctx->st->green_h, ctx->green_h, sizeof(ctx->green_h),
+                       cudaMemcpyHostToDevice, s),
+       "green h");
+    return BX_OK;
+}
+
+int32_t ensure_maps(bx_ctx *ctx, size_t count) {
+    if (count <= ctx->maps_cap) return BX_OK;
+    if (ctx->maps) cudaFree(ctx->maps);
+    ctx->maps = nullptr;
+    size_t cap = count < 1024 ? 1024 : count;
+    CK(cudaMalloc(&ctx->maps, cap * sizeof(MapCoef)), "map table");
+    ctx->maps_cap = cap;
+    return BX_OK;
+}
+
+// Binning scratch for n particles, allocated on the first call for a larger n.
+int32_t ensure_sort_scratch(bx_ctx *ctx, int64_t n) {
+    if (n <= ctx->sort_n) return BX_OK;
+    cudaDeviceSynchronize();
+    void **ps[] = {(void **)&ctx->keys, (void **)&ctx->counts, (void **)&ctx->offs,
+                   (void **)&ctx->sums, (void **)&ctx->id_scr, (void **)&ctx->scr[0],
+                   (void **)&ctx->scr[1], (void **)&ctx->scr[2], (void **)&ctx->scr[3],
+                   (void **)&ctx->scr[4], (void **)&ctx->scr[5]};
+    for (void **p : ps)
+        if (*p) {
+            cudaFree(*p);
+            *p = nullptr;
+        }
+    ctx->sort_n = 0;
+    const long long len = (long long)sort_bricks(ctx->n) * sort_chunks(n);
+    CK(cudaMalloc(&ctx->keys, n * sizeof(int)), "sort keys");
+    CK(cudaMalloc(&ctx->counts, len * sizeof(long long)), "sort counts");
+    CK(cudaMalloc(&ctx->offs, len * sizeof(long long)), "sort offsets");
+    CK(cudaMalloc(&ctx->sums, (len / 2048 + 2) * sizeof(long long)), "sort sums");
+    CK(cudaMalloc(&ctx->id_scr, n * sizeof(long long)), "sort ids");
+    for (int k = 0; k < 6; ++k) CK(cudaMalloc(&ctx->scr[k], n * sizeof(double)), "sort arrays");
+    ctx->sort_n = n;
+    return BX_OK;
+}
+
+int32_t read_state(bx_ctx *ctx, TrackState *h, cudaStream_t s) {
+    CK(cudaMemcpyAsync(h, ctx->st, sizeof(TrackState), cudaMemcpyDeviceToHost, s), "read state");
+    CK(cudaStreamSynchronize(s), "sync");
+    return BX_OK;
+}
+
+void init_state(TrackState *h) {
+    memset(h, 0, sizeof(*h));
+    for (int d = 0; d < 3; ++d) {
+        h->mm[d] = dkey(INFINITY);
+        h->mm[3 + d] = dkey(-INFINITY);
+    }
+}
+
+
+void slice_schedule(const bx_lattice *lat, std::vector<int> &sel, std::vector<double> &sds) {
+    sel.clear();
+    sds.clear();
+    for (int i = 0; i < lat->count; ++i)
+        for (int k = 0; k < lat->elements[i].nslice; ++k) {
+            sel.push_back(i);
+            sds.push_back(lat->elements[i].length / lat->elements[i].nslice);
+        }
+}
+
+void build_map_table(const bx_lattice *lat, const std::vector<int> &sel,
+                     const std::vector<double> &sds, int64_t first, int64_t nkicks, const Ref &r,
+                     std::vector<MapCoef> &tab) {
+    tab.clear();
+    tab.reserve(nkicks + 1);
+    Mat hk, hn, mm;
+    element_map(lat->elements[sel[first]], 0.5 * sds[first], r, hk);
+    tab.push_back(to_coef(hk));
+    for (int64_t k = first; k < first + nkicks; ++k) {
+        if (k + 1 < first + nkicks) {
+            element_map(lat->elements[sel[k + 1]], 0.5 * sds[k + 1], r, hn);
+            mat_mul(hn, hk, mm);
+            tab.push_back(to_coef(mm));
+            memcpy(hk, hn, sizeof(Mat));
+        } else {
+            tab.push_back(to_coef(hk));
+        }
+    }
+    // kick factors of kick k and the map class, in table entry 1 + k
+    for (int64_t k = 0; k < nkicks; ++k) {
+        const double ds = sds[first + k];
+        tab[1 + k].kick_t = r.sign * ds / (r.mass_eV * (r.bg * r.bg));
+        tab[1 + k].kick_z = -r.sign * ds / (r.mass_eV * r.bg);
+    }
+    for (auto &m : tab) m.kind = (double)map_kind(m);
+}
+
+int32_t ensure_moment_scratch(bx_ctx *ctx, int64_t n) {
+    int nb = moments_blocks(n);
+    if (nb * 21 > ctx->mom_partial_cap) {
+        if (ctx->mom_partial) cudaFree(ctx->mom_partial);
+        ctx->mom_partial = nullptr;
+        CK(cudaMalloc(&ctx->mom_partial, (size_t)nb * 21 * sizeof(double)), "moments scratch");
+        ctx->mom_partial_cap = nb * 21;
+    }
+    return BX_OK;
+}
+
+}  // namespace bt

@@ -233,13 +233,13 @@ struct XIn {
 };
 
 template <int M, int SRC>
-__device__ __forceinline__ double x_value(const XIn &in, int n, int x, int y, int z) {
+__device__ __forceinline__ double x_value(const XIn &in, int n, int nin, int x, int y, int z) {
     if constexpr (SRC == SRC_GREEN) {
         const int a = min(x, M - x), b = min(y, M - y), c = min(z, M - z), q = n + 1;
         return in.g[((long long)c * q + b) * q + a];
     } else {
-        if (x >= n) return 0.0;
-        const long long i = ((long long)z * n + y) * n + x;
+        if (x >= nin) return 0.0;
+        const long long i = ((long long)z * nin + y) * nin + x;
         if constexpr (SRC == SRC_RHO) return in.rho[i];
         return in.scale * (((double)in.acc_hi[i] * 2147483648.0 + (double)in.acc_lo[i]) * 0x1p-51);
     }
@@ -248,7 +248,8 @@ __device__ __forceinline__ double x_value(const XIn &in, int n, int x, int y, in
 // x pass (forward, real to complex).  Rows (y, y+1) of plane z become one
 // complex line a + i b; after the transform A_k = (Z_k + conj Z_{m-k})/2 and
 // B_k = (Z_k - conj Z_{m-k})/(2i), k = 0..n.  ny, nz rows/planes are read
-// (n, n for the padded rho; m, m for the Green's function).
+// (nin, nin for a source cube of nin^3 nodes: n for rho, n+2 for the adjoint
+// source on nodes -1..n; m, m for the Green's function).
 // Output out[(z*ny + y)*P + k].
 template <int M, int SRC>
 __global__ void __launch_bounds__(FFT_TPB) k_fft_x_fwd(XIn in, int n, int ny, int nz,
@@ -257,6 +258,7 @@ __global__ void __launch_bounds__(FFT_TPB) k_fft_x_fwd(XIn in, int n, int ny, in
                                                        const int *gate) {
     if (gate && *gate == 0) return;
     if (SRC == SRC_ACC && in.scale_ptr) in.scale = *in.scale_ptr;
+    const int nin = ny;
     constexpr int T = Shape<M>::T, LPB = FFT_TPB / T, V = M / T;
     extern __shared__ double2 smem[];
     double2 *stw = smem, *sl = smem + M;
@@ -274,8 +276,8 @@ __global__ void __launch_bounds__(FFT_TPB) k_fft_x_fwd(XIn in, int n, int ny, in
 #pragma unroll
         for (int m = 0; m < R0; ++m) {
             const int e = first_index<M>(t, j, m);
-            v[j * R0 + m] = live ? make_double2(x_value<M, SRC>(in, n, e, y, z),
-                                                x_value<M, SRC>(in, n, e, y + 1, z))
+            v[j * R0 + m] = live ? make_double2(x_value<M, SRC>(in, n, nin, e, y, z),
+                                                x_value<M, SRC>(in, n, nin, e, y + 1, z))
                                  : make_double2(0.0, 0.0);
         }
     double2 *s = sl + team * M;
@@ -482,27 +484,31 @@ static inline unsigned blocks_lines(long long lines, int M) {
     return (unsigned)((lines + lpb - 1) / lpb);
 }
 
+// phi (nodes -1..n) = G (*) source, the source a cube of nin^3 nodes at
+// doubled-grid offsets 0..nin-1 (nin = n: rho; nin = n+2: the adjoint source).
 template <int M>
-static cudaError_t solve_m(const FftPlan *p, const XIn &in, int src, double *phi, cudaStream_t s) {
+static cudaError_t solve_m(const FftPlan *p, const XIn &in, int src, int nin, double *phi,
+                           cudaStream_t s) {
     const int n = p->n;
     const long long P = n + 1, q = n + 2;
     const size_t sm = smem_bytes(M);
     double2 *S1 = p->buf, *S2 = p->buf2, *S3 = p->buf, *S4 = p->buf2;
-    // x: rows y, z < n in pairs -> S1[z][y][kx]
-    const long long xpairs = (long long)(n / 2) * n;
+    // x: rows y, z < nin in pairs -> S1[z][y][kx]
+    const long long xpairs = (long long)(nin / 2) * nin;
     if (src == SRC_ACC)
         BT_LAUNCH(K_FFT_X, s, k_fft_x_fwd<M, SRC_ACC><<<blocks_lines(xpairs, M), FFT_TPB, sm, s>>>(
-                                  in, n, n, n, p->tw, S1, nullptr));
+                                  in, n, nin, nin, p->tw, S1, nullptr));
     else
         BT_LAUNCH(K_FFT_X, s, k_fft_x_fwd<M, SRC_RHO><<<blocks_lines(xpairs, M), FFT_TPB, sm, s>>>(
-                                  in, n, n, n, p->tw, S1, nullptr));
-    // y: lines (z < n, kx), inputs y < n -> S2[z][ky][kx], all ky
-    BT_LAUNCH(K_FFT_YZ, s, k_fft_lines<M, MODE_FWD><<<blocks_lines(n * P, M), FFT_TPB, sm, s>>>(
-                               S1, n * P, P, n, S2, M * P, P, M, n, (int)P, nullptr, nullptr, p->tw, nullptr));
-    // z fused: lines (ky < m, kx), inputs z < n -> S3[zz][ky][kx], zz < n+2
+                                  in, n, nin, nin, p->tw, S1, nullptr));
+    // y: lines (z < nin, kx), inputs y < nin -> S2[z][ky][kx], all ky
+    BT_LAUNCH(K_FFT_YZ, s, k_fft_lines<M, MODE_FWD><<<blocks_lines(nin * P, M), FFT_TPB, sm, s>>>(
+                               S1, nin * P, P, nin, S2, M * P, P, M, nin, (int)P, nullptr, nullptr,
+                               p->tw, nullptr));
+    // z fused: lines (ky < m, kx), inputs z < nin -> S3[zz][ky][kx], zz < n+2
     BT_LAUNCH(K_FFT_ZSOLVE, s,
               k_fft_lines<M, MODE_ZSOLVE><<<blocks_lines((long long)M * P, M), FFT_TPB, sm, s>>>(
-                  S2, P, (long long)M * P, n, S3, P, (long long)M * P, (int)q, M, (int)P, p->ghat,
+                  S2, P, (long long)M * P, nin, S3, P, (long long)M * P, (int)q, M, (int)P, p->ghat,
                   nullptr, p->tw, nullptr));
     // inverse y: lines (zz < n+2, kx), all ky -> S4[zz][yy][kx]
     BT_LAUNCH(K_FFT_YZ, s, k_fft_lines<M, MODE_INV><<<blocks_lines(q * P, M), FFT_TPB, sm, s>>>(
@@ -537,14 +543,15 @@ static cudaError_t green_m(const FftPlan *p, const double *gtable, cudaStream_t 
     return cudaGetLastError();
 }
 
-static cudaError_t solve_any(const FftPlan *p, const XIn &in, int src, double *phi, cudaStream_t s) {
+static cudaError_t solve_any(const FftPlan *p, const XIn &in, int src, int nin, double *phi,
+                             cudaStream_t s) {
     switch (p->m) {
-        case 16: return solve_m<16>(p, in, src, phi, s);
-        case 32: return solve_m<32>(p, in, src, phi, s);
-        case 64: return solve_m<64>(p, in, src, phi, s);
-        case 128: return solve_m<128>(p, in, src, phi, s);
-        case 256: return solve_m<256>(p, in, src, phi, s);
-        case 512: return solve_m<512>(p, in, src, phi, s);
+        case 16: return solve_m<16>(p, in, src, nin, phi, s);
+        case 32: return solve_m<32>(p, in, src, nin, phi, s);
+        case 64: return solve_m<64>(p, in, src, nin, phi, s);
+        case 128: return solve_m<128>(p, in, src, nin, phi, s);
+        case 256: return solve_m<256>(p, in, src, nin, phi, s);
+        case 512: return solve_m<512>(p, in, src, nin, phi, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -552,7 +559,18 @@ static cudaError_t solve_any(const FftPlan *p, const XIn &in, int src, double *p
 cudaError_t solve_rho_to_phi(const FftPlan *p, const double *rho, double *phi, cudaStream_t s) {
     XIn in{};
     in.rho = rho;
-    return solve_any(p, in, SRC_RHO, phi, s);
+    return solve_any(p, in, SRC_RHO, p->n, phi, s);
+}
+
+// Transpose of the solve (G even, its circulant symmetric): the source
+// phibar on nodes -1..n ((n+2)^3, index node + 1) placed at doubled-grid
+// offsets 0..n+1 (a shift by one node), convolved with G; the result for
+// node j = 0..n-1 is out[j + 2] in each dimension of the (n+2)^3 output.
+cudaError_t solve_adjoint_shifted(const FftPlan *p, const double *phibar, double *out,
+                                  cudaStream_t s) {
+    XIn in{};
+    in.rho = phibar;
+    return solve_any(p, in, SRC_RHO, p->n + 2, out, s);
 }
 
 cudaError_t solve_acc_to_phi(const FftPlan *p, const unsigned long long *acc_hi,
@@ -563,7 +581,7 @@ cudaError_t solve_acc_to_phi(const FftPlan *p, const unsigned long long *acc_hi,
     in.acc_lo = acc_lo;
     in.scale = scale;
     in.scale_ptr = scale_dev;
-    return solve_any(p, in, SRC_ACC, phi, s);
+    return solve_any(p, in, SRC_ACC, p->n, phi, s);
 }
 
 cudaError_t green_spectrum_from_table(const FftPlan *p, const double *gtable, cudaStream_t s,

@@ -1,0 +1,90 @@
+// Per-particle arithmetic shared by the forward particle kernels and their
+// adjoints, so that both see bit-identical cells, fractions and maps.
+#pragma once
+
+#include "common.cuh"
+#include "fixed.cuh"
+
+namespace bt {
+
+// Map structure classes (see MapCoef): drift (x += m01 px, y += m23 py,
+// t += m45 pt), no dispersion (2x2 blocks and the t-pt term), general.
+enum MapKind { MAP_NONE = 0, MAP_DRIFT = 1, MAP_QUAD = 2, MAP_GENERAL = 3, MAP_TABLE = 4 };
+
+template <int MK>
+__device__ __forceinline__ void apply_map_k(const MapCoef &m, double &x, double &px, double &y,
+                                            double &py, double &t, double pt) {
+    if constexpr (MK == MAP_DRIFT) {
+        x = fma(m.m01, px, x);
+        y = fma(m.m23, py, y);
+        t = fma(m.m45, pt, t);
+    } else if constexpr (MK == MAP_QUAD) {
+        double nx = m.m00 * x + m.m01 * px;
+        double npx = m.m10 * x + m.m11 * px;
+        double ny = m.m22 * y + m.m23 * py;
+        double npy = m.m32 * y + m.m33 * py;
+        t = fma(m.m45, pt, t);
+        x = nx;
+        px = npx;
+        y = ny;
+        py = npy;
+    } else if constexpr (MK == MAP_GENERAL) {
+        double nx = m.m00 * x + m.m01 * px + m.m05 * pt;
+        double npx = m.m10 * x + m.m11 * px + m.m15 * pt;
+        double ny = m.m22 * y + m.m23 * py;
+        double npy = m.m32 * y + m.m33 * py;
+        double nt = t + m.m40 * x + m.m41 * px + m.m45 * pt;
+        x = nx;
+        px = npx;
+        y = ny;
+        py = npy;
+        t = nt;
+    }
+}
+
+// MAP_TABLE: the map (and its class in `kind`) comes from the per-call
+// device table; the class branch is uniform across the grid.
+__device__ __forceinline__ void apply_map_table(const MapCoef &m, double &x, double &px, double &y,
+                                                double &py, double &t, double pt) {
+    const int k = (int)m.kind;
+    if (k == MAP_DRIFT) apply_map_k<MAP_DRIFT>(m, x, px, y, py, t, pt);
+    else if (k == MAP_QUAD) apply_map_k<MAP_QUAD>(m, x, px, y, py, t, pt);
+    else apply_map_k<MAP_GENERAL>(m, x, px, y, py, t, pt);
+}
+
+// All six finite: the largest exponent field (from the 32-bit high words,
+// combined with integer max so the test stays on the integer pipes) is below
+// the all-ones exponent of Inf/NaN.
+__device__ __forceinline__ bool finite6(double a, double b, double c, double d, double e, double f) {
+    const unsigned m = 0x7FF00000u;
+    const unsigned hm = max(max(max((unsigned)__double2hiint(a) & m, (unsigned)__double2hiint(b) & m),
+                                max((unsigned)__double2hiint(c) & m, (unsigned)__double2hiint(d) & m)),
+                            max((unsigned)__double2hiint(e) & m, (unsigned)__double2hiint(f) & m));
+    return hm != m;
+}
+
+// A box far from the origin relative to its cell size needs the unfused u.
+__host__ __device__ __forceinline__ bool box_far_offset(const Box &b) {
+    for (int d = 0; d < 3; ++d)
+        if (fabs(b.lo[d] * b.inv_h[d]) > 4096.0 || fabs(b.hi[d] * b.inv_h[d]) > 4096.0) return true;
+    return false;
+}
+
+// Cell index and 52-bit fraction per dimension from u, with integer
+// operations only.  u below -1e-9 or above n-1+1e-6 (beyond the rounding of
+// u for a particle inside [lo, hi)) sets `outside`.
+constexpr unsigned long long NEG_TOL_BITS = 0x3E112E0BE826D695ull;  // bits of 1e-9
+__device__ __forceinline__ void cell_frac(double u, int nn, int &cell, unsigned long long &F,
+                                          bool &outside) {
+    const unsigned long long umax = (unsigned long long)(nn - 1) << 52;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(u);
+    unsigned long long U = to_fixed52(u);
+    outside |= ((b >> 63) && abs_bits(u) > NEG_TOL_BITS) || U > umax + 4503599627ull;
+    if (U > umax) U = umax;
+    unsigned long long i = U >> 52;
+    if (i > (unsigned long long)(nn - 2)) i = nn - 2;
+    F = U - (i << 52);
+    cell = (int)i;
+}
+
+}  // namespace bt

@@ -13,6 +13,7 @@
 // run in 64-bit fixed point on the integer pipes.
 #include "common.cuh"
 #include "fixed.cuh"
+#include "particle_math.cuh"
 
 namespace bt {
 
@@ -24,50 +25,6 @@ static inline int grid_for(int64_t n) {
     return (int)(b < 1 ? 1 : b);
 }
 
-// Map structure classes (see MapCoef): drift (x += m01 px, y += m23 py,
-// t += m45 pt), no dispersion (2x2 blocks and the t-pt term), general.
-enum MapKind { MAP_NONE = 0, MAP_DRIFT = 1, MAP_QUAD = 2, MAP_GENERAL = 3, MAP_TABLE = 4 };
-
-template <int MK>
-__device__ __forceinline__ void apply_map_k(const MapCoef &m, double &x, double &px, double &y,
-                                            double &py, double &t, double pt) {
-    if constexpr (MK == MAP_DRIFT) {
-        x = fma(m.m01, px, x);
-        y = fma(m.m23, py, y);
-        t = fma(m.m45, pt, t);
-    } else if constexpr (MK == MAP_QUAD) {
-        double nx = m.m00 * x + m.m01 * px;
-        double npx = m.m10 * x + m.m11 * px;
-        double ny = m.m22 * y + m.m23 * py;
-        double npy = m.m32 * y + m.m33 * py;
-        t = fma(m.m45, pt, t);
-        x = nx;
-        px = npx;
-        y = ny;
-        py = npy;
-    } else if constexpr (MK == MAP_GENERAL) {
-        double nx = m.m00 * x + m.m01 * px + m.m05 * pt;
-        double npx = m.m10 * x + m.m11 * px + m.m15 * pt;
-        double ny = m.m22 * y + m.m23 * py;
-        double npy = m.m32 * y + m.m33 * py;
-        double nt = t + m.m40 * x + m.m41 * px + m.m45 * pt;
-        x = nx;
-        px = npx;
-        y = ny;
-        py = npy;
-        t = nt;
-    }
-}
-
-// MAP_TABLE: the map (and its class in `kind`) comes from the per-call
-// device table; the class branch is uniform across the grid.
-__device__ __forceinline__ void apply_map_table(const MapCoef &m, double &x, double &px, double &y,
-                                                double &py, double &t, double pt) {
-    const int k = (int)m.kind;
-    if (k == MAP_DRIFT) apply_map_k<MAP_DRIFT>(m, x, px, y, py, t, pt);
-    else if (k == MAP_QUAD) apply_map_k<MAP_QUAD>(m, x, px, y, py, t, pt);
-    else apply_map_k<MAP_GENERAL>(m, x, px, y, py, t, pt);
-}
 
 int map_kind(const MapCoef &m) {
     if (m.m05 == 0.0 && m.m15 == 0.0 && m.m40 == 0.0 && m.m41 == 0.0) {
@@ -140,16 +97,6 @@ __device__ __forceinline__ void block_keys_commit(long long lo[3], long long hi[
     }
 }
 
-// All six finite: the largest exponent field (from the 32-bit high words,
-// combined with integer max so the test stays on the integer pipes) is below
-// the all-ones exponent of Inf/NaN.
-__device__ __forceinline__ bool finite6(double a, double b, double c, double d, double e, double f) {
-    const unsigned m = 0x7FF00000u;
-    const unsigned hm = max(max(max((unsigned)__double2hiint(a) & m, (unsigned)__double2hiint(b) & m),
-                                max((unsigned)__double2hiint(c) & m, (unsigned)__double2hiint(d) & m)),
-                            max((unsigned)__double2hiint(e) & m, (unsigned)__double2hiint(f) & m));
-    return hm != m;
-}
 
 __global__ void k_minmax(const double *__restrict__ x, const double *__restrict__ px,
                          const double *__restrict__ y, const double *__restrict__ py,
@@ -189,12 +136,8 @@ cudaError_t launch_minmax(double *const c[6], int64_t n, double betagamma, Track
 // extents floored at 1e-6 of the largest (1e-6 m if all are zero).  Explicit
 // round-to-nearest intrinsics keep every operation as written (no FMA
 // contraction), so the decision matches a plain IEEE evaluation.
-// A box far from the origin relative to its cell size needs the unfused u.
-__host__ __device__ __forceinline__ bool box_far_offset(const Box &b) {
-    for (int d = 0; d < 3; ++d)
-        if (fabs(b.lo[d] * b.inv_h[d]) > 4096.0 || fabs(b.hi[d] * b.inv_h[d]) > 4096.0) return true;
-    return false;
-}
+// With a replay table (differentiation runs) the box of each kick is taken
+// from the table instead, a regrid being a box that differs from the current.
 
 // With `advance` (tracking), the kick index of the call advances, the global
 // kick counter is logged and incremented, and the gates of this kick are set.
@@ -219,7 +162,19 @@ __device__ void box_rule_body(TrackState *st, int nn, long long *log, int64_t ca
                 need = true;
         }
     }
-    if (need) {
+    if (st->box_replay) {
+        const Box &rb = st->box_replay[st->kick];
+        need = st->has_box == 0;
+        for (int d = 0; d < 3; ++d)
+            need = need || rb.lo[d] != st->box.lo[d] || rb.hi[d] != st->box.hi[d] ||
+                   rb.h[d] != st->box.h[d] || rb.inv_h[d] != st->box.inv_h[d];
+        if (need) {
+            st->box = rb;
+            st->has_box = 1;
+            if (st->nlog < cap) log[st->nlog] = st->kick;
+            st->nlog += 1;
+        }
+    } else if (need) {
         for (int d = 0; d < 3; ++d) {
             double c = __dmul_rn(0.5, __dadd_rn(mn[d], mx[d]));
             double w = __dmul_rn(0.55, ext[d]);
@@ -245,6 +200,9 @@ __device__ void box_rule_body(TrackState *st, int nn, long long *log, int64_t ca
                           : 0;
     if (advance) {
         const int k = st->k_in_call;
+        if (st->green_stale) st->green_builds += 1;
+        if (st->box_hist) st->box_hist[st->kick] = st->box;
+        if (st->slot_hist) st->slot_hist[st->kick] = st->green_builds - 1;
         st->deposit_gate = (finite && (need || k == 0)) ? 1 : 0;
         st->sort_gate = (finite && st->sort_interval > 0 && k % st->sort_interval == 0) ? 1 : 0;
         st->next_gate = (finite && k + 1 < st->nkicks_call) ? 1 : 0;
@@ -302,6 +260,9 @@ __global__ void k_call_init(TrackState *st, int nkicks, double q_macro, int sort
         st->sort_interval = sort_interval;
         st->kick = kick0;
         st->deposit_gate = st->sort_gate = st->next_gate = 0;
+        st->box_hist = nullptr;
+        st->box_replay = nullptr;
+        st->slot_hist = nullptr;
     }
 }
 
@@ -463,6 +424,7 @@ constexpr int TILE_CAP = 4096;         // nodes of the shared-memory deposit til
 
 struct PartArgs {
     double *x, *px, *y, *py, *t, *pt;
+    double *ox, *opx, *oy, *opy, *ot, *opt;   // GATHER output (= input unless out of place)
     int64_t n;
     double nbg;                        // -beta*gamma
     const Box *box;
@@ -486,22 +448,6 @@ struct PartArgs {
 // floored box of a single particle) takes the subtraction first.
 bool box_needs_exact_u(const Box &b) { return box_far_offset(b); }
 
-// Cell index and 52-bit fraction per dimension from u, with integer
-// operations only.  u below -1e-9 or above n-1+1e-6 (beyond the rounding of
-// u for a particle inside [lo, hi)) sets `outside`.
-constexpr unsigned long long NEG_TOL_BITS = 0x3E112E0BE826D695ull;  // bits of 1e-9
-__device__ __forceinline__ void cell_frac(double u, int nn, int &cell, unsigned long long &F,
-                                          bool &outside) {
-    const unsigned long long umax = (unsigned long long)(nn - 1) << 52;
-    const unsigned long long b = (unsigned long long)__double_as_longlong(u);
-    unsigned long long U = to_fixed52(u);
-    outside |= ((b >> 63) && abs_bits(u) > NEG_TOL_BITS) || U > umax + 4503599627ull;
-    if (U > umax) U = umax;
-    unsigned long long i = U >> 52;
-    if (i > (unsigned long long)(nn - 2)) i = nn - 2;
-    F = U - (i << 52);
-    cell = (int)i;
-}
 
 // GATHER: CIC interpolation of the fixed-point field at the current position,
 //         kick, then the map (MK) and the store.
@@ -579,12 +525,12 @@ __global__ void __launch_bounds__(TPB, 3) k_particles(PartArgs a) {
             if constexpr (MK == MAP_TABLE) apply_map_table(a.map, x, px, y, py, t, pt);
             else apply_map_k<MK>(a.map, x, px, y, py, t, pt);
             bad |= !finite6(x, px, y, py, t, pt);
-            a.x[p] = x;
-            a.px[p] = px;
-            a.y[p] = y;
-            a.py[p] = py;
-            a.t[p] = t;
-            a.pt[p] = pt;
+            a.ox[p] = x;
+            a.opx[p] = px;
+            a.oy[p] = y;
+            a.opy[p] = py;
+            a.ot[p] = t;
+            a.opt[p] = pt;
         }
         if constexpr (DEP || MM) {
             if constexpr (MM) {
@@ -716,6 +662,12 @@ static PartArgs part_args(double *const c[6], int64_t n, double betagamma, const
     a.py = c[3];
     a.t = c[4];
     a.pt = c[5];
+    a.ox = c[0];
+    a.opx = c[1];
+    a.oy = c[2];
+    a.opy = c[3];
+    a.ot = c[4];
+    a.opt = c[5];
     a.n = n;
     a.nbg = -betagamma;
     a.box = box;
@@ -777,6 +729,41 @@ cudaError_t launch_track_particles(double *const c[6], int64_t n, double betagam
     if (e != cudaSuccess) return e;
     a.gate = &st->next_gate;
     return launch_pk<MAP_NONE, false, true, true>(a, s, K_DEPOSIT);
+}
+
+// Out-of-place device-driven kick (differentiation recompute): A reads cin and
+// writes cout, then (gated on the next kick) B deposits cout's positions.
+cudaError_t launch_track_particles_oop(double *const cin[6], double *const cout[6], int64_t n,
+                                       double betagamma, const Box *box, int nn, const EFix *ef,
+                                       const int *escale, const MapCoef *maps,
+                                       unsigned long long *acc_hi, unsigned long long *acc_lo,
+                                       TrackState *st, int32_t *status, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    PartArgs a = part_args(cin, n, betagamma, box, nn);
+    a.ox = cout[0];
+    a.opx = cout[1];
+    a.oy = cout[2];
+    a.opy = cout[3];
+    a.ot = cout[4];
+    a.opt = cout[5];
+    a.ef = ef;
+    a.escale = escale;
+    a.st = st;
+    a.status = status;
+    a.maps = maps;
+    a.dst = st;
+    cudaError_t e = launch_pk<MAP_TABLE, true, false, false>(a, s, K_GATHER);
+    if (e != cudaSuccess) return e;
+    e = launch_zero_acc(acc_hi, acc_lo, nn, &st->next_gate, s);
+    if (e != cudaSuccess) return e;
+    PartArgs b = part_args(cout, n, betagamma, box, nn);
+    b.acc_hi = acc_hi;
+    b.acc_lo = acc_lo;
+    b.st = st;
+    b.status = status;
+    b.dst = st;
+    b.gate = &st->next_gate;
+    return launch_pk<MAP_NONE, false, true, true>(b, s, K_DEPOSIT);
 }
 
 // Device-driven deposit of the current positions when the box rule asks for it.
