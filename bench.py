@@ -75,6 +75,8 @@ def parse():
     p.add_argument("--workload", default="chicane_25e6_128")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-grad", action="store_true",
+                   help="skip the gradient measurement (fodo8_grad_1e6_64)")
     p.add_argument("--particles", type=int, default=None,
                    help="override the workload's particle count (small profiling cases)")
     return p.parse_args()
@@ -236,6 +238,115 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def grad_bench(dev, checkpoint_interval: int = 20, fd_params=(3, 9)):
+    """Reverse-mode gradient of the final (eps_x, eps_y, sigma_x, sigma_y) of the
+    fodo8_grad_1e6_64 workload (1e6-particle Twiss bunch, 8 quadrupole
+    strengths x 5 super-periods, 200 kicks, 64^3 grid, checkpoints every 20
+    kicks) with respect to the 8 k's and 6 Twiss parameters.
+    T_fwd: plain tracking of the same bunch (bx_track, the default path).
+    T_bwd: the recording forward plus the reverse pass (recompute + adjoint),
+    i.e. everything a gradient costs beyond nothing.  T_fd: 2 x 14 forward
+    runs.  Central differences (box sequence replayed) are checked on a few
+    parameters at h = 1e-6 and 1e-8 relative."""
+    import torch
+    import paper_2208_02382_b300 as btk
+    w = bg.workload("fodo8_grad_1e6_64")
+    sp = btk.Species(w.species.mass_MeV, w.species.kinetic_MeV, w.species.charge_sign)
+    xi = torch.tensor(bg.standard_normal6(w.n_particles, seed=w.seed), dtype=torch.float64,
+                      device=dev)
+    ks = list(bg.KS_FODO8)
+    tw = list(bg.TWISS_FODO)
+    lat = w.lattice
+    fam = bg.fodo8_families(lat)
+    weights = [1.0, 1.0, 1.0, 1.0]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    # plain tracking (warm once: Green's function and graph set-up are per call)
+    trk = btk.Tracker(w.n_grid)
+    for rep in range(2):
+        beam = btk.Beam(btk.twiss_beam(tw, xi), sp, w.bunch_charge_C)
+        trk.reset()
+        _, t_fwd = timed(lambda: trk.track(beam, lat, 0, w.kicks))
+    trk.sync()
+    # gradient: recording forward + reverse (warm once)
+    g = btk.Tracker(w.n_grid)
+    for rep in range(2):
+        gbeam = btk.Beam(btk.twiss_beam(tw, xi), sp, w.bunch_charge_C)
+        _, t_gf = timed(lambda: g.grad_forward(gbeam, lat, checkpoint_interval))
+        boxes = g.grad_boxes()
+        (dk_el, S, _), t_gb = timed(lambda: g.grad_backward(gbeam, weights, want_zbar0=False))
+    g.sync()
+    dk = np.zeros(8)
+    for d, f in zip(dk_el, fam):
+        if f >= 0:
+            dk[f] += d
+    dtw = np.array(btk.twiss_grad(tw, S))
+    grad = np.concatenate([dk, dtw])
+    # central differences on the replayed box sequence
+    fdt = btk.Tracker(w.n_grid)
+
+    def objective(kk, tt):
+        els = bg.fodo8_lattice(kk, 5, 2)
+        b = btk.Beam(btk.twiss_beam(tt, xi), sp, w.bunch_charge_C)
+        fdt.grad_forward(b, els, w.kicks, box_replay=boxes)
+        m = fdt.moments(b).cpu().numpy()
+        o = [math.sqrt(m[6] * m[12] - m[7] ** 2), math.sqrt(m[17] * m[21] - m[18] ** 2),
+             math.sqrt(m[6]), math.sqrt(m[17])]
+        return float(np.dot(weights, o))
+
+    fd_out = {}
+    for h in (1e-6, 1e-8):
+        errs = []
+        for pi in fd_params:
+            kk, tt = list(ks), list(tw)
+            if pi < 8:
+                d = h * abs(kk[pi])
+                kk[pi] += d
+                fp = objective(kk, tt)
+                kk[pi] -= 2 * d
+                fm = objective(kk, tt)
+                scale = np.max(np.abs(dk))
+            else:
+                d = h * abs(tt[pi - 8])
+                tt[pi - 8] += d
+                fp = objective(kk, tt)
+                tt[pi - 8] -= 2 * d
+                fm = objective(kk, tt)
+                scale = np.max(np.abs(dtw))
+            fd = (fp - fm) / (2 * d)
+            errs.append({"param": (f"k{pi}" if pi < 8 else
+                                   ["alpha_x", "beta_x", "eps_x", "alpha_y", "beta_y",
+                                    "eps_y"][pi - 8]),
+                         "adjoint": float(grad[pi]), "fd": fd,
+                         "rel_err": abs(fd - float(grad[pi])) / float(scale)})
+        fd_out[f"h={h:g}"] = errs
+    for t in (trk, g, fdt):
+        t.close()
+    return {"workload": w.name, "particles": w.n_particles, "grid": w.n_grid, "kicks": w.kicks,
+            "checkpoint_interval": checkpoint_interval, "parameters": 14,
+            "objective": "eps_x + eps_y + sigma_x + sigma_y of the final bunch",
+            "t_fwd_ms": t_fwd, "t_grad_forward_ms": t_gf, "t_grad_backward_ms": t_gb,
+            "t_bwd_ms": t_gf + t_gb - 0.0,
+            "ratio_total_over_fwd": (t_fwd + t_gf + t_gb) / t_fwd,
+            "ratio_bwd_over_fwd": (t_gf + t_gb) / t_fwd,
+            "t_fd_ms": 28 * t_fwd, "speedup_vs_fd": 28 * t_fwd / (t_gf + t_gb),
+            "gradient": {"dk": dk.tolist(), "dtwiss": dtw.tolist()},
+            "fd_check": fd_out,
+            "what": "t_fwd = bx_track of the 200 kicks; t_bwd = recording forward "
+                    "(bx_grad_forward) + reverse pass (bx_grad_backward: recompute "
+                    "every segment + adjoint kernels + chain rule); ratio_total_over_fwd = "
+                    "(t_fwd + t_bwd)/t_fwd; FD with the box sequence replayed"}
+
+
 def run_ours(args, w):
     import torch
     import paper_2208_02382_b300 as btk
@@ -362,6 +473,9 @@ def run_ours(args, w):
                        "kick (lattice from host) and bx_moments read back (slice "
                        "diagnostics), final bunch D2H; bytes per step are totals / steps"}
         trk2.close()
+    gradient = None
+    if rank == 0 and not args.no_grad:
+        gradient = grad_bench(dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, sample_particles=2_000_000, kicks_timed=5)
@@ -376,7 +490,7 @@ def run_ours(args, w):
                            "step": "one slice: map, box rule, deposit, solve, gather+kick",
                            "l2": f"inputs larger than L2 (particle SoA {npart * 48 / 1e9:.2f} GB)",
                            "parallelism": f"replicas x{world}"},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gradient": gradient,
                 "gpu_launches": launches, "clocks": clocks, "wall_s_timed": wall,
                 "profiled": {"steps": k_prof, "ms_per_step": ms_per_kick_prof,
                              "what": "same kernels launched one by one with CUDA events "
