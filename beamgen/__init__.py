@@ -206,6 +206,41 @@ class Workload:
         return gaussian6d(n, self.sigmas, seed=self.seed)
 
 
+@dataclass(frozen=True)
+class Variant:
+    """One problem of a batch: bunch size and seed, grid, FODO strengths."""
+    n_particles: int
+    n_grid: int
+    kf: float
+    kd: float
+    seed: int
+
+    def lattice(self, periods=10, nslice=4):
+        return fodo_lattice(periods, nslice, self.kf, self.kd)
+
+    def particles(self) -> np.ndarray:
+        return gaussian6d(self.n_particles, seed=self.seed)
+
+
+def batch_variants(count: int = 256, seed: int = 0, n_min: float = 1e4, n_max: float = 5e5,
+                   spread: float = 0.2, grids=(32, 64)) -> List[Variant]:
+    """Lattice variants of the Listing-1 FODO: k_QF, k_QD drawn uniformly within
+    +-spread of +1 and -1 (per quadrupole family), particle counts
+    floor(10^U(log10 n_min, log10 n_max)), grid 32^3 or 64^3 with equal odds,
+    bunch seeds 1000 + index."""
+    g = _rng(seed)
+    out = []
+    lo, hi = np.log10(n_min), np.log10(n_max)
+    for i in range(int(count)):
+        u = g.random(4)
+        n = int(np.floor(10.0 ** (lo + (hi - lo) * u[0])))
+        grid = grids[0] if u[1] < 0.5 else grids[1]
+        kf = 1.0 * (1.0 + spread * (2.0 * u[2] - 1.0))
+        kd = -1.0 * (1.0 + spread * (2.0 * u[3] - 1.0))
+        out.append(Variant(n, grid, kf, kd, 1000 + i))
+    return out
+
+
 def workload(name: str) -> Workload:
     """The three tracking workloads:
 

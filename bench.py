@@ -77,6 +77,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-grad", action="store_true",
                    help="skip the gradient measurement (fodo8_grad_1e6_64)")
+    p.add_argument("--no-batch", action="store_true",
+                   help="skip the batched-variants measurement (batch_256_fodo)")
     p.add_argument("--particles", type=int, default=None,
                    help="override the workload's particle count (small profiling cases)")
     return p.parse_args()
@@ -347,6 +349,92 @@ def grad_bench(dev, checkpoint_interval: int = 20, fd_params=(3, 9)):
                     "(t_fwd + t_bwd)/t_fwd; FD with the box sequence replayed"}
 
 
+def batch_bench(dev, count: int = 256, periods: int = 10, nslice: int = 4, seed: int = 0):
+    """256 Listing-1 FODO variants (k_QF, k_QD within +-20%, 1e4..5e5 particles
+    log-uniform, 32^3 or 64^3 grid, 1 GeV p, 10 nC, FODO x10 with 4 slices per
+    element = 200 kicks): every variant's whole lattice as ONE graph launch
+    (bx_batch_launch) against the same problems one after another
+    (bx_reset + bx_track each, the default per-kick graph path).  Both start
+    from the same initial bunches; aggregate particle-steps/s."""
+    import torch
+    import paper_2208_02382_b300 as btk
+    variants = bg.batch_variants(count, seed=seed)
+    spc = bg.PROTON_1GEV
+    sp = btk.Species(spc.mass_MeV, spc.kinetic_MeV, spc.charge_sign)
+    charge = 10e-9
+    lats = [v.lattice(periods, nslice) for v in variants]
+    kicks = bg.count_kicks(lats[0])
+    init = [torch.tensor(v.particles(), dtype=torch.float64, device=dev) for v in variants]
+    trks = [btk.Tracker(v.n_grid) for v in variants]
+    beams = [btk.Beam(c.clone(), sp, charge) for c in init]
+    stream = torch.cuda.current_stream()
+    psteps = float(sum(v.n_particles for v in variants)) * kicks
+
+    def restore():
+        for b, c in zip(beams, init):
+            b.coords.copy_(c)
+            b.ids.copy_(torch.arange(b.n, dtype=torch.int64, device=dev))
+
+    def events():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    # sequential: per-kick graphs built once per context (one-kick warm-up)
+    for t, b, lat in zip(trks, beams, lats):
+        t.reset()
+        t.track(b, lat, 0, 1)
+    restore()
+    torch.cuda.synchronize()
+    e0, e1 = events()
+    w0 = time.perf_counter()
+    e0.record(stream)
+    for t, b, lat in zip(trks, beams, lats):
+        t.reset()
+        t.track(b, lat, 0, -1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1)
+    wall_seq = time.perf_counter() - w0
+    for t in trks:
+        t.sync()
+    # batch: build once, warm launch, timed launch from the same initial bunches
+    restore()
+    torch.cuda.synchronize()
+    c0 = time.perf_counter()
+    batch = btk.Batch(trks, beams, lats)
+    t_build = time.perf_counter() - c0
+    batch.launch()
+    torch.cuda.synchronize()
+    restore()
+    torch.cuda.synchronize()
+    e0, e1 = events()
+    w0 = time.perf_counter()
+    e0.record(stream)
+    batch.launch()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1)
+    wall_batch = time.perf_counter() - w0
+    for t in trks:
+        t.sync()
+    batch.close()
+    for t in trks:
+        t.close()
+    n32 = sum(1 for v in variants if v.n_grid == 32)
+    return {"workload": f"batch_{count}_fodo", "variants": count, "kicks_per_variant": kicks,
+            "particles_total": int(sum(v.n_particles for v in variants)),
+            "particles_min_max": [min(v.n_particles for v in variants),
+                                  max(v.n_particles for v in variants)],
+            "grids": {"32": n32, "64": count - n32},
+            "batched": {"ms": t_batch, "particle_steps_per_s": psteps / (t_batch * 1e-3),
+                        "graph_launches": 1, "wall_s": wall_batch},
+            "sequential": {"ms": t_seq, "particle_steps_per_s": psteps / (t_seq * 1e-3),
+                           "graph_launches": count * kicks, "wall_s": wall_seq},
+            "speedup": t_seq / t_batch, "graph_build_s": t_build,
+            "what": "batched = one bx_batch_launch (one CUDA graph: a WHILE loop over the kick "
+                    "per variant); sequential = bx_reset + bx_track per variant (one graph "
+                    "launch per kick); same initial bunches, same kernels, bitwise equal results"}
+
+
 def run_ours(args, w):
     import torch
     import paper_2208_02382_b300 as btk
@@ -476,6 +564,9 @@ def run_ours(args, w):
     gradient = None
     if rank == 0 and not args.no_grad:
         gradient = grad_bench(dev)
+    batching = None
+    if rank == 0 and not args.no_batch:
+        batching = batch_bench(dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, sample_particles=2_000_000, kicks_timed=5)
@@ -491,6 +582,7 @@ def run_ours(args, w):
                            "l2": f"inputs larger than L2 (particle SoA {npart * 48 / 1e9:.2f} GB)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gradient": gradient,
+                "batching": batching,
                 "gpu_launches": launches, "clocks": clocks, "wall_s_timed": wall,
                 "profiled": {"steps": k_prof, "ms_per_step": ms_per_kick_prof,
                              "what": "same kernels launched one by one with CUDA events "

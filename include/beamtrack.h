@@ -55,6 +55,7 @@ extern "C" {
 #define BX_SBEND 2
 
 typedef struct bx_ctx bx_ctx;
+typedef struct bx_batch bx_batch;
 
 /* Options of a context.
  * n_grid      : nodes per dimension N of the charge/potential grid; a power
@@ -290,6 +291,39 @@ int32_t bx_grad_backward(bx_ctx *ctx, const bx_beam *beam, const double weights[
 /* Boxes of the last bx_grad_forward: up to `cap` kicks of 12 doubles
  * {lo[3], hi[3], h[3], 1/h[3]} into out (host); *count = kicks.  Synchronous. */
 int32_t bx_grad_boxes(bx_ctx *ctx, double *out, int64_t cap, int64_t *count);
+
+/* ---- Batches of independent tracking problems --------------------------
+ * No counterpart in the paper: many lattice variants (e.g. a scan of
+ * quadrupole strengths) or bunches of uneven particle counts and grid sizes
+ * tracked at once.  Each problem is one context (its own grid size and
+ * scratch), one beam and one lattice; bx_batch_launch runs every problem's
+ * whole lattice, each exactly as bx_reset + bx_track(ctx, beam, lattice, 0,
+ * -1) would (same kernels, same results bit for bit), as ONE CUDA graph
+ * launch: the graph holds one independent branch per problem, a state reset
+ * and the first half map followed by a device-side WHILE loop over that
+ * problem's kick (the box-rule kernel of each kick decides whether another
+ * kick follows and which optional parts run).  The problems' kernels
+ * interleave on the GPU. */
+
+/* Build the batch graph for `count` problems (ctxs[i], beams[i], lattices[i];
+ * contexts distinct; the beams' arrays and ids must stay allocated and at the
+ * same addresses while the batch exists).  Uploads each problem's map table
+ * into its context, sizes its re-binning scratch, captures and instantiates
+ * the graph.  Synchronous on `stream`.  Errors via bx_batch_last_error(NULL). */
+int32_t bx_batch_create(bx_batch **out, int32_t count, bx_ctx *const *ctxs,
+                        bx_beam *const *beams, const bx_lattice *const *lattices, void *stream);
+
+/* One graph launch: every problem of the batch tracks its whole lattice from
+ * its beam's current coordinates (fresh box and Green's function).
+ * Asynchronous on `stream`; device errors surface through bx_sync of each
+ * problem's context. */
+int32_t bx_batch_launch(bx_batch *batch, void *stream);
+
+/* Free the batch's graph (the contexts and beams are the caller's). */
+int32_t bx_batch_destroy(bx_batch *batch);
+
+/* Text of the last batch error (or of bx_batch_create when batch is NULL). */
+const char *bx_batch_last_error(const bx_batch *batch);
 
 /* Wait for the stream and return the device status word (then clear it). */
 int32_t bx_sync(bx_ctx *ctx, void *stream);

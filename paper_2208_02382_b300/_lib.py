@@ -70,6 +70,12 @@ SIGNATURES = {
                                    POINTER(c_double), POINTER(c_double), POINTER(c_void_p),
                                    c_void_p]),
     "bx_grad_boxes": (c_int32, [c_void_p, POINTER(c_double), c_int64, POINTER(c_int64)]),
+    "bx_batch_create": (c_int32, [POINTER(c_void_p), c_int32, POINTER(c_void_p),
+                                  POINTER(POINTER(bx_beam)), POINTER(POINTER(bx_lattice)),
+                                  c_void_p]),
+    "bx_batch_launch": (c_int32, [c_void_p, c_void_p]),
+    "bx_batch_destroy": (c_int32, [c_void_p]),
+    "bx_batch_last_error": (c_char_p, [c_void_p]),
     "bx_last_error": (c_char_p, [c_void_p]),
 }
 

@@ -288,3 +288,50 @@ class Tracker:
         _check(self.lib, self.ctx, self.lib.bx_grad_boxes(self.ctx, buf, cnt.value,
                                                           ctypes.byref(cnt)))
         return [[buf[12 * i + j] for j in range(12)] for i in range(cnt.value)]
+
+
+class Batch:
+    """Independent tracking problems (tracker, beam, elements) run by one CUDA
+    graph launch (bx_batch_*): each problem tracks its whole lattice exactly
+    as tracker.reset() + tracker.track(beam, elements) would."""
+
+    def __init__(self, trackers: Sequence[Tracker], beams: Sequence[Beam], lattices,
+                 space_charge: bool = True):
+        self.lib = L.load()
+        n = len(trackers)
+        if not (n == len(beams) == len(lattices)) or n == 0:
+            raise ValueError("one beam and one lattice per tracker")
+        self._keep = []
+        ctxs = (ctypes.c_void_p * n)(*[t.ctx for t in trackers])
+        bs = [b.c_struct() for b in beams]
+        lats = []
+        for els in lattices:
+            lat, arr = lattice_struct(els, space_charge)
+            lats.append(lat)
+            self._keep.append(arr)
+        bp = (ctypes.POINTER(L.bx_beam) * n)(*[ctypes.pointer(b) for b in bs])
+        lp = (ctypes.POINTER(L.bx_lattice) * n)(*[ctypes.pointer(x) for x in lats])
+        self._keep += [bs, lats, trackers, beams]
+        h = ctypes.c_void_p()
+        rc = self.lib.bx_batch_create(ctypes.byref(h), n, ctxs, bp, lp, _stream())
+        if rc != L.BX_OK:
+            msg = self.lib.bx_batch_last_error(None)
+            raise L.BeamtrackError(rc, msg.decode() if msg else "")
+        self.handle = h
+
+    def launch(self):
+        rc = self.lib.bx_batch_launch(self.handle, _stream())
+        if rc != L.BX_OK:
+            msg = self.lib.bx_batch_last_error(self.handle)
+            raise L.BeamtrackError(rc, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.bx_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

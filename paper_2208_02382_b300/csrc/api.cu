@@ -17,138 +17,6 @@
 
 using namespace bt;
 
-namespace {
-
-// The kernels of one device-driven kick, in pieces (so the graph builder can
-// put the gated pieces into conditional bodies).
-struct KickArgs {
-    bx_ctx *ctx;
-    double *const *c;
-    int64_t *id;
-    int64_t n;
-    double bg;
-    bool binning;
-};
-
-cudaError_t kick_green(const KickArgs &k, cudaStream_t s) {
-    bx_ctx *ctx = k.ctx;
-    cudaError_t e = launch_igf_table(ctx->n, nullptr, ctx->fcorner, ctx->gtable, s, ctx->st);
-    if (e == cudaSuccess) e = green_spectrum_from_table(&ctx->plan, ctx->gtable, s, &ctx->st->green_stale);
-    if (e == cudaSuccess) e = launch_green_commit(ctx->st, s);
-    return e;
-}
-
-cudaError_t kick_sort(const KickArgs &k, cudaStream_t s) {
-    bx_ctx *ctx = k.ctx;
-    return launch_sort(k.c, (long long *)k.id, k.n, k.bg, &ctx->st->box, ctx->n, ctx->keys,
-                       ctx->counts, ctx->offs, ctx->sums, ctx->scr, ctx->id_scr, ctx->dev_ptrs, s,
-                       &ctx->st->sort_gate);
-}
-
-cudaError_t kick_deposit(const KickArgs &k, cudaStream_t s) {
-    bx_ctx *ctx = k.ctx;
-    return launch_track_deposit(k.c, k.n, k.bg, &ctx->st->box, ctx->n, ctx->acc_hi, ctx->acc_lo,
-                                ctx->st, ctx->status, s);
-}
-
-cudaError_t kick_solve_field_push(const KickArgs &k, cudaStream_t s) {
-    bx_ctx *ctx = k.ctx;
-    cudaError_t e = solve_acc_to_phi(&ctx->plan, ctx->acc_hi, ctx->acc_lo, 0.0, ctx->phi, s,
-                                     &ctx->st->rho_scale);
-    if (e == cudaSuccess)
-        e = launch_field(ctx->phi, ctx->n, &ctx->st->box, 0.0, 0.0, 0.0, ctx->efield, ctx->emax,
-                         ctx->efix, ctx->escale, s, ctx->st, ctx->maps);
-    if (e == cudaSuccess)
-        e = launch_track_particles(k.c, k.n, k.bg, &ctx->st->box, ctx->n, ctx->efix, ctx->escale,
-                                   ctx->maps, ctx->acc_hi, ctx->acc_lo, ctx->st, ctx->status, s, 1);
-    return e;
-}
-
-cudaError_t kick_next_deposit(const KickArgs &k, cudaStream_t s) {
-    bx_ctx *ctx = k.ctx;
-    return launch_track_particles(k.c, k.n, k.bg, &ctx->st->box, ctx->n, ctx->efix, ctx->escale,
-                                  ctx->maps, ctx->acc_hi, ctx->acc_lo, ctx->st, ctx->status, s, 2);
-}
-
-// Plain launches of one kick (gated kernels return at once when not needed).
-cudaError_t kick_plain(const KickArgs &k, cudaStream_t s) {
-    bx_ctx *ctx = k.ctx;
-    cudaError_t e = launch_box_rule(ctx->st, ctx->n, k.n, ctx->log, ctx->log_cap, true, s);
-    if (e == cudaSuccess) e = kick_green(k, s);
-    if (e == cudaSuccess && k.binning) e = kick_sort(k, s);
-    if (e == cudaSuccess) e = kick_deposit(k, s);
-    if (e == cudaSuccess) e = kick_solve_field_push(k, s);
-    if (e == cudaSuccess) e = kick_next_deposit(k, s);
-    return e;
-}
-
-// Adds an IF node on condition `h` at the current point of the capture on
-// `cs` and captures `body` into it on `bs`.
-template <class F>
-cudaError_t capture_if(cudaStream_t cs, cudaStream_t bs, cudaGraph_t cg,
-                       cudaGraphConditionalHandle h, F body) {
-    cudaStreamCaptureStatus status;
-    const cudaGraphNode_t *deps = nullptr;
-    size_t ndeps = 0;
-    cudaError_t e = cudaStreamGetCaptureInfo(cs, &status, nullptr, nullptr, &deps, nullptr, &ndeps);
-    if (e != cudaSuccess) return e;
-    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
-    p.conditional.handle = h;
-    p.conditional.type = cudaGraphCondTypeIf;
-    p.conditional.size = 1;
-    cudaGraphNode_t node;
-    e = cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &p);
-    if (e != cudaSuccess) return e;
-    cudaGraph_t g = p.conditional.phGraph_out[0];
-    e = cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
-    if (e != cudaSuccess) return e;
-    e = cudaStreamBeginCaptureToGraph(bs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-    if (e != cudaSuccess) return e;
-    cudaError_t eb = body(bs);
-    e = cudaStreamEndCapture(bs, &g);
-    return eb != cudaSuccess ? eb : e;
-}
-
-// One kick as a CUDA graph: box rule (sets the conditions), IF(Green's
-// function stale){rebuild}, IF(re-bin due){sort}, IF(deposit needed){deposit},
-// solve + field + gather/kick/map, IF(next kick){deposit for it}.
-cudaError_t build_kick_graph(const KickArgs &k, cudaGraphExec_t *exec) {
-    bx_ctx *ctx = k.ctx;
-    cudaError_t e = cudaSuccess;
-    if (!ctx->cap_stream) e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess && !ctx->body_stream)
-        e = cudaStreamCreateWithFlags(&ctx->body_stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return e;
-    cudaStream_t cs = ctx->cap_stream, bs = ctx->body_stream;
-    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
-    if (e != cudaSuccess) return e;
-    cudaGraph_t cg = nullptr;
-    cudaStreamCaptureStatus status;
-    e = cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, nullptr, nullptr, nullptr);
-    cudaGraphConditionalHandle hg = 0, hs = 0, hd = 0, hn = 0;
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hg, cg, 0, cudaGraphCondAssignDefault);
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hs, cg, 0, cudaGraphCondAssignDefault);
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hd, cg, 0, cudaGraphCondAssignDefault);
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hn, cg, 0, cudaGraphCondAssignDefault);
-    if (e == cudaSuccess)
-        e = launch_box_rule_graph(ctx->st, ctx->n, ctx->log, ctx->log_cap, hg, hs, hd, hn, cs);
-    if (e == cudaSuccess) e = capture_if(cs, bs, cg, hg, [&](cudaStream_t b) { return kick_green(k, b); });
-    if (e == cudaSuccess && k.binning)
-        e = capture_if(cs, bs, cg, hs, [&](cudaStream_t b) { return kick_sort(k, b); });
-    if (e == cudaSuccess) e = capture_if(cs, bs, cg, hd, [&](cudaStream_t b) { return kick_deposit(k, b); });
-    if (e == cudaSuccess) e = kick_solve_field_push(k, cs);
-    if (e == cudaSuccess)
-        e = capture_if(cs, bs, cg, hn, [&](cudaStream_t b) { return kick_next_deposit(k, b); });
-    cudaGraph_t graph = nullptr;
-    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
-    if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
-    if (graph) cudaGraphDestroy(graph);
-    cudaGetLastError();  // clear a sticky capture error, if any
-    return e;
-}
-
-}  // namespace
 
 int32_t bt::set_noctx_error(int32_t code, const char *msg) { return fail(nullptr, code, msg); }
 

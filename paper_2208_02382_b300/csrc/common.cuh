@@ -166,7 +166,10 @@ cudaError_t launch_track_particles(double *const c[6], int64_t n, double betagam
 cudaError_t launch_box_rule_graph(TrackState *st, int nn, long long *log, int64_t cap,
                                   cudaGraphConditionalHandle hg, cudaGraphConditionalHandle hs,
                                   cudaGraphConditionalHandle hd, cudaGraphConditionalHandle hn,
-                                  cudaStream_t s);
+                                  cudaStream_t s, cudaGraphConditionalHandle hl = 0,
+                                  bool has_loop = false);
+cudaError_t launch_state_reset(TrackState *st, int nkicks, double q_macro, int sort_interval,
+                               cudaStream_t s);
 cudaError_t launch_track_particles_oop(double *const cin[6], double *const cout[6], int64_t n,
                                        double betagamma, const Box *box, int nn, const EFix *ef,
                                        const int *escale, const MapCoef *maps,

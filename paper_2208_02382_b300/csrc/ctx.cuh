@@ -105,4 +105,16 @@ int32_t read_state(bx_ctx *ctx, TrackState *h, cudaStream_t s);
 void init_state(TrackState *h);
 void grad_free(bx_ctx *ctx);
 
+// kick.cu: the pieces of one device-driven kick and its graphs
+struct KickArgs {
+    bx_ctx *ctx;
+    double *const *c;
+    int64_t *id;
+    int64_t n;
+    double bg;
+    bool binning;
+};
+cudaError_t kick_plain(const KickArgs &k, cudaStream_t s);
+cudaError_t build_kick_graph(const KickArgs &k, cudaGraphExec_t *exec);
+
 }  // namespace bt

@@ -26,22 +26,26 @@ struct dd {
 
 __device__ __forceinline__ dd dd_make(double a) { return {a, 0.0}; }
 
+// The error-free transformations are written with round-to-nearest intrinsics,
+// which the compiler never fuses into an FMA with a neighbouring operation
+// (a contracted a*b + c would no longer match the separately rounded product
+// that the error term describes).
 __device__ __forceinline__ dd two_sum(double a, double b) {
-    double s = a + b;
-    double bb = s - a;
-    double e = (a - (s - bb)) + (b - bb);
+    const double s = __dadd_rn(a, b);
+    const double bb = __dsub_rn(s, a);
+    const double e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
     return {s, e};
 }
 
 __device__ __forceinline__ dd fast_two_sum(double a, double b) {  // |a| >= |b|
-    double s = a + b;
-    double e = b - (s - a);
+    const double s = __dadd_rn(a, b);
+    const double e = __dsub_rn(b, __dsub_rn(s, a));
     return {s, e};
 }
 
 __device__ __forceinline__ dd two_prod(double a, double b) {
-    double p = a * b;
-    double e = fma(a, b, -p);
+    const double p = __dmul_rn(a, b);
+    const double e = fma(a, b, -p);
     return {p, e};
 }
 

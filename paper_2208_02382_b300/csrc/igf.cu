@@ -12,10 +12,23 @@
 // double-double and G is rounded to double once.  Corner coordinates are
 // (i - 1/2) h, never zero; ln(u + r) for u < 0 is ln((r^2 - u^2)/(r - u)).
 //
-// Two kernels: one thread per corner of the (n+2)^3 corner lattice evaluates
-// F once; one thread per octant cell (n+1)^3 forms the corner sum.
+// Far cells (corner radius |h|/2 at most 1/16 of the distance R) take the
+// cell-integrated Taylor series instead (igf_far.cuh, written by
+// gen_igf_far.py): G = V/(4 pi eps0 R) (1 + sum_{n=1..6} Q_n(U,V,W)/R^2n), U =
+// (x/R)^2 etc., with Q_n's coefficients formed once per block from h; the
+// truncation error is below 1.4e-17 of G and the series terms are at most
+// 1/250 of the leading V/R, which is formed in double-double.  Only the near
+// region (a box of about 16|h|/h_d cells per dimension around the origin)
+// needs corner values.
+//
+// Two kernels: one thread per corner of the near region evaluates F once;
+// one thread per octant cell (n+1)^3 forms the corner sum (near) or the series
+// (far).
+#include <algorithm>
+
 #include "common.cuh"
 #include "dd.cuh"
+#include "igf_far.cuh"
 
 namespace bt {
 
@@ -46,6 +59,16 @@ __device__ dd igf_antiderivative(dd x, dd y, dd z) {
     return f;
 }
 
+// A cell at distance R (squared R2) is far when R2 >= 64 (hx^2 + hy^2 + hz^2),
+// i.e. |h|/2 <= R/16.
+__device__ __forceinline__ bool igf_is_far(double R2, double hsum2) { return R2 >= 64.0 * hsum2; }
+
+// Near cells have index below 8|h|/h_d + 1 in dimension d (rounding slack).
+__device__ __forceinline__ int igf_near_extent(int n, double hd, double hsum2) {
+    const double e = 8.0 * sqrt(hsum2) / hd;
+    return e >= (double)n ? n : min(n, (int)e + 1);
+}
+
 // With a tracking state `gate`, the cell size is the state's box h and the
 // kernel does nothing unless the Green's function is stale.
 __global__ void k_igf_corner(int n, double hx, double hy, double hz, double2 *__restrict__ fc,
@@ -57,31 +80,113 @@ __global__ void k_igf_corner(int n, double hx, double hy, double hz, double2 *__
         hz = gate->box.h[2];
     }
     const int m = n + 2;
-    const long long total = (long long)m * m * m;
+    const double hsum2 = hx * hx + hy * hy + hz * hz;
+    // corners 0..A+1 per dimension serve the near cells 0..A
+    const int ci = igf_near_extent(n, hx, hsum2) + 2, cj = igf_near_extent(n, hy, hsum2) + 2,
+              ck = igf_near_extent(n, hz, hsum2) + 2;
+    const long long total = (long long)ci * cj * ck;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
-        int i = (int)(idx % m);
-        int j = (int)((idx / m) % m);
-        int k = (int)(idx / ((long long)m * m));
+        int i = (int)(idx % ci);
+        int j = (int)((idx / ci) % cj);
+        int k = (int)(idx / ((long long)ci * cj));
         dd x = two_prod(i - 0.5, hx);
         dd y = two_prod(j - 0.5, hy);
         dd z = two_prod(k - 0.5, hz);
         dd f = igf_antiderivative(x, y, z);
-        fc[idx] = make_double2(f.hi, f.lo);
+        fc[((long long)k * m + j) * m + i] = make_double2(f.hi, f.lo);
     }
 }
 
-__global__ void k_igf_sum(int n, const double2 *__restrict__ fc, double *__restrict__ g,
-                          const TrackState *gate) {
-    if (gate && (!gate->green_stale || gate->halt)) return;
+constexpr int IGF_FAR_NC = 83;  // sum over n = 1..6 of (n+1)(n+2)/2 monomials
+
+// Coefficients of Q_n (n = 1..6) over U^i V^j W^k for half-sides a = h/2:
+// sum over (p,q,t) of a_x^2p a_y^2q a_z^2t times the tabulated coefficient.
+__device__ void igf_far_coefficients(double hx, double hy, double hz, double *c) {
+    const double ax2 = 0.25 * hx * hx, ay2 = 0.25 * hy * hy, az2 = 0.25 * hz * hz;
+    for (int k = threadIdx.x; k < IGF_FAR_NC; k += blockDim.x) {
+        int n = 1, base = 0;
+        while (k >= base + (n + 1) * (n + 2) / 2) {
+            base += (n + 1) * (n + 2) / 2;
+            ++n;
+        }
+        const int nt = (n + 1) * (n + 2) / 2, mono = k - base;
+        double acc = 0.0;
+        int ti = 0;
+        for (int p = n; p >= 0; --p)
+            for (int q = n - p; q >= 0; --q, ++ti) {
+                const int t = n - p - q;
+                double A = 1.0;
+                for (int e = 0; e < p; ++e) A *= ax2;
+                for (int e = 0; e < q; ++e) A *= ay2;
+                for (int e = 0; e < t; ++e) A *= az2;
+                acc = fma(A, IGF_FAR_P[IGF_FAR_OFF[n - 1] + ti * nt + mono], acc);
+            }
+        c[k] = acc;
+    }
+}
+
+// G of a far cell at (x, y, z) = (a hx, b hy, c hz), with the coefficients c.
+__device__ double igf_far_cell(int a, int b, int cc, double hx, double hy, double hz,
+                               const double *c) {
+    const dd x = two_prod((double)a, hx), y = two_prod((double)b, hy), z = two_prod((double)cc, hz);
+    const dd R2 = dd_add(dd_add(dd_mul(x, x), dd_mul(y, y)), dd_mul(z, z));
+    const double iR2 = 1.0 / R2.hi;
+    const double U = x.hi * x.hi * iR2, V = y.hi * y.hi * iR2, W = z.hi * z.hi * iR2;
+    double Up[7], Vp[7], Wp[7];
+    Up[0] = Vp[0] = Wp[0] = 1.0;
+#pragma unroll
+    for (int e = 1; e <= 6; ++e) {
+        Up[e] = Up[e - 1] * U;
+        Vp[e] = Vp[e - 1] * V;
+        Wp[e] = Wp[e - 1] * W;
+    }
+    // corr = sum_n Q_n iR2^n, Horner in iR2 from n = 6 down
+    double corr = 0.0;
+    int base = IGF_FAR_NC;
+#pragma unroll
+    for (int n = 6; n >= 1; --n) {
+        const int nt = (n + 1) * (n + 2) / 2;
+        base -= nt;
+        double qn = 0.0;
+        int mi = 0;
+#pragma unroll
+        for (int i = n; i >= 0; --i)
+#pragma unroll
+            for (int j = n - i; j >= 0; --j, ++mi) qn = fma(c[base + mi], Up[i] * Vp[j] * Wp[n - i - j], qn);
+        corr = (corr + qn) * iR2;
+    }
+    const dd ke = {KE_HI, KE_LO};
+    const dd vol = dd_mul_d(two_prod(hx, hy), hz);
+    const dd lead = dd_div(dd_mul(ke, vol), dd_sqrt(R2));
+    return lead.hi + fma(lead.hi, corr, lead.lo);
+}
+
+__global__ void k_igf_sum(int n, double hx, double hy, double hz, const double2 *__restrict__ fc,
+                          double *__restrict__ g, const TrackState *gate) {
+    if (gate) {
+        if (!gate->green_stale || gate->halt) return;
+        hx = gate->box.h[0];
+        hy = gate->box.h[1];
+        hz = gate->box.h[2];
+    }
+    __shared__ double sc[IGF_FAR_NC];
+    igf_far_coefficients(hx, hy, hz, sc);
+    __syncthreads();
     const int m = n + 2, q = n + 1;
     const long long total = (long long)q * q * q;
     const dd ke = {KE_HI, KE_LO};
+    const double hsum2 = hx * hx + hy * hy + hz * hz;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         int a = (int)(idx % q);
         int b = (int)((idx / q) % q);
         int c = (int)(idx / ((long long)q * q));
+        const double xa = a * hx, yb = b * hy, zc = c * hz;
+        if (igf_is_far(xa * xa + yb * yb + zc * zc, hsum2)) {
+            g[idx] = igf_far_cell(a, b, c, hx, hy, hz, sc);
+            continue;
+        }
         dd s = dd_make(0.0);
         for (int dk = 0; dk < 2; ++dk)
             for (int dj = 0; dj < 2; ++dj)
@@ -98,12 +203,18 @@ __global__ void k_igf_sum(int n, const double2 *__restrict__ fc, double *__restr
 
 cudaError_t launch_igf_table(int n, const double h[3], double *fcorner, double *gtable,
                              cudaStream_t s, const TrackState *gate) {
-    const int m = n + 2, q = n + 1;
-    long long tc = (long long)m * m * m, ts = (long long)q * q * q;
-    int bc = (int)((tc + 127) / 128), bs = (int)((ts + 255) / 256);
+    const int q = n + 1;
+    const long long ts = (long long)q * q * q;
+    // the near region's size is known on the device only (h may come from the
+    // state): a grid-stride launch of at most 148 x 8 blocks covers it
+    const int m = n + 2;
+    const long long tc = (long long)m * m * m;
+    int bc = (int)std::min<long long>((tc + 127) / 128, 148 * 8);
+    int bs = (int)std::min<long long>((ts + 255) / 256, 148 * 16);
     const double h0 = h ? h[0] : 0.0, h1 = h ? h[1] : 0.0, h2 = h ? h[2] : 0.0;
     BT_LAUNCH(K_IGF_CORNER, s, k_igf_corner<<<bc, 128, 0, s>>>(n, h0, h1, h2, (double2 *)fcorner, gate));
-    BT_LAUNCH(K_IGF_SUM, s, k_igf_sum<<<bs, 256, 0, s>>>(n, (const double2 *)fcorner, gtable, gate));
+    BT_LAUNCH(K_IGF_SUM, s, k_igf_sum<<<bs, 256, 0, s>>>(n, h0, h1, h2, (const double2 *)fcorner,
+                                                         gtable, gate));
     return cudaGetLastError();
 }
 

@@ -226,20 +226,23 @@ __global__ void k_box_rule_graph(TrackState *st, int nn, long long *log, int64_t
                                  cudaGraphConditionalHandle h_green,
                                  cudaGraphConditionalHandle h_sort,
                                  cudaGraphConditionalHandle h_dep,
-                                 cudaGraphConditionalHandle h_next) {
+                                 cudaGraphConditionalHandle h_next,
+                                 cudaGraphConditionalHandle h_loop, int has_loop) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     box_rule_body(st, nn, log, cap, 1);
     cudaGraphSetConditional(h_green, st->green_stale ? 1u : 0u);
     cudaGraphSetConditional(h_sort, st->sort_gate ? 1u : 0u);
     cudaGraphSetConditional(h_dep, st->deposit_gate ? 1u : 0u);
     cudaGraphSetConditional(h_next, st->next_gate ? 1u : 0u);
+    if (has_loop) cudaGraphSetConditional(h_loop, st->next_gate ? 1u : 0u);
 }
 
 cudaError_t launch_box_rule_graph(TrackState *st, int nn, long long *log, int64_t cap,
                                   cudaGraphConditionalHandle hg, cudaGraphConditionalHandle hs,
                                   cudaGraphConditionalHandle hd, cudaGraphConditionalHandle hn,
-                                  cudaStream_t s) {
-    BT_LAUNCH(K_BOX, s, k_box_rule_graph<<<1, 32, 0, s>>>(st, nn, log, cap, hg, hs, hd, hn));
+                                  cudaStream_t s, cudaGraphConditionalHandle hl, bool has_loop) {
+    BT_LAUNCH(K_BOX, s, k_box_rule_graph<<<1, 32, 0, s>>>(st, nn, log, cap, hg, hs, hd, hn, hl,
+                                                           has_loop ? 1 : 0));
     return cudaGetLastError();
 }
 
@@ -251,6 +254,31 @@ cudaError_t launch_box_rule(TrackState *st, int nn, int64_t n, long long *log, i
 }
 
 // Start of a device-driven bx_track call.
+// A fresh tracking state (no box, no Green's function, counters 0) set up
+// for a call of nkicks kicks (the device-side counterpart of bx_reset +
+// the start of bx_track, for graphs that track from scratch at each launch).
+__global__ void k_state_reset(TrackState *st, int nkicks, double q_macro, int sort_interval) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        TrackState z;
+        memset(&z, 0, sizeof(z));
+        for (int d = 0; d < 3; ++d) {
+            z.mm[d] = LLONG_MAX;
+            z.mm[3 + d] = LLONG_MIN;
+        }
+        z.k_in_call = -1;
+        z.nkicks_call = nkicks;
+        z.q_macro = q_macro;
+        z.sort_interval = sort_interval;
+        *st = z;
+    }
+}
+
+cudaError_t launch_state_reset(TrackState *st, int nkicks, double q_macro, int sort_interval,
+                               cudaStream_t s) {
+    BT_LAUNCH(K_BOX, s, k_state_reset<<<1, 32, 0, s>>>(st, nkicks, q_macro, sort_interval));
+    return cudaGetLastError();
+}
+
 __global__ void k_call_init(TrackState *st, int nkicks, double q_macro, int sort_interval,
                             long long kick0) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
