@@ -44,7 +44,7 @@ int32_t bx_create(bx_ctx **out, const bx_options *opt) {
     A((void **)&ctx->rho, n3 * 8);
     A((void **)&ctx->phi, q3 * 8);
     A((void **)&ctx->efield, n3 * sizeof(Field4));
-    A((void **)&ctx->fcorner, q3 * 16);
+    A((void **)&ctx->fcorner, igf_scratch_doubles(n) * sizeof(double));
     A((void **)&ctx->gtable, o3 * 8);
     A((void **)&ctx->st, sizeof(TrackState));
     A((void **)&ctx->tmp_box, sizeof(Box));

@@ -254,6 +254,11 @@ cudaError_t launch_ghat_fetch(const int32_t *slot_hist, long long k, const doubl
                               double *ghat, long long count, int cap, cudaStream_t s);
 cudaError_t launch_twiss_beam(P6 xi, int64_t n, const double c[8], P6 out, cudaStream_t s);
 // igf.cu
+// Doubles of IGF scratch for grid n: the (n+2)^3 corner table in
+// double-double, then the far-field series coefficients.
+inline long long igf_scratch_doubles(int n) {
+    return 2LL * (n + 2) * (n + 2) * (n + 2) + 256;
+}
 cudaError_t launch_igf_table(int n, const double h[3], double *fcorner, double *gtable,
                              cudaStream_t s, const TrackState *gate = nullptr);
 cudaError_t launch_green_commit(TrackState *st, cudaStream_t s);

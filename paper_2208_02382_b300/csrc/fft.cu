@@ -301,7 +301,10 @@ __global__ void __launch_bounds__(FFT_TPB) k_fft_x_fwd(XIn in, int n, int ny, in
 //               inverse; writes like MODE_INV
 //   MODE_GREEN  forward; writes the real part of elements e <= n to the
 //               octant gh_out[(e*P + o)*P + kx] (lines o = ky <= n)
-enum PassMode { MODE_FWD = 0, MODE_INV = 1, MODE_ZSOLVE = 2, MODE_GREEN = 3 };
+//   MODE_FWD_EVEN forward like MODE_FWD
+// MODE_FWD_EVEN and MODE_GREEN read an even sequence from its first half:
+// element e is stored at min(e, M - e).
+enum PassMode { MODE_FWD = 0, MODE_INV = 1, MODE_ZSOLVE = 2, MODE_GREEN = 3, MODE_FWD_EVEN = 4 };
 
 template <int M, int MODE>
 __global__ void __launch_bounds__(FFT_TPB) k_fft_lines(const double2 *__restrict__ in,
@@ -331,7 +334,8 @@ __global__ void __launch_bounds__(FFT_TPB) k_fft_lines(const double2 *__restrict
     for (int j = 0; j < U0; ++j)
 #pragma unroll
         for (int m = 0; m < R0; ++m) {
-            const int e = first_index<M>(t, j, m);
+            int e = first_index<M>(t, j, m);
+            if constexpr (MODE == MODE_GREEN || MODE == MODE_FWD_EVEN) e = min(e, M - e);
             v[j * R0 + m] = (live && e < ne_in) ? src[e * in_e] : make_double2(0.0, 0.0);
         }
     double2 *s = sl + team * M;
@@ -349,7 +353,7 @@ __global__ void __launch_bounds__(FFT_TPB) k_fft_lines(const double2 *__restrict
         line_fft<M, true>(v, s, t, stw);
     }
     if (!live) return;
-    if constexpr (MODE == MODE_FWD) {
+    if constexpr (MODE == MODE_FWD || MODE == MODE_FWD_EVEN) {
         double2 *dst = out + o * out_o + kx;
         for (int e = t; e < nw; e += T) dst[e * out_e] = s[e];
     } else if constexpr (MODE == MODE_GREEN) {
@@ -437,6 +441,7 @@ static void set_attrs() {
     cudaFuncSetAttribute(k_fft_lines<M, MODE_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_fft_lines<M, MODE_ZSOLVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_fft_lines<M, MODE_GREEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_fft_lines<M, MODE_FWD_EVEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_fft_x_inv<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
@@ -521,24 +526,27 @@ static cudaError_t solve_m(const FftPlan *p, const XIn &in, int src, int nin, do
     return cudaGetLastError();
 }
 
+// Spectrum of the doubled Green's function from its octant table.  The doubled
+// G is even in every dimension, so each pass only transforms the lines whose
+// outer indices lie in the first half (0..n) and reads mirrored inputs:
+// x over rows y <= n+1, z <= n; y over lines z <= n; z over lines ky <= n.
 template <int M>
 static cudaError_t green_m(const FftPlan *p, const double *gtable, cudaStream_t s, const int *gate) {
     const int n = p->n;
-    const long long P = n + 1;
+    const long long P = n + 1, ny = n + 2;
     const size_t sm = smem_bytes(M);
     XIn in{};
     in.g = gtable;
-    // x over all m^2 rows of the even extension -> buf[z][y][kx], z, y < m
-    BT_LAUNCH(K_GREEN_X, s, k_fft_x_fwd<M, SRC_GREEN><<<blocks_lines((long long)(M / 2) * M, M),
-                                                        FFT_TPB, sm, s>>>(in, n, M, M, p->tw, p->buf, gate));
-    // y: lines (z < m, kx), all y -> buf2[z][ky][kx], ky <= n
-    BT_LAUNCH(K_GREEN_YZ, s, k_fft_lines<M, MODE_FWD><<<blocks_lines((long long)M * P, M), FFT_TPB,
-                                                        sm, s>>>(p->buf, (long long)M * P, P, M,
-                                                                 p->buf2, P * P, P, (int)P, M,
-                                                                 (int)P, nullptr, nullptr, p->tw, gate));
-    // z: lines (ky <= n, kx), all z -> real part at kz <= n
+    // x: rows y < n+2 (pairs), z <= n -> buf[z][y][kx]
+    BT_LAUNCH(K_GREEN_X, s, k_fft_x_fwd<M, SRC_GREEN><<<blocks_lines((ny / 2) * P, M), FFT_TPB, sm, s>>>(
+                                in, n, (int)ny, (int)P, p->tw, p->buf, gate));
+    // y: lines (z <= n, kx), element y read at min(y, m - y) -> buf2[z][ky][kx], ky <= n
+    BT_LAUNCH(K_GREEN_YZ, s, k_fft_lines<M, MODE_FWD_EVEN><<<blocks_lines(P * P, M), FFT_TPB, sm, s>>>(
+                                 p->buf, ny * P, P, (int)ny, p->buf2, P * P, P, (int)P, (int)P,
+                                 (int)P, nullptr, nullptr, p->tw, gate));
+    // z: lines (ky <= n, kx), element z read at min(z, m - z) -> real part at kz <= n
     BT_LAUNCH(K_GREEN_YZ, s, k_fft_lines<M, MODE_GREEN><<<blocks_lines(P * P, M), FFT_TPB, sm, s>>>(
-                                 p->buf2, P, P * P, M, nullptr, 0, 0, 0, (int)P, (int)P, nullptr,
+                                 p->buf2, P, P * P, (int)P, nullptr, 0, 0, 0, (int)P, (int)P, nullptr,
                                  p->ghat, p->tw, gate));
     return cudaGetLastError();
 }

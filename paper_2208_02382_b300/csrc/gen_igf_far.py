@@ -20,7 +20,7 @@ to 0, then q (resp. j) from n-p down to 0.
 The order-l Taylor term of 1/|R+s| is |s|^l P_l(cos)/R^(l+1) with |P_l| <= 1,
 so after the order-2L term the relative truncation error is below
 rho^(2L+2)/(1 - rho^2), rho = |a|/|R|; igf.cu uses the series where
-rho <= 1/16, L = 6 (below 1.4e-17).
+rho <= 1/8, L = 8 (below 5.6e-17), fewer orders farther out.
 
 Run:  python gen_igf_far.py   (rewrites igf_far.cuh next to this file)
 """
@@ -30,7 +30,7 @@ import os
 from fractions import Fraction
 from math import factorial
 
-L = 6
+L = 8
 
 
 def poly_mul_r2_dx(P, var):

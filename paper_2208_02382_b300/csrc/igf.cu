@@ -12,13 +12,13 @@
 // double-double and G is rounded to double once.  Corner coordinates are
 // (i - 1/2) h, never zero; ln(u + r) for u < 0 is ln((r^2 - u^2)/(r - u)).
 //
-// Far cells (corner radius |h|/2 at most 1/16 of the distance R) take the
+// Far cells (corner radius |h|/2 at most 1/8 of the distance R) take the
 // cell-integrated Taylor series instead (igf_far.cuh, written by
-// gen_igf_far.py): G = V/(4 pi eps0 R) (1 + sum_{n=1..6} Q_n(U,V,W)/R^2n), U =
+// gen_igf_far.py): G = V/(4 pi eps0 R) (1 + sum_{n=1..L} Q_n(U,V,W)/R^2n), U =
 // (x/R)^2 etc., with Q_n's coefficients formed once per block from h; the
-// truncation error is below 1.4e-17 of G and the series terms are at most
-// 1/250 of the leading V/R, which is formed in double-double.  Only the near
-// region (a box of about 16|h|/h_d cells per dimension around the origin)
+// truncation error is below 5.6e-17 of G and the series terms are at most
+// 1/60 of the leading V/R, which is formed in double-double.  Only the near
+// region (a box of about 8|h|/h_d cells per dimension around the origin)
 // needs corner values.
 //
 // Two kernels: one thread per corner of the near region evaluates F once;
@@ -59,13 +59,13 @@ __device__ dd igf_antiderivative(dd x, dd y, dd z) {
     return f;
 }
 
-// A cell at distance R (squared R2) is far when R2 >= 64 (hx^2 + hy^2 + hz^2),
-// i.e. |h|/2 <= R/16.
-__device__ __forceinline__ bool igf_is_far(double R2, double hsum2) { return R2 >= 64.0 * hsum2; }
+// A cell at distance R (squared R2) is far when R2 >= 16 (hx^2 + hy^2 + hz^2),
+// i.e. |h|/2 <= R/8.
+__device__ __forceinline__ bool igf_is_far(double R2, double hsum2) { return R2 >= 16.0 * hsum2; }
 
-// Near cells have index below 8|h|/h_d + 1 in dimension d (rounding slack).
+// Near cells have index below 4|h|/h_d + 1 in dimension d (rounding slack).
 __device__ __forceinline__ int igf_near_extent(int n, double hd, double hsum2) {
-    const double e = 8.0 * sqrt(hsum2) / hd;
+    const double e = 4.0 * sqrt(hsum2) / hd;
     return e >= (double)n ? n : min(n, (int)e + 1);
 }
 
@@ -98,11 +98,18 @@ __global__ void k_igf_corner(int n, double hx, double hy, double hz, double2 *__
     }
 }
 
-constexpr int IGF_FAR_NC = 83;  // sum over n = 1..6 of (n+1)(n+2)/2 monomials
+constexpr int IGF_FAR_NC = 164;  // sum over n = 1..8 of (n+1)(n+2)/2 monomials
 
-// Coefficients of Q_n (n = 1..6) over U^i V^j W^k for half-sides a = h/2:
+// Coefficients of Q_n (n = 1..8) over U^i V^j W^k for half-sides a = h/2:
 // sum over (p,q,t) of a_x^2p a_y^2q a_z^2t times the tabulated coefficient.
-__device__ void igf_far_coefficients(double hx, double hy, double hz, double *c) {
+// One block per build; the sum kernel's blocks read the result.
+__global__ void k_igf_coef(double hx, double hy, double hz, const TrackState *gate, double *c) {
+    if (gate) {
+        if (!gate->green_stale || gate->halt) return;
+        hx = gate->box.h[0];
+        hy = gate->box.h[1];
+        hz = gate->box.h[2];
+    }
     const double ax2 = 0.25 * hx * hx, ay2 = 0.25 * hy * hy, az2 = 0.25 * hz * hz;
     for (int k = threadIdx.x; k < IGF_FAR_NC; k += blockDim.x) {
         int n = 1, base = 0;
@@ -126,28 +133,37 @@ __device__ void igf_far_coefficients(double hx, double hy, double hz, double *c)
     }
 }
 
-// G of a far cell at (x, y, z) = (a hx, b hy, c hz), with the coefficients c.
+// G of a far cell at (x, y, z) = (a hx, b hy, c hz), with the coefficients c
+// and q = V/(4 pi eps0) in double-double.  The series stops at the order L
+// whose remainder rho^(2L+2) is small (rho^2 = |h|^2/(4 R^2)): L = 8 for
+// rho <= 1/8 (5.6e-17), 6 for rho <= 1/16, 5 for rho <= 1/32, 4 for
+// rho <= 1/64, 3 for rho <= 1/256 (each below 1.4e-17).
+// 1/R comes from rsqrt and one Newton step with a double-double residual.
 __device__ double igf_far_cell(int a, int b, int cc, double hx, double hy, double hz,
-                               const double *c) {
+                               double hsum2, const double *c, dd q) {
     const dd x = two_prod((double)a, hx), y = two_prod((double)b, hy), z = two_prod((double)cc, hz);
     const dd R2 = dd_add(dd_add(dd_mul(x, x), dd_mul(y, y)), dd_mul(z, z));
     const double iR2 = 1.0 / R2.hi;
+    const double rho2 = 0.25 * hsum2 * iR2;
+    const int L = rho2 > 1.0 / 256.0 ? 8 : rho2 > 1.0 / 1024.0 ? 6 : rho2 > 1.0 / 4096.0 ? 5
+                : rho2 > 1.0 / 65536.0 ? 4 : 3;
     const double U = x.hi * x.hi * iR2, V = y.hi * y.hi * iR2, W = z.hi * z.hi * iR2;
-    double Up[7], Vp[7], Wp[7];
+    double Up[9], Vp[9], Wp[9];
     Up[0] = Vp[0] = Wp[0] = 1.0;
 #pragma unroll
-    for (int e = 1; e <= 6; ++e) {
+    for (int e = 1; e <= 8; ++e) {
         Up[e] = Up[e - 1] * U;
         Vp[e] = Vp[e - 1] * V;
         Wp[e] = Wp[e - 1] * W;
     }
-    // corr = sum_n Q_n iR2^n, Horner in iR2 from n = 6 down
+    // corr = sum_{n <= L} Q_n iR2^n, Horner in iR2 from n = L down
     double corr = 0.0;
     int base = IGF_FAR_NC;
 #pragma unroll
-    for (int n = 6; n >= 1; --n) {
+    for (int n = 8; n >= 1; --n) {
         const int nt = (n + 1) * (n + 2) / 2;
         base -= nt;
+        if (n > L) continue;
         double qn = 0.0;
         int mi = 0;
 #pragma unroll
@@ -156,14 +172,18 @@ __device__ double igf_far_cell(int a, int b, int cc, double hx, double hy, doubl
             for (int j = n - i; j >= 0; --j, ++mi) qn = fma(c[base + mi], Up[i] * Vp[j] * Wp[n - i - j], qn);
         corr = (corr + qn) * iR2;
     }
-    const dd ke = {KE_HI, KE_LO};
-    const dd vol = dd_mul_d(two_prod(hx, hy), hz);
-    const dd lead = dd_div(dd_mul(ke, vol), dd_sqrt(R2));
+    // 1/R: y0 = rsqrt(R2), y1 = y0 + y0 (1 - R2 y0^2)/2 with the residual in dd
+    const double y0 = rsqrt(R2.hi);
+    const dd t = dd_mul(R2, two_prod(y0, y0));
+    const double e = __dsub_rn(1.0, t.hi) - t.lo;
+    const dd iR = fast_two_sum(y0, 0.5 * y0 * e);
+    const dd lead = dd_mul(q, iR);
     return lead.hi + fma(lead.hi, corr, lead.lo);
 }
 
 __global__ void k_igf_sum(int n, double hx, double hy, double hz, const double2 *__restrict__ fc,
-                          double *__restrict__ g, const TrackState *gate) {
+                          const double *__restrict__ coef, double *__restrict__ g,
+                          const TrackState *gate) {
     if (gate) {
         if (!gate->green_stale || gate->halt) return;
         hx = gate->box.h[0];
@@ -171,12 +191,13 @@ __global__ void k_igf_sum(int n, double hx, double hy, double hz, const double2 
         hz = gate->box.h[2];
     }
     __shared__ double sc[IGF_FAR_NC];
-    igf_far_coefficients(hx, hy, hz, sc);
+    for (int k = threadIdx.x; k < IGF_FAR_NC; k += blockDim.x) sc[k] = coef[k];
     __syncthreads();
     const int m = n + 2, q = n + 1;
     const long long total = (long long)q * q * q;
     const dd ke = {KE_HI, KE_LO};
     const double hsum2 = hx * hx + hy * hy + hz * hz;
+    const dd qv = dd_mul(ke, dd_mul_d(two_prod(hx, hy), hz));
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         int a = (int)(idx % q);
@@ -184,7 +205,7 @@ __global__ void k_igf_sum(int n, double hx, double hy, double hz, const double2 
         int c = (int)(idx / ((long long)q * q));
         const double xa = a * hx, yb = b * hy, zc = c * hz;
         if (igf_is_far(xa * xa + yb * yb + zc * zc, hsum2)) {
-            g[idx] = igf_far_cell(a, b, c, hx, hy, hz, sc);
+            g[idx] = igf_far_cell(a, b, c, hx, hy, hz, hsum2, sc, qv);
             continue;
         }
         dd s = dd_make(0.0);
@@ -203,18 +224,21 @@ __global__ void k_igf_sum(int n, double hx, double hy, double hz, const double2 
 
 cudaError_t launch_igf_table(int n, const double h[3], double *fcorner, double *gtable,
                              cudaStream_t s, const TrackState *gate) {
-    const int q = n + 1;
+    const int q = n + 1, m = n + 2;
     const long long ts = (long long)q * q * q;
+    // series coefficients after the corner table (igf_scratch_doubles)
+    double *coef = fcorner + 2LL * m * m * m;
     // the near region's size is known on the device only (h may come from the
-    // state): a grid-stride launch of at most 148 x 8 blocks covers it
-    const int m = n + 2;
-    const long long tc = (long long)m * m * m;
-    int bc = (int)std::min<long long>((tc + 127) / 128, 148 * 8);
-    int bs = (int)std::min<long long>((ts + 255) / 256, 148 * 16);
+    // state): one-warp blocks, a few per SM, grid-stride.  A corner is a long
+    // serial chain of FP64 double-double work; small blocks spread the ~1e3
+    // corners of a typical near region over all SMs instead of a few.
+    const int bc = 148 * 4;
+    const int bs = (int)std::min<long long>((ts + 255) / 256, 148 * 16);
     const double h0 = h ? h[0] : 0.0, h1 = h ? h[1] : 0.0, h2 = h ? h[2] : 0.0;
-    BT_LAUNCH(K_IGF_CORNER, s, k_igf_corner<<<bc, 128, 0, s>>>(n, h0, h1, h2, (double2 *)fcorner, gate));
+    BT_LAUNCH(K_IGF_CORNER, s, k_igf_coef<<<1, 192, 0, s>>>(h0, h1, h2, gate, coef));
+    BT_LAUNCH(K_IGF_CORNER, s, k_igf_corner<<<bc, 32, 0, s>>>(n, h0, h1, h2, (double2 *)fcorner, gate));
     BT_LAUNCH(K_IGF_SUM, s, k_igf_sum<<<bs, 256, 0, s>>>(n, h0, h1, h2, (const double2 *)fcorner,
-                                                         gtable, gate));
+                                                         coef, gtable, gate));
     return cudaGetLastError();
 }
 
