@@ -378,6 +378,12 @@ def batch_bench(dev, count: int = 256, periods: int = 10, nslice: int = 4, seed:
     def events():
         return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
+    # binning autotuner (grouped by grid and particle-count octave); both the
+    # sequential and the batched runs use its choices
+    c0 = time.perf_counter()
+    tuned = btk.autotune_batch(trks, beams, lats, kicks=32)
+    t_tune = time.perf_counter() - c0
+    restore()
     # sequential: per-kick graphs built once per context (one-kick warm-up)
     for t, b, lat in zip(trks, beams, lats):
         t.reset()
@@ -430,6 +436,10 @@ def batch_bench(dev, count: int = 256, periods: int = 10, nslice: int = 4, seed:
             "sequential": {"ms": t_seq, "particle_steps_per_s": psteps / (t_seq * 1e-3),
                            "graph_launches": count * kicks, "wall_s": wall_seq},
             "speedup": t_seq / t_batch, "graph_build_s": t_build,
+            "autotune": {"seconds": t_tune, "groups": len(tuned),
+                         "choices": {f"{k[0]}^3,2^{k[1]}": list(v) for k, v in sorted(tuned.items())},
+                         "what": "rebin_interval (-1 never) and bin edge per (grid, particle-count "
+                                 "octave) group, timed over 32 kicks by bx_autotune_binning"},
             "what": "batched = one bx_batch_launch (one CUDA graph: a WHILE loop over the kick "
                     "per variant); sequential = bx_reset + bx_track per variant (one graph "
                     "launch per kick); same initial bunches, same kernels, bitwise equal results"}

@@ -58,15 +58,24 @@ typedef struct bx_ctx bx_ctx;
 typedef struct bx_batch bx_batch;
 
 /* Options of a context.
- * n_grid      : nodes per dimension N of the charge/potential grid; a power
- *               of two in [8, 256].  The Poisson solve runs on the doubled
- *               (2N)^3 grid.
- * shape_order : particle shape (Listing 1 set_particle_shape); 1 (CIC) only.
+ * n_grid         : nodes per dimension N of the charge/potential grid; a power
+ *                  of two in [8, 256].  The Poisson solve runs on the doubled
+ *                  (2N)^3 grid.
+ * shape_order    : particle shape (Listing 1 set_particle_shape); 1 (CIC) only.
+ * rebin_interval : kicks between re-binning the particles by grid bin (a
+ *                  stable counting sort that keeps the deposit's shared-memory
+ *                  tiles compact): 0 = default (16), -1 = never, else >= 1.
+ * bin_edge       : grid cells per bin edge: 0 = default (8, or N/16 above
+ *                  N = 128), else a power of two in [2, N/2] with at most 16^3
+ *                  bins.  Neither changes any result, only the speed
+ *                  (bx_autotune_binning picks them by timing).
  */
 typedef struct {
     int32_t n_grid;
     int32_t shape_order;
-    int32_t reserved[6];
+    int32_t rebin_interval;
+    int32_t bin_edge;
+    int32_t reserved[4];
 } bx_options;
 
 /* A bunch.  coord[0..5] = x, px, y, py, t, pt: device pointers to n doubles
@@ -324,6 +333,25 @@ int32_t bx_batch_destroy(bx_batch *batch);
 
 /* Text of the last batch error (or of bx_batch_create when batch is NULL). */
 const char *bx_batch_last_error(const bx_batch *batch);
+
+/* ---- Tuning --------------------------------------------------------------
+ * Re-binning interval and bin edge as in bx_options (takes effect at the next
+ * call; BX_BAD_ARG for invalid values). */
+int32_t bx_set_binning(bx_ctx *ctx, int32_t rebin_interval, int32_t bin_edge);
+
+/* Autotuner of the binning: tracks `kicks` kicks of the lattice from kick 0
+ * (from a fresh state) once per candidate (never re-bin, and every 8 or 32
+ * kicks with each valid bin edge among 4, 8, 16), timing each with CUDA
+ * events, and keeps the fastest (bx_set_binning).  The beam's coordinates and
+ * ids are restored afterwards and the context is reset (bx_reset), so results
+ * do not depend on the tuning.  chosen (host, 2): the chosen rebin_interval and
+ * bin_edge; ms (host, may be NULL): the time of candidate i for i < min(cap,
+ * *count), candidates in the order above; *count: number of candidates.
+ * Needs the beam's id array.  Synchronous; uses 7 n doubles of device scratch
+ * for the saved coordinates and ids while it runs. */
+int32_t bx_autotune_binning(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lattice,
+                            int32_t kicks, int32_t chosen[2], double *ms, int32_t cap,
+                            int32_t *count, void *stream);
 
 /* Wait for the stream and return the device status word (then clear it). */
 int32_t bx_sync(bx_ctx *ctx, void *stream);

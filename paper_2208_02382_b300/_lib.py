@@ -14,7 +14,8 @@ BX_DRIFT, BX_QUAD, BX_SBEND = 0, 1, 2
 
 
 class bx_options(ctypes.Structure):
-    _fields_ = [("n_grid", c_int32), ("shape_order", c_int32), ("reserved", c_int32 * 6)]
+    _fields_ = [("n_grid", c_int32), ("shape_order", c_int32), ("rebin_interval", c_int32),
+                ("bin_edge", c_int32), ("reserved", c_int32 * 4)]
 
 
 class bx_beam(ctypes.Structure):
@@ -76,6 +77,10 @@ SIGNATURES = {
     "bx_batch_launch": (c_int32, [c_void_p, c_void_p]),
     "bx_batch_destroy": (c_int32, [c_void_p]),
     "bx_batch_last_error": (c_char_p, [c_void_p]),
+    "bx_set_binning": (c_int32, [c_void_p, c_int32, c_int32]),
+    "bx_autotune_binning": (c_int32, [c_void_p, POINTER(bx_beam), POINTER(bx_lattice), c_int32,
+                                      POINTER(c_int32), POINTER(c_double), c_int32,
+                                      POINTER(c_int32), c_void_p]),
     "bx_last_error": (c_char_p, [c_void_p]),
 }
 

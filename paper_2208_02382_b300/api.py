@@ -154,11 +154,14 @@ class Grid:
 class Tracker:
     """A libbeamtrack context (bx_create) on the current CUDA device."""
 
-    def __init__(self, n_grid: int, shape_order: int = 1):
+    def __init__(self, n_grid: int, shape_order: int = 1, rebin_interval: int = 0,
+                 bin_edge: int = 0):
         self.lib = L.load()
         opt = L.bx_options()
         opt.n_grid = int(n_grid)
         opt.shape_order = int(shape_order)
+        opt.rebin_interval = int(rebin_interval)
+        opt.bin_edge = int(bin_edge)
         ctx = ctypes.c_void_p()
         rc = self.lib.bx_create(ctypes.byref(ctx), ctypes.byref(opt))
         _check(self.lib, None, rc)
@@ -250,6 +253,24 @@ class Tracker:
     def sync(self):
         _check(self.lib, self.ctx, self.lib.bx_sync(self.ctx, _stream()))
 
+    # ---- tuning
+    def set_binning(self, rebin_interval: int, bin_edge: int):
+        _check(self.lib, self.ctx, self.lib.bx_set_binning(self.ctx, int(rebin_interval),
+                                                           int(bin_edge)))
+
+    def autotune_binning(self, beam: Beam, elements, kicks: int = 32, space_charge: bool = True):
+        """Time the binning candidates on this problem and keep the fastest;
+        returns ((rebin_interval, bin_edge), [ms per candidate])."""
+        b = beam.c_struct()
+        lat, keep = lattice_struct(elements, space_charge)
+        chosen = (ctypes.c_int32 * 2)()
+        ms = (ctypes.c_double * 16)()
+        cnt = ctypes.c_int32()
+        rc = self.lib.bx_autotune_binning(self.ctx, ctypes.byref(b), ctypes.byref(lat), int(kicks),
+                                          chosen, ms, 16, ctypes.byref(cnt), _stream())
+        _check(self.lib, self.ctx, rc)
+        return (chosen[0], chosen[1]), [ms[i] for i in range(min(16, cnt.value))]
+
     # ---- differentiation
     def grad_forward(self, beam: Beam, elements, checkpoint_interval: int = 20,
                      box_replay=None, space_charge: bool = True):
@@ -288,6 +309,25 @@ class Tracker:
         _check(self.lib, self.ctx, self.lib.bx_grad_boxes(self.ctx, buf, cnt.value,
                                                           ctypes.byref(cnt)))
         return [[buf[12 * i + j] for j in range(12)] for i in range(cnt.value)]
+
+
+def autotune_batch(trackers: Sequence[Tracker], beams: Sequence[Beam], lattices, kicks: int = 32):
+    """Binning autotuning for a batch: problems with the same grid size and
+    particle count within a factor of two share one tuning (of the first of
+    them).  Returns {(n_grid, bucket): (rebin_interval, bin_edge)}."""
+    import math
+    groups = {}
+    for t, b, lat in zip(trackers, beams, lattices):
+        key = (t.n, int(math.floor(math.log2(max(1, b.n)))))
+        groups.setdefault(key, []).append((t, b, lat))
+    chosen = {}
+    for key, members in groups.items():
+        t, b, lat = members[0]
+        choice, _ = t.autotune_binning(b, lat, kicks)
+        chosen[key] = choice
+        for t2, _, _ in members[1:]:
+            t2.set_binning(*choice)
+    return chosen
 
 
 class Batch:

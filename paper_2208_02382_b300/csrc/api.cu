@@ -29,9 +29,15 @@ int32_t bx_create(bx_ctx **out, const bx_options *opt) {
     if (n < 8 || n > 256 || (n & (n - 1)) != 0)
         return fail(nullptr, BX_BAD_ARG, "n_grid must be a power of two in [8, 256]");
     if (opt->shape_order != 1) return fail(nullptr, BX_BAD_ARG, "shape_order must be 1 (CIC)");
+    if (opt->rebin_interval < -1) return fail(nullptr, BX_BAD_ARG, "rebin_interval must be >= -1");
+    if (opt->bin_edge != 0 && !sort_brick_edge_valid(n, opt->bin_edge))
+        return fail(nullptr, BX_BAD_ARG,
+                    "bin_edge must be 0 or a power of two in [2, n/2] giving at most 16^3 bins");
     bx_ctx *ctx = new (std::nothrow) bx_ctx();
     if (!ctx) return fail(nullptr, BX_OUT_OF_MEMORY, "host allocation");
     ctx->n = n;
+    ctx->sort_interval = opt->rebin_interval == 0 ? 16 : opt->rebin_interval < 0 ? 0 : opt->rebin_interval;
+    ctx->bin_edge = opt->bin_edge;
     ctx->prof = profiler_new();
     const size_t n3 = (size_t)n * n * n, q3 = (size_t)(n + 2) * (n + 2) * (n + 2);
     const size_t o3 = (size_t)(n + 1) * (n + 1) * (n + 1);

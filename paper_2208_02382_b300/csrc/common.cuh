@@ -180,15 +180,17 @@ cudaError_t launch_track_deposit(double *const c[6], int64_t n, double betagamma
                                  TrackState *st, int32_t *status, cudaStream_t s);
 int map_kind(const MapCoef &m);
 // sort.cu
-int sort_brick_edge(int nn);
+int sort_brick_edge(int nn, int be_opt);
+bool sort_brick_edge_valid(int nn, int be);
 cudaError_t sort_set_pointers(double *const c[6], double *const scratch[6], double **dev_ptrs,
                               cudaStream_t s);
-int sort_bricks(int nn);
+int sort_bricks(int nn, int be);
 int64_t sort_chunks(int64_t n);
 cudaError_t launch_sort(double *const c[6], long long *id, int64_t n, double betagamma,
-                        const Box *box, int nn, int *keys, long long *counts, long long *offs,
-                        long long *sums, double *const scratch[6], long long *id_scratch,
-                        double **dev_ptrs, cudaStream_t s, const int *gate = nullptr);
+                        const Box *box, int nn, int be, int *keys, long long *counts,
+                        long long *offs, long long *sums, double *const scratch[6],
+                        long long *id_scratch, double **dev_ptrs, cudaStream_t s,
+                        const int *gate = nullptr);
 // moments.cu
 cudaError_t launch_moments(double *const c[6], int64_t n, double *partials, int nblocks,
                            double *out, cudaStream_t s);

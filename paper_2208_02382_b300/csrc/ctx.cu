@@ -190,7 +190,9 @@ int32_t ensure_maps(bx_ctx *ctx, size_t count) {
 
 // Binning scratch for n particles, allocated on the first call for a larger n.
 int32_t ensure_sort_scratch(bx_ctx *ctx, int64_t n) {
-    if (n <= ctx->sort_n) return BX_OK;
+    const int nb = sort_bricks(ctx->n, sort_brick_edge(ctx->n, ctx->bin_edge));
+    if (n <= ctx->sort_n && nb == ctx->sort_nb) return BX_OK;
+    if (n < ctx->sort_n) n = ctx->sort_n;
     cudaDeviceSynchronize();
     void **ps[] = {(void **)&ctx->keys, (void **)&ctx->counts, (void **)&ctx->offs,
                    (void **)&ctx->sums, (void **)&ctx->id_scr, (void **)&ctx->scr[0],
@@ -202,7 +204,7 @@ int32_t ensure_sort_scratch(bx_ctx *ctx, int64_t n) {
             *p = nullptr;
         }
     ctx->sort_n = 0;
-    const long long len = (long long)sort_bricks(ctx->n) * sort_chunks(n);
+    const long long len = (long long)nb * sort_chunks(n);
     CK(cudaMalloc(&ctx->keys, n * sizeof(int)), "sort keys");
     CK(cudaMalloc(&ctx->counts, len * sizeof(long long)), "sort counts");
     CK(cudaMalloc(&ctx->offs, len * sizeof(long long)), "sort offsets");
@@ -210,6 +212,7 @@ int32_t ensure_sort_scratch(bx_ctx *ctx, int64_t n) {
     CK(cudaMalloc(&ctx->id_scr, n * sizeof(long long)), "sort ids");
     for (int k = 0; k < 6; ++k) CK(cudaMalloc(&ctx->scr[k], n * sizeof(double)), "sort arrays");
     ctx->sort_n = n;
+    ctx->sort_nb = nb;
     return BX_OK;
 }
 

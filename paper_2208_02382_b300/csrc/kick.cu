@@ -26,7 +26,8 @@ cudaError_t kick_green(const KickArgs &k, cudaStream_t s) {
 
 cudaError_t kick_sort(const KickArgs &k, cudaStream_t s) {
     bx_ctx *ctx = k.ctx;
-    return launch_sort(k.c, (long long *)k.id, k.n, k.bg, &ctx->st->box, ctx->n, ctx->keys,
+    return launch_sort(k.c, (long long *)k.id, k.n, k.bg, &ctx->st->box, ctx->n,
+                       sort_brick_edge(ctx->n, ctx->bin_edge), ctx->keys,
                        ctx->counts, ctx->offs, ctx->sums, ctx->scr, ctx->id_scr, ctx->dev_ptrs, s,
                        &ctx->st->sort_gate);
 }

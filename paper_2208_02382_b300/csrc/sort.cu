@@ -4,9 +4,10 @@
 // shared-memory tile.  Stable and deterministic: the order after sorting is a
 // fixed function of the order before (ties keep their relative order).
 //
-//   keys:    brick of each particle's cell (bricks of be^3 cells, be = 8, or
-//            n/16 above n = 128, so there are at most 16^3 bricks), plus a
-//            per-chunk brick histogram (chunks of SORT_CHUNK particles)
+//   keys:    brick of each particle's cell (bricks of be^3 cells; be = 8, or
+//            n/16 above n = 128, unless the context sets it; at most 16^3
+//            bricks), plus a per-chunk brick histogram (chunks of SORT_CHUNK
+//            particles)
 //   scan:    exclusive prefix over the histograms in brick-major, chunk-minor
 //            order -> the destination of each (brick, chunk) run
 //   scatter: within a chunk, each particle's rank among the earlier particles
@@ -23,10 +24,16 @@ constexpr int SORT_ROUNDS = 64;
 constexpr int SORT_CHUNK = SORT_TPB * SORT_ROUNDS;   // 16384 particles per block
 constexpr int SCAN_TILE = 2048;                      // elements per scan block
 
-int sort_brick_edge(int nn) { return nn <= 128 ? 8 : nn / 16; }
-int sort_bricks(int nn) {
-    int nb = nn / sort_brick_edge(nn);
+int sort_brick_edge(int nn, int be_opt) {
+    if (be_opt > 0) return be_opt;
+    return nn <= 128 ? 8 : nn / 16;
+}
+int sort_bricks(int nn, int be) {
+    int nb = nn / be;
     return nb * nb * nb;
+}
+bool sort_brick_edge_valid(int nn, int be) {
+    return be >= 2 && be <= nn / 2 && (be & (be - 1)) == 0 && sort_bricks(nn, be) <= 4096;
 }
 int64_t sort_chunks(int64_t n) { return (n + SORT_CHUNK - 1) / SORT_CHUNK; }
 
@@ -198,13 +205,14 @@ cudaError_t sort_set_pointers(double *const c[6], double *const scratch[6], doub
 }
 
 cudaError_t launch_sort(double *const c[6], long long *id, int64_t n, double betagamma,
-                        const Box *box, int nn, int *keys, long long *counts, long long *offs,
-                        long long *sums, double *const scratch[6], long long *id_scratch,
-                        double **dev_ptrs, cudaStream_t s, const int *gate) {
+                        const Box *box, int nn, int be, int *keys, long long *counts,
+                        long long *offs, long long *sums, double *const scratch[6],
+                        long long *id_scratch, double **dev_ptrs, cudaStream_t s,
+                        const int *gate) {
     if (n <= 0) return cudaSuccess;
     (void)c;
     (void)scratch;
-    const int be = sort_brick_edge(nn), nb = sort_bricks(nn);
+    const int nb = sort_bricks(nn, be);
     const int64_t nch = sort_chunks(n);
     const size_t hsm = (size_t)nb * sizeof(int);
     cudaFuncSetAttribute(k_sort_keys, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);

@@ -112,3 +112,35 @@ def test_batch_rejects_bad_arguments(bt):
         bt.Batch([trk, trk], [beam, beam], [probs[0][2], probs[0][2]])
     with pytest.raises(Exception):
         bt.Batch([], [], [])
+
+
+def test_binning_autotuner_keeps_results_and_beam(bt):
+    sp, probs = _problems(bt)
+    n, grid, lat, c, _ = probs[3]            # 20000 particles, 32^3
+    trk = bt.Tracker(grid)
+    beam = _beam(bt, sp, c)
+    before = beam.coords.clone()
+    ids_before = beam.ids.clone()
+    (iv, be), ms = trk.autotune_binning(beam, lat, kicks=12)
+    assert torch.equal(beam.coords, before) and torch.equal(beam.ids, ids_before)
+    assert len(ms) >= 2 and all(v > 0 for v in ms)
+    assert iv in (-1, 8, 32) and (iv == -1 or be in (4, 8, 16))
+    trk.track(beam, lat)
+    trk.sync()
+    ref = bt.Tracker(grid)
+    b2 = _beam(bt, sp, c)
+    ref.track(b2, lat)
+    ref.sync()
+    # binning changes particle order, never the physics
+    assert np.array_equal(_in_id_order(beam), _in_id_order(b2))
+    assert trk.regrid_log() == ref.regrid_log()
+
+
+def test_binning_options_validated(bt):
+    with pytest.raises(Exception):
+        bt.Tracker(32, bin_edge=3)
+    with pytest.raises(Exception):
+        bt.Tracker(32, rebin_interval=-2)
+    t = bt.Tracker(64, rebin_interval=-1, bin_edge=4)
+    with pytest.raises(Exception):
+        t.set_binning(8, 64)

@@ -89,6 +89,18 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.bx_destroy(None) == L.BX_OK
 
 
+@pytest.mark.parametrize("n_grid,interval,edge", [(32, -2, 0), (32, 0, 3), (32, 0, 32),
+                                                  (256, 0, 4), (64, 8, 1)])
+def test_create_rejects_bad_binning_on_host(lib, n_grid, interval, edge):
+    opt = L.bx_options()
+    opt.n_grid, opt.shape_order = n_grid, 1
+    opt.rebin_interval, opt.bin_edge = interval, edge
+    ctx = ctypes.c_void_p()
+    assert lib.bx_create(ctypes.byref(ctx), ctypes.byref(opt)) == L.BX_BAD_ARG
+    assert b"bin" in lib.bx_last_error(None)
+
+
+# last: reloads the binding module (new ctypes classes)
 def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
     import importlib
     monkeypatch.setattr(L, "_LIB", None)
