@@ -271,8 +271,9 @@ int32_t bx_twiss_grad(const double twiss[8], const double S[36], double out[6]);
 
 /* Forward pass for differentiation: tracks the beam through the whole
  * lattice (all kicks, from a fresh state: no box, kick counter 0; space
- * charge as lattice->space_charge says), like bx_track but without particle
- * re-binning, and records in the context: the initial bunch, a checkpoint
+ * charge as lattice->space_charge says), like bx_track but re-binning the
+ * particles only once, before the first kick (when beam->id is given; the
+ * particle order is then fixed for the run), and records in the context: the initial bunch, a checkpoint
  * (state and device tracking state) every `checkpoint_interval` kicks, the box
  * of every kick and every Green's function spectrum built.  box_replay (host,
  * may be NULL): 12 doubles per kick {lo[3], hi[3], h[3], 1/h[3]} as returned by

@@ -321,6 +321,27 @@ int32_t bx_grad_forward(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat,
     }
     double *const *c = beam->coord;
     const size_t bytes = (size_t)beam->n * sizeof(double);
+    if (beam->id) {
+        // bin the initial bunch once by grid brick (of a box around it), so the
+        // deposits and the reverse scatter touch compact sets of cells; the
+        // order then stays fixed for the whole run (no later re-binning)
+        if ((rc = ensure_sort_scratch(ctx, beam->n))) return rc;
+        CK(sort_set_pointers(c, ctx->scr, ctx->dev_ptrs, s), "sort pointers");
+        CK(launch_minmax(c, beam->n, g->ref.bg, ctx->st, ctx->status, s), "minmax");
+        CK(launch_box_rule(ctx->st, ctx->n, beam->n, ctx->log, ctx->log_cap, false, s), "box");
+        CK(launch_sort(c, (long long *)beam->id, beam->n, g->ref.bg, &ctx->st->box, ctx->n,
+                       sort_brick_edge(ctx->n, ctx->bin_edge), ctx->keys, ctx->counts,
+                       ctx->offs, ctx->sums, ctx->scr, ctx->id_scr, ctx->dev_ptrs, s),
+           "initial binning");
+        CK(cudaMemcpyAsync(ctx->st, &h, sizeof(h), cudaMemcpyHostToDevice, s), "state");
+        CK(launch_call_init(ctx->st, (int)K, g->q_macro, 0, 0, s), "call init");
+        CK(set_state_ptr<Box>(ctx->st, &TrackState::box_hist, g->box_hist, s), "state");
+        CK(set_state_ptr<int32_t>(ctx->st, &TrackState::slot_hist, g->slot_hist, s), "state");
+        const Box *rp = box_replay ? g->box_replay : nullptr;
+        CK(cudaMemcpyAsync(&ctx->st->box_replay, &rp, sizeof(rp), cudaMemcpyHostToDevice, s),
+           "state");
+        CK(cudaStreamSynchronize(s), "sync");
+    }
     for (int k = 0; k < 6; ++k)
         CK(cudaMemcpyAsync(g->z0 + (size_t)k * beam->n, c[k], bytes, cudaMemcpyDeviceToDevice, s),
            "save z0");

@@ -63,12 +63,14 @@ def _gpu_grad(bt, trk, xi_t, lat, sp, charge, w, C, replay=None, space_charge=Tr
     coords = bt.twiss_beam(bg.TWISS_FODO, xi_t)
     beam = bt.Beam(coords, sp, charge)
     trk.grad_forward(beam, lat, C, box_replay=replay, space_charge=space_charge)
-    final = beam.coords.cpu().numpy().copy()
+    # the recording forward bins the particles once: compare in id order
+    order = np.argsort(beam.ids.cpu().numpy())
+    final = beam.coords.cpu().numpy()[:, order]
     boxes = trk.grad_boxes()
     dk, S, zb = trk.grad_backward(beam, w)
     dtw = bt.twiss_grad(bg.TWISS_FODO, S)
     return {"dk": np.array(dk), "S": np.array(S), "dtwiss": np.array(dtw),
-            "zbar0": zb.cpu().numpy(), "final": final, "boxes": boxes}
+            "zbar0": zb.cpu().numpy()[:, order], "final": final, "boxes": boxes}
 
 
 @pytest.mark.parametrize("space_charge", [True, False])
