@@ -156,9 +156,9 @@ def repeated_lattice(w: bg.Workload, kicks: int):
     return w.lattice * reps
 
 
-def traffic_for(kernel: str, n_units_launch: float):
-    """DRAM bytes per launch from the committed ncu capture, scaled to this
-    launch; null when the kernel source changed since the capture."""
+def ncu_entry(kernel: str):
+    """The committed ncu figures of a kernel, or None when its source changed
+    since the capture."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         tab = json.load(open(path))
@@ -170,9 +170,14 @@ def traffic_for(kernel: str, n_units_launch: float):
         return None
     h = hashlib.sha256(open(os.path.join(ROOT, "paper_2208_02382_b300", "csrc", src),
                             "rb").read()).hexdigest()[:16]
-    if e.get("source_sha") != h:
-        return None
-    return e["bytes_per_unit"] * n_units_launch
+    return e if e.get("source_sha") == h else None
+
+
+def traffic_for(kernel: str, n_units_launch: float):
+    """DRAM bytes per launch from the committed ncu capture, scaled to this
+    launch; null when the kernel source changed since the capture."""
+    e = ncu_entry(kernel)
+    return None if e is None else e["bytes_per_unit"] * n_units_launch
 
 
 def cpu_baseline(w: bg.Workload, sample_particles: int, kicks_timed: int = 1):
@@ -532,11 +537,21 @@ def run_ours(args, w):
                 b2, u2, f2 = ALGO[k2]
                 a2 = f2(npart, w.n_grid) / (ms2 / c2 * 1e-3) / (1e12 if u2 == "TFLOP/s" else 1e9)
                 p2 = FP64_PEAK_TFLOPS if u2 == "TFLOP/s" else peaks.get("hbm_gbs", 6400.0)
+                n2 = ncu_entry(k2)
                 others[k2] = {"bound": b2, "achieved": round(a2, 3), "unit": u2,
-                              "frac": round(a2 / p2, 4), "share_of_step": round(ms2 / ms_prof, 4)}
+                              "frac": round(a2 / p2, 4), "share_of_step": round(ms2 / ms_prof, 4),
+                              "fp64_pipe_active_frac": (n2["fp64_pipe_active_pct"] / 100.0)
+                              if n2 else None}
+        ne = ncu_entry(dname)
         roof = {"kernel": dname, "bound": bound, "achieved": achieved, "peak": peak,
                 "unit": unit, "frac": achieved / peak, "peak_source": peak_src,
-                "traffic": traffic_for(dname, units), "avg_launch_ms": dms / dcnt,
+                "traffic": traffic_for(dname, units),
+                "fp64_pipe_active_frac": (ne["fp64_pipe_active_pct"] / 100.0) if ne else None,
+                "binding": ("FP64 pipe (ncu: FP64 pipe active %.0f%% vs DRAM %.0f%% of "
+                            "measured copy bandwidth)" % (ne["fp64_pipe_active_pct"],
+                                                           100 * achieved / peak))
+                           if ne and unit == "GB/s" else None,
+                "avg_launch_ms": dms / dcnt,
                 "launches": dcnt, "share_of_step": dms / ms_prof, "other_kernels": others}
     # end to end through the public API from pinned host memory
     e2e = None
