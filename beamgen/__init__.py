@@ -101,6 +101,18 @@ def standard_normal6(n: int, seed: int = 0) -> np.ndarray:
     return np.ascontiguousarray(_rng(seed).standard_normal((6, int(n))))
 
 
+# Listing 1 (FODO.py): Waterbag parameters (sigmaX, sigmaY, sigmaT, sigmaPx,
+# sigmaPy, sigmaPt, muxpx, muypy, mutpt) of the rms-matched 2 GeV electron beam
+# with 2 nm unnormalised emittance, 1e4 particles, 1 nC, 25 slices per element.
+LISTING1_WATERBAG = (3.9984884770e-5, 3.9984884770e-5, 1.0e-3, 2.6623538760e-5,
+                     2.6623538760e-5, 2.0e-3, -0.846574929020762, 0.846574929020762, 0.0)
+
+
+def uniform01(n: int, seed: int = 0) -> np.ndarray:
+    """n uniform draws in [0, 1) (the radii of a Waterbag bunch)."""
+    return _rng(seed + 7919).random(int(n))
+
+
 def chicane_lattice(nslice=50):
     """Four sector bends (L=0.5 m, +-0.1 rad) separated by 1 m drifts, preceded
     by two matching quadrupoles (L=0.5 m, k=+-0.5 /m^2)."""

@@ -21,6 +21,7 @@ Modules:
                Hockney doubled-grid solve, field, gather + kick
   igf_quad.c   the integrated Green's function antiderivative in __float128
   track        the split-operator tracking loop and beam moments
+  distribution Waterbag and Gaussian bunches in the Listing-1 parametrisation
   adjoint      reverse-mode gradients of final rms sizes / emittances with
                respect to quadrupole strengths and initial Twiss parameters
 

@@ -60,10 +60,12 @@ class Tracker:
         return sc.kick(coords, e_at, ds, self.ref)
 
     def track(self, coords: np.ndarray, lattice, first_kick: int = 0,
-              nkicks: int | None = None) -> np.ndarray:
+              nkicks: int | None = None, diagnostics: list | None = None) -> np.ndarray:
         """Track (6, n) coordinates through slices [first_kick, first_kick+nkicks)
         of the lattice's slice schedule.  Each slice: map(ds/2), kick(ds) when
-        space charge is on, map(ds/2)."""
+        space charge is on, map(ds/2).  With `diagnostics`, the moments_vector
+        of the bunch at the end of every slice is appended to it (Listing 1
+        set_slice_step_diagnostics)."""
         sched = ph.slice_schedule(lattice)
         stop = len(sched) if nkicks is None else min(len(sched), first_kick + nkicks)
         c = np.array(coords, dtype=np.float64, copy=True)
@@ -75,6 +77,8 @@ class Tracker:
                 c = self.space_charge_kick(c, ds)
             c = ph.push(c, half)
             self.kick_index += 1
+            if diagnostics is not None:
+                diagnostics.append(moments_vector(c))
         return c
 
 
