@@ -158,6 +158,32 @@ int32_t bx_reset(bx_ctx *ctx);
 int32_t bx_track(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lattice,
                  int64_t first_kick, int64_t nkicks, void *stream);
 
+/* bx_track that also writes the beam moments at the end of every slice
+ * (Listing 1 set_slice_step_diagnostics) to moments_device: nkicks x 27
+ * doubles in the layout of bx_moments (means, then the centred second
+ * moments), entry k for the end of slice first_kick + k.  The moments after
+ * each kick are taken back to the slice end through the inverse of the next
+ * half map (linear maps carry moments exactly).  Launches each kick's kernels
+ * one by one.  BX_BAD_ARG for an empty beam. */
+int32_t bx_track_diagnostics(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lattice,
+                             int64_t first_kick, int64_t nkicks, double *moments_device,
+                             void *stream);
+
+/* Initial bunch in the parametrisation of Listing 1 (distribution.Waterbag):
+ * params (host, 9) = {sigmaX, sigmaY, sigmaT, sigmaPx, sigmaPy, sigmaPt,
+ * muxpx, muypy, mutpt}.  Per plane, from unit-rms uncorrelated (a, b):
+ * u = sigmaU/sqrt(1-mu^2) a, pu = sigmaPu (b - mu/sqrt(1-mu^2) a) (reading:
+ * rms u = sigmaU/sqrt(1-mu^2), correlation -mu).  kind 0 (Gaussian): (a, b)
+ * are the normals.  kind 1 (Waterbag, uniform in a 6D ball of unit rms per
+ * coordinate): the direction of the six normals times sqrt(8) u^(1/6).
+ * normals: six device arrays of n standard-normal draws; uniforms: device
+ * array of n draws in [0, 1) (kind 1; may be NULL for kind 0); out: six device
+ * arrays of n.  BX_BAD_ARG for |mu| >= 1 or an unknown kind; errors via
+ * bx_last_error(NULL).  Asynchronous. */
+int32_t bx_distribution_beam(int32_t kind, const double params[9],
+                             const double *const normals[6], const double *uniforms, int64_t n,
+                             double *const out[6], void *stream);
+
 /* Charge deposition (ABLASTR charge deposition reused by ImpactX; Listing 1
  * particle shape 1 = CIC): rho[node] = q * sum_p wx*wy*wz / (hx*hy*hz) over
  * the 8 nodes of each particle's cell, q = charge_sign*bunch_charge_C/n,

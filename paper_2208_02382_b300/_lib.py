@@ -81,6 +81,10 @@ SIGNATURES = {
     "bx_autotune_binning": (c_int32, [c_void_p, POINTER(bx_beam), POINTER(bx_lattice), c_int32,
                                       POINTER(c_int32), POINTER(c_double), c_int32,
                                       POINTER(c_int32), c_void_p]),
+    "bx_track_diagnostics": (c_int32, [c_void_p, POINTER(bx_beam), POINTER(bx_lattice), c_int64,
+                                       c_int64, c_void_p, c_void_p]),
+    "bx_distribution_beam": (c_int32, [c_int32, POINTER(c_double), POINTER(c_void_p), c_void_p,
+                                       c_int64, POINTER(c_void_p), c_void_p]),
     "bx_last_error": (c_char_p, [c_void_p]),
 }
 

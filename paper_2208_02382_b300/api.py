@@ -60,6 +60,23 @@ def twiss_beam(twiss, xi: torch.Tensor) -> torch.Tensor:
     return out
 
 
+def distribution_beam(kind: str, params, normals: torch.Tensor,
+                      uniforms: torch.Tensor | None = None) -> torch.Tensor:
+    """(6, n) bunch in the Listing-1 parametrisation: kind "gaussian" or
+    "waterbag", params = (sigmaX, sigmaY, sigmaT, sigmaPx, sigmaPy, sigmaPt,
+    muxpx, muypy, mutpt), normals (6, n) standard normal draws, uniforms (n,)
+    draws in [0, 1) for the Waterbag."""
+    lib = L.load()
+    k = {"gaussian": 0, "waterbag": 1}[kind]
+    normals = normals.contiguous()
+    out = torch.empty_like(normals)
+    pp = (ctypes.c_double * 9)(*[float(v) for v in params])
+    up = ctypes.c_void_p(uniforms.contiguous().data_ptr()) if uniforms is not None else None
+    _check(lib, None, lib.bx_distribution_beam(k, pp, _ptr6(normals), up, normals.shape[1],
+                                                _ptr6(out), _stream()))
+    return out
+
+
 def twiss_grad(twiss, S) -> list:
     """dL/d(alpha_x, beta_x, eps_x, alpha_y, beta_y, eps_y) from
     S[i][j] = sum_p dL/dz0_i z0_j."""
@@ -183,12 +200,24 @@ class Tracker:
         _check(self.lib, self.ctx, self.lib.bx_reset(self.ctx))
 
     def track(self, beam: Beam, elements, first_kick: int = 0, nkicks: int = -1,
-              space_charge: bool = True):
+              space_charge: bool = True, diagnostics: bool = False):
+        """Track; with diagnostics, return the (kicks, 27) moments at every
+        slice end (layout of moments())."""
         b = beam.c_struct()
         lat, keep = lattice_struct(elements, space_charge)
-        rc = self.lib.bx_track(self.ctx, ctypes.byref(b), ctypes.byref(lat), int(first_kick),
-                               int(nkicks), _stream())
+        if not diagnostics:
+            rc = self.lib.bx_track(self.ctx, ctypes.byref(b), ctypes.byref(lat), int(first_kick),
+                                   int(nkicks), _stream())
+            _check(self.lib, self.ctx, rc)
+            return None
+        total = sum(int(e.nslice) for e in elements)
+        nk = total - int(first_kick) if nkicks < 0 else int(nkicks)
+        out = torch.empty((max(nk, 0), 27), dtype=torch.float64, device=beam.coords.device)
+        rc = self.lib.bx_track_diagnostics(self.ctx, ctypes.byref(b), ctypes.byref(lat),
+                                           int(first_kick), int(nkicks),
+                                           ctypes.c_void_p(out.data_ptr()), _stream())
         _check(self.lib, self.ctx, rc)
+        return out
 
     def deposit(self, beam: Beam, grid: Grid) -> Grid:
         b = beam.c_struct()

@@ -503,6 +503,33 @@ __global__ void k_twiss_beam(P6 xi, int64_t n, double sx, double spx, double ax,
     }
 }
 
+// Listing-1 parametrisation (see bx_distribution_beam): c[3 plane + 0] =
+// sigmaU/sqrt(1-mu^2), c[3 plane + 1] = sigmaPu, c[3 plane + 2] = mu/sqrt(1-mu^2).
+__global__ void k_distribution(int kind, P6 z, const double *__restrict__ uni, int64_t n,
+                               Coef9 c9, P6 out) {
+    const double *c = c9.c;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double a[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a[k] = z.p[k][p];
+        if (kind == 1) {
+            double r2 = 0.0;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) r2 += a[k] * a[k];
+            const double s = sqrt(8.0) * pow(uni[p], 1.0 / 6.0) / sqrt(r2);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) a[k] *= s;
+        }
+#pragma unroll
+        for (int pl = 0; pl < 3; ++pl) {
+            const double u = a[2 * pl], pu = a[2 * pl + 1];
+            out.p[2 * pl][p] = c[3 * pl] * u;
+            out.p[2 * pl + 1][p] = c[3 * pl + 1] * (pu - c[3 * pl + 2] * u);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- launchers
 
 static int grid_lin(long long n) {
@@ -573,6 +600,13 @@ cudaError_t launch_ghat_fetch(const int32_t *slot_hist, long long k, const doubl
 
 cudaError_t launch_set_deposit_gate(TrackState *st, cudaStream_t s) {
     BT_LAUNCH(K_BOX, s, k_set_deposit_gate<<<1, 32, 0, s>>>(st));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_distribution(int kind, P6 z, const double *uni, int64_t n, Coef9 c, P6 out,
+                                cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    BT_LAUNCH(K_ADJ_PART, s, k_distribution<<<grid_lin(n), 256, 0, s>>>(kind, z, uni, n, c, out));
     return cudaGetLastError();
 }
 

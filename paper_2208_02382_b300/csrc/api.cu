@@ -106,8 +106,33 @@ int32_t bx_reset(bx_ctx *ctx) {
     return BX_OK;
 }
 
-int32_t bx_track(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t first_kick,
-                 int64_t nkicks, void *stream) {
+}  // extern "C"
+
+namespace {
+
+// Moments at every slice end (Listing 1 set_slice_step_diagnostics): after
+// kick k the bunch holds P_{k+1} = H_first(k+1) S_k with S_k the state at the
+// end of slice k, so the moments of S_k are those of P_{k+1} taken back through
+// the inverse half map (H^-1 = the element's map over -ds/2); after the last
+// kick of the call the bunch is at the slice end itself.
+int32_t slice_diagnostics(bx_ctx *ctx, const bx_lattice *lat, const std::vector<int> &sel,
+                          const std::vector<double> &sds, int64_t first, int64_t nkicks,
+                          const Ref &r, std::vector<MapCoef> &inv) {
+    inv.assign(nkicks, MapCoef{});
+    for (int64_t k = 0; k < nkicks; ++k) {
+        Mat m;
+        if (k + 1 < nkicks) {
+            element_map(lat->elements[sel[first + k + 1]], -0.5 * sds[first + k + 1], r, m);
+        } else {
+            mat_identity(m);
+        }
+        inv[k] = to_coef(m);
+    }
+    return BX_OK;
+}
+
+int32_t track_impl(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t first_kick,
+                   int64_t nkicks, double *diag, void *stream) {
     if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
     ProfScope prof_scope(ctx->prof);
     int32_t rc = check_beam(ctx, beam);
@@ -136,9 +161,38 @@ int32_t bx_track(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t firs
         return BX_OK;
     }
     double *const *c = beam->coord;
+    std::vector<MapCoef> inv;
+    MapCoef *inv_dev = nullptr;
+    if (diag) {
+        slice_diagnostics(ctx, lat, sel, sds, first_kick, nkicks, r, inv);
+        if ((rc = ensure_maps(ctx, tab.size() + inv.size()))) return rc;
+        // (re-)upload the map table: the buffer may have grown
+        CK(cudaMemcpyAsync(ctx->maps, tab.data(), tab.size() * sizeof(MapCoef),
+                           cudaMemcpyHostToDevice, s),
+           "upload maps");
+        inv_dev = ctx->maps + tab.size();
+        CK(cudaMemcpyAsync(inv_dev, inv.data(), inv.size() * sizeof(MapCoef),
+                           cudaMemcpyHostToDevice, s),
+           "upload inverse maps");
+        if ((rc = ensure_moment_scratch(ctx, beam->n))) return rc;
+    }
+    const int mom_nb = moments_blocks(beam->n);
+    auto diag_after = [&](int64_t k) -> cudaError_t {
+        cudaError_t e = launch_moments(c, beam->n, ctx->mom_partial, mom_nb, diag + 27 * k, s);
+        if (e == cudaSuccess) e = launch_moments_transform(diag + 27 * k, inv_dev + k, s);
+        return e;
+    };
     if (!lat->space_charge) {
-        // maps only: H_first, merged pairs, H_last in one pass per particle
-        CK(launch_push_maps(c, beam->n, ctx->maps, (int)tab.size(), s), "push");
+        if (!diag) {
+            // maps only: H_first, merged pairs, H_last in one pass per particle
+            CK(launch_push_maps(c, beam->n, ctx->maps, (int)tab.size(), s), "push");
+        } else {
+            CK(launch_push_maps(c, beam->n, ctx->maps, 1, s), "push");
+            for (int64_t k = 0; k < nkicks; ++k) {
+                CK(launch_push_maps(c, beam->n, ctx->maps + 1 + k, 1, s), "push");
+                CK(diag_after(k), "slice diagnostics");
+            }
+        }
         ctx->kick += nkicks;
         return BX_OK;
     }
@@ -157,10 +211,11 @@ int32_t bx_track(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t firs
     CK(launch_push_maps(c, beam->n, ctx->maps, 1, s), "push");
     CK(launch_minmax(c, beam->n, r.bg, ctx->st, ctx->status, s), "minmax");
     const KickArgs ka{ctx, c, beam->id, beam->n, r.bg, binning};
-    bool use_graph = !ctx->graphs_off && !profiler_timing(ctx->prof);
+    bool use_graph = !ctx->graphs_off && !profiler_timing(ctx->prof) && !diag;
     if (use_graph) {
         bool same = ctx->kick_exec && ctx->graph_n == beam->n && ctx->graph_id == beam->id &&
-                    ctx->graph_bg == r.bg;
+                    ctx->graph_bg == r.bg && ctx->graph_maps == ctx->maps &&
+                    ctx->graph_sort_n == ctx->sort_n;
         for (int q = 0; q < 6 && same; ++q) same = ctx->graph_c[q] == c[q];
         if (!same) {
             if (ctx->kick_exec) cudaGraphExecDestroy(ctx->kick_exec);
@@ -176,16 +231,36 @@ int32_t bx_track(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t firs
                 ctx->graph_id = beam->id;
                 ctx->graph_n = beam->n;
                 ctx->graph_bg = r.bg;
+                ctx->graph_maps = ctx->maps;
+                ctx->graph_sort_n = ctx->sort_n;
             }
         }
     }
     for (int64_t k = 0; k < nkicks; ++k) {
         if (use_graph) CK(cudaGraphLaunch(ctx->kick_exec, s), "kick graph");
         else CK(kick_plain(ka, s), "kick");
+        if (diag) CK(diag_after(k), "slice diagnostics");
     }
     ctx->kick += nkicks;
     ctx->green_valid = false;  // the device may have rebuilt the spectrum for another h
     return BX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t bx_track(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t first_kick,
+                 int64_t nkicks, void *stream) {
+    return track_impl(ctx, beam, lat, first_kick, nkicks, nullptr, stream);
+}
+
+int32_t bx_track_diagnostics(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat,
+                             int64_t first_kick, int64_t nkicks, double *moments_device,
+                             void *stream) {
+    if (!moments_device) return fail(ctx, BX_BAD_ARG, "moments_device is NULL");
+    if (beam && beam->n == 0) return fail(ctx, BX_BAD_ARG, "diagnostics of an empty beam");
+    return track_impl(ctx, beam, lat, first_kick, nkicks, moments_device, stream);
 }
 
 int32_t bx_deposit(bx_ctx *ctx, const bx_beam *beam, bx_grid *grid, void *stream) {

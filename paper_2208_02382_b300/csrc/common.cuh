@@ -195,6 +195,7 @@ cudaError_t launch_sort(double *const c[6], long long *id, int64_t n, double bet
 cudaError_t launch_moments(double *const c[6], int64_t n, double *partials, int nblocks,
                            double *out, cudaStream_t s);
 int moments_blocks(int64_t n);
+cudaError_t launch_moments_transform(double *mom, const MapCoef *map, cudaStream_t s);
 // fft.cu
 struct FftPlan {
     int n;            // physical grid nodes per dim
@@ -255,6 +256,11 @@ cudaError_t launch_set_deposit_gate(TrackState *st, cudaStream_t s);
 cudaError_t launch_ghat_fetch(const int32_t *slot_hist, long long k, const double *store,
                               double *ghat, long long count, int cap, cudaStream_t s);
 cudaError_t launch_twiss_beam(P6 xi, int64_t n, const double c[8], P6 out, cudaStream_t s);
+struct Coef9 {
+    double c[9];
+};
+cudaError_t launch_distribution(int kind, P6 z, const double *uni, int64_t n, Coef9 c, P6 out,
+                                cudaStream_t s);
 // igf.cu
 // Doubles of IGF scratch for grid n: the (n+2)^3 corner table in
 // double-double, then the far-field series coefficients.

@@ -54,6 +54,8 @@ struct bx_ctx {
     int64_t *graph_id = nullptr;
     int64_t graph_n = -1;
     double graph_bg = 0.0;
+    MapCoef *graph_maps = nullptr;         // map table and sort scratch the graph was built with
+    int64_t graph_sort_n = -1;
     cudaStream_t cap_stream = nullptr, body_stream = nullptr;
     bool graphs_off = false;               // the graph path failed once: plain launches
     Profiler *prof = nullptr;

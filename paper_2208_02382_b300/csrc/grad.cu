@@ -236,6 +236,40 @@ int32_t bx_twiss_beam(const double twiss[8], const double *const xi[6], int64_t 
     return BX_OK;
 }
 
+int32_t bx_distribution_beam(int32_t kind, const double params[9],
+                             const double *const normals[6], const double *uniforms, int64_t n,
+                             double *const out[6], void *stream) {
+    if (!params || !normals || !out) return set_noctx_error(BX_BAD_ARG, "NULL argument");
+    if (kind != 0 && kind != 1) return set_noctx_error(BX_BAD_ARG, "kind must be 0 or 1");
+    if (n < 0) return set_noctx_error(BX_BAD_ARG, "n < 0");
+    if (n > 0) {
+        for (int k = 0; k < 6; ++k)
+            if (!normals[k] || !out[k]) return set_noctx_error(BX_BAD_ARG, "NULL coordinate pointer");
+        if (kind == 1 && !uniforms) return set_noctx_error(BX_BAD_ARG, "uniforms is NULL");
+    }
+    Coef9 c9;
+    double *c = c9.c;
+    for (int pl = 0; pl < 3; ++pl) {
+        const double lam = params[pl], lamp = params[3 + pl], mu = params[6 + pl];
+        if (!std::isfinite(lam) || !std::isfinite(lamp) || !(std::fabs(mu) < 1.0))
+            return set_noctx_error(BX_BAD_ARG, "parameters must be finite with |mu| < 1");
+        const double root = std::sqrt(1.0 - mu * mu);
+        c[3 * pl] = lam / root;
+        c[3 * pl + 1] = lamp;
+        c[3 * pl + 2] = mu / root;
+    }
+    if (n == 0) return BX_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    P6 pz, po;
+    for (int k = 0; k < 6; ++k) {
+        pz.p[k] = const_cast<double *>(normals[k]);
+        po.p[k] = out[k];
+    }
+    const cudaError_t e = launch_distribution(kind, pz, uniforms, n, c9, po, s);
+    if (e != cudaSuccess) return set_noctx_error(BX_CUDA, cudaGetErrorString(e));
+    return BX_OK;
+}
+
 int32_t bx_twiss_grad(const double twiss[8], const double S[36], double out[6]) {
     if (!twiss || !S || !out) return set_noctx_error(BX_BAD_ARG, "NULL argument");
     // S[i*6 + j] = sum_p zbar0_i z0_j.  With u = sqrt(eps beta) xi_u and

@@ -93,4 +93,43 @@ cudaError_t launch_moments(double *const c[6], int64_t n, double *partials, int 
     return cudaGetLastError();
 }
 
+// Moments (means, then the row-major upper triangle of the centred second
+// moments) taken through a linear map of the MapCoef class: mean' = M mean,
+// C' = M C M^T.  One thread.
+__global__ void k_moments_transform(double *__restrict__ mom, const MapCoef *map) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const MapCoef &c = *map;
+    double M[6][6] = {{c.m00, c.m01, 0, 0, 0, c.m05}, {c.m10, c.m11, 0, 0, 0, c.m15},
+                      {0, 0, c.m22, c.m23, 0, 0},     {0, 0, c.m32, c.m33, 0, 0},
+                      {c.m40, c.m41, 0, 0, 1, c.m45}, {0, 0, 0, 0, 0, 1}};
+    double mean[6], C[6][6], T[6][6];
+    for (int i = 0; i < 6; ++i) mean[i] = mom[i];
+    int k = 6;
+    for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j, ++k) C[i][j] = C[j][i] = mom[k];
+    for (int i = 0; i < 6; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < 6; ++j) s += M[i][j] * mean[j];
+        mom[i] = s;
+    }
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) {
+            double s = 0.0;
+            for (int l = 0; l < 6; ++l) s += M[i][l] * C[l][j];
+            T[i][j] = s;
+        }
+    k = 6;
+    for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j, ++k) {
+            double s = 0.0;
+            for (int l = 0; l < 6; ++l) s += T[i][l] * M[j][l];
+            mom[k] = s;
+        }
+}
+
+cudaError_t launch_moments_transform(double *mom, const MapCoef *map, cudaStream_t s) {
+    BT_LAUNCH(K_MOMENTS, s, k_moments_transform<<<1, 32, 0, s>>>(mom, map));
+    return cudaGetLastError();
+}
+
 }  // namespace bt
