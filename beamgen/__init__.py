@@ -22,8 +22,9 @@ from typing import List, Sequence
 
 import numpy as np
 
-# element type codes (shared with the C-ABI header's BX_DRIFT / BX_QUAD / BX_SBEND)
-DRIFT, QUAD, SBEND = 0, 1, 2
+# element type codes (shared with the C-ABI header's BX_DRIFT / BX_QUAD / BX_SBEND /
+# BX_DIPEDGE / BX_CONSTF)
+DRIFT, QUAD, SBEND, DIPEDGE, CONSTF = 0, 1, 2, 3, 4
 
 # rest energies, CODATA 2018 [MeV]
 MASS_PROTON_MEV = 938.27208816
@@ -40,6 +41,7 @@ class Element:
     k: float = 0.0
     angle: float = 0.0
     nslice: int = 1
+    k2: float = 0.0
 
 
 def drift(length, nslice=1):
@@ -52,6 +54,16 @@ def quad(length, k, nslice=1):
 
 def sbend(length, angle, nslice=1):
     return Element(SBEND, float(length), 0.0, float(angle), int(nslice))
+
+
+def dipedge(psi, curvature):
+    """Thin dipole edge: edge angle psi [rad], bend curvature 1/rho [1/m]."""
+    return Element(DIPEDGE, 0.0, float(curvature), float(psi), 0)
+
+
+def constf(length, kx, ky, nslice=1):
+    """Constant transverse focusing channel piece (k_x, k_y in 1/m^2)."""
+    return Element(CONSTF, float(length), float(kx), 0.0, int(nslice), float(ky))
 
 
 def fodo_cell(nslice, kf=1.0, kd=-1.0):
@@ -99,6 +111,19 @@ TWISS_FODO = (-1.5905004, 2.8216194, 3.5e-7, 1.5905004, 2.8216194, 3.5e-7, 1e-3,
 def standard_normal6(n: int, seed: int = 0) -> np.ndarray:
     """(6, n) independent standard normal draws (the xi of a Twiss bunch)."""
     return np.ascontiguousarray(_rng(seed).standard_normal((6, int(n))))
+
+
+def chicane_rect_lattice(nslice=50):
+    """chicane_lattice with rectangular bends: a thin edge of half the bend
+    angle on both faces of every sector bend."""
+    out = []
+    for e in chicane_lattice(nslice):
+        if e.kind == SBEND:
+            h = e.angle / e.length
+            out += [dipedge(0.5 * e.angle, h), e, dipedge(0.5 * e.angle, h)]
+        else:
+            out.append(e)
+    return out
 
 
 # Listing 1 (FODO.py): Waterbag parameters (sigmaX, sigmaY, sigmaT, sigmaPx,

@@ -158,7 +158,7 @@ class Record:
     """What the reverse needs of one kick: element, slice length, half map,
     the coordinates before the first half map (z_in), before the kick (a) and
     after it (b), the box, cell size, Green's spectrum and node field."""
-    __slots__ = ("ie", "ds", "half", "z_in", "a", "b", "box", "h", "ghat", "efield", "q")
+    __slots__ = ("ie", "ds", "half", "z_in", "a", "b", "box", "h", "ghat", "efield", "q", "pre")
 
 
 def forward(z0: np.ndarray, lattice, ref: ph.RefPart, bunch_charge_C: float, n_grid: int,
@@ -168,6 +168,7 @@ def forward(z0: np.ndarray, lattice, ref: ph.RefPart, bunch_charge_C: float, n_g
     the box of each kick is taken from the list instead of the box rule
     (replay).  Returns (final coordinates, records, boxes used)."""
     sched = ph.slice_schedule(lattice)
+    before, after = ph.thin_schedule(lattice)
     c = np.array(z0, dtype=np.float64, copy=True)
     npart = c.shape[1]
     q = sc.macro_charge(bunch_charge_C, npart, ref)
@@ -175,9 +176,13 @@ def forward(z0: np.ndarray, lattice, ref: ph.RefPart, bunch_charge_C: float, n_g
     recs, used = [], []
     for k, (ie, ds) in enumerate(sched):
         e = lattice[ie]
-        half = ph.element_matrix(e.kind, e.length, e.k, e.angle, 0.5 * ds, ref)
+        pre = ph.thin_matrix(lattice, before[k], ref)
+        for it in before[k]:
+            c = ph.push(c, ph.thin_matrix(lattice, [it], ref))
+        half = ph.element_matrix(e.kind, e.length, e.k, e.angle, 0.5 * ds, ref,
+                                 getattr(e, "k2", 0.0))
         r = Record()
-        r.ie, r.ds, r.half, r.z_in = ie, ds, half, c
+        r.ie, r.ds, r.half, r.z_in, r.pre = ie, ds, half, c, pre
         c = ph.push(c, half)
         r.a = c
         if space_charge:
@@ -198,6 +203,8 @@ def forward(z0: np.ndarray, lattice, ref: ph.RefPart, bunch_charge_C: float, n_g
         r.b = c
         c = ph.push(c, half)
         recs.append(r)
+    for it in after:
+        c = ph.push(c, ph.thin_matrix(lattice, [it], ref))
     return c, recs, used
 
 
@@ -282,6 +289,8 @@ def reverse(recs, zbar: np.ndarray, lattice, ref: ph.RefPart, n_grid: int,
     dk = np.zeros(len(lattice))
     hbars = [None] * len(recs)
     zb = np.array(zbar, dtype=np.float64, copy=True)
+    _, after = ph.thin_schedule(lattice)
+    zb = ph.thin_matrix(lattice, after, ref).T @ zb      # thin elements past the last slice
     for idx in range(len(recs) - 1, -1, -1):
         r = recs[idx]
         H = r.half
@@ -289,7 +298,7 @@ def reverse(recs, zbar: np.ndarray, lattice, ref: ph.RefPart, n_grid: int,
         bbar = H.T @ zb
         abar = kick_adjoint(r, bbar, ref, n_grid) if space_charge else bbar
         hbar = hbar + abar @ r.z_in.T      # first half map, input z_in
-        zb = H.T @ abar
+        zb = r.pre.T @ (H.T @ abar)        # then the thin elements before the slice
         hbars[idx] = hbar
         e = lattice[r.ie]
         dk[r.ie] += float(np.sum(hbar * element_matrix_dk(e.kind, 0.5 * r.ds, e.k)))

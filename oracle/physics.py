@@ -24,7 +24,7 @@ C_LIGHT = 299792458.0                # m/s
 Q_E = 1.602176634e-19                # C
 EPS0 = 8.8541878128e-12              # F/m
 
-DRIFT, QUAD, SBEND = 0, 1, 2
+DRIFT, QUAD, SBEND, DIPEDGE, CONSTF = 0, 1, 2, 3, 4
 X, PX, Y, PY, T, PT = range(6)
 
 
@@ -119,13 +119,46 @@ def sbend_matrix(ds: float, rho: float, ref: RefPart) -> np.ndarray:
     return m
 
 
+def dipedge_matrix(psi: float, curvature: float) -> np.ndarray:
+    """Thin hard-edge dipole fringe field (K. L. Brown, SLAC-75, 1972): edge
+    angle psi, bend curvature h = 1/rho;  px += h tan(psi) x,
+    py -= h tan(psi) y.  A rectangular bend of angle theta has psi = theta/2
+    at both faces.  (Paper §Benchmark: chicane; SURVEY reading: edge elements
+    make the chicane achromatic.)"""
+    m = np.eye(6)
+    m[PX, X] = curvature * math.tan(psi)
+    m[PY, Y] = -curvature * math.tan(psi)
+    return m
+
+
+def constf_matrix(ds: float, kx: float, ky: float, ref: RefPart) -> np.ndarray:
+    """Constant linear focusing over ds (paper §Numerical Experiments: "a
+    stationary beam in a constant focusing channel"): u'' = -k_u u per
+    transverse plane, t-row as the drift (reading: no longitudinal focusing)."""
+    m = np.eye(6)
+    m[X:X + 2, X:X + 2] = _focus_block(ds, kx)
+    m[Y:Y + 2, Y:Y + 2] = _focus_block(ds, ky)
+    m[T, PT] = ds / ref.betagamma ** 2
+    return m
+
+
+def is_thin(e) -> bool:
+    """Thin elements (dipole edges) act between slices and take no kick."""
+    return e.kind == DIPEDGE
+
+
 def element_matrix(kind: int, length: float, k: float, angle: float, ds: float,
-                   ref: RefPart) -> np.ndarray:
-    """Map of a piece of arc length ds of the given element."""
+                   ref: RefPart, k2: float = 0.0) -> np.ndarray:
+    """Map of a piece of arc length ds of the given element (the whole of a
+    thin element: ds is ignored)."""
     if kind == DRIFT:
         return drift_matrix(ds, ref)
     if kind == QUAD:
         return quad_matrix(ds, k, ref)
+    if kind == DIPEDGE:
+        return dipedge_matrix(angle, k)
+    if kind == CONSTF:
+        return constf_matrix(ds, k, k2, ref)
     if kind == SBEND:
         if angle == 0.0:
             return drift_matrix(ds, ref)
@@ -142,11 +175,40 @@ def slice_schedule(lattice) -> list:
     """
     out = []
     for ie, e in enumerate(lattice):
+        if is_thin(e):
+            continue
         if e.nslice <= 0 or e.length <= 0.0:
             raise ValueError("element needs nslice > 0 and length > 0")
         ds = e.length / e.nslice
         out.extend((ie, ds) for _ in range(e.nslice))
     return out
+
+
+def thin_schedule(lattice) -> tuple:
+    """Thin elements in beamline order around the slices: (before, after)
+    with before[j] the indices of the thin elements between slice j-1 and
+    slice j (before slice 0 for j = 0) and `after` those past the last slice.
+    A call tracking slices [a, b) applies before[j] ahead of slice j, and
+    `after` when b is the end of the lattice."""
+    n = len(slice_schedule(lattice))
+    before = [[] for _ in range(n)]
+    after = []
+    j = 0
+    for ie, e in enumerate(lattice):
+        if is_thin(e):
+            (before[j] if j < n else after).append(ie)
+        else:
+            j += e.nslice
+    return before, after
+
+
+def thin_matrix(lattice, indices, ref: RefPart) -> np.ndarray:
+    """Product of the thin elements `indices` in beamline order."""
+    m = np.eye(6)
+    for ie in indices:
+        e = lattice[ie]
+        m = element_matrix(e.kind, e.length, e.k, e.angle, 0.0, ref, getattr(e, "k2", 0.0)) @ m
+    return m
 
 
 def symplectic_form() -> np.ndarray:

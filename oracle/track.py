@@ -67,11 +67,16 @@ class Tracker:
         of the bunch at the end of every slice is appended to it (Listing 1
         set_slice_step_diagnostics)."""
         sched = ph.slice_schedule(lattice)
+        before, after = ph.thin_schedule(lattice)
         stop = len(sched) if nkicks is None else min(len(sched), first_kick + nkicks)
         c = np.array(coords, dtype=np.float64, copy=True)
-        for ie, ds in sched[first_kick:stop]:
+        for j in range(first_kick, stop):
+            ie, ds = sched[j]
+            for it in before[j]:
+                c = ph.push(c, ph.thin_matrix(lattice, [it], self.ref))
             e = lattice[ie]
-            half = ph.element_matrix(e.kind, e.length, e.k, e.angle, 0.5 * ds, self.ref)
+            half = ph.element_matrix(e.kind, e.length, e.k, e.angle, 0.5 * ds, self.ref,
+                                     getattr(e, "k2", 0.0))
             c = ph.push(c, half)
             if self.space_charge:
                 c = self.space_charge_kick(c, ds)
@@ -79,6 +84,9 @@ class Tracker:
             self.kick_index += 1
             if diagnostics is not None:
                 diagnostics.append(moments_vector(c))
+        if stop == len(sched) and stop > first_kick:
+            for it in after:
+                c = ph.push(c, ph.thin_matrix(lattice, [it], self.ref))
         return c
 
 

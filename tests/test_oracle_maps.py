@@ -193,3 +193,62 @@ def test_moments_brute_force_small():
     ex = math.sqrt(m["cov"][0, 0] * m["cov"][1, 1] - m["cov"][0, 1] ** 2)
     assert m["eps_x"] == pytest.approx(ex, rel=1e-14)
     assert len(tr.moments_vector(c)) == 27
+
+
+def test_rectangular_bend_chicane_is_achromatic():
+    # four rectangular bends (sector bend + thin edges of half the bend angle
+    # on both faces) close the dispersion: R16 = R26 = 0; sector bends alone
+    # do not
+    ref = ph.RefPart(bg.MASS_ELECTRON_MEV, 500.0, -1.0)
+
+    def total(lat):
+        m = np.eye(6)
+        for e in lat:
+            m = ph.element_matrix(e.kind, e.length, e.k, e.angle, e.length, ref, e.k2) @ m
+        return m
+
+    rect = total(bg.chicane_rect_lattice(1)[2:])
+    sect = total(bg.chicane_lattice(1)[2:])
+    assert abs(rect[0, 5]) < 1e-15 and abs(rect[1, 5]) < 1e-15
+    assert abs(sect[0, 5]) > 1e-2
+    # the edges only act on px, py (thin): det 1, symplectic
+    j = ph.symplectic_form()
+    for psi, h in ((0.05, 0.2), (-0.3, 1.7)):
+        m = ph.dipedge_matrix(psi, h)
+        assert np.abs(m.T @ j @ m - j).max() < 1e-15
+
+
+def test_constant_focusing_solves_its_equation_of_motion():
+    # u'' = -k_u u per plane: compare with direct integration, and k_x = k,
+    # k_y = -k reproduces the quadrupole
+    from scipy.integrate import solve_ivp
+    ref = ph.RefPart(bg.MASS_PROTON_MEV, 1000.0, 1.0)
+    kx, ky, L = 0.8, 2.5, 0.7
+    m = ph.constf_matrix(L, kx, ky, ref)
+    for (a, k) in ((0, kx), (2, ky)):
+        sol = solve_ivp(lambda s, y: [y[1], -k * y[0]], (0, L), [1e-3, 2e-4], rtol=1e-12,
+                        atol=1e-16)
+        assert np.allclose(m[a:a + 2, a:a + 2] @ [1e-3, 2e-4], sol.y[:, -1], rtol=1e-9)
+    assert np.allclose(ph.constf_matrix(L, 1.3, -1.3, ref), ph.quad_matrix(L, 1.3, ref))
+    j = ph.symplectic_form()
+    assert np.abs(m.T @ j @ m - j).max() < 1e-14
+
+
+def test_thin_elements_between_slices_in_tracking():
+    # a lattice with edges tracked slice by slice (no space charge) equals the
+    # product of the element maps, whatever the slicing
+    ref = ph.RefPart(bg.MASS_ELECTRON_MEV, 500.0, -1.0)
+    lat = bg.chicane_rect_lattice(3)
+    c0 = bg.gaussian6d(200, seed=8)
+    t = tr.Tracker(ref, 1e-9, 8, space_charge=False)
+    got = t.track(c0, lat)
+    m = np.eye(6)
+    for e in lat:
+        m = ph.element_matrix(e.kind, e.length, e.k, e.angle, e.length, ref, e.k2) @ m
+    assert np.allclose(got, m @ c0, rtol=1e-12, atol=1e-16)
+    # split calls: thin elements between two calls are applied once
+    t2 = tr.Tracker(ref, 1e-9, 8, space_charge=False)
+    half = len(ph.slice_schedule(lat)) // 2
+    c1 = t2.track(c0, lat, 0, half)
+    c2 = t2.track(c1, lat, half, None)
+    assert np.allclose(c2, got, rtol=1e-12, atol=1e-16)
