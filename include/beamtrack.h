@@ -49,10 +49,13 @@ extern "C" {
 #define BX_CUDA 5           /* a CUDA runtime call failed                   */
 
 /* ---- element types (Listing 1: elements.Drift, elements.Quad; sector bend
- *      from the paper's chicane benchmark) ---------------------------------- */
+ *      from the paper's chicane benchmark; thin dipole edge and constant
+ *      focusing from its list of benchmarks) ---------------------------------- */
 #define BX_DRIFT 0
 #define BX_QUAD 1
 #define BX_SBEND 2
+#define BX_DIPEDGE 3 /* thin: nslice = 0, angle = edge angle, k = curvature 1/rho */
+#define BX_CONSTF 4  /* constant focusing: k = k_x, k2 = k_y [1/m^2]            */
 
 typedef struct bx_ctx bx_ctx;
 typedef struct bx_batch bx_batch;
@@ -95,15 +98,24 @@ typedef struct {
 } bx_beam;
 
 /* One lattice element (Listing 1: Drift(ds, nslice), Quad(ds, k, nslice)).
- * length [m] > 0; k [1/m^2] (quadrupole; k > 0 focuses x); angle [rad]
- * (sector bend, total over the element); nslice >= 1 slices, one
- * space-charge kick per slice. */
+ * Thick elements (drift, quadrupole, sector bend, constant focusing): length
+ * [m] > 0; nslice >= 1 slices, one space-charge kick per slice; k [1/m^2]
+ * (quadrupole: k > 0 focuses x; constant focusing: k_x); angle [rad] (sector
+ * bend, total over the element); k2 [1/m^2] (constant focusing: k_y).
+ * Thin dipole edge (hard-edge fringe field, K. L. Brown SLAC-75: px += h
+ * tan(psi) x, py -= h tan(psi) y): nslice = 0, angle = edge angle psi, k =
+ * curvature h = 1/rho of the bend it belongs to; it takes no kick and acts
+ * between the slices around it (a rectangular bend of angle theta: edges of
+ * theta/2 on both faces).  Thin elements ahead of slice j act in the call
+ * that tracks slice j; those after the last slice act at the end of the
+ * call that tracks it. */
 typedef struct {
     int32_t type;
     int32_t nslice;
     double length;
     double k;
     double angle;
+    double k2;
 } bx_element;
 
 /* A lattice in HOST memory.  space_charge: 0 = maps only

@@ -33,13 +33,15 @@ class Species:
 @dataclass(frozen=True)
 class Element:
     """One lattice element (Listing 1 elements): kind L.BX_DRIFT / BX_QUAD /
-    BX_SBEND, length [m], quadrupole strength k [1/m^2], bend angle [rad],
-    slices (space-charge kicks)."""
+    BX_SBEND / BX_DIPEDGE / BX_CONSTF, length [m], strength k [1/m^2] (edge:
+    curvature 1/rho), bend or edge angle [rad], slices (space-charge kicks;
+    0 for a thin edge), k2 [1/m^2] (constant focusing in y)."""
     kind: int
     length: float
     k: float
     angle: float
     nslice: int
+    k2: float = 0.0
 
 
 def _ptr6(t: torch.Tensor):
@@ -133,6 +135,7 @@ def lattice_struct(elements: Sequence, space_charge: bool):
         arr[i].length = float(e.length)
         arr[i].k = float(e.k)
         arr[i].angle = float(e.angle)
+        arr[i].k2 = float(getattr(e, "k2", 0.0))
     lat = L.bx_lattice()
     lat.elements = ctypes.cast(arr, ctypes.POINTER(L.bx_element))
     lat.count = len(elements)
@@ -210,7 +213,7 @@ class Tracker:
                                    int(nkicks), _stream())
             _check(self.lib, self.ctx, rc)
             return None
-        total = sum(int(e.nslice) for e in elements)
+        total = sum(int(e.nslice) for e in elements if int(e.kind) != L.BX_DIPEDGE)
         nk = total - int(first_kick) if nkicks < 0 else int(nkicks)
         out = torch.empty((max(nk, 0), 27), dtype=torch.float64, device=beam.coords.device)
         rc = self.lib.bx_track_diagnostics(self.ctx, ctypes.byref(b), ctypes.byref(lat),

@@ -25,8 +25,8 @@ class TrackObjectives(torch.autograd.Function):
     def forward(ctx, ks, twiss, xi, tracker, elements, families, species, bunch_charge_C,
                 checkpoint_interval=20, space_charge=True):
         kv = [float(v) for v in ks.detach().cpu().tolist()]
-        els = [api.Element(e.kind, e.length, kv[f] if f >= 0 else e.k, e.angle, e.nslice)
-               for e, f in zip(elements, families)]
+        els = [api.Element(e.kind, e.length, kv[f] if f >= 0 else e.k, e.angle, e.nslice,
+                           getattr(e, "k2", 0.0)) for e, f in zip(elements, families)]
         tw = [float(v) for v in twiss.detach().cpu().tolist()]
         coords = api.twiss_beam(tw, xi)
         beam = api.Beam(coords, species, bunch_charge_C)

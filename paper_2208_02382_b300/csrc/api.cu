@@ -111,22 +111,34 @@ int32_t bx_reset(bx_ctx *ctx) {
 namespace {
 
 // Moments at every slice end (Listing 1 set_slice_step_diagnostics): after
-// kick k the bunch holds P_{k+1} = H_first(k+1) S_k with S_k the state at the
-// end of slice k, so the moments of S_k are those of P_{k+1} taken back through
-// the inverse half map (H^-1 = the element's map over -ds/2); after the last
-// kick of the call the bunch is at the slice end itself.
+// kick k the bunch holds P_{k+1} = H_first(k+1) T_pre(k+1) S_k with S_k the
+// state at the end of slice k (T_pre: thin elements in between), so the
+// moments of S_k are those of P_{k+1} taken back through the inverse of that
+// product; after the last kick of the call the bunch is at the slice end, or
+// past the thin elements that end the lattice.
 int32_t slice_diagnostics(bx_ctx *ctx, const bx_lattice *lat, const std::vector<int> &sel,
                           const std::vector<double> &sds, int64_t first, int64_t nkicks,
                           const Ref &r, std::vector<MapCoef> &inv) {
+    (void)ctx;
+    std::vector<Mat6> pre;
+    Mat6 post;
+    thin_maps(lat, r, pre, post);
+    const int64_t total = (int64_t)sel.size();
     inv.assign(nkicks, MapCoef{});
     for (int64_t k = 0; k < nkicks; ++k) {
-        Mat m;
+        Mat m, mi;
+        const int64_t j = first + k;
         if (k + 1 < nkicks) {
-            element_map(lat->elements[sel[first + k + 1]], -0.5 * sds[first + k + 1], r, m);
+            Mat h;
+            element_map(lat->elements[sel[j + 1]], 0.5 * sds[j + 1], r, h);
+            mat_mul(h, pre[j + 1].a, m);   // P_{k+1} = H_first T_pre S_k
+        } else if (j + 1 == total) {
+            memcpy(m, post.a, sizeof(Mat));
         } else {
             mat_identity(m);
         }
-        inv[k] = to_coef(m);
+        mat_inverse(m, mi);
+        inv[k] = to_coef(mi);
     }
     return BX_OK;
 }

@@ -61,8 +61,17 @@ void focus_block(double ds, double k, double out[2][2]) {
 //   x'  = cos x + rho sin px - rho(1-cos)/beta pt
 //   px' = -sin/rho x + cos px - sin/beta pt
 //   t'  = t + sin/beta x + rho(1-cos)/beta px + rho(sin/beta^2 - theta) pt.
+// Thin dipole edge (K. L. Brown, SLAC-75): edge angle psi = angle, bend
+// curvature h = k: px += h tan(psi) x, py -= h tan(psi) y (ds ignored).
+// Constant focusing: u'' = -k u in x, u'' = -k2 u in y, t-row as the drift.
 void element_map(const bx_element &e, double ds, const Ref &r, Mat m) {
     mat_identity(m);
+    if (e.type == BX_DIPEDGE) {
+        const double f = e.k * std::tan(e.angle);
+        m[1][0] = f;
+        m[3][2] = -f;
+        return;
+    }
     if (e.type == BX_SBEND && e.angle != 0.0) {
         double rho = e.length / e.angle, th = ds / rho;
         double c = std::cos(th), s = std::sin(th), b = r.beta;
@@ -73,10 +82,10 @@ void element_map(const bx_element &e, double ds, const Ref &r, Mat m) {
         return;
     }
     m[4][5] = ds / (r.bg * r.bg);
-    if (e.type == BX_QUAD) {
+    if (e.type == BX_QUAD || e.type == BX_CONSTF) {
         double bx[2][2], by[2][2];
         focus_block(ds, e.k, bx);
-        focus_block(ds, -e.k, by);
+        focus_block(ds, e.type == BX_QUAD ? -e.k : e.k2, by);
         for (int i = 0; i < 2; ++i)
             for (int j = 0; j < 2; ++j) {
                 m[i][j] = bx[i][j];
@@ -86,6 +95,31 @@ void element_map(const bx_element &e, double ds, const Ref &r, Mat m) {
         m[0][1] = ds;
         m[2][3] = ds;
     }
+}
+
+bool element_is_thin(const bx_element &e) { return e.type == BX_DIPEDGE; }
+
+// Gauss-Jordan inverse with partial pivoting (the maps are well conditioned).
+void mat_inverse(const Mat a, Mat out) {
+    double w[6][12];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 12; ++j) w[i][j] = j < 6 ? a[i][j] : (j - 6 == i ? 1.0 : 0.0);
+    for (int c = 0; c < 6; ++c) {
+        int p = c;
+        for (int i = c + 1; i < 6; ++i)
+            if (std::fabs(w[i][c]) > std::fabs(w[p][c])) p = i;
+        if (p != c)
+            for (int j = 0; j < 12; ++j) std::swap(w[p][j], w[c][j]);
+        const double d = w[c][c];
+        for (int j = 0; j < 12; ++j) w[c][j] /= d;
+        for (int i = 0; i < 6; ++i)
+            if (i != c) {
+                const double f = w[i][c];
+                for (int j = 0; j < 12; ++j) w[i][j] -= f * w[c][j];
+            }
+    }
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) out[i][j] = w[i][6 + j];
 }
 
 // out = a * b (apply b first).
@@ -133,13 +167,19 @@ int32_t check_lattice(bx_ctx *ctx, const bx_lattice *l) {
         return fail(ctx, BX_BAD_ARG, "lattice elements missing");
     for (int i = 0; i < l->count; ++i) {
         const bx_element &e = l->elements[i];
-        if (e.type != BX_DRIFT && e.type != BX_QUAD && e.type != BX_SBEND)
+        if (e.type != BX_DRIFT && e.type != BX_QUAD && e.type != BX_SBEND &&
+            e.type != BX_DIPEDGE && e.type != BX_CONSTF)
             return fail(ctx, BX_BAD_ARG, "unknown element type");
+        if (!std::isfinite(e.k) || !std::isfinite(e.angle) || !std::isfinite(e.k2))
+            return fail(ctx, BX_BAD_ARG, "element k/angle/k2 not finite");
+        if (element_is_thin(e)) {
+            if (e.nslice != 0) return fail(ctx, BX_BAD_ARG, "thin element needs nslice = 0");
+            if (!(std::fabs(e.angle) < 1.5)) return fail(ctx, BX_BAD_ARG, "edge angle out of range");
+            continue;
+        }
         if (!(e.length > 0.0) || !std::isfinite(e.length))
             return fail(ctx, BX_BAD_ARG, "element length must be > 0");
         if (e.nslice <= 0) return fail(ctx, BX_BAD_ARG, "element nslice must be >= 1");
-        if (!std::isfinite(e.k) || !std::isfinite(e.angle))
-            return fail(ctx, BX_BAD_ARG, "element k/angle not finite");
     }
     return BX_OK;
 }
@@ -235,10 +275,32 @@ void slice_schedule(const bx_lattice *lat, std::vector<int> &sel, std::vector<do
     sel.clear();
     sds.clear();
     for (int i = 0; i < lat->count; ++i)
-        for (int k = 0; k < lat->elements[i].nslice; ++k) {
+        for (int k = 0; k < (element_is_thin(lat->elements[i]) ? 0 : lat->elements[i].nslice); ++k) {
             sel.push_back(i);
             sds.push_back(lat->elements[i].length / lat->elements[i].nslice);
         }
+}
+
+void thin_maps(const bx_lattice *lat, const Ref &r, std::vector<Mat6> &pre, Mat6 &post) {
+    pre.clear();
+    Mat t;
+    mat_identity(t);
+    for (int i = 0; i < lat->count; ++i) {
+        const bx_element &e = lat->elements[i];
+        if (element_is_thin(e)) {
+            Mat m;
+            element_map(e, 0.0, r, m);
+            mat_mul(m, t, t);
+            continue;
+        }
+        for (int k = 0; k < e.nslice; ++k) {
+            Mat6 p;
+            memcpy(p.a, t, sizeof(Mat));
+            pre.push_back(p);
+            mat_identity(t);
+        }
+    }
+    memcpy(post.a, t, sizeof(Mat));
 }
 
 void build_map_table(const bx_lattice *lat, const std::vector<int> &sel,
@@ -246,17 +308,27 @@ void build_map_table(const bx_lattice *lat, const std::vector<int> &sel,
                      std::vector<MapCoef> &tab) {
     tab.clear();
     tab.reserve(nkicks + 1);
+    std::vector<Mat6> pre;
+    Mat6 post;
+    thin_maps(lat, r, pre, post);
+    const int64_t total = (int64_t)sel.size();
+    // entry 0: H_first(first) T_pre(first); entry 1 + k: H_first(k+1) T_pre(k+1)
+    // H_second(k); the last: T_post (at the end of the lattice) H_second(last)
     Mat hk, hn, mm;
     element_map(lat->elements[sel[first]], 0.5 * sds[first], r, hk);
-    tab.push_back(to_coef(hk));
+    mat_mul(hk, pre[first].a, mm);
+    tab.push_back(to_coef(mm));
     for (int64_t k = first; k < first + nkicks; ++k) {
         if (k + 1 < first + nkicks) {
             element_map(lat->elements[sel[k + 1]], 0.5 * sds[k + 1], r, hn);
-            mat_mul(hn, hk, mm);
+            mat_mul(pre[k + 1].a, hk, mm);
+            mat_mul(hn, mm, mm);
             tab.push_back(to_coef(mm));
             memcpy(hk, hn, sizeof(Mat));
         } else {
-            tab.push_back(to_coef(hk));
+            if (k + 1 == total) mat_mul(post.a, hk, mm);
+            else memcpy(mm, hk, sizeof(Mat));
+            tab.push_back(to_coef(mm));
         }
     }
     // kick factors of kick k and the map class, in table entry 1 + k

@@ -82,6 +82,14 @@ struct Ref {
 Ref make_ref(const bx_beam *b);
 
 typedef double Mat[6][6];
+struct Mat6 {
+    double a[6][6];
+};
+bool element_is_thin(const bx_element &e);
+void mat_inverse(const Mat a, Mat out);
+// Products of the thin elements ahead of every slice (pre[j]: between slice
+// j-1 and slice j) and past the last slice (post), in beamline order.
+void thin_maps(const bx_lattice *lat, const Ref &r, std::vector<Mat6> &pre, Mat6 &post);
 void mat_identity(Mat m);
 void focus_block(double ds, double k, double out[2][2]);
 void element_map(const bx_element &e, double ds, const Ref &r, Mat m);

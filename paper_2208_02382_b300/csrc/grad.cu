@@ -490,8 +490,8 @@ int32_t bx_grad_backward(bx_ctx *ctx, const bx_beam *beam, const double weights[
     if (S_out)
         for (int q = 0; q < 36; ++q) S_out[q] = sums[13 + q];
     if (dk_out) {
-        // chain rule through the merged maps M_0 = H_0, M_t = H_t H_{t-1},
-        // M_K = H_{K-1}: Hbar_t += Mbar_t H_{t-1}^T, Hbar_{t-1} += H_t^T Mbar_t
+        // chain rule through the merged maps to each half-slice map H_k, then
+        // dL/dk of the quadrupoles from dH/dk in closed form
         const int ne = (int)g->elements.size();
         for (int e = 0; e < ne; ++e) dk_out[e] = 0.0;
         std::vector<std::array<double, 36>> hbar(K);
@@ -503,25 +503,53 @@ int32_t bx_grad_backward(bx_ctx *ctx, const bx_beam *beam, const double weights[
             for (int i = 0; i < 6; ++i)
                 for (int jj = 0; jj < 6; ++jj) H[k][6 * i + jj] = m[i][jj];
         }
+        // thin elements between the slices (no parameters; carried through)
+        std::vector<Mat6> pre;
+        Mat6 post;
+        const bx_lattice lat_rec{g->elements.data(), (int32_t)g->elements.size(), 1};
+        thin_maps(&lat_rec, g->ref, pre, post);
+        auto mul = [](const double *a, const double *b, double *out) {  // out = a b
+            double t[36];
+            for (int i = 0; i < 6; ++i)
+                for (int j = 0; j < 6; ++j) {
+                    double s = 0.0;
+                    for (int l = 0; l < 6; ++l) s += a[6 * i + l] * b[6 * l + j];
+                    t[6 * i + j] = s;
+                }
+            memcpy(out, t, sizeof(t));
+        };
+        auto mul_bt = [](const double *a, const double *b, double *acc) {  // acc += a b^T
+            for (int i = 0; i < 6; ++i)
+                for (int j = 0; j < 6; ++j) {
+                    double s = 0.0;
+                    for (int l = 0; l < 6; ++l) s += a[6 * i + l] * b[6 * j + l];
+                    acc[6 * i + j] += s;
+                }
+        };
+        auto mul_at = [](const double *a, const double *b, double *acc) {  // acc += a^T b
+            for (int i = 0; i < 6; ++i)
+                for (int j = 0; j < 6; ++j) {
+                    double s = 0.0;
+                    for (int l = 0; l < 6; ++l) s += a[6 * l + i] * b[6 * l + j];
+                    acc[6 * i + j] += s;
+                }
+        };
+        // M_0 = H_0 T_pre(0); M_t = H_t T_pre(t) H_{t-1}; M_K = T_post H_{K-1}:
+        // the adjoint of each half map is Mbar times the other factors
         for (int64_t t = 0; t <= K; ++t) {
             double mb[36] = {0};
             for (int q = 0; q < 13; ++q) mb[6 * kMbarRow[q] + kMbarCol[q]] = mbar[13 * t + q];
-            if (t == 0 || t == K) {
-                auto &dst = hbar[t == 0 ? 0 : K - 1];
-                for (int q = 0; q < 36; ++q) dst[q] += mb[q];
-                continue;
+            if (t == 0) {
+                mul_bt(mb, &pre[0].a[0][0], hbar[0].data());
+            } else if (t == K) {
+                mul_at(&post.a[0][0], mb, hbar[K - 1].data());
+            } else {
+                double right[36], left[36];
+                mul(&pre[t].a[0][0], H[t - 1].data(), right);   // T_pre(t) H_{t-1}
+                mul(H[t].data(), &pre[t].a[0][0], left);         // H_t T_pre(t)
+                mul_bt(mb, right, hbar[t].data());
+                mul_at(left, mb, hbar[t - 1].data());
             }
-            const auto &Hp = H[t - 1], &Hn = H[t];
-            for (int i = 0; i < 6; ++i)
-                for (int jj = 0; jj < 6; ++jj) {
-                    double a = 0.0, b = 0.0;
-                    for (int l = 0; l < 6; ++l) {
-                        a += mb[6 * i + l] * Hp[6 * jj + l];   // (Mbar H_{t-1}^T)_ij
-                        b += Hn[6 * l + i] * mb[6 * l + jj];   // (H_t^T Mbar)_ij
-                    }
-                    hbar[t][6 * i + jj] += a;
-                    hbar[t - 1][6 * i + jj] += b;
-                }
         }
         for (int64_t k = 0; k < K; ++k) {
             const bx_element &el = g->elements[g->sel[k]];
