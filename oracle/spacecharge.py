@@ -97,12 +97,45 @@ def cic_cells(pos: np.ndarray, box: Box, n: int):
     return idx, frac
 
 
-def deposit(pos: np.ndarray, q_macro: float, box: Box, n: int) -> np.ndarray:
-    """Charge density on the n^3 node grid (C/m^3), CIC.
+def tsc_nodes(pos: np.ndarray, box: Box, n: int):
+    """Nearest node and quadratic B-spline weights per dimension (shape order
+    2, TSC; Listing 1 set_particle_shape(2)).
 
-    Each particle adds q * wx * wy * wz to the 8 nodes of its cell, in particle
-    order, corner by corner; the grid is divided by the cell volume at the end.
+    Reading: u = (X - lo)/h is first limited to [1/2, n - 3/2] (so the three
+    nodes i-1, i, i+1 exist; inside the box rule's 5% margin this only acts on
+    grids of fewer than ~20 nodes), i = floor(u + 1/2) limited to [1, n-2],
+    f = u - i, and the weights of nodes i-1, i, i+1 are
+    (1/2 - f)^2 / 2, 3/4 - f^2, (1/2 + f)^2 / 2.
     """
+    h = box.h(n)
+    idx, wts = [], []
+    for d in range(3):
+        u = np.clip((pos[d] - box.lo[d]) / h[d], 0.5, n - 1.5)
+        i = np.clip(np.floor(u + 0.5), 1, n - 2).astype(np.int64)
+        f = u - i
+        idx.append(i)
+        wts.append((0.5 * (0.5 - f) ** 2, 0.75 - f * f, 0.5 * (0.5 + f) ** 2))
+    return idx, wts
+
+
+def deposit(pos: np.ndarray, q_macro: float, box: Box, n: int, shape: int = 1) -> np.ndarray:
+    """Charge density on the n^3 node grid (C/m^3), CIC (shape 1) or TSC
+    (shape 2).
+
+    Each particle adds q * wx * wy * wz to the 8 nodes of its cell (CIC) or the
+    27 nodes around its nearest node (TSC), in particle order, node by node;
+    the grid is divided by the cell volume at the end.
+    """
+    if shape == 2:
+        (i, j, l), (wx, wy, wz) = tsc_nodes(pos, box, n)
+        rho = np.zeros((n, n, n))
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    np.add.at(rho, (l + dz, j + dy, i + dx),
+                              q_macro * (wx[dx + 1] * wy[dy + 1] * wz[dz + 1]))
+        h = box.h(n)
+        return rho / (h[0] * h[1] * h[2])
     (i, j, l), (fx, fy, fz) = cic_cells(pos, box, n)
     wx, wy, wz = (1.0 - fx, fx), (1.0 - fy, fy), (1.0 - fz, fz)
     rho = np.zeros((n, n, n))
@@ -225,9 +258,20 @@ def field(phi: np.ndarray, h) -> np.ndarray:
 
 # ------------------------------------------------------------ gather + kick
 
-def gather(pos: np.ndarray, efield: np.ndarray, box: Box) -> np.ndarray:
-    """Field at each particle with the same CIC weights as the deposit."""
+def gather(pos: np.ndarray, efield: np.ndarray, box: Box, shape: int = 1) -> np.ndarray:
+    """Field at each particle with the same weights as the deposit (CIC or
+    TSC)."""
     n = efield.shape[1]
+    if shape == 2:
+        (i, j, l), (wx, wy, wz) = tsc_nodes(pos, box, n)
+        out = np.zeros((3, pos.shape[1]))
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    w = wx[dx + 1] * wy[dy + 1] * wz[dz + 1]
+                    for c in range(3):
+                        out[c] += w * efield[c, l + dz, j + dy, i + dx]
+        return out
     (i, j, l), (fx, fy, fz) = cic_cells(pos, box, n)
     wx, wy, wz = (1.0 - fx, fx), (1.0 - fy, fy), (1.0 - fz, fz)
     out = np.zeros((3, pos.shape[1]))

@@ -24,9 +24,12 @@ class Tracker:
     spectrum for the box's cell size, the kick counter and the regrid log."""
 
     def __init__(self, ref: ph.RefPart, bunch_charge_C: float, n_grid: int,
-                 space_charge: bool = True):
+                 space_charge: bool = True, shape: int = 1):
         if n_grid < 2:
             raise ValueError("n_grid >= 2")
+        if shape not in (1, 2):
+            raise ValueError("shape 1 (CIC) or 2 (TSC)")
+        self.shape = int(shape)
         self.ref = ref
         self.bunch_charge_C = bunch_charge_C
         self.n = int(n_grid)
@@ -53,10 +56,10 @@ class Tracker:
             self.ghat = sc.green_hat(self.n, h)
             self.ghat_h = h
         q = sc.macro_charge(self.bunch_charge_C, npart, self.ref)
-        rho = sc.deposit(pos, q, self.box, self.n)
+        rho = sc.deposit(pos, q, self.box, self.n, self.shape)
         phi = sc.solve(rho, h, self.ghat)
         e = sc.field(phi, h)
-        e_at = sc.gather(pos, e, self.box)
+        e_at = sc.gather(pos, e, self.box, self.shape)
         return sc.kick(coords, e_at, ds, self.ref)
 
     def track(self, coords: np.ndarray, lattice, first_kick: int = 0,

@@ -314,3 +314,74 @@ def test_nonfinite_input_is_rejected(oracle_lib):
     c0[0, 3] = np.nan
     with pytest.raises(FloatingPointError):
         tr.Tracker(ref, 1e-9, 8).track(c0, bg.fodo_lattice(1, 1))
+
+
+# ------------------------------------------------------------------- TSC
+
+def test_tsc_weights_moments():
+    # quadratic B-spline: weights sum to 1, their first moment is the offset
+    # f (linear interpolation exact), their second moment about f is 1/4
+    box = sc.Box((0.0, 0.0, 0.0), (7.0, 7.0, 7.0))
+    rng = np.random.default_rng(3)
+    pos = rng.uniform(0.6, 6.4, size=(3, 500))
+    (i, j, l), w = sc.tsc_nodes(pos, box, 8)
+    for d, idx in enumerate((i, j, l)):
+        f = pos[d] - idx
+        s0 = w[d][0] + w[d][1] + w[d][2]
+        s1 = w[d][2] - w[d][0]
+        s2 = w[d][0] * (-1 - f) ** 2 + w[d][1] * f ** 2 + w[d][2] * (1 - f) ** 2
+        assert np.allclose(s0, 1.0, rtol=0, atol=1e-15)
+        assert np.allclose(s1, f, rtol=0, atol=1e-15)
+        assert np.allclose(s2, 0.25, rtol=0, atol=1e-15)
+
+
+def test_tsc_deposit_conserves_charge_and_centroid_and_gathers_linear_fields():
+    n = 16
+    c = bg.gaussian6d(3000, seed=31)
+    ref = ph.RefPart(bg.MASS_PROTON_MEV, 1000.0, 1.0)
+    pos = sc.rest_frame(c, ref)
+    box, _ = sc.box_rule(pos, None)
+    h = box.h(n)
+    q = 1e-12
+    rho = sc.deposit(pos, q, box, n, shape=2)
+    V = h[0] * h[1] * h[2]
+    assert rho.sum() * V == pytest.approx(q * pos.shape[1], rel=1e-13)
+    grid = [box.lo[d] + h[d] * np.arange(n) for d in range(3)]
+    for d, ax in ((0, (0, 1)), (1, (0, 2)), (2, (1, 2))):
+        mom = (rho.sum(axis=ax) * grid[d]).sum() * V
+        assert mom == pytest.approx(q * pos[d].sum(), rel=1e-12)
+    # a linear field is interpolated exactly
+    zz, yy, xx = np.meshgrid(*grid[::-1], indexing="ij")
+    ef = np.stack([2.0 * xx - yy, 3.0 * zz + 1.0, -xx + yy + zz])
+    got = sc.gather(pos, ef, box, shape=2)
+    X, Y, Z = pos
+    want = np.stack([2 * X - Y, 3 * Z + 1, -X + Y + Z])
+    assert np.allclose(got, want, rtol=1e-12, atol=1e-12)
+
+
+def test_tsc_field_converges_to_cic_and_to_the_coulomb_sum():
+    # the same bunch with both shapes: the TSC grid field approaches the direct
+    # Coulomb field as the CIC one does (regression slope and virial in the
+    # core, as for CIC above), and the two grid fields agree closely
+    rng = np.random.default_rng(7)
+    npart = 2000
+    sig = np.array([[1e-3], [1.2e-3], [2e-3]])
+    pos = rng.standard_normal((3, npart)) * sig
+    q = 1e-12
+    direct = sc.coulomb_direct(pos, q)
+    core = ((pos / sig) ** 2).sum(axis=0) < 2.0 ** 2
+    n = 32
+    box, _ = sc.box_rule(pos, None)
+    h = box.h(n)
+    ghat = sc.green_hat(n, h)
+    fields = {}
+    for shape in (1, 2):
+        phi = sc.solve(sc.deposit(pos, q, box, n, shape), h, ghat)
+        fields[shape] = sc.gather(pos, sc.field(phi, h), box, shape)
+    for c in range(3):
+        a, b = fields[2][c, core], direct[c, core]
+        slope = (a @ b) / (a @ a)
+        virial = (pos[c] * fields[2][c]).sum() / (pos[c] * direct[c]).sum()
+        assert 0.95 < slope < 1.1 and 0.95 < virial < 1.02
+    scale = np.sqrt(np.mean(fields[1] ** 2))
+    assert np.sqrt(np.mean((fields[2] - fields[1]) ** 2)) / scale < 0.1
