@@ -28,7 +28,8 @@ int32_t bx_create(bx_ctx **out, const bx_options *opt) {
     int n = opt->n_grid;
     if (n < 8 || n > 256 || (n & (n - 1)) != 0)
         return fail(nullptr, BX_BAD_ARG, "n_grid must be a power of two in [8, 256]");
-    if (opt->shape_order != 1) return fail(nullptr, BX_BAD_ARG, "shape_order must be 1 (CIC)");
+    if (opt->shape_order != 1 && opt->shape_order != 2)
+        return fail(nullptr, BX_BAD_ARG, "shape_order must be 1 (CIC) or 2 (TSC)");
     if (opt->rebin_interval < -1) return fail(nullptr, BX_BAD_ARG, "rebin_interval must be >= -1");
     if (opt->bin_edge != 0 && !sort_brick_edge_valid(n, opt->bin_edge))
         return fail(nullptr, BX_BAD_ARG,
@@ -38,6 +39,7 @@ int32_t bx_create(bx_ctx **out, const bx_options *opt) {
     ctx->n = n;
     ctx->sort_interval = opt->rebin_interval == 0 ? 16 : opt->rebin_interval < 0 ? 0 : opt->rebin_interval;
     ctx->bin_edge = opt->bin_edge;
+    ctx->shape = opt->shape_order;
     ctx->prof = profiler_new();
     const size_t n3 = (size_t)n * n * n, q3 = (size_t)(n + 2) * (n + 2) * (n + 2);
     const size_t o3 = (size_t)(n + 1) * (n + 1) * (n + 1);
@@ -316,7 +318,8 @@ int32_t bx_deposit(bx_ctx *ctx, const bx_beam *beam, bx_grid *grid, void *stream
     }
     const double q_macro =
         beam->n > 0 ? r.sign * std::fabs(beam->bunch_charge_C) / (double)beam->n : 0.0;
-    CK(launch_deposit(c, beam->n, r.bg, box, hb, ctx->n, ctx->acc_hi, ctx->acc_lo, ctx->status, s),
+    CK(launch_deposit(c, beam->n, r.bg, box, hb, ctx->n, ctx->acc_hi, ctx->acc_lo, ctx->status, s,
+                      ctx->shape),
        "deposit");
     CK(launch_acc_to_rho(ctx->acc_hi, ctx->acc_lo, ctx->n, q_macro, box, grid->rho, s), "rho");
     return BX_OK;
@@ -363,7 +366,7 @@ int32_t bx_gather_kick(bx_ctx *ctx, bx_beam *beam, const bx_grid *grid, double d
        "field");
     CK(launch_kick_push_deposit(beam->coord, beam->n, r.bg, ctx->tmp_box, b, ctx->n, ctx->efix,
                                 ctx->escale, nullptr, false, nullptr, nullptr, nullptr,
-                                ctx->status, s),
+                                ctx->status, s, ctx->shape),
        "gather/kick");
     return BX_OK;
 }

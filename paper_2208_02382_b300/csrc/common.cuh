@@ -138,7 +138,7 @@ cudaError_t launch_minmax(double *const c[6], int64_t n, double betagamma, Track
                           int32_t *status, cudaStream_t s);
 cudaError_t launch_deposit(double *const c[6], int64_t n, double betagamma, const Box *box,
                            const Box &box_host, int nn, unsigned long long *acc_hi,
-                           unsigned long long *acc_lo, int32_t *status, cudaStream_t s);
+                           unsigned long long *acc_lo, int32_t *status, cudaStream_t s, int shape = 1);
 cudaError_t launch_acc_to_rho(const unsigned long long *acc_hi, const unsigned long long *acc_lo,
                               int nn, double q_macro, const Box *box, double *rho,
                               cudaStream_t s);
@@ -147,7 +147,7 @@ cudaError_t launch_kick_push_deposit(double *const c[6], int64_t n, double betag
                                      const int *escale,
                                      const MapCoef *map_host, bool deposit,
                                      unsigned long long *acc_hi, unsigned long long *acc_lo,
-                                     TrackState *st, int32_t *status, cudaStream_t s);
+                                     TrackState *st, int32_t *status, cudaStream_t s, int shape = 1);
 cudaError_t launch_box_rule(TrackState *st, int nn, int64_t n, long long *log, int64_t log_cap,
                             bool advance, cudaStream_t s);
 cudaError_t launch_field(const double *phi, int nn, const Box *box, double kx, double ky,
@@ -162,7 +162,7 @@ cudaError_t launch_track_particles(double *const c[6], int64_t n, double betagam
                                    const Box *box, int nn, const EFix *ef, const int *escale,
                                    const MapCoef *maps, unsigned long long *acc_hi,
                                    unsigned long long *acc_lo, TrackState *st, int32_t *status,
-                                   cudaStream_t s, int part = 3);
+                                   cudaStream_t s, int part = 3, int shape = 1);
 cudaError_t launch_box_rule_graph(TrackState *st, int nn, long long *log, int64_t cap,
                                   cudaGraphConditionalHandle hg, cudaGraphConditionalHandle hs,
                                   cudaGraphConditionalHandle hd, cudaGraphConditionalHandle hn,
@@ -174,10 +174,10 @@ cudaError_t launch_track_particles_oop(double *const cin[6], double *const cout[
                                        double betagamma, const Box *box, int nn, const EFix *ef,
                                        const int *escale, const MapCoef *maps,
                                        unsigned long long *acc_hi, unsigned long long *acc_lo,
-                                       TrackState *st, int32_t *status, cudaStream_t s);
+                                       TrackState *st, int32_t *status, cudaStream_t s, int shape = 1);
 cudaError_t launch_track_deposit(double *const c[6], int64_t n, double betagamma, const Box *box,
                                  int nn, unsigned long long *acc_hi, unsigned long long *acc_lo,
-                                 TrackState *st, int32_t *status, cudaStream_t s);
+                                 TrackState *st, int32_t *status, cudaStream_t s, int shape = 1);
 int map_kind(const MapCoef &m);
 // sort.cu
 int sort_brick_edge(int nn, int be_opt);

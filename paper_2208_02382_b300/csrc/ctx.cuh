@@ -45,6 +45,7 @@ struct bx_ctx {
     long long *counts = nullptr, *offs = nullptr, *sums = nullptr, *id_scr = nullptr;
     double *scr[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     double **dev_ptrs = nullptr;
+    int shape = 1;                         // particle shape: 1 CIC, 2 TSC
     int sort_interval = 16;                // kicks between re-binning (0: never)
     int bin_edge = 0;                      // cells per bin edge (0: default)
     int sort_nb = 0;                       // bins the sort scratch is sized for

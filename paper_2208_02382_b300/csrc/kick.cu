@@ -35,7 +35,7 @@ cudaError_t kick_sort(const KickArgs &k, cudaStream_t s) {
 cudaError_t kick_deposit(const KickArgs &k, cudaStream_t s) {
     bx_ctx *ctx = k.ctx;
     return launch_track_deposit(k.c, k.n, k.bg, &ctx->st->box, ctx->n, ctx->acc_hi, ctx->acc_lo,
-                                ctx->st, ctx->status, s);
+                                ctx->st, ctx->status, s, ctx->shape);
 }
 
 cudaError_t kick_solve_field_push(const KickArgs &k, cudaStream_t s) {
@@ -47,14 +47,16 @@ cudaError_t kick_solve_field_push(const KickArgs &k, cudaStream_t s) {
                          ctx->efix, ctx->escale, s, ctx->st, ctx->maps);
     if (e == cudaSuccess)
         e = launch_track_particles(k.c, k.n, k.bg, &ctx->st->box, ctx->n, ctx->efix, ctx->escale,
-                                   ctx->maps, ctx->acc_hi, ctx->acc_lo, ctx->st, ctx->status, s, 1);
+                                   ctx->maps, ctx->acc_hi, ctx->acc_lo, ctx->st, ctx->status, s, 1,
+                                   ctx->shape);
     return e;
 }
 
 cudaError_t kick_next_deposit(const KickArgs &k, cudaStream_t s) {
     bx_ctx *ctx = k.ctx;
     return launch_track_particles(k.c, k.n, k.bg, &ctx->st->box, ctx->n, ctx->efix, ctx->escale,
-                                  ctx->maps, ctx->acc_hi, ctx->acc_lo, ctx->st, ctx->status, s, 2);
+                                  ctx->maps, ctx->acc_hi, ctx->acc_lo, ctx->st, ctx->status, s, 2,
+                                  ctx->shape);
 }
 
 // Plain launches of one kick (gated kernels return at once when not needed).

@@ -468,7 +468,48 @@ struct PartArgs {
     const int *gate;                   // if set and 0, the kernel does nothing
     const MapCoef *maps;               // MAP_TABLE: per-call map table (entry 1 + k)
     const TrackState *dst;             // device-driven: exact_u and k from here
+    int shape;                         // particle shape: 1 CIC, 2 TSC
 };
+
+// Node and offset for the TSC shape (particle shape 2): u limited to
+// [1/2, n - 3/2], nearest node i = floor(u + 1/2) limited to [1, n-2], and
+// G = (u - i + 1/2) 2^52 in [0, 2^52] (so f = u - i = G 2^-52 - 1/2), with
+// integer operations only; `outside` as for CIC.
+__device__ __forceinline__ void tsc_node(double u, int nn, int &node, unsigned long long &G,
+                                         bool &outside) {
+    const unsigned long long umax = (unsigned long long)(nn - 1) << 52;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(u);
+    unsigned long long U = to_fixed52(u);
+    outside |= ((b >> 63) && abs_bits(u) > NEG_TOL_BITS) || U > umax + 4503599627ull;
+    const unsigned long long ulo = 1ull << 51, uhi = (unsigned long long)(2 * nn - 3) << 51;
+    U = U < ulo ? ulo : (U > uhi ? uhi : U);
+    const unsigned long long V = U + (1ull << 51);
+    unsigned long long i = V >> 52;
+    if (i > (unsigned long long)(nn - 2)) i = nn - 2;
+    G = V - (i << 52);
+    node = (int)i;
+}
+
+// TSC weights of nodes i-1, i, i+1 as 52-bit fractions: (1-g)^2/2, the rest,
+// g^2/2 (their sum is exactly 2^52).
+__device__ __forceinline__ void tsc_weights(unsigned long long G, Frac w[3]) {
+    const unsigned long long one = 1ull << 52;
+    const unsigned long long wp = mulshr52(split26(G), split26(G)) >> 1;
+    const unsigned long long wm = mulshr52(split26(one - G), split26(one - G)) >> 1;
+    w[0] = split26(wm);
+    w[1] = split26(one - wm - wp);
+    w[2] = split26(wp);
+}
+
+// (e * W) >> 52 for a signed e (|e| < 2^51) and a fraction W <= 2^52, from
+// 26-bit limbs (error below 2 units of the last place).
+__device__ __forceinline__ long long mulfrac52(long long e, Frac W) {
+    const int eh = (int)(e >> 26);
+    const unsigned el = (unsigned)(e & 0x3FFFFFFll);
+    const long long hh = (long long)eh * (long long)W.hi;
+    const long long mid = (long long)eh * (long long)W.lo + (long long)((unsigned long long)el * W.hi);
+    return hh + (mid >> 26);
+}
 
 // u = (X - lo)/h.  For a box whose offset is small against its cell size
 // (|lo/h| <= 4096, every ordinary box) one FMA, X*(1/h) - lo/h, is within
@@ -477,12 +518,14 @@ struct PartArgs {
 bool box_needs_exact_u(const Box &b) { return box_far_offset(b); }
 
 
-// GATHER: CIC interpolation of the fixed-point field at the current position,
-//         kick, then the map (MK) and the store.
-// DEP:    CIC deposit of the new position (same box) into the accumulators,
-//         through a shared-memory tile covering the block's cells when they fit.
+// GATHER: interpolation of the fixed-point field at the current position
+//         (SH 1: CIC in lerp form; SH 2: TSC, separable sums of fixed-point
+//         products), kick, then the map (MK) and the store.
+// DEP:    deposit of the new position (same box, same shape) into the
+//         accumulators, through a shared-memory tile covering the block's
+//         nodes when they fit.
 // MM:     min/max keys of the new rest-frame positions.
-template <int MK, bool GATHER, bool DEP, bool MM>
+template <int MK, bool GATHER, bool DEP, bool MM, int SH>
 __global__ void __launch_bounds__(TPB, 3) k_particles(PartArgs a) {
     if (a.gate && *a.gate == 0) return;
     if (a.dst) a.exact_u = a.dst->exact_u;
@@ -522,29 +565,56 @@ __global__ void __launch_bounds__(TPB, 3) k_particles(PartArgs a) {
             int c0, c1, c2;
             unsigned long long G0, G1, G2;
             bool out0 = false;
-            if (a.exact_u) {
-                cell_frac((x - lo0) * ih0, nn, c0, G0, out0);
-                cell_frac((y - lo1) * ih1, nn, c1, G1, out0);
-                cell_frac((__dmul_rn(a.nbg, t) - lo2) * ih2, nn, c2, G2, out0);
-            } else {
-                cell_frac(fma(x, ih0, o0), nn, c0, G0, out0);
-                cell_frac(fma(y, ih1, o1), nn, c1, G1, out0);
-                cell_frac(fma(t, tz, o2), nn, c2, G2, out0);
-            }
-            const Frac F0 = split26(G0), F1 = split26(G1), F2 = split26(G2);
-            outside |= out0;
-            // CIC interpolation in lerp form, one field component at a time (a
-            // small live register set): x on the four (y, z) edges, then y, z.
-            const long long *e = &a.ef[((long long)c2 * nn + c1) * nn + c0].x;
-            const long long sy = 4LL * nn, sz = 4LL * nn * nn;  // in int64 units (4 per node)
+            const double u0 = a.exact_u ? (x - lo0) * ih0 : fma(x, ih0, o0);
+            const double u1 = a.exact_u ? (y - lo1) * ih1 : fma(y, ih1, o1);
+            const double u2 = a.exact_u ? (__dmul_rn(a.nbg, t) - lo2) * ih2 : fma(t, tz, o2);
             long long comp[3];
+            const long long sy = 4LL * nn, sz = 4LL * nn * nn;  // in int64 units (4 per node)
+            if constexpr (SH == 2) {
+                tsc_node(u0, nn, c0, G0, out0);
+                tsc_node(u1, nn, c1, G1, out0);
+                tsc_node(u2, nn, c2, G2, out0);
+                outside |= out0;
+                Frac wx[3], wy[3], wz[3];
+                tsc_weights(G0, wx);
+                tsc_weights(G1, wy);
+                tsc_weights(G2, wz);
+                // separable: along x on the nine (y, z) lines, then y, then z
+                const long long *e = &a.ef[((long long)(c2 - 1) * nn + (c1 - 1)) * nn + (c0 - 1)].x;
 #pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
-                const long long *q = e + cc;
-                const long long g00 = lerp52(q[0], q[4], F0), g01 = lerp52(q[sy], q[sy + 4], F0);
-                const long long g10 = lerp52(q[sz], q[sz + 4], F0),
-                                g11 = lerp52(q[sz + sy], q[sz + sy + 4], F0);
-                comp[cc] = lerp52(lerp52(g00, g01, F1), lerp52(g10, g11, F1), F2);
+                for (int cc = 0; cc < 3; ++cc) {
+                    long long gz = 0;
+#pragma unroll
+                    for (int dz = 0; dz < 3; ++dz) {
+                        long long gy = 0;
+#pragma unroll
+                        for (int dy = 0; dy < 3; ++dy) {
+                            const long long *q = e + cc + dz * sz + dy * sy;
+                            const long long gx = mulfrac52(q[0], wx[0]) + mulfrac52(q[4], wx[1]) +
+                                                 mulfrac52(q[8], wx[2]);
+                            gy += mulfrac52(gx, wy[dy]);
+                        }
+                        gz += mulfrac52(gy, wz[dz]);
+                    }
+                    comp[cc] = gz;
+                }
+            } else {
+                cell_frac(u0, nn, c0, G0, out0);
+                cell_frac(u1, nn, c1, G1, out0);
+                cell_frac(u2, nn, c2, G2, out0);
+                const Frac F0 = split26(G0), F1 = split26(G1), F2 = split26(G2);
+                outside |= out0;
+                // CIC interpolation in lerp form, one field component at a time (a
+                // small live register set): x on the four (y, z) edges, then y, z.
+                const long long *e = &a.ef[((long long)c2 * nn + c1) * nn + c0].x;
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) {
+                    const long long *q = e + cc;
+                    const long long g00 = lerp52(q[0], q[4], F0), g01 = lerp52(q[sy], q[sy + 4], F0);
+                    const long long g10 = lerp52(q[sz], q[sz + 4], F0),
+                                    g11 = lerp52(q[sz + sy], q[sz + sy + 4], F0);
+                    comp[cc] = lerp52(lerp52(g00, g01, F1), lerp52(g10, g11, F1), F2);
+                }
             }
             const long long ex = comp[0], ey = comp[1], ez = comp[2];
             px += i64_scaled_to_double(ex, e0);
@@ -574,14 +644,17 @@ __global__ void __launch_bounds__(TPB, 3) k_particles(PartArgs a) {
                 int c0, c1, c2;
                 unsigned long long F0, F1, F2;
                 bool out1 = false;
-                if (a.exact_u) {
-                    cell_frac((x - lo0) * ih0, nn, c0, F0, out1);
-                    cell_frac((y - lo1) * ih1, nn, c1, F1, out1);
-                    cell_frac((__dmul_rn(a.nbg, t) - lo2) * ih2, nn, c2, F2, out1);
+                const double u0 = a.exact_u ? (x - lo0) * ih0 : fma(x, ih0, o0);
+                const double u1 = a.exact_u ? (y - lo1) * ih1 : fma(y, ih1, o1);
+                const double u2 = a.exact_u ? (__dmul_rn(a.nbg, t) - lo2) * ih2 : fma(t, tz, o2);
+                if constexpr (SH == 2) {  // nearest node and offset
+                    tsc_node(u0, nn, c0, F0, out1);
+                    tsc_node(u1, nn, c1, F1, out1);
+                    tsc_node(u2, nn, c2, F2, out1);
                 } else {
-                    cell_frac(fma(x, ih0, o0), nn, c0, F0, out1);
-                    cell_frac(fma(y, ih1, o1), nn, c1, F1, out1);
-                    cell_frac(fma(t, tz, o2), nn, c2, F2, out1);
+                    cell_frac(u0, nn, c0, F0, out1);
+                    cell_frac(u1, nn, c1, F1, out1);
+                    cell_frac(u2, nn, c2, F2, out1);
                 }
                 if (out1 && a.flag_outside) outside = true;  // box not containing the bunch
                 if (!out1) {  // particles outside are left out: the box rule then regrids
@@ -616,9 +689,12 @@ __global__ void __launch_bounds__(TPB, 3) k_particles(PartArgs a) {
             }
         }
         __syncthreads();
-        const int i0 = s_bb[0], j0 = s_bb[1], l0 = s_bb[2];
-        if (i0 == INT_MAX) return;  // nothing to deposit in this block
-        const int tx = s_bb[3] - i0 + 2, ty = s_bb[4] - j0 + 2, tz = s_bb[5] - l0 + 2;
+        if (s_bb[0] == INT_MAX) return;  // nothing to deposit in this block
+        // CIC: nodes c..c+1 of the cells c; TSC: nodes c-1..c+1 around the nodes c
+        constexpr int LOW = SH == 2 ? 1 : 0, SPAN = SH == 2 ? 3 : 2;
+        const int i0 = s_bb[0] - LOW, j0 = s_bb[1] - LOW, l0 = s_bb[2] - LOW;
+        const int tx = s_bb[3] - s_bb[0] + SPAN, ty = s_bb[4] - s_bb[1] + SPAN,
+                  tz = s_bb[5] - s_bb[2] + SPAN;
         const bool use_tile = (long long)tx * ty * tz <= TILE_CAP;
         const unsigned long long one = 1ull << 52;
         if (use_tile) {
@@ -632,22 +708,34 @@ __global__ void __launch_bounds__(TPB, 3) k_particles(PartArgs a) {
             const int cell = scell[slot];
             if (cell < 0) continue;
             const unsigned long long F0 = sF[slot], F1 = sF[CHUNK + slot], F2 = sF[2 * CHUNK + slot];
-            const Frac wx[2] = {split26(one - F0), split26(F0)}, wy[2] = {split26(one - F1), split26(F1)},
-                       wz[2] = {split26(one - F2), split26(F2)};
             const int c2 = cell / nn2, c1 = (cell / nn) % nn, c0 = cell % nn;
+            Frac wx[SPAN], wy[SPAN], wz[SPAN];
+            if constexpr (SH == 2) {
+                tsc_weights(F0, wx);
+                tsc_weights(F1, wy);
+                tsc_weights(F2, wz);
+            } else {
+                wx[0] = split26(one - F0);
+                wx[1] = split26(F0);
+                wy[0] = split26(one - F1);
+                wy[1] = split26(F1);
+                wz[0] = split26(one - F2);
+                wz[1] = split26(F2);
+            }
 #pragma unroll
-            for (int dz = 0; dz < 2; ++dz)
+            for (int dz = 0; dz < SPAN; ++dz)
 #pragma unroll
-                for (int dy = 0; dy < 2; ++dy) {
+                for (int dy = 0; dy < SPAN; ++dy) {
                     const Frac wyz = split26(mulshr52(wy[dy], wz[dz]));
 #pragma unroll
-                    for (int dx = 0; dx < 2; ++dx) {
+                    for (int dx = 0; dx < SPAN; ++dx) {
                         const unsigned long long v = mulshr52(wx[dx], wyz) >> 1;  // 51-bit
+                        const int ni = c0 + dx - LOW, nj = c1 + dy - LOW, nl = c2 + dz - LOW;
                         if (use_tile) {
-                            const int li = ((c2 + dz - l0) * ty + (c1 + dy - j0)) * tx + (c0 + dx - i0);
+                            const int li = ((nl - l0) * ty + (nj - j0)) * tx + (ni - i0);
                             atomicAdd(&tile[li], v);
                         } else {
-                            const long long node = cell + (long long)dz * nn2 + dy * nn + dx;
+                            const long long node = ((long long)nl * nn + nj) * nn + ni;
                             atomicAdd(&a.acc_hi[node], v >> DEP_SPLIT);
                             atomicAdd(&a.acc_lo[node], v & ((1ull << DEP_SPLIT) - 1));
                         }
@@ -672,18 +760,27 @@ static size_t particles_smem(bool dep) {
     return dep ? (size_t)(3 * CHUNK + CHUNK / 2 + TILE_CAP) * sizeof(unsigned long long) : 0;
 }
 
-template <int MK, bool G, bool D, bool M>
-static cudaError_t launch_pk(const PartArgs &a, cudaStream_t s, int kid) {
+template <int MK, bool G, bool D, bool M, int SH>
+static cudaError_t launch_pk_sh(const PartArgs &a, cudaStream_t s, int kid) {
     const size_t sm = particles_smem(D);
-    if (D) cudaFuncSetAttribute(k_particles<MK, G, D, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)sm);
+    if (D)
+        cudaFuncSetAttribute(k_particles<MK, G, D, M, SH>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const unsigned blocks = (unsigned)((a.n + CHUNK - 1) / CHUNK);
-    BT_LAUNCH(kid, s, k_particles<MK, G, D, M><<<blocks, TPB, sm, s>>>(a));
+    BT_LAUNCH(kid, s, k_particles<MK, G, D, M, SH><<<blocks, TPB, sm, s>>>(a));
     return cudaGetLastError();
 }
 
-static PartArgs part_args(double *const c[6], int64_t n, double betagamma, const Box *box, int nn) {
+template <int MK, bool G, bool D, bool M>
+static cudaError_t launch_pk(const PartArgs &a, cudaStream_t s, int kid) {
+    return a.shape == 2 ? launch_pk_sh<MK, G, D, M, 2>(a, s, kid)
+                        : launch_pk_sh<MK, G, D, M, 1>(a, s, kid);
+}
+
+static PartArgs part_args(double *const c[6], int64_t n, double betagamma, const Box *box, int nn,
+                          int shape) {
     PartArgs a{};
+    a.shape = shape;
     a.x = c[0];
     a.px = c[1];
     a.y = c[2];
@@ -707,9 +804,9 @@ cudaError_t launch_kick_push_deposit(double *const c[6], int64_t n, double betag
                                      const Box *box, const Box &box_host, int nn, const EFix *ef,
                                      const int *escale, const MapCoef *map_host, bool deposit,
                                      unsigned long long *acc_hi, unsigned long long *acc_lo,
-                                     TrackState *st, int32_t *status, cudaStream_t s) {
+                                     TrackState *st, int32_t *status, cudaStream_t s, int shape) {
     if (n <= 0) return cudaSuccess;
-    PartArgs a = part_args(c, n, betagamma, box, nn);
+    PartArgs a = part_args(c, n, betagamma, box, nn, shape);
     a.exact_u = box_needs_exact_u(box_host) ? 1 : 0;
     a.ef = ef;
     a.escale = escale;
@@ -739,9 +836,9 @@ cudaError_t launch_track_particles(double *const c[6], int64_t n, double betagam
                                    const Box *box, int nn, const EFix *ef, const int *escale,
                                    const MapCoef *maps, unsigned long long *acc_hi,
                                    unsigned long long *acc_lo, TrackState *st, int32_t *status,
-                                   cudaStream_t s, int part) {
+                                   cudaStream_t s, int part, int shape) {
     if (n <= 0) return cudaSuccess;
-    PartArgs a = part_args(c, n, betagamma, box, nn);
+    PartArgs a = part_args(c, n, betagamma, box, nn, shape);
     a.ef = ef;
     a.escale = escale;
     a.acc_hi = acc_hi;
@@ -765,9 +862,9 @@ cudaError_t launch_track_particles_oop(double *const cin[6], double *const cout[
                                        double betagamma, const Box *box, int nn, const EFix *ef,
                                        const int *escale, const MapCoef *maps,
                                        unsigned long long *acc_hi, unsigned long long *acc_lo,
-                                       TrackState *st, int32_t *status, cudaStream_t s) {
+                                       TrackState *st, int32_t *status, cudaStream_t s, int shape) {
     if (n <= 0) return cudaSuccess;
-    PartArgs a = part_args(cin, n, betagamma, box, nn);
+    PartArgs a = part_args(cin, n, betagamma, box, nn, shape);
     a.ox = cout[0];
     a.opx = cout[1];
     a.oy = cout[2];
@@ -784,7 +881,7 @@ cudaError_t launch_track_particles_oop(double *const cin[6], double *const cout[
     if (e != cudaSuccess) return e;
     e = launch_zero_acc(acc_hi, acc_lo, nn, &st->next_gate, s);
     if (e != cudaSuccess) return e;
-    PartArgs b = part_args(cout, n, betagamma, box, nn);
+    PartArgs b = part_args(cout, n, betagamma, box, nn, shape);
     b.acc_hi = acc_hi;
     b.acc_lo = acc_lo;
     b.st = st;
@@ -797,10 +894,10 @@ cudaError_t launch_track_particles_oop(double *const cin[6], double *const cout[
 // Device-driven deposit of the current positions when the box rule asks for it.
 cudaError_t launch_track_deposit(double *const c[6], int64_t n, double betagamma, const Box *box,
                                  int nn, unsigned long long *acc_hi, unsigned long long *acc_lo,
-                                 TrackState *st, int32_t *status, cudaStream_t s) {
+                                 TrackState *st, int32_t *status, cudaStream_t s, int shape) {
     cudaError_t e = launch_zero_acc(acc_hi, acc_lo, nn, &st->deposit_gate, s);
     if (e != cudaSuccess || n <= 0) return e;
-    PartArgs a = part_args(c, n, betagamma, box, nn);
+    PartArgs a = part_args(c, n, betagamma, box, nn, shape);
     a.acc_hi = acc_hi;
     a.acc_lo = acc_lo;
     a.status = status;
@@ -816,14 +913,14 @@ cudaError_t launch_track_deposit(double *const c[6], int64_t n, double betagamma
 // on particle order.  Particles outside the box are left out and flagged.
 cudaError_t launch_deposit(double *const c[6], int64_t n, double betagamma, const Box *box,
                            const Box &box_host, int nn, unsigned long long *acc_hi,
-                           unsigned long long *acc_lo, int32_t *status, cudaStream_t s) {
+                           unsigned long long *acc_lo, int32_t *status, cudaStream_t s, int shape) {
     size_t nodes = (size_t)nn * nn * nn;
     cudaError_t e = cudaMemsetAsync(acc_hi, 0, nodes * 8, s);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(acc_lo, 0, nodes * 8, s);
     if (e != cudaSuccess) return e;
     if (n <= 0) return cudaSuccess;
-    PartArgs a = part_args(c, n, betagamma, box, nn);
+    PartArgs a = part_args(c, n, betagamma, box, nn, shape);
     a.acc_hi = acc_hi;
     a.acc_lo = acc_lo;
     a.status = status;

@@ -71,7 +71,7 @@ int main(void) {
                      L.BX_DEVICE_TIMEOUT, L.BX_CUDA, L.BX_DRIFT, L.BX_QUAD, L.BX_SBEND]
 
 
-@pytest.mark.parametrize("n_grid,order", [(7, 1), (12, 1), (4, 1), (512, 1), (32, 2)])
+@pytest.mark.parametrize("n_grid,order", [(7, 1), (12, 1), (4, 1), (512, 1), (32, 3), (32, 0)])
 def test_create_rejects_bad_options_on_host(lib, n_grid, order):
     opt = L.bx_options()
     opt.n_grid, opt.shape_order = n_grid, order
