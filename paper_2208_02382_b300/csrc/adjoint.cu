@@ -94,10 +94,10 @@ struct CellU {
         ih0 = b.inv_h[0];
         ih1 = b.inv_h[1];
         ih2 = b.inv_h[2];
-        o0 = -b.lo[0] * ih0;
-        o1 = -b.lo[1] * ih1;
-        o2 = -b.lo[2] * ih2;
-        tz = nbg * ih2;
+        o0 = b.off[0];
+        o1 = b.off[1];
+        o2 = b.off[2];
+        tz = b.tz;
         lo0 = b.lo[0];
         lo1 = b.lo[1];
         lo2 = b.lo[2];

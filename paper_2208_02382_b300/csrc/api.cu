@@ -219,7 +219,7 @@ int32_t track_impl(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t fi
     // per-kick map and kick factors come from the table at index 1 + k; no
     // host decision or synchronisation between kicks.
     CK(launch_call_init(ctx->st, (int)nkicks, q_macro, binning ? ctx->sort_interval : 0,
-                        ctx->kick, s),
+                        ctx->kick, s, r.bg),
        "call init");
     if (binning) CK(sort_set_pointers(c, ctx->scr, ctx->dev_ptrs, s), "sort pointers");
     CK(launch_push_maps(c, beam->n, ctx->maps, 1, s), "push");
@@ -293,13 +293,15 @@ int32_t bx_deposit(bx_ctx *ctx, const bx_beam *beam, bx_grid *grid, void *stream
             if (!(grid->hi[d] > grid->lo[d]) || !std::isfinite(grid->lo[d]) ||
                 !std::isfinite(grid->hi[d]))
                 return fail(ctx, BX_BAD_ARG, "grid box needs finite lo < hi");
-        Box b = explicit_box(grid->lo, grid->hi, ctx->n);
+        Box b = explicit_box(grid->lo, grid->hi, ctx->n, r.bg);
         hb = b;
         CK(cudaMemcpyAsync(ctx->tmp_box, &b, sizeof(b), cudaMemcpyHostToDevice, s), "box");
         for (int d = 0; d < 3; ++d) grid->h[d] = b.h[d];
         box = ctx->tmp_box;
     } else {
         if (beam->n == 0) return fail(ctx, BX_BAD_ARG, "box rule needs particles");
+        const double nbg = -r.bg;
+        CK(cudaMemcpyAsync(&ctx->st->nbg, &nbg, sizeof(nbg), cudaMemcpyHostToDevice, s), "beta gamma");
         CK(launch_minmax(c, beam->n, r.bg, ctx->st, ctx->status, s), "minmax");
         CK(cudaMemcpyAsync(&ctx->st->kick, &ctx->kick, sizeof(long long), cudaMemcpyHostToDevice, s),
            "kick counter");
@@ -358,6 +360,7 @@ int32_t bx_gather_kick(bx_ctx *ctx, bx_beam *beam, const bx_grid *grid, double d
         b.h[d] = grid->h[d];
         b.inv_h[d] = 1.0 / grid->h[d];
     }
+    box_finish(b, -r.bg);
     CK(cudaMemcpyAsync(ctx->tmp_box, &b, sizeof(b), cudaMemcpyHostToDevice, s), "box");
     const double kt = r.sign * ds / (r.mass_eV * (r.bg * r.bg));
     const double kz = -r.sign * ds / (r.mass_eV * r.bg);

@@ -37,9 +37,18 @@ struct __align__(32) EFix {
 };
 
 // Grid box as the kernels read it (device resident for tracking).
+// off = -lo * (1/h) and tz = -(beta gamma) * (1/h_z) are the per-box constants
+// of u = X * (1/h) + off (Z = -beta gamma t: u_z = t * tz + off_z), formed once
+// per box rule (or per explicit box) instead of in every particle thread.
 struct Box {
     double lo[3], hi[3], h[3], inv_h[3];
+    double off[3], tz;
 };
+
+__host__ __device__ inline void box_finish(Box &b, double nbg) {
+    for (int d = 0; d < 3; ++d) b.off[d] = -b.lo[d] * b.inv_h[d];
+    b.tz = nbg * b.inv_h[2];
+}
 
 // Tracking state kept on the device between kicks.
 struct TrackState {
@@ -65,6 +74,7 @@ struct TrackState {
     int32_t halt;           // non-finite box: skip the space-charge work
     double q_macro;         // macroparticle charge [C]
     double rho_scale;       // q_macro / (hx hy hz)
+    double nbg;             // -beta gamma of the beam being tracked
     // Differentiation runs (null otherwise; indexed by the kick counter):
     Box *box_hist;          // the box of every kick is recorded here
     const Box *box_replay;  // the box of every kick is taken from here
@@ -155,7 +165,7 @@ cudaError_t launch_field(const double *phi, int nn, const Box *box, double kx, d
                          int *escale, cudaStream_t s, const TrackState *st = nullptr,
                          const MapCoef *maps = nullptr);
 cudaError_t launch_call_init(TrackState *st, int nkicks, double q_macro, int sort_interval,
-                             long long kick0, cudaStream_t s);
+                             long long kick0, cudaStream_t s, double betagamma);
 cudaError_t launch_zero_acc(unsigned long long *a, unsigned long long *b, int nn, const int *gate,
                             cudaStream_t s);
 cudaError_t launch_track_particles(double *const c[6], int64_t n, double betagamma,
@@ -169,7 +179,7 @@ cudaError_t launch_box_rule_graph(TrackState *st, int nn, long long *log, int64_
                                   cudaStream_t s, cudaGraphConditionalHandle hl = 0,
                                   bool has_loop = false);
 cudaError_t launch_state_reset(TrackState *st, int nkicks, double q_macro, int sort_interval,
-                               cudaStream_t s);
+                               cudaStream_t s, double betagamma);
 cudaError_t launch_track_particles_oop(double *const cin[6], double *const cout[6], int64_t n,
                                        double betagamma, const Box *box, int nn, const EFix *ef,
                                        const int *escale, const MapCoef *maps,

@@ -192,7 +192,7 @@ int32_t check_grid(bx_ctx *ctx, const bx_grid *g, bool need_rho, bool need_phi) 
     return BX_OK;
 }
 
-Box explicit_box(const double lo[3], const double hi[3], int n) {
+Box explicit_box(const double lo[3], const double hi[3], int n, double betagamma) {
     Box b;
     for (int d = 0; d < 3; ++d) {
         b.lo[d] = lo[d];
@@ -200,6 +200,7 @@ Box explicit_box(const double lo[3], const double hi[3], int n) {
         b.h[d] = (hi[d] - lo[d]) / (double)(n - 1);
         b.inv_h[d] = 1.0 / b.h[d];
     }
+    box_finish(b, -betagamma);
     return b;
 }
 

@@ -109,7 +109,7 @@ void build_map_table(const bx_lattice *lat, const std::vector<int> &sel,
 int32_t check_beam(bx_ctx *ctx, const bx_beam *b);
 int32_t check_lattice(bx_ctx *ctx, const bx_lattice *l);
 int32_t check_grid(bx_ctx *ctx, const bx_grid *g, bool need_rho, bool need_phi);
-Box explicit_box(const double lo[3], const double hi[3], int n);
+Box explicit_box(const double lo[3], const double hi[3], int n, double betagamma);
 int32_t ensure_green(bx_ctx *ctx, const double h[3], cudaStream_t s);
 int32_t ensure_maps(bx_ctx *ctx, size_t count);
 int32_t ensure_sort_scratch(bx_ctx *ctx, int64_t n);

@@ -347,7 +347,7 @@ int32_t bx_grad_forward(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat,
     CK(cudaStreamSynchronize(s), "sync");
     ctx->kick = 0;
     ctx->green_valid = false;
-    CK(launch_call_init(ctx->st, (int)K, g->q_macro, 0, 0, s), "call init");
+    CK(launch_call_init(ctx->st, (int)K, g->q_macro, 0, 0, s, g->ref.bg), "call init");
     CK(set_state_ptr<Box>(ctx->st, &TrackState::box_hist, g->box_hist, s), "state");
     CK(set_state_ptr<int32_t>(ctx->st, &TrackState::slot_hist, g->slot_hist, s), "state");
     {
@@ -370,7 +370,7 @@ int32_t bx_grad_forward(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat,
                        ctx->offs, ctx->sums, ctx->scr, ctx->id_scr, ctx->dev_ptrs, s),
            "initial binning");
         CK(cudaMemcpyAsync(ctx->st, &h, sizeof(h), cudaMemcpyHostToDevice, s), "state");
-        CK(launch_call_init(ctx->st, (int)K, g->q_macro, 0, 0, s), "call init");
+        CK(launch_call_init(ctx->st, (int)K, g->q_macro, 0, 0, s, g->ref.bg), "call init");
         CK(set_state_ptr<Box>(ctx->st, &TrackState::box_hist, g->box_hist, s), "state");
         CK(set_state_ptr<int32_t>(ctx->st, &TrackState::slot_hist, g->slot_hist, s), "state");
         const Box *rp = box_replay ? g->box_replay : nullptr;

@@ -11,6 +11,8 @@
 // the linear map, and adding the kick.  Cell indices, CIC fractions and
 // weights, the field interpolation, the charge accumulation and the min/max
 // run in 64-bit fixed point on the integer pipes.
+#include <type_traits>
+
 #include "common.cuh"
 #include "fixed.cuh"
 #include "particle_math.cuh"
@@ -189,6 +191,7 @@ __device__ void box_rule_body(TrackState *st, int nn, long long *log, int64_t ca
         if (st->nlog < cap) log[st->nlog] = st->kick;
         st->nlog += 1;
     }
+    box_finish(st->box, st->nbg);
     bool finite = true;
     for (int d = 0; d < 3; ++d)
         finite = finite && isfinite(st->box.lo[d]) && isfinite(st->box.hi[d]) && st->box.h[d] > 0.0;
@@ -257,7 +260,8 @@ cudaError_t launch_box_rule(TrackState *st, int nn, int64_t n, long long *log, i
 // A fresh tracking state (no box, no Green's function, counters 0) set up
 // for a call of nkicks kicks (the device-side counterpart of bx_reset +
 // the start of bx_track, for graphs that track from scratch at each launch).
-__global__ void k_state_reset(TrackState *st, int nkicks, double q_macro, int sort_interval) {
+__global__ void k_state_reset(TrackState *st, int nkicks, double q_macro, int sort_interval,
+                              double nbg) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         TrackState z;
         memset(&z, 0, sizeof(z));
@@ -269,19 +273,22 @@ __global__ void k_state_reset(TrackState *st, int nkicks, double q_macro, int so
         z.nkicks_call = nkicks;
         z.q_macro = q_macro;
         z.sort_interval = sort_interval;
+        z.nbg = nbg;
         *st = z;
     }
 }
 
 cudaError_t launch_state_reset(TrackState *st, int nkicks, double q_macro, int sort_interval,
-                               cudaStream_t s) {
-    BT_LAUNCH(K_BOX, s, k_state_reset<<<1, 32, 0, s>>>(st, nkicks, q_macro, sort_interval));
+                               cudaStream_t s, double betagamma) {
+    BT_LAUNCH(K_BOX, s, k_state_reset<<<1, 32, 0, s>>>(st, nkicks, q_macro, sort_interval,
+                                                        -betagamma));
     return cudaGetLastError();
 }
 
 __global__ void k_call_init(TrackState *st, int nkicks, double q_macro, int sort_interval,
-                            long long kick0) {
+                            long long kick0, double nbg) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
+        st->nbg = nbg;
         st->k_in_call = -1;
         st->nkicks_call = nkicks;
         st->q_macro = q_macro;
@@ -295,8 +302,9 @@ __global__ void k_call_init(TrackState *st, int nkicks, double q_macro, int sort
 }
 
 cudaError_t launch_call_init(TrackState *st, int nkicks, double q_macro, int sort_interval,
-                             long long kick0, cudaStream_t s) {
-    BT_LAUNCH(K_BOX, s, k_call_init<<<1, 32, 0, s>>>(st, nkicks, q_macro, sort_interval, kick0));
+                             long long kick0, cudaStream_t s, double betagamma) {
+    BT_LAUNCH(K_BOX, s, k_call_init<<<1, 32, 0, s>>>(st, nkicks, q_macro, sort_interval, kick0,
+                                                      -betagamma));
     return cudaGetLastError();
 }
 
@@ -538,8 +546,8 @@ __global__ void __launch_bounds__(TPB, 3) k_particles(PartArgs a) {
     const int nn = a.nn;
     // u = (X - lo)/h as one FMA per dimension: X * (1/h) - lo/h
     const double ih0 = a.box->inv_h[0], ih1 = a.box->inv_h[1], ih2 = a.box->inv_h[2];
-    const double o0 = -a.box->lo[0] * ih0, o1 = -a.box->lo[1] * ih1, o2 = -a.box->lo[2] * ih2;
-    const double tz = a.nbg * ih2;
+    const double o0 = a.box->off[0], o1 = a.box->off[1], o2 = a.box->off[2];
+    const double tz = a.box->tz;
     const double lo0 = a.box->lo[0], lo1 = a.box->lo[1], lo2 = a.box->lo[2];
     int e0 = 0, e1 = 0, e2 = 0;
     if constexpr (GATHER) {
@@ -553,125 +561,133 @@ __global__ void __launch_bounds__(TPB, 3) k_particles(PartArgs a) {
     bool bad = false, outside = false;
     const int64_t base = (int64_t)blockIdx.x * CHUNK;
     if (DEP) __syncthreads();
-#pragma unroll 1
-    for (int it = 0; it < PPT; ++it) {
-        const int slot = it * TPB + threadIdx.x;
-        const int64_t p = base + slot;
-        if (DEP) scell[slot] = -1;
-        if (p >= a.n) continue;
-        double x = a.x[p], y = a.y[p], t = a.t[p];
-        if constexpr (GATHER) {
-            double px = a.px[p], py = a.py[p], pt = a.pt[p];
-            int c0, c1, c2;
-            unsigned long long G0, G1, G2;
-            bool out0 = false;
-            const double u0 = a.exact_u ? (x - lo0) * ih0 : fma(x, ih0, o0);
-            const double u1 = a.exact_u ? (y - lo1) * ih1 : fma(y, ih1, o1);
-            const double u2 = a.exact_u ? (__dmul_rn(a.nbg, t) - lo2) * ih2 : fma(t, tz, o2);
-            long long comp[3];
-            const long long sy = 4LL * nn, sz = 4LL * nn * nn;  // in int64 units (4 per node)
-            if constexpr (SH == 2) {
-                tsc_node(u0, nn, c0, G0, out0);
-                tsc_node(u1, nn, c1, G1, out0);
-                tsc_node(u2, nn, c2, G2, out0);
-                outside |= out0;
-                Frac wx[3], wy[3], wz[3];
-                tsc_weights(G0, wx);
-                tsc_weights(G1, wy);
-                tsc_weights(G2, wz);
-                // separable: along x on the nine (y, z) lines, then y, then z
-                const long long *e = &a.ef[((long long)(c2 - 1) * nn + (c1 - 1)) * nn + (c0 - 1)].x;
-#pragma unroll
-                for (int cc = 0; cc < 3; ++cc) {
-                    long long gz = 0;
-#pragma unroll
-                    for (int dz = 0; dz < 3; ++dz) {
-                        long long gy = 0;
-#pragma unroll
-                        for (int dy = 0; dy < 3; ++dy) {
-                            const long long *q = e + cc + dz * sz + dy * sy;
-                            const long long gx = mulfrac52(q[0], wx[0]) + mulfrac52(q[4], wx[1]) +
-                                                 mulfrac52(q[8], wx[2]);
-                            gy += mulfrac52(gx, wy[dy]);
-                        }
-                        gz += mulfrac52(gy, wz[dz]);
-                    }
-                    comp[cc] = gz;
-                }
-            } else {
-                cell_frac(u0, nn, c0, G0, out0);
-                cell_frac(u1, nn, c1, G1, out0);
-                cell_frac(u2, nn, c2, G2, out0);
-                const Frac F0 = split26(G0), F1 = split26(G1), F2 = split26(G2);
-                outside |= out0;
-                // CIC interpolation in lerp form, one field component at a time (a
-                // small live register set): x on the four (y, z) edges, then y, z.
-                const long long *e = &a.ef[((long long)c2 * nn + c1) * nn + c0].x;
-#pragma unroll
-                for (int cc = 0; cc < 3; ++cc) {
-                    const long long *q = e + cc;
-                    const long long g00 = lerp52(q[0], q[4], F0), g01 = lerp52(q[sy], q[sy + 4], F0);
-                    const long long g10 = lerp52(q[sz], q[sz + 4], F0),
-                                    g11 = lerp52(q[sz + sy], q[sz + sy + 4], F0);
-                    comp[cc] = lerp52(lerp52(g00, g01, F1), lerp52(g10, g11, F1), F2);
-                }
-            }
-            const long long ex = comp[0], ey = comp[1], ez = comp[2];
-            px += i64_scaled_to_double(ex, e0);
-            py += i64_scaled_to_double(ey, e1);
-            pt += i64_scaled_to_double(ez, e2);
-            if constexpr (MK == MAP_TABLE) apply_map_table(a.map, x, px, y, py, t, pt);
-            else apply_map_k<MK>(a.map, x, px, y, py, t, pt);
-            bad |= !finite6(x, px, y, py, t, pt);
-            a.ox[p] = x;
-            a.opx[p] = px;
-            a.oy[p] = y;
-            a.opy[p] = py;
-            a.ot[p] = t;
-            a.opt[p] = pt;
-        }
-        if constexpr (DEP || MM) {
-            if constexpr (MM) {
-                const long long k0 = dkey(x), k1 = dkey(y), k2 = dkey(__dmul_rn(a.nbg, t));
-                klo[0] = min(klo[0], k0);
-                khi[0] = max(khi[0], k0);
-                klo[1] = min(klo[1], k1);
-                khi[1] = max(khi[1], k1);
-                klo[2] = min(klo[2], k2);
-                khi[2] = max(khi[2], k2);
-            }
-            if constexpr (DEP) {
+    // u = (X - lo)/h: one FMA with the box's constants, or (far-offset box)
+    // the subtraction first; a uniform branch selects one of two compiled
+    // copies of the particle loop, so each copy does only its own arithmetic
+    auto particle_loop = [&](auto exact_tag) {
+        constexpr bool EX = decltype(exact_tag)::value;
+    #pragma unroll 1
+        for (int it = 0; it < PPT; ++it) {
+            const int slot = it * TPB + threadIdx.x;
+            const int64_t p = base + slot;
+            if (DEP) scell[slot] = -1;
+            if (p >= a.n) continue;
+            double x = a.x[p], y = a.y[p], t = a.t[p];
+            if constexpr (GATHER) {
+                double px = a.px[p], py = a.py[p], pt = a.pt[p];
                 int c0, c1, c2;
-                unsigned long long F0, F1, F2;
-                bool out1 = false;
-                const double u0 = a.exact_u ? (x - lo0) * ih0 : fma(x, ih0, o0);
-                const double u1 = a.exact_u ? (y - lo1) * ih1 : fma(y, ih1, o1);
-                const double u2 = a.exact_u ? (__dmul_rn(a.nbg, t) - lo2) * ih2 : fma(t, tz, o2);
-                if constexpr (SH == 2) {  // nearest node and offset
-                    tsc_node(u0, nn, c0, F0, out1);
-                    tsc_node(u1, nn, c1, F1, out1);
-                    tsc_node(u2, nn, c2, F2, out1);
+                unsigned long long G0, G1, G2;
+                bool out0 = false;
+                const double u0 = EX ? (x - lo0) * ih0 : fma(x, ih0, o0);
+                const double u1 = EX ? (y - lo1) * ih1 : fma(y, ih1, o1);
+                const double u2 = EX ? (__dmul_rn(a.nbg, t) - lo2) * ih2 : fma(t, tz, o2);
+                long long comp[3];
+                const long long sy = 4LL * nn, sz = 4LL * nn * nn;  // in int64 units (4 per node)
+                if constexpr (SH == 2) {
+                    tsc_node(u0, nn, c0, G0, out0);
+                    tsc_node(u1, nn, c1, G1, out0);
+                    tsc_node(u2, nn, c2, G2, out0);
+                    outside |= out0;
+                    Frac wx[3], wy[3], wz[3];
+                    tsc_weights(G0, wx);
+                    tsc_weights(G1, wy);
+                    tsc_weights(G2, wz);
+                    // separable: along x on the nine (y, z) lines, then y, then z
+                    const long long *e = &a.ef[((long long)(c2 - 1) * nn + (c1 - 1)) * nn + (c0 - 1)].x;
+    #pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) {
+                        long long gz = 0;
+    #pragma unroll
+                        for (int dz = 0; dz < 3; ++dz) {
+                            long long gy = 0;
+    #pragma unroll
+                            for (int dy = 0; dy < 3; ++dy) {
+                                const long long *q = e + cc + dz * sz + dy * sy;
+                                const long long gx = mulfrac52(q[0], wx[0]) + mulfrac52(q[4], wx[1]) +
+                                                     mulfrac52(q[8], wx[2]);
+                                gy += mulfrac52(gx, wy[dy]);
+                            }
+                            gz += mulfrac52(gy, wz[dz]);
+                        }
+                        comp[cc] = gz;
+                    }
                 } else {
-                    cell_frac(u0, nn, c0, F0, out1);
-                    cell_frac(u1, nn, c1, F1, out1);
-                    cell_frac(u2, nn, c2, F2, out1);
+                    cell_frac(u0, nn, c0, G0, out0);
+                    cell_frac(u1, nn, c1, G1, out0);
+                    cell_frac(u2, nn, c2, G2, out0);
+                    const Frac F0 = split26(G0), F1 = split26(G1), F2 = split26(G2);
+                    outside |= out0;
+                    // CIC interpolation in lerp form, one field component at a time (a
+                    // small live register set): x on the four (y, z) edges, then y, z.
+                    const long long *e = &a.ef[((long long)c2 * nn + c1) * nn + c0].x;
+    #pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) {
+                        const long long *q = e + cc;
+                        const long long g00 = lerp52(q[0], q[4], F0), g01 = lerp52(q[sy], q[sy + 4], F0);
+                        const long long g10 = lerp52(q[sz], q[sz + 4], F0),
+                                        g11 = lerp52(q[sz + sy], q[sz + sy + 4], F0);
+                        comp[cc] = lerp52(lerp52(g00, g01, F1), lerp52(g10, g11, F1), F2);
+                    }
                 }
-                if (out1 && a.flag_outside) outside = true;  // box not containing the bunch
-                if (!out1) {  // particles outside are left out: the box rule then regrids
-                    sF[slot] = F0;
-                    sF[CHUNK + slot] = F1;
-                    sF[2 * CHUNK + slot] = F2;
-                    scell[slot] = (c2 * nn + c1) * nn + c0;
-                    blo[0] = min(blo[0], c0);
-                    bhi[0] = max(bhi[0], c0);
-                    blo[1] = min(blo[1], c1);
-                    bhi[1] = max(bhi[1], c1);
-                    blo[2] = min(blo[2], c2);
-                    bhi[2] = max(bhi[2], c2);
+                const long long ex = comp[0], ey = comp[1], ez = comp[2];
+                px += i64_scaled_to_double(ex, e0);
+                py += i64_scaled_to_double(ey, e1);
+                pt += i64_scaled_to_double(ez, e2);
+                if constexpr (MK == MAP_TABLE) apply_map_table(a.map, x, px, y, py, t, pt);
+                else apply_map_k<MK>(a.map, x, px, y, py, t, pt);
+                bad |= !finite6(x, px, y, py, t, pt);
+                a.ox[p] = x;
+                a.opx[p] = px;
+                a.oy[p] = y;
+                a.opy[p] = py;
+                a.ot[p] = t;
+                a.opt[p] = pt;
+            }
+            if constexpr (DEP || MM) {
+                if constexpr (MM) {
+                    const long long k0 = dkey(x), k1 = dkey(y), k2 = dkey(__dmul_rn(a.nbg, t));
+                    klo[0] = min(klo[0], k0);
+                    khi[0] = max(khi[0], k0);
+                    klo[1] = min(klo[1], k1);
+                    khi[1] = max(khi[1], k1);
+                    klo[2] = min(klo[2], k2);
+                    khi[2] = max(khi[2], k2);
+                }
+                if constexpr (DEP) {
+                    int c0, c1, c2;
+                    unsigned long long F0, F1, F2;
+                    bool out1 = false;
+                    const double u0 = EX ? (x - lo0) * ih0 : fma(x, ih0, o0);
+                    const double u1 = EX ? (y - lo1) * ih1 : fma(y, ih1, o1);
+                    const double u2 = EX ? (__dmul_rn(a.nbg, t) - lo2) * ih2 : fma(t, tz, o2);
+                    if constexpr (SH == 2) {  // nearest node and offset
+                        tsc_node(u0, nn, c0, F0, out1);
+                        tsc_node(u1, nn, c1, F1, out1);
+                        tsc_node(u2, nn, c2, F2, out1);
+                    } else {
+                        cell_frac(u0, nn, c0, F0, out1);
+                        cell_frac(u1, nn, c1, F1, out1);
+                        cell_frac(u2, nn, c2, F2, out1);
+                    }
+                    if (out1 && a.flag_outside) outside = true;  // box not containing the bunch
+                    if (!out1) {  // particles outside are left out: the box rule then regrids
+                        sF[slot] = F0;
+                        sF[CHUNK + slot] = F1;
+                        sF[2 * CHUNK + slot] = F2;
+                        scell[slot] = (c2 * nn + c1) * nn + c0;
+                        blo[0] = min(blo[0], c0);
+                        bhi[0] = max(bhi[0], c0);
+                        blo[1] = min(blo[1], c1);
+                        bhi[1] = max(bhi[1], c1);
+                        blo[2] = min(blo[2], c2);
+                        bhi[2] = max(bhi[2], c2);
+                    }
                 }
             }
         }
-    }
+    };
+    if (a.exact_u) particle_loop(std::true_type{});
+    else particle_loop(std::false_type{});
     if (bad) atomicOr(a.status, ST_NONFINITE);
     if (outside) atomicOr(a.status, ST_OUTSIDE);
     if constexpr (MM) block_keys_commit(klo, khi, a.st);
