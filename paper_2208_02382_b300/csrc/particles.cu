@@ -533,8 +533,10 @@ bool box_needs_exact_u(const Box &b) { return box_far_offset(b); }
 //         accumulators, through a shared-memory tile covering the block's
 //         nodes when they fit.
 // MM:     min/max keys of the new rest-frame positions.
+// Gather-only CIC instances (the bulk of tracking) fit 64 registers and run 4
+// blocks per SM; the others keep 3 (TSC's 27-node gather would spill).
 template <int MK, bool GATHER, bool DEP, bool MM, int SH>
-__global__ void __launch_bounds__(TPB, 3) k_particles(PartArgs a) {
+__global__ void __launch_bounds__(TPB, (GATHER && !DEP && SH == 1) ? 4 : 3) k_particles(PartArgs a) {
     if (a.gate && *a.gate == 0) return;
     if (a.dst) a.exact_u = a.dst->exact_u;
     if constexpr (MK == MAP_TABLE) a.map = a.maps[1 + a.dst->k_in_call];
@@ -713,8 +715,14 @@ __global__ void __launch_bounds__(TPB, 3) k_particles(PartArgs a) {
                   tz = s_bb[5] - s_bb[2] + SPAN;
         const bool use_tile = (long long)tx * ty * tz <= TILE_CAP;
         const unsigned long long one = 1ull << 52;
+        // the tile as two 32-bit words per node (low word, high word): native
+        // 32-bit shared atomics, where a 64-bit add would be a compare-and-swap
+        // loop that retries on every collision of sorted neighbours; a carry
+        // out of the low word goes into the high word.  A block adds at most
+        // CHUNK weights below 2^51 to a node, so the high word stays below 2^30.
+        unsigned *tlo = (unsigned *)tile, *thi = tlo + TILE_CAP;
         if (use_tile) {
-            for (int i = threadIdx.x; i < tx * ty * tz; i += TPB) tile[i] = 0ull;
+            for (int i = threadIdx.x; i < tx * ty * tz; i += TPB) tlo[i] = thi[i] = 0u;
             __syncthreads();
         }
         const int nn2 = nn * nn;
@@ -749,7 +757,9 @@ __global__ void __launch_bounds__(TPB, 3) k_particles(PartArgs a) {
                         const int ni = c0 + dx - LOW, nj = c1 + dy - LOW, nl = c2 + dz - LOW;
                         if (use_tile) {
                             const int li = ((nl - l0) * ty + (nj - j0)) * tx + (ni - i0);
-                            atomicAdd(&tile[li], v);
+                            const unsigned lo = (unsigned)v;
+                            const unsigned old = atomicAdd(&tlo[li], lo);
+                            atomicAdd(&thi[li], (unsigned)(v >> 32) + (old + lo < old ? 1u : 0u));
                         } else {
                             const long long node = ((long long)nl * nn + nj) * nn + ni;
                             atomicAdd(&a.acc_hi[node], v >> DEP_SPLIT);
@@ -761,7 +771,7 @@ __global__ void __launch_bounds__(TPB, 3) k_particles(PartArgs a) {
         if (use_tile) {
             __syncthreads();
             for (int i = threadIdx.x; i < tx * ty * tz; i += TPB) {
-                const unsigned long long v = tile[i];
+                const unsigned long long v = ((unsigned long long)thi[i] << 32) + tlo[i];
                 if (v == 0ull) continue;
                 const int ii = i % tx, jj = (i / tx) % ty, ll = i / (tx * ty);
                 const long long node = ((long long)(l0 + ll) * nn + (j0 + jj)) * nn + (i0 + ii);
