@@ -456,7 +456,7 @@ cudaError_t launch_field(const double *phi, int nn, const Box *box, double kx, d
 
 constexpr int PPT = 4;                 // particles per thread
 constexpr int CHUNK = TPB * PPT;       // particles per block
-constexpr int TILE_CAP = 4096;         // nodes of the shared-memory deposit tile
+constexpr int TILE_CAP = 3072;         // nodes of the shared-memory deposit tile
 
 struct PartArgs {
     double *x, *px, *y, *py, *t, *pt;
@@ -533,16 +533,16 @@ bool box_needs_exact_u(const Box &b) { return box_far_offset(b); }
 //         accumulators, through a shared-memory tile covering the block's
 //         nodes when they fit.
 // MM:     min/max keys of the new rest-frame positions.
-// Gather-only CIC instances (the bulk of tracking) fit 64 registers and run 4
-// blocks per SM; the others keep 3 (TSC's 27-node gather would spill).
+// CIC instances fit 64 registers and (with 52 KB of shared memory for DEP) run 4 blocks
+// per SM; TSC instances keep 3 (its 27-node gather would spill at 64).
 template <int MK, bool GATHER, bool DEP, bool MM, int SH>
-__global__ void __launch_bounds__(TPB, (GATHER && !DEP && SH == 1) ? 4 : 3) k_particles(PartArgs a) {
+__global__ void __launch_bounds__(TPB, SH == 1 ? 4 : 3) k_particles(PartArgs a) {
     if (a.gate && *a.gate == 0) return;
     if (a.dst) a.exact_u = a.dst->exact_u;
     if constexpr (MK == MAP_TABLE) a.map = a.maps[1 + a.dst->k_in_call];
     extern __shared__ unsigned long long dsm[];
     unsigned long long *sF = dsm;                                // [3][CHUNK] fractions
-    int *scell = (int *)(dsm + 3 * CHUNK);                       // [CHUNK] linear cell or -1
+    int *scell = (int *)(dsm + 3 * CHUNK);                       // [CHUNK] packed cell or -1
     unsigned long long *tile = dsm + 3 * CHUNK + CHUNK / 2;      // [TILE_CAP]
     __shared__ int s_bb[6];
     const int nn = a.nn;
@@ -584,8 +584,8 @@ __global__ void __launch_bounds__(TPB, (GATHER && !DEP && SH == 1) ? 4 : 3) k_pa
                 const double u1 = EX ? (y - lo1) * ih1 : fma(y, ih1, o1);
                 const double u2 = EX ? (__dmul_rn(a.nbg, t) - lo2) * ih2 : fma(t, tz, o2);
                 long long comp[3];
-                const long long sy = 4LL * nn, sz = 4LL * nn * nn;  // in int64 units (4 per node)
                 if constexpr (SH == 2) {
+                    const long long sy = 4LL * nn, sz = 4LL * nn * nn;  // in int64 units (4 per node)
                     tsc_node(u0, nn, c0, G0, out0);
                     tsc_node(u1, nn, c1, G1, out0);
                     tsc_node(u2, nn, c2, G2, out0);
@@ -619,17 +619,23 @@ __global__ void __launch_bounds__(TPB, (GATHER && !DEP && SH == 1) ? 4 : 3) k_pa
                     cell_frac(u2, nn, c2, G2, out0);
                     const Frac F0 = split26(G0), F1 = split26(G1), F2 = split26(G2);
                     outside |= out0;
-                    // CIC interpolation in lerp form, one field component at a time (a
-                    // small live register set): x on the four (y, z) edges, then y, z.
-                    const long long *e = &a.ef[((long long)c2 * nn + c1) * nn + c0].x;
+                    // CIC interpolation in lerp form: along x on the four (y, z) edges
+                    // of the cell, then y, then z.
+                    const EFix *e = &a.ef[((long long)c2 * nn + c1) * nn + c0];
+                    const long long ny = nn, nz = (long long)nn * nn;
+                    // x and y components of a node in one 16-byte load, z in one 8-byte load
+                    long long gxy[2][4], gz[4];
     #pragma unroll
-                    for (int cc = 0; cc < 3; ++cc) {
-                        const long long *q = e + cc;
-                        const long long g00 = lerp52(q[0], q[4], F0), g01 = lerp52(q[sy], q[sy + 4], F0);
-                        const long long g10 = lerp52(q[sz], q[sz + 4], F0),
-                                        g11 = lerp52(q[sz + sy], q[sz + sy + 4], F0);
-                        comp[cc] = lerp52(lerp52(g00, g01, F1), lerp52(g10, g11, F1), F2);
+                    for (int k = 0; k < 4; ++k) {
+                        const EFix *q = e + (k & 1) * ny + (k >> 1) * nz;
+                        const longlong2 p0 = __ldg((const longlong2 *)q), p1 = __ldg((const longlong2 *)(q + 1));
+                        gxy[0][k] = lerp52(p0.x, p1.x, F0);
+                        gxy[1][k] = lerp52(p0.y, p1.y, F0);
+                        gz[k] = lerp52(__ldg(&q->z), __ldg(&q[1].z), F0);
                     }
+                    comp[0] = lerp52(lerp52(gxy[0][0], gxy[0][1], F1), lerp52(gxy[0][2], gxy[0][3], F1), F2);
+                    comp[1] = lerp52(lerp52(gxy[1][0], gxy[1][1], F1), lerp52(gxy[1][2], gxy[1][3], F1), F2);
+                    comp[2] = lerp52(lerp52(gz[0], gz[1], F1), lerp52(gz[2], gz[3], F1), F2);
                 }
                 const long long ex = comp[0], ey = comp[1], ez = comp[2];
                 px += i64_scaled_to_double(ex, e0);
@@ -676,7 +682,7 @@ __global__ void __launch_bounds__(TPB, (GATHER && !DEP && SH == 1) ? 4 : 3) k_pa
                         sF[slot] = F0;
                         sF[CHUNK + slot] = F1;
                         sF[2 * CHUNK + slot] = F2;
-                        scell[slot] = (c2 * nn + c1) * nn + c0;
+                        scell[slot] = c0 | (c1 << 10) | (c2 << 20);  // n <= 256
                         blo[0] = min(blo[0], c0);
                         bhi[0] = max(bhi[0], c0);
                         blo[1] = min(blo[1], c1);
@@ -725,14 +731,15 @@ __global__ void __launch_bounds__(TPB, (GATHER && !DEP && SH == 1) ? 4 : 3) k_pa
             for (int i = threadIdx.x; i < tx * ty * tz; i += TPB) tlo[i] = thi[i] = 0u;
             __syncthreads();
         }
-        const int nn2 = nn * nn;
 #pragma unroll 1
         for (int it = 0; it < PPT; ++it) {
             const int slot = it * TPB + threadIdx.x;
             const int cell = scell[slot];
             if (cell < 0) continue;
             const unsigned long long F0 = sF[slot], F1 = sF[CHUNK + slot], F2 = sF[2 * CHUNK + slot];
-            const int c2 = cell / nn2, c1 = (cell / nn) % nn, c0 = cell % nn;
+            const int c0 = cell & 1023, c1 = (cell >> 10) & 1023, c2 = cell >> 20;
+            // tile index of the particle's first node; the others are fixed offsets
+            const int lb = ((c2 - LOW - l0) * ty + (c1 - LOW - j0)) * tx + (c0 - LOW - i0);
             Frac wx[SPAN], wy[SPAN], wz[SPAN];
             if constexpr (SH == 2) {
                 tsc_weights(F0, wx);
@@ -756,7 +763,7 @@ __global__ void __launch_bounds__(TPB, (GATHER && !DEP && SH == 1) ? 4 : 3) k_pa
                         const unsigned long long v = mulshr52(wx[dx], wyz) >> 1;  // 51-bit
                         const int ni = c0 + dx - LOW, nj = c1 + dy - LOW, nl = c2 + dz - LOW;
                         if (use_tile) {
-                            const int li = ((nl - l0) * ty + (nj - j0)) * tx + (ni - i0);
+                            const int li = lb + (dz * ty + dy) * tx + dx;
                             const unsigned lo = (unsigned)v;
                             const unsigned old = atomicAdd(&tlo[li], lo);
                             atomicAdd(&thi[li], (unsigned)(v >> 32) + (old + lo < old ? 1u : 0u));
