@@ -42,50 +42,80 @@ __device__ __forceinline__ double2 rot90(double2 a) {
 
 constexpr double RS2 = 0.70710678118654752440;   // sqrt(2)/2
 constexpr double C16 = 0.92387953251128675613;   // cos(pi/8)
-constexpr double S16 = 0.38268343236508977173;   // sin(pi/8)
-
-// multiply by exp(-+ 2 pi i q/8) for q = 1, 3 (q = 2 is rot90)
-template <bool INV>
-__device__ __forceinline__ double2 w8_1(double2 a) {  // (1 -+ i)/sqrt2
-    return INV ? make_double2((a.x - a.y) * RS2, (a.x + a.y) * RS2)
-               : make_double2((a.x + a.y) * RS2, (a.y - a.x) * RS2);
-}
-template <bool INV>
-__device__ __forceinline__ double2 w8_3(double2 a) {  // (-1 -+ i)/sqrt2
-    return INV ? make_double2(-(a.x + a.y) * RS2, (a.x - a.y) * RS2)
-               : make_double2((a.y - a.x) * RS2, -(a.x + a.y) * RS2);
-}
+constexpr double T16 = 0.41421356237309504880;   // tan(pi/8) = sqrt(2) - 1
 
 // ---------------------------------------------------------------- codelets
 // In-place DFT of R values in registers, natural order in and out:
 // y_q = sum_m x_m exp(-+ 2 pi i m q / R)  (radix-2 decimation in time).
+// The last butterfly layer takes each twiddle w = f (a + i b) with one real
+// factor f pulled out, so the twiddle and the butterfly e +- w o cost six
+// FP64 instructions (two for the rotation, four FMAs) instead of eight.
 
-template <bool INV>
-__device__ __forceinline__ void dft4(double2 *v) {
-    double2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-    double2 t2 = cadd(v[1], v[3]), t3 = rot90<INV>(csub(v[1], v[3]));
-    v[0] = cadd(t0, t2);
-    v[2] = csub(t0, t2);
-    v[1] = cadd(t1, t3);
-    v[3] = csub(t1, t3);
+// lo, hi = e +- f r
+__device__ __forceinline__ void bfly_f(double2 e, double2 r, double f, double2 &lo, double2 &hi) {
+    lo = make_double2(fma(r.x, f, e.x), fma(r.y, f, e.y));
+    hi = make_double2(fma(-r.x, f, e.x), fma(-r.y, f, e.y));
 }
 
+// w = exp(-+ i pi/4) = (1 -+ i)/sqrt2: w o = RS2 (o.x +- o.y, o.y -+ o.x)
 template <bool INV>
-__device__ __forceinline__ void dft8(double2 *v) {
-    double2 e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
-    dft4<INV>(e);
-    dft4<INV>(o);
-    o[1] = w8_1<INV>(o[1]);
-    o[2] = rot90<INV>(o[2]);
-    o[3] = w8_3<INV>(o[3]);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        v[q] = cadd(e[q], o[q]);
-        v[q + 4] = csub(e[q], o[q]);
+__device__ __forceinline__ void bfly_w8_1(double2 e, double2 o, double2 &lo, double2 &hi) {
+    const double2 r = INV ? make_double2(o.x - o.y, o.x + o.y) : make_double2(o.x + o.y, o.y - o.x);
+    bfly_f(e, r, RS2, lo, hi);
+}
+// w = exp(-+ 3 i pi/4) = (-1 -+ i)/sqrt2
+template <bool INV>
+__device__ __forceinline__ void bfly_w8_3(double2 e, double2 o, double2 &lo, double2 &hi) {
+    const double2 r = INV ? make_double2(-(o.x + o.y), o.x - o.y) : make_double2(o.y - o.x, -(o.x + o.y));
+    bfly_f(e, r, RS2, lo, hi);
+}
+// w = c (1 + i t): w o = c (o.x - t o.y, o.y + t o.x)
+__device__ __forceinline__ void bfly_ct(double2 e, double2 o, double c, double t, double2 &lo, double2 &hi) {
+    bfly_f(e, make_double2(fma(-o.y, t, o.x), fma(o.x, t, o.y)), c, lo, hi);
+}
+// w = s (t + i): w o = s (t o.x - o.y, o.x + t o.y)
+__device__ __forceinline__ void bfly_st(double2 e, double2 o, double s, double t, double2 &lo, double2 &hi) {
+    bfly_f(e, make_double2(fma(o.x, t, -o.y), fma(o.y, t, o.x)), s, lo, hi);
+}
+
+// DFT-4 of (v0, v1, v2, v3); HALF: v2 = v3 = 0 (not read).
+template <bool INV, bool HALF>
+__device__ __forceinline__ void dft4(double2 *v) {
+    if constexpr (HALF) {
+        const double2 a = v[0], b = v[1], rb = rot90<INV>(b);
+        v[0] = cadd(a, b);
+        v[1] = cadd(a, rb);
+        v[2] = csub(a, b);
+        v[3] = csub(a, rb);
+    } else {
+        double2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        double2 t2 = cadd(v[1], v[3]), t3 = rot90<INV>(csub(v[1], v[3]));
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
     }
 }
 
-template <bool INV>
+// DFT-8; HALF: v4..v7 = 0 (not read).
+template <bool INV, bool HALF>
+__device__ __forceinline__ void dft8(double2 *v) {
+    double2 e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    dft4<INV, HALF>(e);
+    dft4<INV, HALF>(o);
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    bfly_w8_1<INV>(e[1], o[1], v[1], v[5]);
+    const double2 r2 = rot90<INV>(o[2]);
+    v[2] = cadd(e[2], r2);
+    v[6] = csub(e[2], r2);
+    bfly_w8_3<INV>(e[3], o[3], v[3], v[7]);
+}
+
+// DFT-16; HALF: v8..v15 = 0 (not read).  The twiddles exp(-+ 2 pi i q/16)
+// (sg = -1 forward, +1 inverse; S16 = sin(pi/8) = C16 T16) are written as
+// C16 (1 + i t) or sg C16 (t + i) with t = +-T16, as RS2 (+-1 +- i), or +-i.
+template <bool INV, bool HALF>
 __device__ __forceinline__ void dft16(double2 *v) {
     double2 e[8], o[8];
 #pragma unroll
@@ -93,28 +123,27 @@ __device__ __forceinline__ void dft16(double2 *v) {
         e[m] = v[2 * m];
         o[m] = v[2 * m + 1];
     }
-    dft8<INV>(e);
-    dft8<INV>(o);
+    dft8<INV, HALF>(e);
+    dft8<INV, HALF>(o);
     const double sg = INV ? 1.0 : -1.0;
-    o[1] = cmul(o[1], make_double2(C16, sg * S16));
-    o[2] = w8_1<INV>(o[2]);
-    o[3] = cmul(o[3], make_double2(S16, sg * C16));
-    o[4] = rot90<INV>(o[4]);
-    o[5] = cmul(o[5], make_double2(-S16, sg * C16));
-    o[6] = w8_3<INV>(o[6]);
-    o[7] = cmul(o[7], make_double2(-C16, sg * S16));
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        v[q] = cadd(e[q], o[q]);
-        v[q + 8] = csub(e[q], o[q]);
-    }
+    v[0] = cadd(e[0], o[0]);
+    v[8] = csub(e[0], o[0]);
+    bfly_ct(e[1], o[1], C16, sg * T16, v[1], v[9]);            // (C16, sg S16)
+    bfly_w8_1<INV>(e[2], o[2], v[2], v[10]);
+    bfly_st(e[3], o[3], sg * C16, sg * T16, v[3], v[11]);      // (S16, sg C16)
+    const double2 r4 = rot90<INV>(o[4]);
+    v[4] = cadd(e[4], r4);
+    v[12] = csub(e[4], r4);
+    bfly_st(e[5], o[5], sg * C16, -sg * T16, v[5], v[13]);     // (-S16, sg C16)
+    bfly_w8_3<INV>(e[6], o[6], v[6], v[14]);
+    bfly_ct(e[7], o[7], -C16, -sg * T16, v[7], v[15]);         // (-C16, sg S16)
 }
 
-template <int R, bool INV>
+template <int R, bool INV, bool HALF = false>
 __device__ __forceinline__ void dft(double2 *v) {
-    if constexpr (R == 4) dft4<INV>(v);
-    else if constexpr (R == 8) dft8<INV>(v);
-    else dft16<INV>(v);
+    if constexpr (R == 4) dft4<INV, HALF>(v);
+    else if constexpr (R == 8) dft8<INV, HALF>(v);
+    else dft16<INV, HALF>(v);
 }
 
 // ------------------------------------------------------------- line shapes
@@ -135,7 +164,7 @@ constexpr int FFT_TPB = 256;
 // elements u + m*(M/R), in v[j*R + m].  Twiddles W_{L R}^{k m} (k = u mod L)
 // are applied before the radix-R DFT; output q of unit u belongs at line
 // position (u-k)*R + q*L + k.
-template <int M, int R, int L, bool INV>
+template <int M, int R, int L, bool INV, bool HALF = false>
 __device__ __forceinline__ void step_regs(double2 *v, int t, const double2 *__restrict__ tw) {
     constexpr int T = Shape<M>::T, U = (M / R) / T;
 #pragma unroll
@@ -150,7 +179,7 @@ __device__ __forceinline__ void step_regs(double2 *v, int t, const double2 *__re
                 x[m] = cmul(x[m], w);
             }
         }
-        dft<R, INV>(x);
+        dft<R, INV, HALF>(x);
     }
 }
 
@@ -183,12 +212,15 @@ __device__ __forceinline__ int first_index(int t, int j, int m) {
 
 // Full line transform: `v` holds the first step's inputs (first_index order);
 // the result (natural order) is left in the team's shared line `s`.  Every
-// thread of the block calls this (it synchronises the block).
-template <int M, bool INV>
+// thread of the block calls this (it synchronises the block).  HALF: the
+// line's upper half (elements M/2..M-1) is zero; these are exactly the inputs
+// m >= R0/2 of every first-step DFT (element u + m M/R0 with u < M/R0), which
+// the half codelets neither read nor add.
+template <int M, bool INV, bool HALF = false>
 __device__ __forceinline__ void line_fft(double2 *v, double2 *s, int t, const double2 *tw) {
     using SH = Shape<M>;
     constexpr int R0 = SH::R0, R1 = SH::R1, R2 = SH::R2;
-    step_regs<M, R0, 1, INV>(v, t, tw);
+    step_regs<M, R0, 1, INV, HALF>(v, t, tw);
     store_step<M, R0, 1>(v, s, t);
     __syncthreads();
     load_step<M, R1>(v, s, t);
@@ -281,7 +313,8 @@ __global__ void __launch_bounds__(FFT_TPB) k_fft_x_fwd(XIn in, int n, int ny, in
                                  : make_double2(0.0, 0.0);
         }
     double2 *s = sl + team * M;
-    line_fft<M, false>(v, s, t, stw);
+    if (SRC != SRC_GREEN && 2 * nin == M) line_fft<M, false, true>(v, s, t, stw);  // rows x < M/2
+    else line_fft<M, false>(v, s, t, stw);
     if (!live) return;
     const int P = n + 1;
     double2 *oa = out + ((long long)z * ny + y) * P, *ob = oa + P;
@@ -339,7 +372,8 @@ __global__ void __launch_bounds__(FFT_TPB) k_fft_lines(const double2 *__restrict
             v[j * R0 + m] = (live && e < ne_in) ? src[e * in_e] : make_double2(0.0, 0.0);
         }
     double2 *s = sl + team * M;
-    line_fft<M, INV1>(v, s, t, stw);
+    if ((MODE == MODE_FWD || MODE == MODE_ZSOLVE) && 2 * ne_in == M) line_fft<M, INV1, true>(v, s, t, stw);
+    else line_fft<M, INV1>(v, s, t, stw);
     if constexpr (MODE == MODE_ZSOLVE) {
         const int b = min(o, M - o);
         for (int e = t; e < M; e += T) {
