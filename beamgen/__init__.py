@@ -23,8 +23,8 @@ from typing import List, Sequence
 import numpy as np
 
 # element type codes (shared with the C-ABI header's BX_DRIFT / BX_QUAD / BX_SBEND /
-# BX_DIPEDGE / BX_CONSTF)
-DRIFT, QUAD, SBEND, DIPEDGE, CONSTF = 0, 1, 2, 3, 4
+# BX_DIPEDGE / BX_CONSTF / BX_MULTIPOLE)
+DRIFT, QUAD, SBEND, DIPEDGE, CONSTF, MULTIPOLE = 0, 1, 2, 3, 4, 5
 
 # rest energies, CODATA 2018 [MeV]
 MASS_PROTON_MEV = 938.27208816
@@ -42,6 +42,7 @@ class Element:
     angle: float = 0.0
     nslice: int = 1
     k2: float = 0.0
+    order: int = 0
 
 
 def drift(length, nslice=1):
@@ -64,6 +65,13 @@ def dipedge(psi, curvature):
 def constf(length, kx, ky, nslice=1):
     """Constant transverse focusing channel piece (k_x, k_y in 1/m^2)."""
     return Element(CONSTF, float(length), float(kx), 0.0, int(nslice), float(ky))
+
+
+def multipole(order, kn, ks=0.0):
+    """Thin multipole of order m (1 dipole, 2 quadrupole, 3 sextupole, ...):
+    integrated normal and skew strengths kn, ks [1/m^(m-1)] (k holds kn, k2
+    holds ks)."""
+    return Element(MULTIPOLE, 0.0, float(kn), 0.0, 0, float(ks), int(order))
 
 
 def fodo_cell(nslice, kf=1.0, kd=-1.0):
@@ -123,6 +131,24 @@ def chicane_rect_lattice(nslice=50):
             out += [dipedge(0.5 * e.angle, h), e, dipedge(0.5 * e.angle, h)]
         else:
             out.append(e)
+    return out
+
+
+def fodo_multipole_lattice(nslice=2, periods=1):
+    """FODO cells of Listing 1 with thin nonlinear multipoles between the
+    elements (the paper lists a chain of thin multipoles among its examples;
+    orders and strengths here are a reading, sized so that each kicks a 1 mm
+    particle by ~1e-5): a skew quadrupole at the start, normal sextupoles at
+    both faces of QF, an octupole and a decapole together at the cell centre,
+    a skew-normal sextupole after QD and a skew dodecapole at the end."""
+    out = []
+    for _ in range(int(periods)):
+        out += [multipole(2, 0.0, 0.01),
+                drift(0.25, nslice), multipole(3, 20.0), quad(1.0, 1.0, nslice),
+                multipole(3, 20.0), drift(0.5, nslice),
+                multipole(4, -6e4, 1e4), multipole(5, 2.4e8),
+                quad(1.0, -1.0, nslice), multipole(3, -15.0, 8.0),
+                drift(0.25, nslice), multipole(6, 0.0, 1.2e12)]
     return out
 
 

@@ -167,6 +167,9 @@ def forward(z0: np.ndarray, lattice, ref: ph.RefPart, bunch_charge_C: float, n_g
     same calls, keeping a Record per kick.  With `boxes` (one sc.Box per kick)
     the box of each kick is taken from the list instead of the box rule
     (replay).  Returns (final coordinates, records, boxes used)."""
+    if any(ph.is_thin(e) and not ph.is_linear_thin(e) for e in lattice):
+        raise ValueError("reverse mode: thin multipoles are not supported (linear thin "
+                         "elements only)")
     sched = ph.slice_schedule(lattice)
     before, after = ph.thin_schedule(lattice)
     c = np.array(z0, dtype=np.float64, copy=True)

@@ -24,7 +24,7 @@ C_LIGHT = 299792458.0                # m/s
 Q_E = 1.602176634e-19                # C
 EPS0 = 8.8541878128e-12              # F/m
 
-DRIFT, QUAD, SBEND, DIPEDGE, CONSTF = 0, 1, 2, 3, 4
+DRIFT, QUAD, SBEND, DIPEDGE, CONSTF, MULTIPOLE = 0, 1, 2, 3, 4, 5
 X, PX, Y, PY, T, PT = range(6)
 
 
@@ -142,9 +142,48 @@ def constf_matrix(ds: float, kx: float, ky: float, ref: RefPart) -> np.ndarray:
     return m
 
 
+def multipole_kick(coords: np.ndarray, order: int, kn: float, ks: float) -> np.ndarray:
+    """Thin multipole of order m (1 dipole, 2 quadrupole, 3 sextupole, ...) with
+    integrated normal and skew strengths kn, ks [1/m^(m-1)] (paper §Numerical
+    Experiments: a chain of thin multipoles; the paper prints no formula).
+
+    Reading: the field of a straight 2D multipole magnet of length L is
+    B_y + i B_x = (B rho / L) (kn + i ks) (x + i y)^(m-1) / (m-1)!, and the
+    Lorentz force on a reference-rigidity particle over L changes the scaled
+    momenta by dpx = -L B_y / (B rho), dpy = +L B_x / (B rho), so that
+        dpx - i dpy = -(kn + i ks) (x + i y)^(m-1) / (m-1)!
+    (m = 2, kn > 0: px -= kn x, py += kn y, focusing in x like a quadrupole
+    with k > 0; m = 3: px -= kn (x^2 - y^2)/2, py += kn x y).  x, y, t and pt
+    are unchanged (a thin kick)."""
+    if order < 1:
+        raise ValueError("multipole order must be >= 1")
+    out = np.array(coords, dtype=np.float64, copy=True)
+    z = out[X] + 1j * out[Y]
+    zp = np.ones_like(z)
+    for _ in range(order - 1):     # z^(m-1) by repeated multiplication
+        zp = zp * z
+    w = (kn + 1j * ks) * zp / math.factorial(order - 1)
+    out[PX] = out[PX] - w.real
+    out[PY] = out[PY] + w.imag
+    return out
+
+
 def is_thin(e) -> bool:
-    """Thin elements (dipole edges) act between slices and take no kick."""
+    """Thin elements (dipole edges, multipoles) act between slices and take
+    no kick."""
+    return e.kind in (DIPEDGE, MULTIPOLE)
+
+
+def is_linear_thin(e) -> bool:
     return e.kind == DIPEDGE
+
+
+def thin_apply(coords: np.ndarray, lattice, ie: int, ref: "RefPart") -> np.ndarray:
+    """Apply the thin element `ie` to (6, n) coordinates."""
+    e = lattice[ie]
+    if e.kind == MULTIPOLE:
+        return multipole_kick(coords, int(e.order), e.k, getattr(e, "k2", 0.0))
+    return push(coords, thin_matrix(lattice, [ie], ref))
 
 
 def element_matrix(kind: int, length: float, k: float, angle: float, ds: float,
@@ -203,10 +242,12 @@ def thin_schedule(lattice) -> tuple:
 
 
 def thin_matrix(lattice, indices, ref: RefPart) -> np.ndarray:
-    """Product of the thin elements `indices` in beamline order."""
+    """Product of the (linear) thin elements `indices` in beamline order."""
     m = np.eye(6)
     for ie in indices:
         e = lattice[ie]
+        if not is_linear_thin(e):
+            raise ValueError("thin_matrix: element %d is not linear" % ie)
         m = element_matrix(e.kind, e.length, e.k, e.angle, 0.0, ref, getattr(e, "k2", 0.0)) @ m
     return m
 

@@ -76,7 +76,7 @@ class Tracker:
         for j in range(first_kick, stop):
             ie, ds = sched[j]
             for it in before[j]:
-                c = ph.push(c, ph.thin_matrix(lattice, [it], self.ref))
+                c = ph.thin_apply(c, lattice, it, self.ref)
             e = lattice[ie]
             half = ph.element_matrix(e.kind, e.length, e.k, e.angle, 0.5 * ds, self.ref,
                                      getattr(e, "k2", 0.0))
@@ -89,7 +89,7 @@ class Tracker:
                 diagnostics.append(moments_vector(c))
         if stop == len(sched) and stop > first_kick:
             for it in after:
-                c = ph.push(c, ph.thin_matrix(lattice, [it], self.ref))
+                c = ph.thin_apply(c, lattice, it, self.ref)
         return c
 
 
