@@ -137,18 +137,20 @@ def chicane_rect_lattice(nslice=50):
 def fodo_multipole_lattice(nslice=2, periods=1):
     """FODO cells of Listing 1 with thin nonlinear multipoles between the
     elements (the paper lists a chain of thin multipoles among its examples;
-    orders and strengths here are a reading, sized so that each kicks a 1 mm
-    particle by ~1e-5): a skew quadrupole at the start, normal sextupoles at
-    both faces of QF, an octupole and a decapole together at the cell centre,
-    a skew-normal sextupole after QD and a skew dodecapole at the end."""
+    orders and strengths here are a reading, sized so that no multipole kicks
+    a particle at 2 cm by more than ~1e-3, which keeps a bunch of 1 mm rms
+    bounded over many cells):
+    a skew quadrupole at the start, normal sextupoles at both faces of QF, an
+    octupole and a decapole together at the cell centre, a skew-normal
+    sextupole after QD and a skew dodecapole at the end."""
     out = []
     for _ in range(int(periods)):
         out += [multipole(2, 0.0, 0.01),
-                drift(0.25, nslice), multipole(3, 20.0), quad(1.0, 1.0, nslice),
-                multipole(3, 20.0), drift(0.5, nslice),
-                multipole(4, -6e4, 1e4), multipole(5, 2.4e8),
-                quad(1.0, -1.0, nslice), multipole(3, -15.0, 8.0),
-                drift(0.25, nslice), multipole(6, 0.0, 1.2e12)]
+                drift(0.25, nslice), multipole(3, 2.0), quad(1.0, 1.0, nslice),
+                multipole(3, 2.0), drift(0.5, nslice),
+                multipole(4, -600.0, 100.0), multipole(5, 1e5),
+                quad(1.0, -1.0, nslice), multipole(3, -1.5, 0.8),
+                drift(0.25, nslice), multipole(6, 0.0, 2e7)]
     return out
 
 

@@ -56,6 +56,8 @@ extern "C" {
 #define BX_SBEND 2
 #define BX_DIPEDGE 3 /* thin: nslice = 0, angle = edge angle, k = curvature 1/rho */
 #define BX_CONSTF 4  /* constant focusing: k = k_x, k2 = k_y [1/m^2]            */
+#define BX_MULTIPOLE 5 /* thin: nslice = 0, order m, k = kn, k2 = ks [1/m^(m-1)] */
+#define BX_MULTIPOLE_MAX_ORDER 12
 
 typedef struct bx_ctx bx_ctx;
 typedef struct bx_batch bx_batch;
@@ -106,9 +108,14 @@ typedef struct {
  * tan(psi) x, py -= h tan(psi) y): nslice = 0, angle = edge angle psi, k =
  * curvature h = 1/rho of the bend it belongs to; it takes no kick and acts
  * between the slices around it (a rectangular bend of angle theta: edges of
- * theta/2 on both faces).  Thin elements ahead of slice j act in the call
- * that tracks slice j; those after the last slice act at the end of the
- * call that tracks it. */
+ * theta/2 on both faces).  Thin multipole (paper: a chain of thin multipoles;
+ * the kick is the reading dpx - i dpy = -(kn + i ks) (x + i y)^(m-1)/(m-1)!
+ * of a straight 2D multipole magnet, so m = 2 with kn > 0 focuses x like a
+ * quadrupole with k > 0): nslice = 0, order = m in 1..BX_MULTIPOLE_MAX_ORDER
+ * (1 dipole, 2 quadrupole, 3 sextupole, ...), k = kn, k2 = ks (integrated
+ * strengths); x, y, t, pt are unchanged.  Thin elements ahead of slice j act
+ * in the call that tracks slice j; those after the last slice act at the end
+ * of the call that tracks it.  order is ignored by the other element types. */
 typedef struct {
     int32_t type;
     int32_t nslice;
@@ -116,6 +123,8 @@ typedef struct {
     double k;
     double angle;
     double k2;
+    int32_t order;
+    int32_t reserved;
 } bx_element;
 
 /* A lattice in HOST memory.  space_charge: 0 = maps only

@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbeamtrack.so")
 
 BX_OK, BX_BAD_ARG, BX_NONFINITE, BX_OUT_OF_MEMORY, BX_DEVICE_TIMEOUT, BX_CUDA = range(6)
-BX_DRIFT, BX_QUAD, BX_SBEND, BX_DIPEDGE, BX_CONSTF = 0, 1, 2, 3, 4
+BX_DRIFT, BX_QUAD, BX_SBEND, BX_DIPEDGE, BX_CONSTF, BX_MULTIPOLE = 0, 1, 2, 3, 4, 5
+BX_MULTIPOLE_MAX_ORDER = 12
 
 
 class bx_options(ctypes.Structure):
@@ -26,7 +27,8 @@ class bx_beam(ctypes.Structure):
 
 class bx_element(ctypes.Structure):
     _fields_ = [("type", c_int32), ("nslice", c_int32), ("length", c_double),
-                ("k", c_double), ("angle", c_double), ("k2", c_double)]
+                ("k", c_double), ("angle", c_double), ("k2", c_double),
+                ("order", c_int32), ("reserved", c_int32)]
 
 
 class bx_lattice(ctypes.Structure):

@@ -33,15 +33,17 @@ class Species:
 @dataclass(frozen=True)
 class Element:
     """One lattice element (Listing 1 elements): kind L.BX_DRIFT / BX_QUAD /
-    BX_SBEND / BX_DIPEDGE / BX_CONSTF, length [m], strength k [1/m^2] (edge:
-    curvature 1/rho), bend or edge angle [rad], slices (space-charge kicks;
-    0 for a thin edge), k2 [1/m^2] (constant focusing in y)."""
+    BX_SBEND / BX_DIPEDGE / BX_CONSTF / BX_MULTIPOLE, length [m], strength k
+    [1/m^2] (edge: curvature 1/rho; multipole: kn), bend or edge angle [rad],
+    slices (space-charge kicks; 0 for a thin element), k2 [1/m^2] (constant
+    focusing in y; multipole: ks), order (multipole order m)."""
     kind: int
     length: float
     k: float
     angle: float
     nslice: int
     k2: float = 0.0
+    order: int = 0
 
 
 def _ptr6(t: torch.Tensor):
@@ -136,6 +138,7 @@ def lattice_struct(elements: Sequence, space_charge: bool):
         arr[i].k = float(e.k)
         arr[i].angle = float(e.angle)
         arr[i].k2 = float(getattr(e, "k2", 0.0))
+        arr[i].order = int(getattr(e, "order", 0))
     lat = L.bx_lattice()
     lat.elements = ctypes.cast(arr, ctypes.POINTER(L.bx_element))
     lat.count = len(elements)

@@ -162,6 +162,10 @@ int32_t track_impl(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t fi
     if (first_kick < 0 || first_kick > total || nkicks < 0 || first_kick + nkicks > total)
         return fail(ctx, BX_BAD_ARG, "kick range outside the slice schedule");
     if (nkicks == 0) return BX_OK;
+    if (diag && lattice_has_multipoles(lat))
+        return fail(ctx, BX_BAD_ARG,
+                    "per-slice diagnostics need a lattice without thin multipoles (their moments "
+                    "do not carry back through a nonlinear kick)");
     const Ref r = make_ref(beam);
     // map table: H_first, H_{k+1} H_k for inner boundaries, H_last
     std::vector<MapCoef> tab;
@@ -199,11 +203,11 @@ int32_t track_impl(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t fi
     if (!lat->space_charge) {
         if (!diag) {
             // maps only: H_first, merged pairs, H_last in one pass per particle
-            CK(launch_push_maps(c, beam->n, ctx->maps, (int)tab.size(), s), "push");
+            CK(launch_push_maps(c, beam->n, ctx->maps, (int)(nkicks + 1), s, ctx->status), "push");
         } else {
-            CK(launch_push_maps(c, beam->n, ctx->maps, 1, s), "push");
+            CK(launch_push_maps(c, beam->n, ctx->maps, 1, s, ctx->status), "push");
             for (int64_t k = 0; k < nkicks; ++k) {
-                CK(launch_push_maps(c, beam->n, ctx->maps + 1 + k, 1, s), "push");
+                CK(launch_push_maps(c, beam->n, ctx->maps + 1 + k, 1, s, ctx->status), "push");
                 CK(diag_after(k), "slice diagnostics");
             }
         }
@@ -222,7 +226,7 @@ int32_t track_impl(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t fi
                         ctx->kick, s, r.bg),
        "call init");
     if (binning) CK(sort_set_pointers(c, ctx->scr, ctx->dev_ptrs, s), "sort pointers");
-    CK(launch_push_maps(c, beam->n, ctx->maps, 1, s), "push");
+    CK(launch_push_maps(c, beam->n, ctx->maps, 1, s, ctx->status), "push");
     CK(launch_minmax(c, beam->n, r.bg, ctx->st, ctx->status, s), "minmax");
     const KickArgs ka{ctx, c, beam->id, beam->n, r.bg, binning};
     bool use_graph = !ctx->graphs_off && !profiler_timing(ctx->prof) && !diag;

@@ -22,7 +22,33 @@ enum : int32_t { ST_NONFINITE = 1, ST_TIMEOUT = 2, ST_OUTSIDE = 4 };
 struct MapCoef {
     double m00, m01, m05, m10, m11, m15, m22, m23, m32, m33, m40, m41, m45;
     double kick_t, kick_z, kind;
+    double aux;   // kind MAP_SPLIT: offset, in entries, from this entry to its SplitRec
 };
+
+// Map structure classes (see MapCoef): drift (x += m01 px, y += m23 py,
+// t += m45 pt), no dispersion (2x2 blocks and the t-pt term), general;
+// MAP_TABLE selects the per-call table in the particle kernels; MAP_SPLIT
+// (stored kind only): two linear parts with thin multipoles between them, in
+// the entry's SplitRec.
+enum MapKind { MAP_NONE = 0, MAP_DRIFT = 1, MAP_QUAD = 2, MAP_GENERAL = 3, MAP_TABLE = 4,
+               MAP_SPLIT = 5 };
+
+// Thin multipoles of orders 1..MP_MAX: kick polynomial terms z^0..z^(MP_MAX-1).
+constexpr int MP_MAX = 12;
+static_assert(MP_MAX == BX_MULTIPOLE_MAX_ORDER, "multipole orders of the ABI");
+
+// A map-table entry with thin multipoles at the slice boundary inside it:
+// z -> after(N(before(z))) with the thin kick N: px -= Re P, py += Im P,
+// P = sum_{j < nc} (cr[j] + i ci[j]) (x + i y)^j (all multipoles at that
+// boundary summed: their kicks depend on x, y only, so they commute with each
+// other and with the linear thin elements there, which `after` holds).
+struct SplitRec {
+    MapCoef before, after;
+    double nc;
+    double cr[MP_MAX], ci[MP_MAX];
+};
+// table entries (MapCoef units) one SplitRec takes, appended after the entries
+constexpr int SPLIT_UNITS = (int)((sizeof(SplitRec) + sizeof(MapCoef) - 1) / sizeof(MapCoef));
 
 // Pre-scaled field at a node (momentum change per unit CIC weight), padded to
 // 32 bytes so that one node is one aligned 256-bit load.
@@ -143,7 +169,7 @@ int32_t set_noctx_error(int32_t code, const char *msg);
 // ---- launchers (defined in the .cu files) --------------------------------
 // particles.cu
 cudaError_t launch_push_maps(double *const c[6], int64_t n, const MapCoef *maps, int nmaps,
-                             cudaStream_t s);
+                             cudaStream_t s, int32_t *status);
 cudaError_t launch_minmax(double *const c[6], int64_t n, double betagamma, TrackState *st,
                           int32_t *status, cudaStream_t s);
 cudaError_t launch_deposit(double *const c[6], int64_t n, double betagamma, const Box *box,

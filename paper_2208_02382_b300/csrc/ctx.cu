@@ -97,7 +97,13 @@ void element_map(const bx_element &e, double ds, const Ref &r, Mat m) {
     }
 }
 
-bool element_is_thin(const bx_element &e) { return e.type == BX_DIPEDGE; }
+bool element_is_thin(const bx_element &e) { return e.type == BX_DIPEDGE || e.type == BX_MULTIPOLE; }
+
+bool lattice_has_multipoles(const bx_lattice *lat) {
+    for (int i = 0; i < lat->count; ++i)
+        if (lat->elements[i].type == BX_MULTIPOLE) return true;
+    return false;
+}
 
 // Gauss-Jordan inverse with partial pivoting (the maps are well conditioned).
 void mat_inverse(const Mat a, Mat out) {
@@ -168,13 +174,16 @@ int32_t check_lattice(bx_ctx *ctx, const bx_lattice *l) {
     for (int i = 0; i < l->count; ++i) {
         const bx_element &e = l->elements[i];
         if (e.type != BX_DRIFT && e.type != BX_QUAD && e.type != BX_SBEND &&
-            e.type != BX_DIPEDGE && e.type != BX_CONSTF)
+            e.type != BX_DIPEDGE && e.type != BX_CONSTF && e.type != BX_MULTIPOLE)
             return fail(ctx, BX_BAD_ARG, "unknown element type");
         if (!std::isfinite(e.k) || !std::isfinite(e.angle) || !std::isfinite(e.k2))
             return fail(ctx, BX_BAD_ARG, "element k/angle/k2 not finite");
         if (element_is_thin(e)) {
             if (e.nslice != 0) return fail(ctx, BX_BAD_ARG, "thin element needs nslice = 0");
-            if (!(std::fabs(e.angle) < 1.5)) return fail(ctx, BX_BAD_ARG, "edge angle out of range");
+            if (e.type == BX_DIPEDGE && !(std::fabs(e.angle) < 1.5))
+                return fail(ctx, BX_BAD_ARG, "edge angle out of range");
+            if (e.type == BX_MULTIPOLE && (e.order < 1 || e.order > BX_MULTIPOLE_MAX_ORDER))
+                return fail(ctx, BX_BAD_ARG, "multipole order must be in 1..BX_MULTIPOLE_MAX_ORDER");
             continue;
         }
         if (!(e.length > 0.0) || !std::isfinite(e.length))
@@ -289,6 +298,7 @@ void thin_maps(const bx_lattice *lat, const Ref &r, std::vector<Mat6> &pre, Mat6
     for (int i = 0; i < lat->count; ++i) {
         const bx_element &e = lat->elements[i];
         if (element_is_thin(e)) {
+            if (e.type == BX_MULTIPOLE) continue;  // nonlinear: thin_multipoles
             Mat m;
             element_map(e, 0.0, r, m);
             mat_mul(m, t, t);
@@ -304,6 +314,48 @@ void thin_maps(const bx_lattice *lat, const Ref &r, std::vector<Mat6> &pre, Mat6
     memcpy(post.a, t, sizeof(Mat));
 }
 
+void thin_multipoles(const bx_lattice *lat, std::vector<MpPoly> &pre, MpPoly &post) {
+    pre.clear();
+    MpPoly q;
+    for (int i = 0; i < lat->count; ++i) {
+        const bx_element &e = lat->elements[i];
+        if (e.type == BX_MULTIPOLE) {
+            // kick polynomial term (kn + i ks) z^(m-1) / (m-1)!
+            const int j = e.order - 1;
+            double f = 1.0;
+            for (int a = 2; a <= j; ++a) f *= (double)a;
+            q.cr[j] += e.k / f;
+            q.ci[j] += e.k2 / f;
+            if (j + 1 > q.nc) q.nc = j + 1;
+            continue;
+        }
+        if (element_is_thin(e)) continue;
+        for (int k = 0; k < e.nslice; ++k) {
+            pre.push_back(q);
+            q = MpPoly();
+        }
+    }
+    post = q;
+}
+
+// Appends a MAP_SPLIT record for entry `idx` (before, multipoles, after).
+static void add_split(std::vector<MapCoef> &tab, std::vector<SplitRec> &recs, size_t idx,
+                      const Mat before, const Mat after, const MpPoly &q) {
+    SplitRec rec;
+    memset(&rec, 0, sizeof(rec));
+    rec.before = to_coef(before);
+    rec.after = to_coef(after);
+    rec.before.kind = rec.after.kind = (double)MAP_GENERAL;
+    rec.nc = (double)q.nc;
+    for (int j = 0; j < MP_MAX; ++j) {
+        rec.cr[j] = q.cr[j];
+        rec.ci[j] = q.ci[j];
+    }
+    tab[idx].kind = (double)MAP_SPLIT;
+    tab[idx].aux = (double)recs.size();  // record number for now; offset below
+    recs.push_back(rec);
+}
+
 void build_map_table(const bx_lattice *lat, const std::vector<int> &sel,
                      const std::vector<double> &sds, int64_t first, int64_t nkicks, const Ref &r,
                      std::vector<MapCoef> &tab) {
@@ -312,24 +364,38 @@ void build_map_table(const bx_lattice *lat, const std::vector<int> &sel,
     std::vector<Mat6> pre;
     Mat6 post;
     thin_maps(lat, r, pre, post);
+    std::vector<MpPoly> mp;
+    MpPoly mp_post;
+    thin_multipoles(lat, mp, mp_post);
+    std::vector<SplitRec> recs;
     const int64_t total = (int64_t)sel.size();
+    Mat eye;
+    mat_identity(eye);
     // entry 0: H_first(first) T_pre(first); entry 1 + k: H_first(k+1) T_pre(k+1)
-    // H_second(k); the last: T_post (at the end of the lattice) H_second(last)
-    Mat hk, hn, mm;
+    // H_second(k); the last: T_post (at the end of the lattice) H_second(last).
+    // Thin multipoles at a boundary sit between H_second (or nothing, ahead of
+    // the first slice) and T_pre H_first (or T_post).
+    Mat hk, hn, mm, after;
     element_map(lat->elements[sel[first]], 0.5 * sds[first], r, hk);
     mat_mul(hk, pre[first].a, mm);
     tab.push_back(to_coef(mm));
+    if (mp[first].nc) add_split(tab, recs, 0, eye, mm, mp[first]);
     for (int64_t k = first; k < first + nkicks; ++k) {
         if (k + 1 < first + nkicks) {
             element_map(lat->elements[sel[k + 1]], 0.5 * sds[k + 1], r, hn);
             mat_mul(pre[k + 1].a, hk, mm);
             mat_mul(hn, mm, mm);
             tab.push_back(to_coef(mm));
+            if (mp[k + 1].nc) {
+                mat_mul(hn, pre[k + 1].a, after);
+                add_split(tab, recs, tab.size() - 1, hk, after, mp[k + 1]);
+            }
             memcpy(hk, hn, sizeof(Mat));
         } else {
             if (k + 1 == total) mat_mul(post.a, hk, mm);
             else memcpy(mm, hk, sizeof(Mat));
             tab.push_back(to_coef(mm));
+            if (k + 1 == total && mp_post.nc) add_split(tab, recs, tab.size() - 1, hk, post.a, mp_post);
         }
     }
     // kick factors of kick k and the map class, in table entry 1 + k
@@ -338,7 +404,18 @@ void build_map_table(const bx_lattice *lat, const std::vector<int> &sel,
         tab[1 + k].kick_t = r.sign * ds / (r.mass_eV * (r.bg * r.bg));
         tab[1 + k].kick_z = -r.sign * ds / (r.mass_eV * r.bg);
     }
-    for (auto &m : tab) m.kind = (double)map_kind(m);
+    for (auto &m : tab)
+        if ((int)m.kind != MAP_SPLIT) m.kind = (double)map_kind(m);
+    // the records after the entries; aux = offset from the entry to its record
+    const size_t nent = tab.size();
+    for (size_t i = 0; i < nent; ++i)
+        if ((int)tab[i].kind == MAP_SPLIT) {
+            const size_t rec_at = nent + (size_t)tab[i].aux * SPLIT_UNITS;
+            tab[i].aux = (double)(rec_at - i);
+        }
+    tab.resize(nent + recs.size() * SPLIT_UNITS);
+    for (size_t q = 0; q < recs.size(); ++q)
+        memcpy((void *)&tab[nent + q * SPLIT_UNITS], &recs[q], sizeof(SplitRec));
 }
 
 int32_t ensure_moment_scratch(bx_ctx *ctx, int64_t n) {

@@ -87,10 +87,17 @@ struct Mat6 {
     double a[6][6];
 };
 bool element_is_thin(const bx_element &e);
+bool lattice_has_multipoles(const bx_lattice *lat);
 void mat_inverse(const Mat a, Mat out);
-// Products of the thin elements ahead of every slice (pre[j]: between slice
-// j-1 and slice j) and past the last slice (post), in beamline order.
+// Products of the linear thin elements ahead of every slice (pre[j]: between
+// slice j-1 and slice j) and past the last slice (post), in beamline order.
 void thin_maps(const bx_lattice *lat, const Ref &r, std::vector<Mat6> &pre, Mat6 &post);
+// Summed kick polynomials of the thin multipoles at the same places.
+struct MpPoly {
+    int nc = 0;
+    double cr[MP_MAX] = {}, ci[MP_MAX] = {};
+};
+void thin_multipoles(const bx_lattice *lat, std::vector<MpPoly> &pre, MpPoly &post);
 void mat_identity(Mat m);
 void focus_block(double ds, double k, double out[2][2]);
 void element_map(const bx_element &e, double ds, const Ref &r, Mat m);
@@ -101,7 +108,8 @@ MapCoef to_coef(const Mat m);
 void slice_schedule(const bx_lattice *lat, std::vector<int> &sel, std::vector<double> &sds);
 // Map table of kicks [first, first + nkicks): entry 0 the first half map,
 // entry 1 + k the map after kick k (merged halves) with the kick factors of
-// kick k and the map class.
+// kick k and the map class; entries at a slice boundary with thin multipoles
+// are MAP_SPLIT, their SplitRecs appended after the nkicks + 1 entries.
 void build_map_table(const bx_lattice *lat, const std::vector<int> &sel,
                      const std::vector<double> &sds, int64_t first, int64_t nkicks, const Ref &r,
                      std::vector<MapCoef> &tab);

@@ -137,12 +137,17 @@ __device__ __forceinline__ dd dd_tab(const double *hi, const double *lo, int j) 
 
 // log(a), a > 0: a = 2^e m with m in [1, 2); c = 1 + j/128 nearest to m;
 // log m = log c + 2 atanh(s), s = (m - c)/(m + c), |s| <= 2e-3, the atanh
-// series through s^11 (next term below 1e-31 relative).
+// series through s^11 (next term below 1e-31 relative).  a = 0 gives -Inf,
+// a < 0 or NaN gives NaN, a = +Inf gives +Inf; the table index stays in
+// range for every input.
 __device__ __noinline__ dd dd_log(dd a) {
+    if (!(a.hi > 0.0)) return dd{a.hi == 0.0 ? -INFINITY : NAN, 0.0};
+    if (isinf(a.hi)) return dd{INFINITY, 0.0};
     const int e = ilogb(a.hi);
-    const double sc = ldexp(1.0, -e);
-    const dd m = {a.hi * sc, a.lo * sc};
-    const int j = (int)((m.hi - 1.0) * 128.0 + 0.5);
+    // 2^-e in two exact steps (one overflows for subnormal a)
+    const double s1 = ldexp(1.0, -(e / 2)), s2 = ldexp(1.0, (e / 2) - e);
+    const dd m = {a.hi * s1 * s2, a.lo * s1 * s2};
+    const int j = min(max((int)((m.hi - 1.0) * 128.0 + 0.5), 0), 128);
     const double c = 1.0 + (double)j * (1.0 / 128.0);
     const dd s = dd_div(dd_add_d(m, -c), dd_add_d(m, c));
     const dd x = dd_mul(s, s);
@@ -159,7 +164,7 @@ __device__ __noinline__ dd dd_log(dd a) {
 // atan u with u = (n - c d)/(d + c n) (one division), |u| <= 7.9e-3, the atan
 // series through u^15 (next term below 1e-34 relative).
 __device__ __noinline__ dd dd_atan_ratio_unit(dd n, dd d) {
-    const int j = (int)(n.hi / d.hi * 64.0 + 0.5);
+    const int j = min(max((int)(n.hi / d.hi * 64.0 + 0.5), 0), 64);  // NaN ratio: 0
     const double c = (double)j * (1.0 / 64.0);
     const dd u = dd_div(dd_sub(n, dd_mul_d(d, c)), dd_add(d, dd_mul_d(n, c)));
     const dd x = dd_mul(u, u);

@@ -299,6 +299,8 @@ int32_t bx_grad_forward(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat,
     if (checkpoint_interval <= 0) return fail(ctx, BX_BAD_ARG, "checkpoint_interval must be >= 1");
     if (ctx->shape != 1)
         return fail(ctx, BX_BAD_ARG, "the reverse mode supports particle shape 1 (CIC) only");
+    if (lattice_has_multipoles(lat))
+        return fail(ctx, BX_BAD_ARG, "the reverse mode supports linear thin elements only (no multipoles)");
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<int> sel;
     std::vector<double> sds;
@@ -381,7 +383,7 @@ int32_t bx_grad_forward(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat,
     for (int k = 0; k < 6; ++k)
         CK(cudaMemcpyAsync(g->z0 + (size_t)k * beam->n, c[k], bytes, cudaMemcpyDeviceToDevice, s),
            "save z0");
-    CK(launch_push_maps(c, beam->n, ctx->maps, 1, s), "push");
+    CK(launch_push_maps(c, beam->n, ctx->maps, 1, s, ctx->status), "push");
     CK(launch_minmax(c, beam->n, g->ref.bg, ctx->st, ctx->status, s), "minmax");
     for (int64_t k = 0; k < K; ++k) {
         if (k % C == 0) {

@@ -187,7 +187,7 @@ cudaError_t capture_branch(cudaGraph_t top, const KickArgs &k, int nkicks, doubl
                                                   cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return e;
     e = launch_state_reset(ctx->st, nkicks, q_macro, sort_interval, s0, k.bg);
-    if (e == cudaSuccess) e = launch_push_maps(k.c, k.n, ctx->maps, 1, s0);
+    if (e == cudaSuccess) e = launch_push_maps(k.c, k.n, ctx->maps, 1, s0, ctx->status);
     if (e == cudaSuccess) e = launch_minmax(k.c, k.n, k.bg, ctx->st, ctx->status, s0);
     cudaGraphConditionalHandle hw = 0;
     if (e == cudaSuccess)
@@ -271,7 +271,7 @@ int32_t bx_batch_create(bx_batch **out, int32_t count, bx_ctx *const *ctxs,
                 if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(b->s[0], top, nullptr, nullptr, 0,
                                                                         cudaStreamCaptureModeRelaxed);
                 if (e == cudaSuccess) {
-                    cudaError_t e1 = launch_push_maps(beam->coord, beam->n, ctx->maps, (int)tab.size(), b->s[0]);
+                    cudaError_t e1 = launch_push_maps(beam->coord, beam->n, ctx->maps, (int)(K + 1), b->s[0], ctx->status);
                     cudaGraph_t g = top;
                     e = cudaStreamEndCapture(b->s[0], &g);
                     if (e1 != cudaSuccess) e = e1;

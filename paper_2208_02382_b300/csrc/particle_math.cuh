@@ -7,10 +7,6 @@
 
 namespace bt {
 
-// Map structure classes (see MapCoef): drift (x += m01 px, y += m23 py,
-// t += m45 pt), no dispersion (2x2 blocks and the t-pt term), general.
-enum MapKind { MAP_NONE = 0, MAP_DRIFT = 1, MAP_QUAD = 2, MAP_GENERAL = 3, MAP_TABLE = 4 };
-
 template <int MK>
 __device__ __forceinline__ void apply_map_k(const MapCoef &m, double &x, double &px, double &y,
                                             double &py, double &t, double pt) {
@@ -42,13 +38,43 @@ __device__ __forceinline__ void apply_map_k(const MapCoef &m, double &x, double 
     }
 }
 
+// Thin multipole kick of a SplitRec: P(x + i y) by Horner's rule in complex
+// FP64, then px -= Re P, py += Im P.
+__device__ __forceinline__ void thin_multipole_kick(const SplitRec &r, double x, double &px,
+                                                    double y, double &py) {
+    const int nc = (int)r.nc;
+    double pr = 0.0, pi = 0.0;
+    for (int j = nc - 1; j >= 0; --j) {  // P = P z + c_j
+        const double nr = fma(pr, x, fma(-pi, y, r.cr[j]));
+        pi = fma(pr, y, fma(pi, x, r.ci[j]));
+        pr = nr;
+    }
+    px -= pr;
+    py += pi;
+}
+
+__device__ __forceinline__ void apply_split(const SplitRec &r, double &x, double &px, double &y,
+                                            double &py, double &t, double pt) {
+    apply_map_k<MAP_GENERAL>(r.before, x, px, y, py, t, pt);
+    thin_multipole_kick(r, x, px, y, py);
+    apply_map_k<MAP_GENERAL>(r.after, x, px, y, py, t, pt);
+}
+
+// The SplitRec of table entry `row` (kind MAP_SPLIT).
+__device__ __forceinline__ const SplitRec *split_rec(const MapCoef *row) {
+    return reinterpret_cast<const SplitRec *>(row + (long long)row->aux);
+}
+
 // MAP_TABLE: the map (and its class in `kind`) comes from the per-call
-// device table; the class branch is uniform across the grid.
-__device__ __forceinline__ void apply_map_table(const MapCoef &m, double &x, double &px, double &y,
-                                                double &py, double &t, double pt) {
+// device table entry `row` (a copy of it in `m`); the class branch is
+// uniform across the grid.
+__device__ __forceinline__ void apply_map_table(const MapCoef &m, const MapCoef *row, double &x,
+                                                double &px, double &y, double &py, double &t,
+                                                double pt) {
     const int k = (int)m.kind;
     if (k == MAP_DRIFT) apply_map_k<MAP_DRIFT>(m, x, px, y, py, t, pt);
     else if (k == MAP_QUAD) apply_map_k<MAP_QUAD>(m, x, px, y, py, t, pt);
+    else if (k == MAP_SPLIT) apply_split(*split_rec(row), x, px, y, py, t, pt);
     else apply_map_k<MAP_GENERAL>(m, x, px, y, py, t, pt);
 }
 

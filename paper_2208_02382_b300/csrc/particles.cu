@@ -43,24 +43,30 @@ int map_kind(const MapCoef &m) {
 __global__ void k_push_maps(double *__restrict__ x, double *__restrict__ px,
                             double *__restrict__ y, double *__restrict__ py,
                             double *__restrict__ t, const double *__restrict__ pt, int64_t n,
-                            const MapCoef *__restrict__ maps, int nmaps) {
+                            const MapCoef *__restrict__ maps, int nmaps, int32_t *status) {
+    bool bad = false;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         double a = x[p], b = px[p], c = y[p], d = py[p], e = t[p], f = pt[p];
-        for (int k = 0; k < nmaps; ++k) apply_map_k<MAP_GENERAL>(maps[k], a, b, c, d, e, f);
+        for (int k = 0; k < nmaps; ++k) {
+            if ((int)maps[k].kind == MAP_SPLIT) apply_split(*split_rec(maps + k), a, b, c, d, e, f);
+            else apply_map_k<MAP_GENERAL>(maps[k], a, b, c, d, e, f);
+        }
+        bad |= !finite6(a, b, c, d, e, f);
         x[p] = a;
         px[p] = b;
         y[p] = c;
         py[p] = d;
         t[p] = e;
     }
+    if (bad && status) atomicOr(status, ST_NONFINITE);
 }
 
 cudaError_t launch_push_maps(double *const c[6], int64_t n, const MapCoef *maps, int nmaps,
-                             cudaStream_t s) {
+                             cudaStream_t s, int32_t *status) {
     if (n <= 0 || nmaps <= 0) return cudaSuccess;
     BT_LAUNCH(K_PUSH, s, k_push_maps<<<grid_for(n), TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4],
-                                                                 c[5], n, maps, nmaps));
+                                                                 c[5], n, maps, nmaps, status));
     return cudaGetLastError();
 }
 
@@ -192,9 +198,13 @@ __device__ void box_rule_body(TrackState *st, int nn, long long *log, int64_t ca
         st->nlog += 1;
     }
     box_finish(st->box, st->nbg);
+    // a box that is not finite (a bunch with Inf/NaN coordinates, or extents
+    // beyond the double range) halts the kick: no Green's function, deposit,
+    // sort or next kick (the particle kernel flags the coordinates)
     bool finite = true;
     for (int d = 0; d < 3; ++d)
-        finite = finite && isfinite(st->box.lo[d]) && isfinite(st->box.hi[d]) && st->box.h[d] > 0.0;
+        finite = finite && isfinite(st->box.lo[d]) && isfinite(st->box.hi[d]) && st->box.h[d] > 0.0 &&
+                 isfinite(st->box.h[d]) && isfinite(st->box.inv_h[d]);
     st->regrid = need ? 1 : 0;
     st->halt = finite ? 0 : 1;
     st->green_stale = (finite && (st->box.h[0] != st->green_h[0] || st->box.h[1] != st->green_h[1] ||
@@ -475,6 +485,7 @@ struct PartArgs {
     int flag_outside;                  // report deposit particles outside the box
     const int *gate;                   // if set and 0, the kernel does nothing
     const MapCoef *maps;               // MAP_TABLE: per-call map table (entry 1 + k)
+    const MapCoef *row;                // MAP_TABLE: this kick's entry (set by the kernel)
     const TrackState *dst;             // device-driven: exact_u and k from here
     int shape;                         // particle shape: 1 CIC, 2 TSC
 };
@@ -539,7 +550,10 @@ template <int MK, bool GATHER, bool DEP, bool MM, int SH>
 __global__ void __launch_bounds__(TPB, SH == 1 ? 4 : 3) k_particles(PartArgs a) {
     if (a.gate && *a.gate == 0) return;
     if (a.dst) a.exact_u = a.dst->exact_u;
-    if constexpr (MK == MAP_TABLE) a.map = a.maps[1 + a.dst->k_in_call];
+    if constexpr (MK == MAP_TABLE) {
+        a.row = a.maps + 1 + a.dst->k_in_call;
+        a.map = *a.row;
+    }
     extern __shared__ unsigned long long dsm[];
     unsigned long long *sF = dsm;                                // [3][CHUNK] fractions
     int *scell = (int *)(dsm + 3 * CHUNK);                       // [CHUNK] packed cell or -1
@@ -641,7 +655,7 @@ __global__ void __launch_bounds__(TPB, SH == 1 ? 4 : 3) k_particles(PartArgs a) 
                 px += i64_scaled_to_double(ex, e0);
                 py += i64_scaled_to_double(ey, e1);
                 pt += i64_scaled_to_double(ez, e2);
-                if constexpr (MK == MAP_TABLE) apply_map_table(a.map, x, px, y, py, t, pt);
+                if constexpr (MK == MAP_TABLE) apply_map_table(a.map, a.row, x, px, y, py, t, pt);
                 else apply_map_k<MK>(a.map, x, px, y, py, t, pt);
                 bad |= !finite6(x, px, y, py, t, pt);
                 a.ox[p] = x;

@@ -114,7 +114,7 @@ def test_tracking_through_multipoles_is_symplectic():
     # the composed map of thick linear elements and thin multipoles (space
     # charge off) has a symplectic Jacobian at any particle
     lat = bg.fodo_multipole_lattice(2)
-    z = np.array([1e-3, 1e-4, -0.8e-3, 0.5e-4, 1e-3, 1e-4])
+    z = np.array([3e-3, 3e-4, -2.4e-3, 1.5e-4, 3e-3, 3e-4])
     t = tr.Tracker(REF, 1e-9, 8, space_charge=False)
     eps = np.array([1e-8, 1e-9, 1e-8, 1e-9, 1e-8, 1e-9])   # central differences, O(eps^2)
     jac = np.zeros((6, 6))
@@ -129,7 +129,7 @@ def test_tracking_through_multipoles_is_symplectic():
     lin = [e for e in lat if e.kind != ph.MULTIPOLE or e.order <= 2]
     zl = t.track(z[:, None], lin)[:, 0]
     zn = t.track(z[:, None], lat)[:, 0]
-    assert np.max(np.abs(zn - zl)) > 1e-5
+    assert np.max(np.abs(zn - zl)) > 3e-5
 
 
 def test_multipoles_between_slices_and_split_calls():
