@@ -66,10 +66,13 @@ typedef struct bx_batch bx_batch;
  * n_grid         : nodes per dimension N of the charge/potential grid; a power
  *                  of two in [8, 256].  The Poisson solve runs on the doubled
  *                  (2N)^3 grid.
- * shape_order    : particle shape (Listing 1 set_particle_shape); 1 (CIC) only.
+ * shape_order    : particle shape (Listing 1 set_particle_shape): 1 (CIC) or
+ *                  2 (TSC).
  * rebin_interval : kicks between re-binning the particles by grid bin (a
  *                  stable counting sort that keeps the deposit's shared-memory
- *                  tiles compact): 0 = default (16), -1 = never, else >= 1.
+ *                  tiles compact), counted on the context's kick counter (it
+ *                  carries over between bx_track calls until bx_reset): 0 =
+ *                  default (16), -1 = never, else >= 1.
  * bin_edge       : grid cells per bin edge: 0 = default (8, or N/16 above
  *                  N = 128), else a power of two in [2, N/2] with at most 16^3
  *                  bins.  Neither changes any result, only the speed

@@ -226,8 +226,7 @@ int32_t track_impl(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t fi
                         ctx->kick, s, r.bg),
        "call init");
     if (binning) CK(sort_set_pointers(c, ctx->scr, ctx->dev_ptrs, s), "sort pointers");
-    CK(launch_push_maps(c, beam->n, ctx->maps, 1, s, ctx->status), "push");
-    CK(launch_minmax(c, beam->n, r.bg, ctx->st, ctx->status, s), "minmax");
+    CK(launch_push_maps(c, beam->n, ctx->maps, 1, s, ctx->status, ctx->st, r.bg), "push");
     const KickArgs ka{ctx, c, beam->id, beam->n, r.bg, binning};
     bool use_graph = !ctx->graphs_off && !profiler_timing(ctx->prof) && !diag;
     if (use_graph) {

@@ -169,7 +169,8 @@ int32_t set_noctx_error(int32_t code, const char *msg);
 // ---- launchers (defined in the .cu files) --------------------------------
 // particles.cu
 cudaError_t launch_push_maps(double *const c[6], int64_t n, const MapCoef *maps, int nmaps,
-                             cudaStream_t s, int32_t *status);
+                             cudaStream_t s, int32_t *status, TrackState *st = nullptr,
+                             double betagamma = 0.0);
 cudaError_t launch_minmax(double *const c[6], int64_t n, double betagamma, TrackState *st,
                           int32_t *status, cudaStream_t s);
 cudaError_t launch_deposit(double *const c[6], int64_t n, double betagamma, const Box *box,
@@ -231,6 +232,7 @@ cudaError_t launch_sort(double *const c[6], long long *id, int64_t n, double bet
 cudaError_t launch_moments(double *const c[6], int64_t n, double *partials, int nblocks,
                            double *out, cudaStream_t s);
 int moments_blocks(int64_t n);
+size_t moments_scratch_doubles(int nblocks);
 cudaError_t launch_moments_transform(double *mom, const MapCoef *map, cudaStream_t s);
 // fft.cu
 struct FftPlan {

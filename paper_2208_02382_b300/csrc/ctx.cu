@@ -419,12 +419,12 @@ void build_map_table(const bx_lattice *lat, const std::vector<int> &sel,
 }
 
 int32_t ensure_moment_scratch(bx_ctx *ctx, int64_t n) {
-    int nb = moments_blocks(n);
-    if (nb * 21 > ctx->mom_partial_cap) {
+    const int need = (int)moments_scratch_doubles(moments_blocks(n));
+    if (need > ctx->mom_partial_cap) {
         if (ctx->mom_partial) cudaFree(ctx->mom_partial);
         ctx->mom_partial = nullptr;
-        CK(cudaMalloc(&ctx->mom_partial, (size_t)nb * 21 * sizeof(double)), "moments scratch");
-        ctx->mom_partial_cap = nb * 21;
+        CK(cudaMalloc(&ctx->mom_partial, (size_t)need * sizeof(double)), "moments scratch");
+        ctx->mom_partial_cap = need;
     }
     return BX_OK;
 }

@@ -383,8 +383,7 @@ int32_t bx_grad_forward(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat,
     for (int k = 0; k < 6; ++k)
         CK(cudaMemcpyAsync(g->z0 + (size_t)k * beam->n, c[k], bytes, cudaMemcpyDeviceToDevice, s),
            "save z0");
-    CK(launch_push_maps(c, beam->n, ctx->maps, 1, s, ctx->status), "push");
-    CK(launch_minmax(c, beam->n, g->ref.bg, ctx->st, ctx->status, s), "minmax");
+    CK(launch_push_maps(c, beam->n, ctx->maps, 1, s, ctx->status, ctx->st, g->ref.bg), "push");
     for (int64_t k = 0; k < K; ++k) {
         if (k % C == 0) {
             const int64_t sg = k / C;

@@ -187,8 +187,7 @@ cudaError_t capture_branch(cudaGraph_t top, const KickArgs &k, int nkicks, doubl
                                                   cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return e;
     e = launch_state_reset(ctx->st, nkicks, q_macro, sort_interval, s0, k.bg);
-    if (e == cudaSuccess) e = launch_push_maps(k.c, k.n, ctx->maps, 1, s0, ctx->status);
-    if (e == cudaSuccess) e = launch_minmax(k.c, k.n, k.bg, ctx->st, ctx->status, s0);
+    if (e == cudaSuccess) e = launch_push_maps(k.c, k.n, ctx->maps, 1, s0, ctx->status, ctx->st, k.bg);
     cudaGraphConditionalHandle hw = 0;
     if (e == cudaSuccess)
         e = cudaGraphConditionalHandleCreate(&hw, top, 1, cudaGraphCondAssignDefault);

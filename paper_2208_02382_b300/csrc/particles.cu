@@ -38,39 +38,7 @@ int map_kind(const MapCoef &m) {
     return MAP_GENERAL;
 }
 
-// ---------------------------------------------------------------- push only
-
-__global__ void k_push_maps(double *__restrict__ x, double *__restrict__ px,
-                            double *__restrict__ y, double *__restrict__ py,
-                            double *__restrict__ t, const double *__restrict__ pt, int64_t n,
-                            const MapCoef *__restrict__ maps, int nmaps, int32_t *status) {
-    bool bad = false;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        double a = x[p], b = px[p], c = y[p], d = py[p], e = t[p], f = pt[p];
-        for (int k = 0; k < nmaps; ++k) {
-            if ((int)maps[k].kind == MAP_SPLIT) apply_split(*split_rec(maps + k), a, b, c, d, e, f);
-            else apply_map_k<MAP_GENERAL>(maps[k], a, b, c, d, e, f);
-        }
-        bad |= !finite6(a, b, c, d, e, f);
-        x[p] = a;
-        px[p] = b;
-        y[p] = c;
-        py[p] = d;
-        t[p] = e;
-    }
-    if (bad && status) atomicOr(status, ST_NONFINITE);
-}
-
-cudaError_t launch_push_maps(double *const c[6], int64_t n, const MapCoef *maps, int nmaps,
-                             cudaStream_t s, int32_t *status) {
-    if (n <= 0 || nmaps <= 0) return cudaSuccess;
-    BT_LAUNCH(K_PUSH, s, k_push_maps<<<grid_for(n), TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4],
-                                                                 c[5], n, maps, nmaps, status));
-    return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------ min/max
+// --------------------------------------------------- min/max and push only
 
 // Block min/max of order-preserving keys, folded into the state with integer
 // atomics (exact, order-free).  All threads of the block must call it.
@@ -105,6 +73,49 @@ __device__ __forceinline__ void block_keys_commit(long long lo[3], long long hi[
     }
 }
 
+
+// Maps (each by its class, uniform per entry) applied to every particle; with
+// `st`, also the min/max keys of the new rest-frame positions (the box rule's
+// input), so a call's prologue reads the bunch once.
+__global__ void k_push_maps(double *__restrict__ x, double *__restrict__ px,
+                            double *__restrict__ y, double *__restrict__ py,
+                            double *__restrict__ t, const double *__restrict__ pt, int64_t n,
+                            const MapCoef *__restrict__ maps, int nmaps, int32_t *status,
+                            TrackState *st, double nbg) {
+    bool bad = false;
+    long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        double a = x[p], b = px[p], c = y[p], d = py[p], e = t[p], f = pt[p];
+        for (int k = 0; k < nmaps; ++k) apply_map_table(maps[k], maps + k, a, b, c, d, e, f);
+        bad |= !finite6(a, b, c, d, e, f);
+        x[p] = a;
+        px[p] = b;
+        y[p] = c;
+        py[p] = d;
+        t[p] = e;
+        if (st) {
+            const long long k0 = dkey(a), k1 = dkey(c), k2 = dkey(__dmul_rn(nbg, e));
+            lo[0] = min(lo[0], k0);
+            hi[0] = max(hi[0], k0);
+            lo[1] = min(lo[1], k1);
+            hi[1] = max(hi[1], k1);
+            lo[2] = min(lo[2], k2);
+            hi[2] = max(hi[2], k2);
+        }
+    }
+    if (bad && status) atomicOr(status, ST_NONFINITE);
+    if (st) block_keys_commit(lo, hi, st);
+}
+
+cudaError_t launch_push_maps(double *const c[6], int64_t n, const MapCoef *maps, int nmaps,
+                             cudaStream_t s, int32_t *status, TrackState *st, double betagamma) {
+    if (n <= 0 || nmaps <= 0) return cudaSuccess;
+    BT_LAUNCH(K_PUSH, s, k_push_maps<<<grid_for(n), TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4],
+                                                                 c[5], n, maps, nmaps, status, st,
+                                                                 -betagamma));
+    return cudaGetLastError();
+}
 
 __global__ void k_minmax(const double *__restrict__ x, const double *__restrict__ px,
                          const double *__restrict__ y, const double *__restrict__ py,
@@ -217,7 +228,10 @@ __device__ void box_rule_body(TrackState *st, int nn, long long *log, int64_t ca
         if (st->box_hist) st->box_hist[st->kick] = st->box;
         if (st->slot_hist) st->slot_hist[st->kick] = st->green_builds - 1;
         st->deposit_gate = (finite && (need || k == 0)) ? 1 : 0;
-        st->sort_gate = (finite && st->sort_interval > 0 && k % st->sort_interval == 0) ? 1 : 0;
+        // re-binning on the global kick count (it carries over between calls,
+        // so tracking one kick per call re-bins every sort_interval kicks too)
+        st->sort_gate =
+            (finite && st->sort_interval > 0 && st->kick % st->sort_interval == 0) ? 1 : 0;
         st->next_gate = (finite && k + 1 < st->nkicks_call) ? 1 : 0;
         st->exact_u = box_far_offset(st->box) ? 1 : 0;
         st->rho_scale = st->q_macro / (st->box.h[0] * st->box.h[1] * st->box.h[2]);
