@@ -115,7 +115,9 @@ def main():
     vals = []
     for (_, coef) in rows:
         vals += [repr(float(c)) for c in coef]
-    lines.append(f"__constant__ double IGF_FAR_P[{len(vals)}] = {{")
+    # global memory, read through the read-only path: the coefficient kernel's
+    # threads read different entries (constant memory would serialize them)
+    lines.append(f"__device__ const double IGF_FAR_P[{len(vals)}] = {{")
     for i in range(0, len(vals), 4):
         lines.append("    " + ", ".join(vals[i:i + 4]) + ",")
     lines.append("};")

@@ -41,22 +41,23 @@ __device__ dd ln_u_plus_r(dd u, dd r, dd rest2) {
     return dd_log(dd_div(rest2, dd_sub(r, u)));
 }
 
-__device__ dd igf_antiderivative(dd x, dd y, dd z) {
-    dd x2 = dd_mul(x, x), y2 = dd_mul(y, y), z2 = dd_mul(z, z);
-    dd r = dd_sqrt(dd_add(dd_add(x2, y2), z2));
-    dd a1 = dd_atan_ratio(dd_mul(x, y), dd_mul(z, r));
-    dd a2 = dd_atan_ratio(dd_mul(x, z), dd_mul(y, r));
-    dd a3 = dd_atan_ratio(dd_mul(y, z), dd_mul(x, r));
-    dd lx = ln_u_plus_r(x, r, dd_add(y2, z2));
-    dd ly = ln_u_plus_r(y, r, dd_add(x2, z2));
-    dd lz = ln_u_plus_r(z, r, dd_add(x2, y2));
-    dd f = dd_scale(dd_mul(z2, a1), -0.5);
-    f = dd_sub(f, dd_scale(dd_mul(y2, a2), 0.5));
-    f = dd_sub(f, dd_scale(dd_mul(x2, a3), 0.5));
-    f = dd_add(f, dd_mul(dd_mul(y, z), lx));
-    f = dd_add(f, dd_mul(dd_mul(x, z), ly));
-    f = dd_add(f, dd_mul(dd_mul(x, y), lz));
-    return f;
+// The antiderivative F at corner (x, y, z), split over three lanes: lane j
+// (0, 1, 2) forms the j-th atan term (z^2, y^2, x^2 times atan(xy/(zr)),
+// atan(xz/(yr)), atan(yz/(xr)), halved) and the j-th log term (yz ln(x+r),
+// xz ln(y+r), xy ln(z+r)); all three lanes take the same path.  The caller
+// sums the six terms in a fixed order.
+__device__ void igf_terms(dd x, dd y, dd z, int j, dd &at, dd &lg) {
+    const dd x2 = dd_mul(x, x), y2 = dd_mul(y, y), z2 = dd_mul(z, z);
+    const dd r = dd_sqrt(dd_add(dd_add(x2, y2), z2));
+    // lane j's operands (selects, no divergence)
+    const dd an = j == 0 ? dd_mul(x, y) : (j == 1 ? dd_mul(x, z) : dd_mul(y, z));
+    const dd ad = j == 0 ? dd_mul(z, r) : (j == 1 ? dd_mul(y, r) : dd_mul(x, r));
+    const dd ap = j == 0 ? z2 : (j == 1 ? y2 : x2);
+    at = dd_scale(dd_mul(ap, dd_atan_ratio(an, ad)), 0.5);
+    const dd lu = j == 0 ? x : (j == 1 ? y : z);
+    const dd lr = j == 0 ? dd_add(y2, z2) : (j == 1 ? dd_add(x2, z2) : dd_add(x2, y2));
+    const dd lp = j == 0 ? dd_mul(y, z) : (j == 1 ? dd_mul(x, z) : dd_mul(x, y));
+    lg = dd_mul(lp, ln_u_plus_r(lu, r, lr));
 }
 
 // A cell at distance R (squared R2) is far when R2 >= 16 (hx^2 + hy^2 + hz^2),
@@ -70,7 +71,8 @@ __device__ __forceinline__ int igf_near_extent(int n, double hd, double hsum2) {
 }
 
 // With a tracking state `gate`, the cell size is the state's box h and the
-// kernel does nothing unless the Green's function is stale.
+// kernel does nothing unless the Green's function is stale.  Four lanes per
+// corner (three used), eight corners per warp.
 __global__ void k_igf_corner(int n, double hx, double hy, double hz, double2 *__restrict__ fc,
                              const TrackState *gate) {
     if (gate) {
@@ -85,16 +87,34 @@ __global__ void k_igf_corner(int n, double hx, double hy, double hz, double2 *__
     const int ci = igf_near_extent(n, hx, hsum2) + 2, cj = igf_near_extent(n, hy, hsum2) + 2,
               ck = igf_near_extent(n, hz, hsum2) + 2;
     const long long total = (long long)ci * cj * ck;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        int i = (int)(idx % ci);
-        int j = (int)((idx / ci) % cj);
-        int k = (int)(idx / ((long long)ci * cj));
-        dd x = two_prod(i - 0.5, hx);
-        dd y = two_prod(j - 0.5, hy);
-        dd z = two_prod(k - 0.5, hz);
-        dd f = igf_antiderivative(x, y, z);
-        fc[((long long)k * m + j) * m + i] = make_double2(f.hi, f.lo);
+    const int lane = threadIdx.x & 3, j = lane < 3 ? lane : 2;
+    const long long stride = (long long)gridDim.x * blockDim.x / 4;
+    // every lane of a group runs the same iterations (the shuffles need all 32)
+    for (long long base = (blockIdx.x * (long long)blockDim.x) / 4; base < total; base += stride) {
+        const long long idx = base + threadIdx.x / 4;
+        const bool live = idx < total;
+        const long long id = live ? idx : 0;
+        const int i = (int)(id % ci);
+        const int jj = (int)((id / ci) % cj);
+        const int k = (int)(id / ((long long)ci * cj));
+        dd at, lg;
+        igf_terms(two_prod(i - 0.5, hx), two_prod(jj - 0.5, hy), two_prod(k - 0.5, hz), j, at, lg);
+        // lane 0 of the group gathers the other lanes' terms
+        const int g0 = threadIdx.x & ~3;
+        const double a1h = __shfl_sync(0xffffffffu, at.hi, g0 + 1), a1l = __shfl_sync(0xffffffffu, at.lo, g0 + 1);
+        const double a2h = __shfl_sync(0xffffffffu, at.hi, g0 + 2), a2l = __shfl_sync(0xffffffffu, at.lo, g0 + 2);
+        const double l1h = __shfl_sync(0xffffffffu, lg.hi, g0 + 1), l1l = __shfl_sync(0xffffffffu, lg.lo, g0 + 1);
+        const double l2h = __shfl_sync(0xffffffffu, lg.hi, g0 + 2), l2l = __shfl_sync(0xffffffffu, lg.lo, g0 + 2);
+        if (lane == 0 && live) {
+            // F = -z^2/2 atan(..) - y^2/2 atan(..) - x^2/2 atan(..) + yz ln + xz ln + xy ln
+            dd f = dd_neg(at);
+            f = dd_sub(f, dd{a1h, a1l});
+            f = dd_sub(f, dd{a2h, a2l});
+            f = dd_add(f, lg);
+            f = dd_add(f, dd{l1h, l1l});
+            f = dd_add(f, dd{l2h, l2l});
+            fc[((long long)k * m + jj) * m + i] = make_double2(f.hi, f.lo);
+        }
     }
 }
 
@@ -102,7 +122,8 @@ constexpr int IGF_FAR_NC = 164;  // sum over n = 1..8 of (n+1)(n+2)/2 monomials
 
 // Coefficients of Q_n (n = 1..8) over U^i V^j W^k for half-sides a = h/2:
 // sum over (p,q,t) of a_x^2p a_y^2q a_z^2t times the tabulated coefficient.
-// One block per build; the sum kernel's blocks read the result.
+// Six one-warp blocks per build (the work of one SM's FP64 pipe spread over
+// six); the sum kernel's blocks read the result.
 __global__ void k_igf_coef(double hx, double hy, double hz, const TrackState *gate, double *c) {
     if (gate) {
         if (!gate->green_stale || gate->halt) return;
@@ -111,7 +132,15 @@ __global__ void k_igf_coef(double hx, double hy, double hz, const TrackState *ga
         hz = gate->box.h[2];
     }
     const double ax2 = 0.25 * hx * hx, ay2 = 0.25 * hy * hy, az2 = 0.25 * hz * hz;
-    for (int k = threadIdx.x; k < IGF_FAR_NC; k += blockDim.x) {
+    // powers a^2p, p <= 8, per dimension
+    double P[9], Q[9], T[9];
+    P[0] = Q[0] = T[0] = 1.0;
+    for (int e = 1; e <= 8; ++e) {
+        P[e] = P[e - 1] * ax2;
+        Q[e] = Q[e - 1] * ay2;
+        T[e] = T[e - 1] * az2;
+    }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < IGF_FAR_NC; k += gridDim.x * blockDim.x) {
         int n = 1, base = 0;
         while (k >= base + (n + 1) * (n + 2) / 2) {
             base += (n + 1) * (n + 2) / 2;
@@ -121,14 +150,9 @@ __global__ void k_igf_coef(double hx, double hy, double hz, const TrackState *ga
         double acc = 0.0;
         int ti = 0;
         for (int p = n; p >= 0; --p)
-            for (int q = n - p; q >= 0; --q, ++ti) {
-                const int t = n - p - q;
-                double A = 1.0;
-                for (int e = 0; e < p; ++e) A *= ax2;
-                for (int e = 0; e < q; ++e) A *= ay2;
-                for (int e = 0; e < t; ++e) A *= az2;
-                acc = fma(A, IGF_FAR_P[IGF_FAR_OFF[n - 1] + ti * nt + mono], acc);
-            }
+            for (int q = n - p; q >= 0; --q, ++ti)
+                acc = fma(P[p] * Q[q] * T[n - p - q],
+                          __ldg(&IGF_FAR_P[IGF_FAR_OFF[n - 1] + ti * nt + mono]), acc);
         c[k] = acc;
     }
 }
@@ -230,12 +254,13 @@ cudaError_t launch_igf_table(int n, const double h[3], double *fcorner, double *
     double *coef = fcorner + 2LL * m * m * m;
     // the near region's size is known on the device only (h may come from the
     // state): one-warp blocks, a few per SM, grid-stride.  A corner is a long
-    // serial chain of FP64 double-double work; small blocks spread the ~1e3
-    // corners of a typical near region over all SMs instead of a few.
+    // chain of FP64 double-double work; three lanes share it and one-warp
+    // blocks spread the ~1e3 corners of a typical near region over all SMs
+    // instead of a few.
     const int bc = 148 * 4;
     const int bs = (int)std::min<long long>((ts + 255) / 256, 148 * 16);
     const double h0 = h ? h[0] : 0.0, h1 = h ? h[1] : 0.0, h2 = h ? h[2] : 0.0;
-    BT_LAUNCH(K_IGF_CORNER, s, k_igf_coef<<<1, 192, 0, s>>>(h0, h1, h2, gate, coef));
+    BT_LAUNCH(K_IGF_CORNER, s, k_igf_coef<<<6, 32, 0, s>>>(h0, h1, h2, gate, coef));
     BT_LAUNCH(K_IGF_CORNER, s, k_igf_corner<<<bc, 32, 0, s>>>(n, h0, h1, h2, (double2 *)fcorner, gate));
     BT_LAUNCH(K_IGF_SUM, s, k_igf_sum<<<bs, 256, 0, s>>>(n, h0, h1, h2, (const double2 *)fcorner,
                                                          coef, gtable, gate));
