@@ -322,15 +322,16 @@ int32_t bx_twiss_grad(const double twiss[8], const double S[36], double out[6]);
 /* Forward pass for differentiation: tracks the beam through the whole
  * lattice (all kicks, from a fresh state: no box, kick counter 0; space
  * charge as lattice->space_charge says), like bx_track but re-binning the
- * particles only once, before the first kick (when beam->id is given; the
- * particle order is then fixed for the run), and records in the context: the initial bunch, a checkpoint
+ * particles (when beam->id is given) before the first kick and at every
+ * checkpoint, keeping each re-binning's particle map for the reverse pass,
+ * and records in the context: the initial bunch, a checkpoint
  * (state and device tracking state) every `checkpoint_interval` kicks, the box
  * of every kick and every Green's function spectrum built.  box_replay (host,
  * may be NULL): 12 doubles per kick {lo[3], hi[3], h[3], 1/h[3]} as returned by
  * bx_grad_boxes; the box of each kick is then taken from it instead of the
  * box rule.  The beam arrays hold the final bunch afterwards.  Device memory
- * of the recording: about (ceil(K/C) + C + 3) * 48 bytes per particle plus
- * C * 32 * n^3 + (K + 1) * 8 * (n+1)^3 bytes (K kicks, C = checkpoint_interval,
+ * of the recording: about (ceil(K/C) + C + 3) * 48 + 4 * ceil(K/C) bytes per
+ * particle plus C * 32 * n^3 + (K + 1) * 8 * (n+1)^3 bytes (K kicks, C = checkpoint_interval,
  * n = n_grid); allocated on the first call for a given size.  Asynchronous
  * except the allocation; BX_BAD_ARG for an empty beam or lattice. */
 int32_t bx_grad_forward(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lattice,

@@ -22,6 +22,7 @@
 // the scatter accumulates in int64 fixed point (order-independent integer
 // atomics, so the reverse pass is bitwise reproducible).  Block sums run in a
 // fixed order.
+#include <algorithm>
 #include <climits>
 
 #include "common.cuh"
@@ -616,6 +617,26 @@ cudaError_t launch_twiss_beam(P6 xi_dev, int64_t n, const double c[8], P6 out_de
     BT_LAUNCH(K_ADJ_PART, s, k_twiss_beam<<<grid_lin(n), 256, 0, s>>>(
                                  xi_dev, n, c[0], c[1], c[2], c[3], c[4], c[5], c[6], c[7],
                                  out_dev));
+    return cudaGetLastError();
+}
+
+__global__ void k_permute6(P6 in, const int *__restrict__ dest, int64_t n, P6 out, int gather) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = dest[p];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            if (gather) out.p[c][p] = in.p[c][d];
+            else out.p[c][d] = in.p[c][p];
+        }
+    }
+}
+
+cudaError_t launch_permute6(P6 in, const int *dest, int64_t n, P6 out, bool gather,
+                            cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int b = (int)std::min<int64_t>((n + 255) / 256, 148 * 16);
+    BT_LAUNCH(K_ADJ_PART, s, k_permute6<<<b, 256, 0, s>>>(in, dest, n, out, gather ? 1 : 0));
     return cudaGetLastError();
 }
 

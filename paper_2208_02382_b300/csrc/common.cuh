@@ -227,7 +227,7 @@ cudaError_t launch_sort(double *const c[6], long long *id, int64_t n, double bet
                         const Box *box, int nn, int be, int *keys, long long *counts,
                         long long *offs, long long *sums, double *const scratch[6],
                         long long *id_scratch, double **dev_ptrs, cudaStream_t s,
-                        const int *gate = nullptr);
+                        const int *gate = nullptr, int *dest_out = nullptr);
 // moments.cu
 cudaError_t launch_moments(double *const c[6], int64_t n, double *partials, int nblocks,
                            double *out, cudaStream_t s);
@@ -286,6 +286,11 @@ int adj_blocks(int64_t n);
 cudaError_t launch_adj_seed(P6 c, int64_t n, const double *mom, const double w[4], P6 A,
                             unsigned long long *amax, cudaStream_t s);
 cudaError_t launch_adj_kick(const AdjKick &k, cudaStream_t s);
+// Six arrays through a re-binning map dest (particle p went to slot dest[p]):
+// gather out[p] = in[dest[p]] (back to the order before), else scatter
+// out[dest[p]] = in[p] (forward).
+cudaError_t launch_permute6(P6 in, const int *dest, int64_t n, P6 out, bool gather,
+                            cudaStream_t s);
 cudaError_t launch_adj_initial(P6 A, P6 z0, int64_t n, const MapCoef *map0, P6 out, double *part,
                                double *sums, cudaStream_t s);
 cudaError_t launch_ghat_store(const TrackState *st, double *store, double *ghat, long long count,

@@ -20,6 +20,8 @@
 //   field ring         C n^3 EFix     the fixed-point field of each kick
 //   Green's store      up to K + 1 spectra (n+1)^3, one per build
 //   box/slot history   K
+//   re-binning maps    ceil(K/C) n int32 (destination of each particle at the
+//                      re-binning that starts a segment)
 //   adjoint            6 n, 3 n^3 int64 scatter, 2 (n+2)^3 grid, (K+1) 13 map adjoints
 #include <algorithm>
 #include <array>
@@ -48,6 +50,8 @@ struct GradTape {
     unsigned long long *amax = nullptr;
     int *sexp = nullptr;
     double *part = nullptr, *mbar = nullptr, *sums0 = nullptr, *mom = nullptr;
+    int *perm = nullptr;     // per segment: destination slot of each particle at its re-binning
+    bool binned = false;     // segments >= 1 start with a re-binning
     // host record of the run
     std::vector<bx_element> elements;
     std::vector<int> sel;
@@ -63,7 +67,7 @@ void grad_free(bx_ctx *ctx) {
     if (!g) return;
     void *ptrs[] = {g->z0, g->ckpt, g->ring, g->ckst, g->efix_ring, g->escale_ring, g->box_hist,
                     g->box_replay, g->slot_hist, g->ghat_store, g->adj, g->kbar, g->phibar,
-                    g->rb, g->amax, g->sexp, g->part, g->mbar, g->sums0, g->mom};
+                    g->rb, g->amax, g->sexp, g->part, g->mbar, g->sums0, g->mom, g->perm};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete g;
@@ -125,6 +129,7 @@ static int32_t grad_alloc(bx_ctx *ctx, int64_t np, int64_t K, int C) {
     A((void **)&g->mbar, sizeof(double) * 13 * (K + 1));
     A((void **)&g->sums0, sizeof(double) * 49);
     A((void **)&g->mom, sizeof(double) * 27);
+    A((void **)&g->perm, sizeof(int) * np * g->nseg);
     if (e != cudaSuccess) {
         grad_free(ctx);
         return cuda_fail(ctx, e, "differentiation tape");
@@ -360,9 +365,9 @@ int32_t bx_grad_forward(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat,
     double *const *c = beam->coord;
     const size_t bytes = (size_t)beam->n * sizeof(double);
     if (beam->id) {
-        // bin the initial bunch once by grid brick (of a box around it), so the
-        // deposits and the reverse scatter touch compact sets of cells; the
-        // order then stays fixed for the whole run (no later re-binning)
+        // bin the initial bunch by grid brick (of a box around it), so the
+        // deposits and the reverse scatter touch compact sets of cells (each
+        // later segment starts with another re-binning)
         if ((rc = ensure_sort_scratch(ctx, beam->n))) return rc;
         CK(sort_set_pointers(c, ctx->scr, ctx->dev_ptrs, s), "sort pointers");
         CK(launch_minmax(c, beam->n, g->ref.bg, ctx->st, ctx->status, s), "minmax");
@@ -384,9 +389,18 @@ int32_t bx_grad_forward(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat,
         CK(cudaMemcpyAsync(g->z0 + (size_t)k * beam->n, c[k], bytes, cudaMemcpyDeviceToDevice, s),
            "save z0");
     CK(launch_push_maps(c, beam->n, ctx->maps, 1, s, ctx->status, ctx->st, g->ref.bg), "push");
+    g->binned = beam->id != nullptr;
     for (int64_t k = 0; k < K; ++k) {
         if (k % C == 0) {
             const int64_t sg = k / C;
+            if (sg > 0 && g->binned)
+                // re-bin (the order decays as the lattice turns phase space),
+                // keeping where each particle went for the reverse pass
+                CK(launch_sort(c, (long long *)beam->id, beam->n, g->ref.bg, &ctx->st->box, ctx->n,
+                               sort_brick_edge(ctx->n, ctx->bin_edge), ctx->keys, ctx->counts,
+                               ctx->offs, ctx->sums, ctx->scr, ctx->id_scr, ctx->dev_ptrs, s,
+                               nullptr, g->perm + (size_t)sg * beam->n),
+                   "re-binning");
             double *dst = g->ckpt + (size_t)sg * 6 * beam->n;
             for (int q = 0; q < 6; ++q)
                 CK(cudaMemcpyAsync(dst + (size_t)q * beam->n, c[q], bytes, cudaMemcpyDeviceToDevice, s),
@@ -474,10 +488,28 @@ int32_t bx_grad_backward(bx_ctx *ctx, const bx_beam *beam, const double weights[
             CK(launch_adj_kick(a, s), "adjoint kick");
             std::swap(cur, nxt);
         }
+        if (sg > 0 && g->binned) {
+            // the segment started with a re-binning: back to the order before it
+            P6 tmp = p6(g->ring + st6, np);
+            CK(launch_permute6(adj, g->perm + (size_t)sg * np, np, tmp, true, s), "un-binning");
+            CK(cudaMemcpyAsync(g->adj, g->ring + st6, st6 * sizeof(double), cudaMemcpyDeviceToDevice, s),
+               "un-binning");
+        }
     }
     P6 out = adj;
     if (zbar0) out = p6(zbar0);
     CK(launch_adj_initial(adj, p6(g->z0, np), np, ctx->maps, out, g->part, g->sums0, s), "initial");
+    if (zbar0 && g->binned)
+        // dL/dz0 in the beam's (final) particle order: the segments' re-binnings
+        // in forward order
+        for (int sg = 1; sg < g->nseg; ++sg) {
+            P6 tmp = p6(g->ring + st6, np);
+            CK(launch_permute6(out, g->perm + (size_t)sg * np, np, tmp, false, s), "re-binning");
+            for (int q = 0; q < 6; ++q)
+                CK(cudaMemcpyAsync(out.p[q], tmp.p[q], (size_t)np * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, s),
+                   "re-binning");
+        }
     std::vector<double> mbar((size_t)13 * (K + 1)), sums(49);
     CK(cudaMemcpyAsync(mbar.data() + 13, g->mbar + 13, sizeof(double) * 13 * K,
                        cudaMemcpyDeviceToHost, s),

@@ -145,7 +145,7 @@ __global__ void k_sort_scatter(const int *__restrict__ keys, const long long *__
                                const double *const *__restrict__ src,
                                const long long *__restrict__ id_src,
                                double *const *__restrict__ dst, long long *__restrict__ id_dst,
-                               const int *gate) {
+                               const int *gate, int *__restrict__ dest_out) {
     if (gate && *gate == 0) return;
     extern __shared__ int running[];
     for (int i = threadIdx.x; i < nbricks; i += SORT_TPB) running[i] = 0;
@@ -174,6 +174,7 @@ __global__ void k_sort_scatter(const int *__restrict__ keys, const long long *__
 #pragma unroll
             for (int c = 0; c < 6; ++c) dst[c][d] = src[c][p];
             id_dst[d] = id_src[p];
+            if (dest_out) dest_out[p] = (int)d;
         }
         __syncthreads();
     }
@@ -208,7 +209,7 @@ cudaError_t launch_sort(double *const c[6], long long *id, int64_t n, double bet
                         const Box *box, int nn, int be, int *keys, long long *counts,
                         long long *offs, long long *sums, double *const scratch[6],
                         long long *id_scratch, double **dev_ptrs, cudaStream_t s,
-                        const int *gate) {
+                        const int *gate, int *dest_out) {
     if (n <= 0) return cudaSuccess;
     (void)c;
     (void)scratch;
@@ -228,7 +229,7 @@ cudaError_t launch_sort(double *const c[6], long long *id, int64_t n, double bet
     BT_LAUNCH(K_SORT, s, k_scan_apply<<<(unsigned)nt, SORT_TPB, 0, s>>>(counts, len, sums, offs, gate));
     BT_LAUNCH(K_SORT, s, k_sort_scatter<<<(unsigned)nch, SORT_TPB, hsm, s>>>(
                              keys, offs, n, nb, nch, dp, id, (double *const *)(dev_ptrs + 6),
-                             id_scratch, gate));
+                             id_scratch, gate, dest_out));
     const int cb = (int)((n + 255) / 256) < 148 * 16 ? (int)((n + 255) / 256) : 148 * 16;
     BT_LAUNCH(K_SORT, s, k_sort_copy_back<<<cb, 256, 0, s>>>(dev_ptrs, id_scratch, id, n, gate));
     return cudaGetLastError();

@@ -63,7 +63,7 @@ def _gpu_grad(bt, trk, xi_t, lat, sp, charge, w, C, replay=None, space_charge=Tr
     coords = bt.twiss_beam(bg.TWISS_FODO, xi_t)
     beam = bt.Beam(coords, sp, charge)
     trk.grad_forward(beam, lat, C, box_replay=replay, space_charge=space_charge)
-    # the recording forward bins the particles once: compare in id order
+    # the recording forward re-bins the particles: compare in id order
     order = np.argsort(beam.ids.cpu().numpy())
     final = beam.coords.cpu().numpy()[:, order]
     boxes = trk.grad_boxes()
@@ -129,15 +129,21 @@ def test_gradients_match_central_differences_box_replayed(bt):
 
 
 def test_gradients_independent_of_checkpoint_interval_and_reproducible(bt):
+    # the recording forward re-bins the bunch at every checkpoint, so another
+    # interval means another particle order and FP64 sums in another order:
+    # equal to rounding; the same interval twice is bitwise the same
     npart, n, charge = 2000, 16, 10e-9
     xi, xi_t, lat, sp = _setup(bt, npart, n, 1, charge, seed=7)
     w = np.array([1.0, 1.0, 1.0, 1.0])
     trk = bt.Tracker(n)
     runs = [_gpu_grad(bt, trk, xi_t, lat, sp, charge, w, C=c) for c in (1, 7, 20, 20)]
-    for r in runs[1:]:
-        assert np.array_equal(r["dk"], runs[0]["dk"])
-        assert np.array_equal(r["S"], runs[0]["S"])
-        assert np.array_equal(r["zbar0"], runs[0]["zbar0"])
+    for r in runs[1:3]:
+        assert _rel(r["dk"], runs[0]["dk"]) < 1e-12
+        assert _rel(r["S"], runs[0]["S"]) < 1e-12
+        assert max(_rel(r["zbar0"][q], runs[0]["zbar0"][q]) for q in range(6)) < 1e-12
+        assert np.array_equal(r["final"], runs[0]["final"])
+    for key in ("dk", "S", "zbar0", "final"):
+        assert np.array_equal(runs[3][key], runs[2][key])
 
 
 def test_autograd_function(bt):
