@@ -223,10 +223,12 @@ int32_t track_impl(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t fi
     // per-kick map and kick factors come from the table at index 1 + k; no
     // host decision or synchronisation between kicks.
     CK(launch_call_init(ctx->st, (int)nkicks, q_macro, binning ? ctx->sort_interval : 0,
-                        ctx->kick, s, r.bg),
+                        ctx->kick, s, r.bg, true),
        "call init");
     if (binning) CK(sort_set_pointers(c, ctx->scr, ctx->dev_ptrs, s), "sort pointers");
-    CK(launch_push_maps(c, beam->n, ctx->maps, 1, s, ctx->status, ctx->st, r.bg), "push");
+    CK(launch_track_prologue(c, beam->n, r.bg, &ctx->st->box, ctx->n, ctx->maps, ctx->acc_hi,
+                             ctx->acc_lo, ctx->st, ctx->status, s, ctx->shape),
+       "prologue");
     const KickArgs ka{ctx, c, beam->id, beam->n, r.bg, binning};
     bool use_graph = !ctx->graphs_off && !profiler_timing(ctx->prof) && !diag;
     if (use_graph) {

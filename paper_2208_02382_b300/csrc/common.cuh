@@ -106,7 +106,7 @@ struct TrackState {
     const Box *box_replay;  // the box of every kick is taken from here
     int32_t *slot_hist;     // index of the Green's function build in use
     int32_t green_builds;   // Green's function builds so far
-    int32_t pad2;
+    int32_t pro_dep;        // the call's prologue deposited into the box kept from before
 };
 
 // Order-preserving map between doubles and signed 64-bit keys (monotone for
@@ -192,7 +192,14 @@ cudaError_t launch_field(const double *phi, int nn, const Box *box, double kx, d
                          int *escale, cudaStream_t s, const TrackState *st = nullptr,
                          const MapCoef *maps = nullptr);
 cudaError_t launch_call_init(TrackState *st, int nkicks, double q_macro, int sort_interval,
-                             long long kick0, cudaStream_t s, double betagamma);
+                             long long kick0, cudaStream_t s, double betagamma,
+                             bool fused_prologue = false);
+// First half map of a tracking call (table entry 0) with the min/max keys and,
+// when a box was kept from the previous call, the first kick's deposit into it.
+cudaError_t launch_track_prologue(double *const c[6], int64_t n, double betagamma, const Box *box,
+                                  int nn, const MapCoef *maps, unsigned long long *acc_hi,
+                                  unsigned long long *acc_lo, TrackState *st, int32_t *status,
+                                  cudaStream_t s, int shape);
 cudaError_t launch_zero_acc(unsigned long long *a, unsigned long long *b, int nn, const int *gate,
                             cudaStream_t s);
 cudaError_t launch_track_particles(double *const c[6], int64_t n, double betagamma,

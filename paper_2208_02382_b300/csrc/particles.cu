@@ -227,7 +227,10 @@ __device__ void box_rule_body(TrackState *st, int nn, long long *log, int64_t ca
         if (st->green_stale) st->green_builds += 1;
         if (st->box_hist) st->box_hist[st->kick] = st->box;
         if (st->slot_hist) st->slot_hist[st->kick] = st->green_builds - 1;
-        st->deposit_gate = (finite && (need || k == 0)) ? 1 : 0;
+        // deposit for this kick unless it is in the accumulators already: the
+        // previous kick's B, or (first kick of a call) the fused prologue into
+        // the box that the rule kept
+        st->deposit_gate = (finite && (need || (k == 0 && !st->pro_dep))) ? 1 : 0;
         // re-binning on the global kick count (it carries over between calls,
         // so tracking one kick per call re-bins every sort_interval kicks too)
         st->sort_gate =
@@ -310,8 +313,11 @@ cudaError_t launch_state_reset(TrackState *st, int nkicks, double q_macro, int s
 }
 
 __global__ void k_call_init(TrackState *st, int nkicks, double q_macro, int sort_interval,
-                            long long kick0, double nbg) {
+                            long long kick0, double nbg, int fused_prologue) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
+        // a fused prologue deposits into the box of the previous call when one
+        // exists and was made for the same beta gamma (its u_z constant)
+        st->pro_dep = fused_prologue && st->has_box && st->nbg == nbg ? 1 : 0;
         st->nbg = nbg;
         st->k_in_call = -1;
         st->nkicks_call = nkicks;
@@ -326,9 +332,10 @@ __global__ void k_call_init(TrackState *st, int nkicks, double q_macro, int sort
 }
 
 cudaError_t launch_call_init(TrackState *st, int nkicks, double q_macro, int sort_interval,
-                             long long kick0, cudaStream_t s, double betagamma) {
+                             long long kick0, cudaStream_t s, double betagamma,
+                             bool fused_prologue) {
     BT_LAUNCH(K_BOX, s, k_call_init<<<1, 32, 0, s>>>(st, nkicks, q_macro, sort_interval, kick0,
-                                                      -betagamma));
+                                                      -betagamma, fused_prologue ? 1 : 0));
     return cudaGetLastError();
 }
 
@@ -498,6 +505,7 @@ struct PartArgs {
     int exact_u;                       // u = (X - lo) * (1/h) instead of one FMA
     int flag_outside;                  // report deposit particles outside the box
     const int *gate;                   // if set and 0, the kernel does nothing
+    const int *dep_if;                 // if set and 0, no deposit (the rest runs)
     const MapCoef *maps;               // MAP_TABLE: per-call map table (entry 1 + k)
     const MapCoef *row;                // MAP_TABLE: this kick's entry (set by the kernel)
     const TrackState *dst;             // device-driven: exact_u and k from here
@@ -558,10 +566,14 @@ bool box_needs_exact_u(const Box &b) { return box_far_offset(b); }
 //         accumulators, through a shared-memory tile covering the block's
 //         nodes when they fit.
 // MM:     min/max keys of the new rest-frame positions.
+// Without GATHER, a map MK (MAP_TABLE: entry 0 at a call's start) is applied
+// and stored before DEP/MM (a tracking call's fused prologue).
 // CIC instances fit 64 registers and (with 52 KB of shared memory for DEP) run 4 blocks
-// per SM; TSC instances keep 3 (its 27-node gather would spill at 64).
+// per SM; TSC instances and the map-plus-deposit prologue keep 3 (they would
+// spill at 64).
 template <int MK, bool GATHER, bool DEP, bool MM, int SH>
-__global__ void __launch_bounds__(TPB, SH == 1 ? 4 : 3) k_particles(PartArgs a) {
+__global__ void __launch_bounds__(TPB, (SH == 1 && !(DEP && MK != MAP_NONE)) ? 4 : 3)
+    k_particles(PartArgs a) {
     if (a.gate && *a.gate == 0) return;
     if (a.dst) a.exact_u = a.dst->exact_u;
     if constexpr (MK == MAP_TABLE) {
@@ -591,6 +603,8 @@ __global__ void __launch_bounds__(TPB, SH == 1 ? 4 : 3) k_particles(PartArgs a) 
     bool bad = false, outside = false;
     const int64_t base = (int64_t)blockIdx.x * CHUNK;
     if (DEP) __syncthreads();
+    bool dep_on = DEP;                                  // uniform over the grid
+    if constexpr (DEP) dep_on = !a.dep_if || *a.dep_if != 0;
     // u = (X - lo)/h: one FMA with the box's constants, or (far-offset box)
     // the subtraction first; a uniform branch selects one of two compiled
     // copies of the particle loop, so each copy does only its own arithmetic
@@ -678,6 +692,17 @@ __global__ void __launch_bounds__(TPB, SH == 1 ? 4 : 3) k_particles(PartArgs a) 
                 a.opy[p] = py;
                 a.ot[p] = t;
                 a.opt[p] = pt;
+            } else if constexpr (MK != MAP_NONE) {
+                double px = a.px[p], py = a.py[p];
+                const double pt = a.pt[p];
+                if constexpr (MK == MAP_TABLE) apply_map_table(a.map, a.row, x, px, y, py, t, pt);
+                else apply_map_k<MK>(a.map, x, px, y, py, t, pt);
+                bad |= !finite6(x, px, y, py, t, pt);
+                a.ox[p] = x;
+                a.opx[p] = px;
+                a.oy[p] = y;
+                a.opy[p] = py;
+                a.ot[p] = t;
             }
             if constexpr (DEP || MM) {
                 if constexpr (MM) {
@@ -689,7 +714,7 @@ __global__ void __launch_bounds__(TPB, SH == 1 ? 4 : 3) k_particles(PartArgs a) 
                     klo[2] = min(klo[2], k2);
                     khi[2] = max(khi[2], k2);
                 }
-                if constexpr (DEP) {
+                if constexpr (DEP) if (dep_on) {
                     int c0, c1, c2;
                     unsigned long long F0, F1, F2;
                     bool out1 = false;
@@ -728,6 +753,7 @@ __global__ void __launch_bounds__(TPB, SH == 1 ? 4 : 3) k_particles(PartArgs a) 
     if (outside) atomicOr(a.status, ST_OUTSIDE);
     if constexpr (MM) block_keys_commit(klo, khi, a.st);
     if constexpr (DEP) {
+        if (!dep_on) return;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             int l = blo[d], h = bhi[d];
@@ -950,6 +976,27 @@ cudaError_t launch_track_particles_oop(double *const cin[6], double *const cout[
     b.dst = st;
     b.gate = &st->next_gate;
     return launch_pk<MAP_NONE, false, true, true>(b, s, K_DEPOSIT);
+}
+
+// A tracking call's prologue in one pass: table entry 0 (the first half map),
+// the min/max keys of the new positions, and, when the state kept a box from
+// the previous call (pro_dep, set by the call init), the first kick's deposit
+// into that box; the box rule then deposits again only if it regrids.
+cudaError_t launch_track_prologue(double *const c[6], int64_t n, double betagamma, const Box *box,
+                                  int nn, const MapCoef *maps, unsigned long long *acc_hi,
+                                  unsigned long long *acc_lo, TrackState *st, int32_t *status,
+                                  cudaStream_t s, int shape) {
+    cudaError_t e = launch_zero_acc(acc_hi, acc_lo, nn, &st->pro_dep, s);
+    if (e != cudaSuccess || n <= 0) return e;
+    PartArgs a = part_args(c, n, betagamma, box, nn, shape);
+    a.maps = maps;
+    a.dst = st;
+    a.st = st;
+    a.acc_hi = acc_hi;
+    a.acc_lo = acc_lo;
+    a.status = status;
+    a.dep_if = &st->pro_dep;
+    return launch_pk<MAP_TABLE, false, true, true>(a, s, K_PUSH);
 }
 
 // Device-driven deposit of the current positions when the box rule asks for it.
