@@ -102,26 +102,58 @@ __global__ void k_mom_sum(const double *__restrict__ x, const double *__restrict
     }
 }
 
-// Means (fixed-order sums of the partials) into out[0..5], and the scale
-// exponents s_c into scale[0..5]: 2^s_c times the extent of coordinate c
-// about its mean stays below 2^43, so a product is below 2^87, a thread's sum
-// of at most 256 of them below 2^95 (its high word fits a signed 32-bit
-// integer), and the sum over up to 2^31 particles below 2^118.
-__global__ void k_mom_means(const double *__restrict__ partial, int nblocks, int64_t n,
-                            double *__restrict__ out, int *__restrict__ scale) {
+// Means (a fixed-order reduction of the partials) into out[0..5], and the
+// scale exponents s_c into scale[0..5].  One block.
+__global__ void __launch_bounds__(MOM_TPB) k_mom_means(const double *__restrict__ partial,
+                                                     int nblocks, int64_t n,
+                                                     double *__restrict__ out,
+                                                     int *__restrict__ scale) {
+    // each thread folds blocks t, t + 256, ... (in that order), then a fixed
+    // shared-memory tree: the same result for the same partials every time
+    __shared__ double ss[6][MOM_TPB];
+    __shared__ long long slo[6][MOM_TPB], shi[6][MOM_TPB];
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    long long lo[6], hi[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        lo[c] = LLONG_MAX;
+        hi[c] = LLONG_MIN;
+    }
+    for (int b = threadIdx.x; b < nblocks; b += MOM_TPB) {
+        const double *pb = partial + (size_t)b * MOM_P1;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            v[c] += pb[c];
+            lo[c] = min(lo[c], reinterpret_cast<const long long *>(pb)[6 + c]);
+            hi[c] = max(hi[c], reinterpret_cast<const long long *>(pb)[12 + c]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        ss[c][threadIdx.x] = v[c];
+        slo[c][threadIdx.x] = lo[c];
+        shi[c][threadIdx.x] = hi[c];
+    }
+    __syncthreads();
+    for (int st = MOM_TPB / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                ss[c][threadIdx.x] += ss[c][threadIdx.x + st];
+                slo[c][threadIdx.x] = min(slo[c][threadIdx.x], slo[c][threadIdx.x + st]);
+                shi[c][threadIdx.x] = max(shi[c][threadIdx.x], shi[c][threadIdx.x + st]);
+            }
+        __syncthreads();
+    }
     const int c = threadIdx.x;
     if (c >= 6) return;
-    double s = 0.0;
-    long long lo = LLONG_MAX, hi = LLONG_MIN;
-    for (int b = 0; b < nblocks; ++b) {
-        const double *pb = partial + (size_t)b * MOM_P1;
-        s += pb[c];
-        lo = min(lo, reinterpret_cast<const long long *>(pb)[6 + c]);
-        hi = max(hi, reinterpret_cast<const long long *>(pb)[12 + c]);
-    }
-    const double mean = s / (double)n;
+    // scale exponent s_c: 2^s_c times the extent of coordinate c about its
+    // mean stays below 2^43, so a product is below 2^87, a thread's sum of at
+    // most 256 of them below 2^95 (its high word fits a signed 32-bit
+    // integer), and the sum over up to 2^31 particles below 2^118
+    const double mean = ss[c][0] / (double)n;
     out[c] = mean;
-    const double ext = fmax(dkey_inv(hi) - mean, mean - dkey_inv(lo));
+    const double ext = fmax(dkey_inv(shi[c][0]) - mean, mean - dkey_inv(slo[c][0]));
     const int B = 43;
     int sc = 0;
     if (ext > 0.0 && isfinite(ext)) sc = B - (ilogb(ext) + 1);  // ext < 2^(ilogb + 1)
@@ -215,22 +247,28 @@ __global__ void __launch_bounds__(MOM_TPB) k_mom_cov(
     }
 }
 
-// out[6 + k] = (sum over blocks of the 128-bit partial k) 2^-(s_a + s_b) / n.
+// out[6 + k] = (sum over blocks of the 128-bit partial k) 2^-(s_a + s_b) / n,
+// one warp per k (exact integer sums: any order).
 __global__ void k_mom_cov_final(const unsigned long long *__restrict__ partial, int nblocks,
                                 int64_t n, const int *__restrict__ scale,
                                 double *__restrict__ out) {
-    const int k = threadIdx.x;
-    if (k >= 21) return;
+    const int k = blockIdx.x, lane = threadIdx.x;
+    long long h = 0;
+    unsigned long long l = 0;
+    for (int q = lane; q < nblocks; q += 32)
+        add128(h, l, (long long)partial[(size_t)q * MOM_P2 + 2 * k], partial[(size_t)q * MOM_P2 + 2 * k + 1]);
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long hh = __shfl_xor_sync(0xffffffffu, h, o);
+        const unsigned long long ll = __shfl_xor_sync(0xffffffffu, l, o);
+        add128(h, l, hh, ll);
+    }
+    if (lane != 0) return;
     int a = 0, r = k;
     while (r >= 6 - a) {
         r -= 6 - a;
         ++a;
     }
     const int b = a + r;
-    long long h = 0;
-    unsigned long long l = 0;
-    for (int q = 0; q < nblocks; ++q)
-        add128(h, l, (long long)partial[(size_t)q * MOM_P2 + 2 * k], partial[(size_t)q * MOM_P2 + 2 * k + 1]);
     if (scale[a] == INT_MIN || scale[b] == INT_MIN) {
         out[6 + k] = NAN;
         return;
@@ -243,10 +281,10 @@ cudaError_t launch_moments(double *const c[6], int64_t n, double *partials, int 
                            double *out, cudaStream_t s) {
     int *scale = reinterpret_cast<int *>(partials + (size_t)nblocks * MOM_P2);
     BT_LAUNCH(K_MOMENTS, s, k_mom_sum<<<nblocks, MOM_TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5], n, partials));
-    BT_LAUNCH(K_MOMENTS, s, k_mom_means<<<1, 32, 0, s>>>(partials, nblocks, n, out, scale));
+    BT_LAUNCH(K_MOMENTS, s, k_mom_means<<<1, MOM_TPB, 0, s>>>(partials, nblocks, n, out, scale));
     BT_LAUNCH(K_MOMENTS, s, k_mom_cov<<<nblocks, MOM_TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5], n, out, scale,
                                                                     reinterpret_cast<unsigned long long *>(partials)));
-    BT_LAUNCH(K_MOMENTS, s, k_mom_cov_final<<<1, 32, 0, s>>>(reinterpret_cast<const unsigned long long *>(partials),
+    BT_LAUNCH(K_MOMENTS, s, k_mom_cov_final<<<21, 32, 0, s>>>(reinterpret_cast<const unsigned long long *>(partials),
                                                               nblocks, n, scale, out));
     return cudaGetLastError();
 }
