@@ -157,6 +157,35 @@ __global__ void k_igf_coef(double hx, double hy, double hz, const TrackState *ga
     }
 }
 
+// sum_{n <= L} Q_n(U, V, W) iR2^n = sum over 1 <= i+j+k <= L of
+// c_ijk a^i b^j w^k with a = U iR2, b = V iR2, w = W iR2, by nested Horner
+// schemes in w, b, a (one FMA per coefficient plus one per (i, j) and per i:
+// 164 + 44 at L = 8, against two products and an FMA per monomial).  c holds
+// order n's coefficients from offset sum_{m < n} (m+1)(m+2)/2, the monomial
+// U^i V^j W^(n-i-j) at (n-i)(n-i+1)/2 + (n-i-j) within its order.
+template <int L>
+__device__ __forceinline__ double igf_far_series(double a, double b, double w, const double *c) {
+    double sa = 0.0;
+#pragma unroll
+    for (int i = L; i >= 0; --i) {
+        double sb = 0.0;
+#pragma unroll
+        for (int j = L - i; j >= 0; --j) {
+            double sw = 0.0;
+#pragma unroll
+            for (int k = L - i - j; k >= 0; --k) {
+                const int n = i + j + k;
+                const int base = n * (n + 1) * (n + 2) / 6 - 1;   // sum_{m=1}^{n-1} (m+1)(m+2)/2
+                const double cv = n == 0 ? 0.0 : c[base + (n - i) * (n - i + 1) / 2 + (n - i - j)];
+                sw = fma(sw, w, cv);
+            }
+            sb = fma(sb, b, sw);
+        }
+        sa = fma(sa, a, sb);
+    }
+    return sa;
+}
+
 // G of a far cell at (x, y, z) = (a hx, b hy, c hz), with the coefficients c
 // and q = V/(4 pi eps0) in double-double.  The series stops at the order L
 // whose remainder rho^(2L+2) is small (rho^2 = |h|^2/(4 R^2)): L = 8 for
@@ -169,33 +198,14 @@ __device__ double igf_far_cell(int a, int b, int cc, double hx, double hy, doubl
     const dd R2 = dd_add(dd_add(dd_mul(x, x), dd_mul(y, y)), dd_mul(z, z));
     const double iR2 = 1.0 / R2.hi;
     const double rho2 = 0.25 * hsum2 * iR2;
-    const int L = rho2 > 1.0 / 256.0 ? 8 : rho2 > 1.0 / 1024.0 ? 6 : rho2 > 1.0 / 4096.0 ? 5
-                : rho2 > 1.0 / 65536.0 ? 4 : 3;
-    const double U = x.hi * x.hi * iR2, V = y.hi * y.hi * iR2, W = z.hi * z.hi * iR2;
-    double Up[9], Vp[9], Wp[9];
-    Up[0] = Vp[0] = Wp[0] = 1.0;
-#pragma unroll
-    for (int e = 1; e <= 8; ++e) {
-        Up[e] = Up[e - 1] * U;
-        Vp[e] = Vp[e - 1] * V;
-        Wp[e] = Wp[e - 1] * W;
-    }
-    // corr = sum_{n <= L} Q_n iR2^n, Horner in iR2 from n = L down
-    double corr = 0.0;
-    int base = IGF_FAR_NC;
-#pragma unroll
-    for (int n = 8; n >= 1; --n) {
-        const int nt = (n + 1) * (n + 2) / 2;
-        base -= nt;
-        if (n > L) continue;
-        double qn = 0.0;
-        int mi = 0;
-#pragma unroll
-        for (int i = n; i >= 0; --i)
-#pragma unroll
-            for (int j = n - i; j >= 0; --j, ++mi) qn = fma(c[base + mi], Up[i] * Vp[j] * Wp[n - i - j], qn);
-        corr = (corr + qn) * iR2;
-    }
+    const double i4 = iR2 * iR2;
+    const double sa = x.hi * x.hi * i4, sb = y.hi * y.hi * i4, sw = z.hi * z.hi * i4;
+    double corr;
+    if (rho2 > 1.0 / 256.0) corr = igf_far_series<8>(sa, sb, sw, c);
+    else if (rho2 > 1.0 / 1024.0) corr = igf_far_series<6>(sa, sb, sw, c);
+    else if (rho2 > 1.0 / 4096.0) corr = igf_far_series<5>(sa, sb, sw, c);
+    else if (rho2 > 1.0 / 65536.0) corr = igf_far_series<4>(sa, sb, sw, c);
+    else corr = igf_far_series<3>(sa, sb, sw, c);
     // 1/R: y0 = rsqrt(R2), y1 = y0 + y0 (1 - R2 y0^2)/2 with the residual in dd
     const double y0 = rsqrt(R2.hi);
     const dd t = dd_mul(R2, two_prod(y0, y0));
