@@ -91,6 +91,20 @@ def dist_env():
     return world, rank, local
 
 
+def aggregate_replicas(seconds: float, units: float, pg=None, device=None):
+    """Replicas (each rank tracks its own bunch, no data-path collective): the
+    slowest rank's time and all ranks' units, so value = units / seconds is
+    the whole job's throughput.  pg: torch.distributed (any backend) or None."""
+    if pg is None:
+        return float(seconds), float(units)
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    pg.all_reduce(u, op=pg.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -504,12 +518,10 @@ def run_ours(args, w):
     ms_prof = ep0.elapsed_time(ep1)
     prof = trk.profile_read()
     trk.profile(False)
+    ms, psteps = aggregate_replicas(ms, float(npart) * args.steps, pg, dev)
     if pg:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
         pg.barrier()
-    value = world * npart * args.steps / (ms * 1e-3)
+    value = psteps / (ms * 1e-3)
     launches_per_step = sum(v[1] for v in prof.values()) / k_prof
     launches = int(round(launches_per_step * args.steps))
     ms_per_kick_prof = ms_prof / k_prof
@@ -574,12 +586,9 @@ def run_ours(args, w):
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         trk2.sync()
-        if pg:
-            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s, e2e_units = aggregate_replicas(e2e_s, float(npart) * k_e2e, pg, dev)
         bunch_bytes = 6 * 8 * npart
-        e2e = {"value": world * npart * k_e2e / e2e_s, "unit": UNIT,
+        e2e = {"value": e2e_units / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": (bunch_bytes + k_e2e * 0) / k_e2e,
                "d2h_bytes_per_step": (bunch_bytes + k_e2e * 27 * 8) / k_e2e,
                "steps": k_e2e,
