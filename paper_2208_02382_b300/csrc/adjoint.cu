@@ -322,9 +322,10 @@ __global__ void k_adj_phibar(const long long *__restrict__ kbar, int nn, const i
                              const Box *box, const MapCoef *map, double *__restrict__ phibar) {
     const int q = nn + 2;
     const long long n3 = (long long)nn * nn * nn, q3 = (long long)q * q * q;
-    const double c0 = ldexp(map->kick_t / (2.0 * box->h[0]), -sexp[0]);
-    const double c1 = ldexp(map->kick_t / (2.0 * box->h[1]), -sexp[1]);
-    const double c2 = ldexp(map->kick_z / (2.0 * box->h[2]), -sexp[2]);
+    // the forward field's k/(2h), formed the same way (from 1/h)
+    const double c0 = ldexp(map->kick_t * (0.5 * box->inv_h[0]), -sexp[0]);
+    const double c1 = ldexp(map->kick_t * (0.5 * box->inv_h[1]), -sexp[1]);
+    const double c2 = ldexp(map->kick_z * (0.5 * box->inv_h[2]), -sexp[2]);
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < q3;
          idx += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(idx % q) - 1, j = (int)((idx / q) % q) - 1, l = (int)(idx / ((long long)q * q)) - 1;

@@ -398,9 +398,10 @@ __global__ void k_field(const double *__restrict__ phi, int nn, const Box *box, 
         kz = m.kick_z;
     }
     const int q = nn + 2;
-    const double cx = -kx / (2.0 * box->h[0]);
-    const double cy = -ky / (2.0 * box->h[1]);
-    const double cz = -kz / (2.0 * box->h[2]);
+    // -k/(2h) from the box's 1/h: products, not three FP64 divisions per thread
+    const double cx = -kx * (0.5 * box->inv_h[0]);
+    const double cy = -ky * (0.5 * box->inv_h[1]);
+    const double cz = -kz * (0.5 * box->inv_h[2]);
     const long long nodes = (long long)nn * nn * nn;
     double m0 = 0.0, m1 = 0.0, m2 = 0.0;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nodes;
