@@ -64,6 +64,17 @@ __device__ void igf_terms(dd x, dd y, dd z, int j, dd &at, dd &lg) {
 // i.e. |h|/2 <= R/8.
 __device__ __forceinline__ bool igf_is_far(double R2, double hsum2) { return R2 >= 16.0 * hsum2; }
 
+// The far test of cell (a, b, c), rounded step by step (no contraction) so
+// that the corner kernel (which skips corners no near cell reads) and the sum
+// kernel (which reads the corners of near cells) always agree.
+__device__ __forceinline__ bool igf_cell_is_far(int a, int b, int c, double hx, double hy, double hz,
+                                                double hsum2) {
+    const double xa = __dmul_rn((double)a, hx), yb = __dmul_rn((double)b, hy),
+                 zc = __dmul_rn((double)c, hz);
+    const double R2 = __dadd_rn(__dadd_rn(__dmul_rn(xa, xa), __dmul_rn(yb, yb)), __dmul_rn(zc, zc));
+    return igf_is_far(R2, hsum2);
+}
+
 // Near cells have index below 4|h|/h_d + 1 in dimension d (rounding slack).
 __device__ __forceinline__ int igf_near_extent(int n, double hd, double hsum2) {
     const double e = 4.0 * sqrt(hsum2) / hd;
@@ -97,15 +108,20 @@ __global__ void k_igf_corner(int n, double hx, double hy, double hz, double2 *__
         const int i = (int)(id % ci);
         const int jj = (int)((id / ci) % cj);
         const int k = (int)(id / ((long long)ci * cj));
-        dd at, lg;
-        igf_terms(two_prod(i - 0.5, hx), two_prod(jj - 0.5, hy), two_prod(k - 0.5, hz), j, at, lg);
+        // corner (i, jj, k) serves cells i-1..i, jj-1..jj, k-1..k; when the one
+        // nearest the origin is far, all are, and no near cell reads the corner
+        const bool need = live && !igf_cell_is_far(max(i - 1, 0), max(jj - 1, 0), max(k - 1, 0),
+                                                   hx, hy, hz, hsum2);
+        dd at = {0.0, 0.0}, lg = {0.0, 0.0};
+        if (need)
+            igf_terms(two_prod(i - 0.5, hx), two_prod(jj - 0.5, hy), two_prod(k - 0.5, hz), j, at, lg);
         // lane 0 of the group gathers the other lanes' terms
         const int g0 = threadIdx.x & ~3;
         const double a1h = __shfl_sync(0xffffffffu, at.hi, g0 + 1), a1l = __shfl_sync(0xffffffffu, at.lo, g0 + 1);
         const double a2h = __shfl_sync(0xffffffffu, at.hi, g0 + 2), a2l = __shfl_sync(0xffffffffu, at.lo, g0 + 2);
         const double l1h = __shfl_sync(0xffffffffu, lg.hi, g0 + 1), l1l = __shfl_sync(0xffffffffu, lg.lo, g0 + 1);
         const double l2h = __shfl_sync(0xffffffffu, lg.hi, g0 + 2), l2l = __shfl_sync(0xffffffffu, lg.lo, g0 + 2);
-        if (lane == 0 && live) {
+        if (lane == 0 && need) {
             // F = -z^2/2 atan(..) - y^2/2 atan(..) - x^2/2 atan(..) + yz ln + xz ln + xy ln
             dd f = dd_neg(at);
             f = dd_sub(f, dd{a1h, a1l});
@@ -237,8 +253,7 @@ __global__ void k_igf_sum(int n, double hx, double hy, double hz, const double2 
         int a = (int)(idx % q);
         int b = (int)((idx / q) % q);
         int c = (int)(idx / ((long long)q * q));
-        const double xa = a * hx, yb = b * hy, zc = c * hz;
-        if (igf_is_far(xa * xa + yb * yb + zc * zc, hsum2)) {
+        if (igf_cell_is_far(a, b, c, hx, hy, hz, hsum2)) {
             g[idx] = igf_far_cell(a, b, c, hx, hy, hz, hsum2, sc, qv);
             continue;
         }
