@@ -212,18 +212,22 @@ __device__ double igf_far_cell(int a, int b, int cc, double hx, double hy, doubl
                                double hsum2, const double *c, dd q) {
     const dd x = two_prod((double)a, hx), y = two_prod((double)b, hy), z = two_prod((double)cc, hz);
     const dd R2 = dd_add(dd_add(dd_mul(x, x), dd_mul(y, y)), dd_mul(z, z));
-    const double iR2 = 1.0 / R2.hi;
+    // 1/R^2 for the corrections from the same rsqrt as 1/R below (a few ulps:
+    // the corrections are at most 1/60 of G)
+    const double y0 = rsqrt(R2.hi);
+    const double iR2 = y0 * y0;
     const double rho2 = 0.25 * hsum2 * iR2;
     const double i4 = iR2 * iR2;
     const double sa = x.hi * x.hi * i4, sb = y.hi * y.hi * i4, sw = z.hi * z.hi * i4;
+    // series order from rho^2 > 0, compared as bit patterns (integer pipes)
+    const long long rb = __double_as_longlong(rho2);
     double corr;
-    if (rho2 > 1.0 / 256.0) corr = igf_far_series<8>(sa, sb, sw, c);
-    else if (rho2 > 1.0 / 1024.0) corr = igf_far_series<6>(sa, sb, sw, c);
-    else if (rho2 > 1.0 / 4096.0) corr = igf_far_series<5>(sa, sb, sw, c);
-    else if (rho2 > 1.0 / 65536.0) corr = igf_far_series<4>(sa, sb, sw, c);
+    if (rb > 0x3F70000000000000ll) corr = igf_far_series<8>(sa, sb, sw, c);        // 2^-8
+    else if (rb > 0x3F50000000000000ll) corr = igf_far_series<6>(sa, sb, sw, c);   // 2^-10
+    else if (rb > 0x3F30000000000000ll) corr = igf_far_series<5>(sa, sb, sw, c);   // 2^-12
+    else if (rb > 0x3EF0000000000000ll) corr = igf_far_series<4>(sa, sb, sw, c);   // 2^-16
     else corr = igf_far_series<3>(sa, sb, sw, c);
     // 1/R: y0 = rsqrt(R2), y1 = y0 + y0 (1 - R2 y0^2)/2 with the residual in dd
-    const double y0 = rsqrt(R2.hi);
     const dd t = dd_mul(R2, two_prod(y0, y0));
     const double e = __dsub_rn(1.0, t.hi) - t.lo;
     const dd iR = fast_two_sum(y0, 0.5 * y0 * e);
