@@ -194,6 +194,27 @@ def test_track_in_pieces_equals_one_call(bt):
     assert t1.regrid_log() == t2.regrid_log()
 
 
+def test_track_one_kick_per_call_matches_oracle(bt):
+    # every call after the first deposits its first kick in the prologue, into
+    # the box kept from the call before (the box rule re-deposits on a regrid);
+    # re-binning runs on the context's kick count across the calls
+    w = bg.workload("fodo_1e4_32")
+    c = w.particles(3_000)
+    sp = bt.Species(w.species.mass_MeV, w.species.kinetic_MeV, w.species.charge_sign)
+    beam = bt.Beam(torch.tensor(c, device=DEV), sp, w.bunch_charge_C)
+    trk = bt.Tracker(16)
+    trk.set_binning(4, 0)
+    nk = 24
+    for k in range(nk):
+        trk.track(beam, w.lattice, k, 1)
+    trk.sync()
+    ref = oracle_ref(w.species)
+    otr = tr.Tracker(ref, w.bunch_charge_C, 16)
+    want = otr.track(c, w.lattice, 0, nk)
+    assert coord_rel_err(to_np(beam), want) <= REL_TOL
+    assert trk.regrid_log() == otr.regrid_log
+
+
 @pytest.mark.parametrize("npart", [0, 1, 2, 3])
 def test_track_degenerate_bunches(bt, npart):
     """Empty bunch, a single particle (all extents zero, floored box) and
