@@ -77,6 +77,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-grad", action="store_true",
                    help="skip the gradient measurement (fodo8_grad_1e6_64)")
+    p.add_argument("--no-variants", action="store_true",
+                   help="skip the TSC / thin-multipole / per-slice-diagnostics measurements")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched-variants measurement (batch_256_fodo)")
     p.add_argument("--particles", type=int, default=None,
@@ -369,6 +371,91 @@ def grad_bench(dev, checkpoint_interval: int = 20, fd_params=(3, 9)):
                     "replayed"}
 
 
+def _kick_ms(trk, beam, lat, first, nk, **kw):
+    """Device time per kick of one tracking call (CUDA events on the stream)."""
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = trk.track(beam, lat, first, nk, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    trk.sync()
+    return e0.elapsed_time(e1) / nk, out
+
+
+def variants_bench(dev, kicks: int = 40):
+    """The variant rows on one GPU, each timed over `kicks` kicks after a warm-up
+    call: TSC (particle shape 2) on chicane_25e6_128 next to CIC on the same
+    kicks; the rectangular-bend chicane (thin dipole edges) and FODO cells with
+    thin multipoles (1e6 particles, 64^3); the paper's FODO benchmark (Listing
+    1: 1e4 Waterbag electrons, 2 GeV, 25 slices per element) with per-slice
+    diagnostics read back, against the same run without them."""
+    import torch
+    import paper_2208_02382_b300 as btk
+    out = {}
+    w = bg.workload("chicane_25e6_128")
+    c0 = torch.tensor(w.particles(), dtype=torch.float64, device=dev)
+    sp = btk.Species(w.species.mass_MeV, w.species.kinetic_MeV, w.species.charge_sign)
+    for name, shape in (("cic", 1), ("tsc", 2)):
+        trk = btk.Tracker(w.n_grid, shape_order=shape)
+        beam = btk.Beam(c0.clone(), sp, w.bunch_charge_C)
+        trk.track(beam, w.lattice, 0, 5)
+        ms, _ = _kick_ms(trk, beam, w.lattice, 5, kicks)
+        out[f"chicane_25e6_128_{name}"] = {"ms_per_step": ms,
+                                           "particle_steps_per_s": w.n_particles / (ms * 1e-3)}
+        trk.close()
+        del beam
+    # the chicane with rectangular bends: thin edges merged into the maps
+    trk = btk.Tracker(w.n_grid)
+    beam = btk.Beam(c0.clone(), sp, w.bunch_charge_C)
+    lat = bg.chicane_rect_lattice(50)
+    trk.track(beam, lat, 0, 5)
+    ms, _ = _kick_ms(trk, beam, lat, 5, kicks)
+    out["chicane_rect_25e6_128"] = {"ms_per_step": ms,
+                                    "particle_steps_per_s": w.n_particles / (ms * 1e-3)}
+    trk.close()
+    del beam, c0
+    torch.cuda.empty_cache()
+    # FODO cells with thin multipoles against the same cells without them
+    f = bg.workload("fodo_1e6_64")
+    c1 = torch.tensor(f.particles(), dtype=torch.float64, device=dev)
+    spf = btk.Species(f.species.mass_MeV, f.species.kinetic_MeV, f.species.charge_sign)
+    for name, lat in (("fodo_1e6_64", bg.fodo_lattice(10, 4)),
+                      ("fodo_multipole_1e6_64", bg.fodo_multipole_lattice(4, periods=10))):
+        trk = btk.Tracker(f.n_grid)
+        beam = btk.Beam(c1.clone(), spf, f.bunch_charge_C)
+        trk.track(beam, lat, 0, 5)
+        ms, _ = _kick_ms(trk, beam, lat, 5, kicks)
+        out[name] = {"ms_per_step": ms, "particle_steps_per_s": f.n_particles / (ms * 1e-3)}
+        trk.close()
+    del c1
+    torch.cuda.empty_cache()
+    # Listing 1: one FODO cell, 25 slices per element, with and without the
+    # per-slice moments
+    e2 = bg.ELECTRON_2GEV
+    spe = btk.Species(e2.mass_MeV, e2.kinetic_MeV, e2.charge_sign)
+    z = torch.tensor(bg.standard_normal6(10_000, seed=0), device=dev)
+    u = torch.tensor(bg.uniform01(10_000, seed=0), device=dev)
+    cell = bg.fodo_cell(25)
+    nk = bg.count_kicks(cell)
+    res = {}
+    for diag in (False, True):
+        trk = btk.Tracker(32)
+        beam = btk.Beam(btk.distribution_beam("waterbag", bg.LISTING1_WATERBAG, z, u), spe, 1e-9)
+        trk.track(beam, cell, 0, nk, diagnostics=diag)
+        trk.reset()
+        beam = btk.Beam(btk.distribution_beam("waterbag", bg.LISTING1_WATERBAG, z, u), spe, 1e-9)
+        ms, _ = _kick_ms(trk, beam, cell, 0, nk, diagnostics=diag)
+        res["with_diagnostics" if diag else "without"] = ms
+        trk.close()
+    out["listing1_fodo_1e4_32"] = {"ms_per_slice": res, "slices": nk}
+    out["what"] = ("ms per kick (one slice) over %d kicks after a warm-up call, CUDA events; "
+                   "the Listing-1 FODO cell from a fresh state, 125 slices, diagnostics = the "
+                   "27 moments at every slice end" % kicks)
+    return out
+
+
 def batch_bench(dev, count: int = 256, periods: int = 10, nslice: int = 4, seed: int = 0):
     """256 Listing-1 FODO variants (k_QF, k_QD within +-20%, 1e4..5e5 particles
     log-uniform, 32^3 or 64^3 grid, 1 GeV p, 10 nC, FODO x10 with 4 slices per
@@ -599,6 +686,9 @@ def run_ours(args, w):
     gradient = None
     if rank == 0 and not args.no_grad:
         gradient = grad_bench(dev)
+    variants = None
+    if rank == 0 and not args.no_variants:
+        variants = variants_bench(dev)
     batching = None
     if rank == 0 and not args.no_batch:
         batching = batch_bench(dev)
@@ -617,7 +707,7 @@ def run_ours(args, w):
                            "l2": f"inputs larger than L2 (particle SoA {npart * 48 / 1e9:.2f} GB)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gradient": gradient,
-                "batching": batching,
+                "batching": batching, "variants": variants,
                 "gpu_launches": launches, "clocks": clocks, "wall_s_timed": wall,
                 "profiled": {"steps": k_prof, "ms_per_step": ms_per_kick_prof,
                              "what": "same kernels launched one by one with CUDA events "
