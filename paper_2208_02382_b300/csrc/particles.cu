@@ -628,7 +628,6 @@ __global__ void __launch_bounds__(TPB, (SH == 1 && !(DEP && MK != MAP_NONE)) ? 4
                 const double u2 = EX ? (__dmul_rn(a.nbg, t) - lo2) * ih2 : fma(t, tz, o2);
                 long long comp[3];
                 if constexpr (SH == 2) {
-                    const long long sy = 4LL * nn, sz = 4LL * nn * nn;  // in int64 units (4 per node)
                     tsc_node(u0, nn, c0, G0, out0);
                     tsc_node(u1, nn, c1, G1, out0);
                     tsc_node(u2, nn, c2, G2, out0);
@@ -637,25 +636,37 @@ __global__ void __launch_bounds__(TPB, (SH == 1 && !(DEP && MK != MAP_NONE)) ? 4
                     tsc_weights(G0, wx);
                     tsc_weights(G1, wy);
                     tsc_weights(G2, wz);
-                    // separable: along x on the nine (y, z) lines, then y, then z
-                    const long long *e = &a.ef[((long long)(c2 - 1) * nn + (c1 - 1)) * nn + (c0 - 1)].x;
+                    // separable: along x on the nine (y, z) lines, then y, then z;
+                    // a node's x, y components in one 16-byte load, z in one 8-byte load
+                    const EFix *e = &a.ef[((long long)(c2 - 1) * nn + (c1 - 1)) * nn + (c0 - 1)];
+                    const long long ny = nn, nz = (long long)nn * nn;
+                    long long gz[3] = {0, 0, 0};
     #pragma unroll
-                    for (int cc = 0; cc < 3; ++cc) {
-                        long long gz = 0;
+                    for (int dz = 0; dz < 3; ++dz) {
+                        long long gy[3] = {0, 0, 0};
     #pragma unroll
-                        for (int dz = 0; dz < 3; ++dz) {
-                            long long gy = 0;
-    #pragma unroll
-                            for (int dy = 0; dy < 3; ++dy) {
-                                const long long *q = e + cc + dz * sz + dy * sy;
-                                const long long gx = mulfrac52(q[0], wx[0]) + mulfrac52(q[4], wx[1]) +
-                                                     mulfrac52(q[8], wx[2]);
-                                gy += mulfrac52(gx, wy[dy]);
-                            }
-                            gz += mulfrac52(gy, wz[dz]);
+                        for (int dy = 0; dy < 3; ++dy) {
+                            const EFix *q = e + dz * nz + dy * ny;
+                            const longlong2 p0 = __ldg((const longlong2 *)q),
+                                            p1 = __ldg((const longlong2 *)(q + 1)),
+                                            p2 = __ldg((const longlong2 *)(q + 2));
+                            const long long gxx = mulfrac52(p0.x, wx[0]) + mulfrac52(p1.x, wx[1]) +
+                                                  mulfrac52(p2.x, wx[2]);
+                            const long long gxy = mulfrac52(p0.y, wx[0]) + mulfrac52(p1.y, wx[1]) +
+                                                  mulfrac52(p2.y, wx[2]);
+                            const long long gxz = mulfrac52(__ldg(&q[0].z), wx[0]) +
+                                                  mulfrac52(__ldg(&q[1].z), wx[1]) +
+                                                  mulfrac52(__ldg(&q[2].z), wx[2]);
+                            gy[0] += mulfrac52(gxx, wy[dy]);
+                            gy[1] += mulfrac52(gxy, wy[dy]);
+                            gy[2] += mulfrac52(gxz, wy[dy]);
                         }
-                        comp[cc] = gz;
+    #pragma unroll
+                        for (int cc = 0; cc < 3; ++cc) gz[cc] += mulfrac52(gy[cc], wz[dz]);
                     }
+                    comp[0] = gz[0];
+                    comp[1] = gz[1];
+                    comp[2] = gz[2];
                 } else {
                     cell_frac(u0, nn, c0, G0, out0);
                     cell_frac(u1, nn, c1, G1, out0);
