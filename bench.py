@@ -37,28 +37,28 @@ UNIT = "particle-steps/s"
 FP64_PEAK_TFLOPS = 2 * 148 * 2.032e9 * 2 / 1e12
 
 
-def _fft_line_flops(m):
-    return 5.0 * m * math.log2(m)  # radix-2 complex FFT count
-
-
 # Algorithmic work per launch of each kernel kind for the roofline of the
 # dominant kernel: (bound, unit, f(n_particles, n_grid) -> amount per launch).
 #   gather_kick_push: read and write the six FP64 coordinates, 96 B/particle
 #   deposit:          read x, y, t, 24 B/particle
-#   fft_zsolve:       m (n+1) z-lines, forward + inverse transform and the
-#                     Green multiply (2 m flops) each
-#   fft_yz:           the forward (n (n+1) lines) or inverse ((n+2)(n+1))
-#                     y pass, counted as their mean
-#   fft_x / fft_xinv: n^2/2 and (n+2)^2/2 complex lines (two real rows each)
+# The tracking solve runs in int64 fixed point on the integer pipes; its
+# passes count the spectrum data they must read and write (16-byte complex
+# values, m = 2n, P = n+1):
+#   fft_x:      the accumulators (16 B/node) in, n^2 P values out
+#   fft_yz:     mean of the forward y pass (n^2 P in, n m P out) and the
+#               inverse y pass ((n+2) m P in, (n+2)^2 P out)
+#   fft_zsolve: n m P in, the quantised Green's octant (P^3 x 8 B), (n+2) m P out
+#   fft_xinv:   (n+2)^2 P in, phi on (n+2)^3 nodes (8 B) out
 ALGO = {
     "gather_kick_push": ("hbm", "GB/s", lambda npart, n: 96.0 * npart),
     "deposit": ("hbm", "GB/s", lambda npart, n: 24.0 * npart),
-    "fft_zsolve": ("alu", "TFLOP/s",
-                   lambda npart, n: (2 * n) * (n + 1) * (2 * _fft_line_flops(2 * n) + 4 * n)),
-    "fft_yz": ("alu", "TFLOP/s",
-               lambda npart, n: 0.5 * (n * (n + 1) + (n + 2) * (n + 1)) * _fft_line_flops(2 * n)),
-    "fft_x": ("alu", "TFLOP/s", lambda npart, n: n * n / 2 * _fft_line_flops(2 * n)),
-    "fft_xinv": ("alu", "TFLOP/s", lambda npart, n: (n + 2) ** 2 / 2 * _fft_line_flops(2 * n)),
+    "fft_zsolve": ("hbm", "GB/s", lambda npart, n: 16.0 * (n + 1) * 2 * n * (2 * n + 2)
+                   + 8.0 * (n + 1) ** 3),
+    "fft_yz": ("hbm", "GB/s", lambda npart, n: 0.5 * 16.0 * (n + 1) * (
+        n * n + 2 * n * n + (n + 2) * 2 * n + (n + 2) ** 2)),
+    "fft_x": ("hbm", "GB/s", lambda npart, n: 16.0 * n ** 3 + 16.0 * n * n * (n + 1)),
+    "fft_xinv": ("hbm", "GB/s", lambda npart, n: 16.0 * (n + 2) ** 2 * (n + 1)
+                 + 8.0 * (n + 2) ** 3),
 }
 KERNEL_SOURCES = {
     "gather_kick_push": "particles.cu", "deposit": "particles.cu",

@@ -51,7 +51,6 @@ int32_t bx_create(bx_ctx **out, const bx_options *opt) {
     A((void **)&ctx->acc_lo, n3 * 8);
     A((void **)&ctx->rho, n3 * 8);
     A((void **)&ctx->phi, q3 * 8);
-    A((void **)&ctx->efield, n3 * sizeof(Field4));
     A((void **)&ctx->fcorner, igf_scratch_doubles(n) * sizeof(double));
     A((void **)&ctx->gtable, o3 * 8);
     A((void **)&ctx->st, sizeof(TrackState));
@@ -83,7 +82,7 @@ int32_t bx_destroy(bx_ctx *ctx) {
     if (!ctx) return BX_OK;
     cudaDeviceSynchronize();
     grad_free(ctx);
-    void *ptrs[] = {ctx->acc_hi, ctx->acc_lo, ctx->rho, ctx->phi, ctx->efield, ctx->fcorner,
+    void *ptrs[] = {ctx->acc_hi, ctx->acc_lo, ctx->rho, ctx->phi, ctx->fcorner,
                     ctx->gtable, ctx->st, ctx->tmp_box, ctx->status, ctx->log,
                     ctx->mom_partial, ctx->maps, ctx->efix, ctx->emax, ctx->escale,
                     ctx->dev_ptrs, ctx->keys, ctx->counts, ctx->offs, ctx->sums, ctx->id_scr,
@@ -369,7 +368,7 @@ int32_t bx_gather_kick(bx_ctx *ctx, bx_beam *beam, const bx_grid *grid, double d
     CK(cudaMemcpyAsync(ctx->tmp_box, &b, sizeof(b), cudaMemcpyHostToDevice, s), "box");
     const double kt = r.sign * ds / (r.mass_eV * (r.bg * r.bg));
     const double kz = -r.sign * ds / (r.mass_eV * r.bg);
-    CK(launch_field(grid->phi, ctx->n, ctx->tmp_box, kt, kt, kz, ctx->efield, ctx->emax,
+    CK(launch_field(grid->phi, ctx->n, ctx->tmp_box, kt, kt, kz, ctx->emax,
                     ctx->efix, ctx->escale, s),
        "field");
     CK(launch_kick_push_deposit(beam->coord, beam->n, r.bg, ctx->tmp_box, b, ctx->n, ctx->efix,

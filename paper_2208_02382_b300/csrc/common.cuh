@@ -50,14 +50,10 @@ struct SplitRec {
 // table entries (MapCoef units) one SplitRec takes, appended after the entries
 constexpr int SPLIT_UNITS = (int)((sizeof(SplitRec) + sizeof(MapCoef) - 1) / sizeof(MapCoef));
 
-// Pre-scaled field at a node (momentum change per unit CIC weight), padded to
-// 32 bytes so that one node is one aligned 256-bit load.
-struct __align__(32) Field4 {
-    double x, y, z, w;
-};
-
-// The same field in int64 fixed point: E_fix = rint(E * 2^e_d) per component
-// (exponents kept separately), so the interpolation runs on the integer pipes.
+// Pre-scaled field at a node (momentum change per unit CIC weight) in int64
+// fixed point: E_fix = rint(E * 2^e_d) per component (exponents kept
+// separately), so the interpolation runs on the integer pipes; padded to 32
+// bytes so that a node's x, y components are one aligned 16-byte load.
 struct __align__(32) EFix {
     long long x, y, z, w;
 };
@@ -188,8 +184,8 @@ cudaError_t launch_kick_push_deposit(double *const c[6], int64_t n, double betag
 cudaError_t launch_box_rule(TrackState *st, int nn, int64_t n, long long *log, int64_t log_cap,
                             bool advance, cudaStream_t s);
 cudaError_t launch_field(const double *phi, int nn, const Box *box, double kx, double ky,
-                         double kz, double *efield, unsigned long long *emax, EFix *efix,
-                         int *escale, cudaStream_t s, const TrackState *st = nullptr,
+                         double kz, unsigned long long *emax, EFix *efix, int *escale,
+                         cudaStream_t s, const TrackState *st = nullptr,
                          const MapCoef *maps = nullptr);
 cudaError_t launch_call_init(TrackState *st, int nkicks, double q_macro, int sort_interval,
                              long long kick0, cudaStream_t s, double betagamma,
@@ -242,6 +238,13 @@ int moments_blocks(int64_t n);
 size_t moments_scratch_doubles(int nblocks);
 cudaError_t launch_moments_transform(double *mom, const MapCoef *map, cudaStream_t s);
 // fft.cu
+// Scales of the block-floating-point tracking solve (fft.cu), set with each
+// Green's spectrum: D >= max |G^| (the spectrum is stored as round(G^ 2^62 / D))
+// and the output factor D / m^3.
+struct FixScales {
+    double D, F;
+};
+
 struct FftPlan {
     int n;            // physical grid nodes per dim
     int m;            // doubled size 2n
@@ -249,6 +252,10 @@ struct FftPlan {
     double2 *buf2;
     double2 *tw;      // m twiddles exp(-2 pi i j/m)
     double *ghat;     // (n+1)^3 real even octant of the doubled Green's function spectrum
+    longlong2 *twq;   // the twiddles in Q63 (fixed-point solve)
+    long long *ghat_q;   // the spectrum octant as round(G^ 2^62 / D)
+    FixScales *fs;       // device
+    int *fexp;           // line exponents of the fixed-point passes
 };
 cudaError_t fft_plan_init(FftPlan *p, int n);
 void fft_plan_free(FftPlan *p);
@@ -256,6 +263,9 @@ cudaError_t solve_rho_to_phi(const FftPlan *p, const double *rho, double *phi, c
 cudaError_t solve_acc_to_phi(const FftPlan *p, const unsigned long long *acc_hi,
                              const unsigned long long *acc_lo, double scale, double *phi,
                              cudaStream_t s, const double *scale_dev = nullptr);
+cudaError_t solve_acc_to_phi_fixed(const FftPlan *p, const unsigned long long *acc_hi,
+                                   const unsigned long long *acc_lo, double scale, double *phi,
+                                   cudaStream_t s, const double *scale_dev);
 cudaError_t green_spectrum_from_table(const FftPlan *p, const double *gtable, cudaStream_t s,
                                       const int *gate = nullptr);
 cudaError_t solve_adjoint_shifted(const FftPlan *p, const double *phibar, double *out,

@@ -22,7 +22,7 @@ struct bx_ctx {
     int n = 0;
     FftPlan plan{};
     unsigned long long *acc_hi = nullptr, *acc_lo = nullptr;
-    double *rho = nullptr, *phi = nullptr, *efield = nullptr;
+    double *rho = nullptr, *phi = nullptr;
     double *fcorner = nullptr, *gtable = nullptr;
     TrackState *st = nullptr;      // device
     Box *tmp_box = nullptr;        // device scratch for explicit boxes

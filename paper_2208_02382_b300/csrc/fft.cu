@@ -23,6 +23,8 @@
 //    holds the line in registers, applies radix-4/8/16 DFT codelets with
 //    twiddles exp(-+2 pi i j/m) from a shared-memory table (built once with
 //    sincospi), and exchanges values through shared memory between radix steps.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace bt {
@@ -38,6 +40,23 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 w) {
 template <bool INV>
 __device__ __forceinline__ double2 rot90(double2 a) {
     return INV ? make_double2(-a.y, a.x) : make_double2(a.y, -a.x);
+}
+
+// int64 fixed-point complex values (the tracking solve): sums are exact, a
+// product by a constant or twiddle f in [-1, 1] (Q63: f 2^63) is
+// floor(a f / 2^63) from the high half of one 64x64-bit product (|a| < 2^62).
+__device__ __forceinline__ long long mulq(long long a, long long f) {
+    return __mul64hi((long long)((unsigned long long)a << 1), f);
+}
+__device__ __forceinline__ long long q63(double c) { return (long long)(c * 0x1p63); }  // |c| < 1
+__device__ __forceinline__ longlong2 cadd(longlong2 a, longlong2 b) { return make_longlong2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ longlong2 csub(longlong2 a, longlong2 b) { return make_longlong2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ longlong2 cmul(longlong2 a, longlong2 w) {
+    return make_longlong2(mulq(a.x, w.x) - mulq(a.y, w.y), mulq(a.x, w.y) + mulq(a.y, w.x));
+}
+template <bool INV>
+__device__ __forceinline__ longlong2 rot90(longlong2 a) {
+    return INV ? make_longlong2(-a.y, a.x) : make_longlong2(a.y, -a.x);
 }
 
 constexpr double RS2 = 0.70710678118654752440;   // sqrt(2)/2
@@ -78,18 +97,45 @@ __device__ __forceinline__ void bfly_st(double2 e, double2 o, double s, double t
     bfly_f(e, make_double2(fma(o.x, t, -o.y), fma(o.y, t, o.x)), s, lo, hi);
 }
 
+// The same butterflies on fixed-point values (the real factor f and t as
+// Q63 constants, folded at compile time).
+__device__ __forceinline__ void bfly_f(longlong2 e, longlong2 r, double f, longlong2 &lo, longlong2 &hi) {
+    const long long fq = q63(f);
+    const longlong2 fr = make_longlong2(mulq(r.x, fq), mulq(r.y, fq));
+    lo = cadd(e, fr);
+    hi = csub(e, fr);
+}
+template <bool INV>
+__device__ __forceinline__ void bfly_w8_1(longlong2 e, longlong2 o, longlong2 &lo, longlong2 &hi) {
+    const longlong2 r = INV ? make_longlong2(o.x - o.y, o.x + o.y) : make_longlong2(o.x + o.y, o.y - o.x);
+    bfly_f(e, r, RS2, lo, hi);
+}
+template <bool INV>
+__device__ __forceinline__ void bfly_w8_3(longlong2 e, longlong2 o, longlong2 &lo, longlong2 &hi) {
+    const longlong2 r = INV ? make_longlong2(-(o.x + o.y), o.x - o.y) : make_longlong2(o.y - o.x, -(o.x + o.y));
+    bfly_f(e, r, RS2, lo, hi);
+}
+__device__ __forceinline__ void bfly_ct(longlong2 e, longlong2 o, double c, double t, longlong2 &lo, longlong2 &hi) {
+    const long long tq = q63(t);
+    bfly_f(e, make_longlong2(o.x - mulq(o.y, tq), o.y + mulq(o.x, tq)), c, lo, hi);
+}
+__device__ __forceinline__ void bfly_st(longlong2 e, longlong2 o, double s, double t, longlong2 &lo, longlong2 &hi) {
+    const long long tq = q63(t);
+    bfly_f(e, make_longlong2(mulq(o.x, tq) - o.y, mulq(o.y, tq) + o.x), s, lo, hi);
+}
+
 // DFT-4 of (v0, v1, v2, v3); HALF: v2 = v3 = 0 (not read).
-template <bool INV, bool HALF>
-__device__ __forceinline__ void dft4(double2 *v) {
+template <bool INV, bool HALF, class C>
+__device__ __forceinline__ void dft4(C *v) {
     if constexpr (HALF) {
-        const double2 a = v[0], b = v[1], rb = rot90<INV>(b);
+        const C a = v[0], b = v[1], rb = rot90<INV>(b);
         v[0] = cadd(a, b);
         v[1] = cadd(a, rb);
         v[2] = csub(a, b);
         v[3] = csub(a, rb);
     } else {
-        double2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-        double2 t2 = cadd(v[1], v[3]), t3 = rot90<INV>(csub(v[1], v[3]));
+        C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        C t2 = cadd(v[1], v[3]), t3 = rot90<INV>(csub(v[1], v[3]));
         v[0] = cadd(t0, t2);
         v[2] = csub(t0, t2);
         v[1] = cadd(t1, t3);
@@ -98,15 +144,15 @@ __device__ __forceinline__ void dft4(double2 *v) {
 }
 
 // DFT-8; HALF: v4..v7 = 0 (not read).
-template <bool INV, bool HALF>
-__device__ __forceinline__ void dft8(double2 *v) {
-    double2 e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+template <bool INV, bool HALF, class C>
+__device__ __forceinline__ void dft8(C *v) {
+    C e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
     dft4<INV, HALF>(e);
     dft4<INV, HALF>(o);
     v[0] = cadd(e[0], o[0]);
     v[4] = csub(e[0], o[0]);
     bfly_w8_1<INV>(e[1], o[1], v[1], v[5]);
-    const double2 r2 = rot90<INV>(o[2]);
+    const C r2 = rot90<INV>(o[2]);
     v[2] = cadd(e[2], r2);
     v[6] = csub(e[2], r2);
     bfly_w8_3<INV>(e[3], o[3], v[3], v[7]);
@@ -115,9 +161,9 @@ __device__ __forceinline__ void dft8(double2 *v) {
 // DFT-16; HALF: v8..v15 = 0 (not read).  The twiddles exp(-+ 2 pi i q/16)
 // (sg = -1 forward, +1 inverse; S16 = sin(pi/8) = C16 T16) are written as
 // C16 (1 + i t) or sg C16 (t + i) with t = +-T16, as RS2 (+-1 +- i), or +-i.
-template <bool INV, bool HALF>
-__device__ __forceinline__ void dft16(double2 *v) {
-    double2 e[8], o[8];
+template <bool INV, bool HALF, class C>
+__device__ __forceinline__ void dft16(C *v) {
+    C e[8], o[8];
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
         e[m] = v[2 * m];
@@ -131,7 +177,7 @@ __device__ __forceinline__ void dft16(double2 *v) {
     bfly_ct(e[1], o[1], C16, sg * T16, v[1], v[9]);            // (C16, sg S16)
     bfly_w8_1<INV>(e[2], o[2], v[2], v[10]);
     bfly_st(e[3], o[3], sg * C16, sg * T16, v[3], v[11]);      // (S16, sg C16)
-    const double2 r4 = rot90<INV>(o[4]);
+    const C r4 = rot90<INV>(o[4]);
     v[4] = cadd(e[4], r4);
     v[12] = csub(e[4], r4);
     bfly_st(e[5], o[5], sg * C16, -sg * T16, v[5], v[13]);     // (-S16, sg C16)
@@ -139,8 +185,8 @@ __device__ __forceinline__ void dft16(double2 *v) {
     bfly_ct(e[7], o[7], -C16, -sg * T16, v[7], v[15]);         // (-C16, sg S16)
 }
 
-template <int R, bool INV, bool HALF = false>
-__device__ __forceinline__ void dft(double2 *v) {
+template <int R, bool INV, bool HALF = false, class C>
+__device__ __forceinline__ void dft(C *v) {
     if constexpr (R == 4) dft4<INV, HALF>(v);
     else if constexpr (R == 8) dft8<INV, HALF>(v);
     else dft16<INV, HALF>(v);
@@ -164,17 +210,17 @@ constexpr int FFT_TPB = 256;
 // elements u + m*(M/R), in v[j*R + m].  Twiddles W_{L R}^{k m} (k = u mod L)
 // are applied before the radix-R DFT; output q of unit u belongs at line
 // position (u-k)*R + q*L + k.
-template <int M, int R, int L, bool INV, bool HALF = false>
-__device__ __forceinline__ void step_regs(double2 *v, int t, const double2 *__restrict__ tw) {
+template <int M, int R, int L, bool INV, bool HALF = false, class C>
+__device__ __forceinline__ void step_regs(C *v, int t, const C *__restrict__ tw) {
     constexpr int T = Shape<M>::T, U = (M / R) / T;
 #pragma unroll
     for (int j = 0; j < U; ++j) {
-        double2 *x = v + j * R;
+        C *x = v + j * R;
         if constexpr (L > 1) {
             const int u = t + j * T, k = u % L;
 #pragma unroll
             for (int m = 1; m < R; ++m) {
-                double2 w = tw[(k * m) * (M / (L * R))];
+                C w = tw[(k * m) * (M / (L * R))];
                 if (INV) w.y = -w.y;
                 x[m] = cmul(x[m], w);
             }
@@ -183,8 +229,8 @@ __device__ __forceinline__ void step_regs(double2 *v, int t, const double2 *__re
     }
 }
 
-template <int M, int R, int L>
-__device__ __forceinline__ void store_step(const double2 *v, double2 *s, int t) {
+template <int M, int R, int L, class C>
+__device__ __forceinline__ void store_step(const C *v, C *s, int t) {
     constexpr int T = Shape<M>::T, U = (M / R) / T;
 #pragma unroll
     for (int j = 0; j < U; ++j) {
@@ -194,8 +240,8 @@ __device__ __forceinline__ void store_step(const double2 *v, double2 *s, int t) 
     }
 }
 
-template <int M, int R>
-__device__ __forceinline__ void load_step(double2 *v, const double2 *s, int t) {
+template <int M, int R, class C>
+__device__ __forceinline__ void load_step(C *v, const C *s, int t) {
     constexpr int T = Shape<M>::T, U = (M / R) / T;
 #pragma unroll
     for (int j = 0; j < U; ++j)
@@ -216,8 +262,8 @@ __device__ __forceinline__ int first_index(int t, int j, int m) {
 // line's upper half (elements M/2..M-1) is zero; these are exactly the inputs
 // m >= R0/2 of every first-step DFT (element u + m M/R0 with u < M/R0), which
 // the half codelets neither read nor add.
-template <int M, bool INV, bool HALF = false>
-__device__ __forceinline__ void line_fft(double2 *v, double2 *s, int t, const double2 *tw) {
+template <int M, bool INV, bool HALF = false, class C>
+__device__ __forceinline__ void line_fft(C *v, C *s, int t, const C *tw) {
     using SH = Shape<M>;
     constexpr int R0 = SH::R0, R1 = SH::R1, R2 = SH::R2;
     step_regs<M, R0, 1, INV, HALF>(v, t, tw);
@@ -237,8 +283,8 @@ __device__ __forceinline__ void line_fft(double2 *v, double2 *s, int t, const do
     __syncthreads();
 }
 
-template <int M>
-__device__ __forceinline__ void load_twiddles(double2 *stw, const double2 *__restrict__ tw) {
+template <int M, class C>
+__device__ __forceinline__ void load_twiddles(C *stw, const C *__restrict__ tw) {
     for (int i = threadIdx.x; i < M; i += blockDim.x) stw[i] = tw[i];
 }
 
@@ -457,6 +503,354 @@ __global__ void k_twiddle(double2 *tw, int m) {
     }
 }
 
+// ------------------------------------------------ fixed-point tracking solve
+//
+// The same passes in block floating point on int64 values, for the tracking
+// solve from the deposit accumulators: on this GPU the integer pipes issue
+// tens of times more operations per clock than the FP64 pipe.  Every line
+// transform carries one exponent E (a stored value v means v 2^E):
+//  * on input, a pass aligns its line's elements to the largest exponent
+//    among them (rounded right shifts), then shifts the whole line so that
+//    the sum of the moduli of its elements, L1, is in (2^59, 2^60];
+//  * every intermediate value of a line transform is a sum of its inputs
+//    times unit-modulus factors, each input at most once, so it stays below
+//    L1 <= 2^60 (sums of a real and an imaginary part below 2^61; products by
+//    Q63 constants and twiddles floor(a f 2^-63) need |a| < 2^62);
+//  * the line's result keeps the line's exponent (x pass: per row pair;
+//    forward y: per (z, kx); z solve: per (ky, kx); inverse y: per (zz, kx)),
+//    so each value has the precision of its line, as in floating point with
+//    one exponent per line;
+//  * the z solve multiplies by the Green's spectrum as round(G^ 2^62 / D),
+//    D >= max |G^| (G > 0: max |G^| = G^(0)), then renormalises the line;
+//  * phi = value 2^E scale_acc 2^-51 D / m^3.
+
+constexpr int FIX_EMPTY = -100000;   // exponent of an all-zero line (aligns below any other)
+
+__device__ __forceinline__ long long rshr(long long v, int sh) {
+    if (sh <= 0) return v;
+    if (sh >= 63) return 0;
+    return (v + (1ll << (sh - 1))) >> sh;
+}
+// v 2^-sh (rounded for sh > 0, exact for sh <= 0 given the L1 bound)
+__device__ __forceinline__ longlong2 scale2n(longlong2 v, int sh) {
+    if (sh >= 0) return make_longlong2(rshr(v.x, sh), rshr(v.y, sh));
+    return make_longlong2((long long)((unsigned long long)v.x << (-sh)),
+                          (long long)((unsigned long long)v.y << (-sh)));
+}
+__device__ __forceinline__ unsigned long long l1_part(longlong2 v) {
+    const unsigned long long ax = (unsigned long long)(v.x < 0 ? -v.x : v.x);
+    const unsigned long long ay = (unsigned long long)(v.y < 0 ? -v.y : v.y);
+    return ((ax + ay) >> 16) + 1;   // an upper bound of |v| / 2^16, no overflow over a line
+}
+
+// Reductions over the T threads of a line team (teams are T consecutive
+// lanes; a 64-thread team spans two warps and exchanges through `red`, two
+// words per team).  Every thread of the block calls them.
+template <int T>
+__device__ __forceinline__ long long team_max(long long v, long long *red) {
+    constexpr int W = T < 32 ? T : 32;
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if constexpr (T > 32) {
+        const int team = threadIdx.x / T, half = (threadIdx.x % T) / 32;
+        if ((threadIdx.x & 31) == 0) red[2 * team + half] = v;
+        __syncthreads();
+        v = max(red[2 * team], red[2 * team + 1]);
+        __syncthreads();
+    }
+    return v;
+}
+template <int T>
+__device__ __forceinline__ unsigned long long team_sum(unsigned long long v, long long *red) {
+    constexpr int W = T < 32 ? T : 32;
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if constexpr (T > 32) {
+        const int team = threadIdx.x / T, half = (threadIdx.x % T) / 32;
+        if ((threadIdx.x & 31) == 0) red[2 * team + half] = (long long)v;
+        __syncthreads();
+        v = (unsigned long long)red[2 * team] + (unsigned long long)red[2 * team + 1];
+        __syncthreads();
+    }
+    return v;
+}
+
+// Normalisation shift of a line from its L1 bound (in units of 2^16): the
+// line times 2^-t has L1 in (2^59, 2^60] (t < 0 shifts left); 0 for an
+// all-zero line.
+__device__ __forceinline__ int norm_shift(unsigned long long l1_16) {
+    if (l1_16 == 0) return 0;
+    const int bits = 64 - __clzll((long long)l1_16) + 16;   // L1 < 2^bits
+    return bits - 60;
+}
+
+// Aligns the V values of a thread (exponents ev, FIX_EMPTY for zeros) to the
+// team's largest exponent, normalises the line and returns its exponent.
+template <int M, int V>
+__device__ __forceinline__ int align_line(longlong2 *v, const int *ev, long long *red) {
+    constexpr int T = Shape<M>::T;
+    int emax = FIX_EMPTY;
+#pragma unroll
+    for (int i = 0; i < V; ++i) emax = max(emax, ev[i]);
+    emax = (int)team_max<T>(emax, red);
+    unsigned long long l1 = 0;
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        v[i] = scale2n(v[i], emax - ev[i]);
+        l1 += l1_part(v[i]) - 1 + ((v[i].x | v[i].y) != 0);
+    }
+    l1 = team_sum<T>(l1, red);
+    const int t = norm_shift(l1);
+#pragma unroll
+    for (int i = 0; i < V; ++i) v[i] = scale2n(v[i], t);
+    return l1 ? emax + t : FIX_EMPTY;
+}
+
+// accumulator value (hi 2^31 + lo, 2^51 per particle)
+__device__ __forceinline__ unsigned __int128 acc_value(const unsigned long long *__restrict__ hi,
+                                                       const unsigned long long *__restrict__ lo,
+                                                       long long i) {
+    return ((unsigned __int128)hi[i] << DEP_SPLIT) + lo[i];
+}
+__device__ __forceinline__ int bitlen128(unsigned __int128 v) {
+    const unsigned long long h = (unsigned long long)(v >> 64), l = (unsigned long long)v;
+    return h ? 128 - __clzll((long long)h) : (l ? 64 - __clzll((long long)l) : 0);
+}
+__device__ __forceinline__ long long shift128(unsigned __int128 v, int t) {
+    if (t <= 0) return (long long)(v << (-t));
+    return (long long)((v + ((unsigned __int128)1 << (t - 1))) >> t);
+}
+
+// forward x pass from the accumulators (rows in pairs, as k_fft_x_fwd):
+// out[(z*n + y)*P + k], P = n+1; the pair's exponent in e1[z*n + y], e1[z*n + y + 1].
+// The pair is normalised by its largest value: L1 < m 2^bits(max).
+template <int M>
+__global__ void __launch_bounds__(FFT_TPB) k_fftq_x_fwd(const unsigned long long *__restrict__ acc_hi,
+                                                        const unsigned long long *__restrict__ acc_lo,
+                                                        int n, const longlong2 *__restrict__ tw,
+                                                        longlong2 *__restrict__ out,
+                                                        int *__restrict__ e1) {
+    constexpr int T = Shape<M>::T, LPB = FFT_TPB / T, V = M / T;
+    extern __shared__ longlong2 smq[];
+    __shared__ long long red[2 * LPB];
+    longlong2 *stw = smq, *sl = smq + M;
+    load_twiddles<M>(stw, tw);
+    const int team = threadIdx.x / T, t = threadIdx.x % T;
+    const long long pairs = (long long)(n / 2) * n;
+    const long long pr = (long long)blockIdx.x * LPB + team;
+    const bool live = pr < pairs;
+    const int z = live ? (int)(pr / (n / 2)) : 0, y = live ? (int)(pr % (n / 2)) * 2 : 0;
+    __syncthreads();
+    constexpr int R0 = Shape<M>::R0, U0 = (M / R0) / T;
+    const long long row = ((long long)z * n + y) * n;
+    unsigned __int128 va[V], vb[V];
+    int mb = 0;
+#pragma unroll
+    for (int j = 0; j < U0; ++j)
+#pragma unroll
+        for (int m = 0; m < R0; ++m) {
+            const int e = first_index<M>(t, j, m), i = j * R0 + m;
+            va[i] = (live && e < n) ? acc_value(acc_hi, acc_lo, row + e) : 0;
+            vb[i] = (live && e < n) ? acc_value(acc_hi, acc_lo, row + n + e) : 0;
+            mb = max(mb, max(bitlen128(va[i]), bitlen128(vb[i])));
+        }
+    mb = (int)team_max<T>(mb, red);
+    constexpr int LGM = M == 16 ? 4 : M == 32 ? 5 : M == 64 ? 6 : M == 128 ? 7 : M == 256 ? 8 : 9;
+    const int sh = mb + LGM - 60;
+    longlong2 v[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) v[i] = make_longlong2(shift128(va[i], sh), shift128(vb[i], sh));
+    longlong2 *s = sl + team * M;
+    line_fft<M, false, true>(v, s, t, stw);  // rows x < M/2
+    if (!live) return;
+    const int P = n + 1;
+    longlong2 *oa = out + ((long long)z * n + y) * P, *ob = oa + P;
+    for (int k = t; k <= n; k += T) {
+        const longlong2 zk = s[k], zc = s[(M - k) & (M - 1)];
+        oa[k] = make_longlong2((zk.x + zc.x) >> 1, (zk.y - zc.y) >> 1);
+        ob[k] = make_longlong2((zk.y + zc.y) >> 1, (zc.x - zk.x) >> 1);
+    }
+    if (t == 0) e1[(long long)z * n + y] = e1[(long long)z * n + y + 1] = mb ? sh : FIX_EMPTY;
+}
+
+// Strided line passes as k_fft_lines (MODE_FWD: forward y; MODE_ZSOLVE:
+// forward z, times the quantised Green's spectrum, inverse z; MODE_INV:
+// inverse y).  Element e of line (o, kx) has exponent
+// ein[o*ein_o + e*ein_e + kx*ein_k]; the line's exponent goes to eout[o*P + kx].
+template <int M, int MODE>
+__global__ void __launch_bounds__(FFT_TPB) k_fftq_lines(const longlong2 *__restrict__ in,
+                                                        long long in_o, long long in_e, int ne_in,
+                                                        const int *__restrict__ ein, long long ein_o,
+                                                        long long ein_e, long long ein_k,
+                                                        longlong2 *__restrict__ out,
+                                                        long long out_o, long long out_e, int nw,
+                                                        int *__restrict__ eout,
+                                                        int no, int P,
+                                                        const long long *__restrict__ gq,
+                                                        const longlong2 *__restrict__ tw) {
+    constexpr int T = Shape<M>::T, LPB = FFT_TPB / T, V = M / T;
+    constexpr bool INV1 = MODE == MODE_INV;
+    extern __shared__ longlong2 smq[];
+    __shared__ long long red[2 * LPB];
+    longlong2 *stw = smq, *sl = smq + M;
+    load_twiddles<M>(stw, tw);
+    const int team = threadIdx.x / T, t = threadIdx.x % T;
+    const long long line = (long long)blockIdx.x * LPB + team;
+    const bool live = line < (long long)no * P;
+    const int o = live ? (int)(line / P) : 0, kx = live ? (int)(line % P) : 0;
+    __syncthreads();
+    longlong2 v[V];
+    int ev[V];
+    constexpr int R0 = Shape<M>::R0, U0 = (M / R0) / T;
+    const longlong2 *src = in + o * in_o + kx;
+    const int *esrc = ein + o * ein_o + kx * ein_k;
+#pragma unroll
+    for (int j = 0; j < U0; ++j)
+#pragma unroll
+        for (int m = 0; m < R0; ++m) {
+            const int e = first_index<M>(t, j, m), i = j * R0 + m;
+            const bool ok = live && e < ne_in;
+            v[i] = ok ? src[e * in_e] : make_longlong2(0, 0);
+            ev[i] = ok ? esrc[e * ein_e] : FIX_EMPTY;
+        }
+    int E = align_line<M, V>(v, ev, red);
+    longlong2 *s = sl + team * M;
+    if ((MODE == MODE_FWD || MODE == MODE_ZSOLVE) && 2 * ne_in == M) line_fft<M, INV1, true>(v, s, t, stw);
+    else line_fft<M, INV1>(v, s, t, stw);
+    if constexpr (MODE == MODE_ZSOLVE) {
+        const int b = min(o, M - o);
+        for (int e = t; e < M; e += T) {
+            const int c = min(e, M - e);
+            const long long g = live ? gq[((long long)c * P + b) * P + kx] : 0;
+            const longlong2 a = s[e];
+            // floor(a g 2^-62), |a| <= 2^60
+            s[e] = make_longlong2(__mul64hi((long long)((unsigned long long)a.x << 2), g),
+                                  __mul64hi((long long)((unsigned long long)a.y << 2), g));
+        }
+        __syncthreads();
+        load_step<M, R0>(v, s, t);
+        __syncthreads();
+        // renormalise the product line (all elements share exponent E)
+#pragma unroll
+        for (int i = 0; i < V; ++i) ev[i] = E;
+        E = align_line<M, V>(v, ev, red);
+        line_fft<M, true>(v, s, t, stw);
+    }
+    if (live && t == 0) eout[(long long)o * P + kx] = E;
+    if (!live) return;
+    longlong2 *dst = out + o * out_o + kx;
+    if constexpr (MODE == MODE_FWD) {
+        for (int e = t; e < nw; e += T) dst[e * out_e] = s[e];
+    } else {
+        for (int w = t; w < nw; w += T) dst[w * out_e] = s[(w + M - 1) & (M - 1)];
+    }
+}
+
+// inverse x pass (complex to real, as k_fft_x_inv); element kx of rows
+// (zz, yy), (zz, yy+1) has exponent e4[zz*P + kx]; writes phi[(zz*q + yy)*q + w]
+// = value 2^E scale_dev-or-scale 2^-51 D / m^3, nodes -1..n.
+template <int M>
+__global__ void __launch_bounds__(FFT_TPB) k_fftq_x_inv(const longlong2 *__restrict__ in, int n,
+                                                        const int *__restrict__ e4,
+                                                        const FixScales *__restrict__ fs,
+                                                        double scale, const double *scale_dev,
+                                                        const longlong2 *__restrict__ tw,
+                                                        double *__restrict__ phi) {
+    constexpr int T = Shape<M>::T, LPB = FFT_TPB / T, V = M / T;
+    extern __shared__ longlong2 smq[];
+    __shared__ long long red[2 * LPB];
+    longlong2 *stw = smq, *sl = smq + M;
+    load_twiddles<M>(stw, tw);
+    const int q = n + 2, P = n + 1, team = threadIdx.x / T, t = threadIdx.x % T;
+    const long long pairs = (long long)q * (q / 2);
+    const long long pr = (long long)blockIdx.x * LPB + team;
+    const bool live = pr < pairs;
+    const int zz = live ? (int)(pr / (q / 2)) : 0, yy = live ? (int)(pr % (q / 2)) * 2 : 0;
+    __syncthreads();
+    const longlong2 *ra = in + ((long long)zz * q + yy) * P, *rb = ra + P;
+    const int *er = e4 + (long long)zz * P;
+    longlong2 v[V];
+    int ev[V];
+    constexpr int R0 = Shape<M>::R0, U0 = (M / R0) / T;
+    // exponents first: the packed value A + iB of element e comes from kx = e or m - e
+    int emax = FIX_EMPTY;
+#pragma unroll
+    for (int j = 0; j < U0; ++j)
+#pragma unroll
+        for (int m = 0; m < R0; ++m) {
+            const int e = first_index<M>(t, j, m), i = j * R0 + m;
+            const int k = e <= n ? e : M - e;
+            ev[i] = live ? er[k] : FIX_EMPTY;
+            emax = max(emax, ev[i]);
+        }
+    emax = (int)team_max<T>(emax, red);
+#pragma unroll
+    for (int j = 0; j < U0; ++j)
+#pragma unroll
+        for (int m = 0; m < R0; ++m) {
+            const int e = first_index<M>(t, j, m), i = j * R0 + m;
+            longlong2 z = make_longlong2(0, 0);
+            if (live) {
+                const int d = emax - ev[i];
+                if (e <= n) {
+                    const longlong2 a = scale2n(ra[e], d), b = scale2n(rb[e], d);
+                    z = make_longlong2(a.x - b.y, a.y + b.x);
+                } else {
+                    const longlong2 a = scale2n(ra[M - e], d), b = scale2n(rb[M - e], d);
+                    z = make_longlong2(a.x + b.y, b.x - a.y);
+                }
+            }
+            v[i] = z;
+            ev[i] = emax;
+        }
+    // |A + iB| <= |A| + |B| <= 2^61.x: renormalise (now all at exponent emax)
+    const int E = align_line<M, V>(v, ev, red);
+    longlong2 *s = sl + team * M;
+    line_fft<M, true>(v, s, t, stw);
+    if (!live) return;
+    const double sc = (scale_dev ? *scale_dev : scale) * fs->F * ldexp(1.0, E - 51);
+    double *pa = phi + ((long long)zz * q + yy) * q, *pb = pa + q;
+    for (int w = t; w < q; w += T) {
+        const longlong2 z = s[(w + M - 1) & (M - 1)];
+        pa[w] = (double)z.x * sc;
+        pb[w] = (double)z.y * sc;
+    }
+}
+
+// Twiddles exp(-2 pi i j/m) in Q63 (1 as 2^63 - 1).
+__global__ void k_twiddle_q(longlong2 *tw, int m) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) {
+        double s, c;
+        sincospi(2.0 * j / m, &s, &c);
+        auto q = [](double v) {
+            return v >= 1.0 ? 0x7FFFFFFFFFFFFFFFll : v <= -1.0 ? -0x7FFFFFFFFFFFFFFFll
+                                                               : __double2ll_rn(v * 0x1p63);
+        };
+        tw[j] = make_longlong2(q(c), q(-s));
+    }
+}
+
+// round(G^ 2^62 / D) on the spectrum octant, D = G^(0) (1 + 1e-9) >= max |G^|
+// (G > 0); fs = {D, D / m^3}.  No usable spectrum: a zero spectrum, phi NaN.
+__global__ void k_green_quant(const double *__restrict__ gh, long long cnt, int M,
+                              FixScales *__restrict__ fs, long long *__restrict__ gq,
+                              const int *gate) {
+    if (gate && *gate == 0) return;
+    const double g0 = gh[0];
+    const bool ok = g0 > 0.0 && isfinite(g0);
+    const double D = ok ? g0 * (1.0 + 1e-9) : 0.0, inv = ok ? 0x1p62 / D : 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        fs->D = D;
+        fs->F = ok ? D / ((double)M * M * M) : __longlong_as_double(0x7FF8000000000000ll);
+    }
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < cnt;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double r = fmin(fmax(gh[i] * inv, -0x1p62), 0x1p62);
+        gq[i] = ok ? __double2ll_rn(r) : 0;
+    }
+}
+
 // ------------------------------------------------------------------ driver
 
 static int team_size(int M) { return M == 512 ? 64 : M == 256 ? 16 : M >= 64 ? 8 : 4; }
@@ -477,6 +871,11 @@ static void set_attrs() {
     cudaFuncSetAttribute(k_fft_lines<M, MODE_GREEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_fft_lines<M, MODE_FWD_EVEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_fft_x_inv<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_fftq_x_fwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_fftq_lines<M, MODE_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_fftq_lines<M, MODE_ZSOLVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_fftq_lines<M, MODE_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_fftq_x_inv<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 cudaError_t fft_plan_init(FftPlan *p, int n) {
@@ -484,12 +883,22 @@ cudaError_t fft_plan_init(FftPlan *p, int n) {
     p->m = 2 * n;
     p->buf = p->buf2 = p->tw = nullptr;
     p->ghat = nullptr;
+    p->twq = nullptr;
+    p->ghat_q = nullptr;
+    p->fs = nullptr;
+    p->fexp = nullptr;
     const long long m = p->m, P = n + 1;
     const long long big = m * m * P;  // largest spectrum (the Green's x pass output)
     cudaError_t e = cudaMalloc(&p->buf, big * sizeof(double2));
     if (e == cudaSuccess) e = cudaMalloc(&p->buf2, big * sizeof(double2));
     if (e == cudaSuccess) e = cudaMalloc(&p->tw, m * sizeof(double2));
     if (e == cudaSuccess) e = cudaMalloc(&p->ghat, P * P * P * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&p->twq, m * sizeof(longlong2));
+    if (e == cudaSuccess) e = cudaMalloc(&p->ghat_q, P * P * P * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&p->fs, sizeof(FixScales));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&p->fexp, ((long long)n * n + n * P + m * P + (n + 2) * P) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->fs, 0, sizeof(FixScales));
     if (e != cudaSuccess) {
         fft_plan_free(p);
         return e;
@@ -504,6 +913,7 @@ cudaError_t fft_plan_init(FftPlan *p, int n) {
         default: return cudaErrorInvalidValue;
     }
     BT_LAUNCH(K_TWIDDLE, (cudaStream_t)0, k_twiddle<<<(p->m + 255) / 256, 256>>>(p->tw, p->m));
+    BT_LAUNCH(K_TWIDDLE, (cudaStream_t)0, k_twiddle_q<<<(p->m + 255) / 256, 256>>>(p->twq, p->m));
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     return e;
@@ -514,8 +924,16 @@ void fft_plan_free(FftPlan *p) {
     if (p->buf2) cudaFree(p->buf2);
     if (p->tw) cudaFree(p->tw);
     if (p->ghat) cudaFree(p->ghat);
+    if (p->twq) cudaFree(p->twq);
+    if (p->ghat_q) cudaFree(p->ghat_q);
+    if (p->fs) cudaFree(p->fs);
+    if (p->fexp) cudaFree(p->fexp);
     p->buf = p->buf2 = p->tw = nullptr;
     p->ghat = nullptr;
+    p->twq = nullptr;
+    p->ghat_q = nullptr;
+    p->fs = nullptr;
+    p->fexp = nullptr;
 }
 
 static inline unsigned blocks_lines(long long lines, int M) {
@@ -560,6 +978,38 @@ static cudaError_t solve_m(const FftPlan *p, const XIn &in, int src, int nin, do
     return cudaGetLastError();
 }
 
+// The tracking solve in block floating point (passes and layouts as solve_m
+// with the accumulators as the source); line exponents in p->fexp:
+// e1[z][y] (n^2), e2[z][kx] (n P), e3[ky][kx] (m P), e4[zz][kx] ((n+2) P).
+template <int M>
+static cudaError_t solve_fix_m(const FftPlan *p, const unsigned long long *acc_hi,
+                              const unsigned long long *acc_lo, double scale,
+                              const double *scale_dev, double *phi, cudaStream_t s) {
+    const int n = p->n;
+    const long long P = n + 1, q = n + 2;
+    const size_t sm = smem_bytes(M);
+    longlong2 *S1 = (longlong2 *)p->buf, *S2 = (longlong2 *)p->buf2, *S3 = S1, *S4 = S2;
+    int *e1 = p->fexp, *e2 = e1 + (long long)n * n, *e3 = e2 + n * P, *e4 = e3 + M * P;
+    BT_LAUNCH(K_FFT_X, s, k_fftq_x_fwd<M><<<blocks_lines((long long)(n / 2) * n, M), FFT_TPB, sm, s>>>(
+                              acc_hi, acc_lo, n, p->twq, S1, e1));
+    // y: lines (z, kx), element y with exponent e1[z][y]
+    BT_LAUNCH(K_FFT_YZ, s, k_fftq_lines<M, MODE_FWD><<<blocks_lines(n * P, M), FFT_TPB, sm, s>>>(
+                               S1, n * P, P, n, e1, n, 1, 0, S2, M * P, P, M, e2, n, (int)P,
+                               nullptr, p->twq));
+    // z: lines (ky, kx), element z with exponent e2[z][kx]
+    BT_LAUNCH(K_FFT_ZSOLVE, s,
+              k_fftq_lines<M, MODE_ZSOLVE><<<blocks_lines((long long)M * P, M), FFT_TPB, sm, s>>>(
+                  S2, P, (long long)M * P, n, e2, 0, P, 1, S3, P, (long long)M * P, (int)q, e3, M,
+                  (int)P, p->ghat_q, p->twq));
+    // inverse y: lines (zz, kx), element ky with exponent e3[ky][kx]
+    BT_LAUNCH(K_FFT_YZ, s, k_fftq_lines<M, MODE_INV><<<blocks_lines(q * P, M), FFT_TPB, sm, s>>>(
+                               S3, (long long)M * P, P, M, e3, 0, P, 1, S4, q * P, P, (int)q, e4,
+                               (int)q, (int)P, nullptr, p->twq));
+    BT_LAUNCH(K_FFT_XINV, s, k_fftq_x_inv<M><<<blocks_lines(q * (q / 2), M), FFT_TPB, sm, s>>>(
+                                 S4, n, e4, p->fs, scale, scale_dev, p->twq, phi));
+    return cudaGetLastError();
+}
+
 // Spectrum of the doubled Green's function from its octant table.  The doubled
 // G is even in every dimension, so each pass only transforms the lines whose
 // outer indices lie in the first half (0..n) and reads mirrored inputs:
@@ -582,6 +1032,10 @@ static cudaError_t green_m(const FftPlan *p, const double *gtable, cudaStream_t 
     BT_LAUNCH(K_GREEN_YZ, s, k_fft_lines<M, MODE_GREEN><<<blocks_lines(P * P, M), FFT_TPB, sm, s>>>(
                                  p->buf2, P, P * P, (int)P, nullptr, 0, 0, 0, (int)P, (int)P, nullptr,
                                  p->ghat, p->tw, gate));
+    // the block-floating-point solve's quantised spectrum
+    const long long cnt = P * P * P;
+    const unsigned qb = (unsigned)std::min<long long>((cnt + 255) / 256, 148 * 8);
+    BT_LAUNCH(K_GREEN_YZ, s, k_green_quant<<<qb, 256, 0, s>>>(p->ghat, cnt, M, p->fs, p->ghat_q, gate));
     return cudaGetLastError();
 }
 
@@ -624,6 +1078,20 @@ cudaError_t solve_acc_to_phi(const FftPlan *p, const unsigned long long *acc_hi,
     in.scale = scale;
     in.scale_ptr = scale_dev;
     return solve_any(p, in, SRC_ACC, p->n, phi, s);
+}
+
+cudaError_t solve_acc_to_phi_fixed(const FftPlan *p, const unsigned long long *acc_hi,
+                                   const unsigned long long *acc_lo, double scale, double *phi,
+                                   cudaStream_t s, const double *scale_dev) {
+    switch (p->m) {
+        case 16: return solve_fix_m<16>(p, acc_hi, acc_lo, scale, scale_dev, phi, s);
+        case 32: return solve_fix_m<32>(p, acc_hi, acc_lo, scale, scale_dev, phi, s);
+        case 64: return solve_fix_m<64>(p, acc_hi, acc_lo, scale, scale_dev, phi, s);
+        case 128: return solve_fix_m<128>(p, acc_hi, acc_lo, scale, scale_dev, phi, s);
+        case 256: return solve_fix_m<256>(p, acc_hi, acc_lo, scale, scale_dev, phi, s);
+        case 512: return solve_fix_m<512>(p, acc_hi, acc_lo, scale, scale_dev, phi, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t green_spectrum_from_table(const FftPlan *p, const double *gtable, cudaStream_t s,

@@ -177,7 +177,7 @@ static cudaError_t grad_kick(bx_ctx *ctx, double *const cin[6], double *const co
         e = solve_acc_to_phi(&ctx->plan, ctx->acc_hi, ctx->acc_lo, 0.0, ctx->phi, s,
                              &ctx->st->rho_scale);
     if (e == cudaSuccess)
-        e = launch_field(ctx->phi, ctx->n, &ctx->st->box, 0.0, 0.0, 0.0, ctx->efield, ctx->emax,
+        e = launch_field(ctx->phi, ctx->n, &ctx->st->box, 0.0, 0.0, 0.0, ctx->emax,
                          efix, escale, s, ctx->st, ctx->maps);
     if (e == cudaSuccess)
         e = launch_track_particles_oop(cin, cout, np, bg, &ctx->st->box, ctx->n, efix, escale,

@@ -40,10 +40,10 @@ cudaError_t kick_deposit(const KickArgs &k, cudaStream_t s) {
 
 cudaError_t kick_solve_field_push(const KickArgs &k, cudaStream_t s) {
     bx_ctx *ctx = k.ctx;
-    cudaError_t e = solve_acc_to_phi(&ctx->plan, ctx->acc_hi, ctx->acc_lo, 0.0, ctx->phi, s,
-                                     &ctx->st->rho_scale);
+    cudaError_t e = solve_acc_to_phi_fixed(&ctx->plan, ctx->acc_hi, ctx->acc_lo, 0.0, ctx->phi, s,
+                                           &ctx->st->rho_scale);
     if (e == cudaSuccess)
-        e = launch_field(ctx->phi, ctx->n, &ctx->st->box, 0.0, 0.0, 0.0, ctx->efield, ctx->emax,
+        e = launch_field(ctx->phi, ctx->n, &ctx->st->box, 0.0, 0.0, 0.0, ctx->emax,
                          ctx->efix, ctx->escale, s, ctx->st, ctx->maps);
     if (e == cudaSuccess)
         e = launch_track_particles(k.c, k.n, k.bg, &ctx->st->box, ctx->n, ctx->efix, ctx->escale,

@@ -387,40 +387,79 @@ cudaError_t launch_acc_to_rho(const unsigned long long *acc_hi, const unsigned l
 // Rest-frame field by centred differences on nodes 0..n-1 from phi on nodes
 // -1..n, pre-multiplied by the kick factor of the slice:
 //   E'_d = c_d (phi(+e_d) - phi(-e_d)),  c_d = -kick_d / (2 h_d),
-// so the interpolated value is the momentum change.  Also the max |E'_d|.
-__global__ void k_field(const double *__restrict__ phi, int nn, const Box *box, double kx,
-                        double ky, double kz, Field4 *__restrict__ ef,
-                        unsigned long long *__restrict__ emax, const TrackState *st,
-                        const MapCoef *maps) {
+// so the interpolated value is the momentum change; stored in int64 fixed
+// point, E_fix = rint(E'_d 2^e_d) with max |E'_d| 2^e_d in [2^49, 2^50).  Two
+// passes over phi (which stays in L2 between them): the per-component max
+// |phi(+e_d) - phi(-e_d)| (max |E'_d| = |c_d| times it: rounding is monotone),
+// then the conversion.  The FP64 pipe only forms the differences and one
+// product per component (c_d 2^e_d in one constant when that is a normal
+// double); maxima, rounding to integers and the indexing (n is a power of
+// two) run on the integer pipes.
+struct FieldCoef {
+    double cx, cy, cz;
+};
+
+__device__ __forceinline__ FieldCoef field_coef(const Box *box, double kx, double ky, double kz,
+                                                const TrackState *st, const MapCoef *maps) {
     if (maps) {  // tracking: kick factors of this kick from the per-call table
         const MapCoef &m = maps[1 + st->k_in_call];
         kx = ky = m.kick_t;
         kz = m.kick_z;
     }
-    const int q = nn + 2;
     // -k/(2h) from the box's 1/h: products, not three FP64 divisions per thread
-    const double cx = -kx * (0.5 * box->inv_h[0]);
-    const double cy = -ky * (0.5 * box->inv_h[1]);
-    const double cz = -kz * (0.5 * box->inv_h[2]);
-    const long long nodes = (long long)nn * nn * nn;
-    double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+    return FieldCoef{-kx * (0.5 * box->inv_h[0]), -ky * (0.5 * box->inv_h[1]),
+                     -kz * (0.5 * box->inv_h[2])};
+}
+
+// phi(+e_d) - phi(-e_d) at node idx (x fastest, lg = log2 n).
+__device__ __forceinline__ void phi_diffs(const double *__restrict__ phi, int nn, int lg,
+                                          long long idx, double &dx, double &dy, double &dz) {
+    const int q = nn + 2;
+    const int i = (int)(idx & (nn - 1)), j = (int)((idx >> lg) & (nn - 1)), l = (int)(idx >> (2 * lg));
+    const long long qq = (long long)q * q;
+    const long long c = (l + 1) * qq + (long long)(j + 1) * q + (i + 1);
+    dx = __ldg(&phi[c + 1]) - __ldg(&phi[c - 1]);
+    dy = __ldg(&phi[c + q]) - __ldg(&phi[c - q]);
+    dz = __ldg(&phi[c + qq]) - __ldg(&phi[c - qq]);
+}
+
+// rint(v) (round half to even) from the bits, on the integer pipes: the
+// FP64 conversion instruction's result for |v| < 2^62; larger values and
+// infinities saturate to +-(2^63 - 1), NaN gives 0.
+__device__ __forceinline__ long long rint_bits(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7FF) - 1023;
+    if (e < -1) return 0;
+    if (e > 61) {
+        if (e == 1024 && (b & 0xFFFFFFFFFFFFFull)) return 0;
+        return (b >> 63) ? -LLONG_MAX : LLONG_MAX;
+    }
+    const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    unsigned long long r;
+    if (e >= 52) {
+        r = mant << (e - 52);
+    } else {
+        const int sh = 52 - e;                       // 1..53
+        r = mant >> sh;
+        const unsigned long long rem = mant & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        r += (rem > half || (rem == half && (r & 1ull))) ? 1ull : 0ull;
+    }
+    return (b >> 63) ? -(long long)r : (long long)r;
+}
+
+__global__ void k_field(const double *__restrict__ phi, int nn, int lg,
+                        unsigned long long *__restrict__ emax) {
+    const long long nodes = 1ll << (3 * lg);
+    unsigned long long b0 = 0, b1 = 0, b2 = 0;   // max |difference| as bit patterns
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nodes;
          idx += (long long)gridDim.x * blockDim.x) {
-        int i = (int)(idx % nn), j = (int)((idx / nn) % nn), l = (int)(idx / ((long long)nn * nn));
-        long long c = ((long long)(l + 1) * q + (j + 1)) * q + (i + 1);
-        double ex = cx * (phi[c + 1] - phi[c - 1]);
-        double ey = cy * (phi[c + q] - phi[c - q]);
-        double ez = cz * (phi[c + (long long)q * q] - phi[c - (long long)q * q]);
-        ef[idx] = Field4{ex, ey, ez, 0.0};
-        m0 = fmax(m0, fabs(ex));
-        m1 = fmax(m1, fabs(ey));
-        m2 = fmax(m2, fabs(ez));
+        double dx, dy, dz;
+        phi_diffs(phi, nn, lg, idx, dx, dy, dz);
+        b0 = max(b0, abs_bits(dx));
+        b1 = max(b1, abs_bits(dy));
+        b2 = max(b2, abs_bits(dz));
     }
-    // maxima of non-negative doubles as their bit patterns (they order alike):
-    // warp, then block, then one atomic per block and component
-    unsigned long long b0 = (unsigned long long)__double_as_longlong(m0);
-    unsigned long long b1 = (unsigned long long)__double_as_longlong(m1);
-    unsigned long long b2 = (unsigned long long)__double_as_longlong(m2);
+    // (NaN bit patterns sort above Inf: a NaN difference makes the max non-finite)
     for (int o = 16; o > 0; o >>= 1) {
         b0 = max(b0, __shfl_xor_sync(0xffffffffu, b0, o));
         b1 = max(b1, __shfl_xor_sync(0xffffffffu, b1, o));
@@ -444,43 +483,65 @@ __global__ void k_field(const double *__restrict__ phi, int nn, const Box *box, 
 // differences fit the 26-bit-limb interpolation, interpolated values convert
 // to double exactly, and the resolution (2^-49 of the largest value) is that
 // of a double.
-__device__ __forceinline__ int field_exponent(unsigned long long maxbits) {
-    const double m = __longlong_as_double((long long)maxbits);
+__device__ __forceinline__ int field_exponent(double m) {
     if (!(m > 0.0) || !isfinite(m)) return 0;
     return 49 - ilogb(m);
 }
 
-// Field in int64 fixed point: E_fix = rint(E' * 2^e_d); exponents in escale.
-__global__ void k_efix(const Field4 *__restrict__ ef, long long nodes,
-                       const unsigned long long *__restrict__ emax, EFix *__restrict__ out,
-                       int *__restrict__ escale) {
-    const int e0 = field_exponent(emax[0]), e1 = field_exponent(emax[1]), e2 = field_exponent(emax[2]);
+// One component's conversion: c 2^e as one constant when it is a normal
+// double (then diff * (c 2^e) = (c diff) 2^e exactly for every value that
+// does not round to 0), else the product and a scaling.
+struct FieldConv {
+    double c, k;
+    int e;
+    bool fused;
+};
+__device__ __forceinline__ FieldConv field_conv(double c, unsigned long long maxdiff_bits) {
+    FieldConv f;
+    f.c = c;
+    f.e = field_exponent(fabs(c) * __longlong_as_double((long long)maxdiff_bits));
+    f.k = ldexp(c, f.e);
+    const unsigned long long kb = abs_bits(f.k);
+    f.fused = kb >= 0x0010000000000000ull && kb < 0x7FF0000000000000ull;
+    return f;
+}
+__device__ __forceinline__ long long field_fix(const FieldConv &f, double diff) {
+    return rint_bits(f.fused ? diff * f.k : ldexp(f.c * diff, f.e));
+}
+
+__global__ void k_efix(const double *__restrict__ phi, int nn, int lg, const Box *box, double kx,
+                       double ky, double kz, const unsigned long long *__restrict__ emax,
+                       EFix *__restrict__ out, int *__restrict__ escale, const TrackState *st,
+                       const MapCoef *maps) {
+    const FieldCoef c = field_coef(box, kx, ky, kz, st, maps);
+    const FieldConv f0 = field_conv(c.cx, emax[0]), f1 = field_conv(c.cy, emax[1]),
+                    f2 = field_conv(c.cz, emax[2]);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        escale[0] = e0;
-        escale[1] = e1;
-        escale[2] = e2;
+        escale[0] = f0.e;
+        escale[1] = f1.e;
+        escale[2] = f2.e;
     }
+    const long long nodes = 1ll << (3 * lg);
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
          i += (long long)gridDim.x * blockDim.x) {
-        const Field4 v = ef[i];
-        out[i] = EFix{__double2ll_rn(ldexp(v.x, e0)), __double2ll_rn(ldexp(v.y, e1)),
-                      __double2ll_rn(ldexp(v.z, e2)), 0};
+        double dx, dy, dz;
+        phi_diffs(phi, nn, lg, i, dx, dy, dz);
+        out[i] = EFix{field_fix(f0, dx), field_fix(f1, dy), field_fix(f2, dz), 0};
     }
 }
 
 cudaError_t launch_field(const double *phi, int nn, const Box *box, double kx, double ky,
-                         double kz, double *efield, unsigned long long *emax, EFix *efix,
-                         int *escale, cudaStream_t s, const TrackState *st,
-                         const MapCoef *maps) {
-    long long nodes = (long long)nn * nn * nn;
+                         double kz, unsigned long long *emax, EFix *efix, int *escale,
+                         cudaStream_t s, const TrackState *st, const MapCoef *maps) {
+    const int lg = __builtin_ctz((unsigned)nn);
+    const long long nodes = 1ll << (3 * lg);
     cudaError_t e = cudaMemsetAsync(emax, 0, 3 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const int blocks = (int)((nodes + TPB - 1) / TPB);
     const int fblocks = blocks < 148 * 8 ? blocks : 148 * 8;
-    BT_LAUNCH(K_FIELD, s, k_field<<<fblocks, TPB, 0, s>>>(phi, nn, box, kx, ky, kz,
-                                                          (Field4 *)efield, emax, st, maps));
-    BT_LAUNCH(K_EFIX, s, k_efix<<<blocks, TPB, 0, s>>>((const Field4 *)efield, nodes, emax, efix,
-                                                       escale));
+    BT_LAUNCH(K_FIELD, s, k_field<<<fblocks, TPB, 0, s>>>(phi, nn, lg, emax));
+    BT_LAUNCH(K_EFIX, s, k_efix<<<fblocks, TPB, 0, s>>>(phi, nn, lg, box, kx, ky, kz, emax, efix,
+                                                        escale, st, maps));
     return cudaGetLastError();
 }
 
