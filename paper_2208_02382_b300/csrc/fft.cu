@@ -1033,10 +1033,7 @@ static cudaError_t green_m(const FftPlan *p, const double *gtable, cudaStream_t 
                                  p->buf2, P, P * P, (int)P, nullptr, 0, 0, 0, (int)P, (int)P, nullptr,
                                  p->ghat, p->tw, gate));
     // the block-floating-point solve's quantised spectrum
-    const long long cnt = P * P * P;
-    const unsigned qb = (unsigned)std::min<long long>((cnt + 255) / 256, 148 * 8);
-    BT_LAUNCH(K_GREEN_YZ, s, k_green_quant<<<qb, 256, 0, s>>>(p->ghat, cnt, M, p->fs, p->ghat_q, gate));
-    return cudaGetLastError();
+    return green_quantize(p, s, gate);
 }
 
 static cudaError_t solve_any(const FftPlan *p, const XIn &in, int src, int nin, double *phi,
@@ -1092,6 +1089,16 @@ cudaError_t solve_acc_to_phi_fixed(const FftPlan *p, const unsigned long long *a
         case 512: return solve_fix_m<512>(p, acc_hi, acc_lo, scale, scale_dev, phi, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// ghat_q and the scales from ghat (after a build or after loading a stored
+// spectrum into ghat).
+cudaError_t green_quantize(const FftPlan *p, cudaStream_t s, const int *gate) {
+    const long long P = p->n + 1, cnt = P * P * P;
+    const unsigned qb = (unsigned)std::min<long long>((cnt + 255) / 256, 148 * 8);
+    BT_LAUNCH(K_GREEN_YZ, s, k_green_quant<<<qb, 256, 0, s>>>(p->ghat, cnt, p->m, p->fs, p->ghat_q,
+                                                              gate));
+    return cudaGetLastError();
 }
 
 cudaError_t green_spectrum_from_table(const FftPlan *p, const double *gtable, cudaStream_t s,

@@ -157,6 +157,8 @@ static cudaError_t grad_green(bx_ctx *ctx, bool load, cudaStream_t s) {
     if (e == cudaSuccess)
         e = launch_ghat_store(ctx->st, g->ghat_store, ctx->plan.ghat, g->o3, g->ghat_cap,
                               load ? 1 : 0, ctx->status, s);
+    // a loaded spectrum: its copy for the block-floating-point solve
+    if (e == cudaSuccess && load) e = green_quantize(&ctx->plan, s, &ctx->st->green_stale);
     if (e == cudaSuccess) e = launch_green_commit(ctx->st, s);
     return e;
 }
@@ -174,8 +176,8 @@ static cudaError_t grad_kick(bx_ctx *ctx, double *const cin[6], double *const co
         e = launch_track_deposit(cin, np, bg, &ctx->st->box, ctx->n, ctx->acc_hi, ctx->acc_lo,
                                  ctx->st, ctx->status, s);
     if (e == cudaSuccess)
-        e = solve_acc_to_phi(&ctx->plan, ctx->acc_hi, ctx->acc_lo, 0.0, ctx->phi, s,
-                             &ctx->st->rho_scale);
+        e = solve_acc_to_phi_fixed(&ctx->plan, ctx->acc_hi, ctx->acc_lo, 0.0, ctx->phi, s,
+                                   &ctx->st->rho_scale);
     if (e == cudaSuccess)
         e = launch_field(ctx->phi, ctx->n, &ctx->st->box, 0.0, 0.0, 0.0, ctx->emax,
                          efix, escale, s, ctx->st, ctx->maps);
@@ -450,6 +452,7 @@ int32_t bx_grad_backward(bx_ctx *ctx, const bx_beam *beam, const double weights[
         // recompute then loads a stored spectrum wherever the forward built one
         CK(launch_ghat_fetch(g->slot_hist, k0, g->ghat_store, ctx->plan.ghat, g->o3, g->ghat_cap, s),
            "spectrum");
+        CK(green_quantize(&ctx->plan, s), "spectrum");
         for (int64_t k = k0; k < k1; ++k) {
             const int64_t j = k - k0;
             P6 pin = p6(g->ring + (size_t)j * st6, np), pout = p6(g->ring + (size_t)(j + 1) * st6, np);
