@@ -640,7 +640,9 @@ def run_ours(args, w):
                 others[k2] = {"bound": b2, "achieved": round(a2, 3), "unit": u2,
                               "frac": round(a2 / p2, 4), "share_of_step": round(ms2 / ms_prof, 4),
                               "fp64_pipe_active_frac": (n2["fp64_pipe_active_pct"] / 100.0)
-                              if n2 else None}
+                              if n2 else None,
+                              "issue_active_frac": (n2["issue_active_pct"] / 100.0)
+                              if n2 and "issue_active_pct" in n2 else None}
         ne = ncu_entry(dname)
         roof = {"kernel": dname, "bound": bound, "achieved": achieved, "peak": peak,
                 "unit": unit, "frac": achieved / peak, "peak_source": peak_src,

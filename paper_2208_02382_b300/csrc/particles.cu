@@ -450,15 +450,21 @@ __device__ __forceinline__ long long rint_bits(double v) {
 __global__ void k_field(const double *__restrict__ phi, int nn, int lg,
                         unsigned long long *__restrict__ emax) {
     const long long nodes = 1ll << (3 * lg);
-    unsigned long long b0 = 0, b1 = 0, b2 = 0;   // max |difference| as bit patterns
+    // max |difference| from the bit patterns shifted left by one (the sign
+    // falls out; a mask would be compiled as an FP64 absolute value)
+    unsigned long long b0 = 0, b1 = 0, b2 = 0;
+    auto key = [](double v) { return (unsigned long long)__double_as_longlong(v) << 1; };
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nodes;
          idx += (long long)gridDim.x * blockDim.x) {
         double dx, dy, dz;
         phi_diffs(phi, nn, lg, idx, dx, dy, dz);
-        b0 = max(b0, abs_bits(dx));
-        b1 = max(b1, abs_bits(dy));
-        b2 = max(b2, abs_bits(dz));
+        b0 = max(b0, key(dx));
+        b1 = max(b1, key(dy));
+        b2 = max(b2, key(dz));
     }
+    b0 >>= 1;
+    b1 >>= 1;
+    b2 >>= 1;
     // (NaN bit patterns sort above Inf: a NaN difference makes the max non-finite)
     for (int o = 16; o > 0; o >>= 1) {
         b0 = max(b0, __shfl_xor_sync(0xffffffffu, b0, o));
@@ -508,6 +514,9 @@ __device__ __forceinline__ FieldConv field_conv(double c, unsigned long long max
 __device__ __forceinline__ long long field_fix(const FieldConv &f, double diff) {
     return rint_bits(f.fused ? diff * f.k : ldexp(f.c * diff, f.e));
 }
+__device__ __forceinline__ long long field_fix_fused(const FieldConv &f, double diff) {
+    return rint_bits(diff * f.k);
+}
 
 __global__ void k_efix(const double *__restrict__ phi, int nn, int lg, const Box *box, double kx,
                        double ky, double kz, const unsigned long long *__restrict__ emax,
@@ -522,11 +531,22 @@ __global__ void k_efix(const double *__restrict__ phi, int nn, int lg, const Box
         escale[2] = f2.e;
     }
     const long long nodes = 1ll << (3 * lg);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
-         i += (long long)gridDim.x * blockDim.x) {
-        double dx, dy, dz;
-        phi_diffs(phi, nn, lg, i, dx, dy, dz);
-        out[i] = EFix{field_fix(f0, dx), field_fix(f1, dy), field_fix(f2, dz), 0};
+    // the uniform choice outside the loop (a per-node select would also run
+    // the scaling path on the FP64 pipe)
+    if (f0.fused && f1.fused && f2.fused) {
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
+             i += (long long)gridDim.x * blockDim.x) {
+            double dx, dy, dz;
+            phi_diffs(phi, nn, lg, i, dx, dy, dz);
+            out[i] = EFix{field_fix_fused(f0, dx), field_fix_fused(f1, dy), field_fix_fused(f2, dz), 0};
+        }
+    } else {
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
+             i += (long long)gridDim.x * blockDim.x) {
+            double dx, dy, dz;
+            phi_diffs(phi, nn, lg, i, dx, dy, dz);
+            out[i] = EFix{field_fix(f0, dx), field_fix(f1, dy), field_fix(f2, dz), 0};
+        }
     }
 }
 
