@@ -77,6 +77,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-grad", action="store_true",
                    help="skip the gradient measurement (fodo8_grad_1e6_64)")
+    p.add_argument("--no-tune", action="store_true",
+                   help="keep the default binning (re-bin every 16 kicks) instead of the "
+                        "autotuner's choice")
     p.add_argument("--no-variants", action="store_true",
                    help="skip the TSC / thin-multipole / per-slice-diagnostics measurements")
     p.add_argument("--no-batch", action="store_true",
@@ -576,6 +579,14 @@ def run_ours(args, w):
     beam = btk.Beam(torch.tensor(coords_h, dtype=torch.float64, device=dev), sp, w.bunch_charge_C)
     trk = btk.Tracker(w.n_grid)
     stream = torch.cuda.current_stream()
+    # binning as a user would set it: the autotuner times the candidates on the
+    # first 64 kicks of this problem (bunch restored, context reset afterwards)
+    binning = {"rebin_interval": 16, "bin_edge": 0, "tuned": False}
+    if not args.no_tune:
+        t_tune = time.perf_counter()
+        (iv, be), _ = trk.autotune_binning(beam, lat, kicks=64)
+        binning = {"rebin_interval": iv, "bin_edge": be, "tuned": True, "tuned_over_kicks": 64,
+                   "tuning_s": round(time.perf_counter() - t_tune, 2)}
     # warm-up (first box and Green's function build, kick-graph capture happen here)
     trk.track(beam, lat, 0, args.warmup)
     trk.sync()
@@ -662,6 +673,7 @@ def run_ours(args, w):
         mom_h = torch.empty(27, dtype=torch.float64).pin_memory()
         k_e2e = min(args.steps, 200)
         trk2 = btk.Tracker(w.n_grid)
+        trk2.set_binning(binning["rebin_interval"], binning["bin_edge"])
         beam2 = btk.Beam(torch.empty_like(beam.coords), sp, w.bunch_charge_C)
         if pg:
             pg.barrier()
@@ -707,7 +719,7 @@ def run_ours(args, w):
                            "doubled_grid": 2 * w.n_grid, "kicks_in_lattice": w.kicks,
                            "step": "one slice: map, box rule, deposit, solve, gather+kick",
                            "l2": f"inputs larger than L2 (particle SoA {npart * 48 / 1e9:.2f} GB)",
-                           "parallelism": f"replicas x{world}"},
+                           "parallelism": f"replicas x{world}", "binning": binning},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gradient": gradient,
                 "batching": batching, "variants": variants,
                 "gpu_launches": launches, "clocks": clocks, "wall_s_timed": wall,

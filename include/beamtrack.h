@@ -392,8 +392,9 @@ const char *bx_batch_last_error(const bx_batch *batch);
 int32_t bx_set_binning(bx_ctx *ctx, int32_t rebin_interval, int32_t bin_edge);
 
 /* Autotuner of the binning: tracks `kicks` kicks of the lattice from kick 0
- * (from a fresh state) once per candidate (never re-bin, and every 8 or 32
- * kicks with each valid bin edge among 4, 8, 16), timing each with CUDA
+ * (from a fresh state) once per candidate (never re-bin, and every 8, 16, 32
+ * or 64 kicks, those not longer than the timed kicks, with each valid bin
+ * edge among 4, 8, 16), timing each with CUDA
  * events, and keeps the fastest (bx_set_binning).  The beam's coordinates and
  * ids are restored afterwards and the context is reset (bx_reset), so results
  * do not depend on the tuning.  chosen (host, 2): the chosen rebin_interval and

@@ -45,12 +45,18 @@ int32_t bx_autotune_binning(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, i
     if (!beam->id || beam->n <= 0) return fail(ctx, BX_BAD_ARG, "tuning needs particles with ids");
     if (kicks <= 0) return fail(ctx, BX_BAD_ARG, "kicks must be >= 1");
     cudaStream_t s = (cudaStream_t)stream;
-    // candidates: never; every 8 and 32 kicks with each valid edge of 4, 8, 16
+    int64_t total = 0;
+    for (int i = 0; i < lat->count; ++i) total += lat->elements[i].nslice;
+    const int64_t nk = std::min<int64_t>(kicks, total);
+    // candidates: never; every 8, 16, 32 or 64 kicks (intervals no longer
+    // than the timed window, so that each candidate's window holds its sorts)
+    // with each valid edge of 4, 8, 16
     std::vector<std::pair<int, int>> cand;
     cand.push_back({-1, 0});
-    for (int iv : {8, 32})
-        for (int be : {4, 8, 16})
-            if (sort_brick_edge_valid(ctx->n, be)) cand.push_back({iv, be});
+    for (int iv : {8, 16, 32, 64})
+        if (iv <= nk)
+            for (int be : {4, 8, 16})
+                if (sort_brick_edge_valid(ctx->n, be)) cand.push_back({iv, be});
     if (count) *count = (int32_t)cand.size();
     // save the bunch
     const int64_t n = beam->n;
@@ -76,9 +82,6 @@ int32_t bx_autotune_binning(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, i
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    int64_t total = 0;
-    for (int i = 0; i < lat->count; ++i) total += lat->elements[i].nslice;
-    const int64_t nk = std::min<int64_t>(kicks, total);
     int best = -1;
     float best_ms = 0.0f;
     const int old_iv = ctx->sort_interval == 0 ? -1 : ctx->sort_interval, old_be = ctx->bin_edge;
