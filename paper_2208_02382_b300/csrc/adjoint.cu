@@ -570,8 +570,9 @@ cudaError_t launch_adj_kick(const AdjKick &k, cudaStream_t s) {
                                  k.slot_hist, k.kick, k.ghat_store, k.plan->ghat, k.ghat_count,
                                  k.ghat_cap));
     e = cudaGetLastError();
+    if (e == cudaSuccess) e = green_quantize(k.plan, s);
     if (e != cudaSuccess) return e;
-    e = solve_adjoint_shifted(k.plan, k.phibar, k.rb, s);
+    e = solve_adjoint_shifted_fixed(k.plan, k.phibar, k.rb, s);
     if (e != cudaSuccess) return e;
     Adj2Args a2{k.P, k.A, k.box, -k.betagamma, k.nn, k.n, k.rb, k.q_macro, k.amax_out};
     BT_LAUNCH(K_ADJ_PART, s, k_adj_kick2<<<nb, ATPB, 0, s>>>(a2));

@@ -266,6 +266,8 @@ cudaError_t solve_acc_to_phi(const FftPlan *p, const unsigned long long *acc_hi,
 cudaError_t solve_acc_to_phi_fixed(const FftPlan *p, const unsigned long long *acc_hi,
                                    const unsigned long long *acc_lo, double scale, double *phi,
                                    cudaStream_t s, const double *scale_dev);
+cudaError_t solve_adjoint_shifted_fixed(const FftPlan *p, const double *phibar, double *out,
+                                        cudaStream_t s);
 cudaError_t green_quantize(const FftPlan *p, cudaStream_t s, const int *gate = nullptr);
 cudaError_t green_spectrum_from_table(const FftPlan *p, const double *gtable, cudaStream_t s,
                                       const int *gate = nullptr);

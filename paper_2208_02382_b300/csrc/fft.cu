@@ -673,6 +673,82 @@ __global__ void __launch_bounds__(FFT_TPB) k_fftq_x_fwd(const unsigned long long
     if (t == 0) e1[(long long)z * n + y] = e1[(long long)z * n + y + 1] = mb ? sh : FIX_EMPTY;
 }
 
+// rint(v 2^-sh) from the bits (round half to even, integer pipes), for
+// |v 2^-sh| < 2^62; zero and subnormal v give 0.
+__device__ __forceinline__ long long rint_scaled(double v, int sh) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int ex = (int)((b >> 52) & 0x7FF);
+    if (ex == 0) return 0;
+    const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int e = ex - 1075 - sh;   // v 2^-sh = mant 2^e
+    unsigned long long r;
+    if (e >= 0) {
+        r = mant << e;
+    } else if (e < -54) {
+        r = 0;
+    } else {
+        const int k = -e;
+        r = mant >> k;
+        const unsigned long long rem = mant & ((1ull << k) - 1), half = 1ull << (k - 1);
+        r += (rem > half || (rem == half && (r & 1ull))) ? 1ull : 0ull;
+    }
+    return (b >> 63) ? -(long long)r : (long long)r;
+}
+
+// forward x pass from a cube of nin^3 doubles (rows in pairs; nin even, the
+// adjoint's source on nodes -1..n); each pair normalised by its largest
+// exponent: |value| < 2^(E+1), L1 < 2 nin 2^(E+1) <= 2m 2^(E+1).
+template <int M>
+__global__ void __launch_bounds__(FFT_TPB) k_fftq_x_fwd_d(const double *__restrict__ src, int n,
+                                                          int nin, const longlong2 *__restrict__ tw,
+                                                          longlong2 *__restrict__ out,
+                                                          int *__restrict__ e1) {
+    constexpr int T = Shape<M>::T, LPB = FFT_TPB / T, V = M / T;
+    extern __shared__ longlong2 smq[];
+    __shared__ long long red[2 * LPB];
+    longlong2 *stw = smq, *sl = smq + M;
+    load_twiddles<M>(stw, tw);
+    const int team = threadIdx.x / T, t = threadIdx.x % T;
+    const long long pairs = (long long)(nin / 2) * nin;
+    const long long pr = (long long)blockIdx.x * LPB + team;
+    const bool live = pr < pairs;
+    const int z = live ? (int)(pr / (nin / 2)) : 0, y = live ? (int)(pr % (nin / 2)) * 2 : 0;
+    __syncthreads();
+    constexpr int R0 = Shape<M>::R0, U0 = (M / R0) / T;
+    const long long row = ((long long)z * nin + y) * nin;
+    double va[V], vb[V];
+    int ef = 0;   // largest biased exponent field
+#pragma unroll
+    for (int j = 0; j < U0; ++j)
+#pragma unroll
+        for (int m = 0; m < R0; ++m) {
+            const int e = first_index<M>(t, j, m), i = j * R0 + m;
+            va[i] = (live && e < nin) ? src[row + e] : 0.0;
+            vb[i] = (live && e < nin) ? src[row + nin + e] : 0.0;
+            const int fa = (int)(((unsigned long long)__double_as_longlong(va[i]) >> 52) & 0x7FF);
+            const int fb = (int)(((unsigned long long)__double_as_longlong(vb[i]) >> 52) & 0x7FF);
+            ef = max(ef, max(fa, fb));
+        }
+    ef = (int)team_max<T>(ef, red);
+    constexpr int LGM = M == 16 ? 4 : M == 32 ? 5 : M == 64 ? 6 : M == 128 ? 7 : M == 256 ? 8 : 9;
+    // |value| < 2^(ef - 1022); L1 < 2m 2^(ef - 1022) <= 2^60 after the shift
+    const int sh = (ef - 1022) + LGM + 1 - 60;
+    longlong2 v[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) v[i] = make_longlong2(rint_scaled(va[i], sh), rint_scaled(vb[i], sh));
+    longlong2 *s = sl + team * M;
+    line_fft<M, false>(v, s, t, stw);
+    if (!live) return;
+    const int P = n + 1;
+    longlong2 *oa = out + ((long long)z * nin + y) * P, *ob = oa + P;
+    for (int k = t; k <= n; k += T) {
+        const longlong2 zk = s[k], zc = s[(M - k) & (M - 1)];
+        oa[k] = make_longlong2((zk.x + zc.x) >> 1, (zk.y - zc.y) >> 1);
+        ob[k] = make_longlong2((zk.y + zc.y) >> 1, (zc.x - zk.x) >> 1);
+    }
+    if (t == 0) e1[(long long)z * nin + y] = e1[(long long)z * nin + y + 1] = ef ? sh : FIX_EMPTY;
+}
+
 // Strided line passes as k_fft_lines (MODE_FWD: forward y; MODE_ZSOLVE:
 // forward z, times the quantised Green's spectrum, inverse z; MODE_INV:
 // inverse y).  Element e of line (o, kx) has exponent
@@ -748,12 +824,14 @@ __global__ void __launch_bounds__(FFT_TPB) k_fftq_lines(const longlong2 *__restr
 
 // inverse x pass (complex to real, as k_fft_x_inv); element kx of rows
 // (zz, yy), (zz, yy+1) has exponent e4[zz*P + kx]; writes phi[(zz*q + yy)*q + w]
-// = value 2^E scale_dev-or-scale 2^-51 D / m^3, nodes -1..n.
+// = value 2^(E + eoff) scale_dev-or-scale D / m^3, nodes -1..n (eoff = -51
+// for the accumulators, 2^51 per particle; 0 for a double source).
 template <int M>
 __global__ void __launch_bounds__(FFT_TPB) k_fftq_x_inv(const longlong2 *__restrict__ in, int n,
                                                         const int *__restrict__ e4,
                                                         const FixScales *__restrict__ fs,
                                                         double scale, const double *scale_dev,
+                                                        int eoff,
                                                         const longlong2 *__restrict__ tw,
                                                         double *__restrict__ phi) {
     constexpr int T = Shape<M>::T, LPB = FFT_TPB / T, V = M / T;
@@ -808,7 +886,7 @@ __global__ void __launch_bounds__(FFT_TPB) k_fftq_x_inv(const longlong2 *__restr
     longlong2 *s = sl + team * M;
     line_fft<M, true>(v, s, t, stw);
     if (!live) return;
-    const double sc = (scale_dev ? *scale_dev : scale) * fs->F * ldexp(1.0, E - 51);
+    const double sc = (scale_dev ? *scale_dev : scale) * fs->F * ldexp(1.0, E + eoff);
     double *pa = phi + ((long long)zz * q + yy) * q, *pb = pa + q;
     for (int w = t; w < q; w += T) {
         const longlong2 z = s[(w + M - 1) & (M - 1)];
@@ -872,6 +950,7 @@ static void set_attrs() {
     cudaFuncSetAttribute(k_fft_lines<M, MODE_FWD_EVEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_fft_x_inv<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_fftq_x_fwd<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_fftq_x_fwd_d<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_fftq_lines<M, MODE_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_fftq_lines<M, MODE_ZSOLVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_fftq_lines<M, MODE_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -897,7 +976,7 @@ cudaError_t fft_plan_init(FftPlan *p, int n) {
     if (e == cudaSuccess) e = cudaMalloc(&p->ghat_q, P * P * P * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&p->fs, sizeof(FixScales));
     if (e == cudaSuccess)
-        e = cudaMalloc(&p->fexp, ((long long)n * n + n * P + m * P + (n + 2) * P) * sizeof(int));
+        e = cudaMalloc(&p->fexp, ((long long)(n + 2) * (n + 2) + 2 * (n + 2) * P + m * P) * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->fs, 0, sizeof(FixScales));
     if (e != cudaSuccess) {
         fft_plan_free(p);
@@ -978,37 +1057,44 @@ static cudaError_t solve_m(const FftPlan *p, const XIn &in, int src, int nin, do
     return cudaGetLastError();
 }
 
-// The tracking solve in block floating point (passes and layouts as solve_m
-// with the accumulators as the source); line exponents in p->fexp:
-// e1[z][y] (n^2), e2[z][kx] (n P), e3[ky][kx] (m P), e4[zz][kx] ((n+2) P).
+// The solve in block floating point (passes and layouts as solve_m): the
+// source is the accumulators (nin = n) or a cube of nin^3 doubles (src_d);
+// line exponents in p->fexp: e1[z][y] (nin^2), e2[z][kx] (nin P),
+// e3[ky][kx] (m P), e4[zz][kx] ((n+2) P).
 template <int M>
 static cudaError_t solve_fix_m(const FftPlan *p, const unsigned long long *acc_hi,
-                              const unsigned long long *acc_lo, double scale,
-                              const double *scale_dev, double *phi, cudaStream_t s) {
+                              const unsigned long long *acc_lo, const double *src_d, int nin,
+                              double scale, const double *scale_dev, int eoff, double *phi,
+                              cudaStream_t s) {
     const int n = p->n;
     const long long P = n + 1, q = n + 2;
     const size_t sm = smem_bytes(M);
     longlong2 *S1 = (longlong2 *)p->buf, *S2 = (longlong2 *)p->buf2, *S3 = S1, *S4 = S2;
-    int *e1 = p->fexp, *e2 = e1 + (long long)n * n, *e3 = e2 + n * P, *e4 = e3 + M * P;
-    BT_LAUNCH(K_FFT_X, s, k_fftq_x_fwd<M><<<blocks_lines((long long)(n / 2) * n, M), FFT_TPB, sm, s>>>(
-                              acc_hi, acc_lo, n, p->twq, S1, e1));
+    int *e1 = p->fexp, *e2 = e1 + q * q, *e3 = e2 + q * P, *e4 = e3 + M * P;
+    if (src_d)
+        BT_LAUNCH(K_FFT_X, s, k_fftq_x_fwd_d<M><<<blocks_lines((long long)(nin / 2) * nin, M), FFT_TPB,
+                                                   sm, s>>>(src_d, n, nin, p->twq, S1, e1));
+    else
+        BT_LAUNCH(K_FFT_X, s, k_fftq_x_fwd<M><<<blocks_lines((long long)(n / 2) * n, M), FFT_TPB, sm,
+                                                 s>>>(acc_hi, acc_lo, n, p->twq, S1, e1));
     // y: lines (z, kx), element y with exponent e1[z][y]
-    BT_LAUNCH(K_FFT_YZ, s, k_fftq_lines<M, MODE_FWD><<<blocks_lines(n * P, M), FFT_TPB, sm, s>>>(
-                               S1, n * P, P, n, e1, n, 1, 0, S2, M * P, P, M, e2, n, (int)P,
+    BT_LAUNCH(K_FFT_YZ, s, k_fftq_lines<M, MODE_FWD><<<blocks_lines(nin * P, M), FFT_TPB, sm, s>>>(
+                               S1, nin * P, P, nin, e1, nin, 1, 0, S2, M * P, P, M, e2, nin, (int)P,
                                nullptr, p->twq));
     // z: lines (ky, kx), element z with exponent e2[z][kx]
     BT_LAUNCH(K_FFT_ZSOLVE, s,
               k_fftq_lines<M, MODE_ZSOLVE><<<blocks_lines((long long)M * P, M), FFT_TPB, sm, s>>>(
-                  S2, P, (long long)M * P, n, e2, 0, P, 1, S3, P, (long long)M * P, (int)q, e3, M,
-                  (int)P, p->ghat_q, p->twq));
+                  S2, P, (long long)M * P, nin, e2, 0, P, 1, S3, P, (long long)M * P, (int)q, e3,
+                  M, (int)P, p->ghat_q, p->twq));
     // inverse y: lines (zz, kx), element ky with exponent e3[ky][kx]
     BT_LAUNCH(K_FFT_YZ, s, k_fftq_lines<M, MODE_INV><<<blocks_lines(q * P, M), FFT_TPB, sm, s>>>(
                                S3, (long long)M * P, P, M, e3, 0, P, 1, S4, q * P, P, (int)q, e4,
                                (int)q, (int)P, nullptr, p->twq));
     BT_LAUNCH(K_FFT_XINV, s, k_fftq_x_inv<M><<<blocks_lines(q * (q / 2), M), FFT_TPB, sm, s>>>(
-                                 S4, n, e4, p->fs, scale, scale_dev, p->twq, phi));
+                                 S4, n, e4, p->fs, scale, scale_dev, eoff, p->twq, phi));
     return cudaGetLastError();
 }
+
 
 // Spectrum of the doubled Green's function from its octant table.  The doubled
 // G is even in every dimension, so each pass only transforms the lines whose
@@ -1077,18 +1163,35 @@ cudaError_t solve_acc_to_phi(const FftPlan *p, const unsigned long long *acc_hi,
     return solve_any(p, in, SRC_ACC, p->n, phi, s);
 }
 
+static cudaError_t solve_fix_dispatch(const FftPlan *p, const unsigned long long *acc_hi,
+                                      const unsigned long long *acc_lo, const double *src_d,
+                                      int nin, double scale, const double *scale_dev, int eoff,
+                                      double *phi, cudaStream_t s) {
+    switch (p->m) {
+#define BT_FIX_CASE(MM)                                                                          \
+    case MM:                                                                                     \
+        return solve_fix_m<MM>(p, acc_hi, acc_lo, src_d, nin, scale, scale_dev, eoff, phi, s);
+        BT_FIX_CASE(16)
+        BT_FIX_CASE(32)
+        BT_FIX_CASE(64)
+        BT_FIX_CASE(128)
+        BT_FIX_CASE(256)
+        BT_FIX_CASE(512)
+#undef BT_FIX_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t solve_acc_to_phi_fixed(const FftPlan *p, const unsigned long long *acc_hi,
                                    const unsigned long long *acc_lo, double scale, double *phi,
                                    cudaStream_t s, const double *scale_dev) {
-    switch (p->m) {
-        case 16: return solve_fix_m<16>(p, acc_hi, acc_lo, scale, scale_dev, phi, s);
-        case 32: return solve_fix_m<32>(p, acc_hi, acc_lo, scale, scale_dev, phi, s);
-        case 64: return solve_fix_m<64>(p, acc_hi, acc_lo, scale, scale_dev, phi, s);
-        case 128: return solve_fix_m<128>(p, acc_hi, acc_lo, scale, scale_dev, phi, s);
-        case 256: return solve_fix_m<256>(p, acc_hi, acc_lo, scale, scale_dev, phi, s);
-        case 512: return solve_fix_m<512>(p, acc_hi, acc_lo, scale, scale_dev, phi, s);
-        default: return cudaErrorInvalidValue;
-    }
+    return solve_fix_dispatch(p, acc_hi, acc_lo, nullptr, p->n, scale, scale_dev, -51, phi, s);
+}
+
+// The transpose of the solve (as solve_adjoint_shifted) in block floating point.
+cudaError_t solve_adjoint_shifted_fixed(const FftPlan *p, const double *phibar, double *out,
+                                        cudaStream_t s) {
+    return solve_fix_dispatch(p, nullptr, nullptr, phibar, p->n + 2, 1.0, nullptr, 0, out, s);
 }
 
 // ghat_q and the scales from ghat (after a build or after loading a stored
