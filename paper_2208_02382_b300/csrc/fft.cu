@@ -24,6 +24,7 @@
 //    twiddles exp(-+2 pi i j/m) from a shared-memory table (built once with
 //    sincospi), and exchanges values through shared memory between radix steps.
 #include <algorithm>
+#include <climits>
 
 #include "common.cuh"
 
@@ -205,6 +206,13 @@ template <> struct Shape<512> { static constexpr int S = 3, R0 = 8, R1 = 8, R2 =
 
 constexpr int FFT_TPB = 256;
 
+// Line buffers in shared memory hold one 16-byte pad slot per 16 elements:
+// the first radix-16 step stores element 16t + q from thread t, a stride that
+// would put every lane of a warp on the same banks.
+__device__ __forceinline__ int sp(int i) { return i + (i >> 4); }
+template <int M>
+constexpr int kLineStride = M + M / 16;   // elements per padded line buffer
+
 // One Stockham radix step on values held in registers.  Thread t of the team
 // holds units u = t + j*T (j < U = (M/R)/T); unit u's inputs are the line
 // elements u + m*(M/R), in v[j*R + m].  Twiddles W_{L R}^{k m} (k = u mod L)
@@ -236,7 +244,7 @@ __device__ __forceinline__ void store_step(const C *v, C *s, int t) {
     for (int j = 0; j < U; ++j) {
         const int u = t + j * T, k = u % L;
 #pragma unroll
-        for (int q = 0; q < R; ++q) s[(u - k) * R + q * L + k] = v[j * R + q];
+        for (int q = 0; q < R; ++q) s[sp((u - k) * R + q * L + k)] = v[j * R + q];
     }
 }
 
@@ -246,7 +254,7 @@ __device__ __forceinline__ void load_step(C *v, const C *s, int t) {
 #pragma unroll
     for (int j = 0; j < U; ++j)
 #pragma unroll
-        for (int m = 0; m < R; ++m) v[j * R + m] = s[(t + j * T) + m * (M / R)];
+        for (int m = 0; m < R; ++m) v[j * R + m] = s[sp((t + j * T) + m * (M / R))];
 }
 
 // Line element held in register slot (j, m) before the first step.
@@ -358,14 +366,14 @@ __global__ void __launch_bounds__(FFT_TPB) k_fft_x_fwd(XIn in, int n, int ny, in
                                                 x_value<M, SRC>(in, n, nin, e, y + 1, z))
                                  : make_double2(0.0, 0.0);
         }
-    double2 *s = sl + team * M;
+    double2 *s = sl + team * kLineStride<M>;
     if (SRC != SRC_GREEN && 2 * nin == M) line_fft<M, false, true>(v, s, t, stw);  // rows x < M/2
     else line_fft<M, false>(v, s, t, stw);
     if (!live) return;
     const int P = n + 1;
     double2 *oa = out + ((long long)z * ny + y) * P, *ob = oa + P;
     for (int k = t; k <= n; k += T) {
-        const double2 zk = s[k], zc = s[(M - k) & (M - 1)];
+        const double2 zk = s[sp(k)], zc = s[sp((M - k) & (M - 1))];
         oa[k] = make_double2(0.5 * (zk.x + zc.x), 0.5 * (zk.y - zc.y));
         ob[k] = make_double2(0.5 * (zk.y + zc.y), 0.5 * (zc.x - zk.x));
     }
@@ -417,7 +425,7 @@ __global__ void __launch_bounds__(FFT_TPB) k_fft_lines(const double2 *__restrict
             if constexpr (MODE == MODE_GREEN || MODE == MODE_FWD_EVEN) e = min(e, M - e);
             v[j * R0 + m] = (live && e < ne_in) ? src[e * in_e] : make_double2(0.0, 0.0);
         }
-    double2 *s = sl + team * M;
+    double2 *s = sl + team * kLineStride<M>;
     if ((MODE == MODE_FWD || MODE == MODE_ZSOLVE) && 2 * ne_in == M) line_fft<M, INV1, true>(v, s, t, stw);
     else line_fft<M, INV1>(v, s, t, stw);
     if constexpr (MODE == MODE_ZSOLVE) {
@@ -425,7 +433,7 @@ __global__ void __launch_bounds__(FFT_TPB) k_fft_lines(const double2 *__restrict
         for (int e = t; e < M; e += T) {
             const int c = min(e, M - e);
             const double g = live ? gh[((long long)c * P + b) * P + kx] : 0.0;
-            s[e] = make_double2(s[e].x * g, s[e].y * g);
+            s[sp(e)] = make_double2(s[sp(e)].x * g, s[sp(e)].y * g);
         }
         __syncthreads();
         load_step<M, R0>(v, s, t);
@@ -435,12 +443,12 @@ __global__ void __launch_bounds__(FFT_TPB) k_fft_lines(const double2 *__restrict
     if (!live) return;
     if constexpr (MODE == MODE_FWD || MODE == MODE_FWD_EVEN) {
         double2 *dst = out + o * out_o + kx;
-        for (int e = t; e < nw; e += T) dst[e * out_e] = s[e];
+        for (int e = t; e < nw; e += T) dst[e * out_e] = s[sp(e)];
     } else if constexpr (MODE == MODE_GREEN) {
-        for (int e = t; e < P; e += T) gh_out[((long long)e * P + o) * P + kx] = s[e].x;
+        for (int e = t; e < P; e += T) gh_out[((long long)e * P + o) * P + kx] = s[sp(e)].x;
     } else {
         double2 *dst = out + o * out_o + kx;
-        for (int w = t; w < nw; w += T) dst[w * out_e] = s[(w + M - 1) & (M - 1)];
+        for (int w = t; w < nw; w += T) dst[w * out_e] = s[sp((w + M - 1) & (M - 1))];
     }
 }
 
@@ -483,12 +491,12 @@ __global__ void __launch_bounds__(FFT_TPB) k_fft_x_inv(const double2 *__restrict
             }
             v[j * R0 + m] = z;
         }
-    double2 *s = sl + team * M;
+    double2 *s = sl + team * kLineStride<M>;
     line_fft<M, true>(v, s, t, stw);
     if (!live) return;
     double *pa = phi + ((long long)zz * q + yy) * q, *pb = pa + q;
     for (int w = t; w < q; w += T) {
-        const double2 z = s[(w + M - 1) & (M - 1)];
+        const double2 z = s[sp((w + M - 1) & (M - 1))];
         pa[w] = z.x * scale;
         pb[w] = z.y * scale;
     }
@@ -584,27 +592,22 @@ __device__ __forceinline__ int norm_shift(unsigned long long l1_16) {
     return bits - 60;
 }
 
-// Aligns the V values of a thread (exponents ev, FIX_EMPTY for zeros) to the
-// team's largest exponent, normalises the line and returns its exponent.
+// Normalises a line whose values share one exponent: returns the shift t
+// applied (the line times 2^-t has L1 in (2^59, 2^60]), or INT_MIN for an
+// all-zero line.
 template <int M, int V>
-__device__ __forceinline__ int align_line(longlong2 *v, const int *ev, long long *red) {
+__device__ __forceinline__ int normalise_line(longlong2 *v, long long *red) {
     constexpr int T = Shape<M>::T;
-    int emax = FIX_EMPTY;
-#pragma unroll
-    for (int i = 0; i < V; ++i) emax = max(emax, ev[i]);
-    emax = (int)team_max<T>(emax, red);
     unsigned long long l1 = 0;
 #pragma unroll
-    for (int i = 0; i < V; ++i) {
-        v[i] = scale2n(v[i], emax - ev[i]);
-        l1 += l1_part(v[i]) - 1 + ((v[i].x | v[i].y) != 0);
-    }
+    for (int i = 0; i < V; ++i) l1 += l1_part(v[i]) - 1 + ((v[i].x | v[i].y) != 0);
     l1 = team_sum<T>(l1, red);
     const int t = norm_shift(l1);
 #pragma unroll
     for (int i = 0; i < V; ++i) v[i] = scale2n(v[i], t);
-    return l1 ? emax + t : FIX_EMPTY;
+    return l1 ? t : INT_MIN;
 }
+
 
 // accumulator value (hi 2^31 + lo, 2^51 per particle)
 __device__ __forceinline__ unsigned __int128 acc_value(const unsigned long long *__restrict__ hi,
@@ -625,7 +628,7 @@ __device__ __forceinline__ long long shift128(unsigned __int128 v, int t) {
 // out[(z*n + y)*P + k], P = n+1; the pair's exponent in e1[z*n + y], e1[z*n + y + 1].
 // The pair is normalised by its largest value: L1 < m 2^bits(max).
 template <int M>
-__global__ void __launch_bounds__(FFT_TPB) k_fftq_x_fwd(const unsigned long long *__restrict__ acc_hi,
+__global__ void __launch_bounds__(FFT_TPB, 2) k_fftq_x_fwd(const unsigned long long *__restrict__ acc_hi,
                                                         const unsigned long long *__restrict__ acc_lo,
                                                         int n, const longlong2 *__restrict__ tw,
                                                         longlong2 *__restrict__ out,
@@ -660,13 +663,13 @@ __global__ void __launch_bounds__(FFT_TPB) k_fftq_x_fwd(const unsigned long long
     longlong2 v[V];
 #pragma unroll
     for (int i = 0; i < V; ++i) v[i] = make_longlong2(shift128(va[i], sh), shift128(vb[i], sh));
-    longlong2 *s = sl + team * M;
+    longlong2 *s = sl + team * kLineStride<M>;
     line_fft<M, false, true>(v, s, t, stw);  // rows x < M/2
     if (!live) return;
     const int P = n + 1;
     longlong2 *oa = out + ((long long)z * n + y) * P, *ob = oa + P;
     for (int k = t; k <= n; k += T) {
-        const longlong2 zk = s[k], zc = s[(M - k) & (M - 1)];
+        const longlong2 zk = s[sp(k)], zc = s[sp((M - k) & (M - 1))];
         oa[k] = make_longlong2((zk.x + zc.x) >> 1, (zk.y - zc.y) >> 1);
         ob[k] = make_longlong2((zk.y + zc.y) >> 1, (zc.x - zk.x) >> 1);
     }
@@ -699,7 +702,7 @@ __device__ __forceinline__ long long rint_scaled(double v, int sh) {
 // adjoint's source on nodes -1..n); each pair normalised by its largest
 // exponent: |value| < 2^(E+1), L1 < 2 nin 2^(E+1) <= 2m 2^(E+1).
 template <int M>
-__global__ void __launch_bounds__(FFT_TPB) k_fftq_x_fwd_d(const double *__restrict__ src, int n,
+__global__ void __launch_bounds__(FFT_TPB, 2) k_fftq_x_fwd_d(const double *__restrict__ src, int n,
                                                           int nin, const longlong2 *__restrict__ tw,
                                                           longlong2 *__restrict__ out,
                                                           int *__restrict__ e1) {
@@ -736,13 +739,13 @@ __global__ void __launch_bounds__(FFT_TPB) k_fftq_x_fwd_d(const double *__restri
     longlong2 v[V];
 #pragma unroll
     for (int i = 0; i < V; ++i) v[i] = make_longlong2(rint_scaled(va[i], sh), rint_scaled(vb[i], sh));
-    longlong2 *s = sl + team * M;
+    longlong2 *s = sl + team * kLineStride<M>;
     line_fft<M, false>(v, s, t, stw);
     if (!live) return;
     const int P = n + 1;
     longlong2 *oa = out + ((long long)z * nin + y) * P, *ob = oa + P;
     for (int k = t; k <= n; k += T) {
-        const longlong2 zk = s[k], zc = s[(M - k) & (M - 1)];
+        const longlong2 zk = s[sp(k)], zc = s[sp((M - k) & (M - 1))];
         oa[k] = make_longlong2((zk.x + zc.x) >> 1, (zk.y - zc.y) >> 1);
         ob[k] = make_longlong2((zk.y + zc.y) >> 1, (zc.x - zk.x) >> 1);
     }
@@ -754,7 +757,7 @@ __global__ void __launch_bounds__(FFT_TPB) k_fftq_x_fwd_d(const double *__restri
 // inverse y).  Element e of line (o, kx) has exponent
 // ein[o*ein_o + e*ein_e + kx*ein_k]; the line's exponent goes to eout[o*P + kx].
 template <int M, int MODE>
-__global__ void __launch_bounds__(FFT_TPB) k_fftq_lines(const longlong2 *__restrict__ in,
+__global__ void __launch_bounds__(FFT_TPB, 2) k_fftq_lines(const longlong2 *__restrict__ in,
                                                         long long in_o, long long in_e, int ne_in,
                                                         const int *__restrict__ ein, long long ein_o,
                                                         long long ein_e, long long ein_k,
@@ -776,21 +779,31 @@ __global__ void __launch_bounds__(FFT_TPB) k_fftq_lines(const longlong2 *__restr
     const int o = live ? (int)(line / P) : 0, kx = live ? (int)(line % P) : 0;
     __syncthreads();
     longlong2 v[V];
-    int ev[V];
     constexpr int R0 = Shape<M>::R0, U0 = (M / R0) / T;
     const longlong2 *src = in + o * in_o + kx;
     const int *esrc = ein + o * ein_o + kx * ein_k;
+    // the line's largest exponent, then the values aligned to it (exponents
+    // read twice rather than held in registers)
+    int emax = FIX_EMPTY;
+#pragma unroll
+    for (int j = 0; j < U0; ++j)
+#pragma unroll
+        for (int m = 0; m < R0; ++m) {
+            const int e = first_index<M>(t, j, m);
+            if (live && e < ne_in) emax = max(emax, __ldg(&esrc[e * ein_e]));
+        }
+    emax = (int)team_max<T>(emax, red);
 #pragma unroll
     for (int j = 0; j < U0; ++j)
 #pragma unroll
         for (int m = 0; m < R0; ++m) {
             const int e = first_index<M>(t, j, m), i = j * R0 + m;
-            const bool ok = live && e < ne_in;
-            v[i] = ok ? src[e * in_e] : make_longlong2(0, 0);
-            ev[i] = ok ? esrc[e * ein_e] : FIX_EMPTY;
+            v[i] = (live && e < ne_in) ? scale2n(src[e * in_e], emax - __ldg(&esrc[e * ein_e]))
+                                       : make_longlong2(0, 0);
         }
-    int E = align_line<M, V>(v, ev, red);
-    longlong2 *s = sl + team * M;
+    const int t0 = normalise_line<M, V>(v, red);
+    int E = t0 == INT_MIN ? FIX_EMPTY : emax + t0;
+    longlong2 *s = sl + team * kLineStride<M>;
     if ((MODE == MODE_FWD || MODE == MODE_ZSOLVE) && 2 * ne_in == M) line_fft<M, INV1, true>(v, s, t, stw);
     else line_fft<M, INV1>(v, s, t, stw);
     if constexpr (MODE == MODE_ZSOLVE) {
@@ -798,27 +811,26 @@ __global__ void __launch_bounds__(FFT_TPB) k_fftq_lines(const longlong2 *__restr
         for (int e = t; e < M; e += T) {
             const int c = min(e, M - e);
             const long long g = live ? gq[((long long)c * P + b) * P + kx] : 0;
-            const longlong2 a = s[e];
+            const longlong2 a = s[sp(e)];
             // floor(a g 2^-62), |a| <= 2^60
-            s[e] = make_longlong2(__mul64hi((long long)((unsigned long long)a.x << 2), g),
+            s[sp(e)] = make_longlong2(__mul64hi((long long)((unsigned long long)a.x << 2), g),
                                   __mul64hi((long long)((unsigned long long)a.y << 2), g));
         }
         __syncthreads();
         load_step<M, R0>(v, s, t);
         __syncthreads();
         // renormalise the product line (all elements share exponent E)
-#pragma unroll
-        for (int i = 0; i < V; ++i) ev[i] = E;
-        E = align_line<M, V>(v, ev, red);
+        const int t1 = normalise_line<M, V>(v, red);
+        E = (t1 == INT_MIN || E == FIX_EMPTY) ? FIX_EMPTY : E + t1;
         line_fft<M, true>(v, s, t, stw);
     }
     if (live && t == 0) eout[(long long)o * P + kx] = E;
     if (!live) return;
     longlong2 *dst = out + o * out_o + kx;
     if constexpr (MODE == MODE_FWD) {
-        for (int e = t; e < nw; e += T) dst[e * out_e] = s[e];
+        for (int e = t; e < nw; e += T) dst[e * out_e] = s[sp(e)];
     } else {
-        for (int w = t; w < nw; w += T) dst[w * out_e] = s[(w + M - 1) & (M - 1)];
+        for (int w = t; w < nw; w += T) dst[w * out_e] = s[sp((w + M - 1) & (M - 1))];
     }
 }
 
@@ -827,7 +839,7 @@ __global__ void __launch_bounds__(FFT_TPB) k_fftq_lines(const longlong2 *__restr
 // = value 2^(E + eoff) scale_dev-or-scale D / m^3, nodes -1..n (eoff = -51
 // for the accumulators, 2^51 per particle; 0 for a double source).
 template <int M>
-__global__ void __launch_bounds__(FFT_TPB) k_fftq_x_inv(const longlong2 *__restrict__ in, int n,
+__global__ void __launch_bounds__(FFT_TPB, 2) k_fftq_x_inv(const longlong2 *__restrict__ in, int n,
                                                         const int *__restrict__ e4,
                                                         const FixScales *__restrict__ fs,
                                                         double scale, const double *scale_dev,
@@ -848,7 +860,6 @@ __global__ void __launch_bounds__(FFT_TPB) k_fftq_x_inv(const longlong2 *__restr
     const longlong2 *ra = in + ((long long)zz * q + yy) * P, *rb = ra + P;
     const int *er = e4 + (long long)zz * P;
     longlong2 v[V];
-    int ev[V];
     constexpr int R0 = Shape<M>::R0, U0 = (M / R0) / T;
     // exponents first: the packed value A + iB of element e comes from kx = e or m - e
     int emax = FIX_EMPTY;
@@ -856,10 +867,8 @@ __global__ void __launch_bounds__(FFT_TPB) k_fftq_x_inv(const longlong2 *__restr
     for (int j = 0; j < U0; ++j)
 #pragma unroll
         for (int m = 0; m < R0; ++m) {
-            const int e = first_index<M>(t, j, m), i = j * R0 + m;
-            const int k = e <= n ? e : M - e;
-            ev[i] = live ? er[k] : FIX_EMPTY;
-            emax = max(emax, ev[i]);
+            const int e = first_index<M>(t, j, m);
+            if (live) emax = max(emax, __ldg(&er[e <= n ? e : M - e]));
         }
     emax = (int)team_max<T>(emax, red);
 #pragma unroll
@@ -869,7 +878,7 @@ __global__ void __launch_bounds__(FFT_TPB) k_fftq_x_inv(const longlong2 *__restr
             const int e = first_index<M>(t, j, m), i = j * R0 + m;
             longlong2 z = make_longlong2(0, 0);
             if (live) {
-                const int d = emax - ev[i];
+                const int d = emax - __ldg(&er[e <= n ? e : M - e]);
                 if (e <= n) {
                     const longlong2 a = scale2n(ra[e], d), b = scale2n(rb[e], d);
                     z = make_longlong2(a.x - b.y, a.y + b.x);
@@ -879,17 +888,17 @@ __global__ void __launch_bounds__(FFT_TPB) k_fftq_x_inv(const longlong2 *__restr
                 }
             }
             v[i] = z;
-            ev[i] = emax;
         }
     // |A + iB| <= |A| + |B| <= 2^61.x: renormalise (now all at exponent emax)
-    const int E = align_line<M, V>(v, ev, red);
-    longlong2 *s = sl + team * M;
+    const int tn = normalise_line<M, V>(v, red);
+    const int E = (tn == INT_MIN || emax == FIX_EMPTY) ? FIX_EMPTY : emax + tn;
+    longlong2 *s = sl + team * kLineStride<M>;
     line_fft<M, true>(v, s, t, stw);
     if (!live) return;
     const double sc = (scale_dev ? *scale_dev : scale) * fs->F * ldexp(1.0, E + eoff);
     double *pa = phi + ((long long)zz * q + yy) * q, *pb = pa + q;
     for (int w = t; w < q; w += T) {
-        const longlong2 z = s[(w + M - 1) & (M - 1)];
+        const longlong2 z = s[sp((w + M - 1) & (M - 1))];
         pa[w] = (double)z.x * sc;
         pb[w] = (double)z.y * sc;
     }
@@ -934,7 +943,7 @@ __global__ void k_green_quant(const double *__restrict__ gh, long long cnt, int 
 static int team_size(int M) { return M == 512 ? 64 : M == 256 ? 16 : M >= 64 ? 8 : 4; }
 
 static size_t smem_bytes(int M) {
-    return (size_t)(M + (FFT_TPB / team_size(M)) * M) * sizeof(double2);
+    return (size_t)(M + (FFT_TPB / team_size(M)) * (M + M / 16)) * sizeof(double2);
 }
 
 template <int M>
@@ -955,6 +964,13 @@ static void set_attrs() {
     cudaFuncSetAttribute(k_fftq_lines<M, MODE_ZSOLVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_fftq_lines<M, MODE_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_fftq_x_inv<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    // the fixed-point passes are latency-bound: room for two blocks per SM
+    cudaFuncSetAttribute(k_fftq_x_fwd<M>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_fftq_x_fwd_d<M>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_fftq_lines<M, MODE_FWD>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_fftq_lines<M, MODE_ZSOLVE>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_fftq_lines<M, MODE_INV>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_fftq_x_inv<M>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
 cudaError_t fft_plan_init(FftPlan *p, int n) {
