@@ -522,14 +522,17 @@ __global__ void k_efix(const double *__restrict__ phi, int nn, int lg, const Box
                        double ky, double kz, const unsigned long long *__restrict__ emax,
                        EFix *__restrict__ out, int *__restrict__ escale, const TrackState *st,
                        const MapCoef *maps) {
-    const FieldCoef c = field_coef(box, kx, ky, kz, st, maps);
-    const FieldConv f0 = field_conv(c.cx, emax[0]), f1 = field_conv(c.cy, emax[1]),
-                    f2 = field_conv(c.cz, emax[2]);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        escale[0] = f0.e;
-        escale[1] = f1.e;
-        escale[2] = f2.e;
+    // the conversion constants once per block (their FP64 setup per thread
+    // had cost as much as the conversions of a thread's nodes)
+    __shared__ FieldConv sconv[3];
+    if (threadIdx.x < 3) {
+        const FieldCoef c = field_coef(box, kx, ky, kz, st, maps);
+        const double cd = threadIdx.x == 0 ? c.cx : threadIdx.x == 1 ? c.cy : c.cz;
+        sconv[threadIdx.x] = field_conv(cd, emax[threadIdx.x]);
+        if (blockIdx.x == 0) escale[threadIdx.x] = sconv[threadIdx.x].e;
     }
+    __syncthreads();
+    const FieldConv f0 = sconv[0], f1 = sconv[1], f2 = sconv[2];
     const long long nodes = 1ll << (3 * lg);
     // the uniform choice outside the loop (a per-node select would also run
     // the scaling path on the FP64 pipe)
