@@ -39,8 +39,9 @@ FP64_PEAK_TFLOPS = 2 * 148 * 2.032e9 * 2 / 1e12
 
 # Algorithmic work per launch of each kernel kind for the roofline of the
 # dominant kernel: (bound, unit, f(n_particles, n_grid) -> amount per launch).
-#   gather_kick_push: read and write the six FP64 coordinates, 96 B/particle
-#   deposit:          read x, y, t, 24 B/particle
+#   gather_kick_push: read and write the six FP64 coordinates and read the
+#                     deposit's three cell codes, 120 B/particle
+#   deposit:          read x, y, t and write their cell codes, 48 B/particle
 # The tracking solve runs in int64 fixed point on the integer pipes; its
 # passes count the spectrum data they must read and write (16-byte complex
 # values, m = 2n, P = n+1):
@@ -50,8 +51,8 @@ FP64_PEAK_TFLOPS = 2 * 148 * 2.032e9 * 2 / 1e12
 #   fft_zsolve: n m P in, the quantised Green's octant (P^3 x 8 B), (n+2) m P out
 #   fft_xinv:   (n+2)^2 P in, phi on (n+2)^3 nodes (8 B) out
 ALGO = {
-    "gather_kick_push": ("hbm", "GB/s", lambda npart, n: 96.0 * npart),
-    "deposit": ("hbm", "GB/s", lambda npart, n: 24.0 * npart),
+    "gather_kick_push": ("hbm", "GB/s", lambda npart, n: 120.0 * npart),
+    "deposit": ("hbm", "GB/s", lambda npart, n: 48.0 * npart),
     "fft_zsolve": ("hbm", "GB/s", lambda npart, n: 16.0 * (n + 1) * 2 * n * (2 * n + 2)
                    + 8.0 * (n + 1) ** 3),
     "fft_yz": ("hbm", "GB/s", lambda npart, n: 0.5 * 16.0 * (n + 1) * (

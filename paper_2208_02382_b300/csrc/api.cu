@@ -86,7 +86,8 @@ int32_t bx_destroy(bx_ctx *ctx) {
                     ctx->gtable, ctx->st, ctx->tmp_box, ctx->status, ctx->log,
                     ctx->mom_partial, ctx->maps, ctx->efix, ctx->emax, ctx->escale,
                     ctx->dev_ptrs, ctx->keys, ctx->counts, ctx->offs, ctx->sums, ctx->id_scr,
-                    ctx->scr[0], ctx->scr[1], ctx->scr[2], ctx->scr[3], ctx->scr[4], ctx->scr[5]};
+                    ctx->scr[0], ctx->scr[1], ctx->scr[2], ctx->scr[3], ctx->scr[4], ctx->scr[5],
+                    ctx->cells};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     fft_plan_free(&ctx->plan);
@@ -216,6 +217,7 @@ int32_t track_impl(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t fi
     const double q_macro = r.sign * std::fabs(beam->bunch_charge_C) / (double)beam->n;
     const bool binning = beam->id != nullptr;
     if (binning && (rc = ensure_sort_scratch(ctx, beam->n))) return rc;
+    if ((rc = ensure_cells(ctx, beam->n))) return rc;
     // Device-driven kicks: the box rule kernel of each kick sets the gates
     // (Green's function rebuild, deposit of the current positions, re-binning,
     // deposit for a next kick) that the later kernels of the kick read, and the
@@ -226,14 +228,14 @@ int32_t track_impl(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t fi
        "call init");
     if (binning) CK(sort_set_pointers(c, ctx->scr, ctx->dev_ptrs, s), "sort pointers");
     CK(launch_track_prologue(c, beam->n, r.bg, &ctx->st->box, ctx->n, ctx->maps, ctx->acc_hi,
-                             ctx->acc_lo, ctx->st, ctx->status, s, ctx->shape),
+                             ctx->acc_lo, ctx->st, ctx->status, s, ctx->shape, ctx->cells),
        "prologue");
     const KickArgs ka{ctx, c, beam->id, beam->n, r.bg, binning};
     bool use_graph = !ctx->graphs_off && !profiler_timing(ctx->prof) && !diag;
     if (use_graph) {
         bool same = ctx->kick_exec && ctx->graph_n == beam->n && ctx->graph_id == beam->id &&
                     ctx->graph_bg == r.bg && ctx->graph_maps == ctx->maps &&
-                    ctx->graph_sort_n == ctx->sort_n;
+                    ctx->graph_sort_n == ctx->sort_n && ctx->graph_cells == ctx->cells;
         for (int q = 0; q < 6 && same; ++q) same = ctx->graph_c[q] == c[q];
         if (!same) {
             if (ctx->kick_exec) cudaGraphExecDestroy(ctx->kick_exec);
@@ -251,6 +253,7 @@ int32_t track_impl(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t fi
                 ctx->graph_bg = r.bg;
                 ctx->graph_maps = ctx->maps;
                 ctx->graph_sort_n = ctx->sort_n;
+                ctx->graph_cells = ctx->cells;
             }
         }
     }

@@ -192,17 +192,20 @@ cudaError_t launch_call_init(TrackState *st, int nkicks, double q_macro, int sor
                              bool fused_prologue = false);
 // First half map of a tracking call (table entry 0) with the min/max keys and,
 // when a box was kept from the previous call, the first kick's deposit into it.
+// `cells` (3 n, or null): the deposits store each particle's cells there and
+// the gather of the same kick reads them instead of recomputing them.
 cudaError_t launch_track_prologue(double *const c[6], int64_t n, double betagamma, const Box *box,
                                   int nn, const MapCoef *maps, unsigned long long *acc_hi,
                                   unsigned long long *acc_lo, TrackState *st, int32_t *status,
-                                  cudaStream_t s, int shape);
+                                  cudaStream_t s, int shape, unsigned long long *cells = nullptr);
 cudaError_t launch_zero_acc(unsigned long long *a, unsigned long long *b, int nn, const int *gate,
                             cudaStream_t s);
 cudaError_t launch_track_particles(double *const c[6], int64_t n, double betagamma,
                                    const Box *box, int nn, const EFix *ef, const int *escale,
                                    const MapCoef *maps, unsigned long long *acc_hi,
                                    unsigned long long *acc_lo, TrackState *st, int32_t *status,
-                                   cudaStream_t s, int part = 3, int shape = 1);
+                                   cudaStream_t s, int part = 3, int shape = 1,
+                                   unsigned long long *cells = nullptr);
 cudaError_t launch_box_rule_graph(TrackState *st, int nn, long long *log, int64_t cap,
                                   cudaGraphConditionalHandle hg, cudaGraphConditionalHandle hs,
                                   cudaGraphConditionalHandle hd, cudaGraphConditionalHandle hn,
@@ -217,7 +220,8 @@ cudaError_t launch_track_particles_oop(double *const cin[6], double *const cout[
                                        TrackState *st, int32_t *status, cudaStream_t s, int shape = 1);
 cudaError_t launch_track_deposit(double *const c[6], int64_t n, double betagamma, const Box *box,
                                  int nn, unsigned long long *acc_hi, unsigned long long *acc_lo,
-                                 TrackState *st, int32_t *status, cudaStream_t s, int shape = 1);
+                                 TrackState *st, int32_t *status, cudaStream_t s, int shape = 1,
+                                 unsigned long long *cells = nullptr);
 int map_kind(const MapCoef &m);
 // sort.cu
 int sort_brick_edge(int nn, int be_opt);

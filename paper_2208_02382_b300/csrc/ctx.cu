@@ -238,6 +238,20 @@ int32_t ensure_maps(bx_ctx *ctx, size_t count) {
     return BX_OK;
 }
 
+// The cell codes of n particles (deposit -> gather), allocated on the first
+// call for a larger n.
+int32_t ensure_cells(bx_ctx *ctx, int64_t n) {
+    if (n <= ctx->cells_n) return BX_OK;
+    cudaDeviceSynchronize();
+    if (ctx->cells) cudaFree(ctx->cells);
+    ctx->cells = nullptr;
+    ctx->cells_n = 0;
+    CK(cudaMalloc(&ctx->cells, (size_t)3 * n * sizeof(unsigned long long)), "cell codes");
+    CK(cudaMemset(ctx->cells, 0, (size_t)3 * n * sizeof(unsigned long long)), "cell codes");
+    ctx->cells_n = n;
+    return BX_OK;
+}
+
 // Binning scratch for n particles, allocated on the first call for a larger n.
 int32_t ensure_sort_scratch(bx_ctx *ctx, int64_t n) {
     const int nb = sort_bricks(ctx->n, sort_brick_edge(ctx->n, ctx->bin_edge));

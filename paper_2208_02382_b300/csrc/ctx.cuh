@@ -41,6 +41,10 @@ struct bx_ctx {
     int *escale = nullptr;                 // fixed-point exponents
     // particle binning scratch, sized for sort_n particles
     int64_t sort_n = 0;
+    // each particle's cells as the deposit of the current kick computed them
+    // (3 n codes), read by that kick's gather
+    unsigned long long *cells = nullptr;
+    int64_t cells_n = 0;
     int *keys = nullptr;
     long long *counts = nullptr, *offs = nullptr, *sums = nullptr, *id_scr = nullptr;
     double *scr[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -57,6 +61,7 @@ struct bx_ctx {
     double graph_bg = 0.0;
     MapCoef *graph_maps = nullptr;         // map table and sort scratch the graph was built with
     int64_t graph_sort_n = -1;
+    unsigned long long *graph_cells = nullptr;
     cudaStream_t cap_stream = nullptr, body_stream = nullptr;
     bool graphs_off = false;               // the graph path failed once: plain launches
     Profiler *prof = nullptr;
@@ -121,6 +126,7 @@ Box explicit_box(const double lo[3], const double hi[3], int n, double betagamma
 int32_t ensure_green(bx_ctx *ctx, const double h[3], cudaStream_t s);
 int32_t ensure_maps(bx_ctx *ctx, size_t count);
 int32_t ensure_sort_scratch(bx_ctx *ctx, int64_t n);
+int32_t ensure_cells(bx_ctx *ctx, int64_t n);
 int32_t ensure_moment_scratch(bx_ctx *ctx, int64_t n);
 int32_t read_state(bx_ctx *ctx, TrackState *h, cudaStream_t s);
 void init_state(TrackState *h);

@@ -230,11 +230,13 @@ __device__ void box_rule_body(TrackState *st, int nn, long long *log, int64_t ca
         // deposit for this kick unless it is in the accumulators already: the
         // previous kick's B, or (first kick of a call) the fused prologue into
         // the box that the rule kept
-        st->deposit_gate = (finite && (need || (k == 0 && !st->pro_dep))) ? 1 : 0;
         // re-binning on the global kick count (it carries over between calls,
         // so tracking one kick per call re-bins every sort_interval kicks too)
         st->sort_gate =
             (finite && st->sort_interval > 0 && st->kick % st->sort_interval == 0) ? 1 : 0;
+        // after a re-binning the kick deposits again: the charge is the same
+        // (integer sums), but the stored cells must follow the new order
+        st->deposit_gate = (finite && (need || st->sort_gate || (k == 0 && !st->pro_dep))) ? 1 : 0;
         st->next_gate = (finite && k + 1 < st->nkicks_call) ? 1 : 0;
         st->exact_u = box_far_offset(st->box) ? 1 : 0;
         st->rho_scale = st->q_macro / (st->box.h[0] * st->box.h[1] * st->box.h[2]);
@@ -595,7 +597,18 @@ struct PartArgs {
     const MapCoef *row;                // MAP_TABLE: this kick's entry (set by the kernel)
     const TrackState *dst;             // device-driven: exact_u and k from here
     int shape;                         // particle shape: 1 CIC, 2 TSC
+    // cells of the deposit's positions (3 arrays of n, cell_code): DEP
+    // stores them when set, a UL gather loads them instead of recomputing
+    unsigned long long *cell_out;
+    const unsigned long long *cell_in;
 };
+
+// A particle's cell (CIC) or nearest node (TSC) and 53-bit offset in one
+// dimension as the deposit computed them, with the particle's outside flag:
+// outside << 63 | cell << 53 | F (F <= 2^52, cell < 1024).
+__device__ __forceinline__ unsigned long long cell_code(int cell, unsigned long long F, bool outside) {
+    return ((unsigned long long)outside << 63) | ((unsigned long long)cell << 53) | F;
+}
 
 // Node and offset for the TSC shape (particle shape 2): u limited to
 // [1/2, n - 3/2], nearest node i = floor(u + 1/2) limited to [1, n-2], and
@@ -656,7 +669,7 @@ bool box_needs_exact_u(const Box &b) { return box_far_offset(b); }
 // CIC instances fit 64 registers and (with 52 KB of shared memory for DEP) run 4 blocks
 // per SM; TSC instances and the map-plus-deposit prologue keep 3 (they would
 // spill at 64).
-template <int MK, bool GATHER, bool DEP, bool MM, int SH>
+template <int MK, bool GATHER, bool DEP, bool MM, int SH, bool UL = false>
 __global__ void __launch_bounds__(TPB, (SH == 1 && !(DEP && MK != MAP_NONE)) ? 4 : 3)
     k_particles(PartArgs a) {
     if (a.gate && *a.gate == 0) return;
@@ -707,14 +720,37 @@ __global__ void __launch_bounds__(TPB, (SH == 1 && !(DEP && MK != MAP_NONE)) ? 4
                 int c0, c1, c2;
                 unsigned long long G0, G1, G2;
                 bool out0 = false;
-                const double u0 = EX ? (x - lo0) * ih0 : fma(x, ih0, o0);
-                const double u1 = EX ? (y - lo1) * ih1 : fma(y, ih1, o1);
-                const double u2 = EX ? (__dmul_rn(a.nbg, t) - lo2) * ih2 : fma(t, tz, o2);
+                if constexpr (UL) {
+                    // the cells the deposit of these positions into this box computed
+                    constexpr unsigned long long FM = (1ull << 53) - 1;
+                    const unsigned long long k0 = a.cell_in[p], k1 = a.cell_in[a.n + p],
+                                             k2 = a.cell_in[2 * a.n + p];
+                    out0 = ((k0 | k1 | k2) >> 63) != 0;
+                    // limited to the shape's range (as the deposit's are), so that a
+                    // kick halted before any deposit still reads inside the field
+                    constexpr int CLO = SH == 2 ? 1 : 0;
+                    c0 = min(max((int)((k0 >> 53) & 1023), CLO), nn - 2);
+                    c1 = min(max((int)((k1 >> 53) & 1023), CLO), nn - 2);
+                    c2 = min(max((int)((k2 >> 53) & 1023), CLO), nn - 2);
+                    G0 = k0 & FM;
+                    G1 = k1 & FM;
+                    G2 = k2 & FM;
+                } else {
+                    const double u0 = EX ? (x - lo0) * ih0 : fma(x, ih0, o0);
+                    const double u1 = EX ? (y - lo1) * ih1 : fma(y, ih1, o1);
+                    const double u2 = EX ? (__dmul_rn(a.nbg, t) - lo2) * ih2 : fma(t, tz, o2);
+                    if constexpr (SH == 2) {
+                        tsc_node(u0, nn, c0, G0, out0);
+                        tsc_node(u1, nn, c1, G1, out0);
+                        tsc_node(u2, nn, c2, G2, out0);
+                    } else {
+                        cell_frac(u0, nn, c0, G0, out0);
+                        cell_frac(u1, nn, c1, G1, out0);
+                        cell_frac(u2, nn, c2, G2, out0);
+                    }
+                }
                 long long comp[3];
                 if constexpr (SH == 2) {
-                    tsc_node(u0, nn, c0, G0, out0);
-                    tsc_node(u1, nn, c1, G1, out0);
-                    tsc_node(u2, nn, c2, G2, out0);
                     outside |= out0;
                     Frac wx[3], wy[3], wz[3];
                     tsc_weights(G0, wx);
@@ -752,9 +788,6 @@ __global__ void __launch_bounds__(TPB, (SH == 1 && !(DEP && MK != MAP_NONE)) ? 4
                     comp[1] = gz[1];
                     comp[2] = gz[2];
                 } else {
-                    cell_frac(u0, nn, c0, G0, out0);
-                    cell_frac(u1, nn, c1, G1, out0);
-                    cell_frac(u2, nn, c2, G2, out0);
                     const Frac F0 = split26(G0), F1 = split26(G1), F2 = split26(G2);
                     outside |= out0;
                     // CIC interpolation in lerp form: along x on the four (y, z) edges
@@ -825,6 +858,11 @@ __global__ void __launch_bounds__(TPB, (SH == 1 && !(DEP && MK != MAP_NONE)) ? 4
                         cell_frac(u0, nn, c0, F0, out1);
                         cell_frac(u1, nn, c1, F1, out1);
                         cell_frac(u2, nn, c2, F2, out1);
+                    }
+                    if (a.cell_out) {
+                        a.cell_out[p] = cell_code(c0, F0, out1);
+                        a.cell_out[a.n + p] = cell_code(c1, F1, out1);
+                        a.cell_out[2 * a.n + p] = cell_code(c2, F2, out1);
                     }
                     if (out1 && a.flag_outside) outside = true;  // box not containing the bunch
                     if (!out1) {  // particles outside are left out: the box rule then regrids
@@ -943,21 +981,21 @@ static size_t particles_smem(bool dep) {
     return dep ? (size_t)(3 * CHUNK + CHUNK / 2 + TILE_CAP) * sizeof(unsigned long long) : 0;
 }
 
-template <int MK, bool G, bool D, bool M, int SH>
+template <int MK, bool G, bool D, bool M, int SH, bool UL = false>
 static cudaError_t launch_pk_sh(const PartArgs &a, cudaStream_t s, int kid) {
     const size_t sm = particles_smem(D);
     if (D)
-        cudaFuncSetAttribute(k_particles<MK, G, D, M, SH>,
+        cudaFuncSetAttribute(k_particles<MK, G, D, M, SH, UL>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const unsigned blocks = (unsigned)((a.n + CHUNK - 1) / CHUNK);
-    BT_LAUNCH(kid, s, k_particles<MK, G, D, M, SH><<<blocks, TPB, sm, s>>>(a));
+    BT_LAUNCH(kid, s, k_particles<MK, G, D, M, SH, UL><<<blocks, TPB, sm, s>>>(a));
     return cudaGetLastError();
 }
 
-template <int MK, bool G, bool D, bool M>
+template <int MK, bool G, bool D, bool M, bool UL = false>
 static cudaError_t launch_pk(const PartArgs &a, cudaStream_t s, int kid) {
-    return a.shape == 2 ? launch_pk_sh<MK, G, D, M, 2>(a, s, kid)
-                        : launch_pk_sh<MK, G, D, M, 1>(a, s, kid);
+    return a.shape == 2 ? launch_pk_sh<MK, G, D, M, 2, UL>(a, s, kid)
+                        : launch_pk_sh<MK, G, D, M, 1, UL>(a, s, kid);
 }
 
 static PartArgs part_args(double *const c[6], int64_t n, double betagamma, const Box *box, int nn,
@@ -1019,7 +1057,7 @@ cudaError_t launch_track_particles(double *const c[6], int64_t n, double betagam
                                    const Box *box, int nn, const EFix *ef, const int *escale,
                                    const MapCoef *maps, unsigned long long *acc_hi,
                                    unsigned long long *acc_lo, TrackState *st, int32_t *status,
-                                   cudaStream_t s, int part, int shape) {
+                                   cudaStream_t s, int part, int shape, unsigned long long *cells) {
     if (n <= 0) return cudaSuccess;
     PartArgs a = part_args(c, n, betagamma, box, nn, shape);
     a.ef = ef;
@@ -1031,11 +1069,20 @@ cudaError_t launch_track_particles(double *const c[6], int64_t n, double betagam
     a.maps = maps;
     a.dst = st;
     cudaError_t e = cudaSuccess;
-    if (part & 1) e = launch_pk<MAP_TABLE, true, false, false>(a, s, K_GATHER);
+    if (part & 1) {
+        if (cells) {
+            a.cell_in = cells;   // the cells this kick's deposit computed
+            e = launch_pk<MAP_TABLE, true, false, false, true>(a, s, K_GATHER);
+            a.cell_in = nullptr;
+        } else {
+            e = launch_pk<MAP_TABLE, true, false, false>(a, s, K_GATHER);
+        }
+    }
     if (e != cudaSuccess || !(part & 2)) return e;
     e = launch_zero_acc(acc_hi, acc_lo, nn, &st->next_gate, s);
     if (e != cudaSuccess) return e;
     a.gate = &st->next_gate;
+    a.cell_out = cells;
     return launch_pk<MAP_NONE, false, true, true>(a, s, K_DEPOSIT);
 }
 
@@ -1081,7 +1128,7 @@ cudaError_t launch_track_particles_oop(double *const cin[6], double *const cout[
 cudaError_t launch_track_prologue(double *const c[6], int64_t n, double betagamma, const Box *box,
                                   int nn, const MapCoef *maps, unsigned long long *acc_hi,
                                   unsigned long long *acc_lo, TrackState *st, int32_t *status,
-                                  cudaStream_t s, int shape) {
+                                  cudaStream_t s, int shape, unsigned long long *cells) {
     cudaError_t e = launch_zero_acc(acc_hi, acc_lo, nn, &st->pro_dep, s);
     if (e != cudaSuccess || n <= 0) return e;
     PartArgs a = part_args(c, n, betagamma, box, nn, shape);
@@ -1092,13 +1139,15 @@ cudaError_t launch_track_prologue(double *const c[6], int64_t n, double betagamm
     a.acc_lo = acc_lo;
     a.status = status;
     a.dep_if = &st->pro_dep;
+    a.cell_out = cells;
     return launch_pk<MAP_TABLE, false, true, true>(a, s, K_PUSH);
 }
 
 // Device-driven deposit of the current positions when the box rule asks for it.
 cudaError_t launch_track_deposit(double *const c[6], int64_t n, double betagamma, const Box *box,
                                  int nn, unsigned long long *acc_hi, unsigned long long *acc_lo,
-                                 TrackState *st, int32_t *status, cudaStream_t s, int shape) {
+                                 TrackState *st, int32_t *status, cudaStream_t s, int shape,
+                                 unsigned long long *cells) {
     cudaError_t e = launch_zero_acc(acc_hi, acc_lo, nn, &st->deposit_gate, s);
     if (e != cudaSuccess || n <= 0) return e;
     PartArgs a = part_args(c, n, betagamma, box, nn, shape);
@@ -1108,6 +1157,7 @@ cudaError_t launch_track_deposit(double *const c[6], int64_t n, double betagamma
     a.gate = &st->deposit_gate;
     a.dst = st;
     a.flag_outside = 1;
+    a.cell_out = cells;
     return launch_pk<MAP_NONE, false, true, false>(a, s, K_DEPOSIT);
 }
 
