@@ -217,7 +217,7 @@ int32_t track_impl(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t fi
     const double q_macro = r.sign * std::fabs(beam->bunch_charge_C) / (double)beam->n;
     const bool binning = beam->id != nullptr;
     if (binning && (rc = ensure_sort_scratch(ctx, beam->n))) return rc;
-    if ((rc = ensure_cells(ctx, beam->n))) return rc;
+    if (ctx->shape == 1 && (rc = ensure_cells(ctx, beam->n))) return rc;
     // Device-driven kicks: the box rule kernel of each kick sets the gates
     // (Green's function rebuild, deposit of the current positions, re-binning,
     // deposit for a next kick) that the later kernels of the kick read, and the
@@ -228,7 +228,7 @@ int32_t track_impl(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t fi
        "call init");
     if (binning) CK(sort_set_pointers(c, ctx->scr, ctx->dev_ptrs, s), "sort pointers");
     CK(launch_track_prologue(c, beam->n, r.bg, &ctx->st->box, ctx->n, ctx->maps, ctx->acc_hi,
-                             ctx->acc_lo, ctx->st, ctx->status, s, ctx->shape, ctx->cells),
+                             ctx->acc_lo, ctx->st, ctx->status, s, ctx->shape, shared_cells(ctx)),
        "prologue");
     const KickArgs ka{ctx, c, beam->id, beam->n, r.bg, binning};
     bool use_graph = !ctx->graphs_off && !profiler_timing(ctx->prof) && !diag;

@@ -264,9 +264,6 @@ struct FftPlan {
 cudaError_t fft_plan_init(FftPlan *p, int n);
 void fft_plan_free(FftPlan *p);
 cudaError_t solve_rho_to_phi(const FftPlan *p, const double *rho, double *phi, cudaStream_t s);
-cudaError_t solve_acc_to_phi(const FftPlan *p, const unsigned long long *acc_hi,
-                             const unsigned long long *acc_lo, double scale, double *phi,
-                             cudaStream_t s, const double *scale_dev = nullptr);
 cudaError_t solve_acc_to_phi_fixed(const FftPlan *p, const unsigned long long *acc_hi,
                                    const unsigned long long *acc_lo, double scale, double *phi,
                                    cudaStream_t s, const double *scale_dev);

@@ -127,6 +127,12 @@ int32_t ensure_green(bx_ctx *ctx, const double h[3], cudaStream_t s);
 int32_t ensure_maps(bx_ctx *ctx, size_t count);
 int32_t ensure_sort_scratch(bx_ctx *ctx, int64_t n);
 int32_t ensure_cells(bx_ctx *ctx, int64_t n);
+// The cell codes the deposit hands to the gather, or null (the gather computes
+// them): shared for CIC; for TSC the deposit's extra stores cost more than the
+// gather's own nearest-node computation.
+inline unsigned long long *shared_cells(bx_ctx *ctx) {
+    return ctx->shape == 1 ? ctx->cells : nullptr;
+}
 int32_t ensure_moment_scratch(bx_ctx *ctx, int64_t n);
 int32_t read_state(bx_ctx *ctx, TrackState *h, cudaStream_t s);
 void init_state(TrackState *h);

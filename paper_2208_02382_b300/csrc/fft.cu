@@ -305,16 +305,14 @@ __device__ __forceinline__ void load_twiddles(C *stw, const C *__restrict__ tw) 
 //   S4[zz][yy][kx] zz, yy < n+2           (after the inverse y pass)
 // Green's spectrum: Gh[kz][ky][kx], kx, ky, kz <= n (the even octant).
 
-// Source of the x pass: rho as doubles, the fixed-point deposit accumulators
-// (rho = scale * (hi * 2^31 + lo) * 2^-51), or the even extension of the
-// Green's function octant table (full m^3 input, for its spectrum).
-enum XSource { SRC_RHO = 0, SRC_ACC = 1, SRC_GREEN = 2 };
+// Source of the x pass: a cube of doubles (rho, or the adjoint's source), or
+// the even extension of the Green's function octant table (full m^3 input,
+// for its spectrum).  (The tracking solve from the deposit accumulators runs
+// in block floating point, below.)
+enum XSource { SRC_RHO = 0, SRC_GREEN = 2 };
 
 struct XIn {
     const double *rho;
-    const unsigned long long *acc_hi, *acc_lo;
-    double scale;
-    const double *scale_ptr;  // if set, the scale is read from the device
     const double *g;
 };
 
@@ -325,9 +323,7 @@ __device__ __forceinline__ double x_value(const XIn &in, int n, int nin, int x, 
         return in.g[((long long)c * q + b) * q + a];
     } else {
         if (x >= nin) return 0.0;
-        const long long i = ((long long)z * nin + y) * nin + x;
-        if constexpr (SRC == SRC_RHO) return in.rho[i];
-        return in.scale * (((double)in.acc_hi[i] * 2147483648.0 + (double)in.acc_lo[i]) * 0x1p-51);
+        return in.rho[((long long)z * nin + y) * nin + x];
     }
 }
 
@@ -343,7 +339,6 @@ __global__ void __launch_bounds__(FFT_TPB) k_fft_x_fwd(XIn in, int n, int ny, in
                                                        double2 *__restrict__ out,
                                                        const int *gate) {
     if (gate && *gate == 0) return;
-    if (SRC == SRC_ACC && in.scale_ptr) in.scale = *in.scale_ptr;
     const int nin = ny;
     constexpr int T = Shape<M>::T, LPB = FFT_TPB / T, V = M / T;
     extern __shared__ double2 smem[];
@@ -950,7 +945,6 @@ template <int M>
 static void set_attrs() {
     const int sm = (int)smem_bytes(M);
     cudaFuncSetAttribute(k_fft_x_fwd<M, SRC_RHO>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    cudaFuncSetAttribute(k_fft_x_fwd<M, SRC_ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_fft_x_fwd<M, SRC_GREEN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_fft_lines<M, MODE_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_fft_lines<M, MODE_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -1047,12 +1041,8 @@ static cudaError_t solve_m(const FftPlan *p, const XIn &in, int src, int nin, do
     double2 *S1 = p->buf, *S2 = p->buf2, *S3 = p->buf, *S4 = p->buf2;
     // x: rows y, z < nin in pairs -> S1[z][y][kx]
     const long long xpairs = (long long)(nin / 2) * nin;
-    if (src == SRC_ACC)
-        BT_LAUNCH(K_FFT_X, s, k_fft_x_fwd<M, SRC_ACC><<<blocks_lines(xpairs, M), FFT_TPB, sm, s>>>(
-                                  in, n, nin, nin, p->tw, S1, nullptr));
-    else
-        BT_LAUNCH(K_FFT_X, s, k_fft_x_fwd<M, SRC_RHO><<<blocks_lines(xpairs, M), FFT_TPB, sm, s>>>(
-                                  in, n, nin, nin, p->tw, S1, nullptr));
+    BT_LAUNCH(K_FFT_X, s, k_fft_x_fwd<M, SRC_RHO><<<blocks_lines(xpairs, M), FFT_TPB, sm, s>>>(
+                              in, n, nin, nin, p->tw, S1, nullptr));
     // y: lines (z < nin, kx), inputs y < nin -> S2[z][ky][kx], all ky
     BT_LAUNCH(K_FFT_YZ, s, k_fft_lines<M, MODE_FWD><<<blocks_lines(nin * P, M), FFT_TPB, sm, s>>>(
                                S1, nin * P, P, nin, S2, M * P, P, M, nin, (int)P, nullptr, nullptr,
@@ -1166,17 +1156,6 @@ cudaError_t solve_adjoint_shifted(const FftPlan *p, const double *phibar, double
     XIn in{};
     in.rho = phibar;
     return solve_any(p, in, SRC_RHO, p->n + 2, out, s);
-}
-
-cudaError_t solve_acc_to_phi(const FftPlan *p, const unsigned long long *acc_hi,
-                             const unsigned long long *acc_lo, double scale, double *phi,
-                             cudaStream_t s, const double *scale_dev) {
-    XIn in{};
-    in.acc_hi = acc_hi;
-    in.acc_lo = acc_lo;
-    in.scale = scale;
-    in.scale_ptr = scale_dev;
-    return solve_any(p, in, SRC_ACC, p->n, phi, s);
 }
 
 static cudaError_t solve_fix_dispatch(const FftPlan *p, const unsigned long long *acc_hi,

@@ -35,7 +35,7 @@ cudaError_t kick_sort(const KickArgs &k, cudaStream_t s) {
 cudaError_t kick_deposit(const KickArgs &k, cudaStream_t s) {
     bx_ctx *ctx = k.ctx;
     return launch_track_deposit(k.c, k.n, k.bg, &ctx->st->box, ctx->n, ctx->acc_hi, ctx->acc_lo,
-                                ctx->st, ctx->status, s, ctx->shape, ctx->cells);
+                                ctx->st, ctx->status, s, ctx->shape, shared_cells(ctx));
 }
 
 cudaError_t kick_solve_field_push(const KickArgs &k, cudaStream_t s) {
@@ -48,7 +48,7 @@ cudaError_t kick_solve_field_push(const KickArgs &k, cudaStream_t s) {
     if (e == cudaSuccess)
         e = launch_track_particles(k.c, k.n, k.bg, &ctx->st->box, ctx->n, ctx->efix, ctx->escale,
                                    ctx->maps, ctx->acc_hi, ctx->acc_lo, ctx->st, ctx->status, s, 1,
-                                   ctx->shape, ctx->cells);
+                                   ctx->shape, shared_cells(ctx));
     return e;
 }
 
@@ -56,7 +56,7 @@ cudaError_t kick_next_deposit(const KickArgs &k, cudaStream_t s) {
     bx_ctx *ctx = k.ctx;
     return launch_track_particles(k.c, k.n, k.bg, &ctx->st->box, ctx->n, ctx->efix, ctx->escale,
                                   ctx->maps, ctx->acc_hi, ctx->acc_lo, ctx->st, ctx->status, s, 2,
-                                  ctx->shape, ctx->cells);
+                                  ctx->shape, shared_cells(ctx));
 }
 
 // Plain launches of one kick (gated kernels return at once when not needed).
@@ -288,7 +288,8 @@ int32_t bx_batch_create(bx_batch **out, int32_t count, bx_ctx *const *ctxs,
         const bool binning = beam->id != nullptr;
         if (e == cudaSuccess && binning && ensure_sort_scratch(ctx, beam->n) != BX_OK)
             e = cudaErrorMemoryAllocation;
-        if (e == cudaSuccess && ensure_cells(ctx, beam->n) != BX_OK) e = cudaErrorMemoryAllocation;
+        if (e == cudaSuccess && ctx->shape == 1 && ensure_cells(ctx, beam->n) != BX_OK)
+            e = cudaErrorMemoryAllocation;
         if (e == cudaSuccess && binning) e = sort_set_pointers(beam->coord, ctx->scr, ctx->dev_ptrs, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) break;

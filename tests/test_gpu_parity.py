@@ -269,6 +269,25 @@ def test_track_degenerate_bunches(bt, npart):
         assert trk.regrid_log() == otr.regrid_log
 
 
+def test_one_context_tracks_beams_of_different_sizes(bt):
+    """A context keeps per-particle scratch (the deposit's cell codes, the
+    binning buffers) and a captured kick graph; a smaller and then a larger
+    bunch through the same context reuse or reallocate them, and each call
+    matches the oracle."""
+    w = bg.workload("fodo_1e4_32")
+    trk = bt.Tracker(16)
+    for npart, seed in ((6_000, 11), (2_500, 12), (9_001, 13)):
+        c = bg.gaussian6d(npart, seed=seed)
+        beam = gpu_beam(bt, c, w.species, w.bunch_charge_C)
+        trk.reset()
+        trk.track(beam, w.lattice, 0, 30)
+        trk.sync()
+        otr = tr.Tracker(oracle_ref(w.species), w.bunch_charge_C, 16)
+        want = otr.track(c, w.lattice, 0, 30)
+        assert coord_rel_err(to_np(beam), want) <= REL_TOL
+        assert trk.regrid_log() == otr.regrid_log
+
+
 def test_track_is_bitwise_reproducible(bt):
     w = bg.workload("fodo_1e4_32")
     c = w.particles()
