@@ -177,6 +177,9 @@ int32_t bx_reset(bx_ctx *ctx);
  * extent fell below half the box; the new box is centred on the bunch with
  * half-width 0.55 * extent; the Green's function is rebuilt when h changes.
  * The bunch is left at a slice boundary.  nkicks = -1 tracks to the end.
+ * Each kick's solve is the one of bx_solve computed in block floating point
+ * (int64 values, one exponent per FFT line; its kicks agree with an FP64
+ * solve's to about 1e-14 of their size).
  * BX_BAD_ARG if first_kick/nkicks fall outside the schedule or an element is
  * invalid.  Non-finite coordinates are reported as BX_NONFINITE by bx_sync. */
 int32_t bx_track(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lattice,
@@ -221,8 +224,8 @@ int32_t bx_deposit(bx_ctx *ctx, const bx_beam *beam, bx_grid *grid, void *stream
  * Poisson solve): phi = G (*) rho as the aperiodic convolution computed on the
  * zero-padded (2n)^3 grid by FFT (Hockney), with G the cell-integrated
  * Green's function (Qiang et al. 2006) built in double-double precision for
- * the grid's h.  Reads grid->rho and grid->h, writes grid->phi on nodes
- * -1..n. */
+ * the grid's h; FFTs in FP64.  Reads grid->rho and grid->h, writes grid->phi
+ * on nodes -1..n. */
 int32_t bx_solve(bx_ctx *ctx, bx_grid *grid, void *stream);
 
 /* Field gather and momentum kick over a slice ds > 0 (Model Assumptions:
