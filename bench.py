@@ -238,7 +238,7 @@ def run_reference(args, w):
     c = w.particles(sample)
     lat = repeated_lattice(w, args.warmup + args.steps + 1)
     t = tr.Tracker(ref, w.bunch_charge_C, w.n_grid)
-    c = t.track(c, lat, 0, max(1, min(args.warmup, 1)))
+    c = t.track(c, lat, 0, args.warmup)   # the first warm kick builds the Green's function
     start = t.kick_index
     budget = 150.0
     t0 = time.perf_counter()
@@ -251,7 +251,7 @@ def run_reference(args, w):
     dt = time.perf_counter() - t0
     value = sample * steps / dt
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
-            "warmup": 1, "ms_per_step": dt / steps * 1e3, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": dt / steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
             "config": {"workload": w.name, "particles": w.n_particles, "grid": w.n_grid,

@@ -667,10 +667,11 @@ bool box_needs_exact_u(const Box &b) { return box_far_offset(b); }
 // Without GATHER, a map MK (MAP_TABLE: entry 0 at a call's start) is applied
 // and stored before DEP/MM (a tracking call's fused prologue).
 // CIC instances fit 64 registers and (with 52 KB of shared memory for DEP) run 4 blocks
-// per SM; TSC instances and the map-plus-deposit prologue keep 3 (they would
-// spill at 64).
+// per SM; the CIC gather that loads the deposit's cells fits 48 and runs 5 (its
+// field loads are latency-bound); TSC instances and the map-plus-deposit
+// prologue keep 3 (they would spill at 64).
 template <int MK, bool GATHER, bool DEP, bool MM, int SH, bool UL = false>
-__global__ void __launch_bounds__(TPB, (SH == 1 && !(DEP && MK != MAP_NONE)) ? 4 : 3)
+__global__ void __launch_bounds__(TPB, (UL && SH == 1) ? 5 : (SH == 1 && !(DEP && MK != MAP_NONE)) ? 4 : 3)
     k_particles(PartArgs a) {
     if (a.gate && *a.gate == 0) return;
     if (a.dst) a.exact_u = a.dst->exact_u;
