@@ -201,7 +201,7 @@ template <> struct Shape<16> { static constexpr int S = 2, R0 = 4, R1 = 4, R2 = 
 template <> struct Shape<32> { static constexpr int S = 2, R0 = 8, R1 = 4, R2 = 1, T = 4; };
 template <> struct Shape<64> { static constexpr int S = 2, R0 = 8, R1 = 8, R2 = 1, T = 8; };
 template <> struct Shape<128> { static constexpr int S = 2, R0 = 16, R1 = 8, R2 = 1, T = 8; };
-template <> struct Shape<256> { static constexpr int S = 2, R0 = 16, R1 = 16, R2 = 1, T = 16; };
+template <> struct Shape<256> { static constexpr int S = 3, R0 = 8, R1 = 8, R2 = 4, T = 32; };
 template <> struct Shape<512> { static constexpr int S = 3, R0 = 8, R1 = 8, R2 = 8, T = 64; };
 
 constexpr int FFT_TPB = 256;
@@ -527,6 +527,12 @@ __global__ void k_twiddle(double2 *tw, int m) {
 //    D >= max |G^| (G > 0: max |G^| = G^(0)), then renormalises the line;
 //  * phi = value 2^E scale_acc 2^-51 D / m^3.
 
+// Blocks per SM the fixed-point passes are compiled for: three when a thread
+// holds at most 8 values of its line, else two (latency-bound passes whose
+// registers are mostly the line's values).
+template <int M>
+constexpr int fixq_blocks() { return M / Shape<M>::T <= 8 ? 3 : 2; }
+
 constexpr int FIX_EMPTY = -100000;   // exponent of an all-zero line (aligns below any other)
 
 __device__ __forceinline__ long long rshr(long long v, int sh) {
@@ -623,7 +629,7 @@ __device__ __forceinline__ long long shift128(unsigned __int128 v, int t) {
 // out[(z*n + y)*P + k], P = n+1; the pair's exponent in e1[z*n + y], e1[z*n + y + 1].
 // The pair is normalised by its largest value: L1 < m 2^bits(max).
 template <int M>
-__global__ void __launch_bounds__(FFT_TPB, 2) k_fftq_x_fwd(const unsigned long long *__restrict__ acc_hi,
+__global__ void __launch_bounds__(FFT_TPB, fixq_blocks<M>()) k_fftq_x_fwd(const unsigned long long *__restrict__ acc_hi,
                                                         const unsigned long long *__restrict__ acc_lo,
                                                         int n, const longlong2 *__restrict__ tw,
                                                         longlong2 *__restrict__ out,
@@ -697,7 +703,7 @@ __device__ __forceinline__ long long rint_scaled(double v, int sh) {
 // adjoint's source on nodes -1..n); each pair normalised by its largest
 // exponent: |value| < 2^(E+1), L1 < 2 nin 2^(E+1) <= 2m 2^(E+1).
 template <int M>
-__global__ void __launch_bounds__(FFT_TPB, 2) k_fftq_x_fwd_d(const double *__restrict__ src, int n,
+__global__ void __launch_bounds__(FFT_TPB, fixq_blocks<M>()) k_fftq_x_fwd_d(const double *__restrict__ src, int n,
                                                           int nin, const longlong2 *__restrict__ tw,
                                                           longlong2 *__restrict__ out,
                                                           int *__restrict__ e1) {
@@ -752,7 +758,7 @@ __global__ void __launch_bounds__(FFT_TPB, 2) k_fftq_x_fwd_d(const double *__res
 // inverse y).  Element e of line (o, kx) has exponent
 // ein[o*ein_o + e*ein_e + kx*ein_k]; the line's exponent goes to eout[o*P + kx].
 template <int M, int MODE>
-__global__ void __launch_bounds__(FFT_TPB, 2) k_fftq_lines(const longlong2 *__restrict__ in,
+__global__ void __launch_bounds__(FFT_TPB, fixq_blocks<M>()) k_fftq_lines(const longlong2 *__restrict__ in,
                                                         long long in_o, long long in_e, int ne_in,
                                                         const int *__restrict__ ein, long long ein_o,
                                                         long long ein_e, long long ein_k,
@@ -834,7 +840,7 @@ __global__ void __launch_bounds__(FFT_TPB, 2) k_fftq_lines(const longlong2 *__re
 // = value 2^(E + eoff) scale_dev-or-scale D / m^3, nodes -1..n (eoff = -51
 // for the accumulators, 2^51 per particle; 0 for a double source).
 template <int M>
-__global__ void __launch_bounds__(FFT_TPB, 2) k_fftq_x_inv(const longlong2 *__restrict__ in, int n,
+__global__ void __launch_bounds__(FFT_TPB, fixq_blocks<M>()) k_fftq_x_inv(const longlong2 *__restrict__ in, int n,
                                                         const int *__restrict__ e4,
                                                         const FixScales *__restrict__ fs,
                                                         double scale, const double *scale_dev,
@@ -935,7 +941,7 @@ __global__ void k_green_quant(const double *__restrict__ gh, long long cnt, int 
 
 // ------------------------------------------------------------------ driver
 
-static int team_size(int M) { return M == 512 ? 64 : M == 256 ? 16 : M >= 64 ? 8 : 4; }
+static int team_size(int M) { return M == 512 ? 64 : M == 256 ? 32 : M >= 64 ? 8 : 4; }
 
 static size_t smem_bytes(int M) {
     return (size_t)(M + (FFT_TPB / team_size(M)) * (M + M / 16)) * sizeof(double2);
@@ -958,7 +964,7 @@ static void set_attrs() {
     cudaFuncSetAttribute(k_fftq_lines<M, MODE_ZSOLVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_fftq_lines<M, MODE_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     cudaFuncSetAttribute(k_fftq_x_inv<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    // the fixed-point passes are latency-bound: room for two blocks per SM
+    // the fixed-point passes are latency-bound: room for several blocks per SM
     cudaFuncSetAttribute(k_fftq_x_fwd<M>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(k_fftq_x_fwd_d<M>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(k_fftq_lines<M, MODE_FWD>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

@@ -99,6 +99,33 @@ def test_solve_matches_oracle(bt, n, h):
     assert grid_rel_err(phi, ref) <= REL_TOL
 
 
+@pytest.mark.parametrize("n", [128, 256])
+def test_solve_of_point_charge_is_the_green_function(bt, n):
+    """On the grids the oracle tests do not reach (256- and 512-point lines):
+    the solve of a unit charge density at one node j gives phi(i) = G(i - j)
+    at every node -1..n (offsets up to n, the doubled grid's +-n entries
+    included), G the context's own integrated Green's function table; this
+    checks the FFT passes' staging, pruning and crop independently of the
+    tracking solve, which is compared with this one below."""
+    h = (1.0e-4, 1.3e-4, 2.1e-3)
+    trk = bt.Tracker(n)
+    g = trk.green_table(h, DEV).cpu().numpy().reshape(n + 1, n + 1, n + 1)   # [c][b][a]
+    grid = bt.Grid(n, DEV)
+    grid.h = list(h)
+    j = (n // 3, n // 2 + 1, (2 * n) // 3)       # (x, y, z) node
+    rho = torch.zeros(n ** 3, dtype=torch.float64, device=DEV)
+    rho[(j[2] * n + j[1]) * n + j[0]] = 1.0
+    grid.rho.copy_(rho)
+    trk.solve(grid)
+    phi = grid.phi.cpu().numpy().reshape(n + 2, n + 2, n + 2)                # [z][y][x], nodes -1..n
+    idx = np.arange(-1, n + 1)
+    ax = np.abs(idx - j[0])
+    by = np.abs(idx - j[1])
+    cz = np.abs(idx - j[2])
+    want = g[cz[:, None, None], by[None, :, None], ax[None, None, :]]
+    assert grid_rel_err(phi, want) <= 1e-12
+
+
 @pytest.mark.parametrize("n", [32, 128, 256])
 def test_tracking_solve_matches_fp64_solve(bt, n):
     """Tracking solves in block floating point (int64 values, one exponent per
