@@ -200,7 +200,7 @@ template <int M> struct Shape;
 template <> struct Shape<16> { static constexpr int S = 2, R0 = 4, R1 = 4, R2 = 1, T = 4; };
 template <> struct Shape<32> { static constexpr int S = 2, R0 = 8, R1 = 4, R2 = 1, T = 4; };
 template <> struct Shape<64> { static constexpr int S = 2, R0 = 8, R1 = 8, R2 = 1, T = 8; };
-template <> struct Shape<128> { static constexpr int S = 2, R0 = 16, R1 = 8, R2 = 1, T = 8; };
+template <> struct Shape<128> { static constexpr int S = 3, R0 = 8, R1 = 4, R2 = 4, T = 16; };
 template <> struct Shape<256> { static constexpr int S = 3, R0 = 8, R1 = 8, R2 = 4, T = 32; };
 template <> struct Shape<512> { static constexpr int S = 3, R0 = 8, R1 = 8, R2 = 8, T = 64; };
 
@@ -941,7 +941,7 @@ __global__ void k_green_quant(const double *__restrict__ gh, long long cnt, int 
 
 // ------------------------------------------------------------------ driver
 
-static int team_size(int M) { return M == 512 ? 64 : M == 256 ? 32 : M >= 64 ? 8 : 4; }
+static int team_size(int M) { return M == 512 ? 64 : M == 256 ? 32 : M == 128 ? 16 : M == 64 ? 8 : 4; }
 
 static size_t smem_bytes(int M) {
     return (size_t)(M + (FFT_TPB / team_size(M)) * (M + M / 16)) * sizeof(double2);
