@@ -207,8 +207,8 @@ template <> struct Shape<512> { static constexpr int S = 3, R0 = 8, R1 = 8, R2 =
 constexpr int FFT_TPB = 256;
 
 // Line buffers in shared memory hold one 16-byte pad slot per 16 elements:
-// the first radix-16 step stores element 16t + q from thread t, a stride that
-// would put every lane of a warp on the same banks.
+// the first radix step stores element R0 t + q from thread t (R0 = 8 or 16), a
+// stride that without the pads would put most lanes of a warp on the same banks.
 __device__ __forceinline__ int sp(int i) { return i + (i >> 4); }
 template <int M>
 constexpr int kLineStride = M + M / 16;   // elements per padded line buffer
