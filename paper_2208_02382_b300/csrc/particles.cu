@@ -966,13 +966,24 @@ __global__ void __launch_bounds__(TPB, (UL && SH == 1) ? 5 : (SH == 1 && !(DEP &
         }
         if (use_tile) {
             __syncthreads();
+            // tile index i = (ll ty + jj) tx + ii, stepped by TPB with carries
+            // (three divisions per thread instead of three per node)
+            const int sa = TPB % tx, sb = (TPB / tx) % ty, sc = TPB / (tx * ty);
+            int ii = threadIdx.x % tx, jj = (threadIdx.x / tx) % ty, ll = threadIdx.x / (tx * ty);
             for (int i = threadIdx.x; i < tx * ty * tz; i += TPB) {
                 const unsigned long long v = ((unsigned long long)thi[i] << 32) + tlo[i];
-                if (v == 0ull) continue;
-                const int ii = i % tx, jj = (i / tx) % ty, ll = i / (tx * ty);
-                const long long node = ((long long)(l0 + ll) * nn + (j0 + jj)) * nn + (i0 + ii);
-                atomicAdd(&a.acc_hi[node], v >> DEP_SPLIT);
-                atomicAdd(&a.acc_lo[node], v & ((1ull << DEP_SPLIT) - 1));
+                if (v != 0ull) {
+                    const long long node = ((long long)(l0 + ll) * nn + (j0 + jj)) * nn + (i0 + ii);
+                    atomicAdd(&a.acc_hi[node], v >> DEP_SPLIT);
+                    atomicAdd(&a.acc_lo[node], v & ((1ull << DEP_SPLIT) - 1));
+                }
+                ii += sa;
+                int carry = ii >= tx;
+                ii -= carry ? tx : 0;
+                jj += sb + carry;
+                carry = jj >= ty;
+                jj -= carry ? ty : 0;
+                ll += sc + carry;
             }
         }
     }
