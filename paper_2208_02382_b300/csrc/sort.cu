@@ -41,13 +41,14 @@ __device__ __forceinline__ int brick_of(double x, double y, double t, double nbg
                                         int nn, int be) {
     const double u[3] = {(x - b.lo[0]) * b.inv_h[0], (y - b.lo[1]) * b.inv_h[1],
                          (__dmul_rn(nbg, t) - b.lo[2]) * b.inv_h[2]};
-    const int nb = nn / be;
+    const int lb = __ffs(be) - 1;   // be is a power of two
+    const int nb = nn >> lb;
     int k[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         long long c = (long long)(to_fixed52(u[d]) >> 52);  // outside: clamped
         if (c > nn - 2) c = nn - 2;
-        k[d] = (int)(c / be);
+        k[d] = (int)(c >> lb);
     }
     return (k[2] * nb + k[1]) * nb + k[0];
 }
