@@ -123,8 +123,8 @@ def dipedge_matrix(psi: float, curvature: float) -> np.ndarray:
     """Thin hard-edge dipole fringe field (K. L. Brown, SLAC-75, 1972): edge
     angle psi, bend curvature h = 1/rho;  px += h tan(psi) x,
     py -= h tan(psi) y.  A rectangular bend of angle theta has psi = theta/2
-    at both faces.  (Paper §Benchmark: chicane; SURVEY reading: edge elements
-    make the chicane achromatic.)"""
+    at both faces.  (Paper §Benchmark: chicane; reading: edge elements make
+    the chicane achromatic.)"""
     m = np.eye(6)
     m[PX, X] = curvature * math.tan(psi)
     m[PY, Y] = -curvature * math.tan(psi)
