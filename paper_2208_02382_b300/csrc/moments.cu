@@ -23,12 +23,16 @@ constexpr int MOM_TPB = 256;
 constexpr int MOM_P1 = 18;   // pass-1 partial per block: 6 sums, 6 min keys, 6 max keys
 constexpr int MOM_P2 = 42;   // pass-2 partial per block: 21 x (hi, lo) of 128-bit sums
 
-// at most MOM_PPT particles per thread (the per-thread integer sums' bound)
+// at most MOM_PPT particles per thread (the per-thread integer sums' bound),
+// in whole waves of the second-moment pass (128 registers: two blocks of 256
+// threads per SM), so that no wave runs a few long blocks on an idle GPU
 constexpr int MOM_PPT = 256;
 int moments_blocks(int64_t n) {
+    const int64_t resident = 148 * 2;
     const int64_t per = (int64_t)MOM_TPB * MOM_PPT;
-    int64_t b = (n + per - 1) / per;
-    if (b < 148 * 2) b = 148 * 2;                       // fill the GPU
+    int64_t waves = (n + resident * per - 1) / (resident * per);
+    if (waves < 1) waves = 1;
+    int64_t b = resident * waves;
     if (b > (n + MOM_TPB - 1) / MOM_TPB) b = (n + MOM_TPB - 1) / MOM_TPB;
     return (int)(b < 1 ? 1 : b);
 }
