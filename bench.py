@@ -37,11 +37,13 @@ UNIT = "particle-steps/s"
 FP64_PEAK_TFLOPS = 2 * 148 * 2.032e9 * 2 / 1e12
 
 
-# Algorithmic work per launch of each kernel kind for the roofline of the
-# dominant kernel: (bound, unit, f(n_particles, n_grid) -> amount per launch).
-#   gather_kick_push: read and write the six FP64 coordinates and read the
-#                     deposit's three cell codes, 120 B/particle
-#   deposit:          read x, y, t and write their cell codes, 48 B/particle
+# Algorithmic work per launch of each kernel kind for the roofline (the bytes
+# a kernel must move by the definition of its step, whatever this design
+# stores on the side): (bound, unit, f(n_particles, n_grid) -> amount).
+#   gather_kick_push: read and write the six FP64 coordinates, 96 B/particle
+#   deposit:          re-read X, Y, t (24 B) and a 4-byte cell key, 28 B/particle
+# (This design also stores each particle's three 64-bit cell codes in the
+# deposit and reads them in the gather, 24 B more each: `design_bytes`.)
 # The tracking solve runs in int64 fixed point on the integer pipes; its
 # passes count the spectrum data they must read and write (16-byte complex
 # values, m = 2n, P = n+1):
@@ -50,9 +52,10 @@ FP64_PEAK_TFLOPS = 2 * 148 * 2.032e9 * 2 / 1e12
 #               inverse y pass ((n+2) m P in, (n+2)^2 P out)
 #   fft_zsolve: n m P in, the quantised Green's octant (P^3 x 8 B), (n+2) m P out
 #   fft_xinv:   (n+2)^2 P in, phi on (n+2)^3 nodes (8 B) out
+#   moments:    read the six FP64 coordinates, 48 B/particle
 ALGO = {
-    "gather_kick_push": ("hbm", "GB/s", lambda npart, n: 120.0 * npart),
-    "deposit": ("hbm", "GB/s", lambda npart, n: 48.0 * npart),
+    "gather_kick_push": ("hbm", "GB/s", lambda npart, n: 96.0 * npart),
+    "deposit": ("hbm", "GB/s", lambda npart, n: 28.0 * npart),
     "fft_zsolve": ("hbm", "GB/s", lambda npart, n: 16.0 * (n + 1) * 2 * n * (2 * n + 2)
                    + 8.0 * (n + 1) ** 3),
     "fft_yz": ("hbm", "GB/s", lambda npart, n: 0.5 * 16.0 * (n + 1) * (
@@ -61,6 +64,9 @@ ALGO = {
     "fft_xinv": ("hbm", "GB/s", lambda npart, n: 16.0 * (n + 2) ** 2 * (n + 1)
                  + 8.0 * (n + 2) ** 3),
 }
+# Bytes per particle this design's particle kernels move (coordinates plus the
+# deposit's stored cell codes), reported beside the algorithmic figure.
+DESIGN_BYTES = {"gather_kick_push": 120.0, "deposit": 48.0}
 KERNEL_SOURCES = {
     "gather_kick_push": "particles.cu", "deposit": "particles.cu",
     "fft_zsolve": "fft.cu", "fft_yz": "fft.cu", "fft_x": "fft.cu", "fft_xinv": "fft.cu",
@@ -85,6 +91,8 @@ def parse():
                    help="skip the TSC / thin-multipole / per-slice-diagnostics measurements")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched-variants measurement (batch_256_fodo)")
+    p.add_argument("--no-full-lattice", action="store_true",
+                   help="skip the timing of the whole 500-kick lattice beside the headline")
     p.add_argument("--particles", type=int, default=None,
                    help="override the workload's particle count (small profiling cases)")
     return p.parse_args()
@@ -200,6 +208,16 @@ def traffic_for(kernel: str, n_units_launch: float):
     return None if e is None else e["bytes_per_unit"] * n_units_launch
 
 
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_baseline(w: bg.Workload, sample_particles: int, kicks_timed: int = 1):
     """The oracle as it stands on a bounded sample of the workload: one warm
     kick (first box and Green's function), then `kicks_timed` timed kicks of
@@ -218,7 +236,10 @@ def cpu_baseline(w: bg.Workload, sample_particles: int, kicks_timed: int = 1):
     regrid_in_timed = len(t.regrid_log) > nreg
     cores = (os.cpu_count() or 1) if regrid_in_timed else 1
     return {"value": sample_particles * kicks_timed / dt, "unit": UNIT, "cores": cores,
-            "kind": "oracle",
+            "kind": "oracle", "cpu_model": cpu_model(), "host_cores": os.cpu_count(),
+            "why_cores": "the oracle is plain numpy (single-threaded element-wise work, "
+                         "np.add.at deposit, pocketfft); only its float128 Green's function "
+                         "uses OpenMP, and no rebuild falls in the timed kicks",
             "sample": f"{sample_particles} of {w.n_particles} particles of {w.name}, "
                       f"{kicks_timed} kick(s) after one warm kick, full {w.n_grid}^3 grid "
                       f"({'with' if regrid_in_timed else 'no'} Green's function rebuild); "
@@ -257,6 +278,7 @@ def run_reference(args, w):
             "config": {"workload": w.name, "particles": w.n_particles, "grid": w.n_grid,
                        "sample_particles": sample, "parallelism": "host cores"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "cpu_model": cpu_model(), "host_cores": os.cpu_count(),
                              "sample": f"{sample} of {w.n_particles} particles per step at the "
                                        f"full {w.n_grid}^3 grid; {steps} of {args.steps} steps "
                                        f"timed within a {budget:.0f} s budget"},
@@ -617,6 +639,32 @@ def run_ours(args, w):
     ms_prof = ep0.elapsed_time(ep1)
     prof = trk.profile_read()
     trk.profile(False)
+    # the whole lattice (all 500 kicks of the chicane: both quadrupoles, the four
+    # bends, every re-binning and the first box with its Green's function) from
+    # the initial bunch and a fresh context state, once warm and once timed
+    full = None
+    if not args.no_full_lattice:
+        nk_full = w.kicks
+        init = torch.tensor(coords_h, dtype=torch.float64, device=dev)
+        for rep in range(2):
+            beam.coords.copy_(init)
+            beam.ids.copy_(torch.arange(npart, dtype=torch.int64, device=dev))
+            trk.reset()
+            torch.cuda.synchronize()
+            ef0, ef1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ef0.record(stream)
+            trk.track(beam, w.lattice, 0, nk_full)
+            ef1.record(stream)
+            torch.cuda.synchronize()
+            trk.sync()
+        ms_full = ef0.elapsed_time(ef1)
+        full = {"kicks": nk_full, "ms": ms_full, "ms_per_step": ms_full / nk_full,
+                "particle_steps_per_s": npart * nk_full / (ms_full * 1e-3),
+                "regrids": len(trk.regrid_log()),
+                "what": "bx_track over the whole lattice from the initial bunch (context "
+                        "reset: first box and Green's function build included; re-binning "
+                        "as tuned), second of two runs, CUDA events"}
+        del init
     ms, psteps = aggregate_replicas(ms, float(npart) * args.steps, pg, dev)
     if pg:
         pg.barrier()
@@ -651,13 +699,20 @@ def run_ours(args, w):
                 n2 = ncu_entry(k2)
                 others[k2] = {"bound": b2, "achieved": round(a2, 3), "unit": u2,
                               "frac": round(a2 / p2, 4), "share_of_step": round(ms2 / ms_prof, 4),
+                              "avg_launch_ms": round(ms2 / c2, 5),
                               "fp64_pipe_active_frac": (n2["fp64_pipe_active_pct"] / 100.0)
                               if n2 else None,
                               "issue_active_frac": (n2["issue_active_pct"] / 100.0)
                               if n2 and "issue_active_pct" in n2 else None}
         ne = ncu_entry(dname)
+        algo_note = {"gather_kick_push": "96 B/particle: six FP64 coordinates read and written",
+                     "deposit": "28 B/particle: X, Y, t re-read and a 4-byte cell key"}
         roof = {"kernel": dname, "bound": bound, "achieved": achieved, "peak": peak,
                 "unit": unit, "frac": achieved / peak, "peak_source": peak_src,
+                "algorithmic_bytes": algo_note.get(dname),
+                "design_bytes_per_unit": DESIGN_BYTES.get(dname),
+                "design_frac": (DESIGN_BYTES[dname] * npart / avg_s / 1e9 / peak)
+                               if dname in DESIGN_BYTES else None,
                 "traffic": traffic_for(dname, units),
                 "fp64_pipe_active_frac": (ne["fp64_pipe_active_pct"] / 100.0) if ne else None,
                 "binding": ("FP64 pipe (ncu: FP64 pipe active %.0f%% vs DRAM %.0f%% of "
@@ -721,7 +776,8 @@ def run_ours(args, w):
                            "step": "one slice: map, box rule, deposit, solve, gather+kick",
                            "l2": f"inputs larger than L2 (particle SoA {npart * 48 / 1e9:.2f} GB)",
                            "parallelism": f"replicas x{world}", "binning": binning},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gradient": gradient,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "full_lattice": full,
+                "gradient": gradient,
                 "batching": batching, "variants": variants,
                 "gpu_launches": launches, "clocks": clocks, "wall_s_timed": wall,
                 "profiled": {"steps": k_prof, "ms_per_step": ms_per_kick_prof,
