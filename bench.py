@@ -6,9 +6,11 @@
 A step is one s-step of the split-operator tracking (one slice: merged
 half-maps, box rule, CIC deposit, Hockney/IGF Poisson solve, field, gather +
 kick) over the whole bunch.  The metric is particle-steps per second with space
-charge on the 128^3 grid.  Multi-GPU runs (torchrun) are independent replicas
-(the single-bunch step is not sharded); `value` sums all ranks' particle-steps
-over the slowest rank's time.
+charge on the 128^3 grid.  Multi-GPU runs (torchrun) shard one bunch by
+particles (weak scaling: each rank holds the workload's particle count, the
+bunch is all ranks' particles): per kick an allreduce (NCCL) of the integer box
+keys and of the integer charge accumulators, then a redundant solve on every
+rank; `value` sums all ranks' particle-steps over the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -106,9 +108,9 @@ def dist_env():
 
 
 def aggregate_replicas(seconds: float, units: float, pg=None, device=None):
-    """Replicas (each rank tracks its own bunch, no data-path collective): the
-    slowest rank's time and all ranks' units, so value = units / seconds is
-    the whole job's throughput.  pg: torch.distributed (any backend) or None."""
+    """The slowest rank's time and all ranks' units (each rank's share of the
+    particle-steps), so value = units / seconds is the whole job's throughput.
+    pg: torch.distributed (any backend) or None."""
     if pg is None:
         return float(seconds), float(units)
     import torch
@@ -597,6 +599,11 @@ def run_ours(args, w):
     if rank:
         coords_h = bg.gaussian6d(w.n_particles, w.sigmas, seed=w.seed + rank)
     npart = coords_h.shape[1]
+    n_total = npart * world            # one bunch, sharded by particles over the ranks
+
+    def shard(t):
+        if world > 1:
+            t.set_shard(btk.torch_allreduce(), n_total)
     k_prof = min(args.steps, 100)
     lat = repeated_lattice(w, args.warmup + args.steps + k_prof)
     beam = btk.Beam(torch.tensor(coords_h, dtype=torch.float64, device=dev), sp, w.bunch_charge_C)
@@ -604,12 +611,14 @@ def run_ours(args, w):
     stream = torch.cuda.current_stream()
     # binning as a user would set it: the autotuner times the candidates on the
     # first 64 kicks of this problem (bunch restored, context reset afterwards)
-    binning = {"rebin_interval": 16, "bin_edge": 0, "tuned": False}
+    binning = {"rebin_interval": 16, "bin_edge": 0, "cell_order": 0, "tuned": False}
     if not args.no_tune:
         t_tune = time.perf_counter()
-        (iv, be), _ = trk.autotune_binning(beam, lat, kicks=64)
-        binning = {"rebin_interval": iv, "bin_edge": be, "tuned": True, "tuned_over_kicks": 64,
+        (iv, be, co), _ = trk.autotune_binning(beam, lat, kicks=64)
+        binning = {"rebin_interval": iv, "bin_edge": be, "cell_order": co, "tuned": True,
+                   "tuned_over_kicks": 64,
                    "tuning_s": round(time.perf_counter() - t_tune, 2)}
+    shard(trk)
     # warm-up (first box and Green's function build, kick-graph capture happen here)
     trk.track(beam, lat, 0, args.warmup)
     trk.sync()
@@ -729,7 +738,8 @@ def run_ours(args, w):
         mom_h = torch.empty(27, dtype=torch.float64).pin_memory()
         k_e2e = min(args.steps, 200)
         trk2 = btk.Tracker(w.n_grid)
-        trk2.set_binning(binning["rebin_interval"], binning["bin_edge"])
+        trk2.set_binning(binning["rebin_interval"], binning["bin_edge"], binning["cell_order"])
+        shard(trk2)
         beam2 = btk.Beam(torch.empty_like(beam.coords), sp, w.bunch_charge_C)
         if pg:
             pg.barrier()
@@ -775,7 +785,10 @@ def run_ours(args, w):
                            "doubled_grid": 2 * w.n_grid, "kicks_in_lattice": w.kicks,
                            "step": "one slice: map, box rule, deposit, solve, gather+kick",
                            "l2": f"inputs larger than L2 (particle SoA {npart * 48 / 1e9:.2f} GB)",
-                           "parallelism": f"replicas x{world}", "binning": binning},
+                           "parallelism": (f"particle shards x{world} (NCCL allreduce of box "
+                                           f"keys and charge, redundant solve)")
+                           if world > 1 else "single GPU", "bunch_particles": n_total,
+                           "binning": binning},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "full_lattice": full,
                 "gradient": gradient,
                 "batching": batching, "variants": variants,

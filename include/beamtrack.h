@@ -25,7 +25,7 @@
  * - Every call is asynchronous on `stream` (a cudaStream_t, or NULL for the
  *   legacy default stream) unless stated.  Argument errors are detected on
  *   the host before any launch and returned at once; device-side errors
- *   (a non-finite coordinate, a timed-out device wait) are recorded in a
+ *   (a non-finite coordinate, a particle outside a given box) are recorded in a
  *   device status word and returned by the next call that reads it
  *   (bx_sync, bx_moments) or by bx_sync.
  * - Status codes are the BX_* values below; bx_last_error() gives text.
@@ -45,8 +45,11 @@ extern "C" {
 #define BX_BAD_ARG 1        /* null pointer, size out of range, bad element */
 #define BX_NONFINITE 2      /* NaN or Inf found in particle coordinates     */
 #define BX_OUT_OF_MEMORY 3  /* a device allocation of the context failed    */
-#define BX_DEVICE_TIMEOUT 4 /* a bounded device-side wait gave up           */
+#define BX_DEVICE_TIMEOUT 4 /* reserved: no call of this version waits on the
+                             device (batches loop in graph WHILE nodes), so
+                             none returns it                                */
 #define BX_CUDA 5           /* a CUDA runtime call failed                   */
+#define BX_COLLECTIVE 6     /* a sharded run's allreduce callback failed    */
 
 /* ---- element types (Listing 1: elements.Drift, elements.Quad; sector bend
  *      from the paper's chicane benchmark; thin dipole edge and constant
@@ -75,15 +78,21 @@ typedef struct bx_batch bx_batch;
  *                  default (16), -1 = never, else >= 1.
  * bin_edge       : grid cells per bin edge: 0 = default (8, or N/16 above
  *                  N = 128), else a power of two in [2, N/2] with at most 16^3
- *                  bins.  Neither changes any result, only the speed
- *                  (bx_autotune_binning picks them by timing).
+ *                  bins.
+ * cell_order     : 0 = re-bin by bin only; 1 = by bin and, within a bin, by
+ *                  grid cell (a second counting-sort pass), so that runs of
+ *                  consecutive particles share a cell and the CIC deposit adds
+ *                  each run's weights once.  None of the three changes any
+ *                  result, only the speed (bx_autotune_binning picks them by
+ *                  timing).
  */
 typedef struct {
     int32_t n_grid;
     int32_t shape_order;
     int32_t rebin_interval;
     int32_t bin_edge;
-    int32_t reserved[4];
+    int32_t cell_order;
+    int32_t reserved[3];
 } bx_options;
 
 /* A bunch.  coord[0..5] = x, px, y, py, t, pt: device pointers to n doubles
@@ -276,11 +285,15 @@ const char *bx_kernel_name(int32_t id);
  * allocate device memory once they are running (for example an on-line model
  * in an accelerator control loop with a fixed memory footprint, or a host
  * framework that owns all device memory through its own pool).  The paper has
- * no counterpart; it is the arithmetic of bx_deposit with use_box = 1 and
+ * no counterpart.  It is the arithmetic of bx_deposit with use_box = 1 (the
+ * same cells, fixed-point weights and accumulation: bitwise the same rho) and
  * needs no context.
- * beam: as for bx_deposit (device arrays); lo, hi: host arrays, the box (the
- * bunch must lie inside; particles outside are skipped); n: nodes per
- * dimension, a power of two in [8, 64]; rho: device output of n^3 doubles.
+ * beam: as for bx_deposit (device arrays); lo, hi: host arrays, the box;
+ * n: nodes per dimension, a power of two in [8, 64]; rho: device output of
+ * n^3 doubles.  flags_device: NULL, or a device int32 owned by the caller into
+ * which the call ORs BX_NOALLOC_OUTSIDE when particles lay outside the box and
+ * BX_NOALLOC_NONFINITE when a position was NaN or Inf; such particles are
+ * skipped (their charge is missing from rho).  The caller clears the word.
  * Scratch: the fixed-point accumulators live in one static device array of
  * 2 x 64^3 x 8 bytes = 4 MiB that the library holds on every GPU that loads
  * it until the process exits; n > 64 is rejected with BX_BAD_ARG.  Every call
@@ -288,9 +301,11 @@ const char *bx_kernel_name(int32_t id);
  * the GPU race: order them on one stream.  The first call on a device looks up
  * the array's device address with that device current and caches it; make
  * that first call before any stream capture.  Asynchronous on `stream`;
- * errors are returned at once and described by bx_last_error(NULL). */
+ * argument errors are returned at once and described by bx_last_error(NULL). */
+#define BX_NOALLOC_OUTSIDE 1
+#define BX_NOALLOC_NONFINITE 2
 int32_t bx_deposit_noalloc(const bx_beam *beam, const double lo[3], const double hi[3],
-                           int32_t n, double *rho, void *stream);
+                           int32_t n, double *rho, int32_t *flags_device, void *stream);
 
 /* ---- Differentiation (reverse mode) ------------------------------------
  * The paper motivates coupling the code to machine-learning workflows
@@ -390,24 +405,74 @@ int32_t bx_batch_destroy(bx_batch *batch);
 const char *bx_batch_last_error(const bx_batch *batch);
 
 /* ---- Tuning --------------------------------------------------------------
- * Re-binning interval and bin edge as in bx_options (takes effect at the next
- * call; BX_BAD_ARG for invalid values). */
-int32_t bx_set_binning(bx_ctx *ctx, int32_t rebin_interval, int32_t bin_edge);
+ * Re-binning interval, bin edge and cell order as in bx_options (takes effect
+ * at the next call; BX_BAD_ARG for invalid values). */
+int32_t bx_set_binning(bx_ctx *ctx, int32_t rebin_interval, int32_t bin_edge,
+                       int32_t cell_order);
 
-/* Autotuner of the binning: tracks `kicks` kicks of the lattice from kick 0
- * (from a fresh state) once per candidate (never re-bin, and every 8, 16, 32
- * or 64 kicks, those not longer than the timed kicks, with each valid bin
- * edge among 4, 8, 16), timing each with CUDA
- * events, and keeps the fastest (bx_set_binning).  The beam's coordinates and
- * ids are restored afterwards and the context is reset (bx_reset), so results
- * do not depend on the tuning.  chosen (host, 2): the chosen rebin_interval and
- * bin_edge; ms (host, may be NULL): the time of candidate i for i < min(cap,
- * *count), candidates in the order above; *count: number of candidates.
- * Needs the beam's id array.  Synchronous; uses 7 n doubles of device scratch
- * for the saved coordinates and ids while it runs. */
+/* Autotuner of the binning (the bin and deposit layout; no result depends on
+ * it): tracks `kicks` kicks of the lattice from kick 0 (from a fresh state)
+ * once per candidate (never re-bin; and every 8, 16, 32 or 64 kicks, those
+ * not longer than the timed kicks, with each valid bin edge among 4, 8, 16,
+ * in bin order and in cell order), timing each with CUDA events, and keeps
+ * the fastest (bx_set_binning).  The beam's coordinates and ids are restored
+ * afterwards and the context is reset (bx_reset), so results do not depend on
+ * the tuning.  chosen (host, 3): the chosen rebin_interval, bin_edge and
+ * cell_order; ms (host, may be NULL): the time of candidate i for
+ * i < min(cap, *count), candidates in the order above; *count: number of
+ * candidates.  Needs the beam's id array.  Synchronous; uses 7 n doubles of
+ * device scratch for the saved coordinates and ids while it runs. */
 int32_t bx_autotune_binning(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lattice,
-                            int32_t kicks, int32_t chosen[2], double *ms, int32_t cap,
+                            int32_t kicks, int32_t chosen[3], double *ms, int32_t cap,
                             int32_t *count, void *stream);
+
+/* ---- Particle-sharded tracking (one bunch over several processes) -------
+ * ImpactX runs one simulation over many nodes when it is started with MPI
+ * (paper: section ImpactX and the comments of Listing 1), with ABLASTR's
+ * charge deposition and Poisson solve as the routines that cross ranks.
+ * Here each process (rank) holds a share of the bunch's particles in its own
+ * context and beam, and the ranks advance the same kicks in lockstep.  Per
+ * kick, bx_track calls the caller's allreduce twice on the box inputs and
+ * twice on the charge: MIN over the three order-preserving integer keys of the
+ * rest-frame minima, MAX over those of the maxima, then SUM over the two
+ * integer charge accumulators (n^3 values each, the hi and lo parts of the
+ * 51-bit fixed-point CIC weights).  Every rank then applies the same box rule
+ * to the same global extent, solves the same Poisson problem redundantly and
+ * kicks its own particles.  The accumulators are exact integers, so the sum
+ * does not depend on how the bunch is split: the kicked coordinates are
+ * bitwise those of one process tracking the whole bunch. */
+#define BX_OP_SUM 0
+#define BX_OP_MIN 1
+#define BX_OP_MAX 2
+
+/* Combine `count` int64 values at DEVICE address buf over all ranks, in
+ * place (every rank passes the same count and op, in the same order).  The
+ * result must be in buf for work enqueued on `stream` after the callback
+ * returns: enqueue a stream-ordered collective on `stream` (e.g. NCCL), or
+ * synchronize `stream`, reduce through host memory and copy back before
+ * returning.  Return 0 on success; anything else aborts the bx_track call with
+ * BX_COLLECTIVE. */
+typedef int32_t (*bx_allreduce_fn)(int64_t *buf, int64_t count, int32_t op, void *stream,
+                                   void *user);
+
+/* allreduce: the callback; user: passed to it; n_total: particles of the
+ * whole bunch over all ranks (the macroparticle charge is
+ * charge_sign * bunch_charge_C / n_total; every rank gives the whole bunch's
+ * charge in its bx_beam).  A rank may hold no particles. */
+typedef struct {
+    bx_allreduce_fn allreduce;
+    void *user;
+    int64_t n_total;
+} bx_shard;
+
+/* Make the context's bx_track calls one rank of a sharded run (shard = NULL
+ * ends it).  While it is set, bx_track launches each kick's kernels one by
+ * one with the callbacks between them (no CUDA graphs: a collective need not
+ * be capturable), and a beam with more than n_total particles is refused;
+ * bx_track_diagnostics, bx_grad_forward, bx_autotune_binning and batches
+ * refuse a sharded context (BX_BAD_ARG).  bx_deposit, bx_solve, bx_gather_kick
+ * and bx_moments stay local to the rank. */
+int32_t bx_set_shard(bx_ctx *ctx, const bx_shard *shard);
 
 /* Wait for the stream and return the device status word (then clear it). */
 int32_t bx_sync(bx_ctx *ctx, void *stream);

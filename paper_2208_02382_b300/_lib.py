@@ -9,14 +9,17 @@ from ctypes import POINTER, c_char_p, c_double, c_int32, c_int64, c_void_p
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbeamtrack.so")
 
-BX_OK, BX_BAD_ARG, BX_NONFINITE, BX_OUT_OF_MEMORY, BX_DEVICE_TIMEOUT, BX_CUDA = range(6)
+BX_OK, BX_BAD_ARG, BX_NONFINITE, BX_OUT_OF_MEMORY, BX_DEVICE_TIMEOUT, BX_CUDA, BX_COLLECTIVE = \
+    range(7)
+BX_OP_SUM, BX_OP_MIN, BX_OP_MAX = 0, 1, 2
 BX_DRIFT, BX_QUAD, BX_SBEND, BX_DIPEDGE, BX_CONSTF, BX_MULTIPOLE = 0, 1, 2, 3, 4, 5
 BX_MULTIPOLE_MAX_ORDER = 12
+BX_NOALLOC_OUTSIDE, BX_NOALLOC_NONFINITE = 1, 2
 
 
 class bx_options(ctypes.Structure):
     _fields_ = [("n_grid", c_int32), ("shape_order", c_int32), ("rebin_interval", c_int32),
-                ("bin_edge", c_int32), ("reserved", c_int32 * 4)]
+                ("bin_edge", c_int32), ("cell_order", c_int32), ("reserved", c_int32 * 3)]
 
 
 class bx_beam(ctypes.Structure):
@@ -42,6 +45,14 @@ class bx_grid(ctypes.Structure):
                 ("phi", c_void_p)]
 
 
+# int32_t (*)(int64_t *buf, int64_t count, int32_t op, void *stream, void *user)
+bx_allreduce_fn = ctypes.CFUNCTYPE(c_int32, c_void_p, c_int64, c_int32, c_void_p, c_void_p)
+
+
+class bx_shard(ctypes.Structure):
+    _fields_ = [("allreduce", bx_allreduce_fn), ("user", c_void_p), ("n_total", c_int64)]
+
+
 # name -> (restype, argtypes), one entry per declaration in include/beamtrack.h
 SIGNATURES = {
     "bx_create": (c_int32, [POINTER(c_void_p), POINTER(bx_options)]),
@@ -63,7 +74,7 @@ SIGNATURES = {
                                   POINTER(c_int32)]),
     "bx_kernel_name": (c_char_p, [c_int32]),
     "bx_deposit_noalloc": (c_int32, [POINTER(bx_beam), POINTER(c_double), POINTER(c_double),
-                                     c_int32, c_void_p, c_void_p]),
+                                     c_int32, c_void_p, c_void_p, c_void_p]),
     "bx_twiss_beam": (c_int32, [POINTER(c_double), POINTER(c_void_p), c_int64, POINTER(c_void_p),
                                 c_void_p]),
     "bx_twiss_grad": (c_int32, [POINTER(c_double), POINTER(c_double), POINTER(c_double)]),
@@ -79,7 +90,7 @@ SIGNATURES = {
     "bx_batch_launch": (c_int32, [c_void_p, c_void_p]),
     "bx_batch_destroy": (c_int32, [c_void_p]),
     "bx_batch_last_error": (c_char_p, [c_void_p]),
-    "bx_set_binning": (c_int32, [c_void_p, c_int32, c_int32]),
+    "bx_set_binning": (c_int32, [c_void_p, c_int32, c_int32, c_int32]),
     "bx_autotune_binning": (c_int32, [c_void_p, POINTER(bx_beam), POINTER(bx_lattice), c_int32,
                                       POINTER(c_int32), POINTER(c_double), c_int32,
                                       POINTER(c_int32), c_void_p]),
@@ -87,6 +98,7 @@ SIGNATURES = {
                                        c_int64, c_void_p, c_void_p]),
     "bx_distribution_beam": (c_int32, [c_int32, POINTER(c_double), POINTER(c_void_p), c_void_p,
                                        c_int64, POINTER(c_void_p), c_void_p]),
+    "bx_set_shard": (c_int32, [c_void_p, POINTER(bx_shard)]),
     "bx_last_error": (c_char_p, [c_void_p]),
 }
 

@@ -178,13 +178,14 @@ class Tracker:
     """A libbeamtrack context (bx_create) on the current CUDA device."""
 
     def __init__(self, n_grid: int, shape_order: int = 1, rebin_interval: int = 0,
-                 bin_edge: int = 0):
+                 bin_edge: int = 0, cell_order: int = 0):
         self.lib = L.load()
         opt = L.bx_options()
         opt.n_grid = int(n_grid)
         opt.shape_order = int(shape_order)
         opt.rebin_interval = int(rebin_interval)
         opt.bin_edge = int(bin_edge)
+        opt.cell_order = int(cell_order)
         ctx = ctypes.c_void_p()
         rc = self.lib.bx_create(ctypes.byref(ctx), ctypes.byref(opt))
         _check(self.lib, None, rc)
@@ -205,6 +206,30 @@ class Tracker:
     def reset(self):
         _check(self.lib, self.ctx, self.lib.bx_reset(self.ctx))
 
+    def set_shard(self, allreduce, n_total: int = 0):
+        """Make this context one rank of a particle-sharded run (bx_set_shard):
+        `allreduce(t, op)` must reduce the int64 CUDA tensor t in place over all
+        ranks (op one of BX_OP_SUM/MIN/MAX; e.g. torch_allreduce()); n_total:
+        particles of the whole bunch.  allreduce=None ends the shard."""
+        if allreduce is None:
+            _check(self.lib, self.ctx, self.lib.bx_set_shard(self.ctx, None))
+            self._shard = None
+            return
+        dev = torch.cuda.current_device()
+
+        def cb(ptr, count, op, stream, user):
+            try:
+                allreduce(torch.as_tensor(_DeviceInt64(ptr, count), device=dev), int(op))
+                return 0
+            except Exception as exc:   # reported by track() after the call fails
+                self._shard_error = exc
+                return 1
+        fn = L.bx_allreduce_fn(cb)
+        sh = L.bx_shard(fn, None, int(n_total))
+        self._shard = (fn, sh)         # the callback must outlive the calls that use it
+        self._shard_error = None
+        _check(self.lib, self.ctx, self.lib.bx_set_shard(self.ctx, ctypes.byref(sh)))
+
     def track(self, beam: Beam, elements, first_kick: int = 0, nkicks: int = -1,
               space_charge: bool = True, diagnostics: bool = False):
         """Track; with diagnostics, return the (kicks, 27) moments at every
@@ -214,6 +239,9 @@ class Tracker:
         if not diagnostics:
             rc = self.lib.bx_track(self.ctx, ctypes.byref(b), ctypes.byref(lat), int(first_kick),
                                    int(nkicks), _stream())
+            if rc == L.BX_COLLECTIVE and getattr(self, "_shard_error", None) is not None:
+                err, self._shard_error = self._shard_error, None
+                raise L.BeamtrackError(rc, f"allreduce callback: {err!r}") from err
             _check(self.lib, self.ctx, rc)
             return None
         total = sum(int(e.nslice) for e in elements if int(e.kind) != L.BX_DIPEDGE)
@@ -289,22 +317,23 @@ class Tracker:
         _check(self.lib, self.ctx, self.lib.bx_sync(self.ctx, _stream()))
 
     # ---- tuning
-    def set_binning(self, rebin_interval: int, bin_edge: int):
+    def set_binning(self, rebin_interval: int, bin_edge: int, cell_order: int = 0):
         _check(self.lib, self.ctx, self.lib.bx_set_binning(self.ctx, int(rebin_interval),
-                                                           int(bin_edge)))
+                                                           int(bin_edge), int(cell_order)))
 
     def autotune_binning(self, beam: Beam, elements, kicks: int = 32, space_charge: bool = True):
         """Time the binning candidates on this problem and keep the fastest;
-        returns ((rebin_interval, bin_edge), [ms per candidate])."""
+        returns ((rebin_interval, bin_edge, cell_order), [ms per candidate])."""
         b = beam.c_struct()
         lat, keep = lattice_struct(elements, space_charge)
-        chosen = (ctypes.c_int32 * 2)()
-        ms = (ctypes.c_double * 16)()
+        chosen = (ctypes.c_int32 * 3)()
+        cap = 64
+        ms = (ctypes.c_double * cap)()
         cnt = ctypes.c_int32()
         rc = self.lib.bx_autotune_binning(self.ctx, ctypes.byref(b), ctypes.byref(lat), int(kicks),
-                                          chosen, ms, 16, ctypes.byref(cnt), _stream())
+                                          chosen, ms, cap, ctypes.byref(cnt), _stream())
         _check(self.lib, self.ctx, rc)
-        return (chosen[0], chosen[1]), [ms[i] for i in range(min(16, cnt.value))]
+        return (chosen[0], chosen[1], chosen[2]), [ms[i] for i in range(min(cap, cnt.value))]
 
     # ---- differentiation
     def grad_forward(self, beam: Beam, elements, checkpoint_interval: int = 20,
@@ -346,10 +375,51 @@ class Tracker:
         return [[buf[12 * i + j] for j in range(12)] for i in range(cnt.value)]
 
 
+class _DeviceInt64:
+    """Zero-copy view of `count` int64 values at a device address (the
+    library's box keys and charge accumulators) for torch.as_tensor."""
+
+    def __init__(self, ptr: int, count: int):
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": "<i8",
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None}
+
+
+def torch_allreduce(group=None):
+    """The collective of a sharded run over torch.distributed, for
+    Tracker.set_shard: with NCCL in place on the device (stream-ordered); with
+    other backends (gloo) through host memory (the copy to the host waits for
+    the stream, the copy back is ordered on it)."""
+    import torch.distributed as dist
+    ops = {L.BX_OP_SUM: dist.ReduceOp.SUM, L.BX_OP_MIN: dist.ReduceOp.MIN,
+           L.BX_OP_MAX: dist.ReduceOp.MAX}
+    on_device = dist.get_backend(group) == "nccl"
+
+    def reduce(t: torch.Tensor, op: int):
+        if on_device:
+            dist.all_reduce(t, op=ops[op], group=group)
+        else:
+            h = t.cpu()
+            dist.all_reduce(h, op=ops[op], group=group)
+            t.copy_(h)
+    return reduce
+
+
+def shard_range(n_total: int, rank: int, world: int):
+    """[start, stop) of the particles rank `rank` holds when a bunch of
+    n_total particles is split over `world` ranks in contiguous, near-equal
+    shares."""
+    if not (0 <= rank < world):
+        raise ValueError("rank outside the world")
+    base, extra = divmod(int(n_total), int(world))
+    start = rank * base + min(rank, extra)
+    return start, start + base + (1 if rank < extra else 0)
+
+
 def autotune_batch(trackers: Sequence[Tracker], beams: Sequence[Beam], lattices, kicks: int = 32):
     """Binning autotuning for a batch: problems with the same grid size and
     particle count within a factor of two share one tuning (of the first of
-    them).  Returns {(n_grid, bucket): (rebin_interval, bin_edge)}."""
+    them).  Returns {(n_grid, bucket): (rebin_interval, bin_edge, cell_order)}."""
     import math
     groups = {}
     for t, b, lat in zip(trackers, beams, lattices):

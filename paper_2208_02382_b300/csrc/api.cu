@@ -34,11 +34,14 @@ int32_t bx_create(bx_ctx **out, const bx_options *opt) {
     if (opt->bin_edge != 0 && !sort_brick_edge_valid(n, opt->bin_edge))
         return fail(nullptr, BX_BAD_ARG,
                     "bin_edge must be 0 or a power of two in [2, n/2] giving at most 16^3 bins");
+    if (opt->cell_order != 0 && opt->cell_order != 1)
+        return fail(nullptr, BX_BAD_ARG, "cell_order must be 0 or 1");
     bx_ctx *ctx = new (std::nothrow) bx_ctx();
     if (!ctx) return fail(nullptr, BX_OUT_OF_MEMORY, "host allocation");
     ctx->n = n;
     ctx->sort_interval = opt->rebin_interval == 0 ? 16 : opt->rebin_interval < 0 ? 0 : opt->rebin_interval;
     ctx->bin_edge = opt->bin_edge;
+    ctx->cell_order = opt->cell_order != 0;
     ctx->shape = opt->shape_order;
     ctx->prof = profiler_new();
     const size_t n3 = (size_t)n * n * n, q3 = (size_t)(n + 2) * (n + 2) * (n + 2);
@@ -60,7 +63,7 @@ int32_t bx_create(bx_ctx **out, const bx_options *opt) {
     A((void **)&ctx->efix, n3 * sizeof(EFix));
     A((void **)&ctx->emax, 3 * sizeof(unsigned long long));
     A((void **)&ctx->escale, 4 * sizeof(int));
-    A((void **)&ctx->dev_ptrs, 12 * sizeof(double *));
+    A((void **)&ctx->dev_ptrs, 24 * sizeof(double *));
     if (e == cudaSuccess) e = fft_plan_init(&ctx->plan, n);
     if (e == cudaSuccess) {
         TrackState h;
@@ -162,6 +165,11 @@ int32_t track_impl(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t fi
     if (first_kick < 0 || first_kick > total || nkicks < 0 || first_kick + nkicks > total)
         return fail(ctx, BX_BAD_ARG, "kick range outside the slice schedule");
     if (nkicks == 0) return BX_OK;
+    const bool sharded = ctx_sharded(ctx);
+    if (sharded && diag)
+        return fail(ctx, BX_BAD_ARG, "per-slice diagnostics of a sharded run are not supported");
+    if (sharded && beam->n > ctx->shard.n_total)
+        return fail(ctx, BX_BAD_ARG, "the rank holds more particles than the shard's n_total");
     if (diag && lattice_has_multipoles(lat))
         return fail(ctx, BX_BAD_ARG,
                     "per-slice diagnostics need a lattice without thin multipoles (their moments "
@@ -174,7 +182,9 @@ int32_t track_impl(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t fi
     CK(cudaMemcpyAsync(ctx->maps, tab.data(), tab.size() * sizeof(MapCoef),
                        cudaMemcpyHostToDevice, s),
        "upload maps");
-    if (beam->n == 0) {
+    // (a rank of a sharded run with no particles still takes part in every
+    // kick's collectives, with empty extents and no charge)
+    if (beam->n == 0 && !(sharded && lat->space_charge)) {
         ctx->kick += nkicks;
         return BX_OK;
     }
@@ -214,8 +224,11 @@ int32_t track_impl(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t fi
         ctx->kick += nkicks;
         return BX_OK;
     }
-    const double q_macro = r.sign * std::fabs(beam->bunch_charge_C) / (double)beam->n;
-    const bool binning = beam->id != nullptr;
+    // macroparticle charge of the whole bunch (a shard's particles carry the
+    // charge of the bunch's n_total)
+    const double q_macro = r.sign * std::fabs(beam->bunch_charge_C) /
+                           (double)(sharded ? ctx->shard.n_total : beam->n);
+    const bool binning = beam->id != nullptr && beam->n > 0;
     if (binning && (rc = ensure_sort_scratch(ctx, beam->n))) return rc;
     if (ctx->shape == 1 && (rc = ensure_cells(ctx, beam->n))) return rc;
     // Device-driven kicks: the box rule kernel of each kick sets the gates
@@ -231,6 +244,18 @@ int32_t track_impl(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t fi
                              ctx->acc_lo, ctx->st, ctx->status, s, ctx->shape, shared_cells(ctx)),
        "prologue");
     const KickArgs ka{ctx, c, beam->id, beam->n, r.bg, binning};
+    if (sharded) {
+        for (int64_t k = 0; k < nkicks; ++k) {
+            cudaError_t ce = cudaSuccess;
+            rc = kick_sharded(ka, s, &ce);
+            if (rc == BX_COLLECTIVE)
+                return fail(ctx, BX_COLLECTIVE, "the shard's allreduce callback failed");
+            if (rc) return cuda_fail(ctx, ce, "sharded kick");
+        }
+        ctx->kick += nkicks;
+        ctx->green_valid = false;
+        return BX_OK;
+    }
     bool use_graph = !ctx->graphs_off && !profiler_timing(ctx->prof) && !diag;
     if (use_graph) {
         bool same = ctx->kick_exec && ctx->graph_n == beam->n && ctx->graph_id == beam->id &&
@@ -444,6 +469,18 @@ int32_t bx_sync(bx_ctx *ctx, void *stream) {
     if (st & ST_NONFINITE) return fail(ctx, BX_NONFINITE, "non-finite particle coordinates");
     if (st & ST_TIMEOUT) return fail(ctx, BX_DEVICE_TIMEOUT, "a device wait timed out");
     if (st & ST_OUTSIDE) return fail(ctx, BX_BAD_ARG, "a particle lies outside the given box");
+    return BX_OK;
+}
+
+int32_t bx_set_shard(bx_ctx *ctx, const bx_shard *shard) {
+    if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
+    if (!shard) {
+        ctx->shard = bx_shard{};
+        return BX_OK;
+    }
+    if (!shard->allreduce || shard->n_total <= 0)
+        return fail(ctx, BX_BAD_ARG, "a shard needs an allreduce callback and n_total > 0");
+    ctx->shard = *shard;
     return BX_OK;
 }
 

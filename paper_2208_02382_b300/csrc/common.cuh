@@ -132,7 +132,7 @@ constexpr int DEP_SPLIT = 31;
 enum KernelId : int {
     K_PUSH, K_MINMAX, K_BOX, K_IGF_CORNER, K_IGF_SUM, K_DEPOSIT, K_ACC_TO_RHO, K_FFT_X,
     K_FFT_YZ, K_FFT_ZSOLVE, K_FFT_XINV, K_GREEN_X, K_GREEN_YZ, K_FIELD, K_GATHER, K_MOMENTS,
-    K_TWIDDLE, K_EFIX, K_SORT, K_ADJ_PART, K_ADJ_GRID, K_COUNT
+    K_TWIDDLE, K_EFIX, K_SORT, K_ADJ_PART, K_ADJ_GRID, K_ZERO, K_REDEPOSIT, K_COUNT
 };
 
 struct Profiler;
@@ -205,7 +205,7 @@ cudaError_t launch_track_particles(double *const c[6], int64_t n, double betagam
                                    const MapCoef *maps, unsigned long long *acc_hi,
                                    unsigned long long *acc_lo, TrackState *st, int32_t *status,
                                    cudaStream_t s, int part = 3, int shape = 1,
-                                   unsigned long long *cells = nullptr);
+                                   unsigned long long *cells = nullptr, bool runs = false);
 cudaError_t launch_box_rule_graph(TrackState *st, int nn, long long *log, int64_t cap,
                                   cudaGraphConditionalHandle hg, cudaGraphConditionalHandle hs,
                                   cudaGraphConditionalHandle hd, cudaGraphConditionalHandle hn,
@@ -221,7 +221,7 @@ cudaError_t launch_track_particles_oop(double *const cin[6], double *const cout[
 cudaError_t launch_track_deposit(double *const c[6], int64_t n, double betagamma, const Box *box,
                                  int nn, unsigned long long *acc_hi, unsigned long long *acc_lo,
                                  TrackState *st, int32_t *status, cudaStream_t s, int shape = 1,
-                                 unsigned long long *cells = nullptr);
+                                 unsigned long long *cells = nullptr, bool runs = false);
 int map_kind(const MapCoef &m);
 // sort.cu
 int sort_brick_edge(int nn, int be_opt);
@@ -234,7 +234,11 @@ cudaError_t launch_sort(double *const c[6], long long *id, int64_t n, double bet
                         const Box *box, int nn, int be, int *keys, long long *counts,
                         long long *offs, long long *sums, double *const scratch[6],
                         long long *id_scratch, double **dev_ptrs, cudaStream_t s,
-                        const int *gate = nullptr, int *dest_out = nullptr);
+                        const int *gate = nullptr, int *dest_out = nullptr,
+                        bool cell_order = false);
+// Histogram bins the sort scratch needs (cell order adds a pass over the cells
+// of a brick).
+int sort_bins(int nn, int be, bool cell_order);
 // moments.cu
 cudaError_t launch_moments(double *const c[6], int64_t n, double *partials, int nblocks,
                            double *out, cudaStream_t s);

@@ -254,7 +254,7 @@ int32_t ensure_cells(bx_ctx *ctx, int64_t n) {
 
 // Binning scratch for n particles, allocated on the first call for a larger n.
 int32_t ensure_sort_scratch(bx_ctx *ctx, int64_t n) {
-    const int nb = sort_bricks(ctx->n, sort_brick_edge(ctx->n, ctx->bin_edge));
+    const int nb = sort_bins(ctx->n, sort_brick_edge(ctx->n, ctx->bin_edge), ctx->cell_order);
     if (n <= ctx->sort_n && nb == ctx->sort_nb) return BX_OK;
     if (n < ctx->sort_n) n = ctx->sort_n;
     cudaDeviceSynchronize();

@@ -52,6 +52,7 @@ struct bx_ctx {
     int shape = 1;                         // particle shape: 1 CIC, 2 TSC
     int sort_interval = 16;                // kicks between re-binning (0: never)
     int bin_edge = 0;                      // cells per bin edge (0: default)
+    bool cell_order = false;               // re-bin by cell within brick; run deposit
     int sort_nb = 0;                       // bins the sort scratch is sized for
     // per-kick CUDA graph (conditional nodes), rebuilt when the bunch changes
     cudaGraphExec_t kick_exec = nullptr;
@@ -66,6 +67,7 @@ struct bx_ctx {
     bool graphs_off = false;               // the graph path failed once: plain launches
     Profiler *prof = nullptr;
     bt::GradTape *grad = nullptr;          // differentiation tape (grad.cu)
+    bx_shard shard{};                      // sharded run: the collective hook (allreduce set)
     std::string err;
 };
 
@@ -148,6 +150,12 @@ struct KickArgs {
     bool binning;
 };
 cudaError_t kick_plain(const KickArgs &k, cudaStream_t s);
+// One kick of a sharded run: the plain launches of kick_plain with the
+// caller's allreduce of the box keys before the box rule and of the charge
+// accumulators before the solve.  Returns BX_OK, BX_COLLECTIVE (the callback
+// failed) or BX_CUDA (*err holds the CUDA error).
+int32_t kick_sharded(const KickArgs &k, cudaStream_t s, cudaError_t *err);
+inline bool ctx_sharded(const bx_ctx *ctx) { return ctx->shard.allreduce != nullptr; }
 cudaError_t build_kick_graph(const KickArgs &k, cudaGraphExec_t *exec);
 
 }  // namespace bt

@@ -303,6 +303,7 @@ int32_t bx_grad_forward(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat,
     if (rc) return rc;
     if ((rc = check_lattice(ctx, lat))) return rc;
     if (beam->n <= 0) return fail(ctx, BX_BAD_ARG, "differentiation needs particles");
+    if (ctx_sharded(ctx)) return fail(ctx, BX_BAD_ARG, "differentiation of a sharded run is not supported");
     if (checkpoint_interval <= 0) return fail(ctx, BX_BAD_ARG, "checkpoint_interval must be >= 1");
     if (ctx->shape != 1)
         return fail(ctx, BX_BAD_ARG, "the reverse mode supports particle shape 1 (CIC) only");

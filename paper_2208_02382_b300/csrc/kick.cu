@@ -14,6 +14,13 @@
 
 namespace bt {
 
+// The cell-order deposit when the context re-bins by cell (and the particles
+// are re-binned at all); else the particle-order deposit.  Both give bitwise
+// the same charge.
+static bool run_deposit(const bx_ctx *ctx, const KickArgs &k) {
+    return ctx->cell_order && k.binning && ctx->shape == 1;
+}
+
 // The kernels of one device-driven kick, in pieces (so the graph builder can
 // put the gated pieces into conditional bodies).
 cudaError_t kick_green(const KickArgs &k, cudaStream_t s) {
@@ -29,13 +36,14 @@ cudaError_t kick_sort(const KickArgs &k, cudaStream_t s) {
     return launch_sort(k.c, (long long *)k.id, k.n, k.bg, &ctx->st->box, ctx->n,
                        sort_brick_edge(ctx->n, ctx->bin_edge), ctx->keys,
                        ctx->counts, ctx->offs, ctx->sums, ctx->scr, ctx->id_scr, ctx->dev_ptrs, s,
-                       &ctx->st->sort_gate);
+                       &ctx->st->sort_gate, nullptr, ctx->cell_order);
 }
 
 cudaError_t kick_deposit(const KickArgs &k, cudaStream_t s) {
     bx_ctx *ctx = k.ctx;
     return launch_track_deposit(k.c, k.n, k.bg, &ctx->st->box, ctx->n, ctx->acc_hi, ctx->acc_lo,
-                                ctx->st, ctx->status, s, ctx->shape, shared_cells(ctx));
+                                ctx->st, ctx->status, s, ctx->shape, shared_cells(ctx),
+                                run_deposit(ctx, k));
 }
 
 cudaError_t kick_solve_field_push(const KickArgs &k, cudaStream_t s) {
@@ -56,7 +64,7 @@ cudaError_t kick_next_deposit(const KickArgs &k, cudaStream_t s) {
     bx_ctx *ctx = k.ctx;
     return launch_track_particles(k.c, k.n, k.bg, &ctx->st->box, ctx->n, ctx->efix, ctx->escale,
                                   ctx->maps, ctx->acc_hi, ctx->acc_lo, ctx->st, ctx->status, s, 2,
-                                  ctx->shape, shared_cells(ctx));
+                                  ctx->shape, shared_cells(ctx), run_deposit(ctx, k));
 }
 
 // Plain launches of one kick (gated kernels return at once when not needed).
@@ -69,6 +77,33 @@ cudaError_t kick_plain(const KickArgs &k, cudaStream_t s) {
     if (e == cudaSuccess) e = kick_solve_field_push(k, s);
     if (e == cudaSuccess) e = kick_next_deposit(k, s);
     return e;
+}
+
+int32_t kick_sharded(const KickArgs &k, cudaStream_t s, cudaError_t *err) {
+    bx_ctx *ctx = k.ctx;
+    const bx_shard &sh = ctx->shard;
+    *err = cudaSuccess;
+    // the rest-frame extent over all ranks: order-preserving keys, exact
+    int64_t *mm = reinterpret_cast<int64_t *>(ctx->st->mm);
+    if (sh.allreduce(mm, 3, BX_OP_MIN, s, sh.user) != 0) return BX_COLLECTIVE;
+    if (sh.allreduce(mm + 3, 3, BX_OP_MAX, s, sh.user) != 0) return BX_COLLECTIVE;
+    cudaError_t e = launch_box_rule(ctx->st, ctx->n, k.n, ctx->log, ctx->log_cap, true, s);
+    if (e == cudaSuccess) e = kick_green(k, s);
+    if (e == cudaSuccess && k.binning) e = kick_sort(k, s);
+    if (e == cudaSuccess) e = kick_deposit(k, s);
+    if (e != cudaSuccess) {
+        *err = e;
+        return BX_CUDA;
+    }
+    // the bunch's charge: integer sums, independent of the split
+    const int64_t n3 = (int64_t)ctx->n * ctx->n * ctx->n;
+    if (sh.allreduce(reinterpret_cast<int64_t *>(ctx->acc_hi), n3, BX_OP_SUM, s, sh.user) != 0 ||
+        sh.allreduce(reinterpret_cast<int64_t *>(ctx->acc_lo), n3, BX_OP_SUM, s, sh.user) != 0)
+        return BX_COLLECTIVE;
+    e = kick_solve_field_push(k, s);
+    if (e == cudaSuccess) e = kick_next_deposit(k, s);
+    *err = e;
+    return e == cudaSuccess ? BX_OK : BX_CUDA;
 }
 
 // Adds an IF node on condition `h` at the current point of the capture on
@@ -237,6 +272,8 @@ int32_t bx_batch_create(bx_batch **out, int32_t count, bx_ctx *const *ctxs,
             if (ctxs[u] == ctxs[v])
                 return batch_fail(nullptr, BX_BAD_ARG, "a context appears twice in the batch");
         bx_ctx *ctx = ctxs[v];
+        if (ctx_sharded(ctx))
+            return batch_fail(nullptr, BX_BAD_ARG, "problem " + std::to_string(v) + ": sharded context");
         int32_t rc = check_beam(ctx, beams[v]);
         if (!rc) rc = check_lattice(ctx, lattices[v]);
         if (rc) return batch_fail(nullptr, rc, "problem " + std::to_string(v) + ": " + ctx->err);

@@ -8,8 +8,14 @@
 // its scratch.  bx_deposit_noalloc instead keeps the fixed-point accumulators
 // of the deposition in a file-scope device array of fixed size that the
 // library holds on every GPU that loads it, until the process exits.  The
-// caller passes the particles and the output grid; nothing is allocated or
-// freed by the call.
+// caller passes the particles, the output grid and, optionally, a word for the
+// flags of skipped particles; nothing is allocated or freed by the call.
+//
+// The per-particle arithmetic is the context deposit's (bx_deposit with
+// use_box = 1): the same box constants, u = (X - lo)/h, cells and 52-bit
+// fractions (cell_frac), fixed-point CIC weights (cic_weights) and the
+// same split of the 51-bit weights into the two integer accumulators, so the
+// two give bitwise the same charge density.
 //
 // Limits and sharing: at most NOALLOC_MAX_NODES = 64^3 grid nodes (n <= 64),
 // i.e. 2 x 64^3 x 8 bytes = 4 MiB of accumulators.  Every call on a device
@@ -22,7 +28,8 @@
 #include <cmath>
 #include <mutex>
 
-#include "common.cuh"
+#include "ctx.cuh"
+#include "particle_math.cuh"
 
 namespace bt {
 
@@ -34,78 +41,63 @@ static __device__ __align__(256) unsigned long long g_noalloc_acc[2 * NOALLOC_MA
 
 namespace {
 
-struct BoxV {
-    double lo[3], h[3], inv_h[3];
-};
-
-__device__ __forceinline__ unsigned long long na_to_fixed52(double u) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(u);
-    int e = (int)((b >> 52) & 0x7FF) - 1023;
-    if (e < -60 || u <= 0.0) return 0ull;
-    unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    return e >= 0 ? (mant << e) : (mant >> (-e));
-}
-
-__device__ __forceinline__ unsigned long long na_mulshr52(unsigned long long a,
-                                                         unsigned long long b) {
-    unsigned long long lo = a * b, hi = __umul64hi(a, b);
-    return (hi << 12) | (lo >> 52);
-}
-
-// Same arithmetic as the context deposit: CIC weights in unsigned fixed point,
-// summed by integer atomics (order-independent).  Particles outside the box
-// are skipped.
+// One particle per thread (grid-stride): its cell and weights as the context
+// deposit forms them, added to the 8 nodes with 64-bit integer atomics
+// (order-independent sums).  Particles outside the box (as the context
+// deposit decides it) and particles with a non-finite position are skipped
+// and reported in *flags (when given).
+template <bool EX>
 __global__ void k_deposit_noalloc(const double *__restrict__ x, const double *__restrict__ y,
-                                  const double *__restrict__ t, int64_t n, double nbg, BoxV box,
-                                  int nn, unsigned long long *__restrict__ acc) {
+                                  const double *__restrict__ t, int64_t n, double nbg, Box box,
+                                  int nn, unsigned long long *__restrict__ acc,
+                                  int32_t *__restrict__ flags) {
     unsigned long long *acc_hi = acc, *acc_lo = acc + (long long)nn * nn * nn;
-    const unsigned long long one = 1ull << 52;
-    const unsigned long long umax = (unsigned long long)(nn - 1) << 52;
+    bool any_out = false, any_bad = false;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
-        double u[3];
-        u[0] = (x[p] - box.lo[0]) * box.inv_h[0];
-        u[1] = (y[p] - box.lo[1]) * box.inv_h[1];
-        u[2] = (__dmul_rn(nbg, t[p]) - box.lo[2]) * box.inv_h[2];
-        int cell[3];
-        unsigned long long w[3][2];
+        const double xp = x[p], yp = y[p], tp = t[p];
+        any_bad |= nonfinite_bits(xp) || nonfinite_bits(yp) || nonfinite_bits(tp);
+        double u0, u1, u2;
+        box_u<EX>(box, nbg, xp, yp, tp, u0, u1, u2);
+        int c0, c1, c2;
+        unsigned long long F0, F1, F2;
         bool outside = false;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            outside |= !(u[d] >= 0.0) || u[d] > (double)(nn - 1) + 1e-6;
-            unsigned long long U = na_to_fixed52(u[d]);
-            if (U > umax) U = umax;
-            unsigned long long i = U >> 52;
-            if (i > (unsigned long long)(nn - 2)) i = nn - 2;
-            unsigned long long f = U - (i << 52);
-            cell[d] = (int)i;
-            w[d][0] = one - f;
-            w[d][1] = f;
+        cell_frac(u0, nn, c0, F0, outside);
+        cell_frac(u1, nn, c1, F1, outside);
+        cell_frac(u2, nn, c2, F2, outside);
+        if (outside) {
+            any_out = true;
+            continue;
         }
-        if (outside) continue;
-        const long long base = ((long long)cell[2] * nn + cell[1]) * nn + cell[0];
+        unsigned long long wc[8];
+        cic_weights(F0, F1, F2, wc);
+        const long long base = ((long long)c2 * nn + c1) * nn + c0;
 #pragma unroll
         for (int dz = 0; dz < 2; ++dz)
 #pragma unroll
             for (int dy = 0; dy < 2; ++dy) {
-                unsigned long long wyz = na_mulshr52(w[1][dy], w[2][dz]);
 #pragma unroll
                 for (int dx = 0; dx < 2; ++dx) {
-                    unsigned long long v = na_mulshr52(w[0][dx], wyz) >> 1;
-                    long long node = base + ((long long)dz * nn + dy) * nn + dx;
+                    const unsigned long long v = wc[(dz * 2 + dy) * 2 + dx];
+                    const long long node = base + ((long long)dz * nn + dy) * nn + dx;
                     atomicAdd(&acc_hi[node], v >> DEP_SPLIT);
                     atomicAdd(&acc_lo[node], v & ((1ull << DEP_SPLIT) - 1));
                 }
             }
     }
+    if (flags && (any_out || any_bad))
+        atomicOr(flags, (any_out ? BX_NOALLOC_OUTSIDE : 0) | (any_bad ? BX_NOALLOC_NONFINITE : 0));
 }
 
-__global__ void k_acc_to_rho_noalloc(const unsigned long long *__restrict__ acc, int nn,
-                                     double scale, double *__restrict__ rho) {
+// rho[node] = q W / (hx hy hz), W = (hi 2^31 + lo) 2^-51 (the context's conversion).
+__global__ void k_acc_to_rho_noalloc(const unsigned long long *__restrict__ acc, int nn, Box box,
+                                     double q_macro, double *__restrict__ rho) {
     const long long nodes = (long long)nn * nn * nn;
+    const double vol = box.h[0] * box.h[1] * box.h[2];
+    const double scale = q_macro / vol;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nodes;
          i += (long long)gridDim.x * blockDim.x) {
-        double w = ((double)acc[i] * 2147483648.0 + (double)acc[nodes + i]) * 0x1p-51;
+        const double w = ((double)acc[i] * 2147483648.0 + (double)acc[nodes + i]) * 0x1p-51;
         rho[i] = scale * w;
     }
 }
@@ -136,7 +128,8 @@ static cudaError_t noalloc_scratch(unsigned long long **out) {
 }  // namespace bt
 
 extern "C" int32_t bx_deposit_noalloc(const bx_beam *beam, const double lo[3], const double hi[3],
-                                      int32_t n, double *rho, void *stream) {
+                                      int32_t n, double *rho, int32_t *flags_device,
+                                      void *stream) {
     using namespace bt;
     if (!beam || !lo || !hi || !rho) return set_noctx_error(BX_BAD_ARG, "NULL argument");
     if (n < 8 || n > NOALLOC_MAX_N || (n & (n - 1)) != 0)
@@ -151,14 +144,11 @@ extern "C" int32_t bx_deposit_noalloc(const bx_beam *beam, const double lo[3], c
         !(beam->charge_sign == 1.0 || beam->charge_sign == -1.0) ||
         !std::isfinite(beam->bunch_charge_C))
         return set_noctx_error(BX_BAD_ARG, "beam species or charge invalid");
-    BoxV b;
-    for (int d = 0; d < 3; ++d) {
+    for (int d = 0; d < 3; ++d)
         if (!(hi[d] > lo[d]) || !std::isfinite(lo[d]) || !std::isfinite(hi[d]))
             return set_noctx_error(BX_BAD_ARG, "box needs finite lo < hi");
-        b.lo[d] = lo[d];
-        b.h[d] = (hi[d] - lo[d]) / (double)(n - 1);
-        b.inv_h[d] = 1.0 / b.h[d];
-    }
+    const Ref r = make_ref(beam);
+    const Box b = explicit_box(lo, hi, n, r.bg);
     unsigned long long *acc = nullptr;
     cudaError_t e = noalloc_scratch(&acc);
     if (e != cudaSuccess) return set_noctx_error(BX_CUDA, cudaGetErrorString(e));
@@ -166,19 +156,20 @@ extern "C" int32_t bx_deposit_noalloc(const bx_beam *beam, const double lo[3], c
     const long long nodes = (long long)n * n * n;
     e = cudaMemsetAsync(acc, 0, 2 * nodes * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return set_noctx_error(BX_CUDA, cudaGetErrorString(e));
-    const double gamma = 1.0 + beam->kinetic_MeV / beam->mass_MeV;
-    const double bg = std::sqrt(gamma * gamma - 1.0);
     if (beam->n > 0) {
         long long blocks = (beam->n + 255) / 256;
         if (blocks > 148 * 16) blocks = 148 * 16;
-        k_deposit_noalloc<<<(int)blocks, 256, 0, s>>>(beam->coord[0], beam->coord[2],
-                                                      beam->coord[4], beam->n, -bg, b, n, acc);
+        if (box_far_offset(b))
+            k_deposit_noalloc<true><<<(int)blocks, 256, 0, s>>>(
+                beam->coord[0], beam->coord[2], beam->coord[4], beam->n, -r.bg, b, n, acc,
+                flags_device);
+        else
+            k_deposit_noalloc<false><<<(int)blocks, 256, 0, s>>>(
+                beam->coord[0], beam->coord[2], beam->coord[4], beam->n, -r.bg, b, n, acc,
+                flags_device);
     }
-    const double q = beam->n > 0 ? beam->charge_sign * std::fabs(beam->bunch_charge_C) /
-                                       (double)beam->n
-                                 : 0.0;
-    const double scale = q / (b.h[0] * b.h[1] * b.h[2]);
-    k_acc_to_rho_noalloc<<<(int)((nodes + 255) / 256), 256, 0, s>>>(acc, n, scale, rho);
+    const double q = beam->n > 0 ? r.sign * std::fabs(beam->bunch_charge_C) / (double)beam->n : 0.0;
+    k_acc_to_rho_noalloc<<<(int)((nodes + 255) / 256), 256, 0, s>>>(acc, n, b, q, rho);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_noctx_error(BX_CUDA, cudaGetErrorString(e));
     return BX_OK;

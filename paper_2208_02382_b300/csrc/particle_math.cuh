@@ -113,4 +113,46 @@ __device__ __forceinline__ void cell_frac(double u, int nn, int &cell, unsigned 
     cell = (int)i;
 }
 
+// u = (X - lo)/h per dimension of a particle at (x, y, t) (rest frame:
+// Z = -beta gamma t): one FMA with the box's constants, X * (1/h) - lo/h, or,
+// for a box far from the origin relative to its cell size (EX), the
+// subtraction first.
+template <bool EX>
+__device__ __forceinline__ void box_u(const Box &b, double nbg, double x, double y, double t,
+                                      double &u0, double &u1, double &u2) {
+    u0 = EX ? (x - b.lo[0]) * b.inv_h[0] : fma(x, b.inv_h[0], b.off[0]);
+    u1 = EX ? (y - b.lo[1]) * b.inv_h[1] : fma(y, b.inv_h[1], b.off[1]);
+    u2 = EX ? (__dmul_rn(nbg, t) - b.lo[2]) * b.inv_h[2] : fma(t, b.tz, b.off[2]);
+}
+
+// floor(a b / 2^51) for a, b <= 2^51, exact (full 64 x 64 -> 128-bit product).
+__device__ __forceinline__ unsigned long long mulfloor51(unsigned long long a, unsigned long long b) {
+    return (__umul64hi(a, b) << 13) | ((a * b) >> 51);
+}
+
+// CIC weights of a particle in its cell as unsigned fixed point with
+// DEP_FRAC_BITS = 51 fractional bits, from the cell fractions F_d (52 bits;
+// the lowest is dropped: u itself carries at most 46 fractional bits on grids
+// of 128 nodes).  With X, Y, Z the fractions and 1 = 2^51: P = floor(X Y),
+// the four x-y weights (1-X)(1-Y) = 1 - X - Y + P, X(1-Y) = X - P,
+// (1-X)Y = Y - P, XY = P, then each times Z: q = floor(W Z) to the node at
+// z+1 and W - q to the node at z.  Five exact floor products; every weight is
+// non-negative (each is its exact value minus the dropped fractions of at most
+// its own products, and an integer) and the eight sum to exactly 1, so the
+// deposit conserves charge exactly.  w[(dz*2 + dy)*2 + dx] is node
+// (c0 + dx, c1 + dy, c2 + dz).
+__device__ __forceinline__ void cic_weights(unsigned long long F0, unsigned long long F1,
+                                            unsigned long long F2, unsigned long long w[8]) {
+    const unsigned long long one = 1ull << DEP_FRAC_BITS;
+    const unsigned long long X = F0 >> 1, Y = F1 >> 1, Z = F2 >> 1;
+    const unsigned long long P = mulfloor51(X, Y);
+    const unsigned long long wxy[4] = {one - X - Y + P, X - P, Y - P, P};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned long long q = mulfloor51(wxy[k], Z);
+        w[k] = wxy[k] - q;
+        w[4 + k] = q;
+    }
+}
+
 }  // namespace bt

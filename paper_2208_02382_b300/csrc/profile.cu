@@ -28,7 +28,7 @@ static const char *const kNames[K_COUNT] = {
     "push_maps", "minmax", "box_rule", "igf_corner", "igf_sum", "deposit", "acc_to_rho",
     "fft_x", "fft_yz", "fft_zsolve", "fft_xinv", "green_x", "green_yz", "field",
     "gather_kick_push", "moments", "twiddle", "efix", "sort", "adjoint_particles",
-    "adjoint_grid"};
+    "adjoint_grid", "zero_acc", "redeposit"};
 
 const char *kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? kNames[id] : ""; }
 

@@ -14,6 +14,13 @@
 //            of its brick (warp match_any, warps taking turns in order);
 //            writes the six coordinates and the id to scratch arrays, which
 //            are then copied back over the caller's arrays.
+// Cell order (bx_set_binning's cell_order): a first pass keyed by the cell's
+// index within its brick writes the scratch arrays, a second (stable) pass
+// keyed by the brick writes the caller's arrays back: particles ordered by
+// brick and within a brick by cell, so runs of particles share a cell and the
+// deposit adds each run's weights once (particles.cu, k_deposit_runs).
+#include <algorithm>
+
 #include "common.cuh"
 #include "fixed.cuh"
 
@@ -37,8 +44,10 @@ bool sort_brick_edge_valid(int nn, int be) {
 }
 int64_t sort_chunks(int64_t n) { return (n + SORT_CHUNK - 1) / SORT_CHUNK; }
 
+// Sort key of a particle: its brick (mode 0) or its cell's index within the
+// brick, x fastest (mode 1).
 __device__ __forceinline__ int brick_of(double x, double y, double t, double nbg, const Box &b,
-                                        int nn, int be) {
+                                        int nn, int be, int mode) {
     const double u[3] = {(x - b.lo[0]) * b.inv_h[0], (y - b.lo[1]) * b.inv_h[1],
                          (__dmul_rn(nbg, t) - b.lo[2]) * b.inv_h[2]};
     const int lb = __ffs(be) - 1;   // be is a power of two
@@ -48,9 +57,9 @@ __device__ __forceinline__ int brick_of(double x, double y, double t, double nbg
     for (int d = 0; d < 3; ++d) {
         long long c = (long long)(to_fixed52(u[d]) >> 52);  // outside: clamped
         if (c > nn - 2) c = nn - 2;
-        k[d] = (int)(c >> lb);
+        k[d] = mode ? (int)(c & (be - 1)) : (int)(c >> lb);
     }
-    return (k[2] * nb + k[1]) * nb + k[0];
+    return mode ? (k[2] * be + k[1]) * be + k[0] : (k[2] * nb + k[1]) * nb + k[0];
 }
 
 __global__ void k_sort_keys(const double *__restrict__ x, const double *__restrict__ y,
@@ -58,7 +67,7 @@ __global__ void k_sort_keys(const double *__restrict__ x, const double *__restri
                             const Box *__restrict__ box, int nn, int be, int nbricks,
                             int64_t nchunks, int *__restrict__ keys,
                             long long *__restrict__ counts, const int *gate,
-                            const double *const *ptrs) {
+                            const double *const *ptrs, int mode) {
     if (gate && *gate == 0) return;
     if (ptrs) {
         x = ptrs[0];
@@ -73,7 +82,7 @@ __global__ void k_sort_keys(const double *__restrict__ x, const double *__restri
     for (int r = 0; r < SORT_ROUNDS; ++r) {
         const int64_t p = base + r * SORT_TPB + threadIdx.x;
         if (p >= n) break;
-        const int k = brick_of(x[p], y[p], t[p], nbg, b, nn, be);
+        const int k = brick_of(x[p], y[p], t[p], nbg, b, nn, be, mode);
         keys[p] = k;
         atomicAdd(&hist[k], 1);
     }
@@ -193,44 +202,71 @@ __global__ void k_sort_copy_back(double *const *__restrict__ ptrs, const long lo
     }
 }
 
-// dev_ptrs (device, 12 pointers) must hold the six coordinate arrays then the
-// six scratch arrays (sort_set_pointers).  With `gate`, every kernel returns
-// at once unless *gate is set.
+// dev_ptrs (device, 24 pointers) must hold the six coordinate arrays then the
+// six scratch arrays, then the same twelve with the halves swapped
+// (sort_set_pointers).  With `gate`, every kernel returns at once unless *gate
+// is set.
 cudaError_t sort_set_pointers(double *const c[6], double *const scratch[6], double **dev_ptrs,
                               cudaStream_t s) {
-    double *h[12];
+    double *h[24];
     for (int k = 0; k < 6; ++k) {
-        h[k] = c[k];
-        h[6 + k] = scratch[k];
+        h[k] = h[18 + k] = c[k];
+        h[6 + k] = h[12 + k] = scratch[k];
     }
     return cudaMemcpyAsync(dev_ptrs, h, sizeof(h), cudaMemcpyHostToDevice, s);
 }
 
-cudaError_t launch_sort(double *const c[6], long long *id, int64_t n, double betagamma,
-                        const Box *box, int nn, int be, int *keys, long long *counts,
-                        long long *offs, long long *sums, double *const scratch[6],
-                        long long *id_scratch, double **dev_ptrs, cudaStream_t s,
-                        const int *gate, int *dest_out) {
-    if (n <= 0) return cudaSuccess;
-    (void)c;
-    (void)scratch;
+int sort_bins(int nn, int be, bool cell_order) {
     const int nb = sort_bricks(nn, be);
+    return cell_order ? std::max(nb, be * be * be) : nb;
+}
+
+// One stable counting-sort pass over the keys of `mode` (see brick_of): the
+// coordinates named by ptrs[0..5] and ids id_src go to ptrs[6..11] and id_dst.
+static cudaError_t sort_pass(int64_t n, double nbg, const Box *box, int nn, int be, int mode,
+                             int *keys, long long *counts, long long *offs, long long *sums,
+                             const long long *id_src, long long *id_dst, double **ptrs,
+                             cudaStream_t s, const int *gate, int *dest_out) {
+    const int nb = mode ? be * be * be : sort_bricks(nn, be);
     const int64_t nch = sort_chunks(n);
     const size_t hsm = (size_t)nb * sizeof(int);
     cudaFuncSetAttribute(k_sort_keys, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
     cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm);
-    const double *const *dp = (const double *const *)dev_ptrs;
+    const double *const *dp = (const double *const *)ptrs;
     BT_LAUNCH(K_SORT, s, k_sort_keys<<<(unsigned)nch, SORT_TPB, hsm, s>>>(
-                             nullptr, nullptr, nullptr, n, -betagamma, box, nn, be, nb, nch, keys,
-                             counts, gate, dp));
+                             nullptr, nullptr, nullptr, n, nbg, box, nn, be, nb, nch, keys,
+                             counts, gate, dp, mode));
     const long long len = (long long)nb * nch;
     const long long nt = (len + SCAN_TILE - 1) / SCAN_TILE;
     BT_LAUNCH(K_SORT, s, k_scan_tiles<<<(unsigned)nt, SORT_TPB, 0, s>>>(counts, len, sums, gate));
     BT_LAUNCH(K_SORT, s, k_scan_sums<<<1, 32, 0, s>>>(sums, nt, gate));
     BT_LAUNCH(K_SORT, s, k_scan_apply<<<(unsigned)nt, SORT_TPB, 0, s>>>(counts, len, sums, offs, gate));
     BT_LAUNCH(K_SORT, s, k_sort_scatter<<<(unsigned)nch, SORT_TPB, hsm, s>>>(
-                             keys, offs, n, nb, nch, dp, id, (double *const *)(dev_ptrs + 6),
-                             id_scratch, gate, dest_out));
+                             keys, offs, n, nb, nch, dp, id_src, (double *const *)(ptrs + 6),
+                             id_dst, gate, dest_out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort(double *const c[6], long long *id, int64_t n, double betagamma,
+                        const Box *box, int nn, int be, int *keys, long long *counts,
+                        long long *offs, long long *sums, double *const scratch[6],
+                        long long *id_scratch, double **dev_ptrs, cudaStream_t s,
+                        const int *gate, int *dest_out, bool cell_order) {
+    if (n <= 0) return cudaSuccess;
+    (void)c;
+    (void)scratch;
+    if (cell_order && !dest_out) {
+        // by cell within brick into the scratch arrays, then (stable) by brick
+        // back into the caller's arrays: ordered by brick, then by cell
+        cudaError_t e = sort_pass(n, -betagamma, box, nn, be, 1, keys, counts, offs, sums, id,
+                                  id_scratch, dev_ptrs, s, gate, nullptr);
+        if (e != cudaSuccess) return e;
+        return sort_pass(n, -betagamma, box, nn, be, 0, keys, counts, offs, sums, id_scratch, id,
+                         dev_ptrs + 12, s, gate, nullptr);
+    }
+    cudaError_t e = sort_pass(n, -betagamma, box, nn, be, 0, keys, counts, offs, sums, id,
+                              id_scratch, dev_ptrs, s, gate, dest_out);
+    if (e != cudaSuccess) return e;
     const int cb = (int)((n + 255) / 256) < 148 * 16 ? (int)((n + 255) / 256) : 148 * 16;
     BT_LAUNCH(K_SORT, s, k_sort_copy_back<<<cb, 256, 0, s>>>(dev_ptrs, id_scratch, id, n, gate));
     return cudaGetLastError();

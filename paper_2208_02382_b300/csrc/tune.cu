@@ -14,16 +14,20 @@ using namespace bt;
 
 extern "C" {
 
-int32_t bx_set_binning(bx_ctx *ctx, int32_t rebin_interval, int32_t bin_edge) {
+int32_t bx_set_binning(bx_ctx *ctx, int32_t rebin_interval, int32_t bin_edge,
+                       int32_t cell_order) {
     if (!ctx) return set_noctx_error(BX_BAD_ARG, "NULL context");
     if (rebin_interval < -1) return fail(ctx, BX_BAD_ARG, "rebin_interval must be >= -1");
     if (bin_edge != 0 && !sort_brick_edge_valid(ctx->n, bin_edge))
         return fail(ctx, BX_BAD_ARG,
                     "bin_edge must be 0 or a power of two in [2, n/2] giving at most 16^3 bins");
+    if (cell_order != 0 && cell_order != 1) return fail(ctx, BX_BAD_ARG, "cell_order must be 0 or 1");
     const int interval = rebin_interval == 0 ? 16 : rebin_interval < 0 ? 0 : rebin_interval;
-    if (interval != ctx->sort_interval || bin_edge != ctx->bin_edge) {
+    if (interval != ctx->sort_interval || bin_edge != ctx->bin_edge ||
+        (cell_order != 0) != ctx->cell_order) {
         ctx->sort_interval = interval;
         ctx->bin_edge = bin_edge;
+        ctx->cell_order = cell_order != 0;
         // the per-kick graph holds the sort's launch parameters
         if (ctx->kick_exec) {
             cudaDeviceSynchronize();
@@ -35,13 +39,14 @@ int32_t bx_set_binning(bx_ctx *ctx, int32_t rebin_interval, int32_t bin_edge) {
 }
 
 int32_t bx_autotune_binning(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int32_t kicks,
-                            int32_t chosen[2], double *ms, int32_t cap, int32_t *count,
+                            int32_t chosen[3], double *ms, int32_t cap, int32_t *count,
                             void *stream) {
     if (!ctx) return set_noctx_error(BX_BAD_ARG, "NULL context");
     int32_t rc = check_beam(ctx, beam);
     if (rc) return rc;
     if ((rc = check_lattice(ctx, lat))) return rc;
     if (!chosen) return fail(ctx, BX_BAD_ARG, "chosen is NULL");
+    if (ctx_sharded(ctx)) return fail(ctx, BX_BAD_ARG, "tune a sharded context on one rank first");
     if (!beam->id || beam->n <= 0) return fail(ctx, BX_BAD_ARG, "tuning needs particles with ids");
     if (kicks <= 0) return fail(ctx, BX_BAD_ARG, "kicks must be >= 1");
     cudaStream_t s = (cudaStream_t)stream;
@@ -50,13 +55,18 @@ int32_t bx_autotune_binning(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, i
     const int64_t nk = std::min<int64_t>(kicks, total);
     // candidates: never; every 8, 16, 32 or 64 kicks (intervals no longer
     // than the timed window, so that each candidate's window holds its sorts)
-    // with each valid edge of 4, 8, 16
-    std::vector<std::pair<int, int>> cand;
-    cand.push_back({-1, 0});
-    for (int iv : {8, 16, 32, 64})
-        if (iv <= nk)
-            for (int be : {4, 8, 16})
-                if (sort_brick_edge_valid(ctx->n, be)) cand.push_back({iv, be});
+    // with each valid edge of 4, 8, 16, in bin order and in cell order (the
+    // cell-order deposit is CIC only)
+    struct Cand {
+        int iv, be, co;
+    };
+    std::vector<Cand> cand;
+    cand.push_back({-1, 0, 0});
+    for (int co = 0; co < (ctx->shape == 1 ? 2 : 1); ++co)
+        for (int iv : {8, 16, 32, 64})
+            if (iv <= nk)
+                for (int be : {4, 8, 16})
+                    if (sort_brick_edge_valid(ctx->n, be)) cand.push_back({iv, be, co});
     if (count) *count = (int32_t)cand.size();
     // save the bunch
     const int64_t n = beam->n;
@@ -85,8 +95,9 @@ int32_t bx_autotune_binning(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, i
     int best = -1;
     float best_ms = 0.0f;
     const int old_iv = ctx->sort_interval == 0 ? -1 : ctx->sort_interval, old_be = ctx->bin_edge;
+    const int old_co = ctx->cell_order ? 1 : 0;
     for (size_t c = 0; c < cand.size() && e == cudaSuccess && rc == BX_OK; ++c) {
-        if ((rc = bx_set_binning(ctx, cand[c].first, cand[c].second))) break;
+        if ((rc = bx_set_binning(ctx, cand[c].iv, cand[c].be, cand[c].co))) break;
         // one untimed pass builds the kick graph for these parameters
         for (int rep = 0; rep < 2 && rc == BX_OK && e == cudaSuccess; ++rep) {
             e = restore();
@@ -115,11 +126,12 @@ int32_t bx_autotune_binning(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, i
     if (e1) cudaEventDestroy(e1);
     cudaFree(save);
     if (rc == BX_OK && e == cudaSuccess && best >= 0) {
-        rc = bx_set_binning(ctx, cand[best].first, cand[best].second);
-        chosen[0] = cand[best].first;
-        chosen[1] = cand[best].second;
+        rc = bx_set_binning(ctx, cand[best].iv, cand[best].be, cand[best].co);
+        chosen[0] = cand[best].iv;
+        chosen[1] = cand[best].be;
+        chosen[2] = cand[best].co;
     } else {
-        bx_set_binning(ctx, old_iv, old_be);
+        bx_set_binning(ctx, old_iv, old_be, old_co);
     }
     if (rc == BX_OK) rc = bx_reset(ctx);
     if (rc) return rc;

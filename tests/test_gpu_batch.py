@@ -121,10 +121,10 @@ def test_binning_autotuner_keeps_results_and_beam(bt):
     beam = _beam(bt, sp, c)
     before = beam.coords.clone()
     ids_before = beam.ids.clone()
-    (iv, be), ms = trk.autotune_binning(beam, lat, kicks=12)
+    (iv, be, co), ms = trk.autotune_binning(beam, lat, kicks=12)
     assert torch.equal(beam.coords, before) and torch.equal(beam.ids, ids_before)
     assert len(ms) >= 2 and all(v > 0 for v in ms)
-    assert iv in (-1, 8, 32) and (iv == -1 or be in (4, 8, 16))
+    assert iv in (-1, 8, 32) and (iv == -1 or be in (4, 8, 16)) and co in (0, 1)
     trk.track(beam, lat)
     trk.sync()
     ref = bt.Tracker(grid)
@@ -141,6 +141,10 @@ def test_binning_options_validated(bt):
         bt.Tracker(32, bin_edge=3)
     with pytest.raises(Exception):
         bt.Tracker(32, rebin_interval=-2)
+    with pytest.raises(Exception):
+        bt.Tracker(32, cell_order=2)
     t = bt.Tracker(64, rebin_interval=-1, bin_edge=4)
     with pytest.raises(Exception):
         t.set_binning(8, 64)
+    with pytest.raises(Exception):
+        t.set_binning(8, 8, -1)

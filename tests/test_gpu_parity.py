@@ -372,3 +372,28 @@ def test_graph_and_plain_launch_paths_agree_bitwise(bt):
     assert np.array_equal(outs[0][1], outs[1][1])
     assert np.array_equal(outs[0][0], outs[1][0])
     assert outs[0][2] == outs[1][2] and len(outs[0][2]) > 3
+
+
+@pytest.mark.parametrize("workload,npart,n,nk,be", [("fodo_1e4_32", 9_001, 16, 40, 4),
+                                                    ("fodo_1e6_64", 200_003, 64, 12, 8),
+                                                    ("chicane_25e6_128", 150_001, 128, 10, 8)])
+def test_cell_order_deposit_is_bitwise_the_bin_order_one(bt, workload, npart, n, nk, be):
+    """Re-binning by cell within bin and the run deposit (consecutive particles
+    of one cell summed in registers, a warp reduction when a warp's lanes end
+    on one cell) against re-binning by bin with the particle-order tile
+    deposit: the same integer charge, so bitwise the same coordinates and
+    regrid log, re-binning every 4 kicks (each sort inside the window)."""
+    w = bg.workload(workload)
+    c = w.particles(npart)
+    outs = []
+    for co in (0, 1):
+        beam = gpu_beam(bt, c, w.species, w.bunch_charge_C)
+        trk = bt.Tracker(n, rebin_interval=4, bin_edge=be, cell_order=co)
+        trk.track(beam, w.lattice, 0, nk)
+        trk.sync()
+        outs.append((to_np(beam), trk.regrid_log()))
+        trk.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
+    otr = tr.Tracker(oracle_ref(w.species), w.bunch_charge_C, n)
+    assert coord_rel_err(outs[1][0], otr.track(c, w.lattice, 0, nk)) <= REL_TOL
