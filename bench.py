@@ -93,6 +93,9 @@ def parse():
                    help="skip the TSC / thin-multipole / per-slice-diagnostics measurements")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the batched-variants measurement (batch_256_fodo)")
+    p.add_argument("--binning", default=None,
+                   help="rebin_interval,bin_edge,cell_order instead of the autotuner "
+                        "(profiling runs)")
     p.add_argument("--no-full-lattice", action="store_true",
                    help="skip the timing of the whole 500-kick lattice beside the headline")
     p.add_argument("--particles", type=int, default=None,
@@ -289,7 +292,7 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
-def grad_bench(dev, checkpoint_interval: int = 20, fd_params=(3, 9)):
+def grad_bench(dev, checkpoint_interval: int = 20):
     """Reverse-mode gradient of the final (eps_x, eps_y, sigma_x, sigma_y) of the
     fodo8_grad_1e6_64 workload (1e6-particle Twiss bunch, 8 quadrupole
     strengths x 5 super-periods, 200 kicks, 64^3 grid, checkpoints every 20
@@ -297,8 +300,10 @@ def grad_bench(dev, checkpoint_interval: int = 20, fd_params=(3, 9)):
     T_fwd: plain tracking of the same bunch (bx_track, the default path).
     A gradient costs the recording forward plus the reverse pass (recompute +
     adjoint, T_bwd); their sum is compared with T_fwd.  T_fd: 2 x 14 forward
-    runs.  Central differences (box sequence replayed) are checked on a few
-    parameters at h = 1e-6 and 1e-8 relative."""
+    runs.  Central differences of all 14 parameters at h = 1e-6 and 1e-8
+    (relative), with the box sequence of the unperturbed run replayed (the
+    function the gradient differentiates) and, beside it, with the box rule
+    live."""
     import torch
     import paper_2208_02382_b300 as btk
     w = bg.workload("fodo8_grad_1e6_64")
@@ -308,7 +313,7 @@ def grad_bench(dev, checkpoint_interval: int = 20, fd_params=(3, 9)):
     ks = list(bg.KS_FODO8)
     tw = list(bg.TWISS_FODO)
     lat = w.lattice
-    fam = bg.fodo8_families(lat)
+    fam = [int(v) for v in bg.fodo8_families(lat)]
     weights = [1.0, 1.0, 1.0, 1.0]
     stream = torch.cuda.current_stream()
 
@@ -336,50 +341,39 @@ def grad_bench(dev, checkpoint_interval: int = 20, fd_params=(3, 9)):
         boxes = g.grad_boxes()
         (dk_el, S, _), t_gb = timed(lambda: g.grad_backward(gbeam, weights, want_zbar0=False))
     g.sync()
-    dk = np.zeros(8)
-    for d, f in zip(dk_el, fam):
-        if f >= 0:
-            dk[f] += d
+    dk = np.array(btk.family_grad(dk_el, fam, 8))
     dtw = np.array(btk.twiss_grad(tw, S))
     grad = np.concatenate([dk, dtw])
-    # central differences on the replayed box sequence
+    names = [f"k{i}" for i in range(8)] + ["alpha_x", "beta_x", "eps_x", "alpha_y", "beta_y",
+                                           "eps_y"]
     fdt = btk.Tracker(w.n_grid)
 
-    def objective(kk, tt):
+    def objective(kk, tt, replay):
         els = bg.fodo8_lattice(kk, 5, 2)
         b = btk.Beam(btk.twiss_beam(tt, xi), sp, w.bunch_charge_C)
-        fdt.grad_forward(b, els, w.kicks, box_replay=boxes)
-        m = fdt.moments(b).cpu().numpy()
-        o = [math.sqrt(m[6] * m[12] - m[7] ** 2), math.sqrt(m[17] * m[21] - m[18] ** 2),
-             math.sqrt(m[6]), math.sqrt(m[17])]
-        return float(np.dot(weights, o))
+        fdt.grad_forward(b, els, w.kicks, box_replay=boxes if replay else None)
+        return float(np.dot(weights, btk.objectives(fdt.moments(b).cpu().tolist())))
 
     fd_out = {}
-    for h in (1e-6, 1e-8):
-        errs = []
-        for pi in fd_params:
-            kk, tt = list(ks), list(tw)
-            if pi < 8:
-                d = h * abs(kk[pi])
-                kk[pi] += d
-                fp = objective(kk, tt)
-                kk[pi] -= 2 * d
-                fm = objective(kk, tt)
-                scale = np.max(np.abs(dk))
-            else:
-                d = h * abs(tt[pi - 8])
-                tt[pi - 8] += d
-                fp = objective(kk, tt)
-                tt[pi - 8] -= 2 * d
-                fm = objective(kk, tt)
-                scale = np.max(np.abs(dtw))
-            fd = (fp - fm) / (2 * d)
-            errs.append({"param": (f"k{pi}" if pi < 8 else
-                                   ["alpha_x", "beta_x", "eps_x", "alpha_y", "beta_y",
-                                    "eps_y"][pi - 8]),
-                         "adjoint": float(grad[pi]), "fd": fd,
-                         "rel_err": abs(fd - float(grad[pi])) / float(scale)})
-        fd_out[f"h={h:g}"] = errs
+    for replay in (True, False):
+        for h in ((1e-6, 1e-8) if replay else (1e-6,)):
+            rows = []
+            for pi in range(14):
+                kk, tt = list(ks), list(tw)
+                vec, idx = (kk, pi) if pi < 8 else (tt, pi - 8)
+                d = h * abs(vec[idx])
+                vec[idx] += d
+                fp = objective(kk, tt, replay)
+                vec[idx] -= 2 * d
+                fm = objective(kk, tt, replay)
+                fd = (fp - fm) / (2 * d)
+                scale = float(np.max(np.abs(dk if pi < 8 else dtw)))
+                rows.append({"param": names[pi], "adjoint": float(grad[pi]), "fd": fd,
+                             "rel_err": abs(fd - float(grad[pi])) / scale})
+            key = f"{'box_replayed' if replay else 'box_rule_live'}_h={h:g}"
+            errs = [r["rel_err"] for r in rows]
+            fd_out[key] = {"params": rows, "max_rel_err": max(errs),
+                           "params_within_1e-6": int(sum(e <= 1e-6 for e in errs))}
     for t in (trk, g, fdt):
         t.close()
     return {"workload": w.name, "particles": w.n_particles, "grid": w.n_grid, "kicks": w.kicks,
@@ -395,8 +389,9 @@ def grad_bench(dev, checkpoint_interval: int = 20, fd_params=(3, 9)):
                     "recording forward (bx_grad_forward, t_fwd_recording) + reverse pass "
                     "(bx_grad_backward: recompute of every checkpoint segment + adjoint "
                     "kernels + chain rule, t_bwd); ratio_gradient_over_fwd = (t_fwd_recording + "
-                    "t_bwd)/t_fwd; t_fd = 2 x 14 plain forwards; FD with the box sequence "
-                    "replayed"}
+                    "t_bwd)/t_fwd; t_fd = 2 x 14 plain forwards; central differences of all "
+                    "14 parameters, rel_err against the largest |gradient| of the parameter's "
+                    "group (k's or Twiss)"}
 
 
 def _kick_ms(trk, beam, lat, first, nk, **kw):
@@ -612,7 +607,11 @@ def run_ours(args, w):
     # binning as a user would set it: the autotuner times the candidates on the
     # first 64 kicks of this problem (bunch restored, context reset afterwards)
     binning = {"rebin_interval": 16, "bin_edge": 0, "cell_order": 0, "tuned": False}
-    if not args.no_tune:
+    if args.binning:
+        iv, be, co = (int(v) for v in args.binning.split(","))
+        trk.set_binning(iv, be, co)
+        binning = {"rebin_interval": iv, "bin_edge": be, "cell_order": co, "tuned": False}
+    elif not args.no_tune:
         t_tune = time.perf_counter()
         (iv, be, co), _ = trk.autotune_binning(beam, lat, kicks=64)
         binning = {"rebin_interval": iv, "bin_edge": be, "cell_order": co, "tuned": True,

@@ -80,11 +80,10 @@ typedef struct bx_batch bx_batch;
  *                  N = 128), else a power of two in [2, N/2] with at most 16^3
  *                  bins.
  * cell_order     : 0 = re-bin by bin only; 1 = by bin and, within a bin, by
- *                  grid cell (a second counting-sort pass), so that runs of
- *                  consecutive particles share a cell and the CIC deposit adds
- *                  each run's weights once.  None of the three changes any
- *                  result, only the speed (bx_autotune_binning picks them by
- *                  timing).
+ *                  grid cell (a second counting-sort pass), so that consecutive
+ *                  particles share field nodes in the gather's loads.  None of
+ *                  the three changes any result, only the speed
+ *                  (bx_autotune_binning picks them by timing).
  */
 typedef struct {
     int32_t n_grid;
@@ -336,6 +335,19 @@ int32_t bx_twiss_beam(const double twiss[8], const double *const xi[6], int64_t 
  * rule through bx_twiss_beam: du/dbeta = u/(2 beta), dpu/dbeta = -pu/(2 beta),
  * du/deps = u/(2 eps), dpu/deps = pu/(2 eps), dpu/dalpha = -u/beta. */
 int32_t bx_twiss_grad(const double twiss[8], const double S[36], double out[6]);
+
+/* The objectives of the differentiation calls from the 27 moments of
+ * bx_moments (host copy): out = (eps_x, eps_y, sigma_x, sigma_y), eps =
+ * sqrt(<du^2><dpu^2> - <du dpu>^2) (unnormalised rms emittance), sigma =
+ * sqrt(<du^2>).  BX_NONFINITE if one is not a finite number.  Host only. */
+int32_t bx_objectives(const double moments[27], double out[4]);
+
+/* Chain rule for quadrupole strengths shared by several elements: dk_family[f]
+ * = sum of dk_element[e] over the elements e with family[e] = f (host arrays;
+ * family[e] = -1: the element's strength is not a parameter).  BX_BAD_ARG for
+ * a family index outside [-1, nfamilies).  Host only. */
+int32_t bx_family_grad(const double *dk_element, const int32_t *family, int32_t count,
+                       int32_t nfamilies, double *dk_family);
 
 /* Forward pass for differentiation: tracks the beam through the whole
  * lattice (all kicks, from a fresh state: no box, kick counter 0; space

@@ -5,5 +5,6 @@ the C ABI of include/beamtrack.h); `api` is its thin Python binding.
 """
 from .api import (Batch, Beam, Element, Grid, Species, Tracker, lattice_struct,  # noqa: F401
                   twiss_beam, twiss_grad, autotune_batch, distribution_beam, shard_range,
+                  objectives, family_grad,
                   torch_allreduce)
 from .autograd import TrackObjectives, track_objectives  # noqa: F401

@@ -99,6 +99,9 @@ SIGNATURES = {
     "bx_distribution_beam": (c_int32, [c_int32, POINTER(c_double), POINTER(c_void_p), c_void_p,
                                        c_int64, POINTER(c_void_p), c_void_p]),
     "bx_set_shard": (c_int32, [c_void_p, POINTER(bx_shard)]),
+    "bx_objectives": (c_int32, [POINTER(c_double), POINTER(c_double)]),
+    "bx_family_grad": (c_int32, [POINTER(c_double), POINTER(c_int32), c_int32, c_int32,
+                                 POINTER(c_double)]),
     "bx_last_error": (c_char_p, [c_void_p]),
 }
 

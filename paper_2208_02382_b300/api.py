@@ -92,6 +92,28 @@ def twiss_grad(twiss, S) -> list:
     return list(out)
 
 
+def objectives(moments) -> list:
+    """(eps_x, eps_y, sigma_x, sigma_y) from the 27 moments (bx_objectives)."""
+    lib = L.load()
+    m = (ctypes.c_double * 27)(*[float(v) for v in moments])
+    out = (ctypes.c_double * 4)()
+    _check(lib, None, lib.bx_objectives(m, out))
+    return list(out)
+
+
+def family_grad(dk_element, family, nfamilies: int) -> list:
+    """Per-family sums of per-element dL/dk (bx_family_grad)."""
+    lib = L.load()
+    n = len(dk_element)
+    if len(family) != n:
+        raise ValueError("one family index per element")
+    dk = (ctypes.c_double * max(1, n))(*[float(v) for v in dk_element])
+    fam = (ctypes.c_int32 * max(1, n))(*[int(v) for v in family])
+    out = (ctypes.c_double * max(1, int(nfamilies)))()
+    _check(lib, None, lib.bx_family_grad(dk, fam, n, int(nfamilies), out))
+    return [out[i] for i in range(int(nfamilies))]
+
+
 class Beam:
     """A bunch on the device: `coords` is a (6, n) float64 CUDA tensor
     (x, px, y, py, t, pt), `ids` an int64 CUDA tensor of length n."""

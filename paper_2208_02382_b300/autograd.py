@@ -31,11 +31,8 @@ class TrackObjectives(torch.autograd.Function):
         coords = api.twiss_beam(tw, xi)
         beam = api.Beam(coords, species, bunch_charge_C)
         tracker.grad_forward(beam, els, checkpoint_interval, space_charge=space_charge)
-        m = tracker.moments(beam).cpu()
-        cxx, cxp, cpp = float(m[6]), float(m[7]), float(m[12])
-        cyy, cyp, cqq = float(m[17]), float(m[18]), float(m[21])
-        out = torch.tensor([(cxx * cpp - cxp * cxp) ** 0.5, (cyy * cqq - cyp * cyp) ** 0.5,
-                            cxx ** 0.5, cyy ** 0.5], dtype=torch.float64)
+        out = torch.tensor(api.objectives(tracker.moments(beam).cpu().tolist()),
+                           dtype=torch.float64)
         ctx.tracker, ctx.beam, ctx.families, ctx.tw = tracker, beam, list(families), tw
         ctx.nk = ks.numel()
         return out
@@ -44,10 +41,7 @@ class TrackObjectives(torch.autograd.Function):
     def backward(ctx, gout):
         w = [float(v) for v in gout.detach().cpu().tolist()]
         dk_el, S, _ = ctx.tracker.grad_backward(ctx.beam, w, want_zbar0=False)
-        dks = torch.zeros(ctx.nk, dtype=torch.float64)
-        for d, f in zip(dk_el, ctx.families):
-            if f >= 0:
-                dks[f] += d
+        dks = torch.tensor(api.family_grad(dk_el, ctx.families, ctx.nk), dtype=torch.float64)
         dtw = torch.zeros(8, dtype=torch.float64)
         dtw[:6] = torch.tensor(api.twiss_grad(ctx.tw, S), dtype=torch.float64)
         return dks, dtw, None, None, None, None, None, None, None, None

@@ -205,7 +205,7 @@ cudaError_t launch_track_particles(double *const c[6], int64_t n, double betagam
                                    const MapCoef *maps, unsigned long long *acc_hi,
                                    unsigned long long *acc_lo, TrackState *st, int32_t *status,
                                    cudaStream_t s, int part = 3, int shape = 1,
-                                   unsigned long long *cells = nullptr, bool runs = false);
+                                   unsigned long long *cells = nullptr, bool spread = false);
 cudaError_t launch_box_rule_graph(TrackState *st, int nn, long long *log, int64_t cap,
                                   cudaGraphConditionalHandle hg, cudaGraphConditionalHandle hs,
                                   cudaGraphConditionalHandle hd, cudaGraphConditionalHandle hn,
@@ -221,7 +221,7 @@ cudaError_t launch_track_particles_oop(double *const cin[6], double *const cout[
 cudaError_t launch_track_deposit(double *const c[6], int64_t n, double betagamma, const Box *box,
                                  int nn, unsigned long long *acc_hi, unsigned long long *acc_lo,
                                  TrackState *st, int32_t *status, cudaStream_t s, int shape = 1,
-                                 unsigned long long *cells = nullptr, bool runs = false);
+                                 unsigned long long *cells = nullptr, bool spread = false);
 int map_kind(const MapCoef &m);
 // sort.cu
 int sort_brick_edge(int nn, int be_opt);

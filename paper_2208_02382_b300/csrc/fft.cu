@@ -8,8 +8,11 @@
 // k - 2n above (G is even: entry k is G(min(k, 2n-k)); offset +-n carries the
 // true value), so phi is exact on nodes -1..n.
 //
-// Design (the FP64 issue rate bounds every pass on this GPU, so the passes do
-// as few floating-point operations as the transform allows):
+// Design (two kinds of passes: FP64 for the Green's function spectrum and the
+// explicit bx_solve, as few floating-point operations as the transform allows
+// since FP64 issue is scarce on this GPU; block floating point on int64 for
+// the tracking solve, on the integer pipes, where the passes are bound by
+// latency rather than by any pipe):
 //  * real-to-complex along x with two real rows packed into one complex line
 //    (a + i b) and separated afterwards by Hermitian symmetry; only kx = 0..n
 //    is kept from then on;
@@ -22,7 +25,10 @@
 //  * each line transform is a mixed-radix Stockham FFT: a team of T threads
 //    holds the line in registers, applies radix-4/8/16 DFT codelets with
 //    twiddles exp(-+2 pi i j/m) from a shared-memory table (built once with
-//    sincospi), and exchanges values through shared memory between radix steps.
+//    sincospi), and exchanges values through its own shared-memory line buffer
+//    between radix steps; a team of at most 32 threads (lines of up to 256
+//    points) synchronises with a warp barrier only, so the block's lines run
+//    independently.
 #include <algorithm>
 #include <climits>
 
@@ -264,6 +270,16 @@ __device__ __forceinline__ int first_index(int t, int j, int m) {
     return (t + j * T) + m * (M / R);
 }
 
+// Barrier between the exchanges of one line team: a team of at most 32
+// threads lies within one warp and owns its line buffer, so the warp barrier
+// suffices and the block's other lines run on independently; wider teams (512-
+// point lines, two warps) synchronise the block.
+template <int M>
+__device__ __forceinline__ void team_sync() {
+    if constexpr (Shape<M>::T <= 32) __syncwarp();
+    else __syncthreads();
+}
+
 // Full line transform: `v` holds the first step's inputs (first_index order);
 // the result (natural order) is left in the team's shared line `s`.  Every
 // thread of the block calls this (it synchronises the block).  HALF: the
@@ -276,19 +292,19 @@ __device__ __forceinline__ void line_fft(C *v, C *s, int t, const C *tw) {
     constexpr int R0 = SH::R0, R1 = SH::R1, R2 = SH::R2;
     step_regs<M, R0, 1, INV, HALF>(v, t, tw);
     store_step<M, R0, 1>(v, s, t);
-    __syncthreads();
+    team_sync<M>();
     load_step<M, R1>(v, s, t);
-    __syncthreads();
+    team_sync<M>();
     step_regs<M, R1, R0, INV>(v, t, tw);
     store_step<M, R1, R0>(v, s, t);
     if constexpr (SH::S == 3) {
-        __syncthreads();
+        team_sync<M>();
         load_step<M, R2>(v, s, t);
-        __syncthreads();
+        team_sync<M>();
         step_regs<M, R2, R0 * R1, INV>(v, t, tw);
         store_step<M, R2, R0 * R1>(v, s, t);
     }
-    __syncthreads();
+    team_sync<M>();
 }
 
 template <int M, class C>
@@ -430,9 +446,9 @@ __global__ void __launch_bounds__(FFT_TPB) k_fft_lines(const double2 *__restrict
             const double g = live ? gh[((long long)c * P + b) * P + kx] : 0.0;
             s[sp(e)] = make_double2(s[sp(e)].x * g, s[sp(e)].y * g);
         }
-        __syncthreads();
+        team_sync<M>();
         load_step<M, R0>(v, s, t);
-        __syncthreads();
+        team_sync<M>();
         line_fft<M, true>(v, s, t, stw);
     }
     if (!live) return;
@@ -817,9 +833,9 @@ __global__ void __launch_bounds__(FFT_TPB, fixq_blocks<M>()) k_fftq_lines(const 
             s[sp(e)] = make_longlong2(__mul64hi((long long)((unsigned long long)a.x << 2), g),
                                   __mul64hi((long long)((unsigned long long)a.y << 2), g));
         }
-        __syncthreads();
+        team_sync<M>();
         load_step<M, R0>(v, s, t);
-        __syncthreads();
+        team_sync<M>();
         // renormalise the product line (all elements share exponent E)
         const int t1 = normalise_line<M, V>(v, red);
         E = (t1 == INT_MIN || E == FIX_EMPTY) ? FIX_EMPTY : E + t1;

@@ -295,6 +295,34 @@ int32_t bx_twiss_grad(const double twiss[8], const double S[36], double out[6]) 
     return BX_OK;
 }
 
+int32_t bx_objectives(const double moments[27], double out[4]) {
+    if (!moments || !out) return set_noctx_error(BX_BAD_ARG, "NULL argument");
+    // row-major upper triangle after the six means: <xx> = 6, <x px> = 7,
+    // <px px> = 12, <yy> = 17, <y py> = 18, <py py> = 21
+    const double cxx = moments[6], cxp = moments[7], cpp = moments[12];
+    const double cyy = moments[17], cyq = moments[18], cqq = moments[21];
+    out[0] = std::sqrt(cxx * cpp - cxp * cxp);
+    out[1] = std::sqrt(cyy * cqq - cyq * cyq);
+    out[2] = std::sqrt(cxx);
+    out[3] = std::sqrt(cyy);
+    for (int k = 0; k < 4; ++k)
+        if (!std::isfinite(out[k])) return set_noctx_error(BX_NONFINITE, "objective not finite");
+    return BX_OK;
+}
+
+int32_t bx_family_grad(const double *dk_element, const int32_t *family, int32_t count,
+                       int32_t nfamilies, double *dk_family) {
+    if (!dk_element || !family || !dk_family || count < 0 || nfamilies < 0)
+        return set_noctx_error(BX_BAD_ARG, "NULL argument or negative count");
+    for (int32_t f = 0; f < nfamilies; ++f) dk_family[f] = 0.0;
+    for (int32_t e = 0; e < count; ++e) {
+        const int32_t f = family[e];
+        if (f < -1 || f >= nfamilies) return set_noctx_error(BX_BAD_ARG, "family index out of range");
+        if (f >= 0) dk_family[f] += dk_element[e];
+    }
+    return BX_OK;
+}
+
 int32_t bx_grad_forward(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat,
                         int32_t checkpoint_interval, const double *box_replay, void *stream) {
     if (!ctx) return set_noctx_error(BX_BAD_ARG, "NULL context");

@@ -14,10 +14,10 @@
 
 namespace bt {
 
-// The cell-order deposit when the context re-bins by cell (and the particles
-// are re-binned at all); else the particle-order deposit.  Both give bitwise
-// the same charge.
-static bool run_deposit(const bx_ctx *ctx, const KickArgs &k) {
+// The deposit with its atomics spread over the block's particles when the
+// context re-bins by cell (and the particles are re-binned at all).  Both
+// forms give bitwise the same charge.
+static bool spread_deposit(const bx_ctx *ctx, const KickArgs &k) {
     return ctx->cell_order && k.binning && ctx->shape == 1;
 }
 
@@ -43,7 +43,7 @@ cudaError_t kick_deposit(const KickArgs &k, cudaStream_t s) {
     bx_ctx *ctx = k.ctx;
     return launch_track_deposit(k.c, k.n, k.bg, &ctx->st->box, ctx->n, ctx->acc_hi, ctx->acc_lo,
                                 ctx->st, ctx->status, s, ctx->shape, shared_cells(ctx),
-                                run_deposit(ctx, k));
+                                spread_deposit(ctx, k));
 }
 
 cudaError_t kick_solve_field_push(const KickArgs &k, cudaStream_t s) {
@@ -64,7 +64,7 @@ cudaError_t kick_next_deposit(const KickArgs &k, cudaStream_t s) {
     bx_ctx *ctx = k.ctx;
     return launch_track_particles(k.c, k.n, k.bg, &ctx->st->box, ctx->n, ctx->efix, ctx->escale,
                                   ctx->maps, ctx->acc_hi, ctx->acc_lo, ctx->st, ctx->status, s, 2,
-                                  ctx->shape, shared_cells(ctx), run_deposit(ctx, k));
+                                  ctx->shape, shared_cells(ctx), spread_deposit(ctx, k));
 }
 
 // Plain launches of one kick (gated kernels return at once when not needed).

@@ -670,7 +670,7 @@ bool box_needs_exact_u(const Box &b) { return box_far_offset(b); }
 // per SM; the CIC gather that loads the deposit's cells fits 48 and runs 5 (its
 // field loads are latency-bound); TSC instances and the map-plus-deposit
 // prologue keep 3 (they would spill at 64).
-template <int MK, bool GATHER, bool DEP, bool MM, int SH, bool UL = false>
+template <int MK, bool GATHER, bool DEP, bool MM, int SH, bool UL = false, bool SPREAD = false>
 __global__ void __launch_bounds__(TPB, (UL && SH == 1) ? 5 : (SH == 1 && !(DEP && MK != MAP_NONE)) ? 4 : 3)
     k_particles(PartArgs a) {
     if (a.gate && *a.gate == 0) return;
@@ -922,7 +922,12 @@ __global__ void __launch_bounds__(TPB, (UL && SH == 1) ? 5 : (SH == 1 && !(DEP &
         }
 #pragma unroll 1
         for (int it = 0; it < PPT; ++it) {
-            const int slot = it * TPB + threadIdx.x;
+            // SPREAD (particles ordered by cell): consecutive lanes take slots
+            // 37 apart (37 is odd: a permutation of the block's CHUNK slots), so
+            // that a warp's atomics go to the nodes of many cells instead of
+            // colliding on the few cells of 32 consecutive particles
+            const int slot = SPREAD ? ((it * TPB + threadIdx.x) * 37) & (CHUNK - 1)
+                                    : it * TPB + threadIdx.x;
             const int cell = scell[slot];
             if (cell < 0) continue;
             const unsigned long long F0 = sF[slot], F1 = sF[CHUNK + slot], F2 = sF[2 * CHUNK + slot];
@@ -988,243 +993,26 @@ __global__ void __launch_bounds__(TPB, (UL && SH == 1) ? 5 : (SH == 1 && !(DEP &
     }
 }
 
-// ------------------------------------------- deposit of cell-ordered particles
-
-// Sum of a 64-bit value below 2^58 / 32 over the 32 lanes of a warp, with the
-// warp's integer reduction on three 26-bit pieces (each piece sum stays below
-// 2^31).  All 32 lanes must call it.
-__device__ __forceinline__ unsigned long long warp_sum_u58(unsigned long long v) {
-    const unsigned m = (1u << 26) - 1;
-    const unsigned long long p0 = __reduce_add_sync(0xffffffffu, (unsigned)(v & m));
-    const unsigned long long p1 = __reduce_add_sync(0xffffffffu, (unsigned)((v >> 26) & m));
-    const unsigned long long p2 = __reduce_add_sync(0xffffffffu, (unsigned)(v >> 52));
-    return p0 + (p1 << 26) + (p2 << 52);
-}
-
-// Adds the eight node weights of a cell (packed c0 | c1 << 10 | c2 << 20) to
-// the block's tile (low and high 32-bit words, the carry of the low word into
-// the high word) or, when the block's cells do not fit a tile, to the global
-// accumulators.  A tile word pair stays exact: a block adds weights of at most
-// RUN_CHUNK particles below 2^51 to a node.
-struct DepTile {
-    unsigned *lo, *hi;
-    int i0, j0, l0, tx, ty;
-    bool use;
-    unsigned long long *acc_hi, *acc_lo;
-    int nn;
-};
-__device__ __forceinline__ void tile_add_cell(const DepTile &t, int cell,
-                                              const unsigned long long w[8]) {
-    const int c0 = cell & 1023, c1 = (cell >> 10) & 1023, c2 = cell >> 20;
-    const int lb = ((c2 - t.l0) * t.ty + (c1 - t.j0)) * t.tx + (c0 - t.i0);
-#pragma unroll
-    for (int dz = 0; dz < 2; ++dz)
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 2; ++dx) {
-                const unsigned long long v = w[(dz * 2 + dy) * 2 + dx];
-                if (v == 0ull) continue;
-                if (t.use) {
-                    const int li = lb + (dz * t.ty + dy) * t.tx + dx;
-                    const unsigned lo = (unsigned)v;
-                    const unsigned old = atomicAdd(&t.lo[li], lo);
-                    atomicAdd(&t.hi[li], (unsigned)(v >> 32) + (old + lo < old ? 1u : 0u));
-                } else {
-                    const long long node = ((long long)(c2 + dz) * t.nn + (c1 + dy)) * t.nn + (c0 + dx);
-                    atomicAdd(&t.acc_hi[node], v >> DEP_SPLIT);
-                    atomicAdd(&t.acc_lo[node], v & ((1ull << DEP_SPLIT) - 1));
-                }
-            }
-}
-
-// CIC deposit (and, with MM, the min/max keys of the rest-frame positions)
-// for particles ordered by cell within brick (a cell-order re-binning), whose
-// consecutive particles mostly share a cell.  Each thread takes RUN_PPT
-// consecutive particles: their cells, fractions and cell codes, then the sum
-// of the node weights (cic_weights, the same as every other deposit) of each
-// run of equal cells in registers.  The run a thread ends on goes to its warp:
-// when all 32 lanes end on one cell (the dense core of a sorted bunch) the
-// warp's integer reduction sums the eight weights and one lane adds them to
-// the tile; otherwise every lane adds its own run.  Integer sums throughout:
-// the accumulators are bitwise those of the particle-order deposit.
-constexpr int RUN_PPT = 4;
-constexpr int RUN_CHUNK = TPB * RUN_PPT;
-template <bool MM, bool EX>
-__device__ __forceinline__ void deposit_runs_body(const PartArgs &a) {
-    extern __shared__ unsigned long long dsm[];
-    __shared__ int s_bb[6];
-    const int nn = a.nn;
-    const Box &B = *a.box;
-    const double ih0 = B.inv_h[0], ih1 = B.inv_h[1], ih2 = B.inv_h[2];
-    const double o0 = B.off[0], o1 = B.off[1], o2 = B.off[2], tz = B.tz;
-    const double lo0 = B.lo[0], lo1 = B.lo[1], lo2 = B.lo[2];
-    if (threadIdx.x < 6) s_bb[threadIdx.x] = threadIdx.x < 3 ? INT_MAX : INT_MIN;
-    long long klo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, khi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
-    int blo[3] = {INT_MAX, INT_MAX, INT_MAX}, bhi[3] = {INT_MIN, INT_MIN, INT_MIN};
-    int cell[RUN_PPT];
-    unsigned long long F[RUN_PPT][3];
-    bool outside = false;
-    const int64_t base = (int64_t)blockIdx.x * RUN_CHUNK + (int64_t)threadIdx.x * RUN_PPT;
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < RUN_PPT; ++j) {
-        cell[j] = -1;
-        const int64_t p = base + j;
-        if (p >= a.n) continue;
-        const double x = a.x[p], y = a.y[p], t = a.t[p];
-        if constexpr (MM) {
-            const long long k0 = dkey(x), k1 = dkey(y), k2 = dkey(__dmul_rn(a.nbg, t));
-            klo[0] = min(klo[0], k0);
-            khi[0] = max(khi[0], k0);
-            klo[1] = min(klo[1], k1);
-            khi[1] = max(khi[1], k1);
-            klo[2] = min(klo[2], k2);
-            khi[2] = max(khi[2], k2);
-        }
-        const double u0 = EX ? (x - lo0) * ih0 : fma(x, ih0, o0);
-        const double u1 = EX ? (y - lo1) * ih1 : fma(y, ih1, o1);
-        const double u2 = EX ? (__dmul_rn(a.nbg, t) - lo2) * ih2 : fma(t, tz, o2);
-        int c0, c1, c2;
-        bool out1 = false;
-        cell_frac(u0, nn, c0, F[j][0], out1);
-        cell_frac(u1, nn, c1, F[j][1], out1);
-        cell_frac(u2, nn, c2, F[j][2], out1);
-        if (a.cell_out) {
-            a.cell_out[p] = cell_code(c0, F[j][0], out1);
-            a.cell_out[a.n + p] = cell_code(c1, F[j][1], out1);
-            a.cell_out[2 * a.n + p] = cell_code(c2, F[j][2], out1);
-        }
-        if (out1) {  // left out: the box rule then regrids
-            outside |= a.flag_outside != 0;
-            continue;
-        }
-        cell[j] = c0 | (c1 << 10) | (c2 << 20);
-        blo[0] = min(blo[0], c0);
-        bhi[0] = max(bhi[0], c0);
-        blo[1] = min(blo[1], c1);
-        bhi[1] = max(bhi[1], c1);
-        blo[2] = min(blo[2], c2);
-        bhi[2] = max(bhi[2], c2);
-    }
-    if (outside) atomicOr(a.status, ST_OUTSIDE);
-    if constexpr (MM) block_keys_commit(klo, khi, a.st);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        int l = blo[d], h = bhi[d];
-        for (int o = 16; o > 0; o >>= 1) {
-            l = min(l, __shfl_xor_sync(0xffffffffu, l, o));
-            h = max(h, __shfl_xor_sync(0xffffffffu, h, o));
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicMin(&s_bb[d], l);
-            atomicMax(&s_bb[3 + d], h);
-        }
-    }
-    __syncthreads();
-    if (s_bb[0] == INT_MAX) return;  // nothing to deposit in this block
-    DepTile T;
-    T.i0 = s_bb[0];
-    T.j0 = s_bb[1];
-    T.l0 = s_bb[2];
-    T.tx = s_bb[3] - s_bb[0] + 2;
-    T.ty = s_bb[4] - s_bb[1] + 2;
-    const int tzn = s_bb[5] - s_bb[2] + 2;
-    T.use = (long long)T.tx * T.ty * tzn <= TILE_CAP;
-    T.lo = (unsigned *)dsm;
-    T.hi = T.lo + TILE_CAP;
-    T.acc_hi = a.acc_hi;
-    T.acc_lo = a.acc_lo;
-    T.nn = nn;
-    const int ntile = T.tx * T.ty * tzn;
-    if (T.use) {
-        for (int i = threadIdx.x; i < ntile; i += TPB) T.lo[i] = T.hi[i] = 0u;
-        __syncthreads();
-    }
-    // runs of equal cells in registers
-    unsigned long long w[8], acc[8];
-    int cur = -1;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) acc[k] = 0ull;
-#pragma unroll
-    for (int j = 0; j < RUN_PPT; ++j) {
-        if (cell[j] < 0) continue;
-        if (cell[j] != cur) {
-            if (cur >= 0) tile_add_cell(T, cur, acc);
-            cur = cell[j];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) acc[k] = 0ull;
-        }
-        cic_weights(F[j][0], F[j][1], F[j][2], w);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] += w[k];
-    }
-    // the run each lane ends on: one add per warp when all lanes share it
-    const unsigned same = __match_any_sync(0xffffffffu, cur);
-    if (same == 0xffffffffu && cur >= 0) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = warp_sum_u58(acc[k]);
-        if ((threadIdx.x & 31) == 0) tile_add_cell(T, cur, acc);
-    } else if (cur >= 0) {
-        tile_add_cell(T, cur, acc);
-    }
-    if (T.use) {
-        __syncthreads();
-        const int sa = TPB % T.tx, sb = (TPB / T.tx) % T.ty, sc = TPB / (T.tx * T.ty);
-        int ii = threadIdx.x % T.tx, jj = (threadIdx.x / T.tx) % T.ty, ll = threadIdx.x / (T.tx * T.ty);
-        for (int i = threadIdx.x; i < ntile; i += TPB) {
-            const unsigned long long v = ((unsigned long long)T.hi[i] << 32) + T.lo[i];
-            if (v != 0ull) {
-                const long long node = ((long long)(T.l0 + ll) * nn + (T.j0 + jj)) * nn + (T.i0 + ii);
-                atomicAdd(&a.acc_hi[node], v >> DEP_SPLIT);
-                atomicAdd(&a.acc_lo[node], v & ((1ull << DEP_SPLIT) - 1));
-            }
-            ii += sa;
-            int carry = ii >= T.tx;
-            ii -= carry ? T.tx : 0;
-            jj += sb + carry;
-            carry = jj >= T.ty;
-            jj -= carry ? T.ty : 0;
-            ll += sc + carry;
-        }
-    }
-}
-
-// u = (X - lo)/h as one FMA, or (far-offset box, from the device state when
-// tracking) the subtraction first: a uniform branch between two copies.
-template <bool MM>
-__global__ void __launch_bounds__(TPB, 2) k_deposit_runs(PartArgs a) {
-    if (a.gate && *a.gate == 0) return;
-    const bool ex = a.dst ? a.dst->exact_u != 0 : a.exact_u != 0;
-    if (ex) deposit_runs_body<MM, true>(a);
-    else deposit_runs_body<MM, false>(a);
-}
-
-// The cell-order deposit (CIC), with or without the min/max keys.
-static cudaError_t launch_deposit_runs(const PartArgs &a, bool mm, cudaStream_t s, int kid) {
-    const size_t sm = (size_t)TILE_CAP * 2 * sizeof(unsigned);
-    const unsigned blocks = (unsigned)((a.n + RUN_CHUNK - 1) / RUN_CHUNK);
-    if (mm) {
-        BT_LAUNCH(kid, s, k_deposit_runs<true><<<blocks, TPB, sm, s>>>(a));
-    } else {
-        BT_LAUNCH(kid, s, k_deposit_runs<false><<<blocks, TPB, sm, s>>>(a));
-    }
-    return cudaGetLastError();
-}
-
 static size_t particles_smem(bool dep) {
     return dep ? (size_t)(3 * CHUNK + CHUNK / 2 + TILE_CAP) * sizeof(unsigned long long) : 0;
 }
 
-template <int MK, bool G, bool D, bool M, int SH, bool UL = false>
+template <int MK, bool G, bool D, bool M, int SH, bool UL = false, bool SPREAD = false>
 static cudaError_t launch_pk_sh(const PartArgs &a, cudaStream_t s, int kid) {
     const size_t sm = particles_smem(D);
     if (D)
-        cudaFuncSetAttribute(k_particles<MK, G, D, M, SH, UL>,
+        cudaFuncSetAttribute(k_particles<MK, G, D, M, SH, UL, SPREAD>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const unsigned blocks = (unsigned)((a.n + CHUNK - 1) / CHUNK);
-    BT_LAUNCH(kid, s, k_particles<MK, G, D, M, SH, UL><<<blocks, TPB, sm, s>>>(a));
+    BT_LAUNCH(kid, s, k_particles<MK, G, D, M, SH, UL, SPREAD><<<blocks, TPB, sm, s>>>(a));
     return cudaGetLastError();
+}
+
+// The deposit of particles ordered by cell (CIC; with or without the min/max
+// keys): the tile deposit with its atomics spread over the block's particles.
+static cudaError_t launch_deposit_spread(const PartArgs &a, bool mm, cudaStream_t s, int kid) {
+    return mm ? launch_pk_sh<MAP_NONE, false, true, true, 1, false, true>(a, s, kid)
+              : launch_pk_sh<MAP_NONE, false, true, false, 1, false, true>(a, s, kid);
 }
 
 template <int MK, bool G, bool D, bool M, bool UL = false>
@@ -1293,7 +1081,7 @@ cudaError_t launch_track_particles(double *const c[6], int64_t n, double betagam
                                    const MapCoef *maps, unsigned long long *acc_hi,
                                    unsigned long long *acc_lo, TrackState *st, int32_t *status,
                                    cudaStream_t s, int part, int shape, unsigned long long *cells,
-                                   bool runs) {
+                                   bool spread) {
     if (n <= 0) {
         // no particles (a rank of a sharded run): the next kick's accumulators
         // must still start from zero
@@ -1323,7 +1111,7 @@ cudaError_t launch_track_particles(double *const c[6], int64_t n, double betagam
     if (e != cudaSuccess) return e;
     a.gate = &st->next_gate;
     a.cell_out = cells;
-    if (runs && shape == 1) return launch_deposit_runs(a, true, s, K_DEPOSIT);
+    if (spread && shape == 1) return launch_deposit_spread(a, true, s, K_DEPOSIT);
     return launch_pk<MAP_NONE, false, true, true>(a, s, K_DEPOSIT);
 }
 
@@ -1388,7 +1176,7 @@ cudaError_t launch_track_prologue(double *const c[6], int64_t n, double betagamm
 cudaError_t launch_track_deposit(double *const c[6], int64_t n, double betagamma, const Box *box,
                                  int nn, unsigned long long *acc_hi, unsigned long long *acc_lo,
                                  TrackState *st, int32_t *status, cudaStream_t s, int shape,
-                                 unsigned long long *cells, bool runs) {
+                                 unsigned long long *cells, bool spread) {
     cudaError_t e = launch_zero_acc(acc_hi, acc_lo, nn, &st->deposit_gate, s);
     if (e != cudaSuccess || n <= 0) return e;
     PartArgs a = part_args(c, n, betagamma, box, nn, shape);
@@ -1399,7 +1187,7 @@ cudaError_t launch_track_deposit(double *const c[6], int64_t n, double betagamma
     a.dst = st;
     a.flag_outside = 1;
     a.cell_out = cells;
-    if (runs && shape == 1) return launch_deposit_runs(a, false, s, K_REDEPOSIT);
+    if (spread && shape == 1) return launch_deposit_spread(a, false, s, K_REDEPOSIT);
     return launch_pk<MAP_NONE, false, true, false>(a, s, K_REDEPOSIT);
 }
 

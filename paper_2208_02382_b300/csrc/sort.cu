@@ -17,8 +17,9 @@
 // Cell order (bx_set_binning's cell_order): a first pass keyed by the cell's
 // index within its brick writes the scratch arrays, a second (stable) pass
 // keyed by the brick writes the caller's arrays back: particles ordered by
-// brick and within a brick by cell, so runs of particles share a cell and the
-// deposit adds each run's weights once (particles.cu, k_deposit_runs).
+// brick and within a brick by cell: consecutive particles share cells and
+// field nodes, which the gather's loads find in L1 (the deposit then spreads
+// its atomics over the block's particles, particles.cu).
 #include <algorithm>
 
 #include "common.cuh"

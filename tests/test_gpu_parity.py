@@ -377,12 +377,11 @@ def test_graph_and_plain_launch_paths_agree_bitwise(bt):
 @pytest.mark.parametrize("workload,npart,n,nk,be", [("fodo_1e4_32", 9_001, 16, 40, 4),
                                                     ("fodo_1e6_64", 200_003, 64, 12, 8),
                                                     ("chicane_25e6_128", 150_001, 128, 10, 8)])
-def test_cell_order_deposit_is_bitwise_the_bin_order_one(bt, workload, npart, n, nk, be):
-    """Re-binning by cell within bin and the run deposit (consecutive particles
-    of one cell summed in registers, a warp reduction when a warp's lanes end
-    on one cell) against re-binning by bin with the particle-order tile
-    deposit: the same integer charge, so bitwise the same coordinates and
-    regrid log, re-binning every 4 kicks (each sort inside the window)."""
+def test_cell_order_binning_is_bitwise_the_bin_order_one(bt, workload, npart, n, nk, be):
+    """Re-binning by cell within bin (a second counting-sort pass; the tile
+    deposit spreads its atomics over the block's particles) against re-binning
+    by bin: the same integer charge, so bitwise the same coordinates and regrid
+    log, re-binning every 4 kicks (each sort inside the window)."""
     w = bg.workload(workload)
     c = w.particles(npart)
     outs = []

@@ -107,3 +107,28 @@ def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
     with pytest.raises(ImportError):
         L.load(str(tmp_path / "missing.so"))
     importlib.reload(L)
+
+
+def test_objectives_match_the_oracle_definition(lib):
+    """bx_objectives (host): eps = sqrt(<du^2><dpu^2> - <du dpu>^2), sigma =
+    sqrt(<du^2>) from the 27 moments, against the oracle's own moments and
+    emittances of a correlated bunch."""
+    import numpy as np
+
+    import beamgen as bg
+    import paper_2208_02382_b300 as bt
+    from oracle import track as tr
+    c = bg.gaussian6d(5_000, seed=4)
+    c[1] += 0.3 * c[0] / 1e-3 * 1e-4          # x-px correlation
+    m = tr.moments(c)
+    got = bt.objectives(tr.moments_vector(c))
+    want = [m["eps_x"], m["eps_y"], float(m["sigma"][0]), float(m["sigma"][2])]
+    assert np.allclose(got, want, rtol=1e-14, atol=0.0)
+
+
+def test_family_grad_sums_elements_and_rejects_bad_indices(lib):
+    import paper_2208_02382_b300 as bt
+    assert bt.family_grad([1.0, 2.0, 3.0, 4.0, 5.0], [0, -1, 1, 0, 1], 2) == [5.0, 8.0]
+    assert bt.family_grad([], [], 3) == [0.0, 0.0, 0.0]
+    with pytest.raises(L.BeamtrackError):
+        bt.family_grad([1.0], [2], 2)
