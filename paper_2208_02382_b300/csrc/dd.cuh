@@ -140,7 +140,7 @@ __device__ __forceinline__ dd dd_tab(const double *hi, const double *lo, int j) 
 // series through s^11 (next term below 1e-31 relative).  a = 0 gives -Inf,
 // a < 0 or NaN gives NaN, a = +Inf gives +Inf; the table index stays in
 // range for every input.
-__device__ __noinline__ dd dd_log(dd a) {
+static __device__ __noinline__ dd dd_log(dd a) {
     if (!(a.hi > 0.0)) return dd{a.hi == 0.0 ? -INFINITY : NAN, 0.0};
     if (isinf(a.hi)) return dd{INFINITY, 0.0};
     const int e = ilogb(a.hi);
@@ -163,7 +163,7 @@ __device__ __noinline__ dd dd_log(dd a) {
 // atan(n/d) for 0 <= n <= d: c = j/64 nearest to n/d; atan(n/d) = atan c +
 // atan u with u = (n - c d)/(d + c n) (one division), |u| <= 7.9e-3, the atan
 // series through u^15 (next term below 1e-34 relative).
-__device__ __noinline__ dd dd_atan_ratio_unit(dd n, dd d) {
+static __device__ __noinline__ dd dd_atan_ratio_unit(dd n, dd d) {
     const int j = min(max((int)(n.hi / d.hi * 64.0 + 0.5), 0), 64);  // NaN ratio: 0
     const double c = (double)j * (1.0 / 64.0);
     const dd u = dd_div(dd_sub(n, dd_mul_d(d, c)), dd_add(d, dd_mul_d(n, c)));

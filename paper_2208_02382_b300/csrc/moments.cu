@@ -1,167 +1,58 @@
 // Beam statistics (ABLASTR beam statistics; the paper's FODO and IOTA
-// benchmarks check second moments and emittances): means, then centred second
+// benchmarks check second moments and emittances): means and centred second
 // moments.
 //
-// Means: per-block FP64 partial sums over fixed contiguous chunks with a fixed
-// shared-memory tree, then a fixed-order sum of the partials (bitwise
-// reproducible for a given particle order); the same pass takes each
-// coordinate's min and max (order-preserving integer keys).
-// Second moments: the 21 sums of d_a d_b (d = coordinate minus its mean) run on
-// the integer pipes instead of the FP64 pipe (21 FP64 FMAs a particle were the
-// bound): d_c is rounded to an integer at 2^s_c, with s_c chosen from the
-// coordinate's extent about its mean and the particle count so that every sum
-// of products fits a signed 128-bit integer; the 64x64 -> 128-bit products are
-// summed exactly (the sums do not depend on particle order or blocking) and
-// converted to double once.  The rounding of d_c (to nearest, unbiased) is at
-// most 2^-44 of the extent; summed over the bunch these errors stay far below
-// the FP64 sum's own.
+// Pass 1 takes each coordinate's exact extent (min/max of order-preserving
+// integer keys, order-free).  From it, per coordinate, a scale 2^k that brings
+// the half-extent below 2^42 and an origin R 2^-k (the extent's midpoint
+// rounded to a multiple of 2^-k).  Pass 2 rounds every coordinate to the
+// integer q = round(x 2^k) - R (integer operations only: no FP64) and forms
+// the exact sums of q and of the 21 products q_a q_b, the products from 21-bit
+// limbs (q = qh 2^21 + ql: q_a q_b = qh_a qh_b 2^42 + (qh_a ql_b + ql_a qh_b)
+// 2^21 + ql_a ql_b, three 64-bit sums of 32 x 32 -> 64-bit products).  Its
+// blocks stage chunks of 1024 particles in shared memory with asynchronous
+// copies (the next chunk loads while the current one is summed), and each warp
+// sums the pairs of one row group of the 6 x 6 matrix.  The blocks' integer
+// sums are added in 128-bit integers and converted once: mean = (R + sum q/N)
+// 2^-k, centred second moment = (sum q_a q_b/N - (sum q_a/N)(sum q_b/N))
+// 2^-(k_a + k_b).  Every sum is exact, so the result does not depend on particle
+// order or blocking; the only roundings are q's (at most 2^-43 of the extent)
+// and the final conversions.
 #include "common.cuh"
+#include "dd.cuh"
 
 namespace bt {
 
-constexpr int MOM_TPB = 256;
-constexpr int MOM_P1 = 18;   // pass-1 partial per block: 6 sums, 6 min keys, 6 max keys
-constexpr int MOM_P2 = 42;   // pass-2 partial per block: 21 x (hi, lo) of 128-bit sums
+constexpr int MOM_TPB = 256;            // eight warps: two per row group of the 6 x 6 matrix
+constexpr int MOM_CHUNK = 1024;         // particles per staged chunk (48 KB of shared memory)
+constexpr int MOM_REC = 72;             // per-block record: 21 x 3 pair sums, 6 sums of q
+constexpr int MOM_HDR = 32;             // scratch header: keys, origins and scales, flags
 
-// at most MOM_PPT particles per thread (the per-thread integer sums' bound),
-// in whole waves of the second-moment pass (128 registers: two blocks of 256
-// threads per SM), so that no wave runs a few long blocks on an idle GPU
-constexpr int MOM_PPT = 256;
 int moments_blocks(int64_t n) {
-    const int64_t resident = 148 * 2;
-    const int64_t per = (int64_t)MOM_TPB * MOM_PPT;
-    int64_t waves = (n + resident * per - 1) / (resident * per);
-    if (waves < 1) waves = 1;
-    int64_t b = resident * waves;
-    if (b > (n + MOM_TPB - 1) / MOM_TPB) b = (n + MOM_TPB - 1) / MOM_TPB;
+    const int64_t chunks = (n + MOM_CHUNK - 1) / MOM_CHUNK;
+    const int64_t cap = 148 * 2;        // two blocks of 2 x 48 KB per SM
+    int64_t b = chunks < cap ? chunks : cap;
     return (int)(b < 1 ? 1 : b);
 }
 
-// doubles of scratch the moments need for `nblocks` blocks (pass-2 partials,
-// reused by pass 1, plus the per-coordinate scales)
-size_t moments_scratch_doubles(int nblocks) { return (size_t)nblocks * MOM_P2 + 8; }
+size_t moments_scratch_doubles(int nblocks) { return MOM_HDR + (size_t)nblocks * MOM_REC; }
 
-template <int K>
-__device__ void block_tree_sum(double (&v)[K], double *out) {
-    __shared__ double sm[K][MOM_TPB];
-#pragma unroll
-    for (int k = 0; k < K; ++k) sm[k][threadIdx.x] = v[k];
-    __syncthreads();
-    for (int s = MOM_TPB / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-#pragma unroll
-            for (int k = 0; k < K; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int k = 0; k < K; ++k) out[k] = sm[k][0];
+// The pairs of warp w (of a row group): row 0 (which also sums q), row 1, row 2
+// and (5, 5), rows 3 and 4; entry p is pair index mom_k(w, p) in row-major
+// upper-triangle order (-1: none).
+__host__ __device__ constexpr int mom_np(int w) { return w == 0 ? 6 : 5; }
+__host__ __device__ constexpr int mom_k(int w, int p) {
+    constexpr int K[4][6] = {{0, 1, 2, 3, 4, 5}, {6, 7, 8, 9, 10, -1}, {11, 12, 13, 14, 20, -1},
+                             {15, 16, 17, 18, 19, -1}};
+    return K[w][p];
 }
-
-__global__ void k_mom_sum(const double *__restrict__ x, const double *__restrict__ px,
-                          const double *__restrict__ y, const double *__restrict__ py,
-                          const double *__restrict__ t, const double *__restrict__ pt, int64_t n,
-                          double *__restrict__ partial) {
-    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-    const int64_t b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
-    double v[6] = {0, 0, 0, 0, 0, 0};
-    long long lo[6], hi[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        lo[c] = LLONG_MAX;
-        hi[c] = LLONG_MIN;
-    }
-    for (int64_t p = b0 + threadIdx.x; p < b1; p += MOM_TPB) {
-        const double q[6] = {x[p], px[p], y[p], py[p], t[p], pt[p]};
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            v[c] += q[c];
-            const long long k = dkey(q[c]);
-            lo[c] = min(lo[c], k);
-            hi[c] = max(hi[c], k);
-        }
-    }
-    double *out = partial + (size_t)blockIdx.x * MOM_P1;
-    block_tree_sum<6>(v, out);
-    // min/max keys: warp, then block (exact, any order)
-    __shared__ long long sk[12][MOM_TPB / 32];
-#pragma unroll
-    for (int c = 0; c < 6; ++c)
-        for (int o = 16; o > 0; o >>= 1) {
-            lo[c] = min(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
-            hi[c] = max(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
-        }
-    if ((threadIdx.x & 31) == 0)
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            sk[c][threadIdx.x >> 5] = lo[c];
-            sk[6 + c][threadIdx.x >> 5] = hi[c];
-        }
-    __syncthreads();
-    if (threadIdx.x < 12) {
-        long long r = sk[threadIdx.x][0];
-        for (int w = 1; w < MOM_TPB / 32; ++w)
-            r = threadIdx.x < 6 ? min(r, sk[threadIdx.x][w]) : max(r, sk[threadIdx.x][w]);
-        reinterpret_cast<long long *>(out)[6 + threadIdx.x] = r;
-    }
+__host__ __device__ constexpr int mom_a(int k) {
+    constexpr int A[21] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 3, 4, 4, 5};
+    return A[k];
 }
-
-// Means (a fixed-order reduction of the partials) into out[0..5], and the
-// scale exponents s_c into scale[0..5].  One block.
-__global__ void __launch_bounds__(MOM_TPB) k_mom_means(const double *__restrict__ partial,
-                                                     int nblocks, int64_t n,
-                                                     double *__restrict__ out,
-                                                     int *__restrict__ scale) {
-    // each thread folds blocks t, t + 256, ... (in that order), then a fixed
-    // shared-memory tree: the same result for the same partials every time
-    __shared__ double ss[6][MOM_TPB];
-    __shared__ long long slo[6][MOM_TPB], shi[6][MOM_TPB];
-    double v[6] = {0, 0, 0, 0, 0, 0};
-    long long lo[6], hi[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        lo[c] = LLONG_MAX;
-        hi[c] = LLONG_MIN;
-    }
-    for (int b = threadIdx.x; b < nblocks; b += MOM_TPB) {
-        const double *pb = partial + (size_t)b * MOM_P1;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-            v[c] += pb[c];
-            lo[c] = min(lo[c], reinterpret_cast<const long long *>(pb)[6 + c]);
-            hi[c] = max(hi[c], reinterpret_cast<const long long *>(pb)[12 + c]);
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        ss[c][threadIdx.x] = v[c];
-        slo[c][threadIdx.x] = lo[c];
-        shi[c][threadIdx.x] = hi[c];
-    }
-    __syncthreads();
-    for (int st = MOM_TPB / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                ss[c][threadIdx.x] += ss[c][threadIdx.x + st];
-                slo[c][threadIdx.x] = min(slo[c][threadIdx.x], slo[c][threadIdx.x + st]);
-                shi[c][threadIdx.x] = max(shi[c][threadIdx.x], shi[c][threadIdx.x + st]);
-            }
-        __syncthreads();
-    }
-    const int c = threadIdx.x;
-    if (c >= 6) return;
-    // scale exponent s_c: 2^s_c times the extent of coordinate c about its
-    // mean stays below 2^43, so a product is below 2^87, a thread's sum of at
-    // most 256 of them below 2^95 (its high word fits a signed 32-bit
-    // integer), and the sum over up to 2^31 particles below 2^118
-    const double mean = ss[c][0] / (double)n;
-    out[c] = mean;
-    const double ext = fmax(dkey_inv(shi[c][0]) - mean, mean - dkey_inv(slo[c][0]));
-    const int B = 43;
-    int sc = 0;
-    if (ext > 0.0 && isfinite(ext)) sc = B - (ilogb(ext) + 1);  // ext < 2^(ilogb + 1)
-    scale[c] = isfinite(mean) && isfinite(ext) ? sc : INT_MIN;
+__host__ __device__ constexpr int mom_b(int k) {
+    constexpr int B[21] = {0, 1, 2, 3, 4, 5, 1, 2, 3, 4, 5, 2, 3, 4, 5, 3, 4, 5, 4, 5, 5};
+    return B[k];
 }
 
 // round(d * 2^s) for |d * 2^s| < 2^62, by exponent/mantissa arithmetic on the
@@ -178,118 +69,304 @@ __device__ __forceinline__ long long fix_round(double d, int s) {
     return (b >> 63) ? -(long long)v : (long long)v;
 }
 
-__device__ __forceinline__ void add128(long long &hi, unsigned long long &lo, long long phi,
-                                       unsigned long long plo) {
-    const unsigned long long r = lo + plo;
-    hi += phi + (r < lo ? 1 : 0);
-    lo = r;
+// Coordinate k of the six arrays (a uniform select, no indexed local array).
+__device__ __forceinline__ const double *coord6(const double *x, const double *px,
+                                                const double *y, const double *py,
+                                                const double *t, const double *pt, int k) {
+    return k == 0 ? x : k == 1 ? px : k == 2 ? y : k == 3 ? py : k == 4 ? t : pt;
 }
 
-__global__ void __launch_bounds__(MOM_TPB) k_mom_cov(
+// Scratch header (as long long): [0..5] min keys, [6..11] max keys, [12..17]
+// scales k, [18..23] origins R, [24..29] the origin's FP64 value (far origins),
+// [30] flags (1: a coordinate not finite; 2 << c: coordinate c far from its
+// origin relative to its extent, q taken from the FP64 difference).
+__global__ void k_mom_init(long long *hdr) {
+    if (threadIdx.x < 6) {
+        hdr[threadIdx.x] = LLONG_MAX;
+        hdr[6 + threadIdx.x] = LLONG_MIN;
+    }
+}
+
+// Pass 1: exact per-coordinate min/max keys (order-free integer atomics).
+__global__ void __launch_bounds__(256) k_mom_extent(
     const double *__restrict__ x, const double *__restrict__ px, const double *__restrict__ y,
     const double *__restrict__ py, const double *__restrict__ t, const double *__restrict__ pt,
-    int64_t n, const double *__restrict__ mean, const int *__restrict__ scale,
-    unsigned long long *__restrict__ partial) {
-    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
-    const int64_t b0 = blockIdx.x * chunk, b1 = min(n, b0 + chunk);
-    double m[6];
-    int sc[6];
+    int64_t n, long long *hdr) {
+    long long lo[6], hi[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        m[k] = mean[k];
-        sc[k] = scale[k] == INT_MIN ? 0 : scale[k];
+        lo[k] = LLONG_MAX;
+        hi[k] = LLONG_MIN;
     }
-    // per-thread sums: (high 32-bit word, low 64-bit word), at most 256 terms
-    int hi32[21];
-    unsigned long long alo[21];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; p + 3 * stride < n; p += 4 * stride) {   // four particles' loads in flight
 #pragma unroll
-    for (int k = 0; k < 21; ++k) {
-        hi32[k] = 0;
-        alo[k] = 0;
+        for (int k = 0; k < 6; ++k) {
+            const double *c = coord6(x, px, y, py, t, pt, k);
+            const long long k0 = dkey(c[p]), k1 = dkey(c[p + stride]), k2 = dkey(c[p + 2 * stride]),
+                            k3 = dkey(c[p + 3 * stride]);
+            lo[k] = min(lo[k], min(min(k0, k1), min(k2, k3)));
+            hi[k] = max(hi[k], max(max(k0, k1), max(k2, k3)));
+        }
     }
-    for (int64_t p = b0 + threadIdx.x; p < b1; p += MOM_TPB) {
-        const long long f[6] = {fix_round(x[p] - m[0], sc[0]), fix_round(px[p] - m[1], sc[1]),
-                                fix_round(y[p] - m[2], sc[2]), fix_round(py[p] - m[3], sc[3]),
-                                fix_round(t[p] - m[4], sc[4]), fix_round(pt[p] - m[5], sc[5])};
-        int k = 0;
+    for (; p < n; p += stride)
 #pragma unroll
-        for (int a = 0; a < 6; ++a)
+        for (int k = 0; k < 6; ++k) {
+            const long long kk = dkey(coord6(x, px, y, py, t, pt, k)[p]);
+            lo[k] = min(lo[k], kk);
+            hi[k] = max(hi[k], kk);
+        }
+    __shared__ long long s_lo[6][8], s_hi[6][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-            for (int b = a; b < 6; ++b, ++k) {
-                const unsigned long long plo = (unsigned long long)f[a] * (unsigned long long)f[b];
-                const unsigned long long r = alo[k] + plo;
-                hi32[k] += (int)__mul64hi(f[a], f[b]) + (r < alo[k] ? 1 : 0);
-                alo[k] = r;
-            }
-    }
-    long long ahi[21];
-#pragma unroll
-    for (int k = 0; k < 21; ++k) ahi[k] = hi32[k];
-    // exact block sum: warp shuffles, then the warps in order
-#pragma unroll
-    for (int k = 0; k < 21; ++k)
+    for (int k = 0; k < 6; ++k) {
         for (int o = 16; o > 0; o >>= 1) {
-            const long long h = __shfl_xor_sync(0xffffffffu, ahi[k], o);
-            const unsigned long long l = __shfl_xor_sync(0xffffffffu, alo[k], o);
-            add128(ahi[k], alo[k], h, l);
+            lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
         }
-    __shared__ long long sh[21][MOM_TPB / 32];
-    __shared__ unsigned long long sl[21][MOM_TPB / 32];
-    if ((threadIdx.x & 31) == 0)
-#pragma unroll
-        for (int k = 0; k < 21; ++k) {
-            sh[k][threadIdx.x >> 5] = ahi[k];
-            sl[k][threadIdx.x >> 5] = alo[k];
+        if (lane == 0) {
+            s_lo[k][warp] = lo[k];
+            s_hi[k][warp] = hi[k];
         }
+    }
     __syncthreads();
-    if (threadIdx.x < 21) {
-        long long h = 0;
-        unsigned long long l = 0;
-        for (int w = 0; w < MOM_TPB / 32; ++w) add128(h, l, sh[threadIdx.x][w], sl[threadIdx.x][w]);
-        partial[(size_t)blockIdx.x * MOM_P2 + 2 * threadIdx.x] = (unsigned long long)h;
-        partial[(size_t)blockIdx.x * MOM_P2 + 2 * threadIdx.x + 1] = l;
+    if (threadIdx.x < 6) {
+        long long a = s_lo[threadIdx.x][0], b = s_hi[threadIdx.x][0];
+        for (int w = 1; w < 8; ++w) {
+            a = min(a, s_lo[threadIdx.x][w]);
+            b = max(b, s_hi[threadIdx.x][w]);
+        }
+        atomicMin(&hdr[threadIdx.x], a);
+        atomicMax(&hdr[6 + threadIdx.x], b);
     }
 }
 
-// out[6 + k] = (sum over blocks of the 128-bit partial k) 2^-(s_a + s_b) / n,
-// one warp per k (exact integer sums: any order).
-__global__ void k_mom_cov_final(const unsigned long long *__restrict__ partial, int nblocks,
-                                int64_t n, const int *__restrict__ scale,
-                                double *__restrict__ out) {
-    const int k = blockIdx.x, lane = threadIdx.x;
-    long long h = 0;
-    unsigned long long l = 0;
-    for (int q = lane; q < nblocks; q += 32)
-        add128(h, l, (long long)partial[(size_t)q * MOM_P2 + 2 * k], partial[(size_t)q * MOM_P2 + 2 * k + 1]);
-    for (int o = 16; o > 0; o >>= 1) {
-        const long long hh = __shfl_xor_sync(0xffffffffu, h, o);
-        const unsigned long long ll = __shfl_xor_sync(0xffffffffu, l, o);
-        add128(h, l, hh, ll);
+// Scales and origins from the extents (one thread per coordinate).
+__global__ void k_mom_prep(long long *hdr) {
+    const int c = threadIdx.x;
+    if (c == 0) hdr[30] = 0;
+    __syncwarp();
+    if (c >= 6) return;
+    const double mn = dkey_inv(hdr[c]), mx = dkey_inv(hdr[6 + c]);
+    const double mid = __dmul_rn(0.5, __dadd_rn(mn, mx));
+    const double half = fmax(__dsub_rn(mx, mid), __dsub_rn(mid, mn));
+    int sc = 0;
+    long long flag = 0, R = 0;
+    if (!(isfinite(mid) && isfinite(half))) {
+        flag = 1;
+    } else {
+        if (half > 0.0) sc = 42 - (ilogb(half) + 1);   // half 2^sc < 2^42
+        if (mid != 0.0 && ilogb(mid) + sc >= 60) flag = 2ll << c;   // far origin: FP64 difference
+        else R = fix_round(mid, sc);
     }
-    if (lane != 0) return;
-    int a = 0, r = k;
-    while (r >= 6 - a) {
-        r -= 6 - a;
-        ++a;
+    hdr[12 + c] = sc;
+    hdr[18 + c] = R;
+    hdr[24 + c] = __double_as_longlong(mid);
+    if (flag) atomicOr(reinterpret_cast<unsigned long long *>(&hdr[30]), (unsigned long long)flag);
+}
+
+__device__ __forceinline__ void cp_async8(double *dst, const double *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Pass 2.  The block's j-th chunk (chunk blockIdx.x + j gridDim.x) goes to
+// buffer j & 1; the six coordinate rows of 1024 doubles are copied
+// asynchronously (the next chunk's copies run while this one is summed),
+// converted in place to q, then summed.
+__global__ void __launch_bounds__(MOM_TPB, 2) k_mom_sums(
+    const double *__restrict__ x, const double *__restrict__ px, const double *__restrict__ y,
+    const double *__restrict__ py, const double *__restrict__ t, const double *__restrict__ pt,
+    int64_t n, const long long *__restrict__ hdr, long long *__restrict__ rec) {
+    extern __shared__ double sbuf[];                 // [2][6][MOM_CHUNK]
+    __shared__ int s_sc[6];
+    __shared__ long long s_R[6];
+    __shared__ double s_mid[6];
+    __shared__ long long s_flag;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, grp = warp & 3, half = warp >> 2;
+    if (tid < 6) {
+        s_sc[tid] = (int)hdr[12 + tid];
+        s_R[tid] = hdr[18 + tid];
+        s_mid[tid] = __longlong_as_double(hdr[24 + tid]);
     }
-    const int b = a + r;
-    if (scale[a] == INT_MIN || scale[b] == INT_MIN) {
-        out[6 + k] = NAN;
-        return;
+    if (tid == 0) s_flag = hdr[30];
+    const int64_t nchunks = (n + MOM_CHUNK - 1) / MOM_CHUNK;
+    auto issue = [&](int64_t ch, int j) {
+        if (ch < nchunks) {
+            const int64_t b0 = ch * MOM_CHUNK;
+            const int cnt = (int)min((int64_t)MOM_CHUNK, n - b0);
+            double *buf = sbuf + (size_t)(j & 1) * 6 * MOM_CHUNK;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const double *src = coord6(x, px, y, py, t, pt, k) + b0;
+                for (int i = tid; i < cnt; i += MOM_TPB) cp_async8(buf + k * MOM_CHUNK + i, src + i);
+            }
+        }
+        cp_async_commit();
+    };
+    // per-lane exact sums over all of the block's chunks (a lane sums at most
+    // 2^11 products below 2^43 per chunk share: far from 2^63)
+    constexpr int NPMAX = 6;
+    long long hh[NPMAX], mid[NPMAX], ll[NPMAX], sq[6];
+#pragma unroll
+    for (int p = 0; p < NPMAX; ++p) hh[p] = mid[p] = ll[p] = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sq[k] = 0;
+    issue(blockIdx.x, 0);
+    __syncthreads();
+    const long long flag = s_flag;
+    int j = 0;
+    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x, ++j) {
+        issue(ch + gridDim.x, j + 1);          // the next chunk, into the other buffer
+        cp_async_wait<1>();                     // this chunk's copies are done
+        __syncthreads();
+        const int64_t b0 = ch * MOM_CHUNK;
+        const int cnt = (int)min((int64_t)MOM_CHUNK, n - b0);
+        double *buf = sbuf + (size_t)(j & 1) * 6 * MOM_CHUNK;
+        long long *q = reinterpret_cast<long long *>(buf);
+        // coordinates to integers, in place
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int sc = s_sc[k];
+            const bool far = (flag >> (k + 1)) & 1;
+            const long long R = s_R[k];
+            const double m = s_mid[k];
+            for (int i = tid; i < cnt; i += MOM_TPB) {
+                const double v = buf[k * MOM_CHUNK + i];
+                q[k * MOM_CHUNK + i] = far ? fix_round(v - m, sc) : fix_round(v, sc) - R;
+            }
+        }
+        __syncthreads();
+        // warp (grp, half): the pairs of row group grp over half the chunk
+        const int i0 = half * (MOM_CHUNK / 2), i1 = min(cnt, i0 + MOM_CHUNK / 2);
+        for (int i = i0 + lane; i < i1; i += 32) {
+            int qh[6], ql[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const long long v = q[k * MOM_CHUNK + i];
+                qh[k] = (int)(v >> 21);
+                ql[k] = (int)(v & 0x1FFFFF);
+                if (grp == 0) sq[k] += v;
+            }
+            switch (grp) {
+#define MOM_ROWS(W)                                                              \
+    case W:                                                                      \
+        _Pragma("unroll") for (int p = 0; p < mom_np(W); ++p) {                  \
+            const int a = mom_a(mom_k(W, p)), b = mom_b(mom_k(W, p));            \
+            hh[p] += (long long)qh[a] * qh[b];                                   \
+            mid[p] += (long long)qh[a] * ql[b] + (long long)ql[a] * qh[b];       \
+            ll[p] += (long long)ql[a] * ql[b];                                   \
+        }                                                                        \
+        break;
+                MOM_ROWS(0)
+                MOM_ROWS(1)
+                MOM_ROWS(2)
+                MOM_ROWS(3)
+#undef MOM_ROWS
+            }
+        }
+        __syncthreads();                        // the buffer is free for the chunk after next
     }
-    const double v = (double)h * 18446744073709551616.0 + (double)l;
-    out[6 + k] = ldexp(v, -(scale[a] + scale[b])) / (double)n;
+    cp_async_wait<0>();
+    // warp sums (each below 2^62), then the two warps of a row group add theirs
+    __shared__ long long s_rec[2][MOM_REC];
+#pragma unroll
+    for (int p = 0; p < NPMAX; ++p)
+        for (int o = 16; o > 0; o >>= 1) {
+            hh[p] += __shfl_xor_sync(0xffffffffu, hh[p], o);
+            mid[p] += __shfl_xor_sync(0xffffffffu, mid[p], o);
+            ll[p] += __shfl_xor_sync(0xffffffffu, ll[p], o);
+        }
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        for (int o = 16; o > 0; o >>= 1) sq[k] += __shfl_xor_sync(0xffffffffu, sq[k], o);
+    if (lane == 0) {
+        for (int p = 0; p < mom_np(grp); ++p) {
+            const int kk = grp == 0 ? mom_k(0, p) : grp == 1 ? mom_k(1, p) : grp == 2 ? mom_k(2, p) : mom_k(3, p);
+            s_rec[half][3 * kk] = hh[p];
+            s_rec[half][3 * kk + 1] = mid[p];
+            s_rec[half][3 * kk + 2] = ll[p];
+        }
+        if (grp == 0)
+            for (int k = 0; k < 6; ++k) s_rec[half][63 + k] = sq[k];
+    }
+    __syncthreads();
+    if (tid < 69) rec[(size_t)blockIdx.x * MOM_REC + tid] = s_rec[0][tid] + s_rec[1][tid];
+}
+
+// 128-bit integer to double-double.
+__device__ __forceinline__ dd i128_to_dd(__int128 v) {
+    const double hi = (double)v;
+    const double lo = (double)(v - (__int128)hi);
+    return fast_two_sum(hi, lo);
+}
+
+// The blocks' records added in 128-bit integers (exact), then the 27 moments
+// (one warp; lane j < 27 takes output j).
+__global__ void k_mom_final(const long long *__restrict__ hdr, const long long *__restrict__ rec,
+                            int nblocks, int64_t n, double *__restrict__ out) {
+    const int lane = threadIdx.x;
+    __shared__ double s_m[6][2];
+    __int128 a = 0, b = 0, c = 0;               // sum q (lanes < 6) or HH, MID, LL
+    if (lane < 27)
+        for (int blk = 0; blk < nblocks; ++blk) {
+            const long long *r = rec + (size_t)blk * MOM_REC;
+            if (lane < 6) {
+                a += r[63 + lane];
+            } else {
+                const int k = lane - 6;
+                a += r[3 * k];
+                b += r[3 * k + 1];
+                c += r[3 * k + 2];
+            }
+        }
+    const bool bad = (hdr[30] & 1) != 0;
+    const double N = (double)n;
+    if (lane < 6) {
+        const dd mq = dd_div_d(i128_to_dd(a), N);            // mean of q
+        s_m[lane][0] = mq.hi;
+        s_m[lane][1] = mq.lo;
+    }
+    __syncwarp();
+    if (lane < 6) {
+        const int sc = (int)hdr[12 + lane];
+        const bool far = (hdr[30] >> (lane + 1)) & 1;
+        const dd mq{s_m[lane][0], s_m[lane][1]};
+        // origin: R 2^-k, or the FP64 midpoint for a far origin
+        const dd org = far ? dd_make(__longlong_as_double(hdr[24 + lane]))
+                           : dd_scale(i128_to_dd((__int128)hdr[18 + lane]), ldexp(1.0, -sc));
+        out[lane] = bad ? NAN : dd_add(org, dd_scale(mq, ldexp(1.0, -sc))).hi;
+    } else if (lane < 27) {
+        const int k = lane - 6, ia = mom_a(k), ib = mom_b(k);
+        const int sa = (int)hdr[12 + ia], sb = (int)hdr[12 + ib];
+        // sum q_a q_b = HH 2^42 + MID 2^21 + LL
+        const dd S = dd_add(dd_scale(i128_to_dd(a), 0x1p42),
+                            dd_add(dd_scale(i128_to_dd(b), 0x1p21), i128_to_dd(c)));
+        const dd ma{s_m[ia][0], s_m[ia][1]}, mb{s_m[ib][0], s_m[ib][1]};
+        const dd v = dd_sub(dd_div_d(S, N), dd_mul(ma, mb));
+        out[lane] = bad ? NAN : ldexp(v.hi, -(sa + sb));
+    }
 }
 
 cudaError_t launch_moments(double *const c[6], int64_t n, double *partials, int nblocks,
                            double *out, cudaStream_t s) {
-    int *scale = reinterpret_cast<int *>(partials + (size_t)nblocks * MOM_P2);
-    BT_LAUNCH(K_MOMENTS, s, k_mom_sum<<<nblocks, MOM_TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5], n, partials));
-    BT_LAUNCH(K_MOMENTS, s, k_mom_means<<<1, MOM_TPB, 0, s>>>(partials, nblocks, n, out, scale));
-    BT_LAUNCH(K_MOMENTS, s, k_mom_cov<<<nblocks, MOM_TPB, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5], n, out, scale,
-                                                                    reinterpret_cast<unsigned long long *>(partials)));
-    BT_LAUNCH(K_MOMENTS, s, k_mom_cov_final<<<21, 32, 0, s>>>(reinterpret_cast<const unsigned long long *>(partials),
-                                                              nblocks, n, scale, out));
+    long long *hdr = reinterpret_cast<long long *>(partials);
+    long long *rec = hdr + MOM_HDR;
+    const size_t sm = (size_t)2 * 6 * MOM_CHUNK * sizeof(double);
+    cudaFuncSetAttribute(k_mom_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int eb = (int)((n + 255) / 256);
+    if (eb > 148 * 8) eb = 148 * 8;
+    if (eb < 1) eb = 1;
+    BT_LAUNCH(K_MOMENTS, s, k_mom_init<<<1, 32, 0, s>>>(hdr));
+    BT_LAUNCH(K_MOMENTS, s, k_mom_extent<<<eb, 256, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5], n, hdr));
+    BT_LAUNCH(K_MOMENTS, s, k_mom_prep<<<1, 32, 0, s>>>(hdr));
+    BT_LAUNCH(K_MOMENTS, s, k_mom_sums<<<nblocks, MOM_TPB, sm, s>>>(c[0], c[1], c[2], c[3], c[4],
+                                                                     c[5], n, hdr, rec));
+    BT_LAUNCH(K_MOMENTS, s, k_mom_final<<<1, 32, 0, s>>>(hdr, rec, nblocks, n, out));
     return cudaGetLastError();
 }
 

@@ -396,3 +396,17 @@ def test_cell_order_binning_is_bitwise_the_bin_order_one(bt, workload, npart, n,
     assert outs[0][1] == outs[1][1]
     otr = tr.Tracker(oracle_ref(w.species), w.bunch_charge_C, n)
     assert coord_rel_err(outs[1][0], otr.track(c, w.lattice, 0, nk)) <= REL_TOL
+
+
+def test_track_medium_workload_long_run_subsample(bt):
+    """fodo_1e6_64's bunch shape (80% Gaussian, 20% uniform-ellipsoid halo), 1 GeV
+    protons, 10 nC, 64^3 grid: a 20 000-particle subsample through the first
+    200 of its 1000 kicks from a fresh state (the box rule regrids on about half
+    of them), against the oracle: identical regrid logs and coordinates to 1e-11
+    after the growth of any rounding difference over 200 space-charge kicks."""
+    w = bg.workload("fodo_1e6_64")
+    c = w.particles(20_000)
+    got, want, trk, otr = _track_both(bt, c, w.species, w.bunch_charge_C, w.lattice, w.n_grid,
+                                      nk=200)
+    assert trk.regrid_log() == otr.regrid_log and len(otr.regrid_log) > 50
+    assert coord_rel_err(got, want) <= REL_TOL
