@@ -31,6 +31,20 @@ __device__ __forceinline__ bool nonfinite_bits(double v) {
            0x7FF0000000000000ull;
 }
 
+// Products of 32-bit operands as 64-bit values, each one wide multiply (the
+// compiler otherwise widens a signed-by-unsigned product of limbs to a full
+// 64 x 64-bit multiply).
+__device__ __forceinline__ long long mul_wide_s(int a, int b) {
+    long long d;
+    asm("mul.wide.s32 %0, %1, %2;" : "=l"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long mul_wide_u(unsigned a, unsigned b) {
+    unsigned long long d;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(d) : "r"(a), "r"(b));
+    return d;
+}
+
 // A 52-bit fraction split into two 26-bit limbs, so that products run on
 // 32x32->64-bit multiplies: F = hi * 2^26 + lo.
 struct Frac {
@@ -44,8 +58,8 @@ __device__ __forceinline__ Frac split26(unsigned long long F) {
 // products (the dropped low product and the truncated middle term leave an
 // error below 2 units of 2^-52).
 __device__ __forceinline__ unsigned long long mulshr52(Frac a, Frac b) {
-    const unsigned long long hh = (unsigned long long)a.hi * b.hi;
-    const unsigned long long mid = (unsigned long long)a.hi * b.lo + (unsigned long long)a.lo * b.hi;
+    const unsigned long long hh = mul_wide_u(a.hi, b.hi);
+    const unsigned long long mid = mul_wide_u(a.hi, b.lo) + mul_wide_u(a.lo, b.hi);
     return hh + (mid >> 26);
 }
 
@@ -57,8 +71,8 @@ __device__ __forceinline__ long long lerp52(long long a, long long b, Frac F) {
     const long long d = b - a;
     const int dh = (int)(d >> 26);
     const unsigned dl = (unsigned)(d & 0x3FFFFFFll);
-    const long long hh = (long long)dh * (long long)F.hi;
-    const long long mid = (long long)dh * (long long)F.lo + (long long)((unsigned long long)dl * F.hi);
+    const long long hh = mul_wide_s(dh, (int)F.hi);
+    const long long mid = mul_wide_s(dh, (int)F.lo) + (long long)mul_wide_u(dl, F.hi);
     return a + hh + (mid >> 26);
 }
 

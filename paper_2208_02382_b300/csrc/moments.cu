@@ -166,6 +166,19 @@ __global__ void k_mom_prep(long long *hdr) {
     if (flag) atomicOr(reinterpret_cast<unsigned long long *>(&hdr[30]), (unsigned long long)flag);
 }
 
+// acc + a b for 32-bit a, b and a 64-bit accumulator: one wide multiply-add
+// (signed, and unsigned for the low limbs).
+__device__ __forceinline__ long long mad_wide_s(int a, int b, long long acc) {
+    long long d;
+    asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(acc));
+    return d;
+}
+__device__ __forceinline__ long long mad_wide_u(unsigned a, unsigned b, long long acc) {
+    long long d;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(acc));
+    return d;
+}
+
 __device__ __forceinline__ void cp_async8(double *dst, const double *src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
@@ -257,9 +270,9 @@ __global__ void __launch_bounds__(MOM_TPB, 2) k_mom_sums(
     case W:                                                                      \
         _Pragma("unroll") for (int p = 0; p < mom_np(W); ++p) {                  \
             const int a = mom_a(mom_k(W, p)), b = mom_b(mom_k(W, p));            \
-            hh[p] += (long long)qh[a] * qh[b];                                   \
-            mid[p] += (long long)qh[a] * ql[b] + (long long)ql[a] * qh[b];       \
-            ll[p] += (long long)ql[a] * ql[b];                                   \
+            hh[p] = mad_wide_s(qh[a], qh[b], hh[p]);                             \
+            mid[p] = mad_wide_s(ql[a], qh[b], mad_wide_s(qh[a], ql[b], mid[p])); \
+            ll[p] = mad_wide_u((unsigned)ql[a], (unsigned)ql[b], ll[p]);         \
         }                                                                        \
         break;
                 MOM_ROWS(0)

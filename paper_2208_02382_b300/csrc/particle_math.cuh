@@ -125,7 +125,8 @@ __device__ __forceinline__ void box_u(const Box &b, double nbg, double x, double
     u2 = EX ? (__dmul_rn(nbg, t) - b.lo[2]) * b.inv_h[2] : fma(t, b.tz, b.off[2]);
 }
 
-// floor(a b / 2^51) for a, b <= 2^51, exact (full 64 x 64 -> 128-bit product).
+// floor(a b / 2^51) for a, b <= 2^51, exact (full 64 x 64 -> 128-bit product;
+// measured faster here than the same floor from 26-bit limb products).
 __device__ __forceinline__ unsigned long long mulfloor51(unsigned long long a, unsigned long long b) {
     return (__umul64hi(a, b) << 13) | ((a * b) >> 51);
 }

@@ -645,8 +645,8 @@ __device__ __forceinline__ void tsc_weights(unsigned long long G, Frac w[3]) {
 __device__ __forceinline__ long long mulfrac52(long long e, Frac W) {
     const int eh = (int)(e >> 26);
     const unsigned el = (unsigned)(e & 0x3FFFFFFll);
-    const long long hh = (long long)eh * (long long)W.hi;
-    const long long mid = (long long)eh * (long long)W.lo + (long long)((unsigned long long)el * W.hi);
+    const long long hh = mul_wide_s(eh, (int)W.hi);
+    const long long mid = mul_wide_s(eh, (int)W.lo) + (long long)mul_wide_u(el, W.hi);
     return hh + (mid >> 26);
 }
 
