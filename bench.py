@@ -712,10 +712,20 @@ def run_ours(args, w):
                               if n2 else None,
                               "issue_active_frac": (n2["issue_active_pct"] / 100.0)
                               if n2 and "issue_active_pct" in n2 else None}
-        ne = ncu_entry(dname)
         algo_note = {"gather_kick_push": "96 B/particle: six FP64 coordinates read and written",
                      "deposit": "28 B/particle: X, Y, t re-read and a 4-byte cell key"}
+        ne = ncu_entry(dname)
+        # the FP64 pipe beside HBM for the particle kernels: FP64 thread
+        # instructions per particle (ncu) against 2 per SM per clock
+        fp64 = None
+        if ne and ne.get("fp64_inst_per_unit") and dname in DESIGN_BYTES:
+            g = ne["fp64_inst_per_unit"] * npart / avg_s / 1e9
+            pk = FP64_PEAK_TFLOPS / 2 * 1e3      # G thread instructions/s
+            fp64 = {"inst_per_particle": ne["fp64_inst_per_unit"], "achieved_ginst_s": g,
+                    "peak_ginst_s": pk, "frac": g / pk,
+                    "peak_source": "unit counts and clock: 2 DFMA/SM/clk x 148 SMs x 2.032 GHz"}
         roof = {"kernel": dname, "bound": bound, "achieved": achieved, "peak": peak,
+                "fp64_pipe": fp64,
                 "unit": unit, "frac": achieved / peak, "peak_source": peak_src,
                 "algorithmic_bytes": algo_note.get(dname),
                 "design_bytes_per_unit": DESIGN_BYTES.get(dname),
