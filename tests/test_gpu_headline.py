@@ -4,9 +4,10 @@ cells of aspect ~1:1000; 1 nC; quadrupoles then four sector bends) on its full
 128^3 grid (256^3 doubled), against the FP64 oracle.
 
 * Particle subsamples tracked from a fresh state: from the lattice start (the
-  first box and Green's function build included) and across the
-  quadrupole -> sector-bend boundary (merged maps with dispersion and
-  path-length terms), with re-binning inside the window.  Coordinates to
+  first box and Green's function build included), across the
+  quadrupole -> sector-bend and sector-bend -> drift boundaries (merged maps
+  with dispersion and path-length terms) and through the end of the lattice,
+  with re-binning inside the window.  Coordinates to
   1e-11 relative, identical regrid logs.
 * The Green's function table at N = 128 for the cell sizes of this workload's
   boxes against the float128 oracle, every one of the 129^3 entries.
@@ -57,6 +58,8 @@ def by_id(beam):
 @pytest.mark.parametrize("npart,first,nk,rebin", [
     (300_001, 0, 8, 16),     # lattice start: first box, Green's function at 128^3
     (200_003, 97, 6, 4),     # kicks 97..102: Q2 -> B1 boundary at kick 100
+    (150_001, 145, 10, 4),   # kicks 145..154: end of B1, into the drift after it
+    (100_003, 490, 10, 4),   # the last ten kicks: the final half map ends the lattice
 ])
 def test_chicane_128_subsample_tracking_matches_oracle(bt, npart, first, nk, rebin):
     c = W.particles(npart)
