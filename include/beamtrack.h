@@ -247,10 +247,12 @@ int32_t bx_gather_kick(bx_ctx *ctx, bx_beam *beam, const bx_grid *grid, double d
 /* Beam statistics (ABLASTR beam statistics; FODO/IOTA benchmarks check second
  * moments): out_device[0..5] = means, out_device[6..26] = the 21 centred
  * second moments in row-major upper-triangle order (00,01,..,05,11,..,55).
- * One pass over the particles: per chunk of 1024 particles exact integer sums
- * of deviations from the chunk's midpoint rounded at 2^-43 of the chunk's
- * extent, combined in double-double in a fixed order (bitwise reproducible for
- * a given particle order).  All 27 are NaN when a coordinate is not finite. */
+ * Two passes over the particles: each coordinate's exact extent, then exact
+ * integer sums of the coordinates rounded at 2^-43 of that extent (relative to
+ * its rounded midpoint) and of their 21 pairwise products, added in 128-bit
+ * integers and converted once.  Every sum is exact, so the result does not
+ * depend on particle order (bitwise reproducible for a given set of
+ * particles).  All 27 are NaN when a coordinate is not finite. */
 int32_t bx_moments(bx_ctx *ctx, const bx_beam *beam, double *out_device, void *stream);
 
 /* Integrated Green's function table used by bx_solve: out_device receives
