@@ -45,9 +45,9 @@ extern "C" {
 #define BX_BAD_ARG 1        /* null pointer, size out of range, bad element */
 #define BX_NONFINITE 2      /* NaN or Inf found in particle coordinates     */
 #define BX_OUT_OF_MEMORY 3  /* a device allocation of the context failed    */
-#define BX_DEVICE_TIMEOUT 4 /* reserved: no call of this version waits on the
-                             device (batches loop in graph WHILE nodes), so
-                             none returns it                                */
+#define BX_DEVICE_TIMEOUT 4 /* a device-side wait ran past its time limit: the
+                             moments' staged copies (2 s per wait), reported
+                             by bx_sync; bx_selftest_wait_timeout makes one */
 #define BX_CUDA 5           /* a CUDA runtime call failed                   */
 #define BX_COLLECTIVE 6     /* a sharded run's allreduce callback failed    */
 
@@ -252,8 +252,19 @@ int32_t bx_gather_kick(bx_ctx *ctx, bx_beam *beam, const bx_grid *grid, double d
  * its rounded midpoint) and of their 21 pairwise products, added in 128-bit
  * integers and converted once.  Every sum is exact, so the result does not
  * depend on particle order (bitwise reproducible for a given set of
- * particles).  All 27 are NaN when a coordinate is not finite. */
+ * particles).  The second pass stages the particles in shared memory with bulk
+ * asynchronous copies when all six arrays are 16-byte aligned (plain loads
+ * otherwise); each wait for a copy is bounded (2 s), and one that runs out
+ * records BX_DEVICE_TIMEOUT for the next bx_sync.  All 27 are NaN when a
+ * coordinate is not finite or a wait ran out. */
 int32_t bx_moments(bx_ctx *ctx, const bx_beam *beam, double *out_device, void *stream);
+
+/* Self-test of that bounded device wait: one block arms a barrier for copies
+ * that are never issued, waits on it for limit_ms (0 < limit_ms <= 10000)
+ * exactly as the moments' staging waits, gives up and records the timeout in
+ * the context's status word.  The next bx_sync returns BX_DEVICE_TIMEOUT (and
+ * clears it); the context stays usable.  Nothing faults or hangs. */
+int32_t bx_selftest_wait_timeout(bx_ctx *ctx, double limit_ms, void *stream);
 
 /* Integrated Green's function table used by bx_solve: out_device receives
  * (n+1)^3 doubles G[(c*(n+1) + b)*(n+1) + a] for offsets a, b, c = 0..n cells

@@ -113,3 +113,22 @@ def moments_vector(coords: np.ndarray) -> np.ndarray:
     m = moments(coords)
     iu = np.triu_indices(6)
     return np.concatenate([m["mean"], m["cov"][iu]])
+
+
+def moments_vector_exact(coords: np.ndarray) -> np.ndarray:
+    """moments_vector in exact rational arithmetic (every double is a
+    rational), rounded once to the nearest double per output: the definition
+    mean_a = sum x_a / N, C_ab = sum (x_a - mean_a)(x_b - mean_b) / N written
+    out without rounding.  Slow: small bunches only."""
+    from fractions import Fraction
+    n = coords.shape[1]
+    if n == 0:
+        raise ValueError("moments of an empty bunch")
+    cols = [[Fraction(float(v)) for v in coords[a]] for a in range(6)]
+    mean = [sum(c, Fraction(0)) / n for c in cols]
+    dev = [[v - mean[a] for v in cols[a]] for a in range(6)]
+    out = [float(m) for m in mean]
+    for a in range(6):
+        for b in range(a, 6):
+            out.append(float(sum((u * w for u, w in zip(dev[a], dev[b])), Fraction(0)) / n))
+    return np.array(out)

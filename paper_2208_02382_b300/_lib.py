@@ -65,6 +65,7 @@ SIGNATURES = {
     "bx_gather_kick": (c_int32, [c_void_p, POINTER(bx_beam), POINTER(bx_grid), c_double,
                                  c_void_p]),
     "bx_moments": (c_int32, [c_void_p, POINTER(bx_beam), c_void_p, c_void_p]),
+    "bx_selftest_wait_timeout": (c_int32, [c_void_p, c_double, c_void_p]),
     "bx_green_table": (c_int32, [c_void_p, POINTER(c_double), c_void_p, c_void_p]),
     "bx_regrid_log": (c_int32, [c_void_p, POINTER(c_int64), c_int64, POINTER(c_int64)]),
     "bx_get_box": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_double), POINTER(c_double)]),

@@ -338,6 +338,12 @@ class Tracker:
     def sync(self):
         _check(self.lib, self.ctx, self.lib.bx_sync(self.ctx, _stream()))
 
+    def selftest_wait_timeout(self, limit_ms: float):
+        """Run the self-test of the bounded device wait; the next sync() raises
+        BeamtrackError with code BX_DEVICE_TIMEOUT."""
+        _check(self.lib, self.ctx, self.lib.bx_selftest_wait_timeout(self.ctx, float(limit_ms),
+                                                                     _stream()))
+
     # ---- tuning
     def set_binning(self, rebin_interval: int, bin_edge: int, cell_order: int = 0):
         _check(self.lib, self.ctx, self.lib.bx_set_binning(self.ctx, int(rebin_interval),

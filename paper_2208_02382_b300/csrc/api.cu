@@ -206,7 +206,7 @@ int32_t track_impl(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t fi
     }
     const int mom_nb = moments_blocks(beam->n);
     auto diag_after = [&](int64_t k) -> cudaError_t {
-        cudaError_t e = launch_moments(c, beam->n, ctx->mom_partial, mom_nb, diag + 27 * k, s);
+        cudaError_t e = launch_moments(c, beam->n, ctx->mom_partial, mom_nb, diag + 27 * k, ctx->status, s);
         if (e == cudaSuccess) e = launch_moments_transform(diag + 27 * k, inv_dev + k, s);
         return e;
     };
@@ -415,8 +415,17 @@ int32_t bx_moments(bx_ctx *ctx, const bx_beam *beam, double *out, void *stream) 
     if (beam->n == 0) return fail(ctx, BX_BAD_ARG, "moments of an empty beam");
     cudaStream_t s = (cudaStream_t)stream;
     if ((rc = ensure_moment_scratch(ctx, beam->n))) return rc;
-    CK(launch_moments(beam->coord, beam->n, ctx->mom_partial, moments_blocks(beam->n), out, s),
+    CK(launch_moments(beam->coord, beam->n, ctx->mom_partial, moments_blocks(beam->n), out,
+                      ctx->status, s),
        "moments");
+    return BX_OK;
+}
+
+int32_t bx_selftest_wait_timeout(bx_ctx *ctx, double limit_ms, void *stream) {
+    if (!ctx) return fail(nullptr, BX_BAD_ARG, "NULL context");
+    if (!(limit_ms > 0.0 && limit_ms <= 10000.0))
+        return fail(ctx, BX_BAD_ARG, "limit_ms must lie in (0, 10000]");
+    CK(launch_wait_selftest(ctx->status, limit_ms, (cudaStream_t)stream), "wait self-test");
     return BX_OK;
 }
 

@@ -241,7 +241,8 @@ cudaError_t launch_sort(double *const c[6], long long *id, int64_t n, double bet
 int sort_bins(int nn, int be, bool cell_order);
 // moments.cu
 cudaError_t launch_moments(double *const c[6], int64_t n, double *partials, int nblocks,
-                           double *out, cudaStream_t s);
+                           double *out, int *status, cudaStream_t s);
+cudaError_t launch_wait_selftest(int *status, double limit_ms, cudaStream_t s);
 int moments_blocks(int64_t n);
 size_t moments_scratch_doubles(int nblocks);
 cudaError_t launch_moments_transform(double *mom, const MapCoef *map, cudaStream_t s);

@@ -464,7 +464,7 @@ int32_t bx_grad_backward(bx_ctx *ctx, const bx_beam *beam, const double weights[
     const int C = g->C;
     // dL/dz of the final bunch
     if ((rc = ensure_moment_scratch(ctx, np))) return rc;
-    CK(launch_moments(beam->coord, np, ctx->mom_partial, moments_blocks(np), g->mom, s), "moments");
+    CK(launch_moments(beam->coord, np, ctx->mom_partial, moments_blocks(np), g->mom, ctx->status, s), "moments");
     P6 adj = p6(g->adj, np);
     CK(launch_adj_seed(p6(beam->coord), np, g->mom, weights, adj, g->amax, s), "seed");
     unsigned long long *cur = g->amax, *nxt = g->amax + 6;

@@ -2,50 +2,55 @@
 // benchmarks check second moments and emittances): means and centred second
 // moments.
 //
-// Pass 1 takes each coordinate's exact extent (min/max of order-preserving
-// integer keys, order-free).  From it, per coordinate, a scale 2^k that brings
-// the half-extent below 2^42 and an origin R 2^-k (the extent's midpoint
-// rounded to a multiple of 2^-k).  Pass 2 rounds every coordinate to the
-// integer q = round(x 2^k) - R (integer operations only: no FP64) and forms
-// the exact sums of q and of the 21 products q_a q_b, the products from 21-bit
-// limbs (q = qh 2^21 + ql: q_a q_b = qh_a qh_b 2^42 + (qh_a ql_b + ql_a qh_b)
-// 2^21 + ql_a ql_b, three 64-bit sums of 32 x 32 -> 64-bit products).  Its
-// blocks stage chunks of 1024 particles in shared memory with asynchronous
-// copies (the next chunk loads while the current one is summed), and each warp
-// sums the pairs of one row group of the 6 x 6 matrix.  The blocks' integer
-// sums are added in 128-bit integers and converted once: mean = (R + sum q/N)
-// 2^-k, centred second moment = (sum q_a q_b/N - (sum q_a/N)(sum q_b/N))
-// 2^-(k_a + k_b).  Every sum is exact, so the result does not depend on particle
-// order or blocking; the only roundings are q's (at most 2^-43 of the extent)
-// and the final conversions.
+// Both passes read the particles the same way: each block's chunks of 1024
+// particles arrive in shared memory by bulk asynchronous copies (TMA), four
+// chunks in flight per block, each completing on an mbarrier whose wait is
+// bounded in time (plain loads when an array is not 16-byte aligned).  Pass 1
+// takes each block's exact per-coordinate extent (min/max of order-preserving
+// integer keys).  Pass 2 first reduces those records and derives per
+// coordinate a scale 2^k that brings the half-extent below 2^42 and an origin
+// R 2^-k (the extent's midpoint rounded to a multiple of 2^-k); it then rounds
+// every coordinate to the integer q = round(x 2^k) - R (x 2^k formed exactly
+// from the exponent field, no FP64 arithmetic) and forms the exact sums of q
+// and of the 21 products q_a q_b, the products from 21-bit limbs (q = qh 2^21
+// + ql, s = qh + ql: q_a q_b = qh_a qh_b 2^42 + (s_a s_b - qh_a qh_b - ql_a
+// ql_b) 2^21 + ql_a ql_b, three 64-bit sums of 32 x 32 -> 64-bit products).
+// One thread takes a whole particle and keeps all 69 sums in registers.  The
+// threads' sums are added per block in 128-bit integers, the blocks' by 64-bit
+// atomics with carry into a 128-bit total, and the last block converts them
+// once: mean = (R + sum q/N) 2^-k, centred second moment = (sum q_a q_b/N -
+// (sum q_a/N)(sum q_b/N)) 2^-(k_a + k_b).  Every sum is exact, so the result
+// does not depend on particle order or blocking; the only roundings are q's
+// (to nearest: at most 2^-43 of the extent) and the final conversions.  No
+// state is kept between calls.
 #include "common.cuh"
 #include "dd.cuh"
 
 namespace bt {
 
-constexpr int MOM_TPB = 256;            // eight warps: two per row group of the 6 x 6 matrix
+constexpr int MOM_TPB = 256;            // one particle per thread and step
 constexpr int MOM_CHUNK = 1024;         // particles per staged chunk (48 KB of shared memory)
-constexpr int MOM_REC = 72;             // per-block record: 21 x 3 pair sums, 6 sums of q
-constexpr int MOM_HDR = 32;             // scratch header: keys, origins and scales, flags
+constexpr int MOM_STAGES = 4;           // chunks in flight per block
+constexpr int MOM_NV = 69;              // sums per thread: 21 x 3 pair sums, 6 sums of q
+constexpr int MOM_ACC = 2 * MOM_NV + 2; // global 128-bit sums (lo, hi words), block counter, flags
+constexpr int MOM_EXT = 16;             // per-block extent record: 6 min keys, 6 max keys, marker
+constexpr int MOM_EXT_MAX = 148 * 4;    // extent blocks at most
+constexpr unsigned long long MOM_WAIT_NS = 2000000000ull;  // bound of one staging wait: 2 s
+constexpr size_t MOM_SMEM = (size_t)MOM_STAGES * 6 * MOM_CHUNK * sizeof(double);
+static_assert((size_t)MOM_TPB * MOM_NV * 8 <= MOM_SMEM, "block sums reuse the staging buffers");
 
+// One block per SM (all 69 sums of a particle live in registers).  A thread
+// sums at most n / (148 * 256) particles' products below 2^43 (about 2^17 for
+// the 5.6e9 particles that fit in memory), far from 2^63.
 int moments_blocks(int64_t n) {
     const int64_t chunks = (n + MOM_CHUNK - 1) / MOM_CHUNK;
-    const int64_t cap = 148 * 2;        // two blocks of 2 x 48 KB per SM
-    int64_t b = chunks < cap ? chunks : cap;
+    const int64_t b = chunks < 148 ? chunks : 148;
     return (int)(b < 1 ? 1 : b);
 }
 
-size_t moments_scratch_doubles(int nblocks) { return MOM_HDR + (size_t)nblocks * MOM_REC; }
+// Scratch (as long long): the global sums, then the extent records.
+size_t moments_scratch_doubles(int) { return MOM_ACC + (size_t)MOM_EXT_MAX * MOM_EXT; }
 
-// The pairs of warp w (of a row group): row 0 (which also sums q), row 1, row 2
-// and (5, 5), rows 3 and 4; entry p is pair index mom_k(w, p) in row-major
-// upper-triangle order (-1: none).
-__host__ __device__ constexpr int mom_np(int w) { return w == 0 ? 6 : 5; }
-__host__ __device__ constexpr int mom_k(int w, int p) {
-    constexpr int K[4][6] = {{0, 1, 2, 3, 4, 5}, {6, 7, 8, 9, 10, -1}, {11, 12, 13, 14, 20, -1},
-                             {15, 16, 17, 18, 19, -1}};
-    return K[w][p];
-}
 __host__ __device__ constexpr int mom_a(int k) {
     constexpr int A[21] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 3, 4, 4, 5};
     return A[k];
@@ -55,115 +60,58 @@ __host__ __device__ constexpr int mom_b(int k) {
     return B[k];
 }
 
-// round(d * 2^s) for |d * 2^s| < 2^62, by exponent/mantissa arithmetic on the
-// integer pipes (ties away from zero; |d * 2^s| < 1/2 gives 0).
-__device__ __forceinline__ long long fix_round(double d, int s) {
+// round(d * 2^s) for |d * 2^s| < 2^62, to nearest, in one of two ways that
+// give the same integer except on exact ties (within 1/2 either way):
+//
+// fix_round_cvt: d 2^s formed exactly by adding s to the exponent field, then
+// one hardware conversion to a 64-bit integer (ties to even; FP64 pipe).  A
+// value that would fall below the normal range (|d 2^s| < 2^-1022; zeros and
+// subnormals) keeps only its sign and low word, a subnormal, which rounds to 0.
+__device__ __forceinline__ long long fix_round_cvt(double d, int s) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned hi = (unsigned)(b >> 32);
+    const int e = (int)((hi >> 20) & 0x7FF);
+    const unsigned hs = (e > 0 && e + s > 0) ? hi + ((unsigned)s << 20) : (hi & 0x80000000u);
+    return __double2ll_rn(__hiloint2double((int)hs, (int)(unsigned)b));
+}
+
+// fix_round_int: exponent and mantissa arithmetic on the integer pipes, no
+// branches (ties away from zero): with the significand m (53 bits) shifted to
+// t = m 2^10 < 2^63, |d| 2^s = t 2^-r and the rounded magnitude is
+// floor((floor(t 2^-(r-1)) + 1) / 2), which is 0 for r >= 64 (r is limited to
+// 64: t 2^-63 < 1); zeros and subnormals take r = 64.
+__device__ __forceinline__ long long fix_round_int(double d, int s) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(d);
     const int e = (int)((b >> 52) & 0x7FF);
-    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = e - 1075 + s;  // |d| 2^s = m 2^sh
-    unsigned long long v;
-    if (e == 0 || sh < -54) v = 0;
-    else if (sh >= 0) v = m << min(sh, 9);
-    else v = (m + (1ull << (-sh - 1))) >> (-sh);
-    return (b >> 63) ? -(long long)v : (long long)v;
+    const unsigned long long t = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 10;
+    const int r1 = e == 0 ? 63 : min(max(1085 - s - e, 1), 64) - 1;
+    const unsigned long long v = ((t >> r1) + 1) >> 1;
+    const long long sg = (long long)b >> 63;
+    return ((long long)v ^ sg) - sg;
 }
 
-// Coordinate k of the six arrays (a uniform select, no indexed local array).
-__device__ __forceinline__ const double *coord6(const double *x, const double *px,
-                                                const double *y, const double *py,
-                                                const double *t, const double *pt, int k) {
-    return k == 0 ? x : k == 1 ? px : k == 2 ? y : k == 3 ? py : k == 4 ? t : pt;
+// Coordinates whose q takes the hardware conversion (bit k for coordinate k);
+// the others take the integer pipes, so that both pipes share the work (four
+// of six measured fastest: 2.5e7 particles, 0.626 ms against 0.677 with none
+// and 0.648 with all six).
+#ifndef MOM_CVT_MASK
+#define MOM_CVT_MASK 0x0F
+#endif
+template <int K>
+__device__ __forceinline__ long long fix_round_k(double d, int s) {
+    if constexpr ((MOM_CVT_MASK >> K) & 1) return fix_round_cvt(d, s);
+    else return fix_round_int(d, s);
 }
 
-// Scratch header (as long long): [0..5] min keys, [6..11] max keys, [12..17]
-// scales k, [18..23] origins R, [24..29] the origin's FP64 value (far origins),
-// [30] flags (1: a coordinate not finite; 2 << c: coordinate c far from its
-// origin relative to its extent, q taken from the FP64 difference).
-__global__ void k_mom_init(long long *hdr) {
-    if (threadIdx.x < 6) {
-        hdr[threadIdx.x] = LLONG_MAX;
-        hdr[6 + threadIdx.x] = LLONG_MIN;
-    }
-}
+// The six coordinate arrays (indexed with unrolled, compile-time k only).
+struct Coords6 {
+    const double *p[6];
+};
 
-// Pass 1: exact per-coordinate min/max keys (order-free integer atomics).
-__global__ void __launch_bounds__(256) k_mom_extent(
-    const double *__restrict__ x, const double *__restrict__ px, const double *__restrict__ y,
-    const double *__restrict__ py, const double *__restrict__ t, const double *__restrict__ pt,
-    int64_t n, long long *hdr) {
-    long long lo[6], hi[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        lo[k] = LLONG_MAX;
-        hi[k] = LLONG_MIN;
-    }
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    for (; p + 3 * stride < n; p += 4 * stride) {   // four particles' loads in flight
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const double *c = coord6(x, px, y, py, t, pt, k);
-            const long long k0 = dkey(c[p]), k1 = dkey(c[p + stride]), k2 = dkey(c[p + 2 * stride]),
-                            k3 = dkey(c[p + 3 * stride]);
-            lo[k] = min(lo[k], min(min(k0, k1), min(k2, k3)));
-            hi[k] = max(hi[k], max(max(k0, k1), max(k2, k3)));
-        }
-    }
-    for (; p < n; p += stride)
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const long long kk = dkey(coord6(x, px, y, py, t, pt, k)[p]);
-            lo[k] = min(lo[k], kk);
-            hi[k] = max(hi[k], kk);
-        }
-    __shared__ long long s_lo[6][8], s_hi[6][8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        for (int o = 16; o > 0; o >>= 1) {
-            lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
-            hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
-        }
-        if (lane == 0) {
-            s_lo[k][warp] = lo[k];
-            s_hi[k][warp] = hi[k];
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < 6) {
-        long long a = s_lo[threadIdx.x][0], b = s_hi[threadIdx.x][0];
-        for (int w = 1; w < 8; ++w) {
-            a = min(a, s_lo[threadIdx.x][w]);
-            b = max(b, s_hi[threadIdx.x][w]);
-        }
-        atomicMin(&hdr[threadIdx.x], a);
-        atomicMax(&hdr[6 + threadIdx.x], b);
-    }
-}
-
-// Scales and origins from the extents (one thread per coordinate).
-__global__ void k_mom_prep(long long *hdr) {
-    const int c = threadIdx.x;
-    if (c == 0) hdr[30] = 0;
-    __syncwarp();
-    if (c >= 6) return;
-    const double mn = dkey_inv(hdr[c]), mx = dkey_inv(hdr[6 + c]);
-    const double mid = __dmul_rn(0.5, __dadd_rn(mn, mx));
-    const double half = fmax(__dsub_rn(mx, mid), __dsub_rn(mid, mn));
-    int sc = 0;
-    long long flag = 0, R = 0;
-    if (!(isfinite(mid) && isfinite(half))) {
-        flag = 1;
-    } else {
-        if (half > 0.0) sc = 42 - (ilogb(half) + 1);   // half 2^sc < 2^42
-        if (mid != 0.0 && ilogb(mid) + sc >= 60) flag = 2ll << c;   // far origin: FP64 difference
-        else R = fix_round(mid, sc);
-    }
-    hdr[12 + c] = sc;
-    hdr[18 + c] = R;
-    hdr[24 + c] = __double_as_longlong(mid);
-    if (flag) atomicOr(reinterpret_cast<unsigned long long *>(&hdr[30]), (unsigned long long)flag);
+__device__ __forceinline__ void key_minmax(double v, long long &lo, long long &hi) {
+    const long long k = dkey(v);
+    lo = min(lo, k);
+    hi = max(hi, k);
 }
 
 // acc + a b for 32-bit a, b and a 64-bit accumulator: one wide multiply-add
@@ -179,207 +127,453 @@ __device__ __forceinline__ long long mad_wide_u(unsigned a, unsigned b, long lon
     return d;
 }
 
-__device__ __forceinline__ void cp_async8(double *dst, const double *src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+// ---- bulk asynchronous copies (TMA) completing on an mbarrier ----------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// The producer's arrival, announcing `bytes` of copies that complete on the barrier.
+__device__ __forceinline__ void mbar_arrive_expect(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+// Wait for the completion of phase `parity` of the barrier; false once
+// limit_ns of global time (or 2^24 polls) went by without it.
+__device__ bool mbar_wait(unsigned bar, unsigned parity, unsigned long long limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 1; it < (1u << 24); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 15) == 0 && global_ns() - t0 > limit_ns) return false;
+    }
+    return false;
+}
+// `bytes` (a multiple of 16, both addresses 16-byte aligned) from global to
+// shared memory, completing on the barrier.
+__device__ __forceinline__ void bulk_copy_g2s(unsigned dst, const void *src, unsigned bytes,
+                                              unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
 
-// Pass 2.  The block's j-th chunk (chunk blockIdx.x + j gridDim.x) goes to
-// buffer j & 1; the six coordinate rows of 1024 doubles are copied
-// asynchronously (the next chunk's copies run while this one is summed),
-// converted in place to q, then summed.
-__global__ void __launch_bounds__(MOM_TPB, 2) k_mom_sums(
-    const double *__restrict__ x, const double *__restrict__ px, const double *__restrict__ y,
-    const double *__restrict__ py, const double *__restrict__ t, const double *__restrict__ pt,
-    int64_t n, const long long *__restrict__ hdr, long long *__restrict__ rec) {
-    extern __shared__ double sbuf[];                 // [2][6][MOM_CHUNK]
+// The block's chunks of 1024 particles (chunk blockIdx.x + j gridDim.x for
+// j = 0, 1, ...), handed to body(ld, cnt) with ld(k, i) = coordinate k of the
+// chunk's particle i.  TMA: chunk j arrives in stage j % 4 of the shared
+// buffers by bulk copies of its six rows (the even part of a ragged chunk;
+// thread 0 copies its odd last particle), four chunks in flight; thread 0
+// refills a stage once every thread is done with it.  pre() runs while the
+// first copies are in flight.  Every wait is bounded: if one runs out, the
+// timeout goes to *status, the copies still in flight are waited for (bounded
+// again) and the result is false.  Not TMA: ld reads global memory.
+template <bool TMA, class Pre, class Body>
+__device__ __forceinline__ bool staged_chunks(const Coords6 c, int64_t n, double *sbuf,
+                                              unsigned long long *bar, unsigned long long wait_ns,
+                                              int *status, Pre &&pre, Body &&body) {
+    const int tid = threadIdx.x;
+    const int64_t nchunks = (n + MOM_CHUNK - 1) / MOM_CHUNK;
+    const int J = blockIdx.x < nchunks ? (int)((nchunks - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+    auto chunk_at = [&](int j) { return (blockIdx.x + (int64_t)j * gridDim.x) * MOM_CHUNK; };
+    if constexpr (!TMA) {
+        pre();
+        for (int j = 0; j < J; ++j) {
+            const int64_t b0 = chunk_at(j);
+            const int cnt = (int)min((int64_t)MOM_CHUNK, n - b0);
+            body([&](int k, int i) { return c.p[k][b0 + i]; }, cnt);
+        }
+        return true;
+    } else {
+        auto issue = [&](int j) {                      // thread 0: chunk j into stage j % 4
+            const int64_t b0 = chunk_at(j);
+            const unsigned bytes = (unsigned)(min((int64_t)MOM_CHUNK, n - b0) & ~1ll) * 8u;
+            const int st = j % MOM_STAGES;
+            const unsigned b = smem_u32(&bar[st]);
+            fence_proxy_async();
+            mbar_arrive_expect(b, 6 * bytes);
+            if (bytes)
+#pragma unroll
+                for (int k = 0; k < 6; ++k)
+                    bulk_copy_g2s(smem_u32(sbuf + (size_t)(st * 6 + k) * MOM_CHUNK), c.p[k] + b0, bytes, b);
+        };
+        if (tid == 0) {
+            for (int st = 0; st < MOM_STAGES; ++st) mbar_init(smem_u32(&bar[st]), 1);
+            fence_proxy_async();
+            for (int j = 0; j < min(J, MOM_STAGES); ++j) issue(j);
+        }
+        __syncthreads();
+        pre();
+        int j = 0;
+        bool ok_all = true;
+        for (; j < J; ++j) {
+            const int st = j % MOM_STAGES;
+            const int64_t b0 = chunk_at(j);
+            const int cnt = (int)min((int64_t)MOM_CHUNK, n - b0);
+            double *sg = sbuf + (size_t)st * 6 * MOM_CHUNK;
+            const bool ok = mbar_wait(smem_u32(&bar[st]), (unsigned)(j / MOM_STAGES) & 1u, wait_ns);
+            if (ok && tid == 0 && (cnt & 1))
+#pragma unroll
+                for (int k = 0; k < 6; ++k) sg[k * MOM_CHUNK + cnt - 1] = c.p[k][b0 + cnt - 1];
+            if (__syncthreads_or(!ok)) {
+                ok_all = false;
+                break;
+            }
+            body([&](int k, int i) { return sg[k * MOM_CHUNK + i]; }, cnt);
+            __syncthreads();                            // every thread is done with stage st
+            if (tid == 0 && j + MOM_STAGES < J) issue(j + MOM_STAGES);
+        }
+        if (!ok_all && tid == 0) {
+            atomicOr(status, ST_TIMEOUT);
+            for (int jj = j; jj < min(J, j + MOM_STAGES); ++jj)
+                mbar_wait(smem_u32(&bar[jj % MOM_STAGES]), (unsigned)(jj / MOM_STAGES) & 1u, wait_ns);
+        }
+        return ok_all;
+    }
+}
+
+// Pass 1: each block's exact per-coordinate min/max keys (order-preserving
+// integer keys of the doubles) into its extent record, with a completion
+// marker (0 if a staging wait ran out).  Block 0 also clears the global sums,
+// block counter and flags that pass 2 adds into.
+template <bool TMA>
+__global__ void __launch_bounds__(MOM_TPB, 1) k_mom_extent(Coords6 c, int64_t n,
+                                                           long long *__restrict__ ext,
+                                                           long long *__restrict__ acc, int *status,
+                                                           unsigned long long wait_ns) {
+    if (blockIdx.x == 0 && threadIdx.x < MOM_ACC) acc[threadIdx.x] = 0;
+    extern __shared__ __align__(128) double sbuf[];
+    __shared__ __align__(8) unsigned long long s_bar[MOM_STAGES];
+    __shared__ long long s_lo[6][MOM_TPB / 32], s_hi[6][MOM_TPB / 32];
+    long long lo[6], hi[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        lo[k] = LLONG_MAX;
+        hi[k] = LLONG_MIN;
+    }
+    const bool ok = staged_chunks<TMA>(c, n, sbuf, s_bar, wait_ns, status, [] {},
+                                       [&](auto ld, int cnt) {
+                                           for (int i = threadIdx.x; i < cnt; i += MOM_TPB)
+#pragma unroll
+                                               for (int k = 0; k < 6; ++k) key_minmax(ld(k, i), lo[k], hi[k]);
+                                       });
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+        if (lane == 0) {
+            s_lo[k][warp] = lo[k];
+            s_hi[k][warp] = hi[k];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {
+        const int k = threadIdx.x % 6;
+        const bool mx = threadIdx.x >= 6;
+        long long v = mx ? s_hi[k][0] : s_lo[k][0];
+        for (int w = 1; w < MOM_TPB / 32; ++w) v = mx ? max(v, s_hi[k][w]) : min(v, s_lo[k][w]);
+        ext[(size_t)blockIdx.x * MOM_EXT + threadIdx.x] = v;
+    }
+    if (threadIdx.x == 12) ext[(size_t)blockIdx.x * MOM_EXT + 12] = ok ? 1 : 0;
+}
+
+// 128-bit integer to double-double: v = c2 2^86 + c1 2^43 + c0 with c1, c0 in
+// [0, 2^43), each part an exact double (hardware 64-bit conversions only).
+__device__ __forceinline__ dd i128_to_dd(__int128 v) {
+    constexpr long long M43 = (1ll << 43) - 1;
+    const double c2 = (double)(long long)(v >> 86);
+    const double c1 = (double)((long long)(v >> 43) & M43);
+    const double c0 = (double)((long long)v & M43);
+    return dd_add_d(two_sum(c2 * 0x1p86, c1 * 0x1p43), c0);
+}
+
+// Pass 2.  Prologue (while the first copies are in flight): the extent from
+// the extent records, and from it per coordinate the scale 2^k (half-extent
+// 2^k < 2^42) and the origin R (the midpoint rounded at 2^-k), or, for a
+// coordinate far from its origin relative to its extent or of zero extent,
+// the FP64 midpoint itself (q from the FP64 difference, then exact); every
+// block derives the same values.  Then every particle's q and its exact sums:
+// per pair, with s = qh + ql, the sums of qh_a qh_b, ql_a ql_b and
+// K = s_a s_b (three wide products; the cross sum is K - hh - ll).  The
+// block's sums, added in 128-bit integers, go into the global sums by 64-bit
+// atomics (the low word's wrap carried into the high word: exact in any
+// order).  The last block to finish converts them into the 27 moments.
+template <bool TMA>
+__global__ void __launch_bounds__(MOM_TPB, 1) k_mom_sums(Coords6 c, int64_t n,
+                                                         const long long *__restrict__ ext, int next,
+                                                         long long *__restrict__ acc, double *out,
+                                                         int *status, unsigned long long wait_ns) {
+    extern __shared__ __align__(128) double sbuf[];   // [4][6][MOM_CHUNK], then the block sums
+    __shared__ __align__(8) unsigned long long s_bar[MOM_STAGES];
+    __shared__ long long s_key[13];
     __shared__ int s_sc[6];
     __shared__ long long s_R[6];
     __shared__ double s_mid[6];
-    __shared__ long long s_flag;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, grp = warp & 3, half = warp >> 2;
-    if (tid < 6) {
-        s_sc[tid] = (int)hdr[12 + tid];
-        s_R[tid] = hdr[18 + tid];
-        s_mid[tid] = __longlong_as_double(hdr[24 + tid]);
-    }
-    if (tid == 0) s_flag = hdr[30];
-    const int64_t nchunks = (n + MOM_CHUNK - 1) / MOM_CHUNK;
-    auto issue = [&](int64_t ch, int j) {
-        if (ch < nchunks) {
-            const int64_t b0 = ch * MOM_CHUNK;
-            const int cnt = (int)min((int64_t)MOM_CHUNK, n - b0);
-            double *buf = sbuf + (size_t)(j & 1) * 6 * MOM_CHUNK;
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const double *src = coord6(x, px, y, py, t, pt, k) + b0;
-                for (int i = tid; i < cnt; i += MOM_TPB) cp_async8(buf + k * MOM_CHUNK + i, src + i);
+    __shared__ unsigned s_flag;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int sc[6];
+    long long R[6];
+    double mid[6];
+    unsigned flag = 0;
+    auto pre = [&] {
+        for (int k = warp; k < 13; k += MOM_TPB / 32) {   // 6 min keys, 6 max keys, the markers
+            const bool is_max = k >= 6 && k < 12;
+            long long v = is_max ? LLONG_MIN : LLONG_MAX;
+            for (int r = lane; r < next; r += 32) {
+                const long long x = ext[(size_t)r * MOM_EXT + k];
+                v = is_max ? max(v, x) : min(v, x);
             }
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long y = __shfl_xor_sync(0xffffffffu, v, o);
+                v = is_max ? max(v, y) : min(v, y);
+            }
+            if (lane == 0) s_key[k] = v;
         }
-        cp_async_commit();
-    };
-    // per-lane exact sums over all of the block's chunks (a lane sums at most
-    // 2^11 products below 2^43 per chunk share: far from 2^63)
-    constexpr int NPMAX = 6;
-    long long hh[NPMAX], mid[NPMAX], ll[NPMAX], sq[6];
-#pragma unroll
-    for (int p = 0; p < NPMAX; ++p) hh[p] = mid[p] = ll[p] = 0;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) sq[k] = 0;
-    issue(blockIdx.x, 0);
-    __syncthreads();
-    const long long flag = s_flag;
-    int j = 0;
-    for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x, ++j) {
-        issue(ch + gridDim.x, j + 1);          // the next chunk, into the other buffer
-        cp_async_wait<1>();                     // this chunk's copies are done
         __syncthreads();
-        const int64_t b0 = ch * MOM_CHUNK;
-        const int cnt = (int)min((int64_t)MOM_CHUNK, n - b0);
-        double *buf = sbuf + (size_t)(j & 1) * 6 * MOM_CHUNK;
-        long long *q = reinterpret_cast<long long *>(buf);
-        // coordinates to integers, in place
+        if (warp == 0) {
+            unsigned f = 0;
+            if (tid < 6) {
+                const double mn = dkey_inv(s_key[tid]), mx = dkey_inv(s_key[6 + tid]);
+                const double m = __dmul_rn(0.5, __dadd_rn(mn, mx));
+                const double half = fmax(__dsub_rn(mx, m), __dsub_rn(m, mn));
+                int k2 = 0;
+                long long r0 = 0;
+                if (!(isfinite(m) && isfinite(half))) {
+                    f = 1;
+                } else {
+                    if (half > 0.0) k2 = 42 - (ilogb(half) + 1);   // half 2^k < 2^42
+                    if (half == 0.0 || (m != 0.0 && ilogb(m) + k2 >= 60)) f = 2u << tid;
+                    else r0 = fix_round_int(m, k2);
+                }
+                s_sc[tid] = k2;
+                s_R[tid] = r0;
+                s_mid[tid] = m;
+            }
+            if (tid == 6 && s_key[12] != 1) f = 1;   // an extent block's wait ran out
+            f = __reduce_or_sync(0xffffffffu, f);
+            if (tid == 0) s_flag = f;
+        }
+        __syncthreads();
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
-            const int sc = s_sc[k];
-            const bool far = (flag >> (k + 1)) & 1;
-            const long long R = s_R[k];
-            const double m = s_mid[k];
-            for (int i = tid; i < cnt; i += MOM_TPB) {
-                const double v = buf[k * MOM_CHUNK + i];
-                q[k * MOM_CHUNK + i] = far ? fix_round(v - m, sc) : fix_round(v, sc) - R;
-            }
+            sc[k] = s_sc[k];
+            R[k] = s_R[k];
+            mid[k] = s_mid[k];
         }
+        flag = s_flag;
+    };
+    long long hh[21], md[21], ll[21], sq[6];
+#pragma unroll
+    for (int p = 0; p < 21; ++p) hh[p] = md[p] = ll[p] = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sq[k] = 0;
+    // a particle's q per coordinate, as 21-bit limbs
+    struct Limbs {
+        int h[6];
+        unsigned l[6];
+    };
+    auto convert = [&](auto ld, int i, auto far_tag) {
+        constexpr bool ANYFAR = decltype(far_tag)::value;
+        Limbs L;
+        auto one = [&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            const double v = ld(k, i);
+            long long q;
+            if constexpr (ANYFAR)
+                q = ((flag >> (k + 1)) & 1) ? fix_round_k<k>(v - mid[k], sc[k]) : fix_round_k<k>(v, sc[k]) - R[k];
+            else
+                q = fix_round_k<k>(v, sc[k]) - R[k];
+            sq[k] += q;
+            L.h[k] = (int)(q >> 21);
+            L.l[k] = (unsigned)q & 0x1FFFFFu;
+        };
+        one(std::integral_constant<int, 0>{});
+        one(std::integral_constant<int, 1>{});
+        one(std::integral_constant<int, 2>{});
+        one(std::integral_constant<int, 3>{});
+        one(std::integral_constant<int, 4>{});
+        one(std::integral_constant<int, 5>{});
+        return L;
+    };
+    // its limb products: hh, ll and K = (qh_a + ql_a)(qh_b + ql_b) per pair
+    // (|qh + ql| < 2^22, so |K| < 2^44)
+    auto accumulate = [&](const Limbs &L) {
+        int sl[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sl[k] = L.h[k] + (int)L.l[k];
+#pragma unroll
+        for (int p = 0; p < 21; ++p) {
+            const int a = mom_a(p), b = mom_b(p);
+            hh[p] = mad_wide_s(L.h[a], L.h[b], hh[p]);
+            md[p] = mad_wide_s(sl[a], sl[b], md[p]);
+            ll[p] = mad_wide_u(L.l[a], L.l[b], ll[p]);
+        }
+    };
+    // two particles per step (twelve independent conversions in flight)
+    auto chunk = [&](auto ld, int cnt, auto far_tag) {
+        int i = tid;
+        for (; i + MOM_TPB < cnt; i += 2 * MOM_TPB) {
+            const Limbs L0 = convert(ld, i, far_tag);
+            const Limbs L1 = convert(ld, i + MOM_TPB, far_tag);
+            accumulate(L0);
+            accumulate(L1);
+        }
+        if (i < cnt) accumulate(convert(ld, i, far_tag));
+    };
+    const bool ok = staged_chunks<TMA>(c, n, sbuf, s_bar, wait_ns, status, pre, [&](auto ld, int cnt) {
+        if (flag & 0x7Eu) chunk(ld, cnt, std::true_type{});
+        else chunk(ld, cnt, std::false_type{});
+    });
+    __shared__ __int128 s_tot[MOM_NV];
+    __shared__ int s_last;
+    if (ok) {
+        // block sums in 128-bit integers: the threads' sums through shared
+        // memory (the staging buffers are free: every copy has been waited for)
         __syncthreads();
-        // warp (grp, half): the pairs of row group grp over half the chunk
-        const int i0 = half * (MOM_CHUNK / 2), i1 = min(cnt, i0 + MOM_CHUNK / 2);
-        for (int i = i0 + lane; i < i1; i += 32) {
-            int qh[6], ql[6];
+        long long *s64 = reinterpret_cast<long long *>(sbuf);
 #pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const long long v = q[k * MOM_CHUNK + i];
-                qh[k] = (int)(v >> 21);
-                ql[k] = (int)(v & 0x1FFFFF);
-                if (grp == 0) sq[k] += v;
+        for (int p = 0; p < 21; ++p) {
+            s64[tid * MOM_NV + 3 * p] = hh[p];
+            s64[tid * MOM_NV + 3 * p + 1] = md[p];
+            s64[tid * MOM_NV + 3 * p + 2] = ll[p];
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s64[tid * MOM_NV + 63 + k] = sq[k];
+        __syncthreads();
+        if (tid < MOM_NV) {
+            __int128 t0 = 0, t1 = 0, t2 = 0, t3 = 0;    // four chains: loads overlap
+            for (int i = 0; i < MOM_TPB; i += 4) {
+                t0 += s64[i * MOM_NV + tid];
+                t1 += s64[(i + 1) * MOM_NV + tid];
+                t2 += s64[(i + 2) * MOM_NV + tid];
+                t3 += s64[(i + 3) * MOM_NV + tid];
             }
-            switch (grp) {
-#define MOM_ROWS(W)                                                              \
-    case W:                                                                      \
-        _Pragma("unroll") for (int p = 0; p < mom_np(W); ++p) {                  \
-            const int a = mom_a(mom_k(W, p)), b = mom_b(mom_k(W, p));            \
-            hh[p] = mad_wide_s(qh[a], qh[b], hh[p]);                             \
-            mid[p] = mad_wide_s(ql[a], qh[b], mad_wide_s(qh[a], ql[b], mid[p])); \
-            ll[p] = mad_wide_u((unsigned)ql[a], (unsigned)ql[b], ll[p]);         \
-        }                                                                        \
-        break;
-                MOM_ROWS(0)
-                MOM_ROWS(1)
-                MOM_ROWS(2)
-                MOM_ROWS(3)
-#undef MOM_ROWS
-            }
+            const __int128 t = (t0 + t1) + (t2 + t3);
+            unsigned long long *g = reinterpret_cast<unsigned long long *>(acc + 2 * tid);
+            const unsigned long long lo = (unsigned long long)t;
+            const unsigned long long old = atomicAdd(g, lo);
+            atomicAdd(g + 1, (unsigned long long)(t >> 64) + (old + lo < old ? 1ull : 0ull));
+            __threadfence();
         }
-        __syncthreads();                        // the buffer is free for the chunk after next
-    }
-    cp_async_wait<0>();
-    // warp sums (each below 2^62), then the two warps of a row group add theirs
-    __shared__ long long s_rec[2][MOM_REC];
-#pragma unroll
-    for (int p = 0; p < NPMAX; ++p)
-        for (int o = 16; o > 0; o >>= 1) {
-            hh[p] += __shfl_xor_sync(0xffffffffu, hh[p], o);
-            mid[p] += __shfl_xor_sync(0xffffffffu, mid[p], o);
-            ll[p] += __shfl_xor_sync(0xffffffffu, ll[p], o);
-        }
-#pragma unroll
-    for (int k = 0; k < 6; ++k)
-        for (int o = 16; o > 0; o >>= 1) sq[k] += __shfl_xor_sync(0xffffffffu, sq[k], o);
-    if (lane == 0) {
-        for (int p = 0; p < mom_np(grp); ++p) {
-            const int kk = grp == 0 ? mom_k(0, p) : grp == 1 ? mom_k(1, p) : grp == 2 ? mom_k(2, p) : mom_k(3, p);
-            s_rec[half][3 * kk] = hh[p];
-            s_rec[half][3 * kk + 1] = mid[p];
-            s_rec[half][3 * kk + 2] = ll[p];
-        }
-        if (grp == 0)
-            for (int k = 0; k < 6; ++k) s_rec[half][63 + k] = sq[k];
+    } else if (tid == 0) {
+        atomicOr(reinterpret_cast<unsigned long long *>(acc + 2 * MOM_NV + 1), 1ull);   // incomplete
+        __threadfence();
     }
     __syncthreads();
-    if (tid < 69) rec[(size_t)blockIdx.x * MOM_REC + tid] = s_rec[0][tid] + s_rec[1][tid];
-}
-
-// 128-bit integer to double-double.
-__device__ __forceinline__ dd i128_to_dd(__int128 v) {
-    const double hi = (double)v;
-    const double lo = (double)(v - (__int128)hi);
-    return fast_two_sum(hi, lo);
-}
-
-// The blocks' records added in 128-bit integers (exact), then the 27 moments
-// (one warp; lane j < 27 takes output j).
-__global__ void k_mom_final(const long long *__restrict__ hdr, const long long *__restrict__ rec,
-                            int nblocks, int64_t n, double *__restrict__ out) {
-    const int lane = threadIdx.x;
+    if (tid == 0) {
+        const unsigned long long done =
+            atomicAdd(reinterpret_cast<unsigned long long *>(acc + 2 * MOM_NV), 1ull);
+        s_last = done == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    // the last block: every block's sums are in
+    __threadfence();
+    if (tid < MOM_NV)
+        s_tot[tid] = (__int128)(unsigned long long)__ldcg(acc + 2 * tid) |
+                     ((__int128)__ldcg(acc + 2 * tid + 1) << 64);
+    __syncthreads();
+    if (warp != 0) return;
     __shared__ double s_m[6][2];
-    __int128 a = 0, b = 0, c = 0;               // sum q (lanes < 6) or HH, MID, LL
-    if (lane < 27)
-        for (int blk = 0; blk < nblocks; ++blk) {
-            const long long *r = rec + (size_t)blk * MOM_REC;
-            if (lane < 6) {
-                a += r[63 + lane];
-            } else {
-                const int k = lane - 6;
-                a += r[3 * k];
-                b += r[3 * k + 1];
-                c += r[3 * k + 2];
-            }
-        }
-    const bool bad = (hdr[30] & 1) != 0;
+    const bool bad = (flag & 1u) || __ldcg(acc + 2 * MOM_NV + 1) != 0;
     const double N = (double)n;
     if (lane < 6) {
-        const dd mq = dd_div_d(i128_to_dd(a), N);            // mean of q
+        const dd mq = dd_div_d(i128_to_dd(s_tot[63 + lane]), N);   // mean of q
         s_m[lane][0] = mq.hi;
         s_m[lane][1] = mq.lo;
     }
     __syncwarp();
     if (lane < 6) {
-        const int sc = (int)hdr[12 + lane];
-        const bool far = (hdr[30] >> (lane + 1)) & 1;
+        const bool far = (flag >> (lane + 1)) & 1u;
         const dd mq{s_m[lane][0], s_m[lane][1]};
         // origin: R 2^-k, or the FP64 midpoint for a far origin
-        const dd org = far ? dd_make(__longlong_as_double(hdr[24 + lane]))
-                           : dd_scale(i128_to_dd((__int128)hdr[18 + lane]), ldexp(1.0, -sc));
-        out[lane] = bad ? NAN : dd_add(org, dd_scale(mq, ldexp(1.0, -sc))).hi;
+        const int k2 = s_sc[lane];
+        const dd org = far ? dd_make(s_mid[lane]) : dd_scale(i128_to_dd((__int128)s_R[lane]), ldexp(1.0, -k2));
+        out[lane] = bad ? NAN : dd_add(org, dd_scale(mq, ldexp(1.0, -k2))).hi;
     } else if (lane < 27) {
         const int k = lane - 6, ia = mom_a(k), ib = mom_b(k);
-        const int sa = (int)hdr[12 + ia], sb = (int)hdr[12 + ib];
-        // sum q_a q_b = HH 2^42 + MID 2^21 + LL
-        const dd S = dd_add(dd_scale(i128_to_dd(a), 0x1p42),
-                            dd_add(dd_scale(i128_to_dd(b), 0x1p21), i128_to_dd(c)));
+        // sum q_a q_b = HH 2^42 + (K - HH - LL) 2^21 + LL, exact in 128 bits
+        // (|sum| < N 2^84)
+        const __int128 HH = s_tot[3 * k], K = s_tot[3 * k + 1], LL = s_tot[3 * k + 2];
+        const dd S = i128_to_dd(HH * ((__int128)1 << 42) + (K - HH - LL) * ((__int128)1 << 21) + LL);
         const dd ma{s_m[ia][0], s_m[ia][1]}, mb{s_m[ib][0], s_m[ib][1]};
         const dd v = dd_sub(dd_div_d(S, N), dd_mul(ma, mb));
-        out[lane] = bad ? NAN : ldexp(v.hi, -(sa + sb));
+        out[lane] = bad ? NAN : ldexp(v.hi, -(s_sc[ia] + s_sc[ib]));
     }
 }
 
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
 cudaError_t launch_moments(double *const c[6], int64_t n, double *partials, int nblocks,
-                           double *out, cudaStream_t s) {
-    long long *hdr = reinterpret_cast<long long *>(partials);
-    long long *rec = hdr + MOM_HDR;
-    const size_t sm = (size_t)2 * 6 * MOM_CHUNK * sizeof(double);
-    cudaFuncSetAttribute(k_mom_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    int eb = (int)((n + 255) / 256);
-    if (eb > 148 * 8) eb = 148 * 8;
-    if (eb < 1) eb = 1;
-    BT_LAUNCH(K_MOMENTS, s, k_mom_init<<<1, 32, 0, s>>>(hdr));
-    BT_LAUNCH(K_MOMENTS, s, k_mom_extent<<<eb, 256, 0, s>>>(c[0], c[1], c[2], c[3], c[4], c[5], n, hdr));
-    BT_LAUNCH(K_MOMENTS, s, k_mom_prep<<<1, 32, 0, s>>>(hdr));
-    BT_LAUNCH(K_MOMENTS, s, k_mom_sums<<<nblocks, MOM_TPB, sm, s>>>(c[0], c[1], c[2], c[3], c[4],
-                                                                     c[5], n, hdr, rec));
-    BT_LAUNCH(K_MOMENTS, s, k_mom_final<<<1, 32, 0, s>>>(hdr, rec, nblocks, n, out));
+                           double *out, int *status, cudaStream_t s) {
+    long long *acc = reinterpret_cast<long long *>(partials);
+    long long *ext = acc + MOM_ACC;
+    Coords6 cc;
+    bool al = true;
+    for (int k = 0; k < 6; ++k) {
+        cc.p[k] = c[k];
+        al = al && aligned16(c[k]);
+    }
+    // staged: one block per SM; plain loads: up to four blocks per SM
+    const int64_t chunks = (n + MOM_CHUNK - 1) / MOM_CHUNK;
+    const int eb = (int)std::max<int64_t>(1, std::min<int64_t>(chunks, al ? 148 : MOM_EXT_MAX));
+    if (al) {
+        cudaFuncSetAttribute(k_mom_extent<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MOM_SMEM);
+        cudaFuncSetAttribute(k_mom_sums<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MOM_SMEM);
+        BT_LAUNCH(K_MOMENTS, s, k_mom_extent<true><<<eb, MOM_TPB, MOM_SMEM, s>>>(cc, n, ext, acc, status,
+                                                                                MOM_WAIT_NS));
+        BT_LAUNCH(K_MOMENTS, s, k_mom_sums<true><<<nblocks, MOM_TPB, MOM_SMEM, s>>>(cc, n, ext, eb, acc, out,
+                                                                                   status, MOM_WAIT_NS));
+    } else {
+        const size_t sm = (size_t)MOM_TPB * MOM_NV * 8;   // the block sums only
+        cudaFuncSetAttribute(k_mom_sums<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        BT_LAUNCH(K_MOMENTS, s, k_mom_extent<false><<<eb, MOM_TPB, 0, s>>>(cc, n, ext, acc, status, MOM_WAIT_NS));
+        BT_LAUNCH(K_MOMENTS, s, k_mom_sums<false><<<nblocks, MOM_TPB, sm, s>>>(cc, n, ext, eb, acc, out,
+                                                                              status, MOM_WAIT_NS));
+    }
+    return cudaGetLastError();
+}
+
+// Self-test of the bounded staging wait: one block arms a barrier for 16
+// bytes of copies that are never issued, waits on it like the moments'
+// staging does, and records the timeout in the status word.
+__global__ void k_wait_selftest(int *status, unsigned long long wait_ns) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        mbar_arrive_expect(smem_u32(&bar), 16);
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(smem_u32(&bar), 0, wait_ns);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+}
+
+cudaError_t launch_wait_selftest(int *status, double limit_ms, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(status, (unsigned long long)(limit_ms * 1e6));
     return cudaGetLastError();
 }
 
