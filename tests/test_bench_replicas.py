@@ -1,9 +1,10 @@
-"""Host logic of the benchmark's N > 1 path, on CPU: the tracking step does not
-shard (one bunch's kick needs the whole bunch's charge), so N GPUs run N
-independent replicas and the job's throughput is all ranks' particle-steps
-over the slowest rank's time.  These tests run that reduction over
-torch.distributed with the gloo backend at world size 2, and check that the
-reference arm's other ranks exit without work or output."""
+"""Host logic of the benchmark, on CPU.  With N > 1 ranks the bench tracks one
+bunch sharded over the ranks (each holds its share of the particles), and the
+job's throughput is all ranks' particle-steps over the slowest rank's time.
+These tests run that reduction over torch.distributed with the gloo backend at
+world size 2, check that the reference arm's other ranks exit without work or
+output, and that the CPU baseline's all-cores run of the oracle (its functions
+over particle chunks in worker processes) tracks like the oracle itself."""
 import os
 import socket
 import subprocess
@@ -70,3 +71,31 @@ def test_reference_arm_other_ranks_exit_quietly():
                        env=env, capture_output=True, text=True, timeout=280, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+@pytest.mark.timeout(300)
+def test_oracle_on_cores_tracks_like_the_oracle():
+    """bench.OracleOnCores (two worker processes) against oracle.track.Tracker:
+    the same regrid log and coordinates to rounding (the chunk grids are summed
+    in chunk order, the only change of operation order)."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    import beamgen as bg
+    from oracle import physics as ph
+    from oracle import track as tr
+    w = bg.workload("fodo_1e4_32")
+    w.n_grid = 16
+    c = w.particles(3001)
+    sp = w.species
+    t = tr.Tracker(ph.RefPart(sp.mass_MeV, sp.kinetic_MeV, sp.charge_sign), w.bunch_charge_C, 16)
+    want = t.track(c, w.lattice, 0, 9)
+    o = bench.OracleOnCores(w, c, 2)
+    try:
+        o.track(w.lattice, 0, 9)
+        got = o.C.copy()
+    finally:
+        o.close()
+    assert o.regrid_log == t.regrid_log
+    rms = np.sqrt(np.mean(want ** 2, axis=1))[:, None]
+    assert np.max(np.abs(got - want) / np.maximum(np.abs(want), rms)) < 1e-13
