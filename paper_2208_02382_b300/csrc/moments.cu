@@ -25,6 +25,7 @@
 // state is kept between calls.
 #include "common.cuh"
 #include "dd.cuh"
+#include "tma.cuh"
 
 namespace bt {
 
@@ -125,58 +126,6 @@ __device__ __forceinline__ long long mad_wide_u(unsigned a, unsigned b, long lon
     long long d;
     asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(acc));
     return d;
-}
-
-// ---- bulk asynchronous copies (TMA) completing on an mbarrier ----------------
-__device__ __forceinline__ unsigned smem_u32(const void *p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-}
-// The producer's arrival, announcing `bytes` of copies that complete on the barrier.
-__device__ __forceinline__ void mbar_arrive_expect(unsigned bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
-    return t;
-}
-// Wait for the completion of phase `parity` of the barrier; false once
-// limit_ns of global time (or 2^24 polls) went by without it.
-__device__ bool mbar_wait(unsigned bar, unsigned parity, unsigned long long limit_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (unsigned it = 1; it < (1u << 24); ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 15) == 0 && global_ns() - t0 > limit_ns) return false;
-    }
-    return false;
-}
-// `bytes` (a multiple of 16, both addresses 16-byte aligned) from global to
-// shared memory, completing on the barrier.
-__device__ __forceinline__ void bulk_copy_g2s(unsigned dst, const void *src, unsigned bytes,
-                                              unsigned bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
 
 // The block's chunks of 1024 particles (chunk blockIdx.x + j gridDim.x for

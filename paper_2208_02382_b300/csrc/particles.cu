@@ -11,6 +11,8 @@
 // the linear map, and adding the kick.  Cell indices, CIC fractions and
 // weights, the field interpolation, the charge accumulation and the min/max
 // run in 64-bit fixed point on the integer pipes.
+#include <algorithm>
+#include <cstdint>
 #include <type_traits>
 
 #include "common.cuh"
@@ -657,6 +659,50 @@ __device__ __forceinline__ long long mulfrac52(long long e, Frac W) {
 bool box_needs_exact_u(const Box &b) { return box_far_offset(b); }
 
 
+// CIC interpolation of the fixed-point field at a particle in cell (c0, c1,
+// c2) with 53-bit offsets G0..G2, in lerp form: along x on the four (y, z)
+// edges of the cell, then y, then z; a node's x and y components in one
+// 16-byte load, z in one 8-byte load.
+__device__ __forceinline__ void cic_field(const EFix *__restrict__ ef, int nn, int c0, int c1,
+                                          int c2, unsigned long long G0, unsigned long long G1,
+                                          unsigned long long G2, long long comp[3]) {
+    const Frac F0 = split26(G0), F1 = split26(G1), F2 = split26(G2);
+    const EFix *e = &ef[((long long)c2 * nn + c1) * nn + c0];
+    const long long ny = nn, nz = (long long)nn * nn;
+    long long gxy[2][4], gz[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const EFix *q = e + (k & 1) * ny + (k >> 1) * nz;
+        const longlong2 p0 = __ldg((const longlong2 *)q), p1 = __ldg((const longlong2 *)(q + 1));
+        gxy[0][k] = lerp52(p0.x, p1.x, F0);
+        gxy[1][k] = lerp52(p0.y, p1.y, F0);
+        gz[k] = lerp52(__ldg(&q->z), __ldg(&q[1].z), F0);
+    }
+    comp[0] = lerp52(lerp52(gxy[0][0], gxy[0][1], F1), lerp52(gxy[0][2], gxy[0][3], F1), F2);
+    comp[1] = lerp52(lerp52(gxy[1][0], gxy[1][1], F1), lerp52(gxy[1][2], gxy[1][3], F1), F2);
+    comp[2] = lerp52(lerp52(gz[0], gz[1], F1), lerp52(gz[2], gz[3], F1), F2);
+}
+
+// A particle's cells and offsets from the deposit's three cell codes, the
+// cells limited to the shape's range (as the deposit's are), so that a kick
+// halted before any deposit still reads inside the field.
+template <int SH>
+__device__ __forceinline__ void decode_cells(unsigned long long k0, unsigned long long k1,
+                                             unsigned long long k2, int nn, int &c0, int &c1,
+                                             int &c2, unsigned long long &G0,
+                                             unsigned long long &G1, unsigned long long &G2,
+                                             bool &out) {
+    constexpr unsigned long long FM = (1ull << 53) - 1;
+    constexpr int CLO = SH == 2 ? 1 : 0;
+    out = ((k0 | k1 | k2) >> 63) != 0;
+    c0 = min(max((int)((k0 >> 53) & 1023), CLO), nn - 2);
+    c1 = min(max((int)((k1 >> 53) & 1023), CLO), nn - 2);
+    c2 = min(max((int)((k2 >> 53) & 1023), CLO), nn - 2);
+    G0 = k0 & FM;
+    G1 = k1 & FM;
+    G2 = k2 & FM;
+}
+
 // GATHER: interpolation of the fixed-point field at the current position
 //         (SH 1: CIC in lerp form; SH 2: TSC, separable sums of fixed-point
 //         products), kick, then the map (MK) and the store.
@@ -701,6 +747,33 @@ __global__ void __launch_bounds__(TPB, (UL && SH == 1) ? 5 : (SH == 1 && !(DEP &
     int blo[3] = {INT_MAX, INT_MAX, INT_MAX}, bhi[3] = {INT_MIN, INT_MIN, INT_MIN};
     bool bad = false, outside = false;
     const int64_t base = (int64_t)blockIdx.x * CHUNK;
+    if constexpr (GATHER && UL) {
+        // the block's rows (six coordinates, three cell codes) into L2 by bulk
+        // prefetches, so that the loads of its later iterations hit L2
+        if (threadIdx.x < 9 && base < a.n) {
+            const int k = threadIdx.x;
+            const void *row = k == 0 ? (const void *)a.x : k == 1 ? (const void *)a.px
+                            : k == 2 ? (const void *)a.y : k == 3 ? (const void *)a.py
+                            : k == 4 ? (const void *)a.t : k == 5 ? (const void *)a.pt
+                                     : (const void *)(a.cell_in + (k - 6) * a.n);
+            const char *src = (const char *)row + base * 8;
+            const unsigned bytes = (unsigned)(min((int64_t)CHUNK, a.n - base) & ~1ll) * 8u;
+            if (((uintptr_t)src & 15u) == 0 && bytes)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes)
+                             : "memory");
+        }
+    }
+    if constexpr (DEP && !GATHER && MK == MAP_NONE) {
+        // the deposit's rows (x, y, t) into L2 by bulk prefetches
+        if (threadIdx.x < 3 && base < a.n) {
+            const double *row = threadIdx.x == 0 ? a.x : threadIdx.x == 1 ? a.y : a.t;
+            const char *src = (const char *)(row + base);
+            const unsigned bytes = (unsigned)(min((int64_t)CHUNK, a.n - base) & ~1ll) * 8u;
+            if (((uintptr_t)src & 15u) == 0 && bytes)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes)
+                             : "memory");
+        }
+    }
     if (DEP) __syncthreads();
     bool dep_on = DEP;                                  // uniform over the grid
     if constexpr (DEP) dep_on = !a.dep_if || *a.dep_if != 0;
@@ -723,19 +796,8 @@ __global__ void __launch_bounds__(TPB, (UL && SH == 1) ? 5 : (SH == 1 && !(DEP &
                 bool out0 = false;
                 if constexpr (UL) {
                     // the cells the deposit of these positions into this box computed
-                    constexpr unsigned long long FM = (1ull << 53) - 1;
-                    const unsigned long long k0 = a.cell_in[p], k1 = a.cell_in[a.n + p],
-                                             k2 = a.cell_in[2 * a.n + p];
-                    out0 = ((k0 | k1 | k2) >> 63) != 0;
-                    // limited to the shape's range (as the deposit's are), so that a
-                    // kick halted before any deposit still reads inside the field
-                    constexpr int CLO = SH == 2 ? 1 : 0;
-                    c0 = min(max((int)((k0 >> 53) & 1023), CLO), nn - 2);
-                    c1 = min(max((int)((k1 >> 53) & 1023), CLO), nn - 2);
-                    c2 = min(max((int)((k2 >> 53) & 1023), CLO), nn - 2);
-                    G0 = k0 & FM;
-                    G1 = k1 & FM;
-                    G2 = k2 & FM;
+                    decode_cells<SH>(a.cell_in[p], a.cell_in[a.n + p], a.cell_in[2 * a.n + p], nn,
+                                     c0, c1, c2, G0, G1, G2, out0);
                 } else {
                     const double u0 = EX ? (x - lo0) * ih0 : fma(x, ih0, o0);
                     const double u1 = EX ? (y - lo1) * ih1 : fma(y, ih1, o1);
@@ -789,25 +851,8 @@ __global__ void __launch_bounds__(TPB, (UL && SH == 1) ? 5 : (SH == 1 && !(DEP &
                     comp[1] = gz[1];
                     comp[2] = gz[2];
                 } else {
-                    const Frac F0 = split26(G0), F1 = split26(G1), F2 = split26(G2);
                     outside |= out0;
-                    // CIC interpolation in lerp form: along x on the four (y, z) edges
-                    // of the cell, then y, then z.
-                    const EFix *e = &a.ef[((long long)c2 * nn + c1) * nn + c0];
-                    const long long ny = nn, nz = (long long)nn * nn;
-                    // x and y components of a node in one 16-byte load, z in one 8-byte load
-                    long long gxy[2][4], gz[4];
-    #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const EFix *q = e + (k & 1) * ny + (k >> 1) * nz;
-                        const longlong2 p0 = __ldg((const longlong2 *)q), p1 = __ldg((const longlong2 *)(q + 1));
-                        gxy[0][k] = lerp52(p0.x, p1.x, F0);
-                        gxy[1][k] = lerp52(p0.y, p1.y, F0);
-                        gz[k] = lerp52(__ldg(&q->z), __ldg(&q[1].z), F0);
-                    }
-                    comp[0] = lerp52(lerp52(gxy[0][0], gxy[0][1], F1), lerp52(gxy[0][2], gxy[0][3], F1), F2);
-                    comp[1] = lerp52(lerp52(gxy[1][0], gxy[1][1], F1), lerp52(gxy[1][2], gxy[1][3], F1), F2);
-                    comp[2] = lerp52(lerp52(gz[0], gz[1], F1), lerp52(gz[2], gz[3], F1), F2);
+                    cic_field(a.ef, nn, c0, c1, c2, G0, G1, G2, comp);
                 }
                 const long long ex = comp[0], ey = comp[1], ez = comp[2];
                 px += i64_scaled_to_double(ex, e0);
