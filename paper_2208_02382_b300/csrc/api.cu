@@ -241,7 +241,8 @@ int32_t track_impl(bx_ctx *ctx, bx_beam *beam, const bx_lattice *lat, int64_t fi
        "call init");
     if (binning) CK(sort_set_pointers(c, ctx->scr, ctx->dev_ptrs, s), "sort pointers");
     CK(launch_track_prologue(c, beam->n, r.bg, &ctx->st->box, ctx->n, ctx->maps, ctx->acc_hi,
-                             ctx->acc_lo, ctx->st, ctx->status, s, ctx->shape, shared_cells(ctx)),
+                             ctx->acc_lo, ctx->st, ctx->status, s, ctx->shape, shared_cells(ctx),
+                             tab.data()),
        "prologue");
     const KickArgs ka{ctx, c, beam->id, beam->n, r.bg, binning};
     if (sharded) {

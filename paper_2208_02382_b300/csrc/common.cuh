@@ -197,7 +197,8 @@ cudaError_t launch_call_init(TrackState *st, int nkicks, double q_macro, int sor
 cudaError_t launch_track_prologue(double *const c[6], int64_t n, double betagamma, const Box *box,
                                   int nn, const MapCoef *maps, unsigned long long *acc_hi,
                                   unsigned long long *acc_lo, TrackState *st, int32_t *status,
-                                  cudaStream_t s, int shape, unsigned long long *cells = nullptr);
+                                  cudaStream_t s, int shape, unsigned long long *cells = nullptr,
+                                  const MapCoef *map0 = nullptr);
 cudaError_t launch_zero_acc(unsigned long long *a, unsigned long long *b, int nn, const int *gate,
                             cudaStream_t s);
 cudaError_t launch_track_particles(double *const c[6], int64_t n, double betagamma,

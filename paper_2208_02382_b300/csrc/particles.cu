@@ -715,9 +715,10 @@ __device__ __forceinline__ void decode_cells(unsigned long long k0, unsigned lon
 // CIC instances fit 64 registers and (with 52 KB of shared memory for DEP) run 4 blocks
 // per SM; the CIC gather that loads the deposit's cells fits 48 and runs 5 (its
 // field loads are latency-bound); TSC instances and the map-plus-deposit
-// prologue keep 3 (they would spill at 64).
+// prologue with the map table's run-time dispatch keep 3 (they would spill at
+// 64); the prologue compiled for one map class fits 64 and runs 4.
 template <int MK, bool GATHER, bool DEP, bool MM, int SH, bool UL = false, bool SPREAD = false>
-__global__ void __launch_bounds__(TPB, (UL && SH == 1) ? 5 : (SH == 1 && !(DEP && MK != MAP_NONE)) ? 4 : 3)
+__global__ void __launch_bounds__(TPB, (UL && SH == 1) ? 5 : (SH == 1 && !(DEP && MK == MAP_TABLE)) ? 4 : 3)
     k_particles(PartArgs a) {
     if (a.gate && *a.gate == 0) return;
     if (a.dst) a.exact_u = a.dst->exact_u;
@@ -1202,7 +1203,8 @@ cudaError_t launch_track_particles_oop(double *const cin[6], double *const cout[
 cudaError_t launch_track_prologue(double *const c[6], int64_t n, double betagamma, const Box *box,
                                   int nn, const MapCoef *maps, unsigned long long *acc_hi,
                                   unsigned long long *acc_lo, TrackState *st, int32_t *status,
-                                  cudaStream_t s, int shape, unsigned long long *cells) {
+                                  cudaStream_t s, int shape, unsigned long long *cells,
+                                  const MapCoef *map0) {
     cudaError_t e = launch_zero_acc(acc_hi, acc_lo, nn, &st->pro_dep, s);
     if (e != cudaSuccess || n <= 0) return e;
     PartArgs a = part_args(c, n, betagamma, box, nn, shape);
@@ -1214,7 +1216,16 @@ cudaError_t launch_track_prologue(double *const c[6], int64_t n, double betagamm
     a.status = status;
     a.dep_if = &st->pro_dep;
     a.cell_out = cells;
-    return launch_pk<MAP_TABLE, false, true, true>(a, s, K_PUSH);
+    // with the host's copy of table entry 0, a kernel compiled for its map
+    // class (by value, fewer registers than the table's run-time dispatch)
+    const int k0 = map0 ? (int)map0->kind : -1;
+    if (k0 == MAP_DRIFT || k0 == MAP_QUAD || k0 == MAP_GENERAL) a.map = *map0;
+    switch (k0) {
+        case MAP_DRIFT: return launch_pk<MAP_DRIFT, false, true, true>(a, s, K_PUSH);
+        case MAP_QUAD: return launch_pk<MAP_QUAD, false, true, true>(a, s, K_PUSH);
+        case MAP_GENERAL: return launch_pk<MAP_GENERAL, false, true, true>(a, s, K_PUSH);
+        default: return launch_pk<MAP_TABLE, false, true, true>(a, s, K_PUSH);
+    }
 }
 
 // Device-driven deposit of the current positions when the box rule asks for it.
