@@ -42,6 +42,23 @@ int map_kind(const MapCoef &m) {
 
 // --------------------------------------------------- min/max and push only
 
+// Warp minimum / maximum of a signed 64-bit value from two 32-bit warp
+// reductions (redux): the extreme high word, then the extreme low word among
+// the lanes holding it (signed 64-bit order is that of (signed high, unsigned
+// low)).  All 32 lanes must call them.
+__device__ __forceinline__ long long warp_min_i64(long long v) {
+    const int h = (int)(v >> 32);
+    const int mh = __reduce_min_sync(0xffffffffu, h);
+    const unsigned ml = __reduce_min_sync(0xffffffffu, h == mh ? (unsigned)v : 0xFFFFFFFFu);
+    return (long long)(((unsigned long long)(unsigned)mh << 32) | ml);
+}
+__device__ __forceinline__ long long warp_max_i64(long long v) {
+    const int h = (int)(v >> 32);
+    const int mh = __reduce_max_sync(0xffffffffu, h);
+    const unsigned ml = __reduce_max_sync(0xffffffffu, h == mh ? (unsigned)v : 0u);
+    return (long long)(((unsigned long long)(unsigned)mh << 32) | ml);
+}
+
 // Block min/max of order-preserving keys, folded into the state with integer
 // atomics (exact, order-free).  All threads of the block must call it.
 __device__ __forceinline__ void block_keys_commit(long long lo[3], long long hi[3],
@@ -50,11 +67,7 @@ __device__ __forceinline__ void block_keys_commit(long long lo[3], long long hi[
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        long long a = lo[d], b = hi[d];
-        for (int o = 16; o > 0; o >>= 1) {
-            a = min(a, __shfl_xor_sync(0xffffffffu, a, o));
-            b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
-        }
+        const long long a = warp_min_i64(lo[d]), b = warp_max_i64(hi[d]);
         if (lane == 0) {
             s_lo[d][w] = a;
             s_hi[d][w] = b;
@@ -937,11 +950,8 @@ __global__ void __launch_bounds__(TPB, (UL && SH == 1) ? 5 : (SH == 1 && !(DEP &
         if (!dep_on) return;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            int l = blo[d], h = bhi[d];
-            for (int o = 16; o > 0; o >>= 1) {
-                l = min(l, __shfl_xor_sync(0xffffffffu, l, o));
-                h = max(h, __shfl_xor_sync(0xffffffffu, h, o));
-            }
+            const int l = __reduce_min_sync(0xffffffffu, blo[d]);
+            const int h = __reduce_max_sync(0xffffffffu, bhi[d]);
             if ((threadIdx.x & 31) == 0) {
                 atomicMin(&s_bb[d], l);
                 atomicMax(&s_bb[3 + d], h);
