@@ -761,27 +761,25 @@ __global__ void __launch_bounds__(TPB, (UL && SH == 1) ? 5 : (SH == 1 && !(DEP &
     int blo[3] = {INT_MAX, INT_MAX, INT_MAX}, bhi[3] = {INT_MIN, INT_MIN, INT_MIN};
     bool bad = false, outside = false;
     const int64_t base = (int64_t)blockIdx.x * CHUNK;
-    if constexpr (GATHER && UL) {
-        // the block's rows (six coordinates, three cell codes) into L2 by bulk
-        // prefetches, so that the loads of its later iterations hit L2
-        if (threadIdx.x < 9 && base < a.n) {
+    {
+        // the rows this block reads (its CHUNK particles) into L2 by bulk
+        // prefetches, one per row, so that the loads of its later iterations
+        // hit L2: the six coordinates where a map is applied or a gather runs
+        // (x, y, t only for a deposit alone), and the cell codes a gather reads
+        constexpr bool ALL6 = GATHER || MK != MAP_NONE;
+        constexpr int NROW = (ALL6 ? 6 : 3) + (GATHER && UL ? 3 : 0);
+        if ((DEP || (GATHER && UL)) && threadIdx.x < NROW && base < a.n) {
             const int k = threadIdx.x;
-            const void *row = k == 0 ? (const void *)a.x : k == 1 ? (const void *)a.px
-                            : k == 2 ? (const void *)a.y : k == 3 ? (const void *)a.py
-                            : k == 4 ? (const void *)a.t : k == 5 ? (const void *)a.pt
-                                     : (const void *)(a.cell_in + (k - 6) * a.n);
+            const void *row;
+            if (ALL6 && k < 6)
+                row = k == 0 ? (const void *)a.x : k == 1 ? (const void *)a.px
+                    : k == 2 ? (const void *)a.y : k == 3 ? (const void *)a.py
+                    : k == 4 ? (const void *)a.t : (const void *)a.pt;
+            else if (!ALL6)
+                row = k == 0 ? (const void *)a.x : k == 1 ? (const void *)a.y : (const void *)a.t;
+            else
+                row = (const void *)(a.cell_in + (k - 6) * a.n);
             const char *src = (const char *)row + base * 8;
-            const unsigned bytes = (unsigned)(min((int64_t)CHUNK, a.n - base) & ~1ll) * 8u;
-            if (((uintptr_t)src & 15u) == 0 && bytes)
-                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes)
-                             : "memory");
-        }
-    }
-    if constexpr (DEP && !GATHER && MK == MAP_NONE) {
-        // the deposit's rows (x, y, t) into L2 by bulk prefetches
-        if (threadIdx.x < 3 && base < a.n) {
-            const double *row = threadIdx.x == 0 ? a.x : threadIdx.x == 1 ? a.y : a.t;
-            const char *src = (const char *)(row + base);
             const unsigned bytes = (unsigned)(min((int64_t)CHUNK, a.n - base) & ~1ll) * 8u;
             if (((uintptr_t)src & 15u) == 0 && bytes)
                 asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes)
