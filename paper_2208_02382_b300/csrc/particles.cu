@@ -794,7 +794,11 @@ __global__ void __launch_bounds__(TPB, (UL && SH == 1) ? 5 : (SH == 1 && !(DEP &
     // copies of the particle loop, so each copy does only its own arithmetic
     auto particle_loop = [&](auto exact_tag) {
         constexpr bool EX = decltype(exact_tag)::value;
-    #pragma unroll 1
+        // the deposit alone (CIC) fully unrolled: 0.523 -> 0.507 ms at 2.5e7
+        // particles, no spills at 64 registers; the others keep one
+        // particle in flight per thread (register budget)
+        constexpr int UNR = (DEP && !GATHER && MK == MAP_NONE && SH == 1) ? PPT : 1;
+    #pragma unroll UNR
         for (int it = 0; it < PPT; ++it) {
             const int slot = it * TPB + threadIdx.x;
             const int64_t p = base + slot;
