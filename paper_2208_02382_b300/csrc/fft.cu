@@ -545,10 +545,10 @@ __global__ void k_twiddle(double2 *tw, int m) {
 
 // Blocks per SM the fixed-point passes are compiled for (latency-bound passes
 // whose registers are mostly the line's values): where a thread holds at most
-// 8 values of its line, four for the x passes and the fused z solve and three
-// for the y passes (measured at 128^3: x 0.038 -> 0.035 ms, z solve 0.246 ->
-// 0.238, inverse x 0.052 -> 0.047 with four; the y passes ran 0.156 -> 0.160
-// with four, a few spilled words); else two.  `strided`: a y pass.
+// 8 values of its line, four, except three for the inverse y pass (measured at
+// 128^3: x 0.038 -> 0.035 ms, z solve 0.246 -> 0.238, inverse x 0.052 ->
+// 0.047, forward y 2 us faster with four; the inverse y pass ran slower with
+// four, a few spilled words); else two.  `strided`: the inverse y pass.
 template <int M, bool strided = false>
 constexpr int fixq_blocks() { return M / Shape<M>::T <= 8 ? (strided ? 3 : 4) : 2; }
 
@@ -777,7 +777,7 @@ __global__ void __launch_bounds__(FFT_TPB, fixq_blocks<M>()) k_fftq_x_fwd_d(cons
 // inverse y).  Element e of line (o, kx) has exponent
 // ein[o*ein_o + e*ein_e + kx*ein_k]; the line's exponent goes to eout[o*P + kx].
 template <int M, int MODE>
-__global__ void __launch_bounds__(FFT_TPB, fixq_blocks<M, MODE != MODE_ZSOLVE>()) k_fftq_lines(const longlong2 *__restrict__ in,
+__global__ void __launch_bounds__(FFT_TPB, fixq_blocks<M, MODE == MODE_INV>()) k_fftq_lines(const longlong2 *__restrict__ in,
                                                         long long in_o, long long in_e, int ne_in,
                                                         const int *__restrict__ ein, long long ein_o,
                                                         long long ein_e, long long ein_k,
