@@ -588,8 +588,25 @@ __device__ __forceinline__ long long team_max(long long v, long long *red) {
     }
     return v;
 }
+// The largest of a 32-bit value over a line team: one warp redux for a team
+// of 32 lanes, the shuffle tree of team_max otherwise.
+template <int T>
+__device__ __forceinline__ int team_max_i32(int v, long long *red) {
+    if constexpr (T == 32) return __reduce_max_sync(0xffffffffu, v);
+    else return (int)team_max<T>(v, red);
+}
+
 template <int T>
 __device__ __forceinline__ unsigned long long team_sum(unsigned long long v, long long *red) {
+    if constexpr (T == 32) {
+        // two 32-bit warp reductions, exact for per-lane values below 2^54: 32
+        // low parts of 27 bits, and 32 high parts v >> 27 below 2^27, each sum
+        // below 2^32 (a lane's share of a line's L1 bound is at most 8 terms of
+        // (|re| + |im|) 2^-16 + 1 with |re|, |im| <= 2^60, below 2^49)
+        const unsigned lo = __reduce_add_sync(0xffffffffu, (unsigned)(v & 0x7FFFFFFull));
+        const unsigned hi = __reduce_add_sync(0xffffffffu, (unsigned)(v >> 27));
+        return ((unsigned long long)hi << 27) + lo;
+    }
     constexpr int W = T < 32 ? T : 32;
 #pragma unroll
     for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -677,7 +694,7 @@ __global__ void __launch_bounds__(FFT_TPB, fixq_blocks<M>()) k_fftq_x_fwd(const 
             vb[i] = (live && e < n) ? acc_value(acc_hi, acc_lo, row + n + e) : 0;
             mb = max(mb, max(bitlen128(va[i]), bitlen128(vb[i])));
         }
-    mb = (int)team_max<T>(mb, red);
+    mb = team_max_i32<T>(mb, red);
     constexpr int LGM = M == 16 ? 4 : M == 32 ? 5 : M == 64 ? 6 : M == 128 ? 7 : M == 256 ? 8 : 9;
     const int sh = mb + LGM - 60;
     longlong2 v[V];
@@ -752,7 +769,7 @@ __global__ void __launch_bounds__(FFT_TPB, fixq_blocks<M>()) k_fftq_x_fwd_d(cons
             const int fb = (int)(((unsigned long long)__double_as_longlong(vb[i]) >> 52) & 0x7FF);
             ef = max(ef, max(fa, fb));
         }
-    ef = (int)team_max<T>(ef, red);
+    ef = team_max_i32<T>(ef, red);
     constexpr int LGM = M == 16 ? 4 : M == 32 ? 5 : M == 64 ? 6 : M == 128 ? 7 : M == 256 ? 8 : 9;
     // |value| < 2^(ef - 1022); L1 < 2m 2^(ef - 1022) <= 2^60 after the shift
     const int sh = (ef - 1022) + LGM + 1 - 60;
@@ -812,7 +829,7 @@ __global__ void __launch_bounds__(FFT_TPB, fixq_blocks<M, MODE == MODE_INV>()) k
             const int e = first_index<M>(t, j, m);
             if (live && e < ne_in) emax = max(emax, __ldg(&esrc[e * ein_e]));
         }
-    emax = (int)team_max<T>(emax, red);
+    emax = team_max_i32<T>(emax, red);
 #pragma unroll
     for (int j = 0; j < U0; ++j)
 #pragma unroll
@@ -890,7 +907,7 @@ __global__ void __launch_bounds__(FFT_TPB, fixq_blocks<M>()) k_fftq_x_inv(const 
             const int e = first_index<M>(t, j, m);
             if (live) emax = max(emax, __ldg(&er[e <= n ? e : M - e]));
         }
-    emax = (int)team_max<T>(emax, red);
+    emax = team_max_i32<T>(emax, red);
 #pragma unroll
     for (int j = 0; j < U0; ++j)
 #pragma unroll
