@@ -27,11 +27,12 @@ struct MapCoef {
 
 // Map structure classes (see MapCoef): drift (x += m01 px, y += m23 py,
 // t += m45 pt), no dispersion (2x2 blocks and the t-pt term), general;
-// MAP_TABLE selects the per-call table in the particle kernels; MAP_SPLIT
-// (stored kind only): two linear parts with thin multipoles between them, in
-// the entry's SplitRec.
+// MAP_BEND: general in x, px, t with a drift in y (y += m23 py, py unchanged:
+// the merged half maps inside a sector bend); MAP_TABLE selects the per-call
+// table in the particle kernels; MAP_SPLIT (stored kind only): two linear parts
+// with thin multipoles between them, in the entry's SplitRec.
 enum MapKind { MAP_NONE = 0, MAP_DRIFT = 1, MAP_QUAD = 2, MAP_GENERAL = 3, MAP_TABLE = 4,
-               MAP_SPLIT = 5 };
+               MAP_SPLIT = 5, MAP_BEND = 6 };
 
 // Thin multipoles of orders 1..MP_MAX: kick polynomial terms z^0..z^(MP_MAX-1).
 constexpr int MP_MAX = 12;

@@ -24,6 +24,14 @@ __device__ __forceinline__ void apply_map_k(const MapCoef &m, double &x, double 
         px = npx;
         y = ny;
         py = npy;
+    } else if constexpr (MK == MAP_BEND) {
+        double nx = m.m00 * x + m.m01 * px + m.m05 * pt;
+        double npx = m.m10 * x + m.m11 * px + m.m15 * pt;
+        double nt = t + m.m40 * x + m.m41 * px + m.m45 * pt;
+        y = fma(m.m23, py, y);
+        x = nx;
+        px = npx;
+        t = nt;
     } else if constexpr (MK == MAP_GENERAL) {
         double nx = m.m00 * x + m.m01 * px + m.m05 * pt;
         double npx = m.m10 * x + m.m11 * px + m.m15 * pt;
@@ -74,6 +82,7 @@ __device__ __forceinline__ void apply_map_table(const MapCoef &m, const MapCoef 
     const int k = (int)m.kind;
     if (k == MAP_DRIFT) apply_map_k<MAP_DRIFT>(m, x, px, y, py, t, pt);
     else if (k == MAP_QUAD) apply_map_k<MAP_QUAD>(m, x, px, y, py, t, pt);
+    else if (k == MAP_BEND) apply_map_k<MAP_BEND>(m, x, px, y, py, t, pt);
     else if (k == MAP_SPLIT) apply_split(*split_rec(row), x, px, y, py, t, pt);
     else apply_map_k<MAP_GENERAL>(m, x, px, y, py, t, pt);
 }

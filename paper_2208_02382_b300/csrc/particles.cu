@@ -37,6 +37,7 @@ int map_kind(const MapCoef &m) {
             return MAP_DRIFT;
         return MAP_QUAD;
     }
+    if (m.m22 == 1.0 && m.m32 == 0.0 && m.m33 == 1.0) return MAP_BEND;
     return MAP_GENERAL;
 }
 
@@ -1124,6 +1125,7 @@ cudaError_t launch_kick_push_deposit(double *const c[6], int64_t n, double betag
         case MAP_NONE: e = launch_pk<MAP_NONE, true, false, false>(a, s, K_GATHER); break;
         case MAP_DRIFT: e = launch_pk<MAP_DRIFT, true, false, false>(a, s, K_GATHER); break;
         case MAP_QUAD: e = launch_pk<MAP_QUAD, true, false, false>(a, s, K_GATHER); break;
+        case MAP_BEND: e = launch_pk<MAP_BEND, true, false, false>(a, s, K_GATHER); break;
         default: e = launch_pk<MAP_GENERAL, true, false, false>(a, s, K_GATHER); break;
     }
     if (e != cudaSuccess || !deposit) return e;
@@ -1231,11 +1233,12 @@ cudaError_t launch_track_prologue(double *const c[6], int64_t n, double betagamm
     // with the host's copy of table entry 0, a kernel compiled for its map
     // class (by value, fewer registers than the table's run-time dispatch)
     const int k0 = map0 ? (int)map0->kind : -1;
-    if (k0 == MAP_DRIFT || k0 == MAP_QUAD || k0 == MAP_GENERAL) a.map = *map0;
+    if (k0 == MAP_DRIFT || k0 == MAP_QUAD || k0 == MAP_GENERAL || k0 == MAP_BEND) a.map = *map0;
     switch (k0) {
         case MAP_DRIFT: return launch_pk<MAP_DRIFT, false, true, true>(a, s, K_PUSH);
         case MAP_QUAD: return launch_pk<MAP_QUAD, false, true, true>(a, s, K_PUSH);
         case MAP_GENERAL: return launch_pk<MAP_GENERAL, false, true, true>(a, s, K_PUSH);
+        case MAP_BEND: return launch_pk<MAP_BEND, false, true, true>(a, s, K_PUSH);
         default: return launch_pk<MAP_TABLE, false, true, true>(a, s, K_PUSH);
     }
 }
