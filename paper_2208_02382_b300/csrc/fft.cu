@@ -28,7 +28,9 @@
 //    sincospi), and exchanges values through its own shared-memory line buffer
 //    between radix steps; a team of at most 32 threads (lines of up to 256
 //    points) synchronises with a warp barrier only, so the block's lines run
-//    independently.
+//    independently; a team's reductions (the block-floating-point exponent
+//    maximum and L1 norm of its line) are warp redux instructions for a team of
+//    one warp and shuffle trees for smaller teams.
 #include <algorithm>
 #include <climits>
 
