@@ -799,10 +799,30 @@ __global__ void __launch_bounds__(TPB, (UL && SH == 1) ? 5 : (SH == 1 && !(DEP &
         // particles, no spills at 64 registers; the others keep one
         // particle in flight per thread (register budget)
         constexpr int UNR = (DEP && !GATHER && MK == MAP_NONE && SH == 1) ? PPT : 1;
+        // UL gather: the next particle's cell codes are loaded one iteration
+        // ahead, so that its field loads need not wait for them
+        unsigned long long nk0 = 0, nk1 = 0, nk2 = 0;
+        if constexpr (GATHER && UL) {
+            const int64_t p0 = base + threadIdx.x;
+            if (p0 < a.n) {
+                nk0 = a.cell_in[p0];
+                nk1 = a.cell_in[a.n + p0];
+                nk2 = a.cell_in[2 * a.n + p0];
+            }
+        }
     #pragma unroll UNR
         for (int it = 0; it < PPT; ++it) {
             const int slot = it * TPB + threadIdx.x;
             const int64_t p = base + slot;
+            const unsigned long long ck0 = nk0, ck1 = nk1, ck2 = nk2;
+            if constexpr (GATHER && UL) {
+                const int64_t pn = p + TPB;
+                if (it + 1 < PPT && pn < a.n) {
+                    nk0 = a.cell_in[pn];
+                    nk1 = a.cell_in[a.n + pn];
+                    nk2 = a.cell_in[2 * a.n + pn];
+                }
+            }
             if (DEP) scell[slot] = -1;
             if (p >= a.n) continue;
             double x = a.x[p], y = a.y[p], t = a.t[p];
@@ -813,8 +833,7 @@ __global__ void __launch_bounds__(TPB, (UL && SH == 1) ? 5 : (SH == 1 && !(DEP &
                 bool out0 = false;
                 if constexpr (UL) {
                     // the cells the deposit of these positions into this box computed
-                    decode_cells<SH>(a.cell_in[p], a.cell_in[a.n + p], a.cell_in[2 * a.n + p], nn,
-                                     c0, c1, c2, G0, G1, G2, out0);
+                    decode_cells<SH>(ck0, ck1, ck2, nn, c0, c1, c2, G0, G1, G2, out0);
                 } else {
                     const double u0 = EX ? (x - lo0) * ih0 : fma(x, ih0, o0);
                     const double u1 = EX ? (y - lo1) * ih1 : fma(y, ih1, o1);
