@@ -675,8 +675,16 @@ bool box_needs_exact_u(const Box &b) { return box_far_offset(b); }
 
 // CIC interpolation of the fixed-point field at a particle in cell (c0, c1,
 // c2) with 53-bit offsets G0..G2, in lerp form: along x on the four (y, z)
-// edges of the cell, then y, then z; a node's x and y components in one
-// 16-byte load, z in one 8-byte load.
+// edges of the cell, then y, then z; each node's record (x, y, z and a pad
+// word) in one 32-byte load.
+// A node's field record (x, y, z and the pad word) in one 32-byte read-only load.
+__device__ __forceinline__ void ld_efix(const EFix *q, long long &x, long long &y, long long &z) {
+    long long pad;
+    asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+        : "=l"(x), "=l"(y), "=l"(z), "=l"(pad)
+        : "l"(q));
+}
+
 __device__ __forceinline__ void cic_field(const EFix *__restrict__ ef, int nn, int c0, int c1,
                                           int c2, unsigned long long G0, unsigned long long G1,
                                           unsigned long long G2, long long comp[3]) {
@@ -687,10 +695,12 @@ __device__ __forceinline__ void cic_field(const EFix *__restrict__ ef, int nn, i
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const EFix *q = e + (k & 1) * ny + (k >> 1) * nz;
-        const longlong2 p0 = __ldg((const longlong2 *)q), p1 = __ldg((const longlong2 *)(q + 1));
-        gxy[0][k] = lerp52(p0.x, p1.x, F0);
-        gxy[1][k] = lerp52(p0.y, p1.y, F0);
-        gz[k] = lerp52(__ldg(&q->z), __ldg(&q[1].z), F0);
+        long long x0, y0, z0, x1, y1, z1;
+        ld_efix(q, x0, y0, z0);
+        ld_efix(q + 1, x1, y1, z1);
+        gxy[0][k] = lerp52(x0, x1, F0);
+        gxy[1][k] = lerp52(y0, y1, F0);
+        gz[k] = lerp52(z0, z1, F0);
     }
     comp[0] = lerp52(lerp52(gxy[0][0], gxy[0][1], F1), lerp52(gxy[0][2], gxy[0][3], F1), F2);
     comp[1] = lerp52(lerp52(gxy[1][0], gxy[1][1], F1), lerp52(gxy[1][2], gxy[1][3], F1), F2);
@@ -856,7 +866,7 @@ __global__ void __launch_bounds__(TPB, (UL && SH == 1) ? 5 : (SH == 1 && !(DEP &
                     tsc_weights(G1, wy);
                     tsc_weights(G2, wz);
                     // separable: along x on the nine (y, z) lines, then y, then z;
-                    // a node's x, y components in one 16-byte load, z in one 8-byte load
+                    // each node record (x, y, z, pad) in one 32-byte load
                     const EFix *e = &a.ef[((long long)(c2 - 1) * nn + (c1 - 1)) * nn + (c0 - 1)];
                     const long long ny = nn, nz = (long long)nn * nn;
                     long long gz[3] = {0, 0, 0};
@@ -866,16 +876,16 @@ __global__ void __launch_bounds__(TPB, (UL && SH == 1) ? 5 : (SH == 1 && !(DEP &
     #pragma unroll
                         for (int dy = 0; dy < 3; ++dy) {
                             const EFix *q = e + dz * nz + dy * ny;
-                            const longlong2 p0 = __ldg((const longlong2 *)q),
-                                            p1 = __ldg((const longlong2 *)(q + 1)),
-                                            p2 = __ldg((const longlong2 *)(q + 2));
-                            const long long gxx = mulfrac52(p0.x, wx[0]) + mulfrac52(p1.x, wx[1]) +
-                                                  mulfrac52(p2.x, wx[2]);
-                            const long long gxy = mulfrac52(p0.y, wx[0]) + mulfrac52(p1.y, wx[1]) +
-                                                  mulfrac52(p2.y, wx[2]);
-                            const long long gxz = mulfrac52(__ldg(&q[0].z), wx[0]) +
-                                                  mulfrac52(__ldg(&q[1].z), wx[1]) +
-                                                  mulfrac52(__ldg(&q[2].z), wx[2]);
+                            long long x0, y0, z0, x1, y1, z1, x2, y2, z2;
+                            ld_efix(q, x0, y0, z0);
+                            ld_efix(q + 1, x1, y1, z1);
+                            ld_efix(q + 2, x2, y2, z2);
+                            const long long gxx = mulfrac52(x0, wx[0]) + mulfrac52(x1, wx[1]) +
+                                                  mulfrac52(x2, wx[2]);
+                            const long long gxy = mulfrac52(y0, wx[0]) + mulfrac52(y1, wx[1]) +
+                                                  mulfrac52(y2, wx[2]);
+                            const long long gxz = mulfrac52(z0, wx[0]) + mulfrac52(z1, wx[1]) +
+                                                  mulfrac52(z2, wx[2]);
                             gy[0] += mulfrac52(gxx, wy[dy]);
                             gy[1] += mulfrac52(gxy, wy[dy]);
                             gy[2] += mulfrac52(gxz, wy[dy]);
