@@ -207,7 +207,6 @@ __global__ void __launch_bounds__(ATPB) k_adj_kick1(Adj1Args a) {
     cu.init(*a.box, a.nbg);
     const int nn = a.nn;
     const long long n3 = (long long)nn * nn * nn;
-    const long long sy = 4LL * nn, sz = 4LL * nn * nn;
     const unsigned long long one = 1ull << 52;
     double acc[13];
 #pragma unroll
@@ -226,21 +225,31 @@ __global__ void __launch_bounds__(ATPB) k_adj_kick1(Adj1Args a) {
         const Frac F0 = split26(F0u), F1 = split26(F1u), F2 = split26(F2u);
         // the forward's interpolation, and the derivatives of the same
         // trilinear form in u (differences of the integer lerps)
-        const long long *e = &a.ef[((long long)c2 * nn + c1) * nn + c0].x;
+        const EFix *e = &a.ef[((long long)c2 * nn + c1) * nn + c0];
         long long val[3], du[3][3];
+        // the four x edges of the cell (y, z) = (0,0), (1,0), (0,1), (1,1): each
+        // node's record in one 32-byte load, per component the edge's lerp in x
+        // and its difference
+        long long g[3][4], dx[3][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const EFix *q = e + (j & 1) * nn + (j >> 1) * (long long)nn * nn;
+            long long v0[3], v1[3];
+            ld_efix(q, v0[0], v0[1], v0[2]);
+            ld_efix(q + 1, v1[0], v1[1], v1[2]);
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                g[cc][j] = lerp52(v0[cc], v1[cc], F0);
+                dx[cc][j] = v1[cc] - v0[cc];
+            }
+        }
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
-            const long long *q = e + cc;
-            const long long q000 = q[0], q001 = q[4], q010 = q[sy], q011 = q[sy + 4];
-            const long long q100 = q[sz], q101 = q[sz + 4], q110 = q[sz + sy], q111 = q[sz + sy + 4];
-            const long long g00 = lerp52(q000, q001, F0), g01 = lerp52(q010, q011, F0);
-            const long long g10 = lerp52(q100, q101, F0), g11 = lerp52(q110, q111, F0);
-            const long long gy0 = lerp52(g00, g01, F1), gy1 = lerp52(g10, g11, F1);
+            const long long gy0 = lerp52(g[cc][0], g[cc][1], F1), gy1 = lerp52(g[cc][2], g[cc][3], F1);
             val[cc] = lerp52(gy0, gy1, F2);
             du[cc][2] = gy1 - gy0;
-            du[cc][1] = lerp52(g01 - g00, g11 - g10, F2);
-            du[cc][0] = lerp52(lerp52(q001 - q000, q011 - q010, F1),
-                               lerp52(q101 - q100, q111 - q110, F1), F2);
+            du[cc][1] = lerp52(g[cc][1] - g[cc][0], g[cc][3] - g[cc][2], F2);
+            du[cc][0] = lerp52(lerp52(dx[cc][0], dx[cc][1], F1), lerp52(dx[cc][2], dx[cc][3], F1), F2);
         }
         // post-kick state (bitwise the forward's)
         const double qx = x, qpx = px + i64_scaled_to_double(val[0], e0);

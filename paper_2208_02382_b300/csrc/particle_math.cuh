@@ -87,6 +87,17 @@ __device__ __forceinline__ void apply_map_table(const MapCoef &m, const MapCoef 
     else apply_map_k<MAP_GENERAL>(m, x, px, y, py, t, pt);
 }
 
+// A node's field record (x, y, z and the pad word; records are 32-byte
+// aligned) in one 32-byte read-only load: half the load instructions of a
+// 16-byte and an 8-byte load, which the gathers' random node accesses are
+// bound by.
+__device__ __forceinline__ void ld_efix(const EFix *q, long long &x, long long &y, long long &z) {
+    long long pad;
+    asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+        : "=l"(x), "=l"(y), "=l"(z), "=l"(pad)
+        : "l"(q));
+}
+
 // All six finite: the largest exponent field (from the 32-bit high words,
 // combined with integer max so the test stays on the integer pipes) is below
 // the all-ones exponent of Inf/NaN.

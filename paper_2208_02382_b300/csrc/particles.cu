@@ -677,14 +677,6 @@ bool box_needs_exact_u(const Box &b) { return box_far_offset(b); }
 // c2) with 53-bit offsets G0..G2, in lerp form: along x on the four (y, z)
 // edges of the cell, then y, then z; each node's record (x, y, z and a pad
 // word) in one 32-byte load.
-// A node's field record (x, y, z and the pad word) in one 32-byte read-only load.
-__device__ __forceinline__ void ld_efix(const EFix *q, long long &x, long long &y, long long &z) {
-    long long pad;
-    asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
-        : "=l"(x), "=l"(y), "=l"(z), "=l"(pad)
-        : "l"(q));
-}
-
 __device__ __forceinline__ void cic_field(const EFix *__restrict__ ef, int nn, int c0, int c1,
                                           int c2, unsigned long long G0, unsigned long long G1,
                                           unsigned long long G2, long long comp[3]) {
