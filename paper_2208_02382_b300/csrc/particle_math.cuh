@@ -96,6 +96,7 @@ __device__ __forceinline__ void ld_efix(const EFix *q, long long &x, long long &
     asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
         : "=l"(x), "=l"(y), "=l"(z), "=l"(pad)
         : "l"(q));
+    (void)pad;
 }
 
 // All six finite: the largest exponent field (from the 32-bit high words,
