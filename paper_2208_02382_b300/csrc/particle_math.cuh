@@ -92,11 +92,10 @@ __device__ __forceinline__ void apply_map_table(const MapCoef &m, const MapCoef 
 // 16-byte and an 8-byte load, which the gathers' random node accesses are
 // bound by.
 __device__ __forceinline__ void ld_efix(const EFix *q, long long &x, long long &y, long long &z) {
-    long long pad;
+    [[maybe_unused]] long long pad;
     asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
         : "=l"(x), "=l"(y), "=l"(z), "=l"(pad)
         : "l"(q));
-    (void)pad;
 }
 
 // All six finite: the largest exponent field (from the 32-bit high words,
